@@ -1,0 +1,413 @@
+"""Benchmark of the sparse-grid isogeometric solve on GB300.
+
+Workload: 3D Poisson on the unit cube, u = sin(pi x) sin(pi y) sin(pi z),
+p = 3 C^2 B-splines, combination level w = 10 (136 component grids with
+10 <= |i| <= 12, 557,030 DoFs in total), batched FP64 matrix-free operator +
+fast-diagonalisation PCG to relative residual 1e-12, then evaluation of every
+component on the 17^3 parametric lattice and the +-combination sum.
+
+A step = load vector (built-in source) + batched solve + evaluation +
+combination, through the C ABI. `value` is the whole job's DoF/s (sum of
+component DoFs over all ranks / step time); each rank under torchrun solves
+its own replica of the workload (weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sparse-grid IGA solve wall time & DoF/s at 1e-8 L2, learned/mixed vs plain PCG"
+WORKLOAD = dict(d=3, p=3, w=10, domain="unit", source="sine", tol=1e-12, lattice=16)
+WORKLOAD_NAME = ("3D unit-cube Poisson, u=sin(pi x)sin(pi y)sin(pi z), p=3 C^2 B-splines, combination "
+                 "level w=10 (136 grids, 10<=|i|<=12, 557030 DoFs), FP64 matrix-free apply + batched "
+                 "FD-PCG to rel. residual 1e-12, eval+combine on the 17^3 parametric lattice")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
+# components solved by the CPU oracle in its bounded sample (assembly + direct solve + evaluation)
+ORACLE_SAMPLE = [(4, 4, 4), (10, 1, 1), (3, 5, 4), (2, 2, 7)]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (runs in a child process with one BLAS thread)
+# ----------------------------------------------------------------------------
+
+def oracle_sample_child(nrep):
+    from oracle import geometry, problems
+    from oracle.galerkin import Component
+    from paper_1707_09598_gb300.inputs import eval_points
+    pts = eval_points(3, WORKLOAD["lattice"])
+    prob = problems.get("sine3")
+    geom = geometry.UnitCube(3)
+    dofs = 0
+    t0 = time.perf_counter()
+    for rep in range(nrep):
+        lv = ORACLE_SAMPLE[rep % len(ORACLE_SAMPLE)]
+        comp = Component(geom, lv, 3).assemble(f=prob.f)
+        u = comp.solve()
+        comp.evaluate(u, pts)
+        dofs += comp.ndof
+    dt = time.perf_counter() - t0
+    print(json.dumps({"dofs": dofs, "seconds": dt, "components": nrep}))
+
+
+def run_oracle_sample(nrep):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(nrep)],
+                         env=env, capture_output=True, text=True, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling (200 ms) around the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def apply_flops(plan):
+    """Algorithmic FP64 flops of one operator apply: untiled sum factorisation
+    (forward: 2(p+1) + 3(p+1) + 3(p+1) FMA per output of the three stages,
+    pointwise 9 FMA per qp, backward mirrored), best axis order per grid."""
+    import itertools
+    p = plan.info.p
+    P1, Q = p + 1, p + 1
+    total = 0.0
+    for g in plan.grids:
+        E = [2 ** g.levels[k] for k in range(3)]
+        nf = [g.n[k] + 2 for k in range(3)]
+        best = None
+        for a, b, c in itertools.permutations(range(3)):
+            s_c = 2 * P1 * nf[a] * nf[b] * Q * E[c]
+            s_b = 3 * P1 * nf[a] * Q * E[b] * Q * E[c]
+            s_a = 3 * P1 * Q * E[a] * Q * E[b] * Q * E[c]
+            fma = 2 * (s_a + s_b + s_c) + 9 * Q ** 3 * E[0] * E[1] * E[2]
+            best = fma if best is None else min(best, fma)
+        total += 2.0 * best
+    return total
+
+
+def fp64_peak_tflops(torch):
+    """Measured FP64 dense peak: cuBLAS DGEMM 8192^3, best of 5 (TFLOP/s)."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)
+    return {}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle, on host cores
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_step = 1
+    for _ in range(args.warmup):
+        run_oracle_sample(per_step)
+    dofs, secs = 0, 0.0
+    for _ in range(args.steps):
+        r = run_oracle_sample(per_step)
+        dofs += r["dofs"]
+        secs += r["seconds"]
+    value = dofs / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "DoF/s", "cores": 1,
+                         "sample": "per step: one component of the workload (cycling %s), assembly + sparse "
+                                   "direct solve + evaluation on 17^3 points, FP64, one BLAS thread"
+                                   % ORACLE_SAMPLE},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1707_09598_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    from paper_1707_09598_gb300 import sgiga
+    from paper_1707_09598_gb300.inputs import eval_points
+
+    W = WORKLOAD
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    P = sgiga.Plan(W["d"], W["p"], W["w"], domain=W["domain"], stream=stream)
+    plan_s = time.perf_counter() - t0
+    ndof, ng = P.info.ndof, P.info.ngrids
+    pts_h = eval_points(W["d"], W["lattice"])
+    npts = len(pts_h)
+    pts = torch.as_tensor(pts_h, device="cuda")
+    uc = torch.zeros(ng * npts, dtype=torch.float64, device="cuda")
+    u = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    iters = []
+
+    def step():
+        sgiga.sgiga_set_rhs_builtin(P.handle, W["source"])
+        st, _ = sgiga.sgiga_solve(P.handle, W["tol"], 50)
+        iters.append(st.iterations)
+        sgiga.sgiga_eval(P.handle, pts, npts, uc)
+        sgiga.sgiga_combine(P.handle, uc, npts, u)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = sgiga.sgiga_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = sgiga.sgiga_launch_count() - l0
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * ndof / (ms / 1e3)
+
+    # accuracy of the combined solution against the stored oracle values
+    gold = np.loadtxt(GOLDEN)[:, 0]
+    uh = u.cpu().numpy()
+    l2 = float(np.linalg.norm(uh - gold) / np.linalg.norm(gold))
+
+    # per-phase times (one extra step, events between the calls)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    sgiga.sgiga_set_rhs_builtin(P.handle, W["source"])
+    ev[1].record(stream)
+    sgiga.sgiga_solve(P.handle, W["tol"], 50)
+    ev[2].record(stream)
+    sgiga.sgiga_eval(P.handle, pts, npts, uc)
+    sgiga.sgiga_combine(P.handle, uc, npts, u)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    phases = {"rhs_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+              "eval_combine_ms": ev[2].elapsed_time(ev[3])}
+
+    # dominant kernel: the FP64 operator apply, timed alone on the plan's stream
+    x = torch.randn(ndof, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    for _ in range(3):
+        sgiga.sgiga_apply(P.handle, x, y)
+    reps = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(reps):
+        sgiga.sgiga_apply(P.handle, x, y)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_s = a0.elapsed_time(a1) / reps / 1e3
+    flops = apply_flops(P)
+    peak64 = fp64_peak_tflops(torch)
+    achieved = flops / apply_s / 1e12
+    g_bytes = 6 * 8 * P.info.nqp + 2 * 8 * ndof
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None,
+                "kernel": "k_op3<3,0> (FP64 sum-factorised stiffness apply)",
+                "apply_ms": apply_s * 1e3, "algorithmic_flops": flops,
+                "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64 pipe)",
+                "hbm_GBps": g_bytes / apply_s / 1e9,
+                "hbm_frac_of_measured": g_bytes / apply_s / 1e9 / load_peaks().get("hbm_gbs", 6800.0)}
+
+    # end to end through the C ABI with host buffers (pinned)
+    xq = torch.zeros(W["d"] * P.info.nqp, dtype=torch.float64, device="cuda")
+    sgiga.sgiga_qp_coords(P.handle, xq)
+    xqh = xq.view(W["d"], -1)
+    f_h = (3 * np.pi ** 2 * torch.sin(np.pi * xqh[0]) * torch.sin(np.pi * xqh[1]) *
+           torch.sin(np.pi * xqh[2])).cpu().pin_memory()
+    del xq, xqh
+    pts_pin = torch.as_tensor(pts_h).pin_memory()
+    u_pin = torch.zeros(npts, dtype=torch.float64).pin_memory()
+    f_np, pts_np, u_np = f_h.numpy(), pts_pin.numpy(), u_pin.numpy()
+
+    def step_e2e():
+        sgiga.sgiga_set_rhs(P.handle, f_np)
+        sgiga.sgiga_solve(P.handle, W["tol"], 50)
+        sgiga.sgiga_eval(P.handle, pts_np, npts, uc)
+        sgiga.sgiga_combine(P.handle, uc, npts, u_np)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    l2_e2e = float(np.linalg.norm(u_np - gold) / np.linalg.norm(gold))
+
+    cpu = None
+    if rank == 0:
+        r = run_oracle_sample(len(ORACLE_SAMPLE))
+        cpu = {"value": r["dofs"] / r["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+               "sample": "%d components of the workload %s: assembly + sparse direct solve + evaluation "
+                         "on 17^3 points, FP64, one BLAS thread, %.1f s" % (len(ORACLE_SAMPLE),
+                                                                            ORACLE_SAMPLE, r["seconds"])}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "ngrids": ng, "ndof": ndof, "nqp": P.info.nqp,
+                       "eval_points": npts, "parallelism": "replica per GPU" if world > 1 else "single GPU",
+                       "l2_policy": "inputs larger than L2 (FP64 geometry planes %.2f GB per apply)"
+                                    % (6 * 8 * P.info.nqp / 1e9)},
+            "accuracy": {"rel_l2_vs_oracle": l2, "rel_l2_vs_oracle_e2e": l2_e2e,
+                         "target": 1e-10, "iterations": max(iters)},
+            "phases_ms": phases, "plan_s": plan_s,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * ndof / e2e_s, "unit": "DoF/s",
+                    "h2d_bytes_per_step": int(P.info.nqp * 8 + npts * W["d"] * 8),
+                    "d2h_bytes_per_step": int(npts * 8)},
+            "gpu_launches": int(launches),
+            "clocks": ck,
+        }
+        print(json.dumps(line))
+    P.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        oracle_sample_child(args.oracle_sample)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * sgiga.h -- C ABI of the GB300 sparse-grid isogeometric Poisson solver.
+ *
+ * What it computes (Beck, Sangalli, Tamellini, arXiv:1707.09598):
+ *   Problem 1 (Sec. 2.1): -Laplace(u) = f in Omega, u = 0 on the boundary,
+ *   discretised on every component grid of the combination technique
+ *   (Sec. 3, eq. TD-combi-tec) by tensor-product B-splines/NURBS pulled back
+ *   through the geometry map F (Sec. 2.2, eqs. F-B-splines, spline_space_phys,
+ *   u-IGA-approx), solved by Galerkin's method, and combined as
+ *       u_J(x) = sum_i c_i u_i(x).
+ *
+ * Index convention. A component is i in N^d with i_k >= min_level and
+ * w <= |i| <= w + d - 1; it has 2^{i_k} elements in direction k and the
+ * combination coefficient c_i = (-1)^{w+d-1-|i|} binom(d-1, w+d-1-|i|)
+ * (Sec. 3, eq. TD-combi-tec with beta = i - min_level). Components are
+ * numbered 0..ngrids-1 in the order sgiga_grid_info reports.
+ *
+ * Vectors. A "packed" vector concatenates the interior (Dirichlet-eliminated)
+ * coefficients of every component, component g starting at dof_off[g]; inside
+ * a component direction 1 varies fastest. Quadrature points (qp) use a
+ * "natural" order: component g's (p+1)E_1 x ... lattice of Gauss points,
+ * direction 1 fastest, starting at qp_off[g].
+ *
+ * Conventions for every call:
+ *   - returns SGIGA_OK (0) or a negative sgiga_status; never aborts; the
+ *     message of the last failure on the calling thread is sgiga_last_error();
+ *   - device pointers unless the parameter says "host or device"; such
+ *     pointers are detected with cudaPointerGetAttributes and staged;
+ *   - work is ordered on the plan's stream; a call returns once its status is
+ *     known (calls that read results back synchronise the stream);
+ *   - the caller owns every buffer it passes; the plan owns the device memory
+ *     it allocates and frees it in sgiga_destroy.
+ */
+#ifndef SGIGA_H
+#define SGIGA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgiga_plan_s* sgiga_plan_t;
+
+typedef enum {
+    SGIGA_OK = 0,
+    SGIGA_ERR_ARG = -1,           /* invalid argument or unsupported configuration */
+    SGIGA_ERR_NOMEM = -2,         /* device or host allocation failed */
+    SGIGA_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
+    SGIGA_ERR_NOT_CONVERGED = -4, /* sgiga_solve reached max_iter before rel_tol */
+    SGIGA_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+    SGIGA_ERR_GEOMETRY = -6       /* det J <= 0 at some quadrature point */
+} sgiga_status;
+
+/* Domains. UNIT: identity map on [0,1]^d. ANNULUS: quarter annulus with radii
+ * 1 and 2 as a NURBS patch (direction 1 radial, degree 1; direction 2 angular,
+ * degree 2, weights 1, sqrt(2)/2, 1), extruded along z in [0,1] when d = 3
+ * (Sec. 4.2). */
+enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1 };
+
+/* Breakpoint grading g(j/E) (Sec. 4.4): UNIFORM g(t) = t; RADICAL
+ * g(t) = 2^(gamma-1) t^gamma for t <= 1/2, 1 - 2^(gamma-1) (1-t)^gamma
+ * otherwise; ONESIDED g(t) = t^gamma. */
+enum { SGIGA_GRADING_UNIFORM = 0, SGIGA_GRADING_RADICAL = 1, SGIGA_GRADING_ONESIDED = 2 };
+
+/* Arithmetic of the solve. FP64: every step in double precision. */
+enum { SGIGA_PREC_FP64 = 0 };
+
+/* Preconditioner of the batched conjugate-gradient solve. FD: fast
+ * diagonalisation with the 1D generalised eigenpairs; NONE: plain CG. */
+enum { SGIGA_PRECOND_FD = 0, SGIGA_PRECOND_NONE = 1 };
+
+/* Built-in right-hand sides f = -Laplace(u) for manufactured solutions u:
+ * SINE      u = prod_k sin(pi x_k)
+ * POLY      u = prod_k x_k (1 - x_k)
+ * ANNULUS   u = x y (x^2+y^2-1)(x^2+y^2-4) sin(x)        (d = 2)
+ * ANNULUS_PAPER u = -(x^2+y^2-1)(x^2+y^2-4) x y^2 [sin(pi z)]  (Sec. 4.2)
+ * ONE       f = 1 */
+enum { SGIGA_SRC_SINE = 0, SGIGA_SRC_POLY = 1, SGIGA_SRC_ANNULUS = 2,
+       SGIGA_SRC_ANNULUS_PAPER = 3, SGIGA_SRC_ONE = 4 };
+
+typedef struct {
+    int d;            /* 2 or 3 */
+    int p;            /* spline degree, 1..4 */
+    int continuity;   /* r of C^r at interior breakpoints, 0..p-1; -1 means p-1 */
+    int w;            /* combination level: components with w <= |i| <= w+d-1 */
+    int min_level;    /* smallest i_k (>= 0); 1 in the usual setting */
+    int domain;       /* SGIGA_DOMAIN_* */
+    int grading;      /* SGIGA_GRADING_* */
+    double gamma;     /* grading exponent (ignored for UNIFORM) */
+    int precision;    /* SGIGA_PREC_* */
+    int precond;      /* SGIGA_PRECOND_* */
+} sgiga_config;
+
+typedef struct {
+    int d, p, continuity, ngrids;
+    long long ndof;   /* packed vector length */
+    long long nqp;    /* total quadrature points */
+    int max_tile_smem; /* bytes of dynamic shared memory of the operator kernel */
+    int ntiles;
+} sgiga_info;
+
+typedef struct {
+    int levels[3];     /* i_k */
+    int n[3];          /* interior DoFs per direction */
+    int coeff;         /* combination coefficient c_i */
+    long long ndof, dof_off, nqp, qp_off;
+} sgiga_grid;
+
+typedef struct {
+    int iterations;          /* outer iterations run (max over components) */
+    int converged;           /* number of components that met rel_tol */
+    double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
+    double seconds;          /* wall time of the call */
+} sgiga_solve_stats;
+
+/* Build a plan: index set and coefficients (Sec. 3), knot vectors and
+ * grading (Sec. 2.2, 4.4), Gauss rule, 1D basis tables (eq. Bsp), geometry
+ * coefficients at every quadrature point, 1D generalised eigenpairs of the
+ * preconditioner, and the tile schedule. `stream` is a cudaStream_t (NULL:
+ * the legacy default stream). On success *out owns its device memory. */
+int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out);
+
+/* Release every resource of the plan (NULL is a no-op). */
+void sgiga_destroy(sgiga_plan_t plan);
+
+int sgiga_plan_info(sgiga_plan_t plan, sgiga_info* out /* host */);
+int sgiga_grid_info(sgiga_plan_t plan, int g, sgiga_grid* out /* host */);
+
+/* Physical coordinates x = F(xi_q) of every quadrature point: xq is a device
+ * buffer [d][nqp] (one plane per coordinate, natural qp order). */
+int sgiga_qp_coords(sgiga_plan_t plan, double* xq);
+
+/* Load vector b_i = sum_q w_q |det J_q| f(x_q) R_i(xi_q) (Sec. 2.2, Galerkin
+ * right-hand side) from f at the quadrature points: f_qp is [nqp] in natural
+ * order, host or device. */
+int sgiga_set_rhs(sgiga_plan_t plan, const double* f_qp);
+
+/* Same, with f from a built-in manufactured solution (SGIGA_SRC_*),
+ * evaluated on the device. */
+int sgiga_set_rhs_builtin(sgiga_plan_t plan, int source);
+
+/* Copy the current packed load vector to b ([ndof], host or device). */
+int sgiga_get_rhs(sgiga_plan_t plan, double* b);
+
+/* y = K x for every component at once (matrix-free, sum factorisation of the
+ * Galerkin stiffness of Sec. 2.2 with Dirichlet rows and columns removed).
+ * x, y: device packed vectors [ndof]; y is overwritten. */
+int sgiga_apply(sgiga_plan_t plan, const double* x, double* y);
+
+/* z = P^{-1} r with the fast-diagonalisation preconditioner of every
+ * component, z = (U_d x .. x U_1) diag(sum_k lambda_k)^{-1} (U_d x .. x U_1)^T r
+ * with the 1D generalised eigenpairs of the parametric stiffness and mass
+ * matrices (a preconditioner the paper does not use: it names such fast
+ * solvers as future work, Sec. 5). Exact inverse on the unit square/cube.
+ * Device packed vectors. */
+int sgiga_precond(sgiga_plan_t plan, const double* r, double* z);
+
+/* Solve K_g u_g = b_g for every component g (batched preconditioned CG,
+ * per-component scalars and convergence) until ||r_g|| <= rel_tol ||b_g|| or
+ * max_iter iterations. The solution stays in the plan (sgiga_get_solution).
+ * Returns SGIGA_ERR_NOT_CONVERGED if some component did not converge. */
+int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
+                sgiga_solve_stats* stats /* host, may be NULL */);
+
+/* Packed solution coefficients (device [ndof]). */
+int sgiga_get_solution(sgiga_plan_t plan, double* u);
+/* Replace the plan's packed solution (device [ndof]); used to evaluate
+ * arbitrary coefficient vectors. */
+int sgiga_set_solution(sgiga_plan_t plan, const double* u);
+
+/* Evaluate every component u_g = sum_i c_i R_i at parametric points
+ * (Sec. 4.1: post-processing): xi is [npts][d] (host or device), u_comp is
+ * [ngrids][npts] (host or device). A parametric point is the same physical
+ * point F(xi) in every component because all share the exact geometry. */
+int sgiga_eval(sgiga_plan_t plan, const double* xi, long long npts, double* u_comp);
+
+/* u[j] = sum_g c_g u_comp[g][j], FP64 with Neumaier compensation
+ * (eq. TD-combi-tec). u_comp [ngrids][npts], u [npts], host or device. */
+int sgiga_combine(sgiga_plan_t plan, const double* u_comp, long long npts, double* u);
+
+/* Diagnostics for parity tests (host outputs). The 1D table of direction
+ * `dir` (0-based) at level `level`: Gauss points xi [E(p+1)], weights w
+ * [E(p+1)] (times h/2), basis values R and derivatives dR [E(p+1)][p+1] of the
+ * p+1 functions first[e] .. first[e]+p nonzero on element e, first [E]. */
+int sgiga_basis_table(sgiga_plan_t plan, int dir, int level, double* xi, double* w,
+                      double* R, double* dR, int* first);
+/* Geometry coefficients of component g in natural qp order: G is
+ * [d(d+1)/2][nqp_g] with the upper triangle of w |det J| (J^T J)^{-1} row by
+ * row ((0,0),(0,1),..), then mw [nqp_g] = w |det J|. Host output. */
+int sgiga_geometry_coeffs(sgiga_plan_t plan, int g, double* G, double* mw);
+/* Generalised eigenpairs K U = M U diag(lam), U^T M U = I, of the 1D interior
+ * matrices of direction `dir` at level `level`: U [n][n] row-major (column j
+ * is eigenvector j), lam [n] ascending. Host outputs. */
+int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam);
+
+const char* sgiga_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a diagnostic count; memsets and copies are not included). */
+long long sgiga_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGIGA_H */

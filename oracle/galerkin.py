@@ -223,14 +223,16 @@ class Component:
         return np.stack(out, axis=1)
 
 
-def stiffness_1d(level, p, r, kind="uniform", gamma=1.0):
-    """1D parametric stiffness and mass matrices of the interior B-splines.
+def stiffness_1d(level, p, r, kind="uniform", gamma=1.0, geom=None, k=0):
+    """1D parametric stiffness and mass matrices of the interior basis functions.
 
-    K_ij = int_0^1 B_i' B_j', M_ij = int_0^1 B_i B_j by (p+1)-point Gauss
-    quadrature per element; dense, interior functions 1..nf-2 only.
+    K_ij = int_0^1 R_i' R_j', M_ij = int_0^1 R_i R_j by (p+1)-point Gauss
+    quadrature per element; dense, interior functions 1..nf-2 only. R are the
+    B-splines of direction k divided by that direction's rational weight
+    function of `geom` (plain B-splines when geom is None).
     """
     from .geometry import UnitCube
-    s = Space1D(level, p, r, UnitCube(1), 0, kind, gamma)
+    s = Space1D(level, p, r, UnitCube(1) if geom is None else geom, 0 if geom is None else k, kind, gamma)
     K = np.zeros((s.nf, s.nf))
     M = np.zeros((s.nf, s.nf))
     for e in range(s.E):

@@ -1,0 +1,199 @@
+// 2D matrix-free operator kernel: y = K x (MODE 0) or the load vector (MODE 1)
+// for every component at once (Problem 1, Sec. 2.2, pulled back to the
+// parametric square).
+//
+//   grad u(q) = (D_a B_b x, B_a D_b x),  v = G_q grad u,
+//   y = (D_a B_b)^T v_a + (B_a D_b)^T v_b.
+// Stages: X --b--> S1 = {B_b X, D_b X} (pencil-major, shared); pencil a in
+// registers (gradients, G from HBM, backward along a, in place); S1 --b^T--> Y,
+// atomically added to the packed output.
+#include "op_common.cuh"
+
+namespace sgiga {
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256, 2)
+k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const int* __restrict__ active) {
+    constexpr int Q = P + 1, P1 = P + 1;
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
+    if (active && !active[td.grid]) return;
+    const GridDesc& g = Pl.grids[td.grid];
+    const int M = Pl.m;
+    int ax[2], T[2], L[2], E0[2], NF[2];
+    long long ST[2];
+    const long long stp[2] = {1, (long long)g.n[0]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        ax[k] = g.perm[k];
+        T[k] = g.T[ax[k]];
+        L[k] = (T[k] - 1) * M + P1;
+        E0[k] = td.e0[ax[k]];
+        NF[k] = g.nf[ax[k]];
+        ST[k] = stp[ax[k]];
+    }
+    const int Ta = T[0], Tb = T[1], La = L[0], Lb = L[1];
+    const int QTb = Q * Tb, npen = QTb, LaP = La | 1;
+    double* tb[2];
+    double* tdv[2];
+    double* cur = sm;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        tb[k] = cur; cur += T[k] * Q * P1;
+        tdv[k] = cur; cur += T[k] * Q * P1;
+    }
+    double* X = cur; cur += La * Lb;
+    double* S1 = cur;
+    const int S1n = npen * LaP;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const Table1D& tt = Pl.tabs[g.tab[ax[k]]];
+        const long long base = (tt.off + (long long)E0[k] * Q) * P1;
+        const int cnt = T[k] * Q * P1;
+        for (int i = tid; i < cnt; i += nth) { tb[k][i] = Pl.R[base + i]; tdv[k][i] = Pl.dR[base + i]; }
+    }
+    const long long doff = g.dof_off;
+    if (MODE == 0) {
+        const int nX = La * Lb;
+        for (int idx = tid; idx < nX; idx += nth) {
+            int ja = idx % La, jb = idx / La;
+            int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
+            double v = 0.0;
+            if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)
+                v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1]];
+            X[idx] = v;
+        }
+        __syncthreads();
+        const int n1 = npen * La;
+        for (int idx = tid; idx < n1; idx += nth) {
+            int ja = idx % La, qb = idx / La;
+            int eb = qb / Q;
+            const double* bt = tb[1] + qb * P1;
+            const double* dt = tdv[1] + qb * P1;
+            const double* xp = X + (eb * M) * La + ja;
+            double sB = 0.0, sD = 0.0;
+#pragma unroll
+            for (int t = 0; t < P1; ++t) {
+                double v = xp[t * La];
+                sB += bt[t] * v;
+                sD += dt[t] * v;
+            }
+            S1[qb * LaP + ja] = sB;
+            S1[S1n + qb * LaP + ja] = sD;
+        }
+        __syncthreads();
+    }
+    const long long nqp = Pl.nqp;
+    const double* __restrict__ G = Pl.G;
+    const double* __restrict__ rho = Pl.rho;
+    for (int pid = tid; pid < npen; pid += nth) {
+        double* c0 = S1 + pid * LaP;
+        double* c1 = c0 + S1n;
+        double a0[P1], a1[P1];
+#pragma unroll
+        for (int t = 0; t < P1; ++t) a0[t] = a1[t] = 0.0;
+        long long gi = td.g_off + pid;
+        for (int ea = 0; ea < Ta; ++ea) {
+            const int base = ea * M;
+            double i0[P1], i1[P1];
+            if (MODE == 0) {
+#pragma unroll
+                for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; }
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int qa = ea * Q + q;
+                const double* bt = tb[0] + qa * P1;
+                const double* dt = tdv[0] + qa * P1;
+                if (MODE == 0) {
+                    double ga = 0.0, gb = 0.0;
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; }
+                    const double G00 = G[gi], G01 = G[nqp + gi], G11 = G[2 * nqp + gi];
+                    const double va = G00 * ga + G01 * gb;
+                    const double vb = G01 * ga + G11 * gb;
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; }
+                } else {
+                    const double rv = rho[gi];
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) a0[t] += bt[t] * rv;
+                }
+                gi += npen;
+            }
+            for (int u = 0; u < M; ++u) {
+                c0[base + u] = a0[0];
+                if (MODE == 0) c1[base + u] = a1[0];
+#pragma unroll
+                for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; }
+                a0[P] = a1[P] = 0.0;
+            }
+        }
+        const int base = Ta * M;
+        for (int u = 0; u <= P - M; ++u) {
+            c0[base + u] = a0[0];
+            if (MODE == 0) c1[base + u] = a1[0];
+#pragma unroll
+            for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; }
+            a0[P] = a1[P] = 0.0;
+        }
+    }
+    __syncthreads();
+    const int nX = La * Lb;
+    for (int idx = tid; idx < nX; idx += nth) {
+        int ja = idx % La, jb = idx / La;
+        int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
+        if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)) continue;
+        int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
+        double yv = 0.0;
+        for (int eb = lo; eb <= hi; ++eb) {
+            const int t = jb - eb * M;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int qb = eb * Q + q;
+                const int o = qb * LaP + ja;
+                yv += tb[1][qb * P1 + t] * S1[o];
+                if (MODE == 0) yv += tdv[1][qb * P1 + t] * S1[S1n + o];
+            }
+        }
+        atomicAdd(&y[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1]], yv);
+    }
+}
+
+template <int P>
+static cudaError_t launch2(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
+                           cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    if (mode == 0)
+        k_op2<P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    else
+        k_op2<P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op2(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
+                       cudaStream_t s) {
+    switch (Pl.p) {
+    case 1: return launch2<1>(Pl, x, y, active, mode, s);
+    case 2: return launch2<2>(Pl, x, y, active, mode, s);
+    case 3: return launch2<3>(Pl, x, y, active, mode, s);
+    case 4: return launch2<4>(Pl, x, y, active, mode, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t set_op2_smem(int p, size_t bytes) {
+    cudaError_t e = cudaSuccess;
+#define SET(PP)                                                                                              \
+    if (p == PP) {                                                                                           \
+        e = cudaFuncSetAttribute(k_op2<PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);   \
+        if (e == cudaSuccess)                                                                                \
+            e = cudaFuncSetAttribute(k_op2<PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+    }
+    SET(1) SET(2) SET(3) SET(4)
+#undef SET
+    return e;
+}
+
+}  // namespace sgiga

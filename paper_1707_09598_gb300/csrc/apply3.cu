@@ -1,0 +1,259 @@
+// 3D matrix-free operator kernel: y = K x (MODE 0) or b = load vector (MODE 1)
+// for every component at once (Galerkin stiffness / right-hand side of
+// Problem 1 pulled back to the parametric cube, Sec. 2.2).
+//
+//   grad u(q) = (D_a B_b B_c x, B_a D_b B_c x, B_a B_b D_c x)   (forward)
+//   v(q)      = G_q grad u(q)                                  (pointwise)
+//   y         = (D_a B_b B_c)^T v_a + (B_a D_b B_c)^T v_b + (B_a B_b D_c)^T v_c
+//
+// B_x / D_x are the 1D tables of values / derivatives at Gauss points. Stages:
+//   X  --c-->  S1 = {B_c X, D_c X}                       (shared)
+//   S1 --b-->  S2 = {B_b S1_B, D_b S1_B, B_b S1_D}       (shared, pencil-major)
+//   pencil a (registers): gradients, G from HBM, backward along a, in place
+//   S2 --b^T--> S1 = {B_b^T W0 + D_b^T W1, B_b^T W2}
+//   S1 --c^T--> Y, atomically added to the packed output vector.
+#include "op_common.cuh"
+
+namespace sgiga {
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256, 2)
+k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const int* __restrict__ active) {
+    constexpr int Q = P + 1, P1 = P + 1;
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
+    if (active && !active[td.grid]) return;
+    const GridDesc& g = Pl.grids[td.grid];
+    const int M = Pl.m;
+    int ax[3], T[3], L[3], E0[3], NF[3];
+    long long ST[3];
+    const long long stp[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ax[k] = g.perm[k];
+        T[k] = g.T[ax[k]];
+        L[k] = (T[k] - 1) * M + P1;
+        E0[k] = td.e0[ax[k]];
+        NF[k] = g.nf[ax[k]];
+        ST[k] = stp[ax[k]];
+    }
+    const int Ta = T[0], Tb = T[1], Tc = T[2], La = L[0], Lb = L[1], Lc = L[2];
+    const int QTb = Q * Tb, QTc = Q * Tc, npen = QTb * QTc, LaP = La | 1;
+    double* tb[3];
+    double* tdv[3];
+    double* cur = sm;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        tb[k] = cur; cur += T[k] * Q * P1;
+        tdv[k] = cur; cur += T[k] * Q * P1;
+    }
+    double* X = cur; cur += (long long)La * Lb * Lc;
+    double* S1 = cur; cur += 2LL * QTc * Lb * La;
+    double* S2 = cur;
+    const int S1n = QTc * Lb * La;
+    const int S2n = npen * LaP;
+
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const Table1D& tt = Pl.tabs[g.tab[ax[k]]];
+        const long long base = (tt.off + (long long)E0[k] * Q) * P1;
+        const int cnt = T[k] * Q * P1;
+        for (int i = tid; i < cnt; i += nth) { tb[k][i] = Pl.R[base + i]; tdv[k][i] = Pl.dR[base + i]; }
+    }
+    const long long doff = g.dof_off;
+    if (MODE == 0) {
+        const int nX = La * Lb * Lc;
+        for (int idx = tid; idx < nX; idx += nth) {
+            int ja = idx % La, r = idx / La, jb = r % Lb, jc = r / Lb;
+            int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
+            double v = 0.0;
+            if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)
+                v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2]];
+            X[idx] = v;
+        }
+        __syncthreads();
+        // stage 1: contract c (DoF -> qp)
+        for (int idx = tid; idx < S1n; idx += nth) {
+            int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
+            int ec = qc / Q;
+            const double* bt = tb[2] + qc * P1;
+            const double* dt = tdv[2] + qc * P1;
+            const double* xp = X + ((ec * M) * Lb + jb) * La + ja;
+            double sB = 0.0, sD = 0.0;
+#pragma unroll
+            for (int t = 0; t < P1; ++t) {
+                double v = xp[t * Lb * La];
+                sB += bt[t] * v;
+                sD += dt[t] * v;
+            }
+            S1[idx] = sB;
+            S1[S1n + idx] = sD;
+        }
+        __syncthreads();
+        // stage 2: contract b
+        const int n2 = npen * La;
+        for (int idx = tid; idx < n2; idx += nth) {
+            int ja = idx % La, r = idx / La, qb = r % QTb, qc = r / QTb;
+            int eb = qb / Q;
+            const double* bt = tb[1] + qb * P1;
+            const double* dt = tdv[1] + qb * P1;
+            const double* s1b = S1 + (qc * Lb + eb * M) * La + ja;
+            const double* s1d = s1b + S1n;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+            for (int t = 0; t < P1; ++t) {
+                double vb = s1b[t * La], vd = s1d[t * La];
+                s0 += bt[t] * vb;
+                s1 += dt[t] * vb;
+                s2 += bt[t] * vd;
+            }
+            int pid = qb + QTb * qc;
+            S2[pid * LaP + ja] = s0;
+            S2[S2n + pid * LaP + ja] = s1;
+            S2[2 * S2n + pid * LaP + ja] = s2;
+        }
+        __syncthreads();
+    }
+    // pencil stage along a
+    const long long nqp = Pl.nqp;
+    const double* __restrict__ G = Pl.G;
+    const double* __restrict__ rho = Pl.rho;
+    for (int pid = tid; pid < npen; pid += nth) {
+        double* c0 = S2 + pid * LaP;
+        double* c1 = c0 + S2n;
+        double* c2 = c1 + S2n;
+        double a0[P1], a1[P1], a2[P1];
+#pragma unroll
+        for (int t = 0; t < P1; ++t) a0[t] = a1[t] = a2[t] = 0.0;
+        long long gi = td.g_off + pid;
+        for (int ea = 0; ea < Ta; ++ea) {
+            const int base = ea * M;
+            double i0[P1], i1[P1], i2[P1];
+            if (MODE == 0) {
+#pragma unroll
+                for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; i2[t] = c2[base + t]; }
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int qa = ea * Q + q;
+                const double* bt = tb[0] + qa * P1;
+                const double* dt = tdv[0] + qa * P1;
+                if (MODE == 0) {
+                    double ga = 0.0, gb = 0.0, gc = 0.0;
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; gc += bt[t] * i2[t]; }
+                    const double G00 = G[gi], G01 = G[nqp + gi], G02 = G[2 * nqp + gi];
+                    const double G11 = G[3 * nqp + gi], G12 = G[4 * nqp + gi], G22 = G[5 * nqp + gi];
+                    const double va = G00 * ga + G01 * gb + G02 * gc;
+                    const double vb = G01 * ga + G11 * gb + G12 * gc;
+                    const double vc = G02 * ga + G12 * gb + G22 * gc;
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; a2[t] += bt[t] * vc; }
+                } else {
+                    const double rv = rho[gi];
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) a0[t] += bt[t] * rv;
+                }
+                gi += npen;
+            }
+            for (int u = 0; u < M; ++u) {
+                c0[base + u] = a0[0];
+                if (MODE == 0) { c1[base + u] = a1[0]; c2[base + u] = a2[0]; }
+#pragma unroll
+                for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; a2[t] = a2[t + 1]; }
+                a0[P] = a1[P] = a2[P] = 0.0;
+            }
+        }
+        const int base = Ta * M;
+        for (int u = 0; u <= P - M; ++u) {
+            c0[base + u] = a0[0];
+            if (MODE == 0) { c1[base + u] = a1[0]; c2[base + u] = a2[0]; }
+#pragma unroll
+            for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; a2[t] = a2[t + 1]; }
+            a0[P] = a1[P] = a2[P] = 0.0;
+        }
+    }
+    __syncthreads();
+    // backward b: S2 -> S1
+    for (int idx = tid; idx < S1n; idx += nth) {
+        int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
+        int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
+        double rB = 0.0, rD = 0.0;
+        for (int eb = lo; eb <= hi; ++eb) {
+            const int t = jb - eb * M;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int qb = eb * Q + q;
+                const int o = (qb + QTb * qc) * LaP + ja;
+                const double bv = tb[1][qb * P1 + t];
+                if (MODE == 0) {
+                    rB += bv * S2[o] + tdv[1][qb * P1 + t] * S2[S2n + o];
+                    rD += bv * S2[2 * S2n + o];
+                } else {
+                    rB += bv * S2[o];
+                }
+            }
+        }
+        S1[idx] = rB;
+        if (MODE == 0) S1[S1n + idx] = rD;
+    }
+    __syncthreads();
+    // backward c and scatter
+    const int nX = La * Lb * Lc;
+    for (int idx = tid; idx < nX; idx += nth) {
+        int ja = idx % La, r = idx / La, jb = r % Lb, jc = r / Lb;
+        int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
+        if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)) continue;
+        int lo = elem_lo(jc, P, M), hi = elem_hi(jc, M, Tc);
+        double yv = 0.0;
+        for (int ec = lo; ec <= hi; ++ec) {
+            const int t = jc - ec * M;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int qc = ec * Q + q;
+                const int o = (qc * Lb + jb) * La + ja;
+                yv += tb[2][qc * P1 + t] * S1[o];
+                if (MODE == 0) yv += tdv[2][qc * P1 + t] * S1[S1n + o];
+            }
+        }
+        atomicAdd(&y[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2]], yv);
+    }
+}
+
+template <int P>
+static cudaError_t launch3(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
+                           cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    if (mode == 0)
+        k_op3<P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    else
+        k_op3<P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op3(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
+                       cudaStream_t s) {
+    switch (Pl.p) {
+    case 1: return launch3<1>(Pl, x, y, active, mode, s);
+    case 2: return launch3<2>(Pl, x, y, active, mode, s);
+    case 3: return launch3<3>(Pl, x, y, active, mode, s);
+    case 4: return launch3<4>(Pl, x, y, active, mode, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t set_op3_smem(int p, size_t bytes) {
+    cudaError_t e = cudaSuccess;
+#define SET(PP)                                                                                              \
+    if (p == PP) {                                                                                           \
+        e = cudaFuncSetAttribute(k_op3<PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);   \
+        if (e == cudaSuccess)                                                                                \
+            e = cudaFuncSetAttribute(k_op3<PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+    }
+    SET(1) SET(2) SET(3) SET(4)
+#undef SET
+    return e;
+}
+
+}  // namespace sgiga

@@ -1,0 +1,882 @@
+// Host planner and C ABI (include/sgiga.h).
+//
+// sgiga_plan builds, once per (domain, p, r, w, grading):
+//   - the index set and coefficients of the combination technique (Sec. 3,
+//     eq. TD-combi-tec);
+//   - per (direction, level) the open knot vector of 2^level elements with
+//     graded breakpoints (Sec. 2.2, Sec. 4.4) and the Gauss rule;
+//   - the tile decomposition of every component and its launch order (largest
+//     tiles first, the greedy longest-processing-time order of Sec. 4.1);
+//   - device tables (basis, geometry coefficients) through the CUDA kernels;
+//   - the 1D generalised eigenpairs of the preconditioner (host, eig.cpp).
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sgiga.h"
+#include "internal.h"
+#include "kernels.h"
+#include "op_common.cuh"
+
+namespace sgiga {
+int generalized_eigen(int n, int bw, const double* K, const double* M, double* U, double* lam);
+}
+
+using namespace sgiga;
+
+std::atomic<long long> sgiga::g_launches{0};
+
+static thread_local std::string g_last_error = "";
+
+static int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            return fail(SGIGA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+        }                                                                                \
+    } while (0)
+
+struct sgiga_plan_s {
+    sgiga_config cfg;
+    int d, p, r, m, Q, ncomp;
+    cudaStream_t stream;
+    std::vector<GridDesc> grids;
+    std::vector<TileDesc> tiles;
+    std::vector<int> sched;
+    std::vector<Table1D> tabs;
+    std::map<std::pair<int, int>, int> tab_of;   // (dir, level) -> table
+    std::vector<int> eig_of_tab;
+    std::vector<Eig1D> eigs;
+    std::vector<Chunk> chunks;
+    std::vector<FDItem> fd[3];
+    std::vector<double> knots, bp;
+    Patch patch;
+    long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
+    int maxE = 1;
+    size_t smem = 0;
+    std::vector<void*> allocs;
+    DevPlan dp;
+    FDItem* d_fd[3] = {nullptr, nullptr, nullptr};
+    double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
+    double *d_t1 = nullptr, *d_t2 = nullptr, *d_partial = nullptr, *d_scal = nullptr, *d_coef = nullptr;
+    int* d_active = nullptr;
+    int* d_iters = nullptr;
+    int* d_nactive = nullptr;
+    int* h_nactive = nullptr;   // pinned
+    void* stage = nullptr;      // device staging for host pointers
+    size_t stage_bytes = 0;
+};
+
+template <typename T>
+static int dalloc(sgiga_plan_s* P, T** out, size_t count) {
+    void* ptr = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SGIGA_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    P->allocs.push_back(ptr);
+    *out = (T*)ptr;
+    return SGIGA_OK;
+}
+
+template <typename T>
+static int upload(sgiga_plan_s* P, T** out, const std::vector<T>& v) {
+    int rc = dalloc(P, out, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SGIGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 1D ingredients
+// ---------------------------------------------------------------------------
+
+// Gauss-Legendre nodes/weights on [-1,1] by Newton's method on P_Q.
+static void gauss_legendre(int Q, double* x, double* w) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < Q; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (Q + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= Q; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (Q == 1) { p1 = z; p0 = 1.0; }
+            dp = Q * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        {   // final derivative at the converged root
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= Q; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (Q == 1) { p1 = z; p0 = 1.0; }
+            dp = Q * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[Q - 1 - i] = z;                       // ascending
+        w[Q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static double grading(int kind, double gamma, double t) {
+    if (kind == SGIGA_GRADING_RADICAL) {
+        double c = std::pow(2.0, gamma - 1.0);
+        return t <= 0.5 ? c * std::pow(t, gamma) : 1.0 - c * std::pow(1.0 - t, gamma);
+    }
+    if (kind == SGIGA_GRADING_ONESIDED) return std::pow(t, gamma);
+    return t;
+}
+
+static void make_patch(int domain, int d, Patch& pt) {
+    std::memset(&pt, 0, sizeof(pt));
+    pt.d = d;
+    for (int k = 0; k < 3; ++k) {
+        pt.deg[k] = 1;
+        pt.nk[k] = 4;
+        pt.nc[k] = 2;
+        pt.knots[k][0] = pt.knots[k][1] = 0.0;
+        pt.knots[k][2] = pt.knots[k][3] = 1.0;
+        for (int i = 0; i < 8; ++i) pt.w[k][i] = 1.0;
+    }
+    if (domain == SGIGA_DOMAIN_UNIT) {
+        int nc = 1 << d;
+        for (int c = 0; c < nc; ++c)
+            for (int k = 0; k < d; ++k) pt.cp[c][k] = (c >> k) & 1;
+        return;
+    }
+    // quarter annulus: direction 0 radial (degree 1), direction 1 angular (degree 2)
+    pt.deg[1] = 2;
+    pt.nk[1] = 6;
+    pt.nc[1] = 3;
+    double kn[6] = {0, 0, 0, 1, 1, 1};
+    for (int i = 0; i < 6; ++i) pt.knots[1][i] = kn[i];
+    pt.w[1][0] = 1.0;
+    pt.w[1][1] = std::sqrt(2.0) / 2.0;
+    pt.w[1][2] = 1.0;
+    pt.rational[1] = 1;
+    const double rad[2] = {1.0, 2.0};
+    const double ang[3][2] = {{1, 0}, {1, 1}, {0, 1}};
+    int nz = d == 3 ? 2 : 1;
+    for (int c = 0; c < nz; ++c)
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 2; ++i) {
+                int ci = i + 2 * (j + 3 * c);
+                pt.cp[ci][0] = rad[i] * ang[j][0];
+                pt.cp[ci][1] = rad[i] * ang[j][1];
+                if (d == 3) pt.cp[ci][2] = c;
+            }
+}
+
+static long long binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// Tile choice: power-of-two element extents per direction and the pencil
+// axis, minimising a per-quadrature-point cost model within the
+// shared-memory budget.
+static void choose_tile(int d, int P, int M, const int* E, size_t budget, int* Tphys, int* perm) {
+    const int Q = P + 1, P1 = P + 1;
+    double best = 1e300;
+    int lim[3] = {1, 1, 1};
+    for (int k = 0; k < d; ++k) lim[k] = std::min(E[k], 64);
+    for (int t0 = 1; t0 <= lim[0]; t0 *= 2)
+        for (int t1 = 1; t1 <= lim[1]; t1 *= 2)
+            for (int t2 = 1; t2 <= lim[2]; t2 *= 2) {
+                int Tp[3] = {t0, t1, t2};
+                // all pencil choices; b, c in the remaining order by size
+                for (int a = 0; a < d; ++a) {
+                    int pr[3] = {a, -1, -1};
+                    int o = 1;
+                    for (int k = 0; k < d; ++k) if (k != a) pr[o++] = k;
+                    if (d == 3 && Tp[pr[2]] > Tp[pr[1]]) std::swap(pr[1], pr[2]);
+                    int Tl[3] = {Tp[pr[0]], d > 1 ? Tp[pr[1]] : 1, d > 2 ? Tp[pr[2]] : 1};
+                    long long sm = op_smem_doubles(d, P, M, Tl) * 8;
+                    if ((size_t)sm > budget) continue;
+                    double La = (Tl[0] - 1) * M + P1, Lb = (Tl[1] - 1) * M + P1, Lc = (Tl[2] - 1) * M + P1;
+                    double QTa = Q * Tl[0], QTb = Q * Tl[1], QTc = Q * Tl[2];
+                    double cost, qp, npen;
+                    if (d == 3) {
+                        npen = QTb * QTc;
+                        qp = QTa * npen;
+                        double s1 = 2.0 * P1 * QTc * Lb * La, s2 = 3.0 * P1 * npen * La;
+                        double pen = (6.0 * P1 + 9.0) * npen * QTa;
+                        if (npen < 256) pen *= 1.0 + 0.25 * (256.0 / npen - 1.0);
+                        cost = 2 * (s1 + s2) + pen + 10.0 * La * Lb * Lc + 6 * 256;
+                    } else {
+                        npen = QTb;
+                        qp = QTa * npen;
+                        double s1 = 2.0 * P1 * QTb * La;
+                        double pen = (4.0 * P1 + 4.0) * npen * QTa;
+                        if (npen < 256) pen *= 1.0 + 0.25 * (256.0 / npen - 1.0);
+                        cost = 2 * s1 + pen + 10.0 * La * Lb + 4 * 256;
+                    }
+                    if (qp > 16384) continue;
+                    double c = cost / qp;
+                    if (c < best - 1e-12) {
+                        best = c;
+                        for (int k = 0; k < 3; ++k) { Tphys[k] = Tp[k]; perm[k] = pr[k] < 0 ? k : pr[k]; }
+                    }
+                }
+                if (d < 3) break;
+            }
+}
+
+// 1D interior matrices of a table, from the device-computed tables.
+static void assemble_1d(int E, int Q, int p, int nf, const double* w, const double* R, const double* dR,
+                        const int* first, std::vector<double>& K, std::vector<double>& Mm) {
+    int n = nf - 2;
+    K.assign((size_t)n * n, 0.0);
+    Mm.assign((size_t)n * n, 0.0);
+    for (int e = 0; e < E; ++e)
+        for (int q = 0; q < Q; ++q) {
+            long long o = (long long)e * Q + q;
+            for (int a = 0; a <= p; ++a) {
+                int i = first[e] + a - 1;
+                if (i < 0 || i >= n) continue;
+                for (int b = 0; b <= p; ++b) {
+                    int j = first[e] + b - 1;
+                    if (j < 0 || j >= n) continue;
+                    K[(size_t)i * n + j] += w[o] * dR[o * (p + 1) + a] * dR[o * (p + 1) + b];
+                    Mm[(size_t)i * n + j] += w[o] * R[o * (p + 1) + a] * R[o * (p + 1) + b];
+                }
+            }
+        }
+}
+
+static void free_plan(sgiga_plan_s* P) {
+    if (!P) return;
+    for (void* a : P->allocs) cudaFree(a);
+    if (P->stage) cudaFree(P->stage);
+    if (P->h_nactive) cudaFreeHost(P->h_nactive);
+    delete P;
+}
+
+static int build(sgiga_plan_s* P) {
+    const sgiga_config& c = P->cfg;
+    const int d = P->d, p = P->p, M = P->m, Q = P->Q;
+    // index set
+    const int mn = c.min_level, w = c.w;
+    const int hi = w + d - 1 - (d - 1) * mn;
+    std::vector<std::array<int, 3>> idx;
+    int lv[3] = {mn, mn, mn};
+    for (lv[2] = (d == 3 ? mn : 0); lv[2] <= (d == 3 ? hi : 0); ++lv[2])
+        for (lv[1] = mn; lv[1] <= hi; ++lv[1])
+            for (lv[0] = mn; lv[0] <= hi; ++lv[0]) {
+                int s = lv[0] + lv[1] + (d == 3 ? lv[2] : 0);
+                if (s < w || s > w + d - 1) continue;
+                idx.push_back({lv[0], lv[1], d == 3 ? lv[2] : 0});
+            }
+    std::sort(idx.begin(), idx.end(), [&](const std::array<int, 3>& a, const std::array<int, 3>& b) {
+        int sa = a[0] + a[1] + a[2], sb = b[0] + b[1] + b[2];
+        if (sa != sb) return sa > sb;
+        for (int k = 0; k < d; ++k) if (a[k] != b[k]) return a[k] < b[k];
+        return false;
+    });
+    if (idx.empty()) return fail(SGIGA_ERR_ARG, "empty index set");
+    for (auto& iv : idx)
+        for (int k = 0; k < d; ++k) if (iv[k] > 20) return fail(SGIGA_ERR_ARG, "level above 20");
+    // tables
+    for (auto& iv : idx)
+        for (int k = 0; k < d; ++k) {
+            auto key = std::make_pair(k, iv[k]);
+            if (P->tab_of.count(key)) continue;
+            Table1D t{};
+            t.dir = k;
+            t.level = iv[k];
+            t.E = 1 << iv[k];
+            t.nf = t.E * M + P->r + 1;
+            t.off = P->tab_entries;
+            P->tab_entries += (long long)t.E * Q;
+            t.eoff = (int)P->bp.size();
+            for (int j = 0; j <= t.E; ++j) P->bp.push_back(grading(c.grading, c.gamma, (double)j / t.E));
+            P->bp[t.eoff] = 0.0;
+            P->bp[t.eoff + t.E] = 1.0;
+            t.koff = (int)P->knots.size();
+            for (int j = 0; j <= p; ++j) P->knots.push_back(0.0);
+            for (int e = 1; e < t.E; ++e)
+                for (int j = 0; j < M; ++j) P->knots.push_back(P->bp[t.eoff + e]);
+            for (int j = 0; j <= p; ++j) P->knots.push_back(1.0);
+            t.nk = (int)P->knots.size() - t.koff;
+            P->maxE = std::max(P->maxE, t.E);
+            P->tab_of[key] = (int)P->tabs.size();
+            P->tabs.push_back(t);
+        }
+    // grids and tiles
+    const size_t budget = 110 * 1024;
+    long long tqp = 0;
+    for (size_t gi = 0; gi < idx.size(); ++gi) {
+        GridDesc g{};
+        int s = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (k < d) {
+                g.lev[k] = idx[gi][k];
+                g.E[k] = 1 << g.lev[k];
+                g.nf[k] = g.E[k] * M + P->r + 1;
+                g.n[k] = g.nf[k] - 2;
+                g.tab[k] = P->tab_of[std::make_pair(k, g.lev[k])];
+                s += g.lev[k];
+            } else {
+                g.lev[k] = 0; g.E[k] = 1; g.nf[k] = 3; g.n[k] = 1; g.tab[k] = 0;
+            }
+        }
+        int t = w + d - 1 - s;
+        g.coeff = (double)((t % 2) ? -1 : 1) * (double)binom(d - 1, t);
+        g.ndof = 1;
+        g.nqp = 1;
+        for (int k = 0; k < d; ++k) { g.ndof *= g.n[k]; g.nqp *= (long long)Q * g.E[k]; }
+        g.dof_off = P->ndof;
+        g.qp_off = P->nqp;
+        P->ndof += g.ndof;
+        P->nqp += g.nqp;
+        choose_tile(d, p, M, g.E, budget, g.T, g.perm);
+        int Tl[3] = {g.T[g.perm[0]], d > 1 ? g.T[g.perm[1]] : 1, d > 2 ? g.T[g.perm[2]] : 1};
+        P->smem = std::max(P->smem, (size_t)op_smem_doubles(d, p, M, Tl) * 8);
+        g.tile0 = (int)P->tiles.size();
+        g.tqp_off = tqp;
+        int nt[3] = {1, 1, 1};
+        for (int k = 0; k < d; ++k) nt[k] = g.E[k] / g.T[k];
+        long long tile_qp = 1;
+        for (int k = 0; k < d; ++k) tile_qp *= (long long)Q * g.T[k];
+        for (int z = 0; z < nt[2]; ++z)
+            for (int y = 0; y < nt[1]; ++y)
+                for (int x = 0; x < nt[0]; ++x) {
+                    TileDesc td{};
+                    td.grid = (int)gi;
+                    td.e0[0] = x * g.T[0];
+                    td.e0[1] = y * g.T[1];
+                    td.e0[2] = z * g.T[2];
+                    td.g_off = tqp;
+                    tqp += tile_qp;
+                    P->tiles.push_back(td);
+                }
+        g.ntiles = (int)P->tiles.size() - g.tile0;
+        // chunks
+        g.chunk0 = (int)P->chunks.size();
+        for (long long o = 0; o < g.ndof; o += 4096) {
+            Chunk ch{};
+            ch.grid = (int)gi;
+            ch.start = g.dof_off + o;
+            ch.len = (int)std::min<long long>(4096, g.ndof - o);
+            P->chunks.push_back(ch);
+        }
+        g.nchunk = (int)P->chunks.size() - g.chunk0;
+        P->grids.push_back(g);
+    }
+    // launch order: tiles with the largest estimated cost first (greedy LPT)
+    P->sched.resize(P->tiles.size());
+    for (size_t i = 0; i < P->tiles.size(); ++i) P->sched[i] = (int)i;
+    std::vector<double> tcost(P->tiles.size());
+    for (size_t i = 0; i < P->tiles.size(); ++i) {
+        const GridDesc& g = P->grids[P->tiles[i].grid];
+        double qp = 1;
+        for (int k = 0; k < d; ++k) qp *= Q * g.T[k];
+        tcost[i] = qp;
+    }
+    std::stable_sort(P->sched.begin(), P->sched.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
+    // preconditioner work items per direction (longest contractions first)
+    for (int k = 0; k < d; ++k) {
+        std::vector<FDItem>& v = P->fd[k];
+        for (size_t gi = 0; gi < P->grids.size(); ++gi) {
+            const GridDesc& g = P->grids[gi];
+            long long n = g.n[k];
+            if (g.ndof == 0) continue;
+            long long ncol = g.ndof / n;
+            for (long long i0 = 0; i0 < n; i0 += 32)
+                for (long long c0 = 0; c0 < ncol; c0 += 64) v.push_back(FDItem{(int)gi, (int)i0, c0});
+        }
+        std::stable_sort(v.begin(), v.end(), [&](const FDItem& a, const FDItem& b) {
+            return P->grids[a.grid].n[k] > P->grids[b.grid].n[k];
+        });
+    }
+    // device data
+    make_patch(c.domain, d, P->patch);
+    std::vector<double> gauss(2 * Q);
+    gauss_legendre(Q, gauss.data(), gauss.data() + Q);
+    DevPlan& D = P->dp;
+    std::memset(&D, 0, sizeof(D));
+    D.d = d; D.p = p; D.m = M; D.Q = Q;
+    D.ngrids = (int)P->grids.size();
+    D.ntiles = (int)P->tiles.size();
+    D.ntabs = (int)P->tabs.size();
+    D.nchunks = (int)P->chunks.size();
+    D.ndof = P->ndof;
+    D.nqp = P->nqp;
+    D.smem_op = P->smem;
+    int rc;
+    GridDesc* dg; TileDesc* dt; int* ds; Table1D* dtab; Chunk* dch; Patch* dpatch;
+    double *dkn, *dbp, *dgauss;
+    std::vector<Patch> pv(1, P->patch);
+    if ((rc = upload(P, &dtab, P->tabs)) || (rc = upload(P, &dt, P->tiles)) || (rc = upload(P, &ds, P->sched)) ||
+        (rc = upload(P, &dch, P->chunks)) || (rc = upload(P, &dpatch, pv)) || (rc = upload(P, &dkn, P->knots)) ||
+        (rc = upload(P, &dbp, P->bp)) || (rc = upload(P, &dgauss, gauss)))
+        return rc;
+    for (int k = 0; k < d; ++k)
+        if ((rc = upload(P, &P->d_fd[k], P->fd[k]))) return rc;
+    D.tiles = dt; D.sched = ds; D.tabs = dtab; D.chunks = dch; D.patch = dpatch;
+    D.knots = dkn; D.bp = dbp; D.gauss = dgauss;
+    int* dfirst; int* dflags;
+    if ((rc = dalloc(P, &D.xi, P->tab_entries)) || (rc = dalloc(P, &D.w, P->tab_entries)) ||
+        (rc = dalloc(P, &D.R, P->tab_entries * (p + 1))) || (rc = dalloc(P, &D.dR, P->tab_entries * (p + 1))) ||
+        (rc = dalloc(P, &dfirst, P->bp.size())) || (rc = dalloc(P, &dflags, 4)))
+        return rc;
+    D.first = dfirst; D.flags = dflags;
+    CUDA_TRY(cudaMemset(dflags, 0, 4 * sizeof(int)));
+    const int ncomp = d * (d + 1) / 2;
+    P->ncomp = ncomp;
+    if ((rc = dalloc(P, &D.G, (size_t)ncomp * P->nqp)) || (rc = dalloc(P, &D.mw, P->nqp)) ||
+        (rc = dalloc(P, &D.rho, P->nqp)))
+        return rc;
+    cudaStream_t s = P->stream;
+    CUDA_TRY(launch_basis_tables(D, P->maxE, s));
+    // eigen tables: one per (level, rational direction or not)
+    std::vector<double> hw(P->tab_entries), hR(P->tab_entries * (p + 1)), hdR(P->tab_entries * (p + 1));
+    std::vector<int> hfirst(P->bp.size());
+    CUDA_TRY(cudaMemcpyAsync(hw.data(), D.w, hw.size() * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hR.data(), D.R, hR.size() * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hdR.data(), D.dR, hdR.size() * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hfirst.data(), D.first, hfirst.size() * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::map<std::pair<int, int>, int> eig_key;
+    std::vector<double> hU, hlam;
+    P->eig_of_tab.assign(P->tabs.size(), -1);
+    for (size_t ti = 0; ti < P->tabs.size(); ++ti) {
+        const Table1D& t = P->tabs[ti];
+        auto key = std::make_pair(t.level, P->patch.rational[t.dir] ? t.dir : -1);
+        auto it = eig_key.find(key);
+        if (it != eig_key.end()) { P->eig_of_tab[ti] = it->second; continue; }
+        std::vector<double> K, Mm;
+        assemble_1d(t.E, Q, p, t.nf, hw.data() + t.off, hR.data() + t.off * (p + 1), hdR.data() + t.off * (p + 1),
+                    hfirst.data() + t.eoff, K, Mm);
+        int n = t.nf - 2;
+        Eig1D e{};
+        e.n = n;
+        e.uoff = (long long)hU.size();
+        e.loff = (long long)hlam.size();
+        hU.resize(hU.size() + (size_t)n * n);
+        hlam.resize(hlam.size() + n);
+        if (n > 0 && generalized_eigen(n, p, K.data(), Mm.data(), hU.data() + e.uoff, hlam.data() + e.loff) != 0)
+            return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed (level " + std::to_string(t.level) + ")");
+        eig_key[key] = (int)P->eigs.size();
+        P->eig_of_tab[ti] = (int)P->eigs.size();
+        P->eigs.push_back(e);
+    }
+    for (auto& g : P->grids)
+        for (int k = 0; k < 3; ++k) g.eig[k] = k < d ? P->eig_of_tab[g.tab[k]] : 0;
+    Eig1D* deig; double *dU, *dlam;
+    if ((rc = upload(P, &deig, P->eigs)) || (rc = upload(P, &dU, hU)) || (rc = upload(P, &dlam, hlam)) ||
+        (rc = upload(P, &dg, P->grids)))
+        return rc;
+    D.eigs = deig; D.U = dU; D.lam = dlam; D.grids = dg;
+    // geometry coefficients
+    CUDA_TRY(launch_geometry(D, s));
+    int hflags[4];
+    CUDA_TRY(cudaMemcpyAsync(hflags, dflags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
+    // operator kernel shared memory
+    if (d == 3) CUDA_TRY(set_op3_smem(p, P->smem)); else CUDA_TRY(set_op2_smem(p, P->smem));
+    // solver vectors and scalars
+    const size_t nd = (size_t)P->ndof, ng = P->grids.size();
+    if ((rc = dalloc(P, &P->d_b, nd)) || (rc = dalloc(P, &P->d_x, nd)) || (rc = dalloc(P, &P->d_r, nd)) ||
+        (rc = dalloc(P, &P->d_z, nd)) || (rc = dalloc(P, &P->d_p, nd)) || (rc = dalloc(P, &P->d_q, nd)) ||
+        (rc = dalloc(P, &P->d_t1, nd)) || (rc = dalloc(P, &P->d_t2, nd)) ||
+        (rc = dalloc(P, &P->d_partial, P->chunks.size())) || (rc = dalloc(P, &P->d_scal, 8 * ng)) ||
+        (rc = dalloc(P, &P->d_active, ng)) || (rc = dalloc(P, &P->d_iters, ng)) || (rc = dalloc(P, &P->d_nactive, 1)))
+        return rc;
+    std::vector<double> coef(ng);
+    for (size_t i = 0; i < ng; ++i) coef[i] = P->grids[i].coeff;
+    if ((rc = upload(P, &P->d_coef, coef))) return rc;
+    CUDA_TRY(cudaMemsetAsync(P->d_b, 0, nd * 8, s));
+    CUDA_TRY(cudaMemsetAsync(P->d_x, 0, nd * 8, s));
+    CUDA_TRY(cudaMallocHost(&P->h_nactive, sizeof(int)));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SGIGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// helpers for host-or-device pointers
+// ---------------------------------------------------------------------------
+
+static bool is_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int ensure_stage(sgiga_plan_s* P, size_t bytes) {
+    if (P->stage_bytes >= bytes) return SGIGA_OK;
+    if (P->stage) cudaFree(P->stage);
+    P->stage = nullptr;
+    P->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&P->stage, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SGIGA_ERR_NOMEM, "staging buffer allocation failed");
+    }
+    P->stage_bytes = bytes;
+    return SGIGA_OK;
+}
+
+static int run_rhs_operator(sgiga_plan_s* P) {
+    const DevPlan& D = P->dp;
+    CUDA_TRY(cudaMemsetAsync(P->d_b, 0, (size_t)P->ndof * 8, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3(D, nullptr, P->d_b, nullptr, 1, P->stream));
+    else CUDA_TRY(launch_op2(D, nullptr, P->d_b, nullptr, 1, P->stream));
+    return SGIGA_OK;
+}
+
+static int apply_op(sgiga_plan_s* P, const double* x, double* y, const int* active) {
+    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 8, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3(P->dp, x, y, active, 0, P->stream));
+    else CUDA_TRY(launch_op2(P->dp, x, y, active, 0, P->stream));
+    return SGIGA_OK;
+}
+
+static int precond(sgiga_plan_s* P, const double* r, double* z, const int* active) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    if (P->cfg.precond == SGIGA_PRECOND_NONE) {
+        CUDA_TRY(launch_copy(z, r, P->ndof, s));
+        return SGIGA_OK;
+    }
+    const int d = P->d;
+    double* t1 = P->d_t1;
+    double* t2 = P->d_t2;
+    const double* in = r;
+    double* bufs[2] = {t1, t2};
+    int cur = 0;
+    for (int k = 0; k < d; ++k) {
+        double* out = bufs[cur];
+        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, k == d - 1, in, out, active, s));
+        in = out;
+        cur ^= 1;
+    }
+    for (int k = 0; k < d; ++k) {
+        double* out = (k == d - 1) ? z : bufs[cur];
+        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, 0, in, out, active, s));
+        in = out;
+        cur ^= 1;
+    }
+    return SGIGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sgiga_last_error(void) { return g_last_error.c_str(); }
+
+long long sgiga_launch_count(void) { return g_launches.load(); }
+
+int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
+    if (!cfg || !out) return fail(SGIGA_ERR_ARG, "null argument");
+    *out = nullptr;
+    sgiga_config c = *cfg;
+    if (c.d != 2 && c.d != 3) return fail(SGIGA_ERR_ARG, "d must be 2 or 3");
+    if (c.p < 1 || c.p > SGIGA_MAXP) return fail(SGIGA_ERR_ARG, "p must be in 1..4");
+    if (c.continuity < 0) c.continuity = c.p - 1;
+    if (c.continuity > c.p - 1) return fail(SGIGA_ERR_ARG, "continuity must be <= p-1");
+    if (c.min_level < 0) return fail(SGIGA_ERR_ARG, "min_level must be >= 0");
+    if (c.w < c.d * c.min_level - c.d + 1) return fail(SGIGA_ERR_ARG, "w too small for min_level");
+    if (c.domain != SGIGA_DOMAIN_UNIT && c.domain != SGIGA_DOMAIN_ANNULUS) return fail(SGIGA_ERR_ARG, "unknown domain");
+    if (c.grading < 0 || c.grading > 2 || (c.grading != 0 && !(c.gamma > 0))) return fail(SGIGA_ERR_ARG, "bad grading");
+    if (c.precision != SGIGA_PREC_FP64) return fail(SGIGA_ERR_ARG, "unsupported precision");
+    if (c.precond != SGIGA_PRECOND_FD && c.precond != SGIGA_PRECOND_NONE) return fail(SGIGA_ERR_ARG, "bad precond");
+    if (c.domain == SGIGA_DOMAIN_ANNULUS && c.p < 2) return fail(SGIGA_ERR_ARG, "annulus needs p >= 2 (exact circle)");
+    sgiga_plan_s* P = new sgiga_plan_s();
+    P->cfg = c;
+    P->d = c.d; P->p = c.p; P->r = c.continuity; P->m = c.p - c.continuity; P->Q = c.p + 1;
+    P->stream = (cudaStream_t)stream;
+    int rc = build(P);
+    if (rc != SGIGA_OK) {
+        std::string msg = g_last_error;
+        free_plan(P);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = P;
+    return SGIGA_OK;
+}
+
+void sgiga_destroy(sgiga_plan_t plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+}
+
+int sgiga_plan_info(sgiga_plan_t P, sgiga_info* out) {
+    if (!P || !out) return fail(SGIGA_ERR_ARG, "null argument");
+    out->d = P->d; out->p = P->p; out->continuity = P->r;
+    out->ngrids = (int)P->grids.size();
+    out->ndof = P->ndof;
+    out->nqp = P->nqp;
+    out->max_tile_smem = (int)P->smem;
+    out->ntiles = (int)P->tiles.size();
+    return SGIGA_OK;
+}
+
+int sgiga_grid_info(sgiga_plan_t P, int g, sgiga_grid* out) {
+    if (!P || !out) return fail(SGIGA_ERR_ARG, "null argument");
+    if (g < 0 || g >= (int)P->grids.size()) return fail(SGIGA_ERR_ARG, "grid index out of range");
+    const GridDesc& gd = P->grids[g];
+    for (int k = 0; k < 3; ++k) {
+        out->levels[k] = k < P->d ? gd.lev[k] : 0;
+        out->n[k] = k < P->d ? gd.n[k] : 1;
+    }
+    out->coeff = (int)gd.coeff;
+    out->ndof = gd.ndof; out->dof_off = gd.dof_off; out->nqp = gd.nqp; out->qp_off = gd.qp_off;
+    return SGIGA_OK;
+}
+
+int sgiga_qp_coords(sgiga_plan_t P, double* xq) {
+    if (!P || !xq) return fail(SGIGA_ERR_ARG, "null argument");
+    CUDA_TRY(launch_qp_coords(P->dp, xq, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_set_rhs(sgiga_plan_t P, const double* f) {
+    if (!P || !f) return fail(SGIGA_ERR_ARG, "null argument");
+    const double* fd = f;
+    if (!is_device(f)) {
+        int rc = ensure_stage(P, (size_t)P->nqp * 8);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(P->stage, f, (size_t)P->nqp * 8, cudaMemcpyHostToDevice, P->stream));
+        fd = (const double*)P->stage;
+    }
+    CUDA_TRY(launch_rhs_density_user(P->dp, fd, P->stream));
+    int rc = run_rhs_operator(P);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_set_rhs_builtin(sgiga_plan_t P, int source) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (source < 0 || source > SGIGA_SRC_ONE) return fail(SGIGA_ERR_ARG, "unknown source");
+    if ((source == SGIGA_SRC_ANNULUS) && P->d != 2) return fail(SGIGA_ERR_ARG, "source needs d = 2");
+    CUDA_TRY(launch_rhs_density_builtin(P->dp, source, P->stream));
+    int rc = run_rhs_operator(P);
+    if (rc) return rc;
+    CUDA_TRY(cudaGetLastError());
+    return SGIGA_OK;
+}
+
+int sgiga_get_rhs(sgiga_plan_t P, double* b) {
+    if (!P || !b) return fail(SGIGA_ERR_ARG, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(b, P->d_b, (size_t)P->ndof * 8, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_apply(sgiga_plan_t P, const double* x, double* y) {
+    if (!P || !x || !y) return fail(SGIGA_ERR_ARG, "null argument");
+    int rc = apply_op(P, x, y, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(cudaGetLastError());
+    return SGIGA_OK;
+}
+
+int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
+    if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
+    return precond(P, r, z, nullptr);
+}
+
+int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats* stats) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!(rel_tol > 0) || max_iter < 1) return fail(SGIGA_ERR_ARG, "rel_tol must be > 0 and max_iter >= 1");
+    auto t0 = std::chrono::steady_clock::now();
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    double* bb = P->d_scal + 0 * ng;
+    double* rz = P->d_scal + 1 * ng;
+    double* pq = P->d_scal + 2 * ng;
+    double* rr = P->d_scal + 3 * ng;
+    double* alpha = P->d_scal + 4 * ng;
+    double* beta = P->d_scal + 5 * ng;
+    double* rznew = P->d_scal + 6 * ng;
+    CUDA_TRY(launch_pcg_init(D, P->d_b, P->d_x, P->d_r, P->d_partial, bb, s));
+    CUDA_TRY(launch_pcg_start(D, bb, P->d_active, P->d_iters, s));
+    int rc = precond(P, P->d_r, P->d_z, P->d_active);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy(P->d_p, P->d_z, P->ndof, s));
+    CUDA_TRY(launch_dot(D, P->d_r, P->d_z, P->d_partial, rz, s));
+    int it = 0, nact = ng;
+    for (it = 0; it < max_iter; ++it) {
+        if ((rc = apply_op(P, P->d_p, P->d_q, P->d_active))) return rc;
+        CUDA_TRY(launch_dot(D, P->d_p, P->d_q, P->d_partial, pq, s));
+        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, P->d_active, s));
+        CUDA_TRY(launch_pcg_update_xr(D, P->d_x, P->d_r, P->d_p, P->d_q, alpha, P->d_active, P->d_partial, rr, s));
+        CUDA_TRY(launch_pcg_check(D, rr, bb, rel_tol * rel_tol, P->d_active, P->d_iters, P->d_nactive, nullptr, s));
+        CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        nact = *P->h_nactive;
+        if (nact == 0) { ++it; break; }
+        if ((rc = precond(P, P->d_r, P->d_z, P->d_active))) return rc;
+        CUDA_TRY(launch_dot(D, P->d_r, P->d_z, P->d_partial, rznew, s));
+        CUDA_TRY(launch_pcg_beta(D, rz, rznew, beta, s));
+        CUDA_TRY(launch_pcg_update_p(D, P->d_p, P->d_z, beta, P->d_active, s));
+    }
+    if (stats) {
+        std::vector<double> hrr(ng), hbb(ng);
+        std::vector<int> hit(ng);
+        CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(hit.data(), P->d_iters, ng * 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        double mx = 0.0;
+        int mi = 0;
+        for (int g = 0; g < ng; ++g) {
+            if (hbb[g] > 0) mx = std::max(mx, std::sqrt(hrr[g] / hbb[g]));
+            mi = std::max(mi, hit[g]);
+        }
+        stats->iterations = mi;
+        stats->converged = ng - nact;
+        stats->max_rel_residual = mx;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
+    return SGIGA_OK;
+}
+
+int sgiga_get_solution(sgiga_plan_t P, double* u) {
+    if (!P || !u) return fail(SGIGA_ERR_ARG, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(u, P->d_x, (size_t)P->ndof * 8, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_set_solution(sgiga_plan_t P, const double* u) {
+    if (!P || !u) return fail(SGIGA_ERR_ARG, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(P->d_x, u, (size_t)P->ndof * 8, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_eval(sgiga_plan_t P, const double* xi, long long npts, double* ucomp) {
+    if (!P || (!xi && npts > 0) || (!ucomp && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
+    if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    if (npts == 0) return SGIGA_OK;
+    const size_t ng = P->grids.size();
+    const size_t xb = (size_t)npts * P->d * 8, ub = (size_t)npts * ng * 8;
+    const bool xdev = is_device(xi), udev = is_device(ucomp);
+    size_t need = (xdev ? 0 : xb) + (udev ? 0 : ub);
+    int rc = ensure_stage(P, need);
+    if (rc) return rc;
+    char* st = (char*)P->stage;
+    const double* xd = xi;
+    if (!xdev) {
+        CUDA_TRY(cudaMemcpyAsync(st, xi, xb, cudaMemcpyHostToDevice, P->stream));
+        xd = (const double*)st;
+        st += xb;
+    }
+    double* ud = udev ? ucomp : (double*)st;
+    CUDA_TRY(cudaMemsetAsync(P->dp.flags + 1, 0, sizeof(int), P->stream));
+    CUDA_TRY(launch_eval(P->dp, P->d_x, xd, npts, ud, P->stream));
+    int hflag = 0;
+    CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->dp.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    if (!udev) CUDA_TRY(cudaMemcpyAsync(ucomp, ud, ub, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    hflag = *P->h_nactive;
+    if (hflag) return fail(SGIGA_ERR_ARG, "evaluation point outside [0,1]^d");
+    return SGIGA_OK;
+}
+
+int sgiga_combine(sgiga_plan_t P, const double* ucomp, long long npts, double* u) {
+    if (!P || (!ucomp && npts > 0) || (!u && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
+    if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    if (npts == 0) return SGIGA_OK;
+    const size_t ng = P->grids.size();
+    const size_t ub = (size_t)npts * ng * 8, ob = (size_t)npts * 8;
+    const bool idev = is_device(ucomp), odev = is_device(u);
+    int rc = ensure_stage(P, (idev ? 0 : ub) + (odev ? 0 : ob));
+    if (rc) return rc;
+    char* st = (char*)P->stage;
+    const double* ud = ucomp;
+    if (!idev) {
+        CUDA_TRY(cudaMemcpyAsync(st, ucomp, ub, cudaMemcpyHostToDevice, P->stream));
+        ud = (const double*)st;
+        st += ub;
+    }
+    double* od = odev ? u : (double*)st;
+    CUDA_TRY(launch_combine(P->dp, ud, npts, P->d_coef, od, P->stream));
+    if (!odev) CUDA_TRY(cudaMemcpyAsync(u, od, ob, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_basis_table(sgiga_plan_t P, int dir, int level, double* xi, double* w, double* R, double* dR,
+                      int* first) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    auto it = P->tab_of.find(std::make_pair(dir, level));
+    if (it == P->tab_of.end()) return fail(SGIGA_ERR_ARG, "no table for this direction and level");
+    const Table1D& t = P->tabs[it->second];
+    const size_t n = (size_t)t.E * P->Q;
+    const int p1 = P->p + 1;
+    cudaStream_t s = P->stream;
+    if (xi) CUDA_TRY(cudaMemcpyAsync(xi, P->dp.xi + t.off, n * 8, cudaMemcpyDeviceToHost, s));
+    if (w) CUDA_TRY(cudaMemcpyAsync(w, P->dp.w + t.off, n * 8, cudaMemcpyDeviceToHost, s));
+    if (R) CUDA_TRY(cudaMemcpyAsync(R, P->dp.R + t.off * p1, n * p1 * 8, cudaMemcpyDeviceToHost, s));
+    if (dR) CUDA_TRY(cudaMemcpyAsync(dR, P->dp.dR + t.off * p1, n * p1 * 8, cudaMemcpyDeviceToHost, s));
+    if (first) CUDA_TRY(cudaMemcpyAsync(first, P->dp.first + t.eoff, (size_t)t.E * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SGIGA_OK;
+}
+
+int sgiga_geometry_coeffs(sgiga_plan_t P, int g, double* G, double* mw) {
+    if (!P || !G || !mw) return fail(SGIGA_ERR_ARG, "null argument");
+    if (g < 0 || g >= (int)P->grids.size()) return fail(SGIGA_ERR_ARG, "grid index out of range");
+    const GridDesc& gd = P->grids[g];
+    const size_t nq = (size_t)gd.nqp;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, (P->ncomp + 1) * nq * 8);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(SGIGA_ERR_NOMEM, "temporary allocation failed"); }
+    cudaStream_t s = P->stream;
+    e = launch_geometry_natural(P->dp, g, gd, tmp, tmp + P->ncomp * nq, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G, tmp, P->ncomp * nq * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mw, tmp + P->ncomp * nq, nq * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(SGIGA_ERR_CUDA, cudaGetErrorString(e));
+    return SGIGA_OK;
+}
+
+int sgiga_fd_eigen(sgiga_plan_t P, int dir, int level, double* U, double* lam) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    auto it = P->tab_of.find(std::make_pair(dir, level));
+    if (it == P->tab_of.end()) return fail(SGIGA_ERR_ARG, "no table for this direction and level");
+    const Eig1D& e = P->eigs[P->eig_of_tab[it->second]];
+    if (U) CUDA_TRY(cudaMemcpy(U, P->dp.U + e.uoff, (size_t)e.n * e.n * 8, cudaMemcpyDeviceToHost));
+    if (lam) CUDA_TRY(cudaMemcpy(lam, P->dp.lam + e.loff, (size_t)e.n * 8, cudaMemcpyDeviceToHost));
+    return SGIGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Evaluation of every component at parametric points and the combination sum
+// (paper Sec. 3, eq. TD-combi-tec; post-processing of Sec. 4.1).
+//
+//   u_g(xi) = sum_i c_i prod_k R_{i_k}(xi_k),  R = B / W_k  (eq. u-IGA-approx)
+//   u(xi)   = sum_g c_g u_g(xi), FP64 with Neumaier compensation.
+#include "kernels.h"
+#include "spline_dev.cuh"
+
+namespace sgiga {
+
+__global__ void k_eval(DevPlan P, const double* __restrict__ coeffs, const double* __restrict__ xi, long long npts,
+                       double* __restrict__ ucomp) {
+    const int g = blockIdx.y;
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npts) return;
+    const GridDesc& gd = P.grids[g];
+    const int d = P.d, p = P.p;
+    double Rv[3][SGIGA_MAXP + 1];
+    int f0[3];
+    for (int k = 0; k < 3; ++k) {
+        if (k >= d) { Rv[k][0] = 1.0; f0[k] = 1; continue; }
+        const Table1D& tb = P.tabs[gd.tab[k]];
+        const double* kn = P.knots + tb.koff;
+        double t = xi[j * d + k];
+        if (!(t >= 0.0 && t <= 1.0)) {  // outside the parametric domain: report, clamp
+            atomicOr(&P.flags[1], 1);
+            t = t < 0.0 ? 0.0 : 1.0;
+        }
+        int s = find_span(kn, tb.nf, p, t);
+        double N[SGIGA_MAXP + 1];
+        basis_funs<SGIGA_MAXP>(kn, s, p, t, N, nullptr);
+        double W, dW;
+        patch_weight_1d(*P.patch, k, t, W, dW);
+        for (int r = 0; r <= p; ++r) Rv[k][r] = N[r] / W;
+        f0[k] = s - p;
+    }
+    const long long st1 = gd.n[0], st2 = (long long)gd.n[0] * gd.n[1];
+    const double* c = coeffs + gd.dof_off;
+    double u = 0.0;
+    const int pc = d == 3 ? p : 0;
+    for (int rc = 0; rc <= pc; ++rc) {
+        int i2 = d == 3 ? f0[2] + rc : 1;
+        if (d == 3 && (i2 < 1 || i2 > gd.nf[2] - 2)) continue;
+        for (int rb = 0; rb <= p; ++rb) {
+            int i1 = f0[1] + rb;
+            if (i1 < 1 || i1 > gd.nf[1] - 2) continue;
+            double wbc = Rv[1][rb] * Rv[2][rc];
+            double acc = 0.0;
+            for (int ra = 0; ra <= p; ++ra) {
+                int i0 = f0[0] + ra;
+                if (i0 < 1 || i0 > gd.nf[0] - 2) continue;
+                acc += Rv[0][ra] * c[(i0 - 1) + (i1 - 1) * st1 + (d == 3 ? (i2 - 1) * st2 : 0)];
+            }
+            u += wbc * acc;
+        }
+    }
+    ucomp[(long long)g * npts + j] = u;
+}
+
+cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts, double* ucomp,
+                        cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((npts + 127) / 128), P.ngrids);
+    SGIGA_COUNT_LAUNCH();
+    k_eval<<<grid, 128, 0, s>>>(P, coeffs, xi, npts, ucomp);
+    return cudaGetLastError();
+}
+
+__global__ void k_combine(int ng, const double* __restrict__ ucomp, long long npts, const double* __restrict__ coef,
+                          double* __restrict__ u) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npts) return;
+    double sum = 0.0, comp = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        double t = coef[g] * ucomp[(long long)g * npts + j];
+        double v = sum + t;
+        comp += fabs(sum) >= fabs(t) ? (sum - v) + t : (t - v) + sum;
+        sum = v;
+    }
+    u[j] = sum + comp;
+}
+
+cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts, const double* coef, double* u,
+                           cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_combine<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(P.ngrids, ucomp, npts, coef, u);
+    return cudaGetLastError();
+}
+
+}  // namespace sgiga

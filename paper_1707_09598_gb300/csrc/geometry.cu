@@ -1,0 +1,252 @@
+// Geometry coefficients and load density at every quadrature point.
+//
+// For the Galerkin stiffness of Problem 1 pulled back to the parametric
+// domain (Sec. 2.2, eqs. F-B-splines, spline_space_phys):
+//   K_ij = sum_q grad R_i^T G_q grad R_j,  G_q = w_q |det J_q| (J_q^T J_q)^{-1},
+//   b_i  = sum_q R_i rho_q,               rho_q = f(F(xi_q)) w_q |det J_q|.
+// G is stored as d(d+1)/2 planes in the LOGICAL axis order of the operator
+// kernel's tiles (a, b, c = perm of the physical directions), tile-major.
+#include <math.h>
+
+#include "kernels.h"
+#include "spline_dev.cuh"
+
+namespace sgiga {
+
+// Tile-major qp index -> per-physical-direction global qp coordinate.
+struct QpLoc {
+    int qg[3];   // global qp index along each physical direction
+};
+
+__device__ __forceinline__ QpLoc tile_qp(const GridDesc& g, const TileDesc& t, int d, int Q, int idx) {
+    const int pa = g.perm[0], pb = g.perm[1], pc = g.perm[2];
+    int QTb = Q * g.T[pb];
+    int npen = d == 3 ? QTb * Q * g.T[pc] : QTb;
+    int qa = idx / npen, pid = idx - qa * npen;
+    int qb = pid % QTb, qc = pid / QTb;
+    QpLoc L;
+    L.qg[0] = L.qg[1] = L.qg[2] = 0;
+    L.qg[pa] = Q * t.e0[pa] + qa;
+    L.qg[pb] = Q * t.e0[pb] + qb;
+    if (d == 3) L.qg[pc] = Q * t.e0[pc] + qc;
+    return L;
+}
+
+__device__ __forceinline__ long long natural_index(const GridDesc& g, int d, int Q, const QpLoc& L) {
+    long long i = L.qg[0];
+    if (d >= 2) i += (long long)Q * g.E[0] * L.qg[1];
+    if (d == 3) i += (long long)Q * g.E[0] * Q * g.E[1] * L.qg[2];
+    return g.qp_off + i;
+}
+
+__device__ __forceinline__ void qp_param(const DevPlan& P, const GridDesc& g, const QpLoc& L, double* xi,
+                                         double& wq) {
+    wq = 1.0;
+    for (int k = 0; k < P.d; ++k) {
+        const Table1D& tb = P.tabs[g.tab[k]];
+        xi[k] = P.xi[tb.off + L.qg[k]];
+        wq *= P.w[tb.off + L.qg[k]];
+    }
+    for (int k = P.d; k < 3; ++k) xi[k] = 0.0;
+}
+
+// Symmetric inverse of J^T J (d x d) times s; returns det J.
+__device__ __forceinline__ double metric(int d, const double J[3][3], double s, double Gp[3][3]) {
+    double A[3][3];
+    for (int k = 0; k < d; ++k)
+        for (int l = 0; l < d; ++l) {
+            double v = 0.0;
+            for (int i = 0; i < d; ++i) v += J[i][k] * J[i][l];
+            A[k][l] = v;
+        }
+    double det;
+    if (d == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        double da = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        double f = s * fabs(det) / da;
+        Gp[0][0] = A[1][1] * f;
+        Gp[1][1] = A[0][0] * f;
+        Gp[0][1] = Gp[1][0] = -A[0][1] * f;
+    } else {
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+              J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+        double c01 = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+        double c02 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+        double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+        double c12 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+        double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        double da = A[0][0] * c00 + A[0][1] * (A[1][2] * A[2][0] - A[1][0] * A[2][2]) + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        double f = s * fabs(det) / da;
+        Gp[0][0] = c00 * f; Gp[0][1] = Gp[1][0] = c01 * f; Gp[0][2] = Gp[2][0] = c02 * f;
+        Gp[1][1] = c11 * f; Gp[1][2] = Gp[2][1] = c12 * f; Gp[2][2] = c22 * f;
+    }
+    return det;
+}
+
+__global__ void k_geometry(DevPlan P) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    const int ncomp = d * (d + 1) / 2;
+    const Patch& pt = *P.patch;
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        double xi[3], wq;
+        qp_param(P, g, L, xi, wq);
+        double x[3], J[3][3];
+        patch_eval(pt, xi, x, J);
+        double Gp[3][3];
+        double det = metric(d, J, wq, Gp);
+        if (!(det > 0.0)) atomicOr(&P.flags[0], 1);
+        long long o = t.g_off + idx;
+        int c = 0;
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) P.G[(long long)(c++) * P.nqp + o] = Gp[g.perm[a]][g.perm[b]];
+        (void)ncomp;
+        P.mw[o] = wq * fabs(det);
+    }
+}
+
+cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_geometry<<<P.ntiles, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+__global__ void k_qp_coords(DevPlan P, double* xq) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        double xi[3], wq, x[3], J[3][3];
+        qp_param(P, g, L, xi, wq);
+        patch_eval(*P.patch, xi, x, J);
+        long long nat = natural_index(g, d, Q, L);
+        for (int k = 0; k < d; ++k) xq[(long long)k * P.nqp + nat] = x[k];
+    }
+}
+
+cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_qp_coords<<<P.ntiles, 256, 0, s>>>(P, xq);
+    return cudaGetLastError();
+}
+
+// f = -Laplace(u) of the built-in manufactured solutions (derived by hand).
+__device__ double builtin_source(int src, int d, const double* x) {
+    const double pi = 3.14159265358979323846;
+    switch (src) {
+    case 0: {  // u = prod sin(pi x_k)
+        double v = d * pi * pi;
+        for (int k = 0; k < d; ++k) v *= sin(pi * x[k]);
+        return v;
+    }
+    case 1: {  // u = prod x_k (1 - x_k): -Laplace u = sum_k 2 prod_{j != k} x_j (1 - x_j)
+        double v = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double t = 2.0;
+            for (int j = 0; j < d; ++j) if (j != k) t *= x[j] * (1.0 - x[j]);
+            v += t;
+        }
+        return v;
+    }
+    case 2: {  // u = x y phi sin x, phi = (r^2-1)(r^2-4)
+        double X = x[0], Y = x[1], r2 = X * X + Y * Y;
+        double phi = (r2 - 1.0) * (r2 - 4.0);
+        double sx = sin(X), cx = cos(X);
+        double lap = phi * (2.0 * Y * cx - X * Y * sx) + 2.0 * (4.0 * r2 - 10.0) * (2.0 * X * Y * sx + X * X * Y * cx) +
+                     X * Y * sx * (16.0 * r2 - 20.0);
+        return -lap;
+    }
+    case 3: {  // u = -phi x y^2 [sin(pi z)]
+        double X = x[0], Y = x[1], r2 = X * X + Y * Y;
+        double phi = (r2 - 1.0) * (r2 - 4.0);
+        double u2 = -phi * X * Y * Y;
+        double lap2 = phi * (-2.0 * X) + 2.0 * (4.0 * r2 - 10.0) * (-3.0 * X * Y * Y) + (-X * Y * Y) * (16.0 * r2 - 20.0);
+        if (d == 2) return -lap2;
+        return (-lap2 + pi * pi * u2) * sin(pi * x[2]);
+    }
+    default:
+        return 1.0;
+    }
+}
+
+__global__ void k_rhs_density(DevPlan P, int src, const double* __restrict__ fnat) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        double f;
+        if (fnat) {
+            f = fnat[natural_index(g, d, Q, L)];
+        } else {
+            double xi[3], wq, x[3], J[3][3];
+            qp_param(P, g, L, xi, wq);
+            patch_eval(*P.patch, xi, x, J);
+            f = builtin_source(src, d, x);
+        }
+        long long o = t.g_off + idx;
+        P.rho[o] = f * P.mw[o];
+    }
+}
+
+cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_rhs_density<<<P.ntiles, 256, 0, s>>>(P, source, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_rhs_density<<<P.ntiles, 256, 0, s>>>(P, 0, f_nat);
+    return cudaGetLastError();
+}
+
+// Copy one grid's G (physical component order) and mw into natural order.
+__global__ void k_geometry_natural(DevPlan P, int tile0, double* Gnat, double* mwnat) {
+    const TileDesc t = P.tiles[tile0 + blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    // logical component index of physical pair (k, l)
+    int lidx[3][3];
+    {
+        int inv[3];
+        for (int a = 0; a < d; ++a) inv[g.perm[a]] = a;
+        int c = 0, tab[3][3];
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) { tab[a][b] = tab[b][a] = c++; }
+        for (int k = 0; k < d; ++k)
+            for (int l = 0; l < d; ++l) lidx[k][l] = tab[inv[k]][inv[l]];
+    }
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        long long nat = natural_index(g, d, Q, L) - g.qp_off;
+        long long o = t.g_off + idx;
+        int c = 0;
+        for (int k = 0; k < d; ++k)
+            for (int l = k; l < d; ++l) Gnat[(long long)(c++) * g.nqp + nat] = P.G[(long long)lidx[k][l] * P.nqp + o];
+        mwnat[nat] = P.mw[o];
+    }
+}
+
+cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh, double* Gnat, double* mwnat,
+                                    cudaStream_t s) {
+    (void)g;
+    SGIGA_COUNT_LAUNCH();
+    k_geometry_natural<<<gh.ntiles, 256, 0, s>>>(P, gh.tile0, Gnat, mwnat);
+    return cudaGetLastError();
+}
+
+}  // namespace sgiga

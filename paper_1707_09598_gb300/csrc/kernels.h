@@ -1,0 +1,80 @@
+// Launchers of the CUDA kernels (defined in the *.cu files of this directory).
+#pragma once
+#include "internal.h"
+
+#include <atomic>
+
+namespace sgiga {
+
+// Number of kernels this library has launched (diagnostic, process-wide).
+extern std::atomic<long long> g_launches;
+#define SGIGA_COUNT_LAUNCH() (::sgiga::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+struct DevPlan {
+    int d, p, m, Q, ngrids, ntiles, ntabs, nchunks;
+    long long ndof, nqp;
+    const GridDesc* grids;
+    const TileDesc* tiles;
+    const int* sched;        // tile indices in launch (LPT) order
+    const Table1D* tabs;
+    const Eig1D* eigs;
+    const Chunk* chunks;
+    const Patch* patch;
+    const double* knots;
+    const double* bp;        // breakpoints per table
+    const double* gauss;     // [Q] nodes on [-1,1] then [Q] weights
+    double* xi;              // per-table Gauss points
+    double* w;               // per-table Gauss weights (times h/2)
+    double* R;               // per-table basis values [E][Q][p+1]
+    double* dR;
+    int* first;              // per-table first function of each element
+    double* G;               // ncomp planes of nqp (tile-major)
+    double* mw;              // w |det J| (tile-major)
+    double* rho;             // f w |det J| (tile-major)
+    const double* U;
+    const double* lam;
+    int* flags;              // [0] = geometry error, [1] = eval error
+    size_t smem_op;          // dynamic shared bytes of the operator kernel
+};
+
+// basis.cu
+cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
+// geometry.cu
+cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s);
+cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s);
+cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s);
+cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh, double* Gnat,
+                                    double* mwnat, cudaStream_t s);
+// apply2.cu / apply3.cu: mode 0 = stiffness apply y += K x, mode 1 = load vector y += b
+cudaError_t launch_op2(const DevPlan& P, const double* x, double* y, const int* active, int mode, cudaStream_t s);
+cudaError_t launch_op3(const DevPlan& P, const double* x, double* y, const int* active, int mode, cudaStream_t s);
+cudaError_t set_op2_smem(int p, size_t bytes);
+cudaError_t set_op3_smem(int p, size_t bytes);
+// fd.cu
+cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
+                           int scale, const double* in, double* out, const int* active, cudaStream_t s);
+// vec.cu
+cudaError_t launch_dot(const DevPlan& P, const double* a, const double* b, double* partial, double* out,
+                       cudaStream_t s);
+cudaError_t launch_pcg_init(const DevPlan& P, const double* b, double* x, double* r, double* partial,
+                            double* bb, cudaStream_t s);
+cudaError_t launch_pcg_update_xr(const DevPlan& P, double* x, double* r, const double* p, const double* q,
+                                 const double* alpha, const int* active, double* partial, double* rr,
+                                 cudaStream_t s);
+cudaError_t launch_pcg_update_p(const DevPlan& P, double* p, const double* z, const double* beta,
+                                const int* active, cudaStream_t s);
+cudaError_t launch_pcg_alpha(const DevPlan& P, const double* rz, const double* pq, double* alpha,
+                             const int* active, cudaStream_t s);
+cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, double* beta, cudaStream_t s);
+cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* bb, double tol2, int* active,
+                             int* iters, int* nactive, double* maxrel, cudaStream_t s);
+cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, int* active, int* iters, cudaStream_t s);
+cudaError_t launch_copy(double* dst, const double* src, long long n, cudaStream_t s);
+// eval.cu
+cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts,
+                        double* ucomp, cudaStream_t s);
+cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts, const double* coef,
+                           double* u, cudaStream_t s);
+
+}  // namespace sgiga

@@ -1,0 +1,29 @@
+// Shared pieces of the matrix-free operator kernels (sum factorisation of the
+// Galerkin stiffness and load vector of Problem 1, Sec. 2.2).
+//
+// A thread block owns one tile of T_a x T_b (x T_c) elements of one component.
+// Logical axes: a = the "pencil" axis processed per thread in registers, b and
+// c the axes contracted through shared memory. Local DoF j of a tile along an
+// axis with first element E0 is the full 1D index E0*m + j (m = p - r = knot
+// multiplicity; element e's functions are e*m .. e*m + p). Dirichlet DoFs
+// (full index 0 and nf-1) read as zero and are never written.
+#pragma once
+#include "internal.h"
+#include "kernels.h"
+
+namespace sgiga {
+
+__device__ __forceinline__ int elem_lo(int j, int P, int M) { return j >= P ? (j - P + M - 1) / M : 0; }
+__device__ __forceinline__ int elem_hi(int j, int M, int T) { int e = j / M; return e < T - 1 ? e : T - 1; }
+
+// Shared-memory footprint (doubles) of one tile; T are logical extents.
+__host__ __device__ inline long long op_smem_doubles(int d, int P, int M, const int* T) {
+    const int Q = P + 1, P1 = P + 1;
+    long long L[3], tab = 0;
+    for (int x = 0; x < d; ++x) { L[x] = (long long)(T[x] - 1) * M + P1; tab += 2LL * P1 * Q * T[x]; }
+    long long LaP = L[0] | 1;
+    if (d == 2) return tab + L[0] * L[1] + 2LL * Q * T[1] * LaP;
+    return tab + L[0] * L[1] * L[2] + 2LL * Q * T[2] * L[1] * L[0] + 3LL * (Q * T[1]) * (Q * T[2]) * LaP;
+}
+
+}  // namespace sgiga

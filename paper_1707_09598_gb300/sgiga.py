@@ -1,0 +1,265 @@
+"""Python binding of the C ABI in include/sgiga.h (argument marshalling only).
+
+Every function has the name of its C entry point and forwards to it through
+ctypes; all arithmetic runs in the CUDA library. Buffers may be torch tensors
+(CUDA or CPU) or numpy arrays, float64 and contiguous; a host buffer is staged
+by the library. Importing this module fails loudly if the library is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsgiga.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsgiga.so is not built (%s); run paper_1707_09598_gb300.build.build()" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SGIGA_OK = 0
+SGIGA_ERR_ARG = -1
+SGIGA_ERR_NOMEM = -2
+SGIGA_ERR_CUDA = -3
+SGIGA_ERR_NOT_CONVERGED = -4
+SGIGA_ERR_TIMEOUT = -5
+SGIGA_ERR_GEOMETRY = -6
+
+DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1}
+GRADING = {"uniform": 0, "radical": 1, "onesided": 2}
+PREC = {"fp64": 0}
+PRECOND = {"fd": 0, "none": 1}
+SOURCE = {"sine": 0, "poly": 1, "annulus": 2, "annulus_paper": 3, "one": 4}
+
+
+class sgiga_config(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("w", ctypes.c_int),
+                ("min_level", ctypes.c_int), ("domain", ctypes.c_int), ("grading", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+class sgiga_info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("ngrids", ctypes.c_int),
+                ("ndof", ctypes.c_longlong), ("nqp", ctypes.c_longlong), ("max_tile_smem", ctypes.c_int),
+                ("ntiles", ctypes.c_int)]
+
+
+class sgiga_grid(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int * 3), ("n", ctypes.c_int * 3), ("coeff", ctypes.c_int),
+                ("ndof", ctypes.c_longlong), ("dof_off", ctypes.c_longlong), ("nqp", ctypes.c_longlong),
+                ("qp_off", ctypes.c_longlong)]
+
+
+class sgiga_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_L = ctypes.c_longlong
+_SIGS = {
+    "sgiga_plan": (_I, [ctypes.POINTER(sgiga_config), _P, ctypes.POINTER(_P)]),
+    "sgiga_destroy": (None, [_P]),
+    "sgiga_plan_info": (_I, [_P, ctypes.POINTER(sgiga_info)]),
+    "sgiga_grid_info": (_I, [_P, _I, ctypes.POINTER(sgiga_grid)]),
+    "sgiga_qp_coords": (_I, [_P, _P]),
+    "sgiga_set_rhs": (_I, [_P, _P]),
+    "sgiga_set_rhs_builtin": (_I, [_P, _I]),
+    "sgiga_get_rhs": (_I, [_P, _P]),
+    "sgiga_apply": (_I, [_P, _P, _P]),
+    "sgiga_precond": (_I, [_P, _P, _P]),
+    "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
+    "sgiga_get_solution": (_I, [_P, _P]),
+    "sgiga_set_solution": (_I, [_P, _P]),
+    "sgiga_eval": (_I, [_P, _P, _L, _P]),
+    "sgiga_combine": (_I, [_P, _P, _L, _P]),
+    "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
+    "sgiga_geometry_coeffs": (_I, [_P, _I, _P, _P]),
+    "sgiga_fd_eigen": (_I, [_P, _I, _I, _P, _P]),
+    "sgiga_last_error": (ctypes.c_char_p, []),
+    "sgiga_launch_count": (ctypes.c_longlong, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = sorted(_SIGS)
+
+
+class SgigaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("sgiga error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc != SGIGA_OK:
+        raise SgigaError(rc, _lib.sgiga_last_error().decode())
+    return rc
+
+
+def _ptr(buf, n=None, dtype=np.float64):
+    """Address of a contiguous buffer (torch tensor or numpy array), checked."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):          # torch tensor
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if buf.dtype != want or not buf.is_contiguous():
+            raise TypeError("expected a contiguous %s tensor" % want)
+        if n is not None and buf.numel() < n:
+            raise ValueError("buffer has %d elements, needs %d" % (buf.numel(), n))
+        return buf.data_ptr()
+    arr = buf
+    if not isinstance(arr, np.ndarray) or arr.dtype != dtype or not arr.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous numpy array of %s" % np.dtype(dtype))
+    if n is not None and arr.size < n:
+        raise ValueError("buffer has %d elements, needs %d" % (arr.size, n))
+    return arr.ctypes.data
+
+
+# --- entry points (same names as the C ABI) ------------------------------------
+
+def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="uniform", gamma=1.0,
+               precision="fp64", precond="fd", stream=None):
+    cfg = sgiga_config(d, p, continuity, w, min_level, DOMAIN[domain], GRADING[grading], float(gamma),
+                       PREC[precision], PRECOND[precond])
+    h = _P()
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(_lib.sgiga_plan(ctypes.byref(cfg), s, ctypes.byref(h)))
+    return h
+
+
+def sgiga_destroy(plan):
+    _lib.sgiga_destroy(plan)
+
+
+def sgiga_plan_info(plan):
+    out = sgiga_info()
+    _check(_lib.sgiga_plan_info(plan, ctypes.byref(out)))
+    return out
+
+
+def sgiga_grid_info(plan, g):
+    out = sgiga_grid()
+    _check(_lib.sgiga_grid_info(plan, g, ctypes.byref(out)))
+    return out
+
+
+def sgiga_qp_coords(plan, xq):
+    _check(_lib.sgiga_qp_coords(plan, _ptr(xq)))
+
+
+def sgiga_set_rhs(plan, f_qp):
+    n = sgiga_plan_info(plan).nqp
+    _check(_lib.sgiga_set_rhs(plan, _ptr(f_qp, n)))
+
+
+def sgiga_set_rhs_builtin(plan, source):
+    _check(_lib.sgiga_set_rhs_builtin(plan, SOURCE[source] if isinstance(source, str) else int(source)))
+
+
+def sgiga_get_rhs(plan, b):
+    _check(_lib.sgiga_get_rhs(plan, _ptr(b, sgiga_plan_info(plan).ndof)))
+
+
+def sgiga_apply(plan, x, y):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_apply(plan, _ptr(x, n), _ptr(y, n)))
+
+
+def sgiga_precond(plan, r, z):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_precond(plan, _ptr(r, n), _ptr(z, n)))
+
+
+def sgiga_solve(plan, rel_tol, max_iter, check=True):
+    st = sgiga_solve_stats()
+    rc = _lib.sgiga_solve(plan, float(rel_tol), int(max_iter), ctypes.byref(st))
+    if check:
+        _check(rc)
+    return st, rc
+
+
+def sgiga_get_solution(plan, u):
+    _check(_lib.sgiga_get_solution(plan, _ptr(u, sgiga_plan_info(plan).ndof)))
+
+
+def sgiga_set_solution(plan, u):
+    _check(_lib.sgiga_set_solution(plan, _ptr(u, sgiga_plan_info(plan).ndof)))
+
+
+def sgiga_eval(plan, xi, npts, u_comp):
+    info = sgiga_plan_info(plan)
+    _check(_lib.sgiga_eval(plan, _ptr(xi, npts * info.d), int(npts), _ptr(u_comp, npts * info.ngrids)))
+
+
+def sgiga_combine(plan, u_comp, npts, u):
+    info = sgiga_plan_info(plan)
+    _check(_lib.sgiga_combine(plan, _ptr(u_comp, npts * info.ngrids), int(npts), _ptr(u, npts)))
+
+
+def sgiga_basis_table(plan, dir, level):
+    info = sgiga_plan_info(plan)
+    E, Q = 2 ** level, info.p + 1
+    xi, w = np.zeros(E * Q), np.zeros(E * Q)
+    R, dR = np.zeros(E * Q * (info.p + 1)), np.zeros(E * Q * (info.p + 1))
+    first = np.zeros(E, dtype=np.int32)
+    _check(_lib.sgiga_basis_table(plan, dir, level, _ptr(xi), _ptr(w), _ptr(R), _ptr(dR),
+                                  _ptr(first, dtype=np.int32)))
+    return xi, w, R.reshape(E, Q, info.p + 1), dR.reshape(E, Q, info.p + 1), first
+
+
+def sgiga_geometry_coeffs(plan, g):
+    info = sgiga_plan_info(plan)
+    gi = sgiga_grid_info(plan, g)
+    nc = info.d * (info.d + 1) // 2
+    G = np.zeros(nc * gi.nqp)
+    mw = np.zeros(gi.nqp)
+    _check(_lib.sgiga_geometry_coeffs(plan, g, _ptr(G), _ptr(mw)))
+    return G.reshape(nc, gi.nqp), mw
+
+
+def sgiga_fd_eigen(plan, dir, level, n):
+    U = np.zeros(n * n)
+    lam = np.zeros(n)
+    _check(_lib.sgiga_fd_eigen(plan, dir, level, _ptr(U), _ptr(lam)))
+    return U.reshape(n, n), lam
+
+
+def sgiga_launch_count():
+    return int(_lib.sgiga_launch_count())
+
+
+def sgiga_last_error():
+    return _lib.sgiga_last_error().decode()
+
+
+class Plan:
+    """Owning handle: a plan plus its metadata (marshalling helper only)."""
+
+    def __init__(self, d, p, w, **kw):
+        self.handle = sgiga_plan(d, p, w, **kw)
+        self.info = sgiga_plan_info(self.handle)
+        self.grids = [sgiga_grid_info(self.handle, g) for g in range(self.info.ngrids)]
+
+    def close(self):
+        if self.handle:
+            sgiga_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

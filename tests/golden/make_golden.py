@@ -1,0 +1,67 @@
+"""Write the oracle's stored expected values used by the full-size GPU parity tests.
+
+Calls only the oracle (oracle/) and the shared seeded input module. Run from
+the repository root:
+
+    python tests/golden/make_golden.py cube_p3_w10
+
+Output: tests/golden/<name>.txt with, for each parametric evaluation point,
+the combined sparse-grid value sum_i c_i u_i(xi) and the values of a few
+selected components. The components are solved in parallel worker processes
+(started with "spawn").
+"""
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+# name -> (domain, d, p, w, problem, eval lattice k, selected components)
+CASES = {
+    "cube_p3_w10": ("unit", 3, 3, 10, "sine3", 16, [(10, 1, 1), (4, 4, 4), (1, 5, 4), (3, 3, 4)]),
+    "annulus_p3_w9": ("annulus", 2, 3, 9, "annulus_sinx", 64, [(9, 1), (5, 5), (1, 9)]),
+}
+
+
+def _one(args):
+    domain, d, p, i, problem, pts = args
+    from oracle import geometry, problems
+    from oracle.galerkin import Component
+    comp = Component(geometry.make(domain, d), i, p).assemble(f=problems.get(problem).f)
+    u = comp.solve()
+    return comp.evaluate(u, pts)
+
+
+def main(name):
+    from oracle import combination
+    from paper_1707_09598_gb300.inputs import eval_points
+    domain, d, p, w, problem, k, sel = CASES[name]
+    pts = eval_points(d, k)
+    idx = combination.index_set(d, w)
+    t0 = time.time()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(8, os.cpu_count())) as pool:
+        vals = pool.map(_one, [(domain, d, p, i, problem, pts) for i, _ in idx], chunksize=1)
+    vals = np.stack(vals)
+    coeffs = np.array([c for _, c in idx], dtype=np.float64)
+    comb = combination.combine(vals, coeffs)
+    grids = [i for i, _ in idx]
+    cols = [comb] + [vals[grids.index(s)] for s in sel]
+    out = os.path.join(HERE, name + ".txt")
+    with open(out, "w") as fh:
+        fh.write("# oracle values written by tests/golden/make_golden.py %s\n" % name)
+        fh.write("# domain=%s d=%d p=%d C^%d w=%d problem=%s lattice k=%d (eval_points(d, k))\n"
+                 % (domain, d, p, p - 1, w, problem, k))
+        fh.write("# columns: combined %s\n" % " ".join("u" + "_".join(map(str, s)) for s in sel))
+        for row in np.stack(cols, axis=1):
+            fh.write(" ".join("%.17e" % v for v in row) + "\n")
+    print("wrote %s in %.1f s" % (out, time.time() - t0))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1])
