@@ -497,7 +497,14 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
     // operator kernel shared memory
-    if (d == 3) CUDA_TRY(set_op3_smem(p, P->smem)); else CUDA_TRY(set_op2_smem(p, P->smem));
+    {   // the attribute only grows, so plans that coexist keep working
+        static size_t granted[2][SGIGA_MAXP + 1] = {{0}};
+        size_t& gr = granted[d - 2][p];
+        if (P->smem > gr) {
+            if (d == 3) CUDA_TRY(set_op3_smem(p, P->smem)); else CUDA_TRY(set_op2_smem(p, P->smem));
+            gr = P->smem;
+        }
+    }
     // solver vectors and scalars
     const size_t nd = (size_t)P->ndof, ng = P->grids.size();
     if ((rc = dalloc(P, &P->d_b, nd)) || (rc = dalloc(P, &P->d_x, nd)) || (rc = dalloc(P, &P->d_r, nd)) ||
