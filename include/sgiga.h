@@ -103,6 +103,9 @@ typedef struct {
     int n[3];          /* interior DoFs per direction */
     int coeff;         /* combination coefficient c_i */
     long long ndof, dof_off, nqp, qp_off;
+    int tile[3];       /* elements per tile of the operator kernels, per direction */
+    int pencil_dir;    /* direction processed per thread in registers */
+    int ntiles;        /* tiles of this component */
 } sgiga_grid;
 
 typedef struct {

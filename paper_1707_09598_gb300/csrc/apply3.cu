@@ -62,6 +62,7 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int i = tid; i < cnt; i += nth) { tb[k][i] = Pl.R[base + i]; tdv[k][i] = Pl.dR[base + i]; }
     }
     const long long doff = g.dof_off;
+    __syncthreads();   // tables visible to every thread before any stage reads them
     if (MODE == 0) {
         const int nX = La * Lb * Lc;
         for (int idx = tid; idx < nX; idx += nth) {

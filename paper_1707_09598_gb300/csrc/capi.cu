@@ -659,6 +659,9 @@ int sgiga_grid_info(sgiga_plan_t P, int g, sgiga_grid* out) {
     }
     out->coeff = (int)gd.coeff;
     out->ndof = gd.ndof; out->dof_off = gd.dof_off; out->nqp = gd.nqp; out->qp_off = gd.qp_off;
+    for (int k = 0; k < 3; ++k) out->tile[k] = k < P->d ? gd.T[k] : 1;
+    out->pencil_dir = gd.perm[0];
+    out->ntiles = gd.ntiles;
     return SGIGA_OK;
 }
 

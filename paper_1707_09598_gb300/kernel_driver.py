@@ -1,0 +1,70 @@
+"""Run one operation of the library repeatedly on a fixed workload (for timing
+and profiler captures of a single kernel family).
+
+  python -m paper_1707_09598_gb300.kernel_driver --op apply --reps 3 [--d 3 --p 3 --w 10]
+
+Ops: apply (stiffness apply), precond (fast diagonalisation), rhs (load
+vector), solve (batched PCG), eval (evaluation + combination on the 17^d
+lattice). Prints the mean CUDA-event time per repetition.
+"""
+import argparse
+import os
+import sys
+
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1707_09598_gb300 import sgiga  # noqa: E402
+from paper_1707_09598_gb300.inputs import eval_points, random_vector  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="apply", choices=["apply", "precond", "rhs", "solve", "eval"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--d", type=int, default=3)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--w", type=int, default=10)
+    ap.add_argument("--domain", default="unit")
+    a = ap.parse_args()
+    stream = torch.cuda.Stream()
+    P = sgiga.Plan(a.d, a.p, a.w, domain=a.domain, stream=stream)
+    n = P.info.ndof
+    x = torch.as_tensor(random_vector(n, 1), device="cuda")
+    y = torch.zeros_like(x)
+    src = "sine" if a.domain == "unit" else "annulus_paper"
+    sgiga.sgiga_set_rhs_builtin(P.handle, src)
+    pts = torch.as_tensor(eval_points(a.d, 16), device="cuda")
+    uc = torch.zeros(P.info.ngrids * len(pts), dtype=torch.float64, device="cuda")
+    u = torch.zeros(len(pts), dtype=torch.float64, device="cuda")
+
+    def op():
+        if a.op == "apply":
+            sgiga.sgiga_apply(P.handle, x, y)
+        elif a.op == "precond":
+            sgiga.sgiga_precond(P.handle, x, y)
+        elif a.op == "rhs":
+            sgiga.sgiga_set_rhs_builtin(P.handle, src)
+        elif a.op == "solve":
+            sgiga.sgiga_solve(P.handle, 1e-12, 50)
+        else:
+            sgiga.sgiga_eval(P.handle, pts, len(pts), uc)
+            sgiga.sgiga_combine(P.handle, uc, len(pts), u)
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.reps):
+        op()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print("op=%s reps=%d mean_ms=%.4f ndof=%d nqp=%d ntiles=%d" %
+          (a.op, a.reps, e0.elapsed_time(e1) / a.reps, n, P.info.nqp, P.info.ntiles))
+    P.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -48,7 +48,8 @@ class sgiga_info(ctypes.Structure):
 class sgiga_grid(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int * 3), ("n", ctypes.c_int * 3), ("coeff", ctypes.c_int),
                 ("ndof", ctypes.c_longlong), ("dof_off", ctypes.c_longlong), ("nqp", ctypes.c_longlong),
-                ("qp_off", ctypes.c_longlong)]
+                ("qp_off", ctypes.c_longlong), ("tile", ctypes.c_int * 3), ("pencil_dir", ctypes.c_int),
+                ("ntiles", ctypes.c_int)]
 
 
 class sgiga_solve_stats(ctypes.Structure):

@@ -147,6 +147,40 @@ def test_apply_and_rhs(sg, case):
             assert _rel(b[sl], comp.b) < 1e-13, (g.levels[:d], _rel(b[sl], comp.b))
 
 
+MULTI_TILE = [("unit", 2, 3, 2, 10, "uniform", 1.0, 1), ("annulus", 2, 2, 1, 10, "radical", 3.0, 1),
+              ("unit", 2, 2, 0, 9, "uniform", 1.0, 1), ("unit", 3, 3, 2, 8, "uniform", 1.0, 1),
+              ("annulus", 3, 2, 1, 7, "uniform", 1.0, 1)]
+
+
+@pytest.mark.parametrize("case", MULTI_TILE)
+def test_apply_multi_tile(sg, case):
+    """Operator apply and load vector on components that span many tiles
+    (sampled components for the 3D cases)."""
+    domain, d, p, r, w, grading, gamma, mn = case
+    src = {"unit": "sine", "annulus": "annulus_paper"}[domain]
+    prob = problems.get({("unit", 2): "sine2", ("unit", 3): "sine3", ("annulus", 2): "annulus_paper2",
+                         ("annulus", 3): "annulus_paper3"}[(domain, d)])
+    with _plan(sg, case) as P:
+        n = P.info.ndof
+        x = random_vector(n, seed=21)
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_apply(P.handle, _dev(x), y)
+        sg.sgiga_set_rhs_builtin(P.handle, src)
+        b = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_get_rhs(P.handle, b)
+        y, b = y.cpu().numpy(), b.cpu().numpy()
+        grids = list(P.grids)
+        if d == 3:
+            multi = [g for g in grids if g.ntiles > 1]
+            grids = [multi[0], multi[len(multi) // 2], multi[-1], grids[0]]
+        assert sum(g.ntiles >= 4 for g in grids) >= 2
+        for g in grids:
+            comp = _component(case, g).assemble(f=prob.f)
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            assert _rel(y[sl], comp.K @ x[sl]) < 1e-13, (g.levels[:d], g.ntiles)
+            assert _rel(b[sl], comp.b) < 1e-13, (g.levels[:d], g.ntiles)
+
+
 @pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3], CASES[5], CASES[7], CASES[8]])
 def test_preconditioner(sg, case):
     domain, d, p, r, w, grading, gamma, mn = case
@@ -275,11 +309,14 @@ def test_cube_p3_w10_full_size(sg):
         sg.sgiga_get_solution(P.handle, u)
         u = u.cpu().numpy()
         prob = problems.get("sine3")
+        # coefficients: forward error <= cond(K) x relative residual; at the solve's
+        # 1e-12 residual the longest components (n = 1025 x 3 x 3) sit near 1e-10
+        # against the direct solve, which carries a rounding error of the same kind
         for sel in [(1, 1, 10), (2, 6, 3)]:
             g = P.grids[levels.index(sel)]
             comp = Component(geometry.UnitCube(3), sel, 3).assemble(f=prob.f)
             sl = slice(g.dof_off, g.dof_off + g.ndof)
-            assert _rel(u[sl], comp.solve()) < 1e-10
+            assert _rel(u[sl], comp.solve()) < 1e-9
 
 
 def test_host_buffers_and_user_rhs(sg):
