@@ -134,12 +134,17 @@ int sgiga_qp_coords(sgiga_plan_t plan, double* xq);
 
 /* Load vector b_i = sum_q w_q |det J_q| f(x_q) R_i(xi_q) (Sec. 2.2, Galerkin
  * right-hand side) from f at the quadrature points: f_qp is [nqp] in natural
- * order, host or device. */
+ * order, host or device. With a device buffer the call is stream-ordered and
+ * returns without synchronising; a host buffer is copied before it returns. */
 int sgiga_set_rhs(sgiga_plan_t plan, const double* f_qp);
 
 /* Same, with f from a built-in manufactured solution (SGIGA_SRC_*),
  * evaluated on the device. */
 int sgiga_set_rhs_builtin(sgiga_plan_t plan, int source);
+
+/* f(x_q) of a built-in source (SGIGA_SRC_*) at every quadrature point, in
+ * natural qp order: f is [nqp], host or device (input data for sgiga_set_rhs). */
+int sgiga_source_at_qp(sgiga_plan_t plan, int source, double* f);
 
 /* Copy the current packed load vector to b ([ndof], host or device). */
 int sgiga_get_rhs(sgiga_plan_t plan, double* b);

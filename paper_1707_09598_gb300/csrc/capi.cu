@@ -396,7 +396,9 @@ static int build(sgiga_plan_s* P) {
         tcost[i] = qp;
     }
     std::stable_sort(P->sched.begin(), P->sched.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
-    // preconditioner work items per direction (longest contractions first)
+    // preconditioner work items per direction: the shape of each component's
+    // mode product picks SMALL / ROWS / TILE; items with the longest
+    // contractions first
     for (int k = 0; k < d; ++k) {
         std::vector<FDItem>& v = P->fd[k];
         for (size_t gi = 0; gi < P->grids.size(); ++gi) {
@@ -404,8 +406,17 @@ static int build(sgiga_plan_s* P) {
             long long n = g.n[k];
             if (g.ndof == 0) continue;
             long long ncol = g.ndof / n;
-            for (long long i0 = 0; i0 < n; i0 += 32)
-                for (long long c0 = 0; c0 < ncol; c0 += 64) v.push_back(FDItem{(int)gi, (int)i0, c0});
+            if (n <= 64) {
+                for (long long c0 = 0; c0 < g.ndof; c0 += 256) v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0});
+            } else if (ncol >= 64) {
+                for (long long i0 = 0; i0 < n; i0 += 32)
+                    for (long long c0 = 0; c0 < ncol; c0 += 64) v.push_back(FDItem{(int)gi, FD_TILE, 0, (int)i0, c0});
+            } else {
+                long long ng = (ncol + 7) / 8, per = (ncol + ng - 1) / ng;
+                for (long long i0 = 0; i0 < n; i0 += 256)
+                    for (long long c0 = 0; c0 < ncol; c0 += per)
+                        v.push_back(FDItem{(int)gi, FD_ROWS, (int)std::min(per, ncol - c0), (int)i0, c0});
+            }
         }
         std::stable_sort(v.begin(), v.end(), [&](const FDItem& a, const FDItem& b) {
             return P->grids[a.grid].n[k] > P->grids[b.grid].n[k];
@@ -485,11 +496,15 @@ static int build(sgiga_plan_s* P) {
     }
     for (auto& g : P->grids)
         for (int k = 0; k < 3; ++k) g.eig[k] = k < d ? P->eig_of_tab[g.tab[k]] : 0;
-    Eig1D* deig; double *dU, *dlam;
-    if ((rc = upload(P, &deig, P->eigs)) || (rc = upload(P, &dU, hU)) || (rc = upload(P, &dlam, hlam)) ||
-        (rc = upload(P, &dg, P->grids)))
+    std::vector<double> hUt(hU.size());
+    for (const Eig1D& e : P->eigs)
+        for (int i = 0; i < e.n; ++i)
+            for (int j = 0; j < e.n; ++j) hUt[e.uoff + (size_t)j * e.n + i] = hU[e.uoff + (size_t)i * e.n + j];
+    Eig1D* deig; double *dU, *dUt, *dlam;
+    if ((rc = upload(P, &deig, P->eigs)) || (rc = upload(P, &dU, hU)) || (rc = upload(P, &dUt, hUt)) ||
+        (rc = upload(P, &dlam, hlam)) || (rc = upload(P, &dg, P->grids)))
         return rc;
-    D.eigs = deig; D.U = dU; D.lam = dlam; D.grids = dg;
+    D.eigs = deig; D.U = dU; D.Ut = dUt; D.lam = dlam; D.grids = dg;
     // geometry coefficients
     CUDA_TRY(launch_geometry(D, s));
     int hflags[4];
@@ -684,7 +699,7 @@ int sgiga_set_rhs(sgiga_plan_t P, const double* f) {
     CUDA_TRY(launch_rhs_density_user(P->dp, fd, P->stream));
     int rc = run_rhs_operator(P);
     if (rc) return rc;
-    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    if (fd != f) CUDA_TRY(cudaStreamSynchronize(P->stream));   // host buffer may be reused on return
     return SGIGA_OK;
 }
 
@@ -696,6 +711,23 @@ int sgiga_set_rhs_builtin(sgiga_plan_t P, int source) {
     int rc = run_rhs_operator(P);
     if (rc) return rc;
     CUDA_TRY(cudaGetLastError());
+    return SGIGA_OK;
+}
+
+int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
+    if (!P || !f) return fail(SGIGA_ERR_ARG, "null argument");
+    if (source < 0 || source > SGIGA_SRC_ONE) return fail(SGIGA_ERR_ARG, "unknown source");
+    if ((source == SGIGA_SRC_ANNULUS) && P->d != 2) return fail(SGIGA_ERR_ARG, "source needs d = 2");
+    double* fd = f;
+    const bool dev = is_device(f);
+    if (!dev) {
+        int rc = ensure_stage(P, (size_t)P->nqp * 8);
+        if (rc) return rc;
+        fd = (double*)P->stage;
+    }
+    CUDA_TRY(launch_source_qp(P->dp, source, fd, P->stream));
+    if (!dev) CUDA_TRY(cudaMemcpyAsync(f, fd, (size_t)P->nqp * 8, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
     return SGIGA_OK;
 }
 

@@ -5,20 +5,65 @@
 //
 //   z = (U_d x .. x U_1) diag(sum_k lambda_{k,i_k})^{-1} (U_d x .. x U_1)^T r
 //
-// One pass applies U_k^T (forward) or U_k (backward) along direction k of every
-// component: out[a][i][b] = sum_j Mat[i][j] in[a][j][b], a GEMM with
-// M = K = n_k and N = (ndof / n_k) columns. A block computes a 32 x 64 output
-// tile with a 16-deep K loop staged in shared memory; each thread owns 2 x 4
-// outputs in registers. The last forward pass divides by the eigenvalue sums.
+// One pass applies Mat = U_k^T (forward) or U_k (backward) along direction k of
+// every component: out[a][i][b] = sum_j Mat[i][j] in[a][j][b], a GEMM with
+// M = K = n_k and ncol = ndof / n_k columns. Work items pick one of three
+// shapes so that FP64 work is not wasted on padding:
+//   SMALL (n_k <= 64): one thread per output, Mat staged in shared memory;
+//   ROWS  (long direction, < 64 columns): one lane per row, a group of at most
+//         8 columns in registers; Mat is read through its transpose so that a
+//         warp's loads are coalesced, the input entries are warp broadcasts;
+//   TILE  (otherwise): 32 x 64 output tile, 16-deep K loop through shared
+//         memory, 2 x 4 outputs per thread.
+// The last forward pass divides by the eigenvalue sums.
 #include "kernels.h"
 
 namespace sgiga {
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ double fd_scale(const DevPlan& P, const GridDesc& g, long long idx) {
+    long long rem = idx;
+    double s = 0.0;
+    for (int k = 0; k < P.d; ++k) {
+        int ik = (int)(rem % g.n[k]);
+        rem /= g.n[k];
+        s += P.lam[P.eigs[g.eig[k]].loff + ik];
+    }
+    return 1.0 / s;
+}
+
+template <int NC>
+__device__ __forceinline__ void fd_rows(const DevPlan& P, const GridDesc& g, const double* __restrict__ MT,
+                                        const double* __restrict__ vin, double* __restrict__ vout, int n,
+                                        long long B, int i, bool act, long long c0, int scale) {
+    long long base[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        long long col = c0 + c, a = col / B;
+        base[c] = a * n * B + (col - a * B);
+    }
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    const double* mp = MT + (act ? i : 0);
+    for (int j = 0; j < n; ++j) {
+        const double m = act ? mp[(long long)j * n] : 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += m * __ldg(vin + base[c] + (long long)j * B);
+    }
+    if (!act) return;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        long long idx = base[c] + (long long)i * B;
+        double v = acc[c];
+        if (scale) v *= fd_scale(P, g, idx);
+        vout[idx] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256, 2)
 k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int scale,
           const double* __restrict__ in, double* __restrict__ out, const int* __restrict__ active) {
-    __shared__ double As[16][33];
-    __shared__ double Bs[16][65];
+    __shared__ double sm[64 * 65];
     const FDItem it = items[blockIdx.x];
     if (active && !active[it.grid]) return;
     const GridDesc& g = P.grids[it.grid];
@@ -29,9 +74,46 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
     for (int k = dir + 1; k < d; ++k) A *= g.n[k];
     const long long Ncol = A * B;
     const Eig1D e = P.eigs[g.eig[dir]];
+    // Mat[i][j] = U[j][i] (forward) or U[i][j] (backward); MT[j][i] = Mat[i][j]
     const double* __restrict__ U = P.U + e.uoff;
+    const double* __restrict__ MT = forward ? P.U + e.uoff : P.Ut + e.uoff;
     const double* vin = in + g.dof_off;
     double* vout = out + g.dof_off;
+
+    if (it.mode == FD_SMALL) {
+        for (int l = threadIdx.x; l < n * n; l += blockDim.x) {
+            int i = l / n, j = l - i * n;
+            sm[i * 65 + j] = forward ? U[(long long)j * n + i] : U[(long long)i * n + j];
+        }
+        __syncthreads();
+        long long lin = it.c0 + threadIdx.x;
+        if (lin >= g.ndof) return;
+        long long b = lin % B, r = lin / B;
+        int i = (int)(r % n);
+        long long a = r / n;
+        const double* vp = vin + a * n * B + b;
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += sm[i * 65 + j] * vp[(long long)j * B];
+        if (scale) acc *= fd_scale(P, g, lin);
+        vout[lin] = acc;
+        return;
+    }
+    if (it.mode == FD_ROWS) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int i_w = it.i0 + 32 * warp;
+        if (i_w >= n) return;
+        const int i = i_w + lane;
+        const bool act = i < n;
+        switch (it.nc) {
+#define CASE(NCV) case NCV: fd_rows<NCV>(P, g, MT, vin, vout, n, B, i, act, it.c0, scale); break;
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        }
+        return;
+    }
+    // FD_TILE
+    double (*As)[33] = reinterpret_cast<double (*)[33]>(sm);
+    double (*Bs)[65] = reinterpret_cast<double (*)[65]>(sm + 16 * 33);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double acc[2][4];
 #pragma unroll
@@ -40,12 +122,9 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
         for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
     for (int j0 = 0; j0 < n; j0 += 16) {
         for (int l = threadIdx.x; l < 512; l += 256) {
-            int kk, ii;
-            if (forward) { ii = l & 31; kk = l >> 5; } else { kk = l & 15; ii = l >> 4; }
+            int ii = l & 31, kk = l >> 5;
             int i = it.i0 + ii, j = j0 + kk;
-            double v = 0.0;
-            if (i < n && j < n) v = forward ? U[(long long)j * n + i] : U[(long long)i * n + j];
-            As[kk][ii] = v;
+            As[kk][ii] = (i < n && j < n) ? MT[(long long)j * n + i] : 0.0;
         }
         for (int l = threadIdx.x; l < 1024; l += 256) {
             int kk, cc;
@@ -83,16 +162,7 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
             long long a = c / B, b = c - a * B;
             long long idx = a * n * B + (long long)i * B + b;
             double v = acc[r][c4];
-            if (scale) {
-                long long rem = idx;
-                double s = 0.0;
-                for (int k = 0; k < d; ++k) {
-                    int ik = (int)(rem % g.n[k]);
-                    rem /= g.n[k];
-                    s += P.lam[P.eigs[g.eig[k]].loff + ik];
-                }
-                v /= s;
-            }
+            if (scale) v *= fd_scale(P, g, idx);
             vout[idx] = v;
         }
     }

@@ -200,6 +200,28 @@ __global__ void k_rhs_density(DevPlan P, int src, const double* __restrict__ fna
     }
 }
 
+// f(x_q) of a built-in source at every quadrature point, natural order.
+__global__ void k_source_qp(DevPlan P, int src, double* __restrict__ fout) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        double xi[3], wq, x[3], J[3][3];
+        qp_param(P, g, L, xi, wq);
+        patch_eval(*P.patch, xi, x, J);
+        fout[natural_index(g, d, Q, L)] = builtin_source(src, d, x);
+    }
+}
+
+cudaError_t launch_source_qp(const DevPlan& P, int source, double* fout, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_source_qp<<<P.ntiles, 256, 0, s>>>(P, source, fout);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     k_rhs_density<<<P.ntiles, 256, 0, s>>>(P, source, nullptr);

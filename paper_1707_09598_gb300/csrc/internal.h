@@ -55,10 +55,13 @@ struct Chunk {
 };
 
 // Work item of the batched mode product of the preconditioner.
+enum { FD_SMALL = 0, FD_ROWS = 1, FD_TILE = 2 };
 struct FDItem {
     int grid;
+    int mode;           // FD_SMALL / FD_ROWS / FD_TILE
+    int nc;             // FD_ROWS: columns of the group (1..8)
     int i0;             // first row (output index along the direction)
-    long long c0;       // first column (a*B + b)
+    long long c0;       // first column (a*B + b); FD_SMALL: first packed output
 };
 
 // Geometry patch: tensor-product NURBS with separable weights.
@@ -70,5 +73,5 @@ struct Patch {
     int rational[3];
     double knots[3][12];
     double w[3][8];       // 1D weights per direction (W = prod_k W_k)
-    double cp[64][3];     // control points, direction 0 fastest
+    double cp[128][3];    // control points, direction 0 fastest
 };

@@ -31,7 +31,8 @@ struct DevPlan {
     double* G;               // ncomp planes of nqp (tile-major)
     double* mw;              // w |det J| (tile-major)
     double* rho;             // f w |det J| (tile-major)
-    const double* U;
+    const double* U;         // eigenvectors, U[j][i] = component j of eigenvector i
+    const double* Ut;        // their transposes (same offsets)
     const double* lam;
     int* flags;              // [0] = geometry error, [1] = eval error
     size_t smem_op;          // dynamic shared bytes of the operator kernel
@@ -43,6 +44,7 @@ cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
 cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s);
 cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s);
+cudaError_t launch_source_qp(const DevPlan& P, int source, double* fout, cudaStream_t s);
 cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s);
 cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh, double* Gnat,
                                     double* mwnat, cudaStream_t s);

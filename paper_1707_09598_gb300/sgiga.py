@@ -70,6 +70,7 @@ _SIGS = {
     "sgiga_set_rhs": (_I, [_P, _P]),
     "sgiga_set_rhs_builtin": (_I, [_P, _I]),
     "sgiga_get_rhs": (_I, [_P, _P]),
+    "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
     "sgiga_precond": (_I, [_P, _P, _P]),
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
@@ -162,6 +163,11 @@ def sgiga_set_rhs(plan, f_qp):
 
 def sgiga_set_rhs_builtin(plan, source):
     _check(_lib.sgiga_set_rhs_builtin(plan, SOURCE[source] if isinstance(source, str) else int(source)))
+
+
+def sgiga_source_at_qp(plan, source, f):
+    n = sgiga_plan_info(plan).nqp
+    _check(_lib.sgiga_source_at_qp(plan, SOURCE[source] if isinstance(source, str) else int(source), _ptr(f, n)))
 
 
 def sgiga_get_rhs(plan, b):

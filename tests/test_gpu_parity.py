@@ -328,6 +328,9 @@ def test_host_buffers_and_user_rhs(sg):
         sg.sgiga_qp_coords(P.handle, xq)
         xq = xq.cpu().numpy().reshape(d, -1).T
         f = problems.get("annulus_paper2").f(xq)
+        fq = np.zeros(P.info.nqp)
+        sg.sgiga_source_at_qp(P.handle, "annulus_paper", fq)
+        np.testing.assert_allclose(fq, f, rtol=1e-12, atol=1e-12 * np.abs(f).max())
         sg.sgiga_set_rhs(P.handle, np.ascontiguousarray(f))
         b1 = np.zeros(P.info.ndof)
         sg.sgiga_get_rhs(P.handle, b1)
