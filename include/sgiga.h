@@ -200,6 +200,41 @@ int sgiga_geometry_coeffs(sgiga_plan_t plan, int g, double* G, double* mw);
  * is eigenvector j), lam [n] ascending. Host outputs. */
 int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free preconditioner apply (the paper has no counterpart; this is
+ * a service for callers of the library).
+ *
+ * For callers that cannot call cudaMalloc where they need it: work recorded
+ * into a CUDA stream capture (allocating there is not allowed in the default
+ * capture mode), real-time loops that must not touch the device allocator
+ * after start-up, and processes whose device memory is owned by another
+ * allocator. It needs no plan: the caller passes the 1D eigenpairs.
+ *
+ * Computes, for ONE tensor-product grid with n[0] x .. x n[d-1] entries
+ * (direction 0 fastest),
+ *     z = (U_{d-1} x .. x U_0) diag(sum_k lam_k)^{-1} (U_{d-1} x .. x U_0)^T r,
+ * the same fast-diagonalisation operator as sgiga_precond.
+ *   d        1..3
+ *   n        host [d], sizes per direction
+ *   U, lam   host arrays of d DEVICE pointers: U[k] is n[k] x n[k] row-major
+ *            (column j = eigenvector j, as sgiga_fd_eigen returns it), lam[k]
+ *            the n[k] eigenvalues
+ *   r, z     device [prod n]; z may alias r
+ *   stream   cudaStream_t (NULL: legacy default stream); the call only
+ *            enqueues kernels and returns without synchronising
+ * Intermediate tensors live in a library-owned device array of
+ * 2 * SGIGA_NOALLOC_MAX_DOFS doubles (4 MB on every GPU that loads the
+ * library, held until the process exits). Grids with more than
+ * SGIGA_NOALLOC_MAX_DOFS entries are rejected with SGIGA_ERR_ARG. The call
+ * allocates nothing. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the array, so calls that overlap on
+ * the GPU race on it: order them on one stream. Returns SGIGA_OK, SGIGA_ERR_ARG
+ * or SGIGA_ERR_CUDA (message in sgiga_last_error()). */
+#define SGIGA_NOALLOC_MAX_DOFS 262144
+int sgiga_fd_apply_noalloc(int d, const int* n, const double* const* U, const double* const* lam,
+                           const double* r, double* z, void* stream);
+
 const char* sgiga_last_error(void);
 
 /* Number of CUDA kernels this library has launched in this process so far

@@ -34,6 +34,8 @@ std::atomic<long long> sgiga::g_launches{0};
 
 static thread_local std::string g_last_error = "";
 
+void sgiga::set_last_error(const char* msg) { g_last_error = msg; }
+
 static int fail(int code, const std::string& msg) {
     g_last_error = msg;
     return code;

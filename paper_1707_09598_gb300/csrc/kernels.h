@@ -6,6 +6,9 @@
 
 namespace sgiga {
 
+// Record the message returned by sgiga_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // Number of kernels this library has launched (diagnostic, process-wide).
 extern std::atomic<long long> g_launches;
 #define SGIGA_COUNT_LAUNCH() (::sgiga::g_launches.fetch_add(1, std::memory_order_relaxed))

@@ -81,6 +81,7 @@ _SIGS = {
     "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "sgiga_geometry_coeffs": (_I, [_P, _I, _P, _P]),
     "sgiga_fd_eigen": (_I, [_P, _I, _I, _P, _P]),
+    "sgiga_fd_apply_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _P, _P]),
     "sgiga_last_error": (ctypes.c_char_p, []),
     "sgiga_launch_count": (ctypes.c_longlong, []),
 }
@@ -236,6 +237,28 @@ def sgiga_fd_eigen(plan, dir, level, n):
     lam = np.zeros(n)
     _check(_lib.sgiga_fd_eigen(plan, dir, level, _ptr(U), _ptr(lam)))
     return U.reshape(n, n), lam
+
+
+SGIGA_NOALLOC_MAX_DOFS = 262144
+
+
+def sgiga_fd_apply_noalloc(n, U, lam, r, z, stream=None, check=True):
+    """Allocation-free fast-diagonalisation apply for one grid (see include/sgiga.h).
+
+    n: sizes per direction; U, lam: per-direction device tensors; r, z: device
+    tensors of prod(n) float64 entries. Returns the status code."""
+    d = len(n)
+    N = 1
+    for v in n:
+        N *= int(v)
+    na = (_I * d)(*[int(v) for v in n])
+    ua = (_P * d)(*[_ptr(u, int(v) * int(v)) for u, v in zip(U, n)])
+    la = (_P * d)(*[_ptr(l_, int(v)) for l_, v in zip(lam, n)])
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = _lib.sgiga_fd_apply_noalloc(d, na, ua, la, _ptr(r, N), _ptr(z, N), s)
+    if check:
+        _check(rc)
+    return rc
 
 
 def sgiga_launch_count():
