@@ -408,16 +408,22 @@ static int build(sgiga_plan_s* P) {
             long long n = g.n[k];
             if (g.ndof == 0) continue;
             long long ncol = g.ndof / n;
+            const int KS = 128;   // contraction depth per item once n > KS
             if (n <= 64) {
-                for (long long c0 = 0; c0 < g.ndof; c0 += 256) v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0});
+                for (long long c0 = 0; c0 < g.ndof; c0 += 256)
+                    v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
             } else if (ncol >= 64) {
                 for (long long i0 = 0; i0 < n; i0 += 32)
-                    for (long long c0 = 0; c0 < ncol; c0 += 64) v.push_back(FDItem{(int)gi, FD_TILE, 0, (int)i0, c0});
+                    for (long long c0 = 0; c0 < ncol; c0 += 64)
+                        for (int j0 = 0; j0 < n; j0 += KS)
+                            v.push_back(FDItem{(int)gi, FD_TILE, 0, (int)i0, c0, j0, (int)std::min<long long>(n, j0 + KS)});
             } else {
                 long long ng = (ncol + 7) / 8, per = (ncol + ng - 1) / ng;
                 for (long long i0 = 0; i0 < n; i0 += 256)
                     for (long long c0 = 0; c0 < ncol; c0 += per)
-                        v.push_back(FDItem{(int)gi, FD_ROWS, (int)std::min(per, ncol - c0), (int)i0, c0});
+                        for (int j0 = 0; j0 < n; j0 += KS)
+                            v.push_back(FDItem{(int)gi, FD_ROWS, (int)std::min(per, ncol - c0), (int)i0, c0, j0,
+                                               (int)std::min<long long>(n, j0 + KS)});
             }
         }
         std::stable_sort(v.begin(), v.end(), [&](const FDItem& a, const FDItem& b) {
@@ -498,6 +504,22 @@ static int build(sgiga_plan_s* P) {
     }
     for (auto& g : P->grids)
         for (int k = 0; k < 3; ++k) g.eig[k] = k < d ? P->eig_of_tab[g.tab[k]] : 0;
+    // reciprocal eigenvalue sums of every packed entry
+    std::vector<double> hdinv((size_t)P->ndof);
+    for (const GridDesc& g : P->grids)
+        for (long long idx = 0; idx < g.ndof; ++idx) {
+            long long rem = idx;
+            double sum = 0.0;
+            for (int k = 0; k < d; ++k) {
+                int ik = (int)(rem % g.n[k]);
+                rem /= g.n[k];
+                sum += hlam[P->eigs[P->eig_of_tab[g.tab[k]]].loff + ik];
+            }
+            hdinv[g.dof_off + idx] = 1.0 / sum;
+        }
+    double* ddinv;
+    if ((rc = upload(P, &ddinv, hdinv))) return rc;
+    D.dinv = ddinv;
     std::vector<double> hUt(hU.size());
     for (const Eig1D& e : P->eigs)
         for (int i = 0; i < e.n; ++i)
@@ -595,15 +617,19 @@ static int precond(sgiga_plan_s* P, const double* r, double* z, const int* activ
     const double* in = r;
     double* bufs[2] = {t1, t2};
     int cur = 0;
+    const size_t bytes = (size_t)P->ndof * 8;
     for (int k = 0; k < d; ++k) {
         double* out = bufs[cur];
-        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, k == d - 1, in, out, active, s));
+        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
+        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
         in = out;
         cur ^= 1;
     }
+    CUDA_TRY(launch_fd_scale(D, (double*)in, active, s));
     for (int k = 0; k < d; ++k) {
         double* out = (k == d - 1) ? z : bufs[cur];
-        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, 0, in, out, active, s));
+        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
+        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
         in = out;
         cur ^= 1;
     }

@@ -15,26 +15,19 @@
 //         warp's loads are coalesced, the input entries are warp broadcasts;
 //   TILE  (otherwise): 32 x 64 output tile, 16-deep K loop through shared
 //         memory, 2 x 4 outputs per thread.
-// The last forward pass divides by the eigenvalue sums.
+// Long contractions (n_k > 128) are split into 128-deep ranges of j so that no
+// block carries more than ~10^5 FMAs; such items add their partial sums
+// atomically into an output that was cleared before the pass. The division by
+// the eigenvalue sums is a separate elementwise pass between the forward and
+// the backward passes, with the reciprocals precomputed per DoF.
 #include "kernels.h"
 
 namespace sgiga {
 
-__device__ __forceinline__ double fd_scale(const DevPlan& P, const GridDesc& g, long long idx) {
-    long long rem = idx;
-    double s = 0.0;
-    for (int k = 0; k < P.d; ++k) {
-        int ik = (int)(rem % g.n[k]);
-        rem /= g.n[k];
-        s += P.lam[P.eigs[g.eig[k]].loff + ik];
-    }
-    return 1.0 / s;
-}
-
 template <int NC>
-__device__ __forceinline__ void fd_rows(const DevPlan& P, const GridDesc& g, const double* __restrict__ MT,
-                                        const double* __restrict__ vin, double* __restrict__ vout, int n,
-                                        long long B, int i, bool act, long long c0, int scale) {
+__device__ __forceinline__ void fd_rows(const double* __restrict__ MT, const double* __restrict__ vin,
+                                        double* __restrict__ vout, int n, long long B, int i, bool act,
+                                        long long c0, int j0, int j1, bool split) {
     long long base[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -45,7 +38,7 @@ __device__ __forceinline__ void fd_rows(const DevPlan& P, const GridDesc& g, con
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = 0.0;
     const double* mp = MT + (act ? i : 0);
-    for (int j = 0; j < n; ++j) {
+    for (int j = j0; j < j1; ++j) {
         const double m = act ? mp[(long long)j * n] : 0.0;
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] += m * __ldg(vin + base[c] + (long long)j * B);
@@ -53,15 +46,13 @@ __device__ __forceinline__ void fd_rows(const DevPlan& P, const GridDesc& g, con
     if (!act) return;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        long long idx = base[c] + (long long)i * B;
-        double v = acc[c];
-        if (scale) v *= fd_scale(P, g, idx);
-        vout[idx] = v;
+        double* o = vout + base[c] + (long long)i * B;
+        if (split) atomicAdd(o, acc[c]); else *o = acc[c];
     }
 }
 
 __global__ void __launch_bounds__(256, 2)
-k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int scale,
+k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
           const double* __restrict__ in, double* __restrict__ out, const int* __restrict__ active) {
     __shared__ double sm[64 * 65];
     const FDItem it = items[blockIdx.x];
@@ -79,6 +70,7 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
     const double* __restrict__ MT = forward ? P.U + e.uoff : P.Ut + e.uoff;
     const double* vin = in + g.dof_off;
     double* vout = out + g.dof_off;
+    const bool split = it.j0 > 0 || it.j1 < n;
 
     if (it.mode == FD_SMALL) {
         for (int l = threadIdx.x; l < n * n; l += blockDim.x) {
@@ -94,7 +86,6 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
         const double* vp = vin + a * n * B + b;
         double acc = 0.0;
         for (int j = 0; j < n; ++j) acc += sm[i * 65 + j] * vp[(long long)j * B];
-        if (scale) acc *= fd_scale(P, g, lin);
         vout[lin] = acc;
         return;
     }
@@ -105,7 +96,7 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
         const int i = i_w + lane;
         const bool act = i < n;
         switch (it.nc) {
-#define CASE(NCV) case NCV: fd_rows<NCV>(P, g, MT, vin, vout, n, B, i, act, it.c0, scale); break;
+#define CASE(NCV) case NCV: fd_rows<NCV>(MT, vin, vout, n, B, i, act, it.c0, it.j0, it.j1, split); break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         }
@@ -120,11 +111,11 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
-    for (int j0 = 0; j0 < n; j0 += 16) {
+    for (int j0 = it.j0; j0 < it.j1; j0 += 16) {
         for (int l = threadIdx.x; l < 512; l += 256) {
             int ii = l & 31, kk = l >> 5;
             int i = it.i0 + ii, j = j0 + kk;
-            As[kk][ii] = (i < n && j < n) ? MT[(long long)j * n + i] : 0.0;
+            As[kk][ii] = (i < n && j < it.j1) ? MT[(long long)j * n + i] : 0.0;
         }
         for (int l = threadIdx.x; l < 1024; l += 256) {
             int kk, cc;
@@ -132,7 +123,7 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
             long long c = it.c0 + cc;
             int j = j0 + kk;
             double v = 0.0;
-            if (c < Ncol && j < n) {
+            if (c < Ncol && j < it.j1) {
                 long long a = c / B, b = c - a * B;
                 v = vin[a * n * B + (long long)j * B + b];
             }
@@ -161,18 +152,31 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward, int
             if (c >= Ncol) continue;
             long long a = c / B, b = c - a * B;
             long long idx = a * n * B + (long long)i * B + b;
-            double v = acc[r][c4];
-            if (scale) v *= fd_scale(P, g, idx);
-            vout[idx] = v;
+            if (split) atomicAdd(vout + idx, acc[r][c4]); else vout[idx] = acc[r][c4];
         }
     }
 }
 
-cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward, int scale,
+cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
                            const double* in, double* out, const int* active, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_fd_pass<<<nitems, 256, 0, s>>>(P, items, dir, forward, scale, in, out, active);
+    k_fd_pass<<<nitems, 256, 0, s>>>(P, items, dir, forward, in, out, active);
+    return cudaGetLastError();
+}
+
+// z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every packed entry.
+__global__ void k_fd_scale(const Chunk* __restrict__ chunks, const double* __restrict__ dinv, double* __restrict__ z,
+                           const int* __restrict__ active) {
+    const Chunk c = chunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) z[c.start + i] *= dinv[c.start + i];
+}
+
+cudaError_t launch_fd_scale(const DevPlan& P, double* z, const int* active, cudaStream_t s) {
+    if (P.nchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_fd_scale<<<P.nchunks, 256, 0, s>>>(P.chunks, P.dinv, z, active);
     return cudaGetLastError();
 }
 

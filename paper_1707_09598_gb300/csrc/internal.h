@@ -62,6 +62,7 @@ struct FDItem {
     int nc;             // FD_ROWS: columns of the group (1..8)
     int i0;             // first row (output index along the direction)
     long long c0;       // first column (a*B + b); FD_SMALL: first packed output
+    int j0, j1;         // contraction range [j0, j1) (split K: partial sums are added atomically)
 };
 
 // Geometry patch: tensor-product NURBS with separable weights.

@@ -37,6 +37,7 @@ struct DevPlan {
     const double* U;         // eigenvectors, U[j][i] = component j of eigenvector i
     const double* Ut;        // their transposes (same offsets)
     const double* lam;
+    const double* dinv;      // [ndof] 1 / sum_k lambda_{k,i_k} of every packed entry
     int* flags;              // [0] = geometry error, [1] = eval error
     size_t smem_op;          // dynamic shared bytes of the operator kernel
 };
@@ -58,7 +59,8 @@ cudaError_t set_op2_smem(int p, size_t bytes);
 cudaError_t set_op3_smem(int p, size_t bytes);
 // fd.cu
 cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
-                           int scale, const double* in, double* out, const int* active, cudaStream_t s);
+                           const double* in, double* out, const int* active, cudaStream_t s);
+cudaError_t launch_fd_scale(const DevPlan& P, double* z, const int* active, cudaStream_t s);
 // vec.cu
 cudaError_t launch_dot(const DevPlan& P, const double* a, const double* b, double* partial, double* out,
                        cudaStream_t s);
