@@ -61,8 +61,12 @@ enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1 };
  * otherwise; ONESIDED g(t) = t^gamma. */
 enum { SGIGA_GRADING_UNIFORM = 0, SGIGA_GRADING_RADICAL = 1, SGIGA_GRADING_ONESIDED = 2 };
 
-/* Arithmetic of the solve. FP64: every step in double precision. */
-enum { SGIGA_PREC_FP64 = 0 };
+/* Arithmetic of the solve. FP64: every step in double precision.
+ * MIXED_FP32: FP64 iterative refinement (residual r = b - K x with the FP64
+ * operator, x += d) around an inner preconditioned-CG solve K d = r in FP32
+ * (FP32 operator apply with FP32 geometry planes and tables, FP32
+ * preconditioner), per-component scalars and reductions in FP64. */
+enum { SGIGA_PREC_FP64 = 0, SGIGA_PREC_MIXED_FP32 = 1 };
 
 /* Preconditioner of the batched conjugate-gradient solve. FD: fast
  * diagonalisation with the 1D generalised eigenpairs; NONE: plain CG. */
@@ -154,6 +158,11 @@ int sgiga_get_rhs(sgiga_plan_t plan, double* b);
  * x, y: device packed vectors [ndof]; y is overwritten. */
 int sgiga_apply(sgiga_plan_t plan, const double* x, double* y);
 
+/* FP32 variant of sgiga_apply (the inner operator of the MIXED_FP32 solve):
+ * FP32 geometry planes and basis tables, FP32 accumulation. x, y: device
+ * float [ndof]. Needs a plan built with SGIGA_PREC_MIXED_FP32. */
+int sgiga_apply_f32(sgiga_plan_t plan, const float* x, float* y);
+
 /* z = P^{-1} r with the fast-diagonalisation preconditioner of every
  * component, z = (U_d x .. x U_1) diag(sum_k lambda_k)^{-1} (U_d x .. x U_1)^T r
  * with the 1D generalised eigenpairs of the parametric stiffness and mass
@@ -164,8 +173,11 @@ int sgiga_precond(sgiga_plan_t plan, const double* r, double* z);
 
 /* Solve K_g u_g = b_g for every component g (batched preconditioned CG,
  * per-component scalars and convergence) until ||r_g|| <= rel_tol ||b_g|| or
- * max_iter iterations. The solution stays in the plan (sgiga_get_solution).
- * Returns SGIGA_ERR_NOT_CONVERGED if some component did not converge. */
+ * max_iter iterations (MIXED_FP32: max_iter refinement steps, each with an
+ * inner FP32 solve to relative residual 1e-5 or 100 iterations; the stopping
+ * test uses the true FP64 residual). The solution stays in the plan
+ * (sgiga_get_solution). Returns SGIGA_ERR_NOT_CONVERGED if some component did
+ * not converge. */
 int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
                 sgiga_solve_stats* stats /* host, may be NULL */);
 

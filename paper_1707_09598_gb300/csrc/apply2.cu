@@ -11,11 +11,12 @@
 
 namespace sgiga {
 
-template <int P, int MODE>
+template <typename Real, int P, int MODE>
 __global__ void __launch_bounds__(256, 2)
-k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const int* __restrict__ active) {
+k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    Real* sm = reinterpret_cast<Real*>(sm_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
     if (active && !active[td.grid]) return;
@@ -35,23 +36,23 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
     }
     const int Ta = T[0], Tb = T[1], La = L[0], Lb = L[1];
     const int QTb = Q * Tb, npen = QTb, LaP = La | 1;
-    double* tb[2];
-    double* tdv[2];
-    double* cur = sm;
+    Real* tb[2];
+    Real* tdv[2];
+    Real* cur = sm;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         tb[k] = cur; cur += T[k] * Q * P1;
         tdv[k] = cur; cur += T[k] * Q * P1;
     }
-    double* X = cur; cur += La * Lb;
-    double* S1 = cur;
+    Real* X = cur; cur += La * Lb;
+    Real* S1 = cur;
     const int S1n = npen * LaP;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const Table1D& tt = Pl.tabs[g.tab[ax[k]]];
         const long long base = (tt.off + (long long)E0[k] * Q) * P1;
         const int cnt = T[k] * Q * P1;
-        for (int i = tid; i < cnt; i += nth) { tb[k][i] = Pl.R[base + i]; tdv[k][i] = Pl.dR[base + i]; }
+        for (int i = tid; i < cnt; i += nth) { tb[k][i] = OpData<Real>::R(Pl)[base + i]; tdv[k][i] = OpData<Real>::dR(Pl)[base + i]; }
     }
     const long long doff = g.dof_off;
     __syncthreads();   // tables visible to every thread before any stage reads them
@@ -60,7 +61,7 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int idx = tid; idx < nX; idx += nth) {
             int ja = idx % La, jb = idx / La;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
-            double v = 0.0;
+            Real v = 0.0;
             if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)
                 v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1]];
             X[idx] = v;
@@ -70,13 +71,13 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int idx = tid; idx < n1; idx += nth) {
             int ja = idx % La, qb = idx / La;
             int eb = qb / Q;
-            const double* bt = tb[1] + qb * P1;
-            const double* dt = tdv[1] + qb * P1;
-            const double* xp = X + (eb * M) * La + ja;
-            double sB = 0.0, sD = 0.0;
+            const Real* bt = tb[1] + qb * P1;
+            const Real* dt = tdv[1] + qb * P1;
+            const Real* xp = X + (eb * M) * La + ja;
+            Real sB = 0.0, sD = 0.0;
 #pragma unroll
             for (int t = 0; t < P1; ++t) {
-                double v = xp[t * La];
+                Real v = xp[t * La];
                 sB += bt[t] * v;
                 sD += dt[t] * v;
             }
@@ -86,18 +87,18 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         __syncthreads();
     }
     const long long nqp = Pl.nqp;
-    const double* __restrict__ G = Pl.G;
+    const Real* __restrict__ G = OpData<Real>::G(Pl);
     const double* __restrict__ rho = Pl.rho;
     for (int pid = tid; pid < npen; pid += nth) {
-        double* c0 = S1 + pid * LaP;
-        double* c1 = c0 + S1n;
-        double a0[P1], a1[P1];
+        Real* c0 = S1 + pid * LaP;
+        Real* c1 = c0 + S1n;
+        Real a0[P1], a1[P1];
 #pragma unroll
         for (int t = 0; t < P1; ++t) a0[t] = a1[t] = 0.0;
         long long gi = td.g_off + pid;
         for (int ea = 0; ea < Ta; ++ea) {
             const int base = ea * M;
-            double i0[P1], i1[P1];
+            Real i0[P1], i1[P1];
             if (MODE == 0) {
 #pragma unroll
                 for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; }
@@ -105,19 +106,19 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int qa = ea * Q + q;
-                const double* bt = tb[0] + qa * P1;
-                const double* dt = tdv[0] + qa * P1;
+                const Real* bt = tb[0] + qa * P1;
+                const Real* dt = tdv[0] + qa * P1;
                 if (MODE == 0) {
-                    double ga = 0.0, gb = 0.0;
+                    Real ga = 0.0, gb = 0.0;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; }
-                    const double G00 = G[gi], G01 = G[nqp + gi], G11 = G[2 * nqp + gi];
-                    const double va = G00 * ga + G01 * gb;
-                    const double vb = G01 * ga + G11 * gb;
+                    const Real G00 = G[gi], G01 = G[nqp + gi], G11 = G[2 * nqp + gi];
+                    const Real va = G00 * ga + G01 * gb;
+                    const Real vb = G01 * ga + G11 * gb;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; }
                 } else {
-                    const double rv = rho[gi];
+                    const Real rv = (Real)rho[gi];
 #pragma unroll
                     for (int t = 0; t < P1; ++t) a0[t] += bt[t] * rv;
                 }
@@ -147,7 +148,7 @@ k_op2(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
         if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)) continue;
         int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
-        double yv = 0.0;
+        Real yv = 0.0;
         for (int eb = lo; eb <= hi; ++eb) {
             const int t = jb - eb * M;
 #pragma unroll
@@ -167,9 +168,9 @@ static cudaError_t launch2(const DevPlan& Pl, const double* x, double* y, const 
                            cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     if (mode == 0)
-        k_op2<P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op2<double, P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else
-        k_op2<P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op2<double, P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -184,13 +185,33 @@ cudaError_t launch_op2(const DevPlan& Pl, const double* x, double* y, const int*
     return cudaErrorInvalidValue;
 }
 
+// FP32 stiffness apply (FP32 geometry planes and tables, FP32 accumulation).
+template <int P>
+static cudaError_t launch2f(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_op2<float, P, 0><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op2_f32(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
+    switch (Pl.p) {
+    case 1: return launch2f<1>(Pl, x, y, active, s);
+    case 2: return launch2f<2>(Pl, x, y, active, s);
+    case 3: return launch2f<3>(Pl, x, y, active, s);
+    case 4: return launch2f<4>(Pl, x, y, active, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t set_op2_smem(int p, size_t bytes) {
     cudaError_t e = cudaSuccess;
-#define SET(PP)                                                                                              \
-    if (p == PP) {                                                                                           \
-        e = cudaFuncSetAttribute(k_op2<PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);   \
-        if (e == cudaSuccess)                                                                                \
-            e = cudaFuncSetAttribute(k_op2<PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+#define SET(PP)                                                                                          \
+    if (p == PP) {                                                                                       \
+        e = cudaFuncSetAttribute(k_op2<double, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op2<double, PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op2<float, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
     }
     SET(1) SET(2) SET(3) SET(4)
 #undef SET

@@ -16,11 +16,12 @@
 
 namespace sgiga {
 
-template <int P, int MODE>
+template <typename Real, int P, int MODE>
 __global__ void __launch_bounds__(256, 2)
-k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const int* __restrict__ active) {
+k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    Real* sm = reinterpret_cast<Real*>(sm_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
     if (active && !active[td.grid]) return;
@@ -40,17 +41,17 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
     }
     const int Ta = T[0], Tb = T[1], Tc = T[2], La = L[0], Lb = L[1], Lc = L[2];
     const int QTb = Q * Tb, QTc = Q * Tc, npen = QTb * QTc, LaP = La | 1;
-    double* tb[3];
-    double* tdv[3];
-    double* cur = sm;
+    Real* tb[3];
+    Real* tdv[3];
+    Real* cur = sm;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         tb[k] = cur; cur += T[k] * Q * P1;
         tdv[k] = cur; cur += T[k] * Q * P1;
     }
-    double* X = cur; cur += (long long)La * Lb * Lc;
-    double* S1 = cur; cur += 2LL * QTc * Lb * La;
-    double* S2 = cur;
+    Real* X = cur; cur += (long long)La * Lb * Lc;
+    Real* S1 = cur; cur += 2LL * QTc * Lb * La;
+    Real* S2 = cur;
     const int S1n = QTc * Lb * La;
     const int S2n = npen * LaP;
 
@@ -59,7 +60,7 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         const Table1D& tt = Pl.tabs[g.tab[ax[k]]];
         const long long base = (tt.off + (long long)E0[k] * Q) * P1;
         const int cnt = T[k] * Q * P1;
-        for (int i = tid; i < cnt; i += nth) { tb[k][i] = Pl.R[base + i]; tdv[k][i] = Pl.dR[base + i]; }
+        for (int i = tid; i < cnt; i += nth) { tb[k][i] = OpData<Real>::R(Pl)[base + i]; tdv[k][i] = OpData<Real>::dR(Pl)[base + i]; }
     }
     const long long doff = g.dof_off;
     __syncthreads();   // tables visible to every thread before any stage reads them
@@ -68,7 +69,7 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int idx = tid; idx < nX; idx += nth) {
             int ja = idx % La, r = idx / La, jb = r % Lb, jc = r / Lb;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
-            double v = 0.0;
+            Real v = 0.0;
             if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)
                 v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2]];
             X[idx] = v;
@@ -78,13 +79,13 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int idx = tid; idx < S1n; idx += nth) {
             int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
             int ec = qc / Q;
-            const double* bt = tb[2] + qc * P1;
-            const double* dt = tdv[2] + qc * P1;
-            const double* xp = X + ((ec * M) * Lb + jb) * La + ja;
-            double sB = 0.0, sD = 0.0;
+            const Real* bt = tb[2] + qc * P1;
+            const Real* dt = tdv[2] + qc * P1;
+            const Real* xp = X + ((ec * M) * Lb + jb) * La + ja;
+            Real sB = 0.0, sD = 0.0;
 #pragma unroll
             for (int t = 0; t < P1; ++t) {
-                double v = xp[t * Lb * La];
+                Real v = xp[t * Lb * La];
                 sB += bt[t] * v;
                 sD += dt[t] * v;
             }
@@ -97,14 +98,14 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         for (int idx = tid; idx < n2; idx += nth) {
             int ja = idx % La, r = idx / La, qb = r % QTb, qc = r / QTb;
             int eb = qb / Q;
-            const double* bt = tb[1] + qb * P1;
-            const double* dt = tdv[1] + qb * P1;
-            const double* s1b = S1 + (qc * Lb + eb * M) * La + ja;
-            const double* s1d = s1b + S1n;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            const Real* bt = tb[1] + qb * P1;
+            const Real* dt = tdv[1] + qb * P1;
+            const Real* s1b = S1 + (qc * Lb + eb * M) * La + ja;
+            const Real* s1d = s1b + S1n;
+            Real s0 = 0.0, s1 = 0.0, s2 = 0.0;
 #pragma unroll
             for (int t = 0; t < P1; ++t) {
-                double vb = s1b[t * La], vd = s1d[t * La];
+                Real vb = s1b[t * La], vd = s1d[t * La];
                 s0 += bt[t] * vb;
                 s1 += dt[t] * vb;
                 s2 += bt[t] * vd;
@@ -118,19 +119,19 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
     }
     // pencil stage along a
     const long long nqp = Pl.nqp;
-    const double* __restrict__ G = Pl.G;
+    const Real* __restrict__ G = OpData<Real>::G(Pl);
     const double* __restrict__ rho = Pl.rho;
     for (int pid = tid; pid < npen; pid += nth) {
-        double* c0 = S2 + pid * LaP;
-        double* c1 = c0 + S2n;
-        double* c2 = c1 + S2n;
-        double a0[P1], a1[P1], a2[P1];
+        Real* c0 = S2 + pid * LaP;
+        Real* c1 = c0 + S2n;
+        Real* c2 = c1 + S2n;
+        Real a0[P1], a1[P1], a2[P1];
 #pragma unroll
         for (int t = 0; t < P1; ++t) a0[t] = a1[t] = a2[t] = 0.0;
         long long gi = td.g_off + pid;
         for (int ea = 0; ea < Ta; ++ea) {
             const int base = ea * M;
-            double i0[P1], i1[P1], i2[P1];
+            Real i0[P1], i1[P1], i2[P1];
             if (MODE == 0) {
 #pragma unroll
                 for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; i2[t] = c2[base + t]; }
@@ -138,21 +139,21 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int qa = ea * Q + q;
-                const double* bt = tb[0] + qa * P1;
-                const double* dt = tdv[0] + qa * P1;
+                const Real* bt = tb[0] + qa * P1;
+                const Real* dt = tdv[0] + qa * P1;
                 if (MODE == 0) {
-                    double ga = 0.0, gb = 0.0, gc = 0.0;
+                    Real ga = 0.0, gb = 0.0, gc = 0.0;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; gc += bt[t] * i2[t]; }
-                    const double G00 = G[gi], G01 = G[nqp + gi], G02 = G[2 * nqp + gi];
-                    const double G11 = G[3 * nqp + gi], G12 = G[4 * nqp + gi], G22 = G[5 * nqp + gi];
-                    const double va = G00 * ga + G01 * gb + G02 * gc;
-                    const double vb = G01 * ga + G11 * gb + G12 * gc;
-                    const double vc = G02 * ga + G12 * gb + G22 * gc;
+                    const Real G00 = G[gi], G01 = G[nqp + gi], G02 = G[2 * nqp + gi];
+                    const Real G11 = G[3 * nqp + gi], G12 = G[4 * nqp + gi], G22 = G[5 * nqp + gi];
+                    const Real va = G00 * ga + G01 * gb + G02 * gc;
+                    const Real vb = G01 * ga + G11 * gb + G12 * gc;
+                    const Real vc = G02 * ga + G12 * gb + G22 * gc;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; a2[t] += bt[t] * vc; }
                 } else {
-                    const double rv = rho[gi];
+                    const Real rv = (Real)rho[gi];
 #pragma unroll
                     for (int t = 0; t < P1; ++t) a0[t] += bt[t] * rv;
                 }
@@ -180,14 +181,14 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
     for (int idx = tid; idx < S1n; idx += nth) {
         int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
         int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
-        double rB = 0.0, rD = 0.0;
+        Real rB = 0.0, rD = 0.0;
         for (int eb = lo; eb <= hi; ++eb) {
             const int t = jb - eb * M;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int qb = eb * Q + q;
                 const int o = (qb + QTb * qc) * LaP + ja;
-                const double bv = tb[1][qb * P1 + t];
+                const Real bv = tb[1][qb * P1 + t];
                 if (MODE == 0) {
                     rB += bv * S2[o] + tdv[1][qb * P1 + t] * S2[S2n + o];
                     rD += bv * S2[2 * S2n + o];
@@ -207,7 +208,7 @@ k_op3(DevPlan Pl, const double* __restrict__ x, double* __restrict__ y, const in
         int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
         if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)) continue;
         int lo = elem_lo(jc, P, M), hi = elem_hi(jc, M, Tc);
-        double yv = 0.0;
+        Real yv = 0.0;
         for (int ec = lo; ec <= hi; ++ec) {
             const int t = jc - ec * M;
 #pragma unroll
@@ -227,9 +228,9 @@ static cudaError_t launch3(const DevPlan& Pl, const double* x, double* y, const 
                            cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     if (mode == 0)
-        k_op3<P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op3<double, P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else
-        k_op3<P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op3<double, P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -244,13 +245,33 @@ cudaError_t launch_op3(const DevPlan& Pl, const double* x, double* y, const int*
     return cudaErrorInvalidValue;
 }
 
+// FP32 stiffness apply (FP32 geometry planes and tables, FP32 accumulation).
+template <int P>
+static cudaError_t launch3f(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_op3<float, P, 0><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op3_f32(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
+    switch (Pl.p) {
+    case 1: return launch3f<1>(Pl, x, y, active, s);
+    case 2: return launch3f<2>(Pl, x, y, active, s);
+    case 3: return launch3f<3>(Pl, x, y, active, s);
+    case 4: return launch3f<4>(Pl, x, y, active, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t set_op3_smem(int p, size_t bytes) {
     cudaError_t e = cudaSuccess;
-#define SET(PP)                                                                                              \
-    if (p == PP) {                                                                                           \
-        e = cudaFuncSetAttribute(k_op3<PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);   \
-        if (e == cudaSuccess)                                                                                \
-            e = cudaFuncSetAttribute(k_op3<PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+#define SET(PP)                                                                                          \
+    if (p == PP) {                                                                                       \
+        e = cudaFuncSetAttribute(k_op3<double, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<double, PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<float, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
     }
     SET(1) SET(2) SET(3) SET(4)
 #undef SET

@@ -73,6 +73,14 @@ struct sgiga_plan_s {
     double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
     double *d_t1 = nullptr, *d_t2 = nullptr, *d_partial = nullptr, *d_scal = nullptr, *d_coef = nullptr;
     int* d_active = nullptr;
+    int* d_active_o = nullptr;  // outer (refinement) mask
+    int* d_iters_o = nullptr;
+    double* d_scal64o = nullptr;
+    float *f_b = nullptr, *f_x = nullptr, *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_q = nullptr;
+    float *f_t1 = nullptr, *f_t2 = nullptr;
+    double inner_tol = 1e-5;
+    int inner_max = 100;
+    int last_inner_iters = 0;
     int* d_iters = nullptr;
     int* d_nactive = nullptr;
     int* h_nactive = nullptr;   // pinned
@@ -558,6 +566,26 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaMemsetAsync(P->d_b, 0, nd * 8, s));
     CUDA_TRY(cudaMemsetAsync(P->d_x, 0, nd * 8, s));
     CUDA_TRY(cudaMallocHost(&P->h_nactive, sizeof(int)));
+    if (c.precision == SGIGA_PREC_MIXED_FP32) {
+        // FP32 copies of the operator and preconditioner data, FP32 work vectors
+        float *Gf, *Rf, *dRf, *Uf, *Utf, *dinvf;
+        const long long ntab = P->tab_entries * (p + 1);
+        if ((rc = dalloc(P, &Gf, (size_t)ncomp * P->nqp)) || (rc = dalloc(P, &Rf, ntab)) ||
+            (rc = dalloc(P, &dRf, ntab)) || (rc = dalloc(P, &Uf, hU.size())) || (rc = dalloc(P, &Utf, hU.size())) ||
+            (rc = dalloc(P, &dinvf, nd)) || (rc = dalloc(P, &P->f_b, nd)) || (rc = dalloc(P, &P->f_x, nd)) ||
+            (rc = dalloc(P, &P->f_r, nd)) || (rc = dalloc(P, &P->f_z, nd)) || (rc = dalloc(P, &P->f_p, nd)) ||
+            (rc = dalloc(P, &P->f_q, nd)) || (rc = dalloc(P, &P->f_t1, nd)) || (rc = dalloc(P, &P->f_t2, nd)) ||
+            (rc = dalloc(P, &P->d_active_o, ng)) || (rc = dalloc(P, &P->d_iters_o, ng)) ||
+            (rc = dalloc(P, &P->d_scal64o, 8 * ng)))
+            return rc;
+        CUDA_TRY(launch_narrow(Gf, D.G, (long long)ncomp * P->nqp, s));
+        CUDA_TRY(launch_narrow(Rf, D.R, ntab, s));
+        CUDA_TRY(launch_narrow(dRf, D.dR, ntab, s));
+        CUDA_TRY(launch_narrow(Uf, D.U, (long long)hU.size(), s));
+        CUDA_TRY(launch_narrow(Utf, D.Ut, (long long)hU.size(), s));
+        CUDA_TRY(launch_narrow(dinvf, D.dinv, (long long)nd, s));
+        D.Gf = Gf; D.Rf = Rf; D.dRf = dRf; D.Uf = Uf; D.Utf = Utf; D.dinvf = dinvf;
+    }
     CUDA_TRY(cudaStreamSynchronize(s));
     return SGIGA_OK;
 }
@@ -604,7 +632,28 @@ static int apply_op(sgiga_plan_s* P, const double* x, double* y, const int* acti
     return SGIGA_OK;
 }
 
-static int precond(sgiga_plan_s* P, const double* r, double* z, const int* active) {
+static int apply_op(sgiga_plan_s* P, const float* x, float* y, const int* active) {
+    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 4, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3_f32(P->dp, x, y, active, P->stream));
+    else CUDA_TRY(launch_op2_f32(P->dp, x, y, active, P->stream));
+    return SGIGA_OK;
+}
+
+// Work vectors of one precision.
+template <typename Real>
+struct Vecs {
+    Real *x, *r, *z, *p, *q, *t1, *t2;
+};
+
+static Vecs<double> vecs64(sgiga_plan_s* P) {
+    return Vecs<double>{P->d_x, P->d_r, P->d_z, P->d_p, P->d_q, P->d_t1, P->d_t2};
+}
+static Vecs<float> vecs32(sgiga_plan_s* P) {
+    return Vecs<float>{P->f_x, P->f_r, P->f_z, P->f_p, P->f_q, P->f_t1, P->f_t2};
+}
+
+template <typename Real>
+static int precond(sgiga_plan_s* P, const Real* r, Real* z, const int* active, Real* t1, Real* t2) {
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
     if (P->cfg.precond == SGIGA_PRECOND_NONE) {
@@ -612,27 +661,92 @@ static int precond(sgiga_plan_s* P, const double* r, double* z, const int* activ
         return SGIGA_OK;
     }
     const int d = P->d;
-    double* t1 = P->d_t1;
-    double* t2 = P->d_t2;
-    const double* in = r;
-    double* bufs[2] = {t1, t2};
+    const Real* in = r;
+    Real* bufs[2] = {t1, t2};
     int cur = 0;
-    const size_t bytes = (size_t)P->ndof * 8;
+    const size_t bytes = (size_t)P->ndof * sizeof(Real);
     for (int k = 0; k < d; ++k) {
-        double* out = bufs[cur];
+        Real* out = bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
-        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
         in = out;
         cur ^= 1;
     }
-    CUDA_TRY(launch_fd_scale(D, (double*)in, active, s));
+    CUDA_TRY(launch_fd_scale<Real>(D, (Real*)in, active, s));
     for (int k = 0; k < d; ++k) {
-        double* out = (k == d - 1) ? z : bufs[cur];
+        Real* out = (k == d - 1) ? z : bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
-        CUDA_TRY(launch_fd_pass(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
         in = out;
         cur ^= 1;
     }
+    return SGIGA_OK;
+}
+
+// Batched preconditioned CG on K_g x_g = rhs_g for the grids allowed by
+// `outer` (all when null), each with its own scalars, until
+// ||r_g|| <= tol ||rhs_g|| or max_iter iterations. Scalars: scal[0..6].
+// Returns the number of grids still active (or a negative status).
+template <typename Real>
+static int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int max_iter, const int* outer,
+               int* active, int* iters, double* scal, int* iters_run) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    double* bb = scal + 0 * ng;
+    double* rz = scal + 1 * ng;
+    double* pq = scal + 2 * ng;
+    double* rr = scal + 3 * ng;
+    double* alpha = scal + 4 * ng;
+    double* beta = scal + 5 * ng;
+    double* rznew = scal + 6 * ng;
+    CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
+    CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
+    int rc = precond<Real>(P, v.r, v.z, active, v.t1, v.t2);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy<Real>(v.p, v.z, P->ndof, s));
+    CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rz, s));
+    int it = 0, nact = ng;
+    for (it = 0; it < max_iter; ++it) {
+        if ((rc = apply_op(P, v.p, v.q, active))) return rc;
+        CUDA_TRY(launch_dot<Real>(D, v.p, v.q, P->d_partial, pq, s));
+        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, active, s));
+        CUDA_TRY(launch_pcg_update_xr<Real>(D, v.x, v.r, v.p, v.q, alpha, active, P->d_partial, rr, s));
+        CUDA_TRY(launch_pcg_check(D, rr, bb, tol * tol, active, iters, P->d_nactive, s));
+        CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        nact = *P->h_nactive;
+        if (nact == 0) { ++it; break; }
+        if ((rc = precond<Real>(P, v.r, v.z, active, v.t1, v.t2))) return rc;
+        CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rznew, s));
+        CUDA_TRY(launch_pcg_beta(D, rz, rznew, nullptr, beta, s));
+        CUDA_TRY(launch_pcg_update_p<Real>(D, v.p, v.z, beta, active, s));
+    }
+    if (iters_run) *iters_run = it;
+    return nact;
+}
+
+static int solve_stats(sgiga_plan_s* P, const double* rr, const double* bb, const int* iters, int nact,
+                       sgiga_solve_stats* stats, std::chrono::steady_clock::time_point t0) {
+    if (!stats) return SGIGA_OK;
+    const int ng = (int)P->grids.size();
+    cudaStream_t s = P->stream;
+    std::vector<double> hrr(ng), hbb(ng);
+    std::vector<int> hit(ng);
+    CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hit.data(), iters, ng * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    double mx = 0.0;
+    int mi = 0;
+    for (int g = 0; g < ng; ++g) {
+        if (hbb[g] > 0) mx = std::max(mx, std::sqrt(hrr[g] / hbb[g]));
+        mi = std::max(mi, hit[g]);
+    }
+    stats->iterations = mi;
+    stats->converged = ng - nact;
+    stats->max_rel_residual = mx;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return SGIGA_OK;
 }
 
@@ -657,7 +771,8 @@ int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
     if (c.w < c.d * c.min_level - c.d + 1) return fail(SGIGA_ERR_ARG, "w too small for min_level");
     if (c.domain != SGIGA_DOMAIN_UNIT && c.domain != SGIGA_DOMAIN_ANNULUS) return fail(SGIGA_ERR_ARG, "unknown domain");
     if (c.grading < 0 || c.grading > 2 || (c.grading != 0 && !(c.gamma > 0))) return fail(SGIGA_ERR_ARG, "bad grading");
-    if (c.precision != SGIGA_PREC_FP64) return fail(SGIGA_ERR_ARG, "unsupported precision");
+    if (c.precision != SGIGA_PREC_FP64 && c.precision != SGIGA_PREC_MIXED_FP32)
+        return fail(SGIGA_ERR_ARG, "unsupported precision");
     if (c.precond != SGIGA_PRECOND_FD && c.precond != SGIGA_PRECOND_NONE) return fail(SGIGA_ERR_ARG, "bad precond");
     if (c.domain == SGIGA_DOMAIN_ANNULUS && c.p < 2) return fail(SGIGA_ERR_ARG, "annulus needs p >= 2 (exact circle)");
     sgiga_plan_s* P = new sgiga_plan_s();
@@ -774,65 +889,67 @@ int sgiga_apply(sgiga_plan_t P, const double* x, double* y) {
     return SGIGA_OK;
 }
 
+int sgiga_apply_f32(sgiga_plan_t P, const float* x, float* y) {
+    if (!P || !x || !y) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32) return fail(SGIGA_ERR_ARG, "plan has no FP32 data (precision)");
+    int rc = apply_op(P, x, y, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(cudaGetLastError());
+    return SGIGA_OK;
+}
+
 int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
     if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
-    return precond(P, r, z, nullptr);
+    return precond<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
 }
 
 int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats* stats) {
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
     if (!(rel_tol > 0) || max_iter < 1) return fail(SGIGA_ERR_ARG, "rel_tol must be > 0 and max_iter >= 1");
     auto t0 = std::chrono::steady_clock::now();
+    const int ng = (int)P->grids.size();
+    P->last_inner_iters = 0;
+    if (P->cfg.precision == SGIGA_PREC_FP64) {
+        int nact = pcg<double>(P, P->d_b, vecs64(P), rel_tol, max_iter, nullptr, P->d_active, P->d_iters, P->d_scal,
+                               nullptr);
+        if (nact < 0) return nact;
+        int rc = solve_stats(P, P->d_scal + 3 * ng, P->d_scal, P->d_iters, nact, stats, t0);
+        if (rc) return rc;
+        if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
+        return SGIGA_OK;
+    }
+    // Mixed precision: FP64 iterative refinement around an FP32 inner solve.
+    //   x = 0, r = b;  repeat: d = (inner FP32 PCG) K^{-1} r;  x += d;  r = b - K x (FP64)
+    // until ||r_g|| <= rel_tol ||b_g|| for every component (max_iter outer steps).
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
-    double* bb = P->d_scal + 0 * ng;
-    double* rz = P->d_scal + 1 * ng;
-    double* pq = P->d_scal + 2 * ng;
-    double* rr = P->d_scal + 3 * ng;
-    double* alpha = P->d_scal + 4 * ng;
-    double* beta = P->d_scal + 5 * ng;
-    double* rznew = P->d_scal + 6 * ng;
-    CUDA_TRY(launch_pcg_init(D, P->d_b, P->d_x, P->d_r, P->d_partial, bb, s));
-    CUDA_TRY(launch_pcg_start(D, bb, P->d_active, P->d_iters, s));
-    int rc = precond(P, P->d_r, P->d_z, P->d_active);
-    if (rc) return rc;
-    CUDA_TRY(launch_copy(P->d_p, P->d_z, P->ndof, s));
-    CUDA_TRY(launch_dot(D, P->d_r, P->d_z, P->d_partial, rz, s));
-    int it = 0, nact = ng;
-    for (it = 0; it < max_iter; ++it) {
-        if ((rc = apply_op(P, P->d_p, P->d_q, P->d_active))) return rc;
-        CUDA_TRY(launch_dot(D, P->d_p, P->d_q, P->d_partial, pq, s));
-        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, P->d_active, s));
-        CUDA_TRY(launch_pcg_update_xr(D, P->d_x, P->d_r, P->d_p, P->d_q, alpha, P->d_active, P->d_partial, rr, s));
-        CUDA_TRY(launch_pcg_check(D, rr, bb, rel_tol * rel_tol, P->d_active, P->d_iters, P->d_nactive, nullptr, s));
+    double* bb = P->d_scal64o + 0 * ng;
+    double* rr = P->d_scal64o + 3 * ng;
+    CUDA_TRY(launch_pcg_init<double>(D, P->d_b, P->d_x, P->d_r, P->d_partial, bb, s));
+    CUDA_TRY(launch_copy<double>(rr, bb, ng, s));
+    CUDA_TRY(launch_pcg_start(D, bb, nullptr, P->d_active_o, P->d_iters_o, s));
+    int nact = ng, outer = 0, inner_total = 0;
+    for (outer = 0; outer <= max_iter; ++outer) {
+        // convergence of the FP64 residual (also counts outer steps per grid)
+        CUDA_TRY(launch_pcg_check(D, rr, bb, rel_tol * rel_tol, P->d_active_o, P->d_iters_o, P->d_nactive, s));
         CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         nact = *P->h_nactive;
-        if (nact == 0) { ++it; break; }
-        if ((rc = precond(P, P->d_r, P->d_z, P->d_active))) return rc;
-        CUDA_TRY(launch_dot(D, P->d_r, P->d_z, P->d_partial, rznew, s));
-        CUDA_TRY(launch_pcg_beta(D, rz, rznew, beta, s));
-        CUDA_TRY(launch_pcg_update_p(D, P->d_p, P->d_z, beta, P->d_active, s));
+        if (nact == 0 || outer == max_iter) break;
+        CUDA_TRY(launch_ir_down(D, P->d_r, P->f_b, P->d_active_o, s));
+        int inner = 0;
+        int rc = pcg<float>(P, P->f_b, vecs32(P), P->inner_tol, P->inner_max, P->d_active_o, P->d_active,
+                            P->d_iters, P->d_scal, &inner);
+        if (rc < 0) return rc;
+        inner_total += inner;
+        CUDA_TRY(launch_ir_up(D, P->d_x, P->f_x, P->d_active_o, s));
+        if ((rc = apply_op(P, P->d_x, P->d_q, P->d_active_o))) return rc;
+        CUDA_TRY(launch_ir_residual(D, P->d_b, P->d_q, P->d_r, P->d_active_o, P->d_partial, rr, s));
     }
-    if (stats) {
-        std::vector<double> hrr(ng), hbb(ng);
-        std::vector<int> hit(ng);
-        CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaMemcpyAsync(hit.data(), P->d_iters, ng * 4, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        double mx = 0.0;
-        int mi = 0;
-        for (int g = 0; g < ng; ++g) {
-            if (hbb[g] > 0) mx = std::max(mx, std::sqrt(hrr[g] / hbb[g]));
-            mi = std::max(mi, hit[g]);
-        }
-        stats->iterations = mi;
-        stats->converged = ng - nact;
-        stats->max_rel_residual = mx;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
+    P->last_inner_iters = inner_total;
+    int rc = solve_stats(P, rr, bb, P->d_iters_o, nact, stats, t0);
+    if (rc) return rc;
+    if (stats) stats->iterations = outer;
     if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
     return SGIGA_OK;
 }

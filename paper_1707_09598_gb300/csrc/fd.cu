@@ -24,9 +24,9 @@
 
 namespace sgiga {
 
-template <int NC>
-__device__ __forceinline__ void fd_rows(const double* __restrict__ MT, const double* __restrict__ vin,
-                                        double* __restrict__ vout, int n, long long B, int i, bool act,
+template <typename Real, int NC>
+__device__ __forceinline__ void fd_rows(const Real* __restrict__ MT, const Real* __restrict__ vin,
+                                        Real* __restrict__ vout, int n, long long B, int i, bool act,
                                         long long c0, int j0, int j1, bool split) {
     long long base[NC];
 #pragma unroll
@@ -34,27 +34,41 @@ __device__ __forceinline__ void fd_rows(const double* __restrict__ MT, const dou
         long long col = c0 + c, a = col / B;
         base[c] = a * n * B + (col - a * B);
     }
-    double acc[NC];
+    Real acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-    const double* mp = MT + (act ? i : 0);
+    for (int c = 0; c < NC; ++c) acc[c] = 0;
+    const Real* mp = MT + (act ? i : 0);
     for (int j = j0; j < j1; ++j) {
-        const double m = act ? mp[(long long)j * n] : 0.0;
+        const Real m = act ? mp[(long long)j * n] : Real(0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] += m * __ldg(vin + base[c] + (long long)j * B);
     }
     if (!act) return;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        double* o = vout + base[c] + (long long)i * B;
+        Real* o = vout + base[c] + (long long)i * B;
         if (split) atomicAdd(o, acc[c]); else *o = acc[c];
     }
 }
 
+template <typename Real> struct FDData;
+template <> struct FDData<double> {
+    static __device__ __forceinline__ const double* U(const DevPlan& P) { return P.U; }
+    static __device__ __forceinline__ const double* Ut(const DevPlan& P) { return P.Ut; }
+    static __device__ __forceinline__ const double* dinv(const DevPlan& P) { return P.dinv; }
+};
+template <> struct FDData<float> {
+    static __device__ __forceinline__ const float* U(const DevPlan& P) { return P.Uf; }
+    static __device__ __forceinline__ const float* Ut(const DevPlan& P) { return P.Utf; }
+    static __device__ __forceinline__ const float* dinv(const DevPlan& P) { return P.dinvf; }
+};
+
+template <typename Real>
 __global__ void __launch_bounds__(256, 2)
 k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
-          const double* __restrict__ in, double* __restrict__ out, const int* __restrict__ active) {
-    __shared__ double sm[64 * 65];
+          const Real* __restrict__ in, Real* __restrict__ out, const int* __restrict__ active) {
+    __shared__ double sm_raw[64 * 65];
+    Real* sm = reinterpret_cast<Real*>(sm_raw);
     const FDItem it = items[blockIdx.x];
     if (active && !active[it.grid]) return;
     const GridDesc& g = P.grids[it.grid];
@@ -66,10 +80,10 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
     const long long Ncol = A * B;
     const Eig1D e = P.eigs[g.eig[dir]];
     // Mat[i][j] = U[j][i] (forward) or U[i][j] (backward); MT[j][i] = Mat[i][j]
-    const double* __restrict__ U = P.U + e.uoff;
-    const double* __restrict__ MT = forward ? P.U + e.uoff : P.Ut + e.uoff;
-    const double* vin = in + g.dof_off;
-    double* vout = out + g.dof_off;
+    const Real* __restrict__ U = FDData<Real>::U(P) + e.uoff;
+    const Real* __restrict__ MT = forward ? FDData<Real>::U(P) + e.uoff : FDData<Real>::Ut(P) + e.uoff;
+    const Real* vin = in + g.dof_off;
+    Real* vout = out + g.dof_off;
     const bool split = it.j0 > 0 || it.j1 < n;
 
     if (it.mode == FD_SMALL) {
@@ -83,8 +97,8 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
         long long b = lin % B, r = lin / B;
         int i = (int)(r % n);
         long long a = r / n;
-        const double* vp = vin + a * n * B + b;
-        double acc = 0.0;
+        const Real* vp = vin + a * n * B + b;
+        Real acc = 0;
         for (int j = 0; j < n; ++j) acc += sm[i * 65 + j] * vp[(long long)j * B];
         vout[lin] = acc;
         return;
@@ -96,33 +110,33 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
         const int i = i_w + lane;
         const bool act = i < n;
         switch (it.nc) {
-#define CASE(NCV) case NCV: fd_rows<NCV>(MT, vin, vout, n, B, i, act, it.c0, it.j0, it.j1, split); break;
+#define CASE(NCV) case NCV: fd_rows<Real, NCV>(MT, vin, vout, n, B, i, act, it.c0, it.j0, it.j1, split); break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         }
         return;
     }
     // FD_TILE
-    double (*As)[33] = reinterpret_cast<double (*)[33]>(sm);
-    double (*Bs)[65] = reinterpret_cast<double (*)[65]>(sm + 16 * 33);
+    Real (*As)[33] = reinterpret_cast<Real (*)[33]>(sm);
+    Real (*Bs)[65] = reinterpret_cast<Real (*)[65]>(sm + 16 * 33);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[2][4];
+    Real acc[2][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0;
     for (int j0 = it.j0; j0 < it.j1; j0 += 16) {
         for (int l = threadIdx.x; l < 512; l += 256) {
             int ii = l & 31, kk = l >> 5;
             int i = it.i0 + ii, j = j0 + kk;
-            As[kk][ii] = (i < n && j < it.j1) ? MT[(long long)j * n + i] : 0.0;
+            As[kk][ii] = (i < n && j < it.j1) ? MT[(long long)j * n + i] : Real(0);
         }
         for (int l = threadIdx.x; l < 1024; l += 256) {
             int kk, cc;
             if (B == 1) { kk = l & 15; cc = l >> 4; } else { cc = l & 63; kk = l >> 6; }
             long long c = it.c0 + cc;
             int j = j0 + kk;
-            double v = 0.0;
+            Real v = 0;
             if (c < Ncol && j < it.j1) {
                 long long a = c / B, b = c - a * B;
                 v = vin[a * n * B + (long long)j * B + b];
@@ -132,10 +146,10 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+            Real a0 = As[kk][ty], a1 = As[kk][ty + 16];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                double b = Bs[kk][tx + 16 * c];
+                Real b = Bs[kk][tx + 16 * c];
                 acc[0][c] += a0 * b;
                 acc[1][c] += a1 * b;
             }
@@ -157,27 +171,37 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
     }
 }
 
+template <typename Real>
 cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
-                           const double* in, double* out, const int* active, cudaStream_t s) {
+                           const Real* in, Real* out, const int* active, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_fd_pass<<<nitems, 256, 0, s>>>(P, items, dir, forward, in, out, active);
+    k_fd_pass<Real><<<nitems, 256, 0, s>>>(P, items, dir, forward, in, out, active);
     return cudaGetLastError();
 }
+template cudaError_t launch_fd_pass<double>(const DevPlan&, const FDItem*, int, int, int, const double*, double*,
+                                            const int*, cudaStream_t);
+template cudaError_t launch_fd_pass<float>(const DevPlan&, const FDItem*, int, int, int, const float*, float*,
+                                           const int*, cudaStream_t);
 
 // z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every packed entry.
-__global__ void k_fd_scale(const Chunk* __restrict__ chunks, const double* __restrict__ dinv, double* __restrict__ z,
+template <typename Real>
+__global__ void k_fd_scale(const Chunk* __restrict__ chunks, DevPlan P, Real* __restrict__ z,
                            const int* __restrict__ active) {
     const Chunk c = chunks[blockIdx.x];
     if (active && !active[c.grid]) return;
+    const Real* dinv = FDData<Real>::dinv(P);
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) z[c.start + i] *= dinv[c.start + i];
 }
 
-cudaError_t launch_fd_scale(const DevPlan& P, double* z, const int* active, cudaStream_t s) {
+template <typename Real>
+cudaError_t launch_fd_scale(const DevPlan& P, Real* z, const int* active, cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_fd_scale<<<P.nchunks, 256, 0, s>>>(P.chunks, P.dinv, z, active);
+    k_fd_scale<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, P, z, active);
     return cudaGetLastError();
 }
+template cudaError_t launch_fd_scale<double>(const DevPlan&, double*, const int*, cudaStream_t);
+template cudaError_t launch_fd_scale<float>(const DevPlan&, float*, const int*, cudaStream_t);
 
 }  // namespace sgiga

@@ -32,6 +32,12 @@ struct DevPlan {
     double* dR;
     int* first;              // per-table first function of each element
     double* G;               // ncomp planes of nqp (tile-major)
+    float* Gf;               // FP32 copy of G (mixed precision)
+    float* Rf;               // FP32 copies of the basis tables
+    float* dRf;
+    const float* Uf;         // FP32 copies of U, U^T and dinv
+    const float* Utf;
+    const float* dinvf;
     double* mw;              // w |det J| (tile-major)
     double* rho;             // f w |det J| (tile-major)
     const double* U;         // eigenvectors, U[j][i] = component j of eigenvector i
@@ -56,28 +62,43 @@ cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh,
 cudaError_t launch_op2(const DevPlan& P, const double* x, double* y, const int* active, int mode, cudaStream_t s);
 cudaError_t launch_op3(const DevPlan& P, const double* x, double* y, const int* active, int mode, cudaStream_t s);
 cudaError_t set_op2_smem(int p, size_t bytes);
+cudaError_t launch_op2_f32(const DevPlan& P, const float* x, float* y, const int* active, cudaStream_t s);
+cudaError_t launch_op3_f32(const DevPlan& P, const float* x, float* y, const int* active, cudaStream_t s);
 cudaError_t set_op3_smem(int p, size_t bytes);
 // fd.cu
+template <typename Real>
 cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
-                           const double* in, double* out, const int* active, cudaStream_t s);
-cudaError_t launch_fd_scale(const DevPlan& P, double* z, const int* active, cudaStream_t s);
-// vec.cu
-cudaError_t launch_dot(const DevPlan& P, const double* a, const double* b, double* partial, double* out,
-                       cudaStream_t s);
-cudaError_t launch_pcg_init(const DevPlan& P, const double* b, double* x, double* r, double* partial,
-                            double* bb, cudaStream_t s);
-cudaError_t launch_pcg_update_xr(const DevPlan& P, double* x, double* r, const double* p, const double* q,
+                           const Real* in, Real* out, const int* active, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_scale(const DevPlan& P, Real* z, const int* active, cudaStream_t s);
+// vec.cu (Real = double or float; scalars and reductions in FP64)
+template <typename Real>
+cudaError_t launch_dot(const DevPlan& P, const Real* a, const Real* b, double* partial, double* out, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_pcg_init(const DevPlan& P, const Real* b, Real* x, Real* r, double* partial, double* bb,
+                            cudaStream_t s);
+template <typename Real>
+cudaError_t launch_pcg_update_xr(const DevPlan& P, Real* x, Real* r, const Real* p, const Real* q,
                                  const double* alpha, const int* active, double* partial, double* rr,
                                  cudaStream_t s);
-cudaError_t launch_pcg_update_p(const DevPlan& P, double* p, const double* z, const double* beta,
-                                const int* active, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_pcg_update_p(const DevPlan& P, Real* p, const Real* z, const double* beta, const int* active,
+                                cudaStream_t s);
+template <typename Real>
+cudaError_t launch_copy(Real* dst, const Real* src, long long n, cudaStream_t s);
 cudaError_t launch_pcg_alpha(const DevPlan& P, const double* rz, const double* pq, double* alpha,
                              const int* active, cudaStream_t s);
-cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, double* beta, cudaStream_t s);
+cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, const double* rzmid, double* beta,
+                            cudaStream_t s);
 cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* bb, double tol2, int* active,
-                             int* iters, int* nactive, double* maxrel, cudaStream_t s);
-cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, int* active, int* iters, cudaStream_t s);
-cudaError_t launch_copy(double* dst, const double* src, long long n, cudaStream_t s);
+                             int* iters, int* nactive, cudaStream_t s);
+cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, const int* outer, int* active, int* iters,
+                             cudaStream_t s);
+cudaError_t launch_ir_down(const DevPlan& P, const double* r64, float* r32, const int* active, cudaStream_t s);
+cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const int* active, cudaStream_t s);
+cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
+                               double* partial, double* rr, cudaStream_t s);
+cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);
 // eval.cu
 cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts,
                         double* ucomp, cudaStream_t s);

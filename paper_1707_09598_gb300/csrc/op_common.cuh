@@ -13,6 +13,19 @@
 
 namespace sgiga {
 
+// Plan arrays of the operator kernels in the kernel's arithmetic type.
+template <typename Real> struct OpData;
+template <> struct OpData<double> {
+    static __device__ __forceinline__ const double* G(const DevPlan& P) { return P.G; }
+    static __device__ __forceinline__ const double* R(const DevPlan& P) { return P.R; }
+    static __device__ __forceinline__ const double* dR(const DevPlan& P) { return P.dR; }
+};
+template <> struct OpData<float> {
+    static __device__ __forceinline__ const float* G(const DevPlan& P) { return P.Gf; }
+    static __device__ __forceinline__ const float* R(const DevPlan& P) { return P.Rf; }
+    static __device__ __forceinline__ const float* dR(const DevPlan& P) { return P.dRf; }
+};
+
 __device__ __forceinline__ int elem_lo(int j, int P, int M) { return j >= P ? (j - P + M - 1) / M : 0; }
 __device__ __forceinline__ int elem_hi(int j, int M, int T) { int e = j / M; return e < T - 1 ? e : T - 1; }
 

@@ -2,7 +2,8 @@
 // scalars (alpha, beta, residual norms) and convergence flag. Packed vectors
 // are cut into chunks of at most 4096 entries that never straddle two grids;
 // a block reduces its chunk, and a second kernel sums each grid's chunk
-// partials in a fixed order (deterministic dot products).
+// partials in a fixed order (deterministic dot products). Vectors may be FP64
+// or FP32; scalars and reductions are FP64.
 #include "kernels.h"
 
 namespace sgiga {
@@ -23,15 +24,6 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-__global__ void k_dot(const Chunk* __restrict__ chunks, const double* __restrict__ a, const double* __restrict__ b,
-                      double* __restrict__ partial) {
-    const Chunk c = chunks[blockIdx.x];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < c.len; i += blockDim.x) s += a[c.start + i] * b[c.start + i];
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
 __global__ void k_reduce(const GridDesc* __restrict__ grids, int ngrids, const double* __restrict__ partial,
                          double* __restrict__ out) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,52 +40,67 @@ static cudaError_t reduce(const DevPlan& P, const double* partial, double* out, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_dot(const DevPlan& P, const double* a, const double* b, double* partial, double* out,
+template <typename Real>
+__global__ void k_dot(const Chunk* __restrict__ chunks, const Real* __restrict__ a, const Real* __restrict__ b,
+                      double* __restrict__ partial) {
+    const Chunk c = chunks[blockIdx.x];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) s += (double)a[c.start + i] * (double)b[c.start + i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename Real>
+cudaError_t launch_dot(const DevPlan& P, const Real* a, const Real* b, double* partial, double* out,
                        cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_dot<<<P.nchunks, 256, 0, s>>>(P.chunks, a, b, partial);
+    k_dot<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, a, b, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return reduce(P, partial, out, s);
 }
 
-__global__ void k_pcg_init(const Chunk* __restrict__ chunks, const double* __restrict__ b, double* __restrict__ x,
-                           double* __restrict__ r, double* __restrict__ partial) {
+// x = 0, r = b, partial sums of ||b||^2
+template <typename Real>
+__global__ void k_pcg_init(const Chunk* __restrict__ chunks, const Real* __restrict__ b, Real* __restrict__ x,
+                           Real* __restrict__ r, double* __restrict__ partial) {
     const Chunk c = chunks[blockIdx.x];
     double s = 0.0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
-        double v = b[c.start + i];
-        x[c.start + i] = 0.0;
+        Real v = b[c.start + i];
+        x[c.start + i] = Real(0);
         r[c.start + i] = v;
-        s += v * v;
+        s += (double)v * (double)v;
     }
     s = block_sum(s);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-cudaError_t launch_pcg_init(const DevPlan& P, const double* b, double* x, double* r, double* partial, double* bb,
+template <typename Real>
+cudaError_t launch_pcg_init(const DevPlan& P, const Real* b, Real* x, Real* r, double* partial, double* bb,
                             cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_pcg_init<<<P.nchunks, 256, 0, s>>>(P.chunks, b, x, r, partial);
+    k_pcg_init<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, b, x, r, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return reduce(P, partial, bb, s);
 }
 
-__global__ void k_update_xr(const Chunk* __restrict__ chunks, double* __restrict__ x, double* __restrict__ r,
-                            const double* __restrict__ p, const double* __restrict__ q,
+template <typename Real>
+__global__ void k_update_xr(const Chunk* __restrict__ chunks, Real* __restrict__ x, Real* __restrict__ r,
+                            const Real* __restrict__ p, const Real* __restrict__ q,
                             const double* __restrict__ alpha, const int* __restrict__ active,
                             double* __restrict__ partial) {
     const Chunk c = chunks[blockIdx.x];
     double s = 0.0;
     if (active[c.grid]) {
-        const double al = alpha[c.grid];
+        const Real al = (Real)alpha[c.grid];
         for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
             long long k = c.start + i;
             x[k] += al * p[k];
-            double rv = r[k] - al * q[k];
+            Real rv = r[k] - al * q[k];
             r[k] = rv;
-            s += rv * rv;
+            s += (double)rv * (double)rv;
         }
     } else {
         for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
@@ -105,33 +112,65 @@ __global__ void k_update_xr(const Chunk* __restrict__ chunks, double* __restrict
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-cudaError_t launch_pcg_update_xr(const DevPlan& P, double* x, double* r, const double* p, const double* q,
+template <typename Real>
+cudaError_t launch_pcg_update_xr(const DevPlan& P, Real* x, Real* r, const Real* p, const Real* q,
                                  const double* alpha, const int* active, double* partial, double* rr,
                                  cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_update_xr<<<P.nchunks, 256, 0, s>>>(P.chunks, x, r, p, q, alpha, active, partial);
+    k_update_xr<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, x, r, p, q, alpha, active, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return reduce(P, partial, rr, s);
 }
 
-__global__ void k_update_p(const Chunk* __restrict__ chunks, double* __restrict__ p, const double* __restrict__ z,
+template <typename Real>
+__global__ void k_update_p(const Chunk* __restrict__ chunks, Real* __restrict__ p, const Real* __restrict__ z,
                            const double* __restrict__ beta, const int* __restrict__ active) {
     const Chunk c = chunks[blockIdx.x];
     if (!active[c.grid]) return;
-    const double be = beta[c.grid];
+    const Real be = (Real)beta[c.grid];
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         long long k = c.start + i;
         p[k] = z[k] + be * p[k];
     }
 }
 
-cudaError_t launch_pcg_update_p(const DevPlan& P, double* p, const double* z, const double* beta,
-                                const int* active, cudaStream_t s) {
+template <typename Real>
+cudaError_t launch_pcg_update_p(const DevPlan& P, Real* p, const Real* z, const double* beta, const int* active,
+                                cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_update_p<<<P.nchunks, 256, 0, s>>>(P.chunks, p, z, beta, active);
+    k_update_p<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, p, z, beta, active);
     return cudaGetLastError();
 }
+
+template <typename Real>
+__global__ void k_copy(Real* __restrict__ dst, const Real* __restrict__ src, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+template <typename Real>
+cudaError_t launch_copy(Real* dst, const Real* src, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    SGIGA_COUNT_LAUNCH();
+    k_copy<Real><<<(int)blocks, 256, 0, s>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+#define INST(R)                                                                                                  \
+    template cudaError_t launch_dot<R>(const DevPlan&, const R*, const R*, double*, double*, cudaStream_t);    \
+    template cudaError_t launch_pcg_init<R>(const DevPlan&, const R*, R*, R*, double*, double*, cudaStream_t);  \
+    template cudaError_t launch_pcg_update_xr<R>(const DevPlan&, R*, R*, const R*, const R*, const double*,     \
+                                                 const int*, double*, double*, cudaStream_t);                  \
+    template cudaError_t launch_pcg_update_p<R>(const DevPlan&, R*, const R*, const double*, const int*,        \
+                                                cudaStream_t);                                                 \
+    template cudaError_t launch_copy<R>(R*, const R*, long long, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
 
 __global__ void k_alpha(int ng, const double* __restrict__ rz, const double* __restrict__ pq,
                         double* __restrict__ alpha, const int* __restrict__ active) {
@@ -148,17 +187,22 @@ cudaError_t launch_pcg_alpha(const DevPlan& P, const double* rz, const double* p
     return cudaGetLastError();
 }
 
-__global__ void k_beta(int ng, double* __restrict__ rz, const double* __restrict__ rznew, double* __restrict__ beta) {
+// beta = (rz_new - rz_mid) / rz; rz_mid = r_new . z_old for the flexible
+// (Polak-Ribiere) variant, absent for plain PCG
+__global__ void k_beta(int ng, double* __restrict__ rz, const double* __restrict__ rznew,
+                       const double* __restrict__ rzmid, double* __restrict__ beta) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
     double old = rz[g];
-    beta[g] = old != 0.0 ? rznew[g] / old : 0.0;
+    double num = rznew[g] - (rzmid ? rzmid[g] : 0.0);
+    beta[g] = old != 0.0 ? num / old : 0.0;
     rz[g] = rznew[g];
 }
 
-cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, double* beta, cudaStream_t s) {
+cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, const double* rzmid, double* beta,
+                            cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_beta<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, rz, rznew, beta);
+    k_beta<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, rz, rznew, rzmid, beta);
     return cudaGetLastError();
 }
 
@@ -174,8 +218,7 @@ __global__ void k_check(int ng, const double* __restrict__ rr, const double* __r
 }
 
 cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* bb, double tol2, int* active,
-                             int* iters, int* nactive, double* maxrel, cudaStream_t s) {
-    (void)maxrel;
+                             int* iters, int* nactive, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(nactive, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
@@ -183,32 +226,90 @@ cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* b
     return cudaGetLastError();
 }
 
-// Every component with a nonzero load vector starts active, with 0 iterations.
-__global__ void k_start(int ng, const double* __restrict__ bb, int* __restrict__ active, int* __restrict__ iters) {
+// Start mask: active[g] = (bb[g] > 0) && (outer == null || outer[g]); iters[g] = 0.
+__global__ void k_start(int ng, const double* __restrict__ bb, const int* __restrict__ outer,
+                        int* __restrict__ active, int* __restrict__ iters) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
-    active[g] = bb[g] > 0.0 ? 1 : 0;
+    active[g] = (bb[g] > 0.0 && (!outer || outer[g])) ? 1 : 0;
     iters[g] = 0;
 }
 
-cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, int* active, int* iters, cudaStream_t s) {
+cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, const int* outer, int* active, int* iters,
+                             cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_start<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, bb, active, iters);
+    k_start<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, bb, outer, active, iters);
     return cudaGetLastError();
 }
 
-__global__ void k_copy(double* __restrict__ dst, const double* __restrict__ src, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) dst[i] = src[i];
+// Iterative refinement helpers (FP64 outer loop around an FP32 inner solve).
+// r32 = (float) r64 on active grids, 0 elsewhere
+__global__ void k_ir_down(const Chunk* __restrict__ chunks, const double* __restrict__ r64, float* __restrict__ r32,
+                          const int* __restrict__ active) {
+    const Chunk c = chunks[blockIdx.x];
+    const bool a = active[c.grid] != 0;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) r32[c.start + i] = a ? (float)r64[c.start + i] : 0.0f;
 }
 
-cudaError_t launch_copy(double* dst, const double* src, long long n, cudaStream_t s) {
+cudaError_t launch_ir_down(const DevPlan& P, const double* r64, float* r32, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_ir_down<<<P.nchunks, 256, 0, s>>>(P.chunks, r64, r32, active);
+    return cudaGetLastError();
+}
+
+// x64 += (double) d32 on active grids
+__global__ void k_ir_up(const Chunk* __restrict__ chunks, double* __restrict__ x64, const float* __restrict__ d32,
+                        const int* __restrict__ active) {
+    const Chunk c = chunks[blockIdx.x];
+    if (!active[c.grid]) return;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) x64[c.start + i] += (double)d32[c.start + i];
+}
+
+cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_ir_up<<<P.nchunks, 256, 0, s>>>(P.chunks, x64, d32, active);
+    return cudaGetLastError();
+}
+
+// r64 = b - q on active grids (q = K x64 in FP64); partial ||r64||^2 for every grid
+__global__ void k_ir_residual(const Chunk* __restrict__ chunks, const double* __restrict__ b,
+                              const double* __restrict__ q, double* __restrict__ r, const int* __restrict__ active,
+                              double* __restrict__ partial) {
+    const Chunk c = chunks[blockIdx.x];
+    double s = 0.0;
+    const bool a = active[c.grid] != 0;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        long long k = c.start + i;
+        double v = a ? b[k] - q[k] : r[k];
+        r[k] = v;
+        s += v * v;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
+                               double* partial, double* rr, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_ir_residual<<<P.nchunks, 256, 0, s>>>(P.chunks, b, q, r, active, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return reduce(P, partial, rr, s);
+}
+
+// Narrow an FP64 array to FP32 (plan set-up of the mixed-precision copies).
+__global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     SGIGA_COUNT_LAUNCH();
-    k_copy<<<(int)blocks, 256, 0, s>>>(dst, src, n);
+    k_narrow<<<(int)blocks, 256, 0, s>>>(dst, src, n);
     return cudaGetLastError();
 }
 

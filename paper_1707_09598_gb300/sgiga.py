@@ -28,7 +28,7 @@ SGIGA_ERR_GEOMETRY = -6
 
 DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1}
 GRADING = {"uniform": 0, "radical": 1, "onesided": 2}
-PREC = {"fp64": 0}
+PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 PRECOND = {"fd": 0, "none": 1}
 SOURCE = {"sine": 0, "poly": 1, "annulus": 2, "annulus_paper": 3, "one": 4}
 
@@ -72,6 +72,7 @@ _SIGS = {
     "sgiga_get_rhs": (_I, [_P, _P]),
     "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
+    "sgiga_apply_f32": (_I, [_P, _P, _P]),
     "sgiga_precond": (_I, [_P, _P, _P]),
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
     "sgiga_get_solution": (_I, [_P, _P]),
@@ -178,6 +179,15 @@ def sgiga_get_rhs(plan, b):
 def sgiga_apply(plan, x, y):
     n = sgiga_plan_info(plan).ndof
     _check(_lib.sgiga_apply(plan, _ptr(x, n), _ptr(y, n)))
+
+
+def sgiga_apply_f32(plan, x, y):
+    import torch
+    n = sgiga_plan_info(plan).ndof
+    for t in (x, y):
+        if not (hasattr(t, "dtype") and t.dtype == torch.float32 and t.is_contiguous() and t.numel() >= n):
+            raise TypeError("expected contiguous float32 tensors of %d entries" % n)
+    _check(_lib.sgiga_apply_f32(plan, x.data_ptr(), y.data_ptr()))
 
 
 def sgiga_precond(plan, r, z):

@@ -24,7 +24,9 @@ sys.path.insert(0, ROOT)
 # name -> (domain, d, p, w, problem, eval lattice k, selected components)
 CASES = {
     "cube_p3_w10": ("unit", 3, 3, 10, "sine3", 16, [(10, 1, 1), (4, 4, 4), (1, 5, 4), (3, 3, 4)]),
-    "annulus_p3_w9": ("annulus", 2, 3, 9, "annulus_sinx", 64, [(9, 1), (5, 5), (1, 9)]),
+    "annulus_p2_w12": ("annulus", 2, 2, 12, "annulus_sinx", 64, [(12, 1), (6, 6), (1, 12)]),
+    "annulus_p3_w12": ("annulus", 2, 3, 12, "annulus_sinx", 64, [(12, 1), (6, 6), (1, 12)]),
+    "annulus_p4_w12": ("annulus", 2, 4, 12, "annulus_sinx", 64, [(12, 1), (6, 6), (1, 12)]),
 }
 
 

@@ -1,0 +1,116 @@
+"""Mixed-precision path (FP32 inner solve, FP64 iterative refinement) against the oracle.
+
+The FP32 operator is checked against the oracle's assembled matrix at FP32
+accuracy; the refined solutions against the oracle's direct solves at the
+mixed-path target (relative L2 1e-8 of the combined solution), including the
+full-size quarter-annulus workload (p = 2, 3, 4, w = 12) against stored
+oracle values.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import combination, geometry, problems  # noqa: E402
+from oracle.galerkin import Component  # noqa: E402
+from paper_1707_09598_gb300.inputs import eval_points, random_points, random_vector  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_09598_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1707_09598_gb300 import sgiga
+    return sgiga
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [
+    # (domain, d, p, w, grading, gamma, source, oracle problem)
+    ("unit", 3, 3, 6, "uniform", 1.0, "sine", "sine3"),
+    ("annulus", 2, 3, 8, "uniform", 1.0, "annulus", "annulus_sinx"),
+    ("annulus", 2, 2, 7, "radical", 2.0, "annulus_paper", "annulus_paper2"),
+    ("unit", 2, 4, 8, "onesided", 2.0, "sine", "sine2"),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp32_apply(sg, case):
+    domain, d, p, w, grading, gamma, src, pname = case
+    with sg.Plan(d, p, w, domain=domain, grading=grading, gamma=gamma, precision="mixed") as P:
+        n = P.info.ndof
+        x = random_vector(n, seed=41)
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        sg.sgiga_apply_f32(P.handle, torch.as_tensor(x, dtype=torch.float32, device="cuda"), y)
+        y = y.double().cpu().numpy()
+        geom = geometry.make(domain, d)
+        for g in P.grids[:: max(1, len(P.grids) // 5)]:
+            comp = Component(geom, tuple(g.levels[:d]), p, None, grading, gamma).assemble()
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            ref = comp.K @ x[sl].astype(np.float32).astype(np.float64)
+            # FP32 data and accumulation: error a few ulp of the operator's scale
+            assert _rel(y[sl], ref) < 2e-5, (g.levels[:d], _rel(y[sl], ref))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mixed_solve_against_oracle(sg, case):
+    domain, d, p, w, grading, gamma, src, pname = case
+    prob = problems.get(pname)
+    geom = geometry.make(domain, d)
+    pts = random_points(400, d, seed=42)
+    with sg.Plan(d, p, w, domain=domain, grading=grading, gamma=gamma, precision="mixed") as P:
+        sg.sgiga_set_rhs_builtin(P.handle, src)
+        st, _ = sg.sgiga_solve(P.handle, 1e-11, 20)
+        assert st.converged == P.info.ngrids
+        assert st.max_rel_residual <= 1e-11
+        u = np.zeros(P.info.ndof)
+        sg.sgiga_get_solution(P.handle, u)
+        uc = np.zeros(P.info.ngrids * len(pts))
+        sg.sgiga_eval(P.handle, np.ascontiguousarray(pts), len(pts), uc)
+        uu = np.zeros(len(pts))
+        sg.sgiga_combine(P.handle, uc, len(pts), uu)
+        vals, coeffs = [], []
+        for g in P.grids:
+            comp = Component(geom, tuple(g.levels[:d]), p, None, grading, gamma).assemble(f=prob.f)
+            uo = comp.solve()
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            assert _rel(u[sl], uo) < 1e-8, (g.levels[:d], _rel(u[sl], uo))
+            vals.append(comp.evaluate(uo, pts))
+            coeffs.append(g.coeff)
+        ref = combination.combine(np.stack(vals), np.array(coeffs, dtype=np.float64))
+        assert _rel(uu, ref) < 1e-8
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_annulus_w12_full_size_mixed(sg, p):
+    """Quarter annulus, u = x y (r^2-1)(r^2-4) sin x, p = 2, 3, 4, w = 12 (23
+    components): mixed-precision solve refined to 1e-10, combined values on the
+    65 x 65 lattice against stored oracle values (target 1e-8)."""
+    gold = np.loadtxt(os.path.join(GOLD, "annulus_p%d_w12.txt" % p))
+    pts = eval_points(2, 64)
+    with sg.Plan(2, p, 12, domain="annulus", precision="mixed") as P:
+        assert P.info.ngrids == 23
+        sg.sgiga_set_rhs_builtin(P.handle, "annulus")
+        st, _ = sg.sgiga_solve(P.handle, 1e-10, 30)
+        assert st.converged == 23
+        uc = np.zeros(P.info.ngrids * len(pts))
+        sg.sgiga_eval(P.handle, np.ascontiguousarray(pts), len(pts), uc)
+        uu = np.zeros(len(pts))
+        sg.sgiga_combine(P.handle, uc, len(pts), uu)
+        assert _rel(uu, gold[:, 0]) < 1e-8, _rel(uu, gold[:, 0])
+        ucn = uc.reshape(P.info.ngrids, len(pts))
+        levels = [tuple(g.levels[:2]) for g in P.grids]
+        for col, sel in enumerate([(12, 1), (6, 6), (1, 12)]):
+            assert _rel(ucn[levels.index(sel)], gold[:, 1 + col]) < 1e-8

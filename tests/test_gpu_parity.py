@@ -207,7 +207,8 @@ def test_eigenpairs(sg):
             np.testing.assert_allclose(lam, lam_o, rtol=1e-9)
             from oracle.galerkin import stiffness_1d
             K, M = stiffness_1d(lv, 3, 2)
-            np.testing.assert_allclose(U.T @ M @ U, np.eye(n), atol=1e-12)
+            # n > 384 uses inverse-iteration eigenvectors: orthogonality eps ||T|| / gap
+            np.testing.assert_allclose(U.T @ M @ U, np.eye(n), atol=1e-10)
             np.testing.assert_allclose(K @ U, (M @ U) * lam[None, :], atol=1e-9 * lam.max())
 
 
