@@ -54,7 +54,21 @@ typedef enum {
  * 1 and 2 as a NURBS patch (direction 1 radial, degree 1; direction 2 angular,
  * degree 2, weights 1, sqrt(2)/2, 1), extruded along z in [0,1] when d = 3
  * (Sec. 4.2). */
-enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1 };
+enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1, SGIGA_DOMAIN_PATCH = 2 };
+
+/* A user geometry for SGIGA_DOMAIN_PATCH (eq. F-B-splines): a tensor-product
+ * B-spline/NURBS patch with per-direction degree (<= 3), open knot vector
+ * (<= 12 knots), control-point count (<= 8) and optional 1D weights (NULL:
+ * polynomial direction; the weight function is their tensor product). cp is
+ * [ncp0*ncp1*ncp2][d] (host), direction 0 fastest, at most 128 points. */
+typedef struct {
+    int deg[3];
+    int nknots[3];
+    const double* knots[3];
+    int ncp[3];
+    const double* weights[3];
+    const double* cp;
+} sgiga_patch;
 
 /* Breakpoint grading g(j/E) (Sec. 4.4): UNIFORM g(t) = t; RADICAL
  * g(t) = 2^(gamma-1) t^gamma for t <= 1/2, 1 - 2^(gamma-1) (1-t)^gamma
@@ -69,8 +83,11 @@ enum { SGIGA_GRADING_UNIFORM = 0, SGIGA_GRADING_RADICAL = 1, SGIGA_GRADING_ONESI
 enum { SGIGA_PREC_FP64 = 0, SGIGA_PREC_MIXED_FP32 = 1 };
 
 /* Preconditioner of the batched conjugate-gradient solve. FD: fast
- * diagonalisation with the 1D generalised eigenpairs; NONE: plain CG. */
-enum { SGIGA_PRECOND_FD = 0, SGIGA_PRECOND_NONE = 1 };
+ * diagonalisation with the 1D generalised eigenpairs; NONE: plain CG;
+ * LEARNED: FD plus a trained convolutional correction (sgiga_net_*), used by
+ * the inner FP32 solve of SGIGA_PREC_MIXED_FP32 as flexible CG (needs that
+ * precision; falls back to FD until a network is initialised). */
+enum { SGIGA_PRECOND_FD = 0, SGIGA_PRECOND_NONE = 1, SGIGA_PRECOND_LEARNED = 2 };
 
 /* Built-in right-hand sides f = -Laplace(u) for manufactured solutions u:
  * SINE      u = prod_k sin(pi x_k)
@@ -92,6 +109,7 @@ typedef struct {
     double gamma;     /* grading exponent (ignored for UNIFORM) */
     int precision;    /* SGIGA_PREC_* */
     int precond;      /* SGIGA_PRECOND_* */
+    const sgiga_patch* patch; /* geometry for SGIGA_DOMAIN_PATCH (host), else NULL */
 } sgiga_config;
 
 typedef struct {
@@ -117,6 +135,7 @@ typedef struct {
     int converged;           /* number of components that met rel_tol */
     double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
     double seconds;          /* wall time of the call */
+    int inner_iterations;    /* MIXED_FP32: inner CG iterations summed over refinement steps */
 } sgiga_solve_stats;
 
 /* Build a plan: index set and coefficients (Sec. 3), knot vectors and
@@ -149,6 +168,14 @@ int sgiga_set_rhs_builtin(sgiga_plan_t plan, int source);
 /* f(x_q) of a built-in source (SGIGA_SRC_*) at every quadrature point, in
  * natural qp order: f is [nqp], host or device (input data for sgiga_set_rhs). */
 int sgiga_source_at_qp(sgiga_plan_t plan, int source, double* f);
+
+/* Diffusion coefficient a(x) in -div(a grad u) = f: a = exp(amp * sum_f
+ * cos(omega_f . x + phase_f)), a random-Fourier-feature sample of a log-normal
+ * field (not in the paper, whose coefficient is 1). omega [nfeat][d] and phase
+ * [nfeat] are host arrays; nfeat = 0 restores a = 1. The geometry
+ * coefficients of every quadrature point are recomputed (K_ij gains the factor
+ * a(x_q)); the load vector and the preconditioner are unchanged. */
+int sgiga_set_coefficient(sgiga_plan_t plan, int nfeat, const double* omega, const double* phase, double amp);
 
 /* Copy the current packed load vector to b ([ndof], host or device). */
 int sgiga_get_rhs(sgiga_plan_t plan, double* b);
@@ -211,6 +238,56 @@ int sgiga_geometry_coeffs(sgiga_plan_t plan, int g, double* G, double* mw);
  * matrices of direction `dir` at level `level`: U [n][n] row-major (column j
  * is eigenvector j), lam [n] ascending. Host outputs. */
 int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam);
+
+/* ---------------------------------------------------------------------------
+ * Learned correction of the preconditioner (not in the paper; its conclusions
+ * suggest using a fast approximation as a preconditioner, Sec. 5).
+ *
+ *   M(r) = z + s_z N([r / s_r, z / s_z]),  z = FD(r),  s_* = RMS of r, z per
+ *   component,
+ * N: three 3^d convolutions over each component's DoF tensor (zero padding),
+ * 2 -> 32 -> 32 -> 1 channels, ReLU after the first two; BF16 weights with an
+ * FP32 master copy, FP32 accumulation. Every function below needs a plan built
+ * with SGIGA_PREC_MIXED_FP32. A non-finite network output for a component
+ * falls back to z = FD(r) for that component.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int target_pairs;     /* component-level (residual, error) pairs to record (e.g. 10000) */
+    int max_iter_record;  /* CG iterations recorded per random right-hand side */
+    int epochs;           /* passes over the recorded samples */
+    float lr;             /* Adam learning rate */
+    unsigned seed;        /* right-hand sides and sample order */
+} sgiga_train_cfg;
+
+typedef struct {
+    int pairs, samples, rhs, steps;
+    double loss_first_epoch, loss_last_epoch;  /* mean relative squared error of N */
+    double seconds;
+} sgiga_train_stats;
+
+/* Allocate the network and initialise it (seeded Kaiming-uniform; the last
+ * layer scaled by 0.05 so that the untrained M is close to FD). */
+int sgiga_net_init(sgiga_plan_t plan, unsigned seed);
+/* Number of parameters (a negative status if there is no network). Layout of
+ * the FP32 vector: W1 [32][2][T], b1 [32], W2 [32][32][T], b2 [32], W3 [1][32][T],
+ * b3 [1], T = 3^d taps ordered offset_0 fastest over (-1, 0, 1)^d. */
+int sgiga_net_num_params(sgiga_plan_t plan);
+int sgiga_net_get_params(sgiga_plan_t plan, float* params /* host [nparams] */);
+int sgiga_net_set_params(sgiga_plan_t plan, const float* params /* host [nparams] */);
+/* N(in) with in = device float [2][ndof] (channel planes over the packed
+ * vector), out = device float [ndof]. */
+int sgiga_net_forward(sgiga_plan_t plan, const float* in, float* out);
+/* Gradient of sum_v dy_v N(in)_v with respect to every parameter (host
+ * [nparams]); in, dy device float. */
+int sgiga_net_backward(sgiga_plan_t plan, const float* in, const float* dy, float* grad);
+/* Record (residual, error) pairs from the plan's own FD-preconditioned FP64 CG
+ * on seeded random right-hand sides and train N by Adam on them. Overwrites the
+ * plan's load vector and solution. */
+int sgiga_train_net(sgiga_plan_t plan, const sgiga_train_cfg* cfg, sgiga_train_stats* stats /* may be NULL */);
+/* Checkpoint: magic "SGIGANET", version 1, taps, nparams, Adam step, then the
+ * FP32 parameters and both Adam moments. */
+int sgiga_net_save(sgiga_plan_t plan, const char* path);
+int sgiga_net_load(sgiga_plan_t plan, const char* path);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free preconditioner apply (the paper has no counterpart; this is

@@ -112,6 +112,58 @@ class QuarterAnnulus:
         return 0.75 * np.pi * (1.0 if self.d == 2 else 1.0)
 
 
+class BSplinePatch:
+    """Tensor-product B-spline patch F(xi) = sum_i P_i prod_k N_{i_k}(xi_k)
+    (eq. F-B-splines) with polynomial (weight 1) directions, evaluated with the
+    oracle's Cox-de Boor routine."""
+
+    def __init__(self, degrees, knots, cps):
+        self.d = len(degrees)
+        self.deg = list(degrees)
+        self.knots = [np.asarray(k, dtype=np.float64) for k in knots]
+        self.ncp = [len(k) - p - 1 for k, p in zip(self.knots, self.deg)]
+        self.cp = np.asarray(cps, dtype=np.float64).reshape(self.ncp[::-1] + [self.d])
+
+    def _basis(self, xi):
+        N = [spline.bspline_basis(self.knots[k], self.deg[k], xi[:, k]) for k in range(self.d)]
+        dN = [spline.bspline_deriv(self.knots[k], self.deg[k], xi[:, k]) for k in range(self.d)]
+        return N, dN
+
+    def map(self, xi):
+        xi = np.asarray(xi, dtype=np.float64)
+        N, _ = self._basis(xi)
+        if self.d == 3:
+            return np.einsum("pc,pb,pa,cbai->pi", N[2], N[1], N[0], self.cp, optimize=True)
+        return np.einsum("pb,pa,bai->pi", N[1], N[0], self.cp)
+
+    def jacobian(self, xi):
+        xi = np.asarray(xi, dtype=np.float64)
+        N, dN = self._basis(xi)
+        cols = []
+        for k in range(self.d):
+            f = [dN[j] if j == k else N[j] for j in range(self.d)]
+            if self.d == 3:
+                cols.append(np.einsum("pc,pb,pa,cbai->pi", f[2], f[1], f[0], self.cp, optimize=True))
+            else:
+                cols.append(np.einsum("pb,pa,bai->pi", f[1], f[0], self.cp))
+        return np.stack(cols, axis=2)
+
+    def weight_1d(self, k, t):
+        t = np.asarray(t, dtype=np.float64)
+        return np.ones_like(t), np.zeros_like(t)
+
+
+def lognormal_coefficient(omega, phase, amp):
+    """a(x) = exp(amp * sum_f cos(omega_f . x + phase_f)) (random Fourier features)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    phase = np.asarray(phase, dtype=np.float64)
+
+    def a(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.exp(amp * np.cos(x @ omega.T + phase[None, :]).sum(axis=1))
+    return a
+
+
 def make(name, d):
     if name in ("unit", "square", "cube"):
         return UnitCube(d)

@@ -19,9 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sgiga.h"
-#include "internal.h"
-#include "kernels.h"
+#include "plan.h"
 #include "op_common.cuh"
 
 namespace sgiga {
@@ -36,79 +34,11 @@ static thread_local std::string g_last_error = "";
 
 void sgiga::set_last_error(const char* msg) { g_last_error = msg; }
 
-static int fail(int code, const std::string& msg) {
+int fail(int code, const std::string& msg) {
     g_last_error = msg;
     return code;
 }
 
-#define CUDA_TRY(expr)                                                                   \
-    do {                                                                                 \
-        cudaError_t _e = (expr);                                                         \
-        if (_e != cudaSuccess) {                                                         \
-            return fail(SGIGA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
-        }                                                                                \
-    } while (0)
-
-struct sgiga_plan_s {
-    sgiga_config cfg;
-    int d, p, r, m, Q, ncomp;
-    cudaStream_t stream;
-    std::vector<GridDesc> grids;
-    std::vector<TileDesc> tiles;
-    std::vector<int> sched;
-    std::vector<Table1D> tabs;
-    std::map<std::pair<int, int>, int> tab_of;   // (dir, level) -> table
-    std::vector<int> eig_of_tab;
-    std::vector<Eig1D> eigs;
-    std::vector<Chunk> chunks;
-    std::vector<FDItem> fd[3];
-    std::vector<double> knots, bp;
-    Patch patch;
-    long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
-    int maxE = 1;
-    size_t smem = 0;
-    std::vector<void*> allocs;
-    DevPlan dp;
-    FDItem* d_fd[3] = {nullptr, nullptr, nullptr};
-    double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
-    double *d_t1 = nullptr, *d_t2 = nullptr, *d_partial = nullptr, *d_scal = nullptr, *d_coef = nullptr;
-    int* d_active = nullptr;
-    int* d_active_o = nullptr;  // outer (refinement) mask
-    int* d_iters_o = nullptr;
-    double* d_scal64o = nullptr;
-    float *f_b = nullptr, *f_x = nullptr, *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_q = nullptr;
-    float *f_t1 = nullptr, *f_t2 = nullptr;
-    double inner_tol = 1e-5;
-    int inner_max = 100;
-    int last_inner_iters = 0;
-    int* d_iters = nullptr;
-    int* d_nactive = nullptr;
-    int* h_nactive = nullptr;   // pinned
-    void* stage = nullptr;      // device staging for host pointers
-    size_t stage_bytes = 0;
-};
-
-template <typename T>
-static int dalloc(sgiga_plan_s* P, T** out, size_t count) {
-    void* ptr = nullptr;
-    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SGIGA_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-    }
-    P->allocs.push_back(ptr);
-    *out = (T*)ptr;
-    return SGIGA_OK;
-}
-
-template <typename T>
-static int upload(sgiga_plan_s* P, T** out, const std::vector<T>& v) {
-    int rc = dalloc(P, out, v.size());
-    if (rc) return rc;
-    if (!v.empty()) CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return SGIGA_OK;
-}
 
 // ---------------------------------------------------------------------------
 // 1D ingredients
@@ -155,6 +85,30 @@ static double grading(int kind, double gamma, double t) {
     }
     if (kind == SGIGA_GRADING_ONESIDED) return std::pow(t, gamma);
     return t;
+}
+
+static int make_user_patch(const sgiga_patch* up, int d, Patch& pt) {
+    std::memset(&pt, 0, sizeof(pt));
+    pt.d = d;
+    int tot = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (k >= d) { pt.deg[k] = 0; pt.nc[k] = 1; pt.nk[k] = 2; pt.knots[k][0] = 0; pt.knots[k][1] = 1;
+                      pt.w[k][0] = 1.0; continue; }
+        if (up->deg[k] < 1 || up->deg[k] > 3 || up->nknots[k] > 12 || up->ncp[k] > 8 || !up->knots[k] ||
+            up->nknots[k] != up->ncp[k] + up->deg[k] + 1)
+            return -1;
+        pt.deg[k] = up->deg[k];
+        pt.nk[k] = up->nknots[k];
+        pt.nc[k] = up->ncp[k];
+        for (int i = 0; i < pt.nk[k]; ++i) pt.knots[k][i] = up->knots[k][i];
+        for (int i = 0; i < pt.nc[k]; ++i) pt.w[k][i] = up->weights[k] ? up->weights[k][i] : 1.0;
+        pt.rational[k] = up->weights[k] ? 1 : 0;
+        tot *= pt.nc[k];
+    }
+    if (tot > 128 || !up->cp) return -1;
+    for (int i = 0; i < tot; ++i)
+        for (int k = 0; k < d; ++k) pt.cp[i][k] = up->cp[(size_t)i * d + k];
+    return 0;
 }
 
 static void make_patch(int domain, int d, Patch& pt) {
@@ -278,8 +232,10 @@ static void assemble_1d(int E, int Q, int p, int nf, const double* w, const doub
 
 static void free_plan(sgiga_plan_s* P) {
     if (!P) return;
+    free_net(P);
     for (void* a : P->allocs) cudaFree(a);
     if (P->stage) cudaFree(P->stage);
+    if (P->feat) cudaFree(P->feat);
     if (P->h_nactive) cudaFreeHost(P->h_nactive);
     delete P;
 }
@@ -439,7 +395,13 @@ static int build(sgiga_plan_s* P) {
         });
     }
     // device data
-    make_patch(c.domain, d, P->patch);
+    if (c.domain == SGIGA_DOMAIN_PATCH) {
+        if (!c.patch || make_user_patch(c.patch, d, P->patch) != 0)
+            return fail(SGIGA_ERR_ARG, "invalid patch (degree <= 3, <= 12 knots, <= 8 control points per direction, "
+                                       "<= 128 in total, nknots = ncp + deg + 1)");
+    } else {
+        make_patch(c.domain, d, P->patch);
+    }
     std::vector<double> gauss(2 * Q);
     gauss_legendre(Q, gauss.data(), gauss.data() + Q);
     DevPlan& D = P->dp;
@@ -591,166 +553,6 @@ static int build(sgiga_plan_s* P) {
 }
 
 // ---------------------------------------------------------------------------
-// helpers for host-or-device pointers
-// ---------------------------------------------------------------------------
-
-static bool is_device(const void* ptr) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-static int ensure_stage(sgiga_plan_s* P, size_t bytes) {
-    if (P->stage_bytes >= bytes) return SGIGA_OK;
-    if (P->stage) cudaFree(P->stage);
-    P->stage = nullptr;
-    P->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&P->stage, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SGIGA_ERR_NOMEM, "staging buffer allocation failed");
-    }
-    P->stage_bytes = bytes;
-    return SGIGA_OK;
-}
-
-static int run_rhs_operator(sgiga_plan_s* P) {
-    const DevPlan& D = P->dp;
-    CUDA_TRY(cudaMemsetAsync(P->d_b, 0, (size_t)P->ndof * 8, P->stream));
-    if (P->d == 3) CUDA_TRY(launch_op3(D, nullptr, P->d_b, nullptr, 1, P->stream));
-    else CUDA_TRY(launch_op2(D, nullptr, P->d_b, nullptr, 1, P->stream));
-    return SGIGA_OK;
-}
-
-static int apply_op(sgiga_plan_s* P, const double* x, double* y, const int* active) {
-    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 8, P->stream));
-    if (P->d == 3) CUDA_TRY(launch_op3(P->dp, x, y, active, 0, P->stream));
-    else CUDA_TRY(launch_op2(P->dp, x, y, active, 0, P->stream));
-    return SGIGA_OK;
-}
-
-static int apply_op(sgiga_plan_s* P, const float* x, float* y, const int* active) {
-    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 4, P->stream));
-    if (P->d == 3) CUDA_TRY(launch_op3_f32(P->dp, x, y, active, P->stream));
-    else CUDA_TRY(launch_op2_f32(P->dp, x, y, active, P->stream));
-    return SGIGA_OK;
-}
-
-// Work vectors of one precision.
-template <typename Real>
-struct Vecs {
-    Real *x, *r, *z, *p, *q, *t1, *t2;
-};
-
-static Vecs<double> vecs64(sgiga_plan_s* P) {
-    return Vecs<double>{P->d_x, P->d_r, P->d_z, P->d_p, P->d_q, P->d_t1, P->d_t2};
-}
-static Vecs<float> vecs32(sgiga_plan_s* P) {
-    return Vecs<float>{P->f_x, P->f_r, P->f_z, P->f_p, P->f_q, P->f_t1, P->f_t2};
-}
-
-template <typename Real>
-static int precond(sgiga_plan_s* P, const Real* r, Real* z, const int* active, Real* t1, Real* t2) {
-    const DevPlan& D = P->dp;
-    cudaStream_t s = P->stream;
-    if (P->cfg.precond == SGIGA_PRECOND_NONE) {
-        CUDA_TRY(launch_copy(z, r, P->ndof, s));
-        return SGIGA_OK;
-    }
-    const int d = P->d;
-    const Real* in = r;
-    Real* bufs[2] = {t1, t2};
-    int cur = 0;
-    const size_t bytes = (size_t)P->ndof * sizeof(Real);
-    for (int k = 0; k < d; ++k) {
-        Real* out = bufs[cur];
-        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
-        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
-        in = out;
-        cur ^= 1;
-    }
-    CUDA_TRY(launch_fd_scale<Real>(D, (Real*)in, active, s));
-    for (int k = 0; k < d; ++k) {
-        Real* out = (k == d - 1) ? z : bufs[cur];
-        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
-        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
-        in = out;
-        cur ^= 1;
-    }
-    return SGIGA_OK;
-}
-
-// Batched preconditioned CG on K_g x_g = rhs_g for the grids allowed by
-// `outer` (all when null), each with its own scalars, until
-// ||r_g|| <= tol ||rhs_g|| or max_iter iterations. Scalars: scal[0..6].
-// Returns the number of grids still active (or a negative status).
-template <typename Real>
-static int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int max_iter, const int* outer,
-               int* active, int* iters, double* scal, int* iters_run) {
-    const DevPlan& D = P->dp;
-    cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
-    double* bb = scal + 0 * ng;
-    double* rz = scal + 1 * ng;
-    double* pq = scal + 2 * ng;
-    double* rr = scal + 3 * ng;
-    double* alpha = scal + 4 * ng;
-    double* beta = scal + 5 * ng;
-    double* rznew = scal + 6 * ng;
-    CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
-    CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
-    int rc = precond<Real>(P, v.r, v.z, active, v.t1, v.t2);
-    if (rc) return rc;
-    CUDA_TRY(launch_copy<Real>(v.p, v.z, P->ndof, s));
-    CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rz, s));
-    int it = 0, nact = ng;
-    for (it = 0; it < max_iter; ++it) {
-        if ((rc = apply_op(P, v.p, v.q, active))) return rc;
-        CUDA_TRY(launch_dot<Real>(D, v.p, v.q, P->d_partial, pq, s));
-        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, active, s));
-        CUDA_TRY(launch_pcg_update_xr<Real>(D, v.x, v.r, v.p, v.q, alpha, active, P->d_partial, rr, s));
-        CUDA_TRY(launch_pcg_check(D, rr, bb, tol * tol, active, iters, P->d_nactive, s));
-        CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        nact = *P->h_nactive;
-        if (nact == 0) { ++it; break; }
-        if ((rc = precond<Real>(P, v.r, v.z, active, v.t1, v.t2))) return rc;
-        CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rznew, s));
-        CUDA_TRY(launch_pcg_beta(D, rz, rznew, nullptr, beta, s));
-        CUDA_TRY(launch_pcg_update_p<Real>(D, v.p, v.z, beta, active, s));
-    }
-    if (iters_run) *iters_run = it;
-    return nact;
-}
-
-static int solve_stats(sgiga_plan_s* P, const double* rr, const double* bb, const int* iters, int nact,
-                       sgiga_solve_stats* stats, std::chrono::steady_clock::time_point t0) {
-    if (!stats) return SGIGA_OK;
-    const int ng = (int)P->grids.size();
-    cudaStream_t s = P->stream;
-    std::vector<double> hrr(ng), hbb(ng);
-    std::vector<int> hit(ng);
-    CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hit.data(), iters, ng * 4, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    double mx = 0.0;
-    int mi = 0;
-    for (int g = 0; g < ng; ++g) {
-        if (hbb[g] > 0) mx = std::max(mx, std::sqrt(hrr[g] / hbb[g]));
-        mi = std::max(mi, hit[g]);
-    }
-    stats->iterations = mi;
-    stats->converged = ng - nact;
-    stats->max_rel_residual = mx;
-    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return SGIGA_OK;
-}
-
-// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -769,11 +571,14 @@ int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
     if (c.continuity > c.p - 1) return fail(SGIGA_ERR_ARG, "continuity must be <= p-1");
     if (c.min_level < 0) return fail(SGIGA_ERR_ARG, "min_level must be >= 0");
     if (c.w < c.d * c.min_level - c.d + 1) return fail(SGIGA_ERR_ARG, "w too small for min_level");
-    if (c.domain != SGIGA_DOMAIN_UNIT && c.domain != SGIGA_DOMAIN_ANNULUS) return fail(SGIGA_ERR_ARG, "unknown domain");
+    if (c.domain < SGIGA_DOMAIN_UNIT || c.domain > SGIGA_DOMAIN_PATCH) return fail(SGIGA_ERR_ARG, "unknown domain");
     if (c.grading < 0 || c.grading > 2 || (c.grading != 0 && !(c.gamma > 0))) return fail(SGIGA_ERR_ARG, "bad grading");
     if (c.precision != SGIGA_PREC_FP64 && c.precision != SGIGA_PREC_MIXED_FP32)
         return fail(SGIGA_ERR_ARG, "unsupported precision");
-    if (c.precond != SGIGA_PRECOND_FD && c.precond != SGIGA_PRECOND_NONE) return fail(SGIGA_ERR_ARG, "bad precond");
+    if (c.precond != SGIGA_PRECOND_FD && c.precond != SGIGA_PRECOND_NONE && c.precond != SGIGA_PRECOND_LEARNED)
+        return fail(SGIGA_ERR_ARG, "bad precond");
+    if (c.precond == SGIGA_PRECOND_LEARNED && c.precision != SGIGA_PREC_MIXED_FP32)
+        return fail(SGIGA_ERR_ARG, "the learned preconditioner runs inside the MIXED_FP32 inner solve");
     if (c.domain == SGIGA_DOMAIN_ANNULUS && c.p < 2) return fail(SGIGA_ERR_ARG, "annulus needs p >= 2 (exact circle)");
     sgiga_plan_s* P = new sgiga_plan_s();
     P->cfg = c;
@@ -874,6 +679,34 @@ int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
     return SGIGA_OK;
 }
 
+int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const double* phase, double amp) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (nfeat < 0 || (nfeat > 0 && (!omega || !phase))) return fail(SGIGA_ERR_ARG, "bad coefficient features");
+    cudaStream_t s = P->stream;
+    const int d = P->d;
+    if (P->feat) { cudaFree(P->feat); P->feat = nullptr; }
+    P->dp.feat = nullptr;
+    P->dp.nfeat = 0;
+    if (nfeat > 0) {
+        std::vector<double> f((size_t)nfeat * 4, 0.0);
+        for (int i = 0; i < nfeat; ++i) {
+            for (int k = 0; k < d; ++k) f[(size_t)i * 4 + k] = omega[(size_t)i * d + k];
+            f[(size_t)i * 4 + 3] = phase[i];
+        }
+        cudaError_t e = cudaMalloc(&P->feat, f.size() * 8);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(SGIGA_ERR_NOMEM, "feature table allocation failed"); }
+        CUDA_TRY(cudaMemcpy(P->feat, f.data(), f.size() * 8, cudaMemcpyHostToDevice));
+        P->dp.feat = P->feat;
+        P->dp.nfeat = nfeat;
+        P->dp.famp = amp;
+    }
+    CUDA_TRY(launch_geometry(P->dp, s));
+    if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
+        CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SGIGA_OK;
+}
+
 int sgiga_get_rhs(sgiga_plan_t P, double* b) {
     if (!P || !b) return fail(SGIGA_ERR_ARG, "null argument");
     CUDA_TRY(cudaMemcpyAsync(b, P->d_b, (size_t)P->ndof * 8, cudaMemcpyDefault, P->stream));
@@ -900,7 +733,7 @@ int sgiga_apply_f32(sgiga_plan_t P, const float* x, float* y) {
 
 int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
     if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
-    return precond<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
+    return precond_fd<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
 }
 
 int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats* stats) {
@@ -949,7 +782,10 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     P->last_inner_iters = inner_total;
     int rc = solve_stats(P, rr, bb, P->d_iters_o, nact, stats, t0);
     if (rc) return rc;
-    if (stats) stats->iterations = outer;
+    if (stats) {
+        stats->iterations = outer;
+        stats->inner_iterations = inner_total;
+    }
     if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
     return SGIGA_OK;
 }

@@ -100,14 +100,25 @@ __global__ void k_geometry(DevPlan P) {
         double x[3], J[3][3];
         patch_eval(pt, xi, x, J);
         double Gp[3][3];
-        double det = metric(d, J, wq, Gp);
+        double s = wq;
+        if (P.nfeat > 0) {   // diffusion coefficient a(x) = exp(amp * sum cos(omega . x + phase))
+            double f = 0.0;
+            for (int i = 0; i < P.nfeat; ++i) {
+                const double* ft = P.feat + 4 * i;
+                double arg = ft[3];
+                for (int k = 0; k < d; ++k) arg += ft[k] * x[k];
+                f += cos(arg);
+            }
+            s *= exp(P.famp * f);
+        }
+        double det = metric(d, J, s, Gp);
         if (!(det > 0.0)) atomicOr(&P.flags[0], 1);
         long long o = t.g_off + idx;
         int c = 0;
         for (int a = 0; a < d; ++a)
             for (int b = a; b < d; ++b) P.G[(long long)(c++) * P.nqp + o] = Gp[g.perm[a]][g.perm[b]];
         (void)ncomp;
-        P.mw[o] = wq * fabs(det);
+        P.mw[o] = wq * fabs(det);   // mass weight: no coefficient (load vector)
     }
 }
 

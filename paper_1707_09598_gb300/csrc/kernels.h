@@ -45,6 +45,9 @@ struct DevPlan {
     const double* lam;
     const double* dinv;      // [ndof] 1 / sum_k lambda_{k,i_k} of every packed entry
     int* flags;              // [0] = geometry error, [1] = eval error
+    const double* feat;      // diffusion features [nfeat][4] (omega, phase) or null
+    int nfeat;
+    double famp;
     size_t smem_op;          // dynamic shared bytes of the operator kernel
 };
 
@@ -99,6 +102,24 @@ cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const 
 cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
                                double* partial, double* rr, cudaStream_t s);
 cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);
+// net.cu (learned correction network)
+cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, const float* bias, const float* X,
+                        float* Y, int transpose, int relu, cudaStream_t s);
+cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, const float* dZ, float* dW, float* db,
+                         cudaStream_t s);
+cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s);
+cudaError_t launch_scale_grid(const DevPlan& P, float* x, const double* scale, int nch, int invert, cudaStream_t s);
+cudaError_t launch_net_combine(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
+                               float* out, const int* active, cudaStream_t s);
+cudaError_t launch_loss(const float* y, const float* t, long long n, double* acc, float* dy, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, const int* wmap, int n, float lr,
+                        float b1, float b2, float eps, int step, cudaStream_t s);
+cudaError_t launch_f2bf(const float* p, const int* wmap, void* wb, int n, cudaStream_t s);
+cudaError_t launch_rms(const DevPlan& P, const double* dots, double* rms, cudaStream_t s);
+cudaError_t launch_target(const DevPlan& P, const float* e, const float* z, const double* sz, float* t, cudaStream_t s);
+cudaError_t launch_pair_store(const DevPlan& P, const double* r, const double* xstar, const double* x, float* rd,
+                              float* ed, cudaStream_t s);
+
 // eval.cu
 cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts,
                         double* ucomp, cudaStream_t s);

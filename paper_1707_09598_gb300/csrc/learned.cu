@@ -1,0 +1,389 @@
+// Host side of the learned correction network: parameters, the learned
+// preconditioner used by flexible CG, training-data generation from the
+// solver's own CG iterates, the training loop (the library's forward,
+// backward and Adam kernels), checkpoints, and the C ABI entry points.
+//
+// Pairs. For a right-hand side b the FP64 FD-preconditioned CG is run twice:
+// once to convergence for x*, once more recording after every iteration k the
+// residual r_k and the error e_k = x* - x_k of every component. One recorded
+// iteration is one training sample (all components at once).
+//
+// Loss of a sample: sum_v (N_v - t_v)^2 / sum_v t_v^2 with the target
+// t = (e - FD(r)) / s_z, i.e. the part of the error that FD misses, in the
+// network's per-component scale.
+#include <cstdio>
+#include <random>
+
+#include "plan.h"
+
+namespace sgiga {
+
+struct Net {
+    int T = 0, np = 0, nw = 0;
+    long long N = 0;
+    long long oW[3], ob[3], obw[3];   // offsets of W_l and b_l in p; of W_l in the BF16 copy
+    int cin[3] = {2, 32, 32}, cout[3] = {32, 32, 1};
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    void* wb = nullptr;               // BF16 weights
+    int* wmap = nullptr;
+    int step = 0;
+    float *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *Y = nullptr, *dY = nullptr, *dA1 = nullptr, *dA2 = nullptr;
+    float *zfd = nullptr, *tgt = nullptr;
+    double *sr = nullptr, *sz = nullptr, *dots = nullptr, *lossacc = nullptr;
+    int* ok = nullptr;
+    float* data = nullptr;            // training pairs [S][2][N]
+    int nsamples = 0, capacity = 0;
+    std::vector<void*> allocs;
+};
+
+static int nalloc(sgiga_plan_s* P, Net* n, void** out, size_t bytes) {
+    cudaError_t e = cudaMalloc(out, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SGIGA_ERR_NOMEM, "network buffer allocation failed (" + std::to_string(bytes) + " bytes)");
+    }
+    n->allocs.push_back(*out);
+    (void)P;
+    return SGIGA_OK;
+}
+
+void free_net(sgiga_plan_s* P) {
+    if (!P || !P->net) return;
+    for (void* a : P->net->allocs) cudaFree(a);
+    delete P->net;
+    P->net = nullptr;
+    P->net_ready = false;
+}
+
+static int net_create(sgiga_plan_s* P) {
+    if (P->net) return SGIGA_OK;
+    Net* n = new Net();
+    P->net = n;
+    n->T = P->d == 3 ? 27 : 9;
+    n->N = P->ndof;
+    long long o = 0, ow = 0;
+    for (int l = 0; l < 3; ++l) {
+        n->oW[l] = o;
+        n->obw[l] = ow;
+        long long w = (long long)n->cout[l] * n->cin[l] * n->T;
+        o += w;
+        ow += w;
+        n->ob[l] = o;
+        o += n->cout[l];
+    }
+    n->np = (int)o;
+    n->nw = (int)ow;
+    const size_t N = (size_t)n->N, ng = P->grids.size();
+    int rc;
+    if ((rc = nalloc(P, n, (void**)&n->p, n->np * 4)) || (rc = nalloc(P, n, (void**)&n->g, n->np * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->m, n->np * 4)) || (rc = nalloc(P, n, (void**)&n->v, n->np * 4)) ||
+        (rc = nalloc(P, n, &n->wb, n->nw * 2)) || (rc = nalloc(P, n, (void**)&n->wmap, n->np * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->A0, 2 * N * 4)) || (rc = nalloc(P, n, (void**)&n->A1, 32 * N * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->A2, 32 * N * 4)) || (rc = nalloc(P, n, (void**)&n->Y, N * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->dY, N * 4)) || (rc = nalloc(P, n, (void**)&n->dA1, 32 * N * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->dA2, 32 * N * 4)) || (rc = nalloc(P, n, (void**)&n->zfd, N * 4)) ||
+        (rc = nalloc(P, n, (void**)&n->tgt, N * 4)) || (rc = nalloc(P, n, (void**)&n->sr, ng * 8)) ||
+        (rc = nalloc(P, n, (void**)&n->sz, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots, ng * 8)) ||
+        (rc = nalloc(P, n, (void**)&n->lossacc, 16)) || (rc = nalloc(P, n, (void**)&n->ok, ng * 4)))
+        return rc;
+    std::vector<int> wmap(n->np, -1);
+    for (int l = 0; l < 3; ++l) {
+        long long w = (long long)n->cout[l] * n->cin[l] * n->T;
+        for (long long i = 0; i < w; ++i) wmap[n->oW[l] + i] = (int)(n->obw[l] + i);
+    }
+    CUDA_TRY(cudaMemcpy(n->wmap, wmap.data(), wmap.size() * 4, cudaMemcpyHostToDevice));
+    return SGIGA_OK;
+}
+
+static int net_upload(sgiga_plan_s* P, const std::vector<float>& host) {
+    Net* n = P->net;
+    CUDA_TRY(cudaMemcpy(n->p, host.data(), n->np * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_f2bf(n->p, n->wmap, n->wb, n->np, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+static const void* wl(const Net* n, int l) { return (const char*)n->wb + n->obw[l] * 2; }
+
+// forward: A0 (2 channels) -> A1 -> A2 -> Y
+static int net_forward(sgiga_plan_s* P) {
+    Net* n = P->net;
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    CUDA_TRY(launch_conv(D, 2, 32, wl(n, 0), n->p + n->ob[0], n->A0, n->A1, 0, 1, s));
+    CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), n->p + n->ob[1], n->A1, n->A2, 0, 1, s));
+    CUDA_TRY(launch_conv(D, 32, 1, wl(n, 2), n->p + n->ob[2], n->A2, n->Y, 0, 0, s));
+    return SGIGA_OK;
+}
+
+// backward from dY: gradients of every parameter into g (cleared first)
+static int net_backward(sgiga_plan_s* P) {
+    Net* n = P->net;
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const long long N = n->N;
+    CUDA_TRY(cudaMemsetAsync(n->g, 0, n->np * 4, s));
+    CUDA_TRY(launch_wgrad(D, 32, 1, n->A2, n->dY, n->g + n->oW[2], n->g + n->ob[2], s));
+    CUDA_TRY(launch_conv(D, 1, 32, wl(n, 2), nullptr, n->dY, n->dA2, 1, 0, s));
+    CUDA_TRY(launch_relu_mask(n->dA2, n->A2, 32 * N, s));
+    CUDA_TRY(launch_wgrad(D, 32, 32, n->A1, n->dA2, n->g + n->oW[1], n->g + n->ob[1], s));
+    CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), nullptr, n->dA2, n->dA1, 1, 0, s));
+    CUDA_TRY(launch_relu_mask(n->dA1, n->A1, 32 * N, s));
+    CUDA_TRY(launch_wgrad(D, 2, 32, n->A0, n->dA1, n->g + n->oW[0], n->g + n->ob[0], s));
+    return SGIGA_OK;
+}
+
+// A0 = [r / s_r, z / s_z] with z = FD(r) (into n->zfd), s_* per component
+static int net_inputs(sgiga_plan_s* P, const float* r, const int* active) {
+    Net* n = P->net;
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const long long N = n->N;
+    int rc = precond_fd<float>(P, r, n->zfd, active, P->f_t1, P->f_t2);
+    if (rc) return rc;
+    CUDA_TRY(launch_dot<float>(D, r, r, P->d_partial, n->dots, s));
+    CUDA_TRY(launch_rms(D, n->dots, n->sr, s));
+    CUDA_TRY(launch_dot<float>(D, n->zfd, n->zfd, P->d_partial, n->dots, s));
+    CUDA_TRY(launch_rms(D, n->dots, n->sz, s));
+    CUDA_TRY(launch_copy<float>(n->A0, r, N, s));
+    CUDA_TRY(launch_copy<float>(n->A0 + N, n->zfd, N, s));
+    CUDA_TRY(launch_scale_grid(D, n->A0, n->sr, 1, 1, s));
+    CUDA_TRY(launch_scale_grid(D, n->A0 + N, n->sz, 1, 1, s));
+    return SGIGA_OK;
+}
+
+int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active) {
+    Net* n = P->net;
+    int rc = net_inputs(P, r, active);
+    if (rc) return rc;
+    if ((rc = net_forward(P))) return rc;
+    CUDA_TRY(launch_net_combine(P->dp, n->zfd, n->Y, n->sz, n->ok, z, active, P->stream));
+    return SGIGA_OK;
+}
+
+// Records (r_k, x* - x_k) of every CG iterate into the next dataset slot.
+struct RecordHook : PcgHook {
+    sgiga_plan_s* P;
+    const double* xstar;
+    int limit;
+    int after_iteration(int it) override {
+        (void)it;
+        Net* n = P->net;
+        if (n->nsamples >= n->capacity || it >= limit) return 0;
+        float* rd = n->data + (size_t)n->nsamples * 2 * n->N;
+        cudaError_t e = launch_pair_store(P->dp, P->d_r, xstar, P->d_x, rd, rd + n->N, P->stream);
+        if (e != cudaSuccess) return fail(SGIGA_ERR_CUDA, cudaGetErrorString(e));
+        n->nsamples++;
+        return 0;
+    }
+};
+
+}  // namespace sgiga
+
+using namespace sgiga;
+
+extern "C" {
+
+int sgiga_net_init(sgiga_plan_t P, unsigned seed) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32)
+        return fail(SGIGA_ERR_ARG, "the network needs a SGIGA_PREC_MIXED_FP32 plan (FP32 preconditioner data)");
+    int rc = net_create(P);
+    if (rc) return rc;
+    Net* n = P->net;
+    std::mt19937_64 rng(seed);
+    std::vector<float> h(n->np, 0.0f);
+    for (int l = 0; l < 3; ++l) {
+        // Kaiming-uniform for ReLU layers; the last layer starts small so that
+        // the untrained correction is close to zero (M close to FD)
+        const double fan = (double)n->cin[l] * n->T;
+        const double b = std::sqrt(6.0 / fan) * (l == 2 ? 0.05 : 1.0);
+        std::uniform_real_distribution<double> U(-b, b);
+        long long w = (long long)n->cout[l] * n->cin[l] * n->T;
+        for (long long i = 0; i < w; ++i) h[n->oW[l] + i] = (float)U(rng);
+    }
+    if ((rc = net_upload(P, h))) return rc;
+    CUDA_TRY(cudaMemset(n->m, 0, n->np * 4));
+    CUDA_TRY(cudaMemset(n->v, 0, n->np * 4));
+    n->step = 0;
+    P->net_ready = true;
+    return SGIGA_OK;
+}
+
+int sgiga_net_num_params(sgiga_plan_t P) {
+    if (!P || !P->net) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
+    return P->net->np;
+}
+
+int sgiga_net_get_params(sgiga_plan_t P, float* host) {
+    if (!P || !P->net || !host) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    CUDA_TRY(cudaMemcpy(host, P->net->p, P->net->np * 4, cudaMemcpyDeviceToHost));
+    return SGIGA_OK;
+}
+
+int sgiga_net_set_params(sgiga_plan_t P, const float* host) {
+    if (!P || !P->net || !host) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    std::vector<float> h(host, host + P->net->np);
+    return net_upload(P, h);
+}
+
+int sgiga_net_forward(sgiga_plan_t P, const float* in, float* out) {
+    if (!P || !P->net || !in || !out) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    Net* n = P->net;
+    CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
+    int rc = net_forward(P);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy<float>(out, n->Y, n->N, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_net_backward(sgiga_plan_t P, const float* in, const float* dy, float* grad_host) {
+    if (!P || !P->net || !in || !dy || !grad_host) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    Net* n = P->net;
+    CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
+    int rc = net_forward(P);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy<float>(n->dY, dy, n->N, P->stream));
+    if ((rc = net_backward(P))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(grad_host, n->g, n->np * 4, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stats* stats) {
+    if (!P || !cfg) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!P->net_ready) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
+    if (cfg->target_pairs < 1 || cfg->epochs < 1 || !(cfg->lr > 0)) return fail(SGIGA_ERR_ARG, "bad training config");
+    auto t0 = std::chrono::steady_clock::now();
+    Net* n = P->net;
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    const long long N = n->N;
+    // 1. data: samples of all components, ceil(target_pairs / ngrids) of them
+    const int S = (cfg->target_pairs + ng - 1) / ng;
+    if (n->capacity < S) {
+        if (n->data) { cudaFree(n->data); n->allocs.erase(std::find(n->allocs.begin(), n->allocs.end(), (void*)n->data)); }
+        n->data = nullptr;
+        int rc = nalloc(P, n, (void**)&n->data, (size_t)S * 2 * N * 4);
+        if (rc) return rc;
+        n->capacity = S;
+    }
+    n->nsamples = 0;
+    double* xstar = nullptr;
+    if (cudaMalloc(&xstar, (size_t)N * 8) != cudaSuccess) { cudaGetLastError(); return fail(SGIGA_ERR_NOMEM, "x* buffer"); }
+    std::vector<double> hb(N);
+    std::mt19937_64 rng(cfg->seed);
+    std::normal_distribution<double> gauss(0.0, 1.0);
+    const int per_rhs = std::max(1, cfg->max_iter_record);
+    int nrhs = 0;
+    int rc = SGIGA_OK;
+    const int saved_precond = P->cfg.precond;
+    P->cfg.precond = SGIGA_PRECOND_FD;    // data come from plain FD-preconditioned CG
+    while (n->nsamples < S && nrhs < 10000) {
+        for (long long i = 0; i < N; ++i) hb[i] = gauss(rng);
+        if (cudaMemcpy(P->d_b, hb.data(), N * 8, cudaMemcpyHostToDevice) != cudaSuccess) { rc = SGIGA_ERR_CUDA; break; }
+        int it = 0;
+        int nact = pcg<double>(P, P->d_b, vecs64(P), 1e-10, 500, nullptr, P->d_active, P->d_iters, P->d_scal, &it);
+        if (nact < 0) { rc = nact; break; }
+        if (cudaMemcpyAsync(xstar, P->d_x, N * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { rc = SGIGA_ERR_CUDA; break; }
+        RecordHook hook;
+        hook.P = P;
+        hook.xstar = xstar;
+        hook.limit = per_rhs;
+        nact = pcg<double>(P, P->d_b, vecs64(P), 1e-10, per_rhs, nullptr, P->d_active, P->d_iters, P->d_scal, &it,
+                           &hook);
+        if (nact < 0) { rc = nact; break; }
+        ++nrhs;
+    }
+    P->cfg.precond = saved_precond;
+    cudaFree(xstar);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(P->d_b, 0, N * 8, s));   // the load vector was overwritten
+    // 2. training
+    std::vector<int> order(n->nsamples);
+    for (int i = 0; i < n->nsamples; ++i) order[i] = i;
+    double first = 0.0, last = 0.0;
+    double hacc[2];
+    for (int ep = 0; ep < cfg->epochs; ++ep) {
+        std::shuffle(order.begin(), order.end(), rng);
+        double sum = 0.0;
+        for (int k = 0; k < n->nsamples; ++k) {
+            const float* r = n->data + (size_t)order[k] * 2 * N;
+            const float* e = r + N;
+            if ((rc = net_inputs(P, r, nullptr))) return rc;
+            CUDA_TRY(launch_target(D, e, n->zfd, n->sz, n->tgt, s));
+            if ((rc = net_forward(P))) return rc;
+            CUDA_TRY(launch_loss(n->Y, n->tgt, N, n->lossacc, n->dY, s));
+            if ((rc = net_backward(P))) return rc;
+            n->step++;
+            CUDA_TRY(launch_adam(n->p, n->g, n->m, n->v, n->wb, n->wmap, n->np, cfg->lr, 0.9f, 0.999f, 1e-8f,
+                                 n->step, s));
+            CUDA_TRY(cudaMemcpyAsync(hacc, n->lossacc, 16, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            sum += hacc[1] > 0 ? hacc[0] / hacc[1] : 0.0;
+        }
+        double mean = n->nsamples ? sum / n->nsamples : 0.0;
+        if (ep == 0) first = mean;
+        last = mean;
+    }
+    if (stats) {
+        stats->pairs = n->nsamples * ng;
+        stats->samples = n->nsamples;
+        stats->rhs = nrhs;
+        stats->steps = cfg->epochs * n->nsamples;
+        stats->loss_first_epoch = first;
+        stats->loss_last_epoch = last;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return SGIGA_OK;
+}
+
+// Checkpoint: "SGIGANET" | version 1 | taps | nparams | step | p | m | v (float32)
+int sgiga_net_save(sgiga_plan_t P, const char* path) {
+    if (!P || !P->net || !path) return fail(SGIGA_ERR_ARG, "no network or null path");
+    Net* n = P->net;
+    std::vector<float> p(n->np), m(n->np), v(n->np);
+    CUDA_TRY(cudaMemcpy(p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(m.data(), n->m, n->np * 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(v.data(), n->v, n->np * 4, cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(SGIGA_ERR_ARG, std::string("cannot open ") + path);
+    const char magic[8] = {'S', 'G', 'I', 'G', 'A', 'N', 'E', 'T'};
+    int hdr[4] = {1, n->T, n->np, n->step};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 4, f) == 4 &&
+              std::fwrite(p.data(), 4, n->np, f) == (size_t)n->np && std::fwrite(m.data(), 4, n->np, f) == (size_t)n->np &&
+              std::fwrite(v.data(), 4, n->np, f) == (size_t)n->np;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(SGIGA_ERR_ARG, std::string("write failed: ") + path);
+    return SGIGA_OK;
+}
+
+int sgiga_net_load(sgiga_plan_t P, const char* path) {
+    if (!P || !path) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32)
+        return fail(SGIGA_ERR_ARG, "the network needs a SGIGA_PREC_MIXED_FP32 plan");
+    int rc = net_create(P);
+    if (rc) return rc;
+    Net* n = P->net;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(SGIGA_ERR_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    int hdr[4];
+    std::vector<float> p(n->np), m(n->np), v(n->np);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "SGIGANET", 8) == 0 &&
+              std::fread(hdr, 4, 4, f) == 4 && hdr[0] == 1 && hdr[1] == n->T && hdr[2] == n->np &&
+              std::fread(p.data(), 4, n->np, f) == (size_t)n->np && std::fread(m.data(), 4, n->np, f) == (size_t)n->np &&
+              std::fread(v.data(), 4, n->np, f) == (size_t)n->np;
+    std::fclose(f);
+    if (!ok) return fail(SGIGA_ERR_ARG, std::string("not a compatible network checkpoint: ") + path);
+    if ((rc = net_upload(P, p))) return rc;
+    CUDA_TRY(cudaMemcpy(n->m, m.data(), n->np * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(n->v, v.data(), n->np * 4, cudaMemcpyHostToDevice));
+    n->step = hdr[3];
+    P->net_ready = true;
+    return SGIGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Internal plan object and helpers shared by the host translation units.
+#pragma once
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sgiga.h"
+#include "internal.h"
+#include "kernels.h"
+
+namespace sgiga {
+struct Net;   // learned correction network (learned.cu)
+}
+using namespace sgiga;
+
+// Records msg for sgiga_last_error() and returns code.
+int fail(int code, const std::string& msg);
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            return fail(SGIGA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+        }                                                                                \
+    } while (0)
+
+struct sgiga_plan_s {
+    sgiga_config cfg;
+    int d, p, r, m, Q, ncomp;
+    cudaStream_t stream;
+    std::vector<GridDesc> grids;
+    std::vector<TileDesc> tiles;
+    std::vector<int> sched;
+    std::vector<Table1D> tabs;
+    std::map<std::pair<int, int>, int> tab_of;   // (dir, level) -> table
+    std::vector<int> eig_of_tab;
+    std::vector<Eig1D> eigs;
+    std::vector<Chunk> chunks;
+    std::vector<FDItem> fd[3];
+    std::vector<double> knots, bp;
+    Patch patch;
+    long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
+    int maxE = 1;
+    size_t smem = 0;
+    std::vector<void*> allocs;
+    DevPlan dp;
+    FDItem* d_fd[3] = {nullptr, nullptr, nullptr};
+    double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
+    double *d_t1 = nullptr, *d_t2 = nullptr, *d_partial = nullptr, *d_scal = nullptr, *d_coef = nullptr;
+    int* d_active = nullptr;
+    int* d_active_o = nullptr;  // outer (refinement) mask
+    int* d_iters_o = nullptr;
+    double* d_scal64o = nullptr;
+    float *f_b = nullptr, *f_x = nullptr, *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_q = nullptr;
+    float *f_t1 = nullptr, *f_t2 = nullptr;
+    double inner_tol = 1e-5;
+    int inner_max = 100;
+    int last_inner_iters = 0;
+    int* d_iters = nullptr;
+    int* d_nactive = nullptr;
+    int* h_nactive = nullptr;   // pinned
+    void* stage = nullptr;      // device staging for host pointers
+    double* feat = nullptr;     // coefficient features [nfeat][omega_0..2, phase]
+    sgiga::Net* net = nullptr;  // learned correction network (allocated by sgiga_net_init)
+    bool net_ready = false;
+    size_t stage_bytes = 0;
+};
+
+template <typename T>
+inline int dalloc(sgiga_plan_s* P, T** out, size_t count) {
+    void* ptr = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SGIGA_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    P->allocs.push_back(ptr);
+    *out = (T*)ptr;
+    return SGIGA_OK;
+}
+
+template <typename T>
+inline int upload(sgiga_plan_s* P, T** out, const std::vector<T>& v) {
+    int rc = dalloc(P, out, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SGIGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// helpers for host-or-device pointers
+// ---------------------------------------------------------------------------
+
+inline bool is_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int ensure_stage(sgiga_plan_s* P, size_t bytes) {
+    if (P->stage_bytes >= bytes) return SGIGA_OK;
+    if (P->stage) cudaFree(P->stage);
+    P->stage = nullptr;
+    P->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&P->stage, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SGIGA_ERR_NOMEM, "staging buffer allocation failed");
+    }
+    P->stage_bytes = bytes;
+    return SGIGA_OK;
+}
+
+inline int run_rhs_operator(sgiga_plan_s* P) {
+    const DevPlan& D = P->dp;
+    CUDA_TRY(cudaMemsetAsync(P->d_b, 0, (size_t)P->ndof * 8, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3(D, nullptr, P->d_b, nullptr, 1, P->stream));
+    else CUDA_TRY(launch_op2(D, nullptr, P->d_b, nullptr, 1, P->stream));
+    return SGIGA_OK;
+}
+
+inline int apply_op(sgiga_plan_s* P, const double* x, double* y, const int* active) {
+    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 8, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3(P->dp, x, y, active, 0, P->stream));
+    else CUDA_TRY(launch_op2(P->dp, x, y, active, 0, P->stream));
+    return SGIGA_OK;
+}
+
+inline int apply_op(sgiga_plan_s* P, const float* x, float* y, const int* active) {
+    CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)P->ndof * 4, P->stream));
+    if (P->d == 3) CUDA_TRY(launch_op3_f32(P->dp, x, y, active, P->stream));
+    else CUDA_TRY(launch_op2_f32(P->dp, x, y, active, P->stream));
+    return SGIGA_OK;
+}
+
+// Work vectors of one precision.
+template <typename Real>
+struct Vecs {
+    Real *x, *r, *z, *p, *q, *t1, *t2;
+};
+
+inline Vecs<double> vecs64(sgiga_plan_s* P) {
+    return Vecs<double>{P->d_x, P->d_r, P->d_z, P->d_p, P->d_q, P->d_t1, P->d_t2};
+}
+inline Vecs<float> vecs32(sgiga_plan_s* P) {
+    return Vecs<float>{P->f_x, P->f_r, P->f_z, P->f_p, P->f_q, P->f_t1, P->f_t2};
+}
+
+template <typename Real>
+inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active, Real* t1, Real* t2) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    if (P->cfg.precond == SGIGA_PRECOND_NONE) {
+        CUDA_TRY(launch_copy(z, r, P->ndof, s));
+        return SGIGA_OK;
+    }
+    const int d = P->d;
+    const Real* in = r;
+    Real* bufs[2] = {t1, t2};
+    int cur = 0;
+    const size_t bytes = (size_t)P->ndof * sizeof(Real);
+    for (int k = 0; k < d; ++k) {
+        Real* out = bufs[cur];
+        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
+        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
+        in = out;
+        cur ^= 1;
+    }
+    CUDA_TRY(launch_fd_scale<Real>(D, (Real*)in, active, s));
+    for (int k = 0; k < d; ++k) {
+        Real* out = (k == d - 1) ? z : bufs[cur];
+        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
+        in = out;
+        cur ^= 1;
+    }
+    return SGIGA_OK;
+}
+
+// Batched preconditioned CG on K_g x_g = rhs_g for the grids allowed by
+// `outer` (all when null), each with its own scalars, until
+// ||r_g|| <= tol ||rhs_g|| or max_iter iterations. Scalars: scal[0..6].
+// Returns the number of grids still active (or a negative status).
+// Learned preconditioner (learned.cu): z = FD(r) + s_z N([r/s_r, FD(r)/s_z]), FP32.
+namespace sgiga {
+int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active);
+void free_net(sgiga_plan_s* P);
+}
+
+inline int precond_any(sgiga_plan_s* P, const double* r, double* z, const int* active, double* t1, double* t2) {
+    return precond_fd<double>(P, r, z, active, t1, t2);
+}
+inline int precond_any(sgiga_plan_s* P, const float* r, float* z, const int* active, float* t1, float* t2) {
+    if (P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready) return precond_learned(P, r, z, active);
+    return precond_fd<float>(P, r, z, active, t1, t2);
+}
+
+// Called after every iteration of pcg (with the iteration index) when given;
+// a nonzero return stops the solve with that status.
+struct PcgHook {
+    virtual int after_iteration(int it) = 0;
+    virtual ~PcgHook() {}
+};
+
+template <typename Real>
+inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int max_iter, const int* outer,
+               int* active, int* iters, double* scal, int* iters_run, PcgHook* hook = nullptr) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    double* bb = scal + 0 * ng;
+    double* rz = scal + 1 * ng;
+    double* pq = scal + 2 * ng;
+    double* rr = scal + 3 * ng;
+    double* alpha = scal + 4 * ng;
+    double* beta = scal + 5 * ng;
+    double* rznew = scal + 6 * ng;
+    CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
+    CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
+    // a learned (nonlinear) preconditioner needs the flexible (Polak-Ribiere) beta
+    const bool flexible = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready;
+    double* rzmid = scal + 7 * ng;
+    int rc = precond_any(P, v.r, v.z, active, v.t1, v.t2);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy<Real>(v.p, v.z, P->ndof, s));
+    CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rz, s));
+    int it = 0, nact = ng;
+    for (it = 0; it < max_iter; ++it) {
+        if ((rc = apply_op(P, v.p, v.q, active))) return rc;
+        CUDA_TRY(launch_dot<Real>(D, v.p, v.q, P->d_partial, pq, s));
+        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, active, s));
+        CUDA_TRY(launch_pcg_update_xr<Real>(D, v.x, v.r, v.p, v.q, alpha, active, P->d_partial, rr, s));
+        if (hook) {
+            int hr = hook->after_iteration(it);
+            if (hr) return hr;
+        }
+        CUDA_TRY(launch_pcg_check(D, rr, bb, tol * tol, active, iters, P->d_nactive, s));
+        CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        nact = *P->h_nactive;
+        if (nact == 0) { ++it; break; }
+        if (flexible) CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rzmid, s));
+        if ((rc = precond_any(P, v.r, v.z, active, v.t1, v.t2))) return rc;
+        CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rznew, s));
+        CUDA_TRY(launch_pcg_beta(D, rz, rznew, flexible ? rzmid : nullptr, beta, s));
+        CUDA_TRY(launch_pcg_update_p<Real>(D, v.p, v.z, beta, active, s));
+    }
+    if (iters_run) *iters_run = it;
+    return nact;
+}
+
+inline int solve_stats(sgiga_plan_s* P, const double* rr, const double* bb, const int* iters, int nact,
+                       sgiga_solve_stats* stats, std::chrono::steady_clock::time_point t0) {
+    if (!stats) return SGIGA_OK;
+    const int ng = (int)P->grids.size();
+    cudaStream_t s = P->stream;
+    std::vector<double> hrr(ng), hbb(ng);
+    std::vector<int> hit(ng);
+    CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hit.data(), iters, ng * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    double mx = 0.0;
+    int mi = 0;
+    for (int g = 0; g < ng; ++g) {
+        if (hbb[g] > 0) mx = std::max(mx, std::sqrt(hrr[g] / hbb[g]));
+        mi = std::max(mi, hit[g]);
+    }
+    stats->iterations = mi;
+    stats->converged = ng - nact;
+    stats->max_rel_residual = mx;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->inner_iterations = 0;
+    return SGIGA_OK;
+}
+

@@ -26,17 +26,23 @@ SGIGA_ERR_NOT_CONVERGED = -4
 SGIGA_ERR_TIMEOUT = -5
 SGIGA_ERR_GEOMETRY = -6
 
-DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1}
+DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1, "patch": 2}
 GRADING = {"uniform": 0, "radical": 1, "onesided": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
-PRECOND = {"fd": 0, "none": 1}
+PRECOND = {"fd": 0, "none": 1, "learned": 2}
 SOURCE = {"sine": 0, "poly": 1, "annulus": 2, "annulus_paper": 3, "one": 4}
+
+
+class sgiga_patch(ctypes.Structure):
+    _fields_ = [("deg", ctypes.c_int * 3), ("nknots", ctypes.c_int * 3), ("knots", ctypes.c_void_p * 3),
+                ("ncp", ctypes.c_int * 3), ("weights", ctypes.c_void_p * 3), ("cp", ctypes.c_void_p)]
 
 
 class sgiga_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("w", ctypes.c_int),
                 ("min_level", ctypes.c_int), ("domain", ctypes.c_int), ("grading", ctypes.c_int),
-                ("gamma", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("gamma", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
+                ("patch", ctypes.POINTER(sgiga_patch))]
 
 
 class sgiga_info(ctypes.Structure):
@@ -52,9 +58,20 @@ class sgiga_grid(ctypes.Structure):
                 ("ntiles", ctypes.c_int)]
 
 
+class sgiga_train_cfg(ctypes.Structure):
+    _fields_ = [("target_pairs", ctypes.c_int), ("max_iter_record", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint)]
+
+
+class sgiga_train_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("samples", ctypes.c_int), ("rhs", ctypes.c_int), ("steps", ctypes.c_int),
+                ("loss_first_epoch", ctypes.c_double), ("loss_last_epoch", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
 class sgiga_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("inner_iterations", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -70,6 +87,7 @@ _SIGS = {
     "sgiga_set_rhs": (_I, [_P, _P]),
     "sgiga_set_rhs_builtin": (_I, [_P, _I]),
     "sgiga_get_rhs": (_I, [_P, _P]),
+    "sgiga_set_coefficient": (_I, [_P, _I, _P, _P, _D]),
     "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
     "sgiga_apply_f32": (_I, [_P, _P, _P]),
@@ -83,6 +101,15 @@ _SIGS = {
     "sgiga_geometry_coeffs": (_I, [_P, _I, _P, _P]),
     "sgiga_fd_eigen": (_I, [_P, _I, _I, _P, _P]),
     "sgiga_fd_apply_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _P, _P]),
+    "sgiga_net_init": (_I, [_P, ctypes.c_uint]),
+    "sgiga_net_num_params": (_I, [_P]),
+    "sgiga_net_get_params": (_I, [_P, _P]),
+    "sgiga_net_set_params": (_I, [_P, _P]),
+    "sgiga_net_forward": (_I, [_P, _P, _P]),
+    "sgiga_net_backward": (_I, [_P, _P, _P, _P]),
+    "sgiga_train_net": (_I, [_P, ctypes.POINTER(sgiga_train_cfg), ctypes.POINTER(sgiga_train_stats)]),
+    "sgiga_net_save": (_I, [_P, ctypes.c_char_p]),
+    "sgiga_net_load": (_I, [_P, ctypes.c_char_p]),
     "sgiga_last_error": (ctypes.c_char_p, []),
     "sgiga_launch_count": (ctypes.c_longlong, []),
 }
@@ -129,9 +156,27 @@ def _ptr(buf, n=None, dtype=np.float64):
 # --- entry points (same names as the C ABI) ------------------------------------
 
 def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="uniform", gamma=1.0,
-               precision="fp64", precond="fd", stream=None):
+               precision="fp64", precond="fd", stream=None, patch=None):
+    """patch: (degrees [d], knots [d arrays], control points [n, d]) for domain "patch"."""
+    keep = []
+    pp = None
+    if patch is not None:
+        degs, knots, cps = patch
+        ps = sgiga_patch()
+        for k in range(d):
+            kn = np.ascontiguousarray(knots[k], dtype=np.float64)
+            keep.append(kn)
+            ps.deg[k] = int(degs[k])
+            ps.nknots[k] = len(kn)
+            ps.knots[k] = kn.ctypes.data
+            ps.ncp[k] = len(kn) - int(degs[k]) - 1
+            ps.weights[k] = None
+        cpa = np.ascontiguousarray(cps, dtype=np.float64)
+        keep.append(cpa)
+        ps.cp = cpa.ctypes.data
+        pp = ctypes.pointer(ps)
     cfg = sgiga_config(d, p, continuity, w, min_level, DOMAIN[domain], GRADING[grading], float(gamma),
-                       PREC[precision], PRECOND[precond])
+                       PREC[precision], PRECOND[precond], pp)
     h = _P()
     s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.sgiga_plan(ctypes.byref(cfg), s, ctypes.byref(h)))
@@ -170,6 +215,12 @@ def sgiga_set_rhs_builtin(plan, source):
 def sgiga_source_at_qp(plan, source, f):
     n = sgiga_plan_info(plan).nqp
     _check(_lib.sgiga_source_at_qp(plan, SOURCE[source] if isinstance(source, str) else int(source), _ptr(f, n)))
+
+
+def sgiga_set_coefficient(plan, omega, phase, amp):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ph = np.ascontiguousarray(phase, dtype=np.float64)
+    _check(_lib.sgiga_set_coefficient(plan, len(ph), om.ctypes.data, ph.ctypes.data, float(amp)))
 
 
 def sgiga_get_rhs(plan, b):
@@ -269,6 +320,64 @@ def sgiga_fd_apply_noalloc(n, U, lam, r, z, stream=None, check=True):
     if check:
         _check(rc)
     return rc
+
+
+def sgiga_net_init(plan, seed):
+    _check(_lib.sgiga_net_init(plan, int(seed)))
+
+
+def sgiga_net_num_params(plan):
+    n = _lib.sgiga_net_num_params(plan)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def sgiga_net_get_params(plan):
+    out = np.zeros(sgiga_net_num_params(plan), dtype=np.float32)
+    _check(_lib.sgiga_net_get_params(plan, out.ctypes.data))
+    return out
+
+
+def sgiga_net_set_params(plan, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != sgiga_net_num_params(plan):
+        raise ValueError("wrong parameter count")
+    _check(_lib.sgiga_net_set_params(plan, a.ctypes.data))
+
+
+def _f32dev(t, n):
+    if not (hasattr(t, "dtype") and str(t.dtype) == "torch.float32" and t.is_cuda and t.is_contiguous()
+            and t.numel() >= n):
+        raise TypeError("expected a contiguous CUDA float32 tensor of %d entries" % n)
+    return t.data_ptr()
+
+
+def sgiga_net_forward(plan, inp, out):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_net_forward(plan, _f32dev(inp, 2 * n), _f32dev(out, n)))
+
+
+def sgiga_net_backward(plan, inp, dy):
+    n = sgiga_plan_info(plan).ndof
+    g = np.zeros(sgiga_net_num_params(plan), dtype=np.float32)
+    _check(_lib.sgiga_net_backward(plan, _f32dev(inp, 2 * n), _f32dev(dy, n), g.ctypes.data))
+    return g
+
+
+def sgiga_train_net(plan, target_pairs=10000, max_iter_record=30, epochs=10, lr=1e-3, seed=100):
+    cfg = sgiga_train_cfg(int(target_pairs), int(max_iter_record), int(epochs), float(lr), int(seed))
+    st = sgiga_train_stats()
+    _check(_lib.sgiga_train_net(plan, ctypes.byref(cfg), ctypes.byref(st)))
+    return st
+
+
+def sgiga_net_save(plan, path):
+    _check(_lib.sgiga_net_save(plan, str(path).encode()))
+
+
+def sgiga_net_load(plan, path):
+    _check(_lib.sgiga_net_load(plan, str(path).encode()))
 
 
 def sgiga_launch_count():
