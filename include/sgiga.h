@@ -136,6 +136,8 @@ typedef struct {
     double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
     double seconds;          /* wall time of the call */
     int inner_iterations;    /* MIXED_FP32: inner CG iterations summed over refinement steps */
+    int fallback;            /* LEARNED: 1 if a refinement step without a tenfold residual
+                                reduction switched the rest of the solve to FD */
 } sgiga_solve_stats;
 
 /* Build a plan: index set and coefficients (Sec. 3), knot vectors and

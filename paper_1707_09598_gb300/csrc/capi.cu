@@ -762,13 +762,29 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     CUDA_TRY(launch_copy<double>(rr, bb, ng, s));
     CUDA_TRY(launch_pcg_start(D, bb, nullptr, P->d_active_o, P->d_iters_o, s));
     int nact = ng, outer = 0, inner_total = 0;
+    P->learned_off = false;
+    double prev_worst = 0.0;
+    std::vector<double> hrr(ng), hbb(ng);
     for (outer = 0; outer <= max_iter; ++outer) {
         // convergence of the FP64 residual (also counts outer steps per grid)
         CUDA_TRY(launch_pcg_check(D, rr, bb, rel_tol * rel_tol, P->d_active_o, P->d_iters_o, P->d_nactive, s));
         CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (P->cfg.precond == SGIGA_PRECOND_LEARNED) {
+            CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
+        }
         CUDA_TRY(cudaStreamSynchronize(s));
         nact = *P->h_nactive;
         if (nact == 0 || outer == max_iter) break;
+        if (P->cfg.precond == SGIGA_PRECOND_LEARNED) {
+            // fall back to FD for the rest of the solve when a refinement step
+            // with the learned preconditioner does not cut the worst residual by 10
+            double worst = 0.0;
+            for (int g = 0; g < ng; ++g)
+                if (hbb[g] > 0) worst = std::max(worst, std::sqrt(hrr[g] / hbb[g]));
+            if (outer > 0 && worst > 0.1 * prev_worst) P->learned_off = true;
+            prev_worst = worst;
+        }
         CUDA_TRY(launch_ir_down(D, P->d_r, P->f_b, P->d_active_o, s));
         int inner = 0;
         int rc = pcg<float>(P, P->f_b, vecs32(P), P->inner_tol, P->inner_max, P->d_active_o, P->d_active,
@@ -785,7 +801,9 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     if (stats) {
         stats->iterations = outer;
         stats->inner_iterations = inner_total;
+        stats->fallback = P->learned_off ? 1 : 0;
     }
+    P->learned_off = false;
     if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
     return SGIGA_OK;
 }

@@ -109,8 +109,10 @@ cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, co
                          cudaStream_t s);
 cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s);
 cudaError_t launch_scale_grid(const DevPlan& P, float* x, const double* scale, int nch, int invert, cudaStream_t s);
-cudaError_t launch_net_combine(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
-                               float* out, const int* active, cudaStream_t s);
+cudaError_t launch_net_candidate(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
+                                 float* cand, cudaStream_t s);
+cudaError_t launch_net_select(const DevPlan& P, const float* z, const float* cand, const int* ok, const double* rz,
+                              const double* rc, float* out, const int* active, cudaStream_t s);
 cudaError_t launch_loss(const float* y, const float* t, long long n, double* acc, float* dy, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, const int* wmap, int n, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);

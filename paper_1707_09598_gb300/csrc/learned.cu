@@ -29,7 +29,7 @@ struct Net {
     int step = 0;
     float *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *Y = nullptr, *dY = nullptr, *dA1 = nullptr, *dA2 = nullptr;
     float *zfd = nullptr, *tgt = nullptr;
-    double *sr = nullptr, *sz = nullptr, *dots = nullptr, *lossacc = nullptr;
+    double *sr = nullptr, *sz = nullptr, *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr;
     int* ok = nullptr;
     float* data = nullptr;            // training pairs [S][2][N]
     int nsamples = 0, capacity = 0;
@@ -83,7 +83,7 @@ static int net_create(sgiga_plan_s* P) {
         (rc = nalloc(P, n, (void**)&n->dY, N * 4)) || (rc = nalloc(P, n, (void**)&n->dA1, 32 * N * 4)) ||
         (rc = nalloc(P, n, (void**)&n->dA2, 32 * N * 4)) || (rc = nalloc(P, n, (void**)&n->zfd, N * 4)) ||
         (rc = nalloc(P, n, (void**)&n->tgt, N * 4)) || (rc = nalloc(P, n, (void**)&n->sr, ng * 8)) ||
-        (rc = nalloc(P, n, (void**)&n->sz, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots, ng * 8)) ||
+        (rc = nalloc(P, n, (void**)&n->sz, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots2, ng * 8)) ||
         (rc = nalloc(P, n, (void**)&n->lossacc, 16)) || (rc = nalloc(P, n, (void**)&n->ok, ng * 4)))
         return rc;
     std::vector<int> wmap(n->np, -1);
@@ -154,10 +154,16 @@ static int net_inputs(sgiga_plan_s* P, const float* r, const int* active) {
 
 int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active) {
     Net* n = P->net;
+    if (P->learned_off) return precond_fd<float>(P, r, z, active, P->f_t1, P->f_t2);
     int rc = net_inputs(P, r, active);
     if (rc) return rc;
     if ((rc = net_forward(P))) return rc;
-    CUDA_TRY(launch_net_combine(P->dp, n->zfd, n->Y, n->sz, n->ok, z, active, P->stream));
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    CUDA_TRY(launch_net_candidate(D, n->zfd, n->Y, n->sz, n->ok, n->tgt, s));
+    CUDA_TRY(launch_dot<float>(D, r, n->zfd, P->d_partial, n->dots, s));
+    CUDA_TRY(launch_dot<float>(D, r, n->tgt, P->d_partial, n->dots2, s));
+    CUDA_TRY(launch_net_select(D, n->zfd, n->tgt, n->ok, n->dots, n->dots2, z, active, s));
     return SGIGA_OK;
 }
 
@@ -284,6 +290,11 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     while (n->nsamples < S && nrhs < 10000) {
         for (long long i = 0; i < N; ++i) hb[i] = gauss(rng);
         if (cudaMemcpy(P->d_b, hb.data(), N * 8, cudaMemcpyHostToDevice) != cudaSuccess) { rc = SGIGA_ERR_CUDA; break; }
+        if (nrhs % 2 == 1) {
+            // smoother right-hand side: b = K FD(xi), xi random (the error FD(xi) is smooth)
+            if ((rc = precond_fd<double>(P, P->d_b, P->d_z, nullptr, P->d_t1, P->d_t2))) break;
+            if ((rc = apply_op(P, P->d_z, P->d_b, nullptr))) break;
+        }
         int it = 0;
         int nact = pcg<double>(P, P->d_b, vecs64(P), 1e-10, 500, nullptr, P->d_active, P->d_iters, P->d_scal, &it);
         if (nact < 0) { rc = nact; break; }

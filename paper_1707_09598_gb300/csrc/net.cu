@@ -179,17 +179,29 @@ __global__ void k_scale_grid(DevPlan P, float* __restrict__ x, const double* __r
         for (int i = threadIdx.x; i < c.len; i += blockDim.x) x[(long long)ch * N + c.start + i] *= f;
 }
 
-// out = z + s_z * y on active grids; a non-finite network output leaves z
-__global__ void k_net_combine(DevPlan P, const float* __restrict__ z, const float* __restrict__ y,
-                              const double* __restrict__ sz, const int* __restrict__ ok, float* __restrict__ out,
-                              const int* __restrict__ active) {
+// cand = z + s_z * y (all grids)
+__global__ void k_net_candidate(DevPlan P, const float* __restrict__ z, const float* __restrict__ y,
+                                const double* __restrict__ sz, float* __restrict__ cand) {
     const Chunk c = P.chunks[blockIdx.x];
-    if (active && !active[c.grid]) return;
     const float s = (float)sz[c.grid];
-    const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         long long k = c.start + i;
-        out[k] = use ? z[k] + s * y[k] : z[k];
+        cand[k] = z[k] + s * y[k];
+    }
+}
+
+// out = cand where the component's network output is finite and
+// r.cand >= r.z / 2 (the learned direction keeps the descent property of FD),
+// else z; active grids only
+__global__ void k_net_select(DevPlan P, const float* __restrict__ z, const float* __restrict__ cand,
+                             const int* __restrict__ ok, const double* __restrict__ rz, const double* __restrict__ rc,
+                             float* __restrict__ out, const int* __restrict__ active) {
+    const Chunk c = P.chunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    const bool use = ok[c.grid] != 0 && rc[c.grid] >= 0.5 * rz[c.grid];
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        long long k = c.start + i;
+        out[k] = use ? cand[k] : z[k];
     }
 }
 
@@ -312,8 +324,8 @@ cudaError_t launch_scale_grid(const DevPlan& P, float* x, const double* scale, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_combine(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
-                               float* out, const int* active, cudaStream_t s) {
+cudaError_t launch_net_candidate(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
+                                 float* cand, cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(ok, 0xff, sizeof(int) * P.ngrids, s);   // all ones = finite
     if (e != cudaSuccess) return e;
@@ -322,7 +334,15 @@ cudaError_t launch_net_combine(const DevPlan& P, const float* z, const float* y,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_net_combine<<<P.nchunks, 256, 0, s>>>(P, z, y, sz, ok, out, active);
+    k_net_candidate<<<P.nchunks, 256, 0, s>>>(P, z, y, sz, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_select(const DevPlan& P, const float* z, const float* cand, const int* ok, const double* rz,
+                              const double* rc, float* out, const int* active, cudaStream_t s) {
+    if (P.nchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_net_select<<<P.nchunks, 256, 0, s>>>(P, z, cand, ok, rz, rc, out, active);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ struct sgiga_plan_s {
     double* feat = nullptr;     // coefficient features [nfeat][omega_0..2, phase]
     sgiga::Net* net = nullptr;  // learned correction network (allocated by sgiga_net_init)
     bool net_ready = false;
+    bool learned_off = false;   // set for the rest of a solve after a refinement step without progress
     size_t stage_bytes = 0;
 };
 
@@ -280,6 +281,7 @@ inline int solve_stats(sgiga_plan_s* P, const double* rr, const double* bb, cons
     stats->max_rel_residual = mx;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     stats->inner_iterations = 0;
+    stats->fallback = 0;
     return SGIGA_OK;
 }
 

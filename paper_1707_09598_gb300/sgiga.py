@@ -71,7 +71,7 @@ class sgiga_train_stats(ctypes.Structure):
 
 class sgiga_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("inner_iterations", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("inner_iterations", ctypes.c_int), ("fallback", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
