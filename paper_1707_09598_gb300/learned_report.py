@@ -1,0 +1,108 @@
+"""Learned-preconditioner comparison on the perturbed-cube workload.
+
+3D Poisson -div(a grad u) = 1 on the unit cube mapped by a seeded cubic
+B-spline perturbation (amplitude 0.1) with a log-normal coefficient a
+(std 0.5, correlation length 0.2, random Fourier features), p = 3, level w
+(12 by default: 199 components). Solves the same problem four ways and prints
+one JSON line:
+
+  fp64_fd      plain FP64 FD-preconditioned CG, tolerance 1e-12 (reference)
+  mixed_fd     FP32 inner FD-CG inside FP64 refinement
+  mixed_learned  FP32 inner flexible CG with M = FD + trained correction
+  (training: target_pairs residual/error pairs from the plan's own CG)
+
+with wall time (CUDA events on the plan's stream), iterations, and the
+relative L2 of each solution's combined values (17^3 lattice) against the
+fp64_fd reference.
+
+  python -m paper_1707_09598_gb300.learned_report [--w 12] [--pairs 10000] [--epochs 6]
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1707_09598_gb300 import sgiga  # noqa: E402
+from paper_1707_09598_gb300.inputs import eval_points, lognormal_features, perturbed_cube_patch  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--w", type=int, default=12)
+    ap.add_argument("--pairs", type=int, default=10000)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--nfeat", type=int, default=128)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    a = ap.parse_args()
+    kn, cp = perturbed_cube_patch(1)
+    om, ph, amp = lognormal_features(2, nfeat=a.nfeat)
+    pts = torch.as_tensor(eval_points(3, 16), device="cuda")
+    stream = torch.cuda.Stream()
+    out = {"workload": "perturbed cube (amp 0.1, seed 1), log-normal a (std 0.5, ell 0.2, %d features, seed 2), "
+                       "f = 1, p = 3, w = %d" % (a.nfeat, a.w)}
+
+    def plan(precision, precond):
+        t0 = time.perf_counter()
+        P = sgiga.Plan(3, 3, a.w, domain="patch", patch=([3, 3, 3], kn, cp), precision=precision,
+                       precond=precond, stream=stream)
+        sgiga.sgiga_set_coefficient(P.handle, om, ph, amp)
+        sgiga.sgiga_set_rhs_builtin(P.handle, "one")
+        return P, time.perf_counter() - t0
+
+    def timed_solve(P, tol, maxit):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st, rc = sgiga.sgiga_solve(P.handle, tol, maxit, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return st, rc, e0.elapsed_time(e1)
+
+    def combined(P):
+        uc = torch.zeros(P.info.ngrids * len(pts), dtype=torch.float64, device="cuda")
+        sgiga.sgiga_eval(P.handle, pts, len(pts), uc)
+        u = torch.zeros(len(pts), dtype=torch.float64, device="cuda")
+        sgiga.sgiga_combine(P.handle, uc, len(pts), u)
+        return u.cpu().numpy()
+
+    P, ps = plan("fp64", "fd")
+    out["ngrids"], out["ndof"] = P.info.ngrids, P.info.ndof
+    timed_solve(P, 1e-12, 2000)               # warm-up
+    st, rc, ms = timed_solve(P, 1e-12, 2000)
+    ref = combined(P)
+    out["fp64_fd"] = {"ms": ms, "iterations": st.iterations, "rc": rc, "plan_s": ps}
+    st, rc, ms = timed_solve(P, a.tol, 2000)
+    out["fp64_fd_at_tol"] = {"ms": ms, "iterations": st.iterations, "rc": rc,
+                             "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
+    P.close()
+    P, ps = plan("mixed", "learned")
+    st, rc, ms = timed_solve(P, a.tol, 50)    # warm-up, also the learned path before training (= FD)
+    st, rc, ms = timed_solve(P, a.tol, 50)
+    out["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
+                       "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
+    sgiga.sgiga_net_init(P.handle, 11)
+    tr = sgiga.sgiga_train_net(P.handle, target_pairs=a.pairs, max_iter_record=30, epochs=a.epochs, lr=1e-3,
+                               seed=100)
+    out["training"] = {"pairs": tr.pairs, "samples": tr.samples, "rhs": tr.rhs, "steps": tr.steps,
+                       "loss_first_epoch": tr.loss_first_epoch, "loss_last_epoch": tr.loss_last_epoch,
+                       "seconds": tr.seconds}
+    sgiga.sgiga_set_rhs_builtin(P.handle, "one")
+    timed_solve(P, a.tol, 50)
+    st, rc, ms = timed_solve(P, a.tol, 50)
+    out["mixed_learned"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
+                            "fallback": st.fallback,
+                            "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
+    P.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
