@@ -250,6 +250,12 @@ def run_ours(args):
     t0 = time.perf_counter()
     P = sgiga.Plan(W["d"], W["p"], W["w"], domain=W["domain"], stream=stream)
     plan_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tune = sgiga.sgiga_autotune(P.handle, reps=3)
+    tune_s = time.perf_counter() - t0
+    tuning = {"seconds": tune_s, "best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
+                                          "apply_ms": tune.best_ms, "ntiles": tune.ntiles},
+              "candidates_ms": [round(tune.ms[i], 4) for i in range(tune.ncand)]}
     ndof, ng = P.info.ndof, P.info.ngrids
     pts_h = eval_points(W["d"], W["lattice"])
     npts = len(pts_h)
@@ -386,7 +392,7 @@ def run_ours(args):
                                     % (6 * 8 * P.info.nqp / 1e9)},
             "accuracy": {"rel_l2_vs_oracle": l2, "rel_l2_vs_oracle_e2e": l2_e2e,
                          "target": 1e-10, "iterations": max(iters)},
-            "phases_ms": phases, "plan_s": plan_s,
+            "phases_ms": phases, "plan_s": plan_s, "autotune": tuning,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": world * ndof / e2e_s, "unit": "DoF/s",

@@ -210,6 +210,31 @@ int sgiga_precond(sgiga_plan_t plan, const double* r, double* z);
 int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
                 sgiga_solve_stats* stats /* host, may be NULL */);
 
+/* Autotuner of the operator kernels' tiles. Re-plans the tiles of every
+ * component under each candidate policy (shared-memory budget per block, cap
+ * on quadrature points per tile; the shape within a policy comes from the
+ * planner's cost model), times `reps` stiffness applies on the plan's stream
+ * for each (CUDA events), and keeps the fastest; the geometry planes are
+ * recomputed in the chosen tile layout. Overwrites the plan's work vectors
+ * (not its load vector or solution). out (host, may be NULL) receives the
+ * per-candidate mean times. */
+typedef struct {
+    int ncand, best, ntiles;
+    double best_ms;
+    double ms[8];
+    int budget[8];    /* bytes of shared memory per block */
+    int qpcap[8];     /* quadrature points per tile at most */
+} sgiga_tune_result;
+int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
+
+/* Solver options. use_graph != 0 (default): each CG loop runs as one captured
+ * CUDA graph whose while-conditional node repeats the iteration body until the
+ * device-side convergence test stops it (no host round trip per iteration);
+ * 0: a host loop that reads the number of active components back every
+ * iteration. inner_tol / inner_max: tolerance and iteration limit of the FP32
+ * inner solve of SGIGA_PREC_MIXED_FP32 (defaults 1e-5, 100). */
+int sgiga_set_solver_options(sgiga_plan_t plan, int use_graph, double inner_tol, int inner_max);
+
 /* Packed solution coefficients (device [ndof]). */
 int sgiga_get_solution(sgiga_plan_t plan, double* u);
 /* Replace the plan's packed solution (device [ndof]); used to evaluate

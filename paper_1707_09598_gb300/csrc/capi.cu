@@ -161,7 +161,7 @@ static long long binom(int n, int k) {
 // Tile choice: power-of-two element extents per direction and the pencil
 // axis, minimising a per-quadrature-point cost model within the
 // shared-memory budget.
-static void choose_tile(int d, int P, int M, const int* E, size_t budget, int* Tphys, int* perm) {
+static void choose_tile(int d, int P, int M, const int* E, size_t budget, long long qpcap, int* Tphys, int* perm) {
     const int Q = P + 1, P1 = P + 1;
     double best = 1e300;
     int lim[3] = {1, 1, 1};
@@ -197,7 +197,7 @@ static void choose_tile(int d, int P, int M, const int* E, size_t budget, int* T
                         if (npen < 256) pen *= 1.0 + 0.25 * (256.0 / npen - 1.0);
                         cost = 2 * s1 + pen + 10.0 * La * Lb + 4 * 256;
                     }
-                    if (qp > 16384) continue;
+                    if (qp > qpcap) continue;
                     double c = cost / qp;
                     if (c < best - 1e-12) {
                         best = c;
@@ -233,11 +233,72 @@ static void assemble_1d(int E, int Q, int p, int nf, const double* w, const doub
 static void free_plan(sgiga_plan_s* P) {
     if (!P) return;
     free_net(P);
+    destroy_loop_graph(P->loop64);
+    destroy_loop_graph(P->loop32);
+    if (P->own_stream) cudaStreamDestroy(P->own_stream);
     for (void* a : P->allocs) cudaFree(a);
     if (P->stage) cudaFree(P->stage);
     if (P->feat) cudaFree(P->feat);
     if (P->h_nactive) cudaFreeHost(P->h_nactive);
     delete P;
+}
+
+// Dynamic shared-memory attribute of the operator kernels; it only grows, so
+// plans that coexist keep working.
+static int grant_op_smem(sgiga_plan_s* P) {
+    static size_t granted[2][SGIGA_MAXP + 1] = {{0}};
+    size_t& gr = granted[P->d - 2][P->p];
+    if (P->smem > gr) {
+        if (P->d == 3) CUDA_TRY(set_op3_smem(P->p, P->smem)); else CUDA_TRY(set_op2_smem(P->p, P->smem));
+        gr = P->smem;
+    }
+    return SGIGA_OK;
+}
+
+// Tile decomposition of every component under a shared-memory budget and a
+// cap on quadrature points per tile; launch order = largest tiles first (the
+// greedy longest-processing-time order of Sec. 4.1). Fills P->tiles, P->sched,
+// the grids' tile fields and P->smem (host side only).
+static void make_tiles(sgiga_plan_s* P, size_t budget, long long qpcap) {
+    const int d = P->d, p = P->p, M = P->m, Q = P->Q;
+    P->tiles.clear();
+    P->smem = 0;
+    long long tqp = 0;
+    for (size_t gi = 0; gi < P->grids.size(); ++gi) {
+        GridDesc& g = P->grids[gi];
+        choose_tile(d, p, M, g.E, budget, qpcap, g.T, g.perm);
+        int Tl[3] = {g.T[g.perm[0]], d > 1 ? g.T[g.perm[1]] : 1, d > 2 ? g.T[g.perm[2]] : 1};
+        P->smem = std::max(P->smem, (size_t)op_smem_doubles(d, p, M, Tl) * 8);
+        g.tile0 = (int)P->tiles.size();
+        g.tqp_off = tqp;
+        int nt[3] = {1, 1, 1};
+        for (int k = 0; k < d; ++k) nt[k] = g.E[k] / g.T[k];
+        long long tile_qp = 1;
+        for (int k = 0; k < d; ++k) tile_qp *= (long long)Q * g.T[k];
+        for (int z = 0; z < nt[2]; ++z)
+            for (int y = 0; y < nt[1]; ++y)
+                for (int x = 0; x < nt[0]; ++x) {
+                    TileDesc td{};
+                    td.grid = (int)gi;
+                    td.e0[0] = x * g.T[0];
+                    td.e0[1] = y * g.T[1];
+                    td.e0[2] = z * g.T[2];
+                    td.g_off = tqp;
+                    tqp += tile_qp;
+                    P->tiles.push_back(td);
+                }
+        g.ntiles = (int)P->tiles.size() - g.tile0;
+    }
+    P->sched.resize(P->tiles.size());
+    for (size_t i = 0; i < P->tiles.size(); ++i) P->sched[i] = (int)i;
+    std::vector<double> tcost(P->tiles.size());
+    for (size_t i = 0; i < P->tiles.size(); ++i) {
+        const GridDesc& g = P->grids[P->tiles[i].grid];
+        double qp = 1;
+        for (int k = 0; k < d; ++k) qp *= Q * g.T[k];
+        tcost[i] = qp;
+    }
+    std::stable_sort(P->sched.begin(), P->sched.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
 }
 
 static int build(sgiga_plan_s* P) {
@@ -291,8 +352,6 @@ static int build(sgiga_plan_s* P) {
             P->tabs.push_back(t);
         }
     // grids and tiles
-    const size_t budget = 110 * 1024;
-    long long tqp = 0;
     for (size_t gi = 0; gi < idx.size(); ++gi) {
         GridDesc g{};
         int s = 0;
@@ -317,28 +376,6 @@ static int build(sgiga_plan_s* P) {
         g.qp_off = P->nqp;
         P->ndof += g.ndof;
         P->nqp += g.nqp;
-        choose_tile(d, p, M, g.E, budget, g.T, g.perm);
-        int Tl[3] = {g.T[g.perm[0]], d > 1 ? g.T[g.perm[1]] : 1, d > 2 ? g.T[g.perm[2]] : 1};
-        P->smem = std::max(P->smem, (size_t)op_smem_doubles(d, p, M, Tl) * 8);
-        g.tile0 = (int)P->tiles.size();
-        g.tqp_off = tqp;
-        int nt[3] = {1, 1, 1};
-        for (int k = 0; k < d; ++k) nt[k] = g.E[k] / g.T[k];
-        long long tile_qp = 1;
-        for (int k = 0; k < d; ++k) tile_qp *= (long long)Q * g.T[k];
-        for (int z = 0; z < nt[2]; ++z)
-            for (int y = 0; y < nt[1]; ++y)
-                for (int x = 0; x < nt[0]; ++x) {
-                    TileDesc td{};
-                    td.grid = (int)gi;
-                    td.e0[0] = x * g.T[0];
-                    td.e0[1] = y * g.T[1];
-                    td.e0[2] = z * g.T[2];
-                    td.g_off = tqp;
-                    tqp += tile_qp;
-                    P->tiles.push_back(td);
-                }
-        g.ntiles = (int)P->tiles.size() - g.tile0;
         // chunks
         g.chunk0 = (int)P->chunks.size();
         for (long long o = 0; o < g.ndof; o += 4096) {
@@ -351,17 +388,7 @@ static int build(sgiga_plan_s* P) {
         g.nchunk = (int)P->chunks.size() - g.chunk0;
         P->grids.push_back(g);
     }
-    // launch order: tiles with the largest estimated cost first (greedy LPT)
-    P->sched.resize(P->tiles.size());
-    for (size_t i = 0; i < P->tiles.size(); ++i) P->sched[i] = (int)i;
-    std::vector<double> tcost(P->tiles.size());
-    for (size_t i = 0; i < P->tiles.size(); ++i) {
-        const GridDesc& g = P->grids[P->tiles[i].grid];
-        double qp = 1;
-        for (int k = 0; k < d; ++k) qp *= Q * g.T[k];
-        tcost[i] = qp;
-    }
-    std::stable_sort(P->sched.begin(), P->sched.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
+    make_tiles(P, 110 * 1024, 16384);
     // preconditioner work items per direction: the shape of each component's
     // mode product picks SMALL / ROWS / TILE; items with the longest
     // contractions first
@@ -425,6 +452,8 @@ static int build(sgiga_plan_s* P) {
     for (int k = 0; k < d; ++k)
         if ((rc = upload(P, &P->d_fd[k], P->fd[k]))) return rc;
     D.tiles = dt; D.sched = ds; D.tabs = dtab; D.chunks = dch; D.patch = dpatch;
+    P->d_tiles = dt;
+    P->d_sched = ds;
     D.knots = dkn; D.bp = dbp; D.gauss = dgauss;
     int* dfirst; int* dflags;
     if ((rc = dalloc(P, &D.xi, P->tab_entries)) || (rc = dalloc(P, &D.w, P->tab_entries)) ||
@@ -506,14 +535,7 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
     // operator kernel shared memory
-    {   // the attribute only grows, so plans that coexist keep working
-        static size_t granted[2][SGIGA_MAXP + 1] = {{0}};
-        size_t& gr = granted[d - 2][p];
-        if (P->smem > gr) {
-            if (d == 3) CUDA_TRY(set_op3_smem(p, P->smem)); else CUDA_TRY(set_op2_smem(p, P->smem));
-            gr = P->smem;
-        }
-    }
+    if ((rc = grant_op_smem(P))) return rc;
     // solver vectors and scalars
     const size_t nd = (size_t)P->ndof, ng = P->grids.size();
     if ((rc = dalloc(P, &P->d_b, nd)) || (rc = dalloc(P, &P->d_x, nd)) || (rc = dalloc(P, &P->d_r, nd)) ||
@@ -527,7 +549,9 @@ static int build(sgiga_plan_s* P) {
     if ((rc = upload(P, &P->d_coef, coef))) return rc;
     CUDA_TRY(cudaMemsetAsync(P->d_b, 0, nd * 8, s));
     CUDA_TRY(cudaMemsetAsync(P->d_x, 0, nd * 8, s));
-    CUDA_TRY(cudaMallocHost(&P->h_nactive, sizeof(int)));
+    CUDA_TRY(cudaMallocHost(&P->h_nactive, 2 * sizeof(int)));
+    if ((rc = dalloc(P, &P->d_counter, 1))) return rc;
+    if (!P->stream) CUDA_TRY(cudaStreamCreate(&P->own_stream));
     if (c.precision == SGIGA_PREC_MIXED_FP32) {
         // FP32 copies of the operator and preconditioner data, FP32 work vectors
         float *Gf, *Rf, *dRf, *Uf, *Utf, *dinvf;
@@ -548,6 +572,39 @@ static int build(sgiga_plan_s* P) {
         CUDA_TRY(launch_narrow(dinvf, D.dinv, (long long)nd, s));
         D.Gf = Gf; D.Rf = Rf; D.dRf = dRf; D.Uf = Uf; D.Utf = Utf; D.dinvf = dinvf;
     }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SGIGA_OK;
+}
+
+// Re-plan the tiles (autotuner): new tile arrays, grids, shared-memory
+// attribute, and the tile-major geometry planes recomputed in the new layout.
+static int retile(sgiga_plan_s* P, size_t budget, long long qpcap) {
+    cudaStream_t s = P->stream;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    make_tiles(P, budget, qpcap);
+    for (void* old : {(void*)P->d_tiles, (void*)P->d_sched}) {
+        auto it = std::find(P->allocs.begin(), P->allocs.end(), old);
+        if (it != P->allocs.end()) P->allocs.erase(it);
+        cudaFree(old);
+    }
+    TileDesc* dt;
+    int* ds;
+    int rc;
+    if ((rc = upload(P, &dt, P->tiles)) || (rc = upload(P, &ds, P->sched))) return rc;
+    P->d_tiles = dt;
+    P->d_sched = ds;
+    DevPlan& D = P->dp;
+    D.tiles = dt;
+    D.sched = ds;
+    D.ntiles = (int)P->tiles.size();
+    D.smem_op = P->smem;
+    CUDA_TRY(cudaMemcpy((void*)D.grids, P->grids.data(), P->grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice));
+    if ((rc = grant_op_smem(P))) return rc;
+    CUDA_TRY(launch_geometry(D, s));
+    if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
+        CUDA_TRY(launch_narrow(D.Gf, D.G, (long long)P->ncomp * P->nqp, s));
+    destroy_loop_graph(P->loop64);
+    destroy_loop_graph(P->loop32);
     CUDA_TRY(cudaStreamSynchronize(s));
     return SGIGA_OK;
 }
@@ -598,6 +655,7 @@ int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
 void sgiga_destroy(sgiga_plan_t plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);
+    if (plan->own_stream) cudaStreamSynchronize(plan->own_stream);
     free_plan(plan);
 }
 
@@ -734,6 +792,56 @@ int sgiga_apply_f32(sgiga_plan_t P, const float* x, float* y) {
 int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
     if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
     return precond_fd<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
+}
+
+int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
+    if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
+    struct Cand { size_t budget; long long qpcap; };
+    const Cand cands[] = {{48 * 1024, 4096}, {48 * 1024, 16384}, {110 * 1024, 8192},
+                          {110 * 1024, 16384}, {200 * 1024, 16384}, {200 * 1024, 32768}};
+    const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
+    cudaStream_t s = P->stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    // probe vector: the plan's direction vector p (overwritten), output q
+    CUDA_TRY(cudaMemsetAsync(P->d_p, 0, (size_t)P->ndof * 8, s));
+    double best = 1e30;
+    int bi = 3;
+    int rc = SGIGA_OK;
+    for (int i = 0; i < nc && rc == SGIGA_OK; ++i) {
+        if ((rc = retile(P, cands[i].budget, cands[i].qpcap))) break;
+        if ((rc = apply_op(P, P->d_b, P->d_q, nullptr))) break;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_op(P, P->d_b, P->d_q, nullptr);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double per = ms / reps;
+        if (out && i < 8) { out->ms[i] = per; out->budget[i] = (int)cands[i].budget; out->qpcap[i] = (int)cands[i].qpcap; }
+        if (per < best) { best = per; bi = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = retile(P, cands[bi].budget, cands[bi].qpcap))) return rc;
+    if (out) {
+        out->ncand = nc;
+        out->best = bi;
+        out->best_ms = best;
+        out->ntiles = (int)P->tiles.size();
+    }
+    return SGIGA_OK;
+}
+
+int sgiga_set_solver_options(sgiga_plan_t P, int use_graph, double inner_tol, int inner_max) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!(inner_tol > 0) || inner_max < 1) return fail(SGIGA_ERR_ARG, "inner_tol must be > 0 and inner_max >= 1");
+    P->use_graph = use_graph != 0;
+    P->inner_tol = inner_tol;
+    P->inner_max = inner_max;
+    return SGIGA_OK;
 }
 
 int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats* stats) {

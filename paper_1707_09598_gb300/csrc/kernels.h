@@ -97,6 +97,8 @@ cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* b
                              int* iters, int* nactive, cudaStream_t s);
 cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, const int* outer, int* active, int* iters,
                              cudaStream_t s);
+cudaError_t launch_loop_cond(int* counter, const int* nactive, int max_iter, cudaGraphConditionalHandle h,
+                             cudaStream_t s);
 cudaError_t launch_ir_down(const DevPlan& P, const double* r64, float* r32, const int* active, cudaStream_t s);
 cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const int* active, cudaStream_t s);
 cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,

@@ -69,6 +69,21 @@ struct sgiga_plan_s {
     sgiga::Net* net = nullptr;  // learned correction network (allocated by sgiga_net_init)
     bool net_ready = false;
     bool learned_off = false;   // set for the rest of a solve after a refinement step without progress
+    bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
+    cudaStream_t own_stream = nullptr;   // capture/launch stream when the plan's stream is the legacy one
+    int* d_counter = nullptr;            // iteration counter of the captured loop
+    TileDesc* d_tiles = nullptr;         // current tile arrays (replaced by the autotuner)
+    int* d_sched = nullptr;
+    struct LoopGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        double tol = -1.0;
+        int max_iter = -1;
+        const void* rhs = nullptr;
+        const int* outer = nullptr;
+        bool flexible = false;
+        bool failed = false;
+    } loop64, loop32;
     size_t stage_bytes = 0;
 };
 
@@ -205,6 +220,108 @@ inline int precond_any(sgiga_plan_s* P, const float* r, float* z, const int* act
     return precond_fd<float>(P, r, z, active, t1, t2);
 }
 
+
+inline void destroy_loop_graph(sgiga_plan_s::LoopGraph& L) {
+    if (L.exec) cudaGraphExecDestroy(L.exec);
+    if (L.graph) cudaGraphDestroy(L.graph);
+    L.exec = nullptr;
+    L.graph = nullptr;
+}
+
+// One CG iteration after the initialisation, in two parts (shared by the host
+// loop and the captured graph body). A: q = K p, alpha, x/r update,
+// convergence check; B: z = M r, beta, p update.
+template <typename Real>
+inline int pcg_body_a(sgiga_plan_s* P, Vecs<Real> v, double tol, int* active, int* iters, double* scal) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    double* bb = scal + 0 * ng;
+    double* rz = scal + 1 * ng;
+    double* pq = scal + 2 * ng;
+    double* rr = scal + 3 * ng;
+    double* alpha = scal + 4 * ng;
+    int rc;
+    if ((rc = apply_op(P, v.p, v.q, active))) return rc;
+    CUDA_TRY(launch_dot<Real>(D, v.p, v.q, P->d_partial, pq, s));
+    CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, active, s));
+    CUDA_TRY(launch_pcg_update_xr<Real>(D, v.x, v.r, v.p, v.q, alpha, active, P->d_partial, rr, s));
+    CUDA_TRY(launch_pcg_check(D, rr, bb, tol * tol, active, iters, P->d_nactive, s));
+    return SGIGA_OK;
+}
+
+template <typename Real>
+inline int pcg_body_b(sgiga_plan_s* P, Vecs<Real> v, int* active, double* scal, bool flexible) {
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    const int ng = (int)P->grids.size();
+    double* rz = scal + 1 * ng;
+    double* beta = scal + 5 * ng;
+    double* rznew = scal + 6 * ng;
+    double* rzmid = scal + 7 * ng;
+    int rc;
+    if (flexible) CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rzmid, s));
+    if ((rc = precond_any(P, v.r, v.z, active, v.t1, v.t2))) return rc;
+    CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rznew, s));
+    CUDA_TRY(launch_pcg_beta(D, rz, rznew, flexible ? rzmid : nullptr, beta, s));
+    CUDA_TRY(launch_pcg_update_p<Real>(D, v.p, v.z, beta, active, s));
+    return SGIGA_OK;
+}
+
+// The CG loop as one graph: a while-conditional node whose body is one
+// iteration and whose condition the last kernel of the body sets on the device.
+// Built on first use and reused while (tol, max_iter, buffers) stay the same.
+template <typename Real>
+inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real> v, const void* rhs, double tol,
+                          int max_iter, const int* outer, int* active, int* iters, double* scal, bool flexible) {
+    cudaStream_t ls = P->stream ? P->stream : P->own_stream;
+    const bool same = L.exec && L.tol == tol && L.max_iter == max_iter && L.rhs == rhs && L.outer == outer &&
+                      L.flexible == flexible;
+    if (!same) {
+        destroy_loop_graph(L);
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaGraphCreate(&g, 0));
+        L.graph = g;
+        cudaGraphConditionalHandle h;
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaStream_t saved = P->stream;
+        P->stream = ls;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(ls, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        int rc = SGIGA_OK;
+        if (e == cudaSuccess) {
+            rc = pcg_body_a<Real>(P, v, tol, active, iters, scal);
+            if (rc == SGIGA_OK) rc = pcg_body_b<Real>(P, v, active, scal, flexible);
+            if (rc == SGIGA_OK) {
+                cudaError_t e2 = launch_loop_cond(P->d_counter, P->d_nactive, max_iter, h, ls);
+                if (e2 != cudaSuccess) rc = fail(SGIGA_ERR_CUDA, cudaGetErrorString(e2));
+            }
+            cudaGraph_t out = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(ls, &out);
+            if (rc == SGIGA_OK && e3 != cudaSuccess) rc = fail(SGIGA_ERR_CUDA, cudaGetErrorString(e3));
+        } else {
+            rc = fail(SGIGA_ERR_CUDA, cudaGetErrorString(e));
+        }
+        P->stream = saved;
+        if (rc) { cudaGetLastError(); destroy_loop_graph(L); return rc; }
+        CUDA_TRY(cudaGraphInstantiate(&L.exec, g, 0));
+        L.tol = tol;
+        L.max_iter = max_iter;
+        L.rhs = rhs;
+        L.outer = outer;
+        L.flexible = flexible;
+    }
+    CUDA_TRY(cudaGraphLaunch(L.exec, ls));
+    return SGIGA_OK;
+}
+
 // Called after every iteration of pcg (with the iteration index) when given;
 // a nonzero return stops the solve with that status.
 struct PcgHook {
@@ -220,40 +337,49 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     const int ng = (int)P->grids.size();
     double* bb = scal + 0 * ng;
     double* rz = scal + 1 * ng;
-    double* pq = scal + 2 * ng;
-    double* rr = scal + 3 * ng;
-    double* alpha = scal + 4 * ng;
-    double* beta = scal + 5 * ng;
-    double* rznew = scal + 6 * ng;
-    CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
-    CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
     // a learned (nonlinear) preconditioner needs the flexible (Polak-Ribiere) beta
     const bool flexible = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready;
-    double* rzmid = scal + 7 * ng;
-    int rc = precond_any(P, v.r, v.z, active, v.t1, v.t2);
+    auto init = [&]() -> int {
+        CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
+        CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
+        int rc = precond_any(P, v.r, v.z, active, v.t1, v.t2);
+        if (rc) return rc;
+        CUDA_TRY(launch_copy<Real>(v.p, v.z, P->ndof, s));
+        CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rz, s));
+        return SGIGA_OK;
+    };
+    int rc = init();
     if (rc) return rc;
-    CUDA_TRY(launch_copy<Real>(v.p, v.z, P->ndof, s));
-    CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rz, s));
+    sgiga_plan_s::LoopGraph& L = sizeof(Real) == 8 ? P->loop64 : P->loop32;
+    if (P->use_graph && !hook && !flexible && !L.failed) {
+        // whole loop on the device: one graph launch, no host round trip per iteration
+        CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
+        rc = pcg_graph_loop<Real>(P, L, v, rhs, tol, max_iter, outer, active, iters, scal, flexible);
+        if (rc == SGIGA_OK) {
+            CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_counter, sizeof(int), cudaMemcpyDeviceToHost,
+                                     P->stream ? P->stream : P->own_stream));
+            CUDA_TRY(cudaMemcpyAsync(P->h_nactive + 1, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost,
+                                     P->stream ? P->stream : P->own_stream));
+            CUDA_TRY(cudaStreamSynchronize(P->stream ? P->stream : P->own_stream));
+            if (iters_run) *iters_run = P->h_nactive[0];
+            return P->h_nactive[1];
+        }
+        L.failed = true;   // this device/driver cannot run the captured loop: host loop from now on
+        cudaGetLastError();
+        if ((rc = init())) return rc;
+    }
     int it = 0, nact = ng;
     for (it = 0; it < max_iter; ++it) {
-        if ((rc = apply_op(P, v.p, v.q, active))) return rc;
-        CUDA_TRY(launch_dot<Real>(D, v.p, v.q, P->d_partial, pq, s));
-        CUDA_TRY(launch_pcg_alpha(D, rz, pq, alpha, active, s));
-        CUDA_TRY(launch_pcg_update_xr<Real>(D, v.x, v.r, v.p, v.q, alpha, active, P->d_partial, rr, s));
+        if ((rc = pcg_body_a<Real>(P, v, tol, active, iters, scal))) return rc;
         if (hook) {
             int hr = hook->after_iteration(it);
             if (hr) return hr;
         }
-        CUDA_TRY(launch_pcg_check(D, rr, bb, tol * tol, active, iters, P->d_nactive, s));
         CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         nact = *P->h_nactive;
         if (nact == 0) { ++it; break; }
-        if (flexible) CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rzmid, s));
-        if ((rc = precond_any(P, v.r, v.z, active, v.t1, v.t2))) return rc;
-        CUDA_TRY(launch_dot<Real>(D, v.r, v.z, P->d_partial, rznew, s));
-        CUDA_TRY(launch_pcg_beta(D, rz, rznew, flexible ? rzmid : nullptr, beta, s));
-        CUDA_TRY(launch_pcg_update_p<Real>(D, v.p, v.z, beta, active, s));
+        if ((rc = pcg_body_b<Real>(P, v, active, scal, flexible))) return rc;
     }
     if (iters_run) *iters_run = it;
     return nact;

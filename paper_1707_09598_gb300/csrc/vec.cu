@@ -242,6 +242,23 @@ cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, const int* oute
     return cudaGetLastError();
 }
 
+// End of one iteration of a graph-captured CG loop: counts the iteration and
+// keeps the loop's while-condition set while some grid is active and the
+// iteration limit is not reached.
+__global__ void k_loop_cond(int* __restrict__ counter, const int* __restrict__ nactive, int max_iter,
+                            cudaGraphConditionalHandle h) {
+    int it = *counter + 1;
+    *counter = it;
+    cudaGraphSetConditional(h, (*nactive > 0 && it < max_iter) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(int* counter, const int* nactive, int max_iter, cudaGraphConditionalHandle h,
+                             cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_loop_cond<<<1, 1, 0, s>>>(counter, nactive, max_iter, h);
+    return cudaGetLastError();
+}
+
 // Iterative refinement helpers (FP64 outer loop around an FP32 inner solve).
 // r32 = (float) r64 on active grids, 0 elsewhere
 __global__ void k_ir_down(const Chunk* __restrict__ chunks, const double* __restrict__ r64, float* __restrict__ r32,

@@ -69,6 +69,11 @@ class sgiga_train_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class sgiga_tune_result(ctypes.Structure):
+    _fields_ = [("ncand", ctypes.c_int), ("best", ctypes.c_int), ("ntiles", ctypes.c_int), ("best_ms", ctypes.c_double),
+                ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8)]
+
+
 class sgiga_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("max_rel_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("inner_iterations", ctypes.c_int), ("fallback", ctypes.c_int)]
@@ -93,6 +98,8 @@ _SIGS = {
     "sgiga_apply_f32": (_I, [_P, _P, _P]),
     "sgiga_precond": (_I, [_P, _P, _P]),
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
+    "sgiga_set_solver_options": (_I, [_P, _I, _D, _I]),
+    "sgiga_autotune": (_I, [_P, _I, ctypes.POINTER(sgiga_tune_result)]),
     "sgiga_get_solution": (_I, [_P, _P]),
     "sgiga_set_solution": (_I, [_P, _P]),
     "sgiga_eval": (_I, [_P, _P, _L, _P]),
@@ -244,6 +251,16 @@ def sgiga_apply_f32(plan, x, y):
 def sgiga_precond(plan, r, z):
     n = sgiga_plan_info(plan).ndof
     _check(_lib.sgiga_precond(plan, _ptr(r, n), _ptr(z, n)))
+
+
+def sgiga_autotune(plan, reps=3):
+    out = sgiga_tune_result()
+    _check(_lib.sgiga_autotune(plan, int(reps), ctypes.byref(out)))
+    return out
+
+
+def sgiga_set_solver_options(plan, use_graph=True, inner_tol=1e-5, inner_max=100):
+    _check(_lib.sgiga_set_solver_options(plan, int(bool(use_graph)), float(inner_tol), int(inner_max)))
 
 
 def sgiga_solve(plan, rel_tol, max_iter, check=True):

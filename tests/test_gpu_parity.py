@@ -353,3 +353,45 @@ def test_errors_are_reported_not_crashes(sg):
         sg.sgiga_set_rhs_builtin(P.handle, "sine")
         st, rc = sg.sgiga_solve(P.handle, 1e-300, 1, check=False)
         assert rc == sg.SGIGA_ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("case,precision", [(CASES[5], "fp64"), (CASES[3], "mixed")])
+def test_graph_loop_matches_host_loop(sg, case, precision):
+    """The CG loop captured as one graph (device-side while node) gives the same
+    iterations and solution as the host-driven loop."""
+    domain, d, p, r, w, grading, gamma, mn = case
+    src = {"unit": "sine", "annulus": "annulus_paper"}[domain]
+    out = []
+    with sg.Plan(d, p, w, domain=domain, continuity=r, min_level=mn, grading=grading, gamma=gamma,
+                 precision=precision) as P:
+        for use_graph in (True, False, True):
+            sg.sgiga_set_solver_options(P.handle, use_graph=use_graph)
+            sg.sgiga_set_rhs_builtin(P.handle, src)
+            st, _ = sg.sgiga_solve(P.handle, 1e-12, 50)
+            u = np.zeros(P.info.ndof)
+            sg.sgiga_get_solution(P.handle, u)
+            out.append((st.iterations, st.inner_iterations, u))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert _rel(out[0][2], out[1][2]) < 1e-12 and _rel(out[2][2], out[1][2]) < 1e-12
+
+
+def test_autotune_keeps_the_operator(sg):
+    """The tile autotuner re-plans tiles and geometry planes; K x is unchanged."""
+    case = ("unit", 3, 3, 2, 7, "uniform", 1.0, 1)
+    with _plan(sg, case) as P:
+        n = P.info.ndof
+        x = _dev(random_vector(n, 61))
+        y0 = torch.zeros_like(x)
+        sg.sgiga_apply(P.handle, x, y0)
+        res = sg.sgiga_autotune(P.handle, reps=2)
+        assert res.ncand >= 4 and 0 <= res.best < res.ncand and res.best_ms > 0
+        y1 = torch.zeros_like(x)
+        sg.sgiga_apply(P.handle, x, y1)
+        assert _rel(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-13
+        sg.sgiga_set_rhs_builtin(P.handle, "sine")
+        st, _ = sg.sgiga_solve(P.handle, 1e-12, 50)
+        u = np.zeros(n)
+        sg.sgiga_get_solution(P.handle, u)
+        g = P.grids[0]
+        comp = _component(case, g).assemble(f=problems.get("sine3").f)
+        assert _rel(u[g.dof_off:g.dof_off + g.ndof], comp.solve()) < 1e-10
