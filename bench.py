@@ -387,6 +387,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "ngrids": ng, "ndof": ndof, "nqp": P.info.nqp,
+                       "diag_metric": P.info.diag_metric,
                        "eval_points": npts, "parallelism": "replica per GPU" if world > 1 else "single GPU",
                        "l2_policy": "inputs larger than L2 (FP64 geometry planes %.2f GB per apply)"
                                     % (6 * 8 * P.info.nqp / 1e9)},

@@ -118,6 +118,8 @@ typedef struct {
     long long nqp;    /* total quadrature points */
     int max_tile_smem; /* bytes of dynamic shared memory of the operator kernel */
     int ntiles;
+    int diag_metric;   /* 1 if every off-diagonal geometry coefficient is exactly zero
+                          (the operator kernels then skip the cross terms) */
 } sgiga_info;
 
 typedef struct {

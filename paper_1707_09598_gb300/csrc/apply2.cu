@@ -11,7 +11,7 @@
 
 namespace sgiga {
 
-template <typename Real, int P, int MODE>
+template <typename Real, int P, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, 2)
 k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
@@ -112,9 +112,15 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                     Real ga = 0.0, gb = 0.0;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; }
-                    const Real G00 = G[gi], G01 = G[nqp + gi], G11 = G[2 * nqp + gi];
-                    const Real va = G00 * ga + G01 * gb;
-                    const Real vb = G01 * ga + G11 * gb;
+                    Real va, vb;
+                    if (DIAG) {   // metric with zero off-diagonal entry: only G_aa, G_bb
+                        va = G[gi] * ga;
+                        vb = G[2 * nqp + gi] * gb;
+                    } else {
+                        const Real G00 = G[gi], G01 = G[nqp + gi], G11 = G[2 * nqp + gi];
+                        va = G00 * ga + G01 * gb;
+                        vb = G01 * ga + G11 * gb;
+                    }
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; }
                 } else {
@@ -167,10 +173,12 @@ template <int P>
 static cudaError_t launch2(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
                            cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    if (mode == 0)
-        k_op2<double, P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    if (mode == 1)
+        k_op2<double, P, 1, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    else if (Pl.diag)
+        k_op2<double, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else
-        k_op2<double, P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op2<double, P, 0, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -189,7 +197,10 @@ cudaError_t launch_op2(const DevPlan& Pl, const double* x, double* y, const int*
 template <int P>
 static cudaError_t launch2f(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_op2<float, P, 0><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    if (Pl.diag)
+        k_op2<float, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    else
+        k_op2<float, P, 0, false><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -207,11 +218,15 @@ cudaError_t set_op2_smem(int p, size_t bytes) {
     cudaError_t e = cudaSuccess;
 #define SET(PP)                                                                                          \
     if (p == PP) {                                                                                       \
-        e = cudaFuncSetAttribute(k_op2<double, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        e = cudaFuncSetAttribute(k_op2<double, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(k_op2<double, PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+            e = cudaFuncSetAttribute(k_op2<double, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(k_op2<float, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+            e = cudaFuncSetAttribute(k_op2<double, PP, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op2<float, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op2<float, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
     }
     SET(1) SET(2) SET(3) SET(4)
 #undef SET

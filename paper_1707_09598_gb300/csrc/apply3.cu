@@ -16,7 +16,7 @@
 
 namespace sgiga {
 
-template <typename Real, int P, int MODE>
+template <typename Real, int P, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, 2)
 k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
@@ -145,11 +145,18 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                     Real ga = 0.0, gb = 0.0, gc = 0.0;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; gc += bt[t] * i2[t]; }
-                    const Real G00 = G[gi], G01 = G[nqp + gi], G02 = G[2 * nqp + gi];
-                    const Real G11 = G[3 * nqp + gi], G12 = G[4 * nqp + gi], G22 = G[5 * nqp + gi];
-                    const Real va = G00 * ga + G01 * gb + G02 * gc;
-                    const Real vb = G01 * ga + G11 * gb + G12 * gc;
-                    const Real vc = G02 * ga + G12 * gb + G22 * gc;
+                    Real va, vb, vc;
+                    if (DIAG) {   // metric with zero off-diagonal entries: only G_aa, G_bb, G_cc
+                        va = G[gi] * ga;
+                        vb = G[3 * nqp + gi] * gb;
+                        vc = G[5 * nqp + gi] * gc;
+                    } else {
+                        const Real G00 = G[gi], G01 = G[nqp + gi], G02 = G[2 * nqp + gi];
+                        const Real G11 = G[3 * nqp + gi], G12 = G[4 * nqp + gi], G22 = G[5 * nqp + gi];
+                        va = G00 * ga + G01 * gb + G02 * gc;
+                        vb = G01 * ga + G11 * gb + G12 * gc;
+                        vc = G02 * ga + G12 * gb + G22 * gc;
+                    }
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { a0[t] += dt[t] * va; a1[t] += bt[t] * vb; a2[t] += bt[t] * vc; }
                 } else {
@@ -227,10 +234,12 @@ template <int P>
 static cudaError_t launch3(const DevPlan& Pl, const double* x, double* y, const int* active, int mode,
                            cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    if (mode == 0)
-        k_op3<double, P, 0><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    if (mode == 1)
+        k_op3<double, P, 1, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    else if (Pl.diag)
+        k_op3<double, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else
-        k_op3<double, P, 1><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+        k_op3<double, P, 0, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -249,7 +258,10 @@ cudaError_t launch_op3(const DevPlan& Pl, const double* x, double* y, const int*
 template <int P>
 static cudaError_t launch3f(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_op3<float, P, 0><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    if (Pl.diag)
+        k_op3<float, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    else
+        k_op3<float, P, 0, false><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
     return cudaGetLastError();
 }
 
@@ -267,11 +279,15 @@ cudaError_t set_op3_smem(int p, size_t bytes) {
     cudaError_t e = cudaSuccess;
 #define SET(PP)                                                                                          \
     if (p == PP) {                                                                                       \
-        e = cudaFuncSetAttribute(k_op3<double, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        e = cudaFuncSetAttribute(k_op3<double, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(k_op3<double, PP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+            e = cudaFuncSetAttribute(k_op3<double, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(k_op3<float, PP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+            e = cudaFuncSetAttribute(k_op3<double, PP, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<float, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<float, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
     }
     SET(1) SET(2) SET(3) SET(4)
 #undef SET

@@ -236,11 +236,25 @@ static void free_plan(sgiga_plan_s* P) {
     destroy_loop_graph(P->loop64);
     destroy_loop_graph(P->loop32);
     if (P->own_stream) cudaStreamDestroy(P->own_stream);
+    if (P->d_eval_vals) cudaFree(P->d_eval_vals);
+    if (P->d_eval_first) cudaFree(P->d_eval_first);
     for (void* a : P->allocs) cudaFree(a);
     if (P->stage) cudaFree(P->stage);
     if (P->feat) cudaFree(P->feat);
     if (P->h_nactive) cudaFreeHost(P->h_nactive);
     delete P;
+}
+
+// After the geometry planes change: is the metric diagonal everywhere?
+static int update_diag(sgiga_plan_s* P) {
+    CUDA_TRY(launch_offdiag_check(P->dp, P->dp.flags + 2, P->stream));
+    int h = 1;
+    CUDA_TRY(cudaMemcpyAsync(&h, P->dp.flags + 2, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    P->dp.diag = h ? 0 : 1;
+    destroy_loop_graph(P->loop64);
+    destroy_loop_graph(P->loop32);
+    return SGIGA_OK;
 }
 
 // Dynamic shared-memory attribute of the operator kernels; it only grows, so
@@ -534,6 +548,7 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaMemcpyAsync(hflags, dflags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
+    if ((rc = update_diag(P))) return rc;
     // operator kernel shared memory
     if ((rc = grant_op_smem(P))) return rc;
     // solver vectors and scalars
@@ -603,10 +618,8 @@ static int retile(sgiga_plan_s* P, size_t budget, long long qpcap) {
     CUDA_TRY(launch_geometry(D, s));
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(D.Gf, D.G, (long long)P->ncomp * P->nqp, s));
-    destroy_loop_graph(P->loop64);
-    destroy_loop_graph(P->loop32);
     CUDA_TRY(cudaStreamSynchronize(s));
-    return SGIGA_OK;
+    return update_diag(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,6 +680,7 @@ int sgiga_plan_info(sgiga_plan_t P, sgiga_info* out) {
     out->nqp = P->nqp;
     out->max_tile_smem = (int)P->smem;
     out->ntiles = (int)P->tiles.size();
+    out->diag_metric = P->dp.diag;
     return SGIGA_OK;
 }
 
@@ -762,7 +776,7 @@ int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const 
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    return SGIGA_OK;
+    return update_diag(P);
 }
 
 int sgiga_get_rhs(sgiga_plan_t P, double* b) {
@@ -948,8 +962,23 @@ int sgiga_eval(sgiga_plan_t P, const double* xi, long long npts, double* ucomp) 
         st += xb;
     }
     double* ud = udev ? ucomp : (double*)st;
+    // per-(table, point) basis values, shared by the components (plan-owned, grown on demand)
+    const size_t need_vals = (size_t)P->tabs.size() * npts;
+    if (need_vals > P->eval_cap) {
+        if (P->d_eval_vals) cudaFree(P->d_eval_vals);
+        if (P->d_eval_first) cudaFree(P->d_eval_first);
+        P->d_eval_vals = nullptr;
+        P->d_eval_first = nullptr;
+        P->eval_cap = 0;
+        if (cudaMalloc(&P->d_eval_vals, need_vals * (P->p + 1) * 8) != cudaSuccess ||
+            cudaMalloc(&P->d_eval_first, need_vals * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SGIGA_ERR_NOMEM, "evaluation basis buffer allocation failed");
+        }
+        P->eval_cap = need_vals;
+    }
     CUDA_TRY(cudaMemsetAsync(P->dp.flags + 1, 0, sizeof(int), P->stream));
-    CUDA_TRY(launch_eval(P->dp, P->d_x, xd, npts, ud, P->stream));
+    CUDA_TRY(launch_eval(P->dp, P->d_x, xd, npts, P->d_eval_vals, P->d_eval_first, ud, P->stream));
     int hflag = 0;
     CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->dp.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     if (!udev) CUDA_TRY(cudaMemcpyAsync(ucomp, ud, ub, cudaMemcpyDeviceToHost, P->stream));

@@ -8,8 +8,34 @@
 
 namespace sgiga {
 
-__global__ void k_eval(DevPlan P, const double* __restrict__ coeffs, const double* __restrict__ xi, long long npts,
-                       double* __restrict__ ucomp) {
+// Basis values of every 1D table at every point: vals[(t*npts + j)*(p+1) + r]
+// = R_{first+r}(xi_j[dir_t]) of table t, first[t*npts + j] = first function.
+// Shared by all components that use the table.
+__global__ void k_eval_basis(DevPlan P, const double* __restrict__ xi, long long npts, double* __restrict__ vals,
+                             int* __restrict__ first) {
+    const int t = blockIdx.y;
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npts) return;
+    const Table1D& tb = P.tabs[t];
+    const int d = P.d, p = P.p;
+    const double* kn = P.knots + tb.koff;
+    double x = xi[j * d + tb.dir];
+    if (!(x >= 0.0 && x <= 1.0)) {  // outside the parametric domain: report, clamp
+        atomicOr(&P.flags[1], 1);
+        x = x < 0.0 ? 0.0 : 1.0;
+    }
+    int s = find_span(kn, tb.nf, p, x);
+    double N[SGIGA_MAXP + 1];
+    basis_funs<SGIGA_MAXP>(kn, s, p, x, N, nullptr);
+    double W, dW;
+    patch_weight_1d(*P.patch, tb.dir, x, W, dW);
+    const long long o = (long long)t * npts + j;
+    for (int r = 0; r <= p; ++r) vals[o * (p + 1) + r] = N[r] / W;
+    first[o] = s - p;
+}
+
+__global__ void k_eval(DevPlan P, const double* __restrict__ coeffs, long long npts,
+                       const double* __restrict__ vals, const int* __restrict__ first, double* __restrict__ ucomp) {
     const int g = blockIdx.y;
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= npts) return;
@@ -19,20 +45,9 @@ __global__ void k_eval(DevPlan P, const double* __restrict__ coeffs, const doubl
     int f0[3];
     for (int k = 0; k < 3; ++k) {
         if (k >= d) { Rv[k][0] = 1.0; f0[k] = 1; continue; }
-        const Table1D& tb = P.tabs[gd.tab[k]];
-        const double* kn = P.knots + tb.koff;
-        double t = xi[j * d + k];
-        if (!(t >= 0.0 && t <= 1.0)) {  // outside the parametric domain: report, clamp
-            atomicOr(&P.flags[1], 1);
-            t = t < 0.0 ? 0.0 : 1.0;
-        }
-        int s = find_span(kn, tb.nf, p, t);
-        double N[SGIGA_MAXP + 1];
-        basis_funs<SGIGA_MAXP>(kn, s, p, t, N, nullptr);
-        double W, dW;
-        patch_weight_1d(*P.patch, k, t, W, dW);
-        for (int r = 0; r <= p; ++r) Rv[k][r] = N[r] / W;
-        f0[k] = s - p;
+        const long long o = (long long)gd.tab[k] * npts + j;
+        f0[k] = first[o];
+        for (int r = 0; r <= p; ++r) Rv[k][r] = vals[o * (p + 1) + r];
     }
     const long long st1 = gd.n[0], st2 = (long long)gd.n[0] * gd.n[1];
     const double* c = coeffs + gd.dof_off;
@@ -57,12 +72,17 @@ __global__ void k_eval(DevPlan P, const double* __restrict__ coeffs, const doubl
     ucomp[(long long)g * npts + j] = u;
 }
 
-cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts, double* ucomp,
-                        cudaStream_t s) {
+cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts, double* vals,
+                        int* first, double* ucomp, cudaStream_t s) {
     if (npts <= 0) return cudaSuccess;
+    dim3 gb((unsigned)((npts + 127) / 128), P.ntabs);
+    SGIGA_COUNT_LAUNCH();
+    k_eval_basis<<<gb, 128, 0, s>>>(P, xi, npts, vals, first);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((npts + 127) / 128), P.ngrids);
     SGIGA_COUNT_LAUNCH();
-    k_eval<<<grid, 128, 0, s>>>(P, coeffs, xi, npts, ucomp);
+    k_eval<<<grid, 128, 0, s>>>(P, coeffs, npts, vals, first, ucomp);
     return cudaGetLastError();
 }
 

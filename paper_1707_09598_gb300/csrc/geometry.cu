@@ -122,6 +122,28 @@ __global__ void k_geometry(DevPlan P) {
     }
 }
 
+// flag = 1 if some off-diagonal geometry coefficient is nonzero
+__global__ void k_offdiag(const double* __restrict__ G, long long nqp, int d, int* __restrict__ flag) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    const int planes3[3] = {1, 2, 4};
+    const int np = d == 3 ? 3 : 1;
+    bool nz = false;
+    for (; i < nqp; i += stride)
+        for (int k = 0; k < np; ++k) nz |= G[(long long)(d == 3 ? planes3[k] : 1) * nqp + i] != 0.0;
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (P.nqp + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    SGIGA_COUNT_LAUNCH();
+    k_offdiag<<<(unsigned)blocks, 256, 0, s>>>(P.G, P.nqp, P.d, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     k_geometry<<<P.ntiles, 256, 0, s>>>(P);

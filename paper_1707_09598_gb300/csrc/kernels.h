@@ -49,12 +49,14 @@ struct DevPlan {
     int nfeat;
     double famp;
     size_t smem_op;          // dynamic shared bytes of the operator kernel
+    int diag;                // every geometry plane off the diagonal is exactly zero
 };
 
 // basis.cu
 cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
 // geometry.cu
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s);
 cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s);
 cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s);
 cudaError_t launch_source_qp(const DevPlan& P, int source, double* fout, cudaStream_t s);
@@ -125,8 +127,8 @@ cudaError_t launch_pair_store(const DevPlan& P, const double* r, const double* x
                               float* ed, cudaStream_t s);
 
 // eval.cu
-cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts,
-                        double* ucomp, cudaStream_t s);
+cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi, long long npts, double* vals,
+                        int* first, double* ucomp, cudaStream_t s);
 cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts, const double* coef,
                            double* u, cudaStream_t s);
 

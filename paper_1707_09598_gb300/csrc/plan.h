@@ -72,6 +72,9 @@ struct sgiga_plan_s {
     bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
     cudaStream_t own_stream = nullptr;   // capture/launch stream when the plan's stream is the legacy one
     int* d_counter = nullptr;            // iteration counter of the captured loop
+    double* d_eval_vals = nullptr;       // evaluation: basis values per (table, point)
+    int* d_eval_first = nullptr;
+    size_t eval_cap = 0;
     TileDesc* d_tiles = nullptr;         // current tile arrays (replaced by the autotuner)
     int* d_sched = nullptr;
     struct LoopGraph {
@@ -83,6 +86,7 @@ struct sgiga_plan_s {
         const int* outer = nullptr;
         bool flexible = false;
         bool failed = false;
+        long long body_kernels = 0;   // kernels per iteration of the captured body
     } loop64, loop32;
     size_t stage_bytes = 0;
 };
@@ -296,6 +300,7 @@ inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real
         P->stream = ls;
         cudaError_t e = cudaStreamBeginCaptureToGraph(ls, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         int rc = SGIGA_OK;
+        const long long count0 = g_launches.load();
         if (e == cudaSuccess) {
             rc = pcg_body_a<Real>(P, v, tol, active, iters, scal);
             if (rc == SGIGA_OK) rc = pcg_body_b<Real>(P, v, active, scal, flexible);
@@ -310,6 +315,9 @@ inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real
             rc = fail(SGIGA_ERR_CUDA, cudaGetErrorString(e));
         }
         P->stream = saved;
+        // capture only records the kernels; they are counted when the graph runs
+        L.body_kernels = g_launches.load() - count0;
+        g_launches.fetch_sub(L.body_kernels);
         if (rc) { cudaGetLastError(); destroy_loop_graph(L); return rc; }
         CUDA_TRY(cudaGraphInstantiate(&L.exec, g, 0));
         L.tol = tol;
@@ -362,6 +370,7 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
                                      P->stream ? P->stream : P->own_stream));
             CUDA_TRY(cudaStreamSynchronize(P->stream ? P->stream : P->own_stream));
             if (iters_run) *iters_run = P->h_nactive[0];
+            g_launches.fetch_add((long long)P->h_nactive[0] * L.body_kernels);
             return P->h_nactive[1];
         }
         L.failed = true;   // this device/driver cannot run the captured loop: host loop from now on

@@ -48,7 +48,7 @@ class sgiga_config(ctypes.Structure):
 class sgiga_info(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("ngrids", ctypes.c_int),
                 ("ndof", ctypes.c_longlong), ("nqp", ctypes.c_longlong), ("max_tile_smem", ctypes.c_int),
-                ("ntiles", ctypes.c_int)]
+                ("ntiles", ctypes.c_int), ("diag_metric", ctypes.c_int)]
 
 
 class sgiga_grid(ctypes.Structure):

@@ -293,6 +293,7 @@ def test_cube_p3_w10_full_size(sg):
     pts = eval_points(3, 16)
     with _plan(sg, case) as P:
         assert P.info.ngrids == 136 and P.info.ndof == 557030
+        assert P.info.diag_metric == 1      # identity map: the cross terms are skipped
         sg.sgiga_set_rhs_builtin(P.handle, "sine")
         st, _ = sg.sgiga_solve(P.handle, 1e-12, 100)
         assert st.converged == 136
