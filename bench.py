@@ -150,9 +150,11 @@ class Clocks:
 def apply_flops(plan):
     """Algorithmic FP64 flops of one operator apply: untiled sum factorisation
     (forward: 2(p+1) + 3(p+1) + 3(p+1) FMA per output of the three stages,
-    pointwise 9 FMA per qp, backward mirrored), best axis order per grid."""
+    pointwise 9 FMA per qp -- 3 when the metric is diagonal --, backward
+    mirrored), best axis order per grid."""
     import itertools
     p = plan.info.p
+    pw = 3 if plan.info.diag_metric else 9
     P1, Q = p + 1, p + 1
     total = 0.0
     for g in plan.grids:
@@ -163,7 +165,7 @@ def apply_flops(plan):
             s_c = 2 * P1 * nf[a] * nf[b] * Q * E[c]
             s_b = 3 * P1 * nf[a] * Q * E[b] * Q * E[c]
             s_a = 3 * P1 * Q * E[a] * Q * E[b] * Q * E[c]
-            fma = 2 * (s_a + s_b + s_c) + 9 * Q ** 3 * E[0] * E[1] * E[2]
+            fma = 2 * (s_a + s_b + s_c) + pw * Q ** 3 * E[0] * E[1] * E[2]
             best = fma if best is None else min(best, fma)
         total += 2.0 * best
     return total
@@ -340,7 +342,7 @@ def run_ours(args):
     flops = apply_flops(P)
     peak64 = fp64_peak_tflops(torch)
     achieved = flops / apply_s / 1e12
-    g_bytes = 6 * 8 * P.info.nqp + 2 * 8 * ndof
+    g_bytes = (3 if P.info.diag_metric else 6) * 8 * P.info.nqp + 2 * 8 * ndof
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                 "frac": achieved / peak64, "traffic": None,
                 "kernel": "k_op3<3,0> (FP64 sum-factorised stiffness apply)",

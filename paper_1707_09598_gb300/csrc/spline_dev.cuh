@@ -111,6 +111,34 @@ __device__ __forceinline__ void patch_eval(const Patch& P, const double* xi, dou
                     for (int k = 0; k < d; ++k) dA[i][k] += g[k] * P.cp[ci][i];
                 }
             }
+    if (!(P.rational[0] || P.rational[1] || P.rational[2])) {
+        // Polynomial patch: all weights are 1 and W = 1, so F = A and J = dA.
+        // Column k of J is summed with direction k innermost,
+        //   J[i][k] = sum_{other dirs} (prod N) * sum_{a_k} dN_k[a_k] cp_i,
+        // so a coordinate that is constant along direction k (an axis-aligned
+        // box) gets an exactly zero derivative there instead of a sum of
+        // cancelling products that leaves rounding residues.
+        for (int i = 0; i < d; ++i) x[i] = A[i];
+        for (int k = 0; k < d; ++k) {
+            const int m1 = k == 0 ? 1 : 0, m2 = k == 2 ? 1 : 2;
+            double Jk[3] = {0, 0, 0};
+            for (int u2 = 0; u2 <= deg[m2]; ++u2)
+                for (int u1 = 0; u1 <= deg[m1]; ++u1) {
+                    double sk[3] = {0, 0, 0};
+                    for (int uk = 0; uk <= deg[k]; ++uk) {
+                        int id[3];
+                        id[m1] = u1; id[m2] = u2; id[k] = uk;
+                        int i0 = s[0] - deg[0] + id[0], i1 = s[1] - deg[1] + id[1], i2 = s[2] - deg[2] + id[2];
+                        int ci = i0 + P.nc[0] * (i1 + (d > 1 ? P.nc[1] : 1) * i2);
+                        for (int i = 0; i < d; ++i) sk[i] += dN[k][uk] * P.cp[ci][i];
+                    }
+                    const double outer = N[m1][u1] * N[m2][u2];
+                    for (int i = 0; i < d; ++i) Jk[i] += outer * sk[i];
+                }
+            for (int i = 0; i < d; ++i) J[i][k] = Jk[i];
+        }
+        return;
+    }
     for (int i = 0; i < d; ++i) {
         x[i] = A[i] / W;
         for (int k = 0; k < d; ++k) J[i][k] = (dA[i][k] * W - A[i] * dW[k]) / (W * W);
