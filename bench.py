@@ -36,6 +36,9 @@ WORKLOAD_NAME = ("3D unit-cube Poisson, u=sin(pi x)sin(pi y)sin(pi z), p=3 C^2 B
 GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
 # components solved by the CPU oracle in its bounded sample (assembly + direct solve + evaluation)
 ORACLE_SAMPLE = [(4, 4, 4), (10, 1, 1), (3, 5, 4), (2, 2, 7)]
+# DRAM bytes (read + write) of one launch of the diagonal-metric FP64 apply on
+# this workload, from one ncu capture; see profiles/k_op3_fp64_apply_cube_p3_w10.md
+APPLY_DRAM_BYTES = 555.391488e6 + 9.998592e6
 
 
 def parse():
@@ -44,6 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the CG loop from the host instead of the captured graph (same kernels; "
+                         "profilers list the kernels of a device-side graph loop only this way)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision line of the same workload")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -91,6 +98,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(v, world, device):
+    """Largest v over all ranks (identity for one rank); every rank gets it."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed / the max-over-ranks time (weak scaling)."""
+    return world * units_per_rank / seconds
 
 
 class Clocks:
@@ -234,6 +257,64 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------
 
+def run_mixed(args, sgiga, torch, f_dev, pts, npts, gold, ndof, world):
+    """The same workload and tolerance with the FP32 inner solve inside FP64
+    iterative refinement (FP64 residual; FP32 apply and preconditioner)."""
+    W = WORKLOAD
+    stream = torch.cuda.Stream()
+    P = sgiga.Plan(W["d"], W["p"], W["w"], domain=W["domain"], precision="mixed", stream=stream)
+    sgiga.sgiga_autotune(P.handle, reps=3)
+    if args.host_loop:
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
+    uc = torch.zeros(P.info.ngrids * npts, dtype=torch.float64, device="cuda")
+    u = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    stats = []
+
+    def step():
+        sgiga.sgiga_set_rhs(P.handle, f_dev)
+        st, _ = sgiga.sgiga_solve(P.handle, W["tol"], 50)
+        stats.append((st.iterations, st.inner_iterations))
+        sgiga.sgiga_eval(P.handle, pts, npts, uc)
+        sgiga.sgiga_combine(P.handle, uc, npts, u)
+
+    for _ in range(args.warmup):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    uh = u.cpu().numpy()
+    # the FP32 apply alone (HBM-bound: FP32 geometry planes + x and y)
+    x = torch.randn(ndof, dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    for _ in range(3):
+        sgiga.sgiga_apply_f32(P.handle, x, y)
+    reps = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(reps):
+        sgiga.sgiga_apply_f32(P.handle, x, y)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_s = a0.elapsed_time(a1) / reps / 1e3
+    nplanes = 3 if P.info.diag_metric else 6
+    g_bytes = nplanes * 4 * P.info.nqp + 2 * 4 * ndof
+    hbm = load_peaks().get("hbm_gbs", 6800.0)
+    out = {"value": whole_job_rate(ndof, world, ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
+           "dtype": "f32 inner solve, f64 residual and combination",
+           "rel_l2_vs_oracle": float(np.linalg.norm(uh - gold) / np.linalg.norm(gold)),
+           "outer_iterations": max(s[0] for s in stats), "inner_iterations": max(s[1] for s in stats),
+           "apply_f32": {"ms": apply_s * 1e3, "algorithmic_bytes": g_bytes, "GBps": g_bytes / apply_s / 1e9,
+                         "frac_of_measured_hbm": g_bytes / apply_s / 1e9 / hbm}}
+    P.close()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -255,9 +336,14 @@ def run_ours(args):
     t0 = time.perf_counter()
     tune = sgiga.sgiga_autotune(P.handle, reps=3)
     tune_s = time.perf_counter() - t0
+    if args.host_loop:
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
     tuning = {"seconds": tune_s, "best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
                                           "apply_ms": tune.best_ms, "ntiles": tune.ntiles},
-              "candidates_ms": [round(tune.ms[i], 4) for i in range(tune.ncand)]}
+              "candidates_ms": [round(tune.ms[i], 4) for i in range(tune.ncand)],
+              "precond_split": {"best_ks": tune.fd_ks[tune.fd_best], "items": tune.fd_nitems,
+                                "candidates_ms": {str(tune.fd_ks[i]): round(tune.fd_ms[i], 4)
+                                                  for i in range(tune.fd_ncand)}}}
     ndof, ng = P.info.ndof, P.info.ngrids
     pts_h = eval_points(W["d"], W["lattice"])
     npts = len(pts_h)
@@ -293,13 +379,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = sgiga.sgiga_launch_count() - l0
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
-    value = world * ndof / (ms / 1e3)
+    value = whole_job_rate(ndof, world, ms / 1e3)
 
     # accuracy of the combined solution against the stored oracle values
     gold = np.loadtxt(GOLDEN)[:, 0]
@@ -344,7 +427,7 @@ def run_ours(args):
     achieved = flops / apply_s / 1e12
     g_bytes = (3 if P.info.diag_metric else 6) * 8 * P.info.nqp + 2 * 8 * ndof
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": None,
+                "frac": achieved / peak64, "traffic": APPLY_DRAM_BYTES if P.info.diag_metric else None,
                 "kernel": "k_op3<3,0> (FP64 sum-factorised stiffness apply)",
                 "apply_ms": apply_s * 1e3, "algorithmic_flops": flops,
                 "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64 pipe)",
@@ -369,12 +452,10 @@ def run_ours(args):
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, "cuda")
     l2_e2e = float(np.linalg.norm(u_np - gold) / np.linalg.norm(gold))
+
+    mixed = None if args.no_mixed else run_mixed(args, sgiga, torch, f_dev, pts, npts, gold, ndof, world)
 
     cpu = None
     if rank == 0:
@@ -392,13 +473,15 @@ def run_ours(args):
                        "diag_metric": P.info.diag_metric,
                        "eval_points": npts, "parallelism": "replica per GPU" if world > 1 else "single GPU",
                        "l2_policy": "inputs larger than L2 (FP64 geometry planes %.2f GB per apply)"
-                                    % (6 * 8 * P.info.nqp / 1e9)},
+                                    % ((3 if P.info.diag_metric else 6) * 8 * P.info.nqp / 1e9),
+                       "cg_loop": "host loop" if args.host_loop else "captured graph with device-side while"},
             "accuracy": {"rel_l2_vs_oracle": l2, "rel_l2_vs_oracle_e2e": l2_e2e,
                          "target": 1e-10, "iterations": max(iters)},
             "phases_ms": phases, "plan_s": plan_s, "autotune": tuning,
             "roofline": roofline,
+            "mixed_fp32_ir": mixed,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * ndof / e2e_s, "unit": "DoF/s",
+            "e2e": {"value": whole_job_rate(ndof, world, e2e_s), "unit": "DoF/s",
                     "h2d_bytes_per_step": int(P.info.nqp * 8 + npts * W["d"] * 8),
                     "d2h_bytes_per_step": int(npts * 8)},
             "gpu_launches": int(launches),

@@ -201,6 +201,10 @@ int sgiga_apply_f32(sgiga_plan_t plan, const float* x, float* y);
  * solvers as future work, Sec. 5). Exact inverse on the unit square/cube.
  * Device packed vectors. */
 int sgiga_precond(sgiga_plan_t plan, const double* r, double* z);
+/* FP32 variant of sgiga_precond (the preconditioner of the MIXED_FP32 inner
+ * solve): FP32 eigenvectors and eigenvalue reciprocals, FP32 accumulation.
+ * r, z: device float [ndof]. Needs a plan built with SGIGA_PREC_MIXED_FP32. */
+int sgiga_precond_f32(sgiga_plan_t plan, const float* r, float* z);
 
 /* Solve K_g u_g = b_g for every component g (batched preconditioned CG,
  * per-component scalars and convergence) until ||r_g|| <= rel_tol ||b_g|| or
@@ -212,20 +216,28 @@ int sgiga_precond(sgiga_plan_t plan, const double* r, double* z);
 int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
                 sgiga_solve_stats* stats /* host, may be NULL */);
 
-/* Autotuner of the operator kernels' tiles. Re-plans the tiles of every
- * component under each candidate policy (shared-memory budget per block, cap
- * on quadrature points per tile; the shape within a policy comes from the
- * planner's cost model), times `reps` stiffness applies on the plan's stream
- * for each (CUDA events), and keeps the fastest; the geometry planes are
- * recomputed in the chosen tile layout. Overwrites the plan's work vectors
- * (not its load vector or solution). out (host, may be NULL) receives the
- * per-candidate mean times. */
+/* Autotuner of the operator and preconditioner work decomposition.
+ * (1) Re-plans the tiles of every component under each candidate policy
+ * (shared-memory budget per block, cap on quadrature points per tile; the
+ * shape within a policy comes from the planner's cost model), times `reps`
+ * stiffness applies on the plan's stream for each (CUDA events), and keeps
+ * the fastest; the geometry planes are recomputed in the chosen tile layout.
+ * (2) Re-splits the fast-diagonalisation mode products into work items of
+ * each candidate contraction depth (fd_ks: entries of a long 1D contraction
+ * per item; shorter items balance the SMs better, longer ones need fewer
+ * atomic partial sums), times `reps` preconditioner applications for each and
+ * keeps the fastest. Overwrites the plan's work vectors (not its load vector
+ * or solution). out (host, may be NULL) receives the per-candidate mean
+ * times. */
 typedef struct {
     int ncand, best, ntiles;
     double best_ms;
     double ms[8];
     int budget[8];    /* bytes of shared memory per block */
     int qpcap[8];     /* quadrature points per tile at most */
+    int fd_ncand, fd_best, fd_nitems;
+    int fd_ks[8];     /* contraction depth per preconditioner work item */
+    double fd_ms[8];  /* mean time of one preconditioner application */
 } sgiga_tune_result;
 int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
 
@@ -236,6 +248,13 @@ int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
  * iteration. inner_tol / inner_max: tolerance and iteration limit of the FP32
  * inner solve of SGIGA_PREC_MIXED_FP32 (defaults 1e-5, 100). */
 int sgiga_set_solver_options(sgiga_plan_t plan, int use_graph, double inner_tol, int inner_max);
+
+/* Contraction depth of the preconditioner's work items: a 1D contraction
+ * longer than ks entries is split into ks-deep items whose partial sums are
+ * added atomically (the autotuner picks ks by measurement; default 128).
+ * ks must be a multiple of 16 in [16, 4096], else SGIGA_ERR_ARG. The result
+ * changes only by summation order. */
+int sgiga_set_precond_split(sgiga_plan_t plan, int ks);
 
 /* Packed solution coefficients (device [ndof]). */
 int sgiga_get_solution(sgiga_plan_t plan, double* u);

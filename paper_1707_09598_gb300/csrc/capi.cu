@@ -246,6 +246,74 @@ static void free_plan(sgiga_plan_s* P) {
 }
 
 // After the geometry planes change: is the metric diagonal everywhere?
+// Preconditioner work items per direction. The shape of each component's
+// mode product picks SMALL / ROWS / TILE; contractions longer than ks are
+// split into ks-deep items whose partial sums add atomically. Items are
+// ordered by estimated FMAs, largest first (greedy longest-processing-time
+// order), so that the short ones fill the tail of the launch.
+static void make_fd_items(sgiga_plan_s* P, int ks) {
+    const int d = P->d;
+    P->fd_ks = ks;
+    for (int k = 0; k < d; ++k) {
+        std::vector<FDItem>& v = P->fd[k];
+        v.clear();
+        std::vector<long long> cost;
+        for (size_t gi = 0; gi < P->grids.size(); ++gi) {
+            const GridDesc& g = P->grids[gi];
+            long long n = g.n[k];
+            if (g.ndof == 0) continue;
+            long long ncol = g.ndof / n;
+            auto depth = [&](int j0) { return (int)std::min<long long>(n, j0 + ks); };
+            if (n <= 64) {
+                for (long long c0 = 0; c0 < g.ndof; c0 += 256) {
+                    v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
+                    cost.push_back(std::min<long long>(256, g.ndof - c0) * n);
+                }
+            } else if (ncol >= 64) {
+                for (long long i0 = 0; i0 < n; i0 += 32)
+                    for (long long c0 = 0; c0 < ncol; c0 += 64)
+                        for (int j0 = 0; j0 < n; j0 += ks) {
+                            v.push_back(FDItem{(int)gi, FD_TILE, 0, (int)i0, c0, j0, depth(j0)});
+                            cost.push_back(std::min<long long>(32, n - i0) * std::min<long long>(64, ncol - c0) *
+                                           (depth(j0) - j0));
+                        }
+            } else {
+                long long ng = (ncol + 7) / 8, per = (ncol + ng - 1) / ng;
+                for (long long i0 = 0; i0 < n; i0 += 256)
+                    for (long long c0 = 0; c0 < ncol; c0 += per)
+                        for (int j0 = 0; j0 < n; j0 += ks) {
+                            int nc = (int)std::min(per, ncol - c0);
+                            v.push_back(FDItem{(int)gi, FD_ROWS, nc, (int)i0, c0, j0, depth(j0)});
+                            cost.push_back(std::min<long long>(256, n - i0) * nc * (depth(j0) - j0));
+                        }
+            }
+        }
+        std::vector<size_t> ord(v.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+        std::vector<FDItem> sorted(v.size());
+        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = v[ord[i]];
+        v.swap(sorted);
+    }
+}
+
+// Re-split the preconditioner work items at depth ks and upload them.
+static int refd(sgiga_plan_s* P, int ks) {
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    make_fd_items(P, ks);
+    for (int k = 0; k < P->d; ++k) {
+        auto it = std::find(P->allocs.begin(), P->allocs.end(), (void*)P->d_fd[k]);
+        if (it != P->allocs.end()) P->allocs.erase(it);
+        cudaFree(P->d_fd[k]);
+        P->d_fd[k] = nullptr;
+        int rc = upload(P, &P->d_fd[k], P->fd[k]);
+        if (rc) return rc;
+    }
+    destroy_loop_graph(P->loop64);   // the captured loops hold the old item arrays
+    destroy_loop_graph(P->loop32);
+    return SGIGA_OK;
+}
+
 static int update_diag(sgiga_plan_s* P) {
     CUDA_TRY(launch_offdiag_check(P->dp, P->dp.flags + 2, P->stream));
     int h = 1;
@@ -403,38 +471,7 @@ static int build(sgiga_plan_s* P) {
         P->grids.push_back(g);
     }
     make_tiles(P, 110 * 1024, 16384);
-    // preconditioner work items per direction: the shape of each component's
-    // mode product picks SMALL / ROWS / TILE; items with the longest
-    // contractions first
-    for (int k = 0; k < d; ++k) {
-        std::vector<FDItem>& v = P->fd[k];
-        for (size_t gi = 0; gi < P->grids.size(); ++gi) {
-            const GridDesc& g = P->grids[gi];
-            long long n = g.n[k];
-            if (g.ndof == 0) continue;
-            long long ncol = g.ndof / n;
-            const int KS = 128;   // contraction depth per item once n > KS
-            if (n <= 64) {
-                for (long long c0 = 0; c0 < g.ndof; c0 += 256)
-                    v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
-            } else if (ncol >= 64) {
-                for (long long i0 = 0; i0 < n; i0 += 32)
-                    for (long long c0 = 0; c0 < ncol; c0 += 64)
-                        for (int j0 = 0; j0 < n; j0 += KS)
-                            v.push_back(FDItem{(int)gi, FD_TILE, 0, (int)i0, c0, j0, (int)std::min<long long>(n, j0 + KS)});
-            } else {
-                long long ng = (ncol + 7) / 8, per = (ncol + ng - 1) / ng;
-                for (long long i0 = 0; i0 < n; i0 += 256)
-                    for (long long c0 = 0; c0 < ncol; c0 += per)
-                        for (int j0 = 0; j0 < n; j0 += KS)
-                            v.push_back(FDItem{(int)gi, FD_ROWS, (int)std::min(per, ncol - c0), (int)i0, c0, j0,
-                                               (int)std::min<long long>(n, j0 + KS)});
-            }
-        }
-        std::stable_sort(v.begin(), v.end(), [&](const FDItem& a, const FDItem& b) {
-            return P->grids[a.grid].n[k] > P->grids[b.grid].n[k];
-        });
-    }
+    make_fd_items(P, 128);
     // device data
     if (c.domain == SGIGA_DOMAIN_PATCH) {
         if (!c.patch || make_user_patch(c.patch, d, P->patch) != 0)
@@ -808,6 +845,12 @@ int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
     return precond_fd<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
 }
 
+int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
+    if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32) return fail(SGIGA_ERR_ARG, "plan has no FP32 data (precision)");
+    return precond_fd<float>(P, r, z, nullptr, P->f_t1, P->f_t2);
+}
+
 int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
     struct Cand { size_t budget; long long qpcap; };
@@ -836,17 +879,53 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         if (out && i < 8) { out->ms[i] = per; out->budget[i] = (int)cands[i].budget; out->qpcap[i] = (int)cands[i].qpcap; }
         if (per < best) { best = per; bi = i; }
     }
+    if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap);
+    // preconditioner item depth
+    const int ks_c[] = {32, 64, 128, 256};
+    const int nks = (int)(sizeof(ks_c) / sizeof(ks_c[0]));
+    double fbest = 1e30;
+    int fbi = 2;
+    for (int i = 0; i < nks && rc == SGIGA_OK; ++i) {
+        if ((rc = refd(P, ks_c[i]))) break;
+        // the precision the plan's CG runs in; plain FD (no learned correction)
+        auto fd_once = [&]() {
+            if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
+                return precond_fd<float>(P, P->f_b, P->f_z, nullptr, P->f_t1, P->f_t2);
+            return precond_fd<double>(P, P->d_b, P->d_z, nullptr, P->d_t1, P->d_t2);
+        };
+        if ((rc = fd_once())) break;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = fd_once();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double per = ms / reps;
+        if (out) { out->fd_ms[i] = per; out->fd_ks[i] = ks_c[i]; }
+        if (per < fbest) { fbest = per; fbi = i; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if ((rc = retile(P, cands[bi].budget, cands[bi].qpcap))) return rc;
+    if ((rc = refd(P, ks_c[fbi]))) return rc;
     if (out) {
         out->ncand = nc;
         out->best = bi;
         out->best_ms = best;
         out->ntiles = (int)P->tiles.size();
+        out->fd_ncand = nks;
+        out->fd_best = fbi;
+        size_t items = 0;
+        for (int k = 0; k < P->d; ++k) items += P->fd[k].size();
+        out->fd_nitems = (int)items;
     }
     return SGIGA_OK;
+}
+
+int sgiga_set_precond_split(sgiga_plan_t P, int ks) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (ks < 16 || ks > 4096 || ks % 16) return fail(SGIGA_ERR_ARG, "ks must be a multiple of 16 in [16, 4096]");
+    return refd(P, ks);
 }
 
 int sgiga_set_solver_options(sgiga_plan_t P, int use_graph, double inner_tol, int inner_max) {

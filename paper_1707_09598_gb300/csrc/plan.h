@@ -46,6 +46,7 @@ struct sgiga_plan_s {
     Patch patch;
     long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
     int maxE = 1;
+    int fd_ks = 128;            // contraction depth per preconditioner work item
     size_t smem = 0;
     std::vector<void*> allocs;
     DevPlan dp;

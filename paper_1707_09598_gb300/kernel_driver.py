@@ -3,7 +3,8 @@ and profiler captures of a single kernel family).
 
   python -m paper_1707_09598_gb300.kernel_driver --op apply --reps 3 [--d 3 --p 3 --w 10]
 
-Ops: apply (stiffness apply), precond (fast diagonalisation), rhs (load
+Ops: apply (stiffness apply), apply_f32 / precond_f32 (the FP32 kernels of
+the mixed-precision plan), precond (fast diagonalisation), rhs (load
 vector), solve (batched PCG), eval (evaluation + combination on the 17^d
 lattice). Prints the mean CUDA-event time per repetition.
 """
@@ -23,7 +24,8 @@ from paper_1707_09598_gb300.inputs import eval_points, random_vector  # noqa: E4
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="apply", choices=["apply", "precond", "rhs", "solve", "eval"])
+    ap.add_argument("--op", default="apply", choices=["apply", "apply_f32", "precond", "precond_f32", "rhs", "solve",
+                                                      "eval"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--p", type=int, default=3)
@@ -31,9 +33,12 @@ def main():
     ap.add_argument("--domain", default="unit")
     a = ap.parse_args()
     stream = torch.cuda.Stream()
-    P = sgiga.Plan(a.d, a.p, a.w, domain=a.domain, stream=stream)
+    f32 = a.op.endswith("_f32")
+    P = sgiga.Plan(a.d, a.p, a.w, domain=a.domain, stream=stream, precision="mixed" if f32 else "fp64")
     n = P.info.ndof
     x = torch.as_tensor(random_vector(n, 1), device="cuda")
+    if f32:
+        x = x.float()
     y = torch.zeros_like(x)
     src = "sine" if a.domain == "unit" else "annulus_paper"
     sgiga.sgiga_set_rhs_builtin(P.handle, src)
@@ -44,6 +49,10 @@ def main():
     def op():
         if a.op == "apply":
             sgiga.sgiga_apply(P.handle, x, y)
+        elif a.op == "apply_f32":
+            sgiga.sgiga_apply_f32(P.handle, x, y)
+        elif a.op == "precond_f32":
+            sgiga.sgiga_precond_f32(P.handle, x, y)
         elif a.op == "precond":
             sgiga.sgiga_precond(P.handle, x, y)
         elif a.op == "rhs":

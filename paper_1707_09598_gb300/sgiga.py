@@ -71,7 +71,9 @@ class sgiga_train_stats(ctypes.Structure):
 
 class sgiga_tune_result(ctypes.Structure):
     _fields_ = [("ncand", ctypes.c_int), ("best", ctypes.c_int), ("ntiles", ctypes.c_int), ("best_ms", ctypes.c_double),
-                ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8)]
+                ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8),
+                ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
+                ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8)]
 
 
 class sgiga_solve_stats(ctypes.Structure):
@@ -96,6 +98,8 @@ _SIGS = {
     "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
     "sgiga_apply_f32": (_I, [_P, _P, _P]),
+    "sgiga_set_precond_split": (_I, [_P, _I]),
+    "sgiga_precond_f32": (_I, [_P, _P, _P]),
     "sgiga_precond": (_I, [_P, _P, _P]),
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
     "sgiga_set_solver_options": (_I, [_P, _I, _D, _I]),
@@ -253,10 +257,23 @@ def sgiga_precond(plan, r, z):
     _check(_lib.sgiga_precond(plan, _ptr(r, n), _ptr(z, n)))
 
 
+def sgiga_precond_f32(plan, r, z):
+    import torch
+    n = sgiga_plan_info(plan).ndof
+    for t in (r, z):
+        if not (hasattr(t, "dtype") and t.dtype == torch.float32 and t.is_contiguous() and t.numel() >= n):
+            raise TypeError("expected contiguous float32 tensors of %d entries" % n)
+    _check(_lib.sgiga_precond_f32(plan, r.data_ptr(), z.data_ptr()))
+
+
 def sgiga_autotune(plan, reps=3):
     out = sgiga_tune_result()
     _check(_lib.sgiga_autotune(plan, int(reps), ctypes.byref(out)))
     return out
+
+
+def sgiga_set_precond_split(plan, ks):
+    _check(_lib.sgiga_set_precond_split(plan, int(ks)))
 
 
 def sgiga_set_solver_options(plan, use_graph=True, inner_tol=1e-5, inner_max=100):

@@ -14,7 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import combination, geometry, problems  # noqa: E402
+from oracle import combination, fd, geometry, problems  # noqa: E402
 from oracle.galerkin import Component  # noqa: E402
 from paper_1707_09598_gb300.inputs import eval_points, random_points, random_vector  # noqa: E402
 
@@ -62,6 +62,27 @@ def test_fp32_apply(sg, case):
             ref = comp.K @ x[sl].astype(np.float32).astype(np.float64)
             # FP32 data and accumulation: error a few ulp of the operator's scale
             assert _rel(y[sl], ref) < 2e-5, (g.levels[:d], _rel(y[sl], ref))
+
+
+@pytest.mark.parametrize("case", CASES[:2])
+def test_fp32_preconditioner(sg, case):
+    """FP32 fast diagonalisation against the oracle's FP64 one: the error is the
+    FP32 rounding of the eigenvectors and of the mode products."""
+    domain, d, p, w, grading, gamma, src, pname = case
+    with sg.Plan(d, p, w, domain=domain, grading=grading, gamma=gamma, precision="mixed") as P:
+        n = P.info.ndof
+        rv = random_vector(n, seed=43)
+        z = torch.zeros(n, dtype=torch.float32, device="cuda")
+        sg.sgiga_precond_f32(P.handle, torch.as_tensor(rv, dtype=torch.float32, device="cuda"), z)
+        z = z.double().cpu().numpy()
+        geom = geometry.make(domain, d)
+        for g in P.grids[:: max(1, len(P.grids) // 5)]:
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            ref = fd.fd_apply(tuple(g.levels[:d]), p, p - 1, rv[sl].astype(np.float32).astype(np.float64),
+                              kind=grading, gamma=gamma, geom=geom)
+            assert _rel(z[sl], ref) < 1e-4, (g.levels[:d], _rel(z[sl], ref))
+        with pytest.raises(TypeError):
+            sg.sgiga_precond_f32(P.handle, torch.zeros(n, dtype=torch.float64, device="cuda"), z)
 
 
 @pytest.mark.parametrize("case", CASES)

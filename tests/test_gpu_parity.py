@@ -197,6 +197,35 @@ def test_preconditioner(sg, case):
             assert _rel(z[sl], ref) < 1e-11, (g.levels[:d], _rel(z[sl], ref))
 
 
+@pytest.mark.parametrize("ks", [16, 32, 64, 128, 256])
+def test_preconditioner_split_depths(sg, ks):
+    """Long 1D contractions (ROWS and TILE items, split into ks-deep partial
+    sums added atomically) give the oracle's FD result at every depth."""
+    case = ("unit", 3, 3, 2, 10, "uniform", 1.0, 1)
+    with _plan(sg, case) as P:
+        sg.sgiga_set_precond_split(P.handle, ks)
+        n = P.info.ndof
+        rv = random_vector(n, seed=13)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_precond(P.handle, _dev(rv), z)
+        z = z.cpu().numpy()
+        # components whose long direction is split: ROWS (few columns) and TILE (>= 64 columns)
+        pick = [(8, 1, 1), (1, 9, 1), (6, 4, 2), (2, 3, 7), (7, 2, 2), (4, 4, 4)]
+        seen = 0
+        for g in P.grids:
+            lv = tuple(g.levels[:3])
+            if lv not in pick:
+                continue
+            seen += 1
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            ref = fd.fd_apply(lv, 3, 2, rv[sl], kind="uniform", gamma=1.0, geom=None)
+            assert _rel(z[sl], ref) < 1e-11, (lv, ks, _rel(z[sl], ref))
+        assert seen == len(pick)
+    with _plan(sg, case) as P:
+        with pytest.raises(sg.SgigaError):
+            sg.sgiga_set_precond_split(P.handle, 24)
+
+
 def test_eigenpairs(sg):
     case = ("unit", 3, 3, 2, 10, "uniform", 1.0, 1)
     with _plan(sg, case) as P:
@@ -384,8 +413,15 @@ def test_autotune_keeps_the_operator(sg):
         x = _dev(random_vector(n, 61))
         y0 = torch.zeros_like(x)
         sg.sgiga_apply(P.handle, x, y0)
+        rv = _dev(random_vector(n, 62))
+        z0 = torch.zeros_like(x)
+        sg.sgiga_precond(P.handle, rv, z0)
         res = sg.sgiga_autotune(P.handle, reps=2)
         assert res.ncand >= 4 and 0 <= res.best < res.ncand and res.best_ms > 0
+        assert res.fd_ncand == 4 and 0 <= res.fd_best < 4 and res.fd_ms[res.fd_best] > 0 and res.fd_nitems > 0
+        z1 = torch.zeros_like(x)
+        sg.sgiga_precond(P.handle, rv, z1)
+        assert _rel(z1.cpu().numpy(), z0.cpu().numpy()) < 1e-13
         y1 = torch.zeros_like(x)
         sg.sgiga_apply(P.handle, x, y1)
         assert _rel(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-13
