@@ -154,8 +154,8 @@ class Component:
             nb, nq = W.shape
             J = self.geom.jacobian(Xi).reshape(nb, nq, d, d)
             det = np.linalg.det(J)
-            if np.any(det <= 0):
-                raise ValueError("non-positive Jacobian determinant")
+            if not (np.all(det > 0) or np.all(det < 0)):
+                raise ValueError("Jacobian determinant vanishes or changes sign")
             JtJinv = np.linalg.inv(np.einsum("eqik,eqil->eqkl", J, J))
             coef = (W * np.abs(det))
             x = self.geom.map(Xi)

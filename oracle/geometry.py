@@ -153,6 +153,27 @@ class BSplinePatch:
         return np.ones_like(t), np.zeros_like(t)
 
 
+class AxisMap:
+    """x = s * xi with s in {-1, 1}^d: the unit square or cube reflected along
+    the directions with s_k = -1 (a bilinear patch of the L-shaped domain;
+    its Jacobian diag(s) may reverse orientation)."""
+
+    def __init__(self, signs):
+        self.s = np.asarray(signs, dtype=np.float64)
+        self.d = len(self.s)
+
+    def map(self, xi):
+        return np.asarray(xi, dtype=np.float64) * self.s[None, :]
+
+    def jacobian(self, xi):
+        n = np.asarray(xi).shape[0]
+        return np.broadcast_to(np.diag(self.s), (n, self.d, self.d)).copy()
+
+    def weight_1d(self, k, t):
+        t = np.asarray(t, dtype=np.float64)
+        return np.ones_like(t), np.zeros_like(t)
+
+
 def lognormal_coefficient(omega, phase, amp):
     """a(x) = exp(amp * sum_f cos(omega_f . x + phase_f)) (random Fourier features)."""
     omega = np.asarray(omega, dtype=np.float64)

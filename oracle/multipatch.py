@@ -1,0 +1,278 @@
+"""Multi-patch components: the L-shaped domain with Dirichlet data.
+
+TEST INFRASTRUCTURE: see the package header. Not in the paper's experiments
+(its multi-patch example, the horseshoe, is out of scope); the L-shape is a
+standard singular test of graded meshes, which is the paper's topic in
+Sec. 4.4.
+
+Domain (-1,1)^2 minus [0,1] x [-1,0], split into three unit squares. Each
+one is the image of [0,1]^2 under x = s * xi, with the parametric origin at
+the re-entrant corner (0,0):
+
+    patch 0: (0,1) x (0,1),    s = ( 1,  1)
+    patch 1: (-1,0) x (0,1),   s = (-1,  1)
+    patch 2: (-1,0) x (-1,0),  s = (-1, -1)
+
+Interfaces: side xi_1 = 0 of patches 0 and 1 (the segment x = 0, 0 < y < 1,
+with the same parameter xi_2 on both); side xi_2 = 0 of patches 1 and 2
+(y = 0, -1 < x < 0, same xi_1). Every other side is a Dirichlet side. A
+component (i_1, i_2) uses the same knot vector of level i_k in direction k on
+every patch, graded toward xi_k = 0 (the corner). The two traces on an
+interface are then the same 1D spline space. Conforming C^0 gluing merges
+the trace functions of the two sides into one global function.
+
+Boundary data g (readings; the paper is silent on nonhomogeneous data):
+corner coefficients interpolate g at the patch corners. The remaining
+coefficients of each Dirichlet side are the L2 projection of g onto the
+side's 1D spline space, with the corner coefficients fixed. The projection
+uses the parametric measure, which is arc length for these unit sides, and
+p+1 Gauss points per element, the rule of the assembly. Then
+b_I <- b_I - K_IB g_B.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import spline
+from .galerkin import Component
+from .geometry import AxisMap
+
+SIGNS = ((1.0, 1.0), (-1.0, 1.0), (-1.0, -1.0))
+# Dirichlet sides per patch: (direction, end) with end 0 at xi_k = 0, 1 at xi_k = 1
+DIRICHLET = (((1, 0), (0, 1), (1, 1)),           # patch 0: y = 0 (x > 0), x = 1, y = 1
+             ((0, 1), (1, 1)),                   # patch 1: x = -1, y = 1
+             ((0, 0), (0, 1), (1, 1)))           # patch 2: x = 0 (y < 0), x = -1, y = -1
+# interface sides: (patch a, patch b, direction whose index is 0 on the side)
+INTERFACES = ((0, 1, 0), (1, 2, 1))
+
+
+def physical(patch, xi):
+    return np.asarray(xi, dtype=np.float64) * np.asarray(SIGNS[patch])[None, :]
+
+
+class LShapeComponent:
+    """Glued, Dirichlet-lifted system of one component grid on the L-shape."""
+
+    def __init__(self, levels, p, r=None, kind="onesided", gamma=1.0):
+        self.levels = tuple(int(v) for v in levels)
+        self.p = p
+        self.r = p - 1 if r is None else r
+        self.kind, self.gamma = kind, gamma
+        self.patches = [Component(AxisMap(s), self.levels, p, self.r, kind, gamma) for s in SIGNS]
+        self.nf = self.patches[0].nf                     # functions per direction (same on every patch)
+        nf0, nf1 = self.nf
+        # global ids of each patch's functions, local full index a + nf0 * b
+        ids = []
+        nxt = 0
+        for q in range(3):
+            gid = -np.ones(nf0 * nf1, dtype=np.int64)
+            for (pa, pb, k) in INTERFACES:
+                if pb != q:
+                    continue
+                # the side with index 0 in direction k: copy the ids of patch pa
+                for t in range(self.nf[1 - k]):
+                    loc = (0 + nf0 * t) if k == 0 else (t + nf0 * 0)
+                    gid[loc] = ids[pa][loc]
+            new = gid < 0
+            gid[new] = nxt + np.arange(new.sum())
+            nxt += int(new.sum())
+            ids.append(gid)
+        self.ids = ids
+        self.nglob = nxt
+        dirich = np.zeros(nxt, dtype=bool)
+        for q in range(3):
+            for (k, end) in DIRICHLET[q]:
+                dirich[ids[q][self._side(k, end)]] = True
+        self.dirichlet = dirich
+        self.interior = np.nonzero(~dirich)[0]
+        self.boundary = np.nonzero(dirich)[0]
+        self.ndof = len(self.interior)
+
+    def _side(self, k, end):
+        """Local full indices of the functions on side (k, end), ordered along the side."""
+        nf0, nf1 = self.nf
+        i = 0 if end == 0 else self.nf[k] - 1
+        t = np.arange(self.nf[1 - k])
+        return (i + nf0 * t) if k == 0 else (t + nf0 * i)
+
+    # -- assembly ---------------------------------------------------------------
+    def assemble(self, f=None, g=None):
+        """Glued stiffness over all functions, load vector, boundary lifting.
+
+        f(x) is the source (None: 0); g(x) the Dirichlet data (None: 0)."""
+        rows, cols, vals = [], [], []
+        b = np.zeros(self.nglob)
+        for q in range(3):
+            comp = self.patches[q].assemble(f=f if f is not None else (lambda x: np.zeros(len(x))))
+            Kf = comp.K_full.tocoo()
+            rows.append(self.ids[q][Kf.row])
+            cols.append(self.ids[q][Kf.col])
+            vals.append(Kf.data)
+            np.add.at(b, self.ids[q], comp.b_full)
+        K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.nglob, self.nglob))
+        self.K_glob = K
+        self.gB = self.boundary_coefficients(g)
+        I, B = self.interior, self.boundary
+        self.K = K[I][:, I].tocsc()
+        self.b = b[I] - K[I][:, B] @ self.gB[B]
+        return self
+
+    def boundary_coefficients(self, g):
+        """Global coefficient vector holding g's lifting on the Dirichlet functions."""
+        c = np.zeros(self.nglob)
+        if g is None:
+            return c
+        for q in range(3):
+            for (k, end) in DIRICHLET[q]:
+                sp1 = self.patches[q].spaces[1 - k]           # the side's parameter direction
+                side = self._side(k, end)
+                xi_fixed = 0.0 if end == 0 else 1.0
+                coef = self._project(sp1, lambda t: g(physical(q, self._side_points(k, xi_fixed, t))))
+                c[self.ids[q][side]] = coef
+        return c
+
+    @staticmethod
+    def _side_points(k, fixed, t):
+        pts = np.zeros((len(t), 2))
+        pts[:, k] = fixed
+        pts[:, 1 - k] = t
+        return pts
+
+    def _project(self, s, gfun):
+        """Coefficients c_0..c_{nf-1} on one side: ends interpolate g, the
+        interior ones are the L2 projection (p+1 Gauss points per element)."""
+        p, nf = self.p, s.nf
+        M = np.zeros((nf, nf))
+        rhs = np.zeros(nf)
+        for e in range(s.E):
+            idx = s.first[e] + np.arange(p + 1)
+            gv = gfun(s.xi[e])
+            for qq in range(s.Q):
+                M[np.ix_(idx, idx)] += s.w[e, qq] * np.outer(s.R[e, qq], s.R[e, qq])
+                rhs[idx] += s.w[e, qq] * gv[qq] * s.R[e, qq]
+        c = np.zeros(nf)
+        c[0] = gfun(np.array([0.0]))[0]
+        c[-1] = gfun(np.array([1.0]))[0]
+        inner = slice(1, nf - 1)
+        r = rhs[inner] - M[inner, 0] * c[0] - M[inner, -1] * c[-1]
+        c[inner] = np.linalg.solve(M[inner, inner], r)
+        return c
+
+    def solve(self, b=None):
+        """Sparse direct solve of the interior system; returns the interior coefficients."""
+        return spla.splu(self.K).solve(self.b if b is None else b)
+
+    def full(self, u):
+        """Global coefficients: interior from u, boundary from the lifting."""
+        c = self.gB.copy()
+        c[self.interior] = u
+        return c
+
+    # -- evaluation -------------------------------------------------------------
+    def evaluate(self, u, patch, xi):
+        """Values and physical gradients of the glued solution at parametric
+        points xi [P, 2] of the given patches [P]."""
+        c = self.full(u)
+        patch = np.asarray(patch)
+        xi = np.asarray(xi, dtype=np.float64)
+        val = np.zeros(len(xi))
+        grad = np.zeros((len(xi), 2))
+        for q in range(3):
+            sel = np.nonzero(patch == q)[0]
+            if len(sel) == 0:
+                continue
+            C = c[self.ids[q]].reshape(self.nf[1], self.nf[0])
+            comp = self.patches[q]
+            v0 = comp.spaces[0].values_at(xi[sel, 0])
+            v1 = comp.spaces[1].values_at(xi[sel, 1])
+            d0 = comp.spaces[0].derivs_at(xi[sel, 0])
+            d1 = comp.spaces[1].derivs_at(xi[sel, 1])
+            val[sel] = np.einsum("pj,ji,pi->p", v1, C, v0)
+            g0 = np.einsum("pj,ji,pi->p", v1, C, d0)
+            g1 = np.einsum("pj,ji,pi->p", d1, C, v0)
+            s = SIGNS[q]                                     # J = diag(s), grad_x = J^{-T} grad_xi
+            grad[sel, 0] = g0 * s[0]
+            grad[sel, 1] = g1 * s[1]
+        return val, grad
+
+
+def error_points(nel=64, nq=4):
+    """Gauss points and weights of a uniform nel x nel mesh on every patch:
+    (patch ids, parametric points, weights); |det J| = 1 on every patch."""
+    z = np.linspace(0.0, 1.0, nel + 1)
+    x, w = spline.element_quadrature(z, nq)
+    x, w = x.reshape(-1), w.reshape(-1)
+    X0, X1 = np.meshgrid(x, x, indexing="xy")
+    W = np.outer(w, w)
+    pts = np.stack([X0.reshape(-1), X1.reshape(-1)], 1)
+    ww = W.reshape(-1)
+    P = np.concatenate([np.full(len(pts), q) for q in range(3)])
+    return P, np.concatenate([pts] * 3), np.concatenate([ww] * 3)
+
+
+def errors(val, grad, u, du, patch, xi, w):
+    """L2 norm and H1 seminorm of (u_h - u) by quadrature on the error points."""
+    x = np.concatenate([physical(q, xi[patch == q]) for q in range(3)])
+    order = np.concatenate([np.nonzero(patch == q)[0] for q in range(3)])
+    ex = np.empty(len(xi))
+    ex[order] = u(x)
+    dex = np.empty((len(xi), 2))
+    dex[order] = du(x)
+    l2 = np.sqrt(np.sum(w * (val - ex) ** 2))
+    h1 = np.sqrt(np.sum(w * np.sum((grad - dex) ** 2, axis=1)))
+    return l2, h1
+
+
+# -- the data of the L-shape workload ------------------------------------------------
+
+def theta(x):
+    """Polar angle in [0, 2pi) measured from the positive x axis."""
+    t = np.arctan2(x[:, 1], x[:, 0])
+    return np.where(t < 0, t + 2 * np.pi, t)
+
+
+def corner_u(x):
+    """u = r^(2/3) sin(2 theta / 3): harmonic, zero on the two sides at the corner."""
+    r = np.hypot(x[:, 0], x[:, 1])
+    return r ** (2.0 / 3.0) * np.sin(2.0 * theta(x) / 3.0)
+
+
+def corner_grad(x):
+    r = np.hypot(x[:, 0], x[:, 1])
+    th = theta(x)
+    ur = (2.0 / 3.0) * r ** (-1.0 / 3.0) * np.sin(2.0 * th / 3.0)
+    ut = (2.0 / 3.0) * r ** (-1.0 / 3.0) * np.cos(2.0 * th / 3.0)   # (1/r) du/dtheta
+    c, s = np.cos(th), np.sin(th)
+    return np.stack([ur * c - ut * s, ur * s + ut * c], 1)
+
+
+def harmonic_quadratic(x):
+    """u = 1 + 2x - 3y + (x^2 - y^2)/2 + xy: harmonic, in every p >= 2 space of
+    the affine patches."""
+    X, Y = x[:, 0], x[:, 1]
+    return 1.0 + 2.0 * X - 3.0 * Y + 0.5 * (X * X - Y * Y) + X * Y
+
+
+def solve_combination(w, p=2, kind="onesided", gamma=1.0, g=corner_u, min_level=1):
+    """Solve every component of level w (2D) on the L-shape; returns
+    [(levels, coefficient, component, interior solution)]."""
+    from .combination import index_set
+    out = []
+    for i, c in index_set(2, w, min_level):
+        comp = LShapeComponent(i, p, kind=kind, gamma=gamma).assemble(g=g)
+        out.append((i, c, comp, comp.solve()))
+    return out
+
+
+def combined(results, patch, xi):
+    """Combined values and physical gradients sum_i c_i u_i (Neumaier-compensated)."""
+    from .combination import combine
+    vals, g0, g1, coef = [], [], [], []
+    for (_, c, comp, u) in results:
+        v, gr = comp.evaluate(u, patch, xi)
+        vals.append(v)
+        g0.append(gr[:, 0])
+        g1.append(gr[:, 1])
+        coef.append(c)
+    return combine(vals, coef), np.stack([combine(g0, coef), combine(g1, coef)], 1)

@@ -881,10 +881,10 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     }
     if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap);
     // preconditioner item depth
-    const int ks_c[] = {32, 64, 128, 256};
+    const int ks_c[] = {16, 32, 64, 128, 256};
     const int nks = (int)(sizeof(ks_c) / sizeof(ks_c[0]));
     double fbest = 1e30;
-    int fbi = 2;
+    int fbi = 3;
     for (int i = 0; i < nks && rc == SGIGA_OK; ++i) {
         if ((rc = refd(P, ks_c[i]))) break;
         // the precision the plan's CG runs in; plain FD (no learned correction)

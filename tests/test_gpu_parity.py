@@ -418,7 +418,7 @@ def test_autotune_keeps_the_operator(sg):
         sg.sgiga_precond(P.handle, rv, z0)
         res = sg.sgiga_autotune(P.handle, reps=2)
         assert res.ncand >= 4 and 0 <= res.best < res.ncand and res.best_ms > 0
-        assert res.fd_ncand == 4 and 0 <= res.fd_best < 4 and res.fd_ms[res.fd_best] > 0 and res.fd_nitems > 0
+        assert res.fd_ncand == 5 and 0 <= res.fd_best < 5 and res.fd_ms[res.fd_best] > 0 and res.fd_nitems > 0
         z1 = torch.zeros_like(x)
         sg.sgiga_precond(P.handle, rv, z1)
         assert _rel(z1.cpu().numpy(), z0.cpu().numpy()) < 1e-13
