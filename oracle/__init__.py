@@ -17,6 +17,11 @@ Modules
   fd           fast-diagonalisation preconditioner written from its
                definition (not in the paper; the CUDA preconditioner's
                definition, cross-checked against the direct solve)
+  multipatch   the L-shaped domain: three glued bilinear patches, Dirichlet
+               lifting by edge L2 projection, L2/H1 errors (not in the
+               paper's experiments; its graded-mesh topic, Sec. 4.4)
+  net          the learned correction network's forward and backward (not in
+               the paper; the CUDA network's definition)
   problems     manufactured solutions; f = -Laplace(u) derived symbolically
   driver       whole-method runs: solve every component, evaluate, combine
 

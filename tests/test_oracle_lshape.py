@@ -1,0 +1,130 @@
+"""Pins of the oracle's L-shaped domain (three glued bilinear patches,
+nonhomogeneous Dirichlet data, one-sided grading toward the re-entrant corner).
+
+What fixes the oracle here, independently of its own code:
+- exact reproduction: a harmonic quadratic lies in every p >= 2 space of the
+  affine patches. Its traces are quadratics that the edge projection
+  reproduces exactly, so every component and the combination equal it to
+  rounding;
+- gluing: the glued stiffness over all functions annihilates constants and is
+  symmetric;
+- symmetry: the data r^(2/3) sin(2 theta/3) is invariant under the
+  reflection (x, y) -> (-y, -x). The reflection maps patch 0 to patch 2 and
+  patch 1 to itself, and swaps the two parametric directions, so component
+  (i1, i2) on one side equals component (i2, i1) on the other;
+- the corner singularity: on uniform meshes the H1 error of the full tensor
+  solve decays like h^(2/3) and the L2 error like h^(4/3) (the regularity of
+  r^(2/3)); grading toward the corner raises the rate of the combined
+  solution (the trend of the paper's graded-mesh experiments, Sec. 4.4).
+"""
+import numpy as np
+import pytest
+
+from oracle import multipatch as mp
+from oracle.driver import rate
+
+
+def _pts(n=6, seed=0):
+    rng = np.random.default_rng(seed)
+    xi = rng.random((3 * n, 2))
+    patch = np.repeat(np.arange(3), n)
+    return patch, xi
+
+
+def _exact(fun, patch, xi):
+    out = np.empty(len(xi))
+    for q in range(3):
+        sel = patch == q
+        out[sel] = fun(mp.physical(q, xi[sel]))
+    return out
+
+
+def _grad_hq(x):
+    X, Y = x[:, 0], x[:, 1]
+    return np.stack([2.0 + X + Y, -3.0 - Y + X], 1)
+
+
+@pytest.mark.parametrize("levels,gamma", [((2, 3), 1.0), ((3, 1), 2.0), ((1, 1), 3.0)])
+def test_harmonic_quadratic_reproduced(levels, gamma):
+    c = mp.LShapeComponent(levels, 2, kind="onesided", gamma=gamma).assemble(g=mp.harmonic_quadratic)
+    u = c.solve()
+    patch, xi = _pts()
+    v, g = c.evaluate(u, patch, xi)
+    assert np.abs(v - _exact(mp.harmonic_quadratic, patch, xi)).max() < 1e-12
+    gx = np.empty((len(xi), 2))
+    for q in range(3):
+        sel = patch == q
+        gx[sel] = _grad_hq(mp.physical(q, xi[sel]))
+    assert np.abs(g - gx).max() < 1e-11
+
+
+def test_harmonic_quadratic_combination_reproduced():
+    res = mp.solve_combination(4, 2, gamma=2.0, g=mp.harmonic_quadratic)
+    patch, xi = _pts(8, 1)
+    v, _ = mp.combined(res, patch, xi)
+    assert np.abs(v - _exact(mp.harmonic_quadratic, patch, xi)).max() < 1e-12
+
+
+def test_gluing_constants_and_symmetry():
+    c = mp.LShapeComponent((3, 2), 2, gamma=2.0).assemble()
+    K = c.K_glob
+    assert np.abs(K @ np.ones(c.nglob)).max() < 1e-12
+    assert abs(K - K.T).max() < 1e-14
+    # shared functions: the two interfaces (nf_2 and nf_1 functions) and the
+    # corner function common to all three patches
+    nf0, nf1 = c.nf
+    assert c.nglob == 3 * nf0 * nf1 - nf1 - nf0
+    # Dirichlet count: every side except the two interfaces
+    assert c.ndof == 3 * nf0 * nf1 - nf1 - nf0 - len(c.boundary)
+
+
+def test_reflection_symmetry():
+    a = mp.LShapeComponent((3, 2), 2, gamma=2.0).assemble(g=mp.corner_u)
+    b = mp.LShapeComponent((2, 3), 2, gamma=2.0).assemble(g=mp.corner_u)
+    ua, ub = a.solve(), b.solve()
+    rng = np.random.default_rng(3)
+    xi = rng.random((20, 2))
+    sw = xi[:, ::-1].copy()
+    va0, _ = a.evaluate(ua, np.zeros(20, int), xi)
+    vb2, _ = b.evaluate(ub, np.full(20, 2), sw)
+    assert np.abs(va0 - vb2).max() < 1e-12
+    va1, _ = a.evaluate(ua, np.ones(20, int), xi)
+    vb1, _ = b.evaluate(ub, np.ones(20, int), sw)
+    assert np.abs(va1 - vb1).max() < 1e-12
+
+
+def test_corner_data_vanishes_on_the_corner_sides():
+    x = np.array([[0.3, 0.0], [0.0, -0.4], [1.0, 0.0], [0.0, -1.0]])
+    assert np.abs(mp.corner_u(x)).max() < 1e-15
+    # harmonic: the 5-point Laplacian of r^(2/3) sin(2 theta/3) vanishes to O(h^2)
+    h = 1e-3
+    p = np.array([[-0.4, 0.3]])
+    lap = sum(mp.corner_u(p + np.array([s])) for s in ([h, 0], [-h, 0], [0, h], [0, -h])) - 4 * mp.corner_u(p)
+    assert abs(lap[0]) / h ** 2 < 1e-4
+
+
+def test_uniform_full_tensor_rates_follow_the_corner_regularity():
+    P, xi, w = mp.error_points(32, 4)
+    L, H, lv = [], [], [3, 4, 5, 6]
+    for l in lv:
+        c = mp.LShapeComponent((l, l), 2, kind="uniform").assemble(g=mp.corner_u)
+        v, g = c.evaluate(c.solve(), P, xi)
+        l2, h1 = mp.errors(v, g, mp.corner_u, mp.corner_grad, P, xi, w)
+        L.append(l2)
+        H.append(h1)
+    assert 0.55 < rate(lv, H) < 0.8          # h^(2/3)
+    assert 1.1 < rate(lv, L) < 1.6           # h^(4/3)
+
+
+def test_grading_raises_the_combined_rate():
+    P, xi, w = mp.error_points(32, 4)
+    ws = [3, 4, 5, 6]
+    rates = {}
+    for gamma in (1.0, 3.0):
+        H = []
+        for W in ws:
+            res = mp.solve_combination(W, 2, gamma=gamma)
+            v, g = mp.combined(res, P, xi)
+            H.append(mp.errors(v, g, mp.corner_u, mp.corner_grad, P, xi, w)[1])
+        rates[gamma] = rate(ws, H)
+    assert rates[3.0] > rates[1.0] + 0.4, rates
