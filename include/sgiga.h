@@ -53,8 +53,24 @@ typedef enum {
 /* Domains. UNIT: identity map on [0,1]^d. ANNULUS: quarter annulus with radii
  * 1 and 2 as a NURBS patch (direction 1 radial, degree 1; direction 2 angular,
  * degree 2, weights 1, sqrt(2)/2, 1), extruded along z in [0,1] when d = 3
- * (Sec. 4.2). */
-enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1, SGIGA_DOMAIN_PATCH = 2 };
+ * (Sec. 4.2). LSHAPE (d = 2): (-1,1)^2 minus [0,1] x [-1,0] as three glued
+ * bilinear patches x = s * xi with the parametric origin at the re-entrant
+ * corner: patch 0 (0,1)x(0,1), s = (1,1); patch 1 (-1,0)x(0,1), s = (-1,1);
+ * patch 2 (-1,0)x(-1,0), s = (-1,-1). Interfaces: xi_1 = 0 of patches 0 and
+ * 1, xi_2 = 0 of patches 1 and 2 (conforming C^0 gluing); every other side is
+ * a Dirichlet side. Every component uses the same knots on the three
+ * patches; grading maps toward xi_k = 0 (use ONESIDED for the corner).
+ * Packed layout of a component: blocks of patch 0, 1, 2; patch q's block
+ * holds its functions (f_0, f_1) (full 1D indices, direction 0 fastest) with
+ * s_0 <= f_0 <= nf_0 - 2 and s_1 <= f_1 <= nf_1 - 2, (s_0, s_1) = (0,1), (1,0),
+ * (1,1) for q = 0, 1, 2. An interface function is stored once: f_0 = 0 of
+ * patches 0 and 1 in patch 0's block, f_1 = 0 of patches 1 and 2 in patch 1's
+ * block.
+ * Preconditioner: weighted additive Schwarz over the patches (Neumann-Neumann
+ * weights 1/2 on interface functions) with one exact fast-diagonalisation
+ * solve per patch. The paper's graded-mesh experiments (Sec. 4.4) motivate
+ * this domain; it is not among them. */
+enum { SGIGA_DOMAIN_UNIT = 0, SGIGA_DOMAIN_ANNULUS = 1, SGIGA_DOMAIN_PATCH = 2, SGIGA_DOMAIN_LSHAPE = 3 };
 
 /* A user geometry for SGIGA_DOMAIN_PATCH (eq. F-B-splines): a tensor-product
  * B-spline/NURBS patch with per-direction degree (<= 3), open knot vector
@@ -94,9 +110,15 @@ enum { SGIGA_PRECOND_FD = 0, SGIGA_PRECOND_NONE = 1, SGIGA_PRECOND_LEARNED = 2 }
  * POLY      u = prod_k x_k (1 - x_k)
  * ANNULUS   u = x y (x^2+y^2-1)(x^2+y^2-4) sin(x)        (d = 2)
  * ANNULUS_PAPER u = -(x^2+y^2-1)(x^2+y^2-4) x y^2 [sin(pi z)]  (Sec. 4.2)
- * ONE       f = 1 */
+ * ONE       f = 1
+ * With Dirichlet data (LSHAPE plans; f = 0, u = g on the Dirichlet sides):
+ * LSHAPE_CORNER  u = r^(2/3) sin(2 theta / 3), theta in [0, 2 pi) from the
+ *                positive x axis (harmonic; singular gradient at the corner)
+ * HARMONIC_QUADRATIC u = 1 + 2x - 3y + (x^2 - y^2)/2 + xy (in every p >= 2
+ *                space of the L-shape: reproduced exactly) */
 enum { SGIGA_SRC_SINE = 0, SGIGA_SRC_POLY = 1, SGIGA_SRC_ANNULUS = 2,
-       SGIGA_SRC_ANNULUS_PAPER = 3, SGIGA_SRC_ONE = 4 };
+       SGIGA_SRC_ANNULUS_PAPER = 3, SGIGA_SRC_ONE = 4, SGIGA_SRC_LSHAPE_CORNER = 5,
+       SGIGA_SRC_HARMONIC_QUADRATIC = 6 };
 
 typedef struct {
     int d;            /* 2 or 3 */
@@ -120,6 +142,8 @@ typedef struct {
     int ntiles;
     int diag_metric;   /* 1 if every off-diagonal geometry coefficient is exactly zero
                           (the operator kernels then skip the cross terms) */
+    int npatches;      /* geometry patches (3 for LSHAPE, else 1) */
+    long long nbpts;   /* boundary data points (sgiga_boundary_points), 0 if none */
 } sgiga_info;
 
 typedef struct {
@@ -166,8 +190,25 @@ int sgiga_qp_coords(sgiga_plan_t plan, double* xq);
 int sgiga_set_rhs(sgiga_plan_t plan, const double* f_qp);
 
 /* Same, with f from a built-in manufactured solution (SGIGA_SRC_*),
- * evaluated on the device. */
+ * evaluated on the device. The two sources with Dirichlet data (LSHAPE plans)
+ * also set the boundary data g = u (as sgiga_set_dirichlet). */
 int sgiga_set_rhs_builtin(sgiga_plan_t plan, int source);
+
+/* Nonhomogeneous Dirichlet data of an LSHAPE plan (not in the paper; the
+ * reading of the build): on each Dirichlet side of each component's patch
+ * pieces, the two end coefficients interpolate g and the others are the L2
+ * projection of g onto the side's 1D spline space (parametric measure = arc
+ * length on these unit sides, p+1 Gauss points per element); then the load
+ * vector becomes b_I - K_IB g_B and evaluations include the boundary part.
+ * sgiga_boundary_points writes the physical points where g is needed, xb
+ * [nbpts][2] (host or device; nbpts from sgiga_plan_info): per component,
+ * per piece, per Dirichlet side, the side's two ends then the Gauss points of
+ * its elements; plus one point (the corner) for a piece whose (0,0) function
+ * is fixed by a neighbour's side. sgiga_set_dirichlet takes g at those
+ * points, g [nbpts] (host or device), or NULL for homogeneous data. Call it
+ * before sgiga_set_rhs. SGIGA_ERR_ARG on a plan without boundary data. */
+int sgiga_boundary_points(sgiga_plan_t plan, double* xb);
+int sgiga_set_dirichlet(sgiga_plan_t plan, const double* g);
 
 /* f(x_q) of a built-in source (SGIGA_SRC_*) at every quadrature point, in
  * natural qp order: f is [nqp], host or device (input data for sgiga_set_rhs). */
@@ -267,6 +308,16 @@ int sgiga_set_solution(sgiga_plan_t plan, const double* u);
  * [ngrids][npts] (host or device). A parametric point is the same physical
  * point F(xi) in every component because all share the exact geometry. */
 int sgiga_eval(sgiga_plan_t plan, const double* xi, long long npts, double* u_comp);
+
+/* Values and physical gradients of every component (2D plans, any domain;
+ * the one evaluation of multi-patch plans). xi [npts][2] parametric points,
+ * patch [npts] the patch of each point (NULL: patch 0), u_comp
+ * [ngrids][npts], grad_comp [2][ngrids][npts] (x then y derivative; NULL to
+ * skip), all host or device. grad u = J^{-T} grad_xi u with J the patch's
+ * Jacobian. Values include the Dirichlet lifting where boundary data is set.
+ * SGIGA_ERR_ARG for d = 3 or a patch id out of range. */
+int sgiga_eval_grad(sgiga_plan_t plan, const double* xi, const int* patch, long long npts, double* u_comp,
+                    double* grad_comp);
 
 /* u[j] = sum_g c_g u_comp[g][j], FP64 with Neumaier compensation
  * (eq. TD-combi-tec). u_comp [ngrids][npts], u [npts], host or device. */

@@ -276,3 +276,43 @@ def combined(results, patch, xi):
         g1.append(gr[:, 1])
         coef.append(c)
     return combine(vals, coef), np.stack([combine(g0, coef), combine(g1, coef)], 1)
+
+
+# lowest kept function per direction on each patch: 0 where the low side is a
+# patch interface (natural condition in the local problem), 1 where it is a
+# Dirichlet side
+KEPT_LO = ((0, 1), (0, 0), (1, 0))
+
+
+def schwarz_apply(comp, r):
+    """Weighted additive Schwarz over the patches (the definition the CUDA
+    preconditioner of multi-patch plans implements; not in the paper):
+
+        z = sum_q E_q^T D_q A_q^{-1} D_q E_q r,
+
+    A_q = the patch's stiffness on the tensor set of its functions
+    [lo_0, nf_0 - 2] x [lo_1, nf_1 - 2] (natural condition at interface sides),
+    E_q = restriction of the glued interior vector to that set, zero at a
+    function of the set that is not an unknown (patch 1's corner function);
+    E_q^T adds back and drops that function. D_q = 1 / (number of patches
+    sharing the function): 1/2 on interface functions, the Neumann-Neumann
+    weighting (without it the interface is corrected twice and the condition
+    number grows like h^-2). r is in the component's interior ordering; comp
+    must be assembled."""
+    nf0, nf1 = comp.nf
+    pos = -np.ones(comp.nglob, dtype=np.int64)
+    pos[comp.interior] = np.arange(comp.ndof)
+    z = np.zeros(comp.ndof)
+    for q in range(3):
+        lo0, lo1 = KEPT_LO[q]
+        a, b = np.meshgrid(np.arange(lo0, nf0 - 1), np.arange(lo1, nf1 - 1), indexing="xy")
+        a, b = a.reshape(-1), b.reshape(-1)
+        loc = a + nf0 * b
+        p = pos[comp.ids[q][loc]]                      # -1: not an unknown
+        shared = 1 + ((a == 0) & (lo0 == 0)).astype(int) + ((b == 0) & (lo1 == 0)).astype(int)
+        w = np.where(p >= 0, 1.0 / shared, 0.0)
+        A = comp.patches[q].K_full[loc][:, loc].toarray()
+        zl = np.linalg.solve(A, w * np.where(p >= 0, r[np.maximum(p, 0)], 0.0)) * w
+        ok = p >= 0
+        np.add.at(z, p[ok], zl[ok])
+    return z

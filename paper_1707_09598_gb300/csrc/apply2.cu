@@ -1,6 +1,10 @@
-// 2D matrix-free operator kernel: y = K x (MODE 0) or the load vector (MODE 1)
-// for every component at once (Problem 1, Sec. 2.2, pulled back to the
-// parametric square).
+// 2D matrix-free operator kernel: y = K x (MODE 0), the load vector (MODE 1)
+// or the boundary lifting y -= K_IB g_B (MODE 2: the input is each piece's
+// array of boundary coefficients over all of its functions) for every
+// component at once (Problem 1, Sec. 2.2, pulled back to the parametric
+// square). Multi-patch pieces read and add their interface functions at the
+// address of the piece that stores them (GridDesc), so y is the glued
+// (assembled) result.
 //
 //   grad u(q) = (D_a B_b x, B_a D_b x),  v = G_q grad u,
 //   y = (D_a B_b)^T v_a + (B_a D_b)^T v_b.
@@ -19,10 +23,10 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     Real* sm = reinterpret_cast<Real*>(sm_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
-    if (active && !active[td.grid]) return;
     const GridDesc& g = Pl.grids[td.grid];
+    if (active && !active[g.comp]) return;
     const int M = Pl.m;
-    int ax[2], T[2], L[2], E0[2], NF[2];
+    int ax[2], T[2], L[2], E0[2], NF[2], KLO[2], SLO[2];
     long long ST[2];
     const long long stp[2] = {1, (long long)g.n[0]};
 #pragma unroll
@@ -33,7 +37,23 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         E0[k] = td.e0[ax[k]];
         NF[k] = g.nf[ax[k]];
         ST[k] = stp[ax[k]];
+        KLO[k] = g.klo[ax[k]];
+        SLO[k] = g.slo[ax[k]];
     }
+    // kept function (logical indices) and its packed address
+    const bool plain = g.alias[0] < 0 && g.alias[1] < 0 && !g.xcorner;
+    auto kept = [&](int fa, int fb) {
+        if (fa < KLO[0] || fa > NF[0] - 2 || fb < KLO[1] || fb > NF[1] - 2) return false;
+        if (plain) return true;
+        return !(fa == 0 && fb == 0);   // the excluded corner of a piece is (0,0) in any axis order
+    };
+    auto addr = [&](int fa, int fb) -> long long {
+        if (plain) return g.dof_off + (fa - SLO[0]) * ST[0] + (fb - SLO[1]) * ST[1];
+        int f[2];
+        f[ax[0]] = fa;
+        f[ax[1]] = fb;
+        return piece_addr2(Pl.grids, g, f[0], f[1]);
+    };
     const int Ta = T[0], Tb = T[1], La = L[0], Lb = L[1];
     const int QTb = Q * Tb, npen = QTb, LaP = La | 1;
     Real* tb[2];
@@ -54,16 +74,21 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         const int cnt = T[k] * Q * P1;
         for (int i = tid; i < cnt; i += nth) { tb[k][i] = OpData<Real>::R(Pl)[base + i]; tdv[k][i] = OpData<Real>::dR(Pl)[base + i]; }
     }
-    const long long doff = g.dof_off;
     __syncthreads();   // tables visible to every thread before any stage reads them
-    if (MODE == 0) {
+    if (MODE != 1) {
         const int nX = La * Lb;
         for (int idx = tid; idx < nX; idx += nth) {
             int ja = idx % La, jb = idx / La;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
             Real v = 0.0;
-            if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)
-                v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1]];
+            if (MODE == 2) {   // every function: boundary coefficients (zero on kept functions)
+                int f[2];
+                f[ax[0]] = fa;
+                f[ax[1]] = fb;
+                v = (Real)Pl.gfull[g.gf_off + f[0] + (long long)f[1] * g.nf[0]];
+            } else if (kept(fa, fb)) {
+                v = x[addr(fa, fb)];
+            }
             X[idx] = v;
         }
         __syncthreads();
@@ -99,7 +124,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         for (int ea = 0; ea < Ta; ++ea) {
             const int base = ea * M;
             Real i0[P1], i1[P1];
-            if (MODE == 0) {
+            if (MODE != 1) {
 #pragma unroll
                 for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; }
             }
@@ -108,7 +133,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 const int qa = ea * Q + q;
                 const Real* bt = tb[0] + qa * P1;
                 const Real* dt = tdv[0] + qa * P1;
-                if (MODE == 0) {
+                if (MODE != 1) {
                     Real ga = 0.0, gb = 0.0;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; }
@@ -132,7 +157,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
             }
             for (int u = 0; u < M; ++u) {
                 c0[base + u] = a0[0];
-                if (MODE == 0) c1[base + u] = a1[0];
+                if (MODE != 1) c1[base + u] = a1[0];
 #pragma unroll
                 for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; }
                 a0[P] = a1[P] = 0.0;
@@ -141,7 +166,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         const int base = Ta * M;
         for (int u = 0; u <= P - M; ++u) {
             c0[base + u] = a0[0];
-            if (MODE == 0) c1[base + u] = a1[0];
+            if (MODE != 1) c1[base + u] = a1[0];
 #pragma unroll
             for (int t = 0; t < P; ++t) { a0[t] = a0[t + 1]; a1[t] = a1[t + 1]; }
             a0[P] = a1[P] = 0.0;
@@ -152,7 +177,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     for (int idx = tid; idx < nX; idx += nth) {
         int ja = idx % La, jb = idx / La;
         int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
-        if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2)) continue;
+        if (!kept(fa, fb)) continue;
         int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
         Real yv = 0.0;
         for (int eb = lo; eb <= hi; ++eb) {
@@ -162,10 +187,10 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 const int qb = eb * Q + q;
                 const int o = qb * LaP + ja;
                 yv += tb[1][qb * P1 + t] * S1[o];
-                if (MODE == 0) yv += tdv[1][qb * P1 + t] * S1[S1n + o];
+                if (MODE != 1) yv += tdv[1][qb * P1 + t] * S1[S1n + o];
             }
         }
-        atomicAdd(&y[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1]], yv);
+        atomicAdd(&y[addr(fa, fb)], MODE == 2 ? -yv : yv);
     }
 }
 
@@ -175,6 +200,8 @@ static cudaError_t launch2(const DevPlan& Pl, const double* x, double* y, const 
     SGIGA_COUNT_LAUNCH();
     if (mode == 1)
         k_op2<double, P, 1, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
+    else if (mode == 2)
+        k_op2<double, P, 2, false><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else if (Pl.diag)
         k_op2<double, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op, s>>>(Pl, x, y, active);
     else
@@ -223,6 +250,8 @@ cudaError_t set_op2_smem(int p, size_t bytes) {
             e = cudaFuncSetAttribute(k_op2<double, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(k_op2<double, PP, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op2<double, PP, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(k_op2<float, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
         if (e == cudaSuccess)                                                                            \

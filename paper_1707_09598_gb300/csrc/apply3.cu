@@ -24,8 +24,8 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     Real* sm = reinterpret_cast<Real*>(sm_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const TileDesc td = Pl.tiles[Pl.sched[blockIdx.x]];
-    if (active && !active[td.grid]) return;
     const GridDesc& g = Pl.grids[td.grid];
+    if (active && !active[g.comp]) return;
     const int M = Pl.m;
     int ax[3], T[3], L[3], E0[3], NF[3];
     long long ST[3];

@@ -209,19 +209,21 @@ static void choose_tile(int d, int P, int M, const int* E, size_t budget, long l
 }
 
 // 1D interior matrices of a table, from the device-computed tables.
-static void assemble_1d(int E, int Q, int p, int nf, const double* w, const double* R, const double* dR,
+// 1D stiffness and mass matrices of the functions klo .. nf-2 (klo = 1: both
+// ends Dirichlet; klo = 0: natural condition at the low end).
+static void assemble_1d(int E, int Q, int p, int nf, int klo, const double* w, const double* R, const double* dR,
                         const int* first, std::vector<double>& K, std::vector<double>& Mm) {
-    int n = nf - 2;
+    int n = nf - 1 - klo;
     K.assign((size_t)n * n, 0.0);
     Mm.assign((size_t)n * n, 0.0);
     for (int e = 0; e < E; ++e)
         for (int q = 0; q < Q; ++q) {
             long long o = (long long)e * Q + q;
             for (int a = 0; a <= p; ++a) {
-                int i = first[e] + a - 1;
+                int i = first[e] + a - klo;
                 if (i < 0 || i >= n) continue;
                 for (int b = 0; b <= p; ++b) {
-                    int j = first[e] + b - 1;
+                    int j = first[e] + b - klo;
                     if (j < 0 || j >= n) continue;
                     K[(size_t)i * n + j] += w[o] * dR[o * (p + 1) + a] * dR[o * (p + 1) + b];
                     Mm[(size_t)i * n + j] += w[o] * R[o * (p + 1) + a] * R[o * (p + 1) + b];
@@ -260,14 +262,14 @@ static void make_fd_items(sgiga_plan_s* P, int ks) {
         std::vector<long long> cost;
         for (size_t gi = 0; gi < P->grids.size(); ++gi) {
             const GridDesc& g = P->grids[gi];
-            long long n = g.n[k];
-            if (g.ndof == 0) continue;
-            long long ncol = g.ndof / n;
+            long long n = g.fn[k];
+            if (g.fd_n == 0) continue;
+            long long ncol = g.fd_n / n;
             auto depth = [&](int j0) { return (int)std::min<long long>(n, j0 + ks); };
             if (n <= 64) {
-                for (long long c0 = 0; c0 < g.ndof; c0 += 256) {
+                for (long long c0 = 0; c0 < g.fd_n; c0 += 256) {
                     v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
-                    cost.push_back(std::min<long long>(256, g.ndof - c0) * n);
+                    cost.push_back(std::min<long long>(256, g.fd_n - c0) * n);
                 }
             } else if (ncol >= 64) {
                 for (long long i0 = 0; i0 < n; i0 += 32)
@@ -433,42 +435,114 @@ static int build(sgiga_plan_s* P) {
             P->tab_of[key] = (int)P->tabs.size();
             P->tabs.push_back(t);
         }
-    // grids and tiles
+    // components and their pieces (one per geometry patch)
+    const bool mp = c.domain == SGIGA_DOMAIN_LSHAPE;
+    const int npatch = mp ? 3 : 1;
+    P->multipatch = mp;
     for (size_t gi = 0; gi < idx.size(); ++gi) {
-        GridDesc g{};
+        CompDesc cd{};
+        cd.piece0 = (int)P->grids.size();
+        cd.npieces = npatch;
+        cd.dof_off = P->ndof;
+        cd.chunk0 = (int)P->chunks.size();
         int s = 0;
-        for (int k = 0; k < 3; ++k) {
-            if (k < d) {
-                g.lev[k] = idx[gi][k];
-                g.E[k] = 1 << g.lev[k];
-                g.nf[k] = g.E[k] * M + P->r + 1;
-                g.n[k] = g.nf[k] - 2;
-                g.tab[k] = P->tab_of[std::make_pair(k, g.lev[k])];
-                s += g.lev[k];
-            } else {
-                g.lev[k] = 0; g.E[k] = 1; g.nf[k] = 3; g.n[k] = 1; g.tab[k] = 0;
+        for (int k = 0; k < d; ++k) s += idx[gi][k];
+        const int t = w + d - 1 - s;
+        cd.coeff = (double)((t % 2) ? -1 : 1) * (double)binom(d - 1, t);
+        for (int q = 0; q < npatch; ++q) {
+            GridDesc g{};
+            g.comp = (int)gi;
+            g.patch = q;
+            g.coeff = cd.coeff;
+            g.gf_off = -1;
+            for (int k = 0; k < 3; ++k) { g.klo[k] = 1; g.slo[k] = 1; g.alias[k] = -1; }
+            if (mp) {
+                // L-shape pieces (GridDesc): patch 0 stores the x = 0 interface (its
+                // xi_1 = 0 side), patch 1 the y = 0 interface (its xi_2 = 0 side);
+                // patch 1's (0,0) function sits at the corner, a Dirichlet point
+                const int base = cd.piece0;
+                if (q == 0) { g.klo[0] = 0; g.slo[0] = 0; }
+                if (q == 1) { g.klo[0] = 0; g.slo[0] = 1; g.alias[0] = base + 0; g.klo[1] = 0; g.slo[1] = 0; g.xcorner = 1; }
+                if (q == 2) { g.klo[1] = 0; g.slo[1] = 1; g.alias[1] = base + 1; }
+            }
+            for (int k = 0; k < 3; ++k) {
+                if (k < d) {
+                    g.lev[k] = idx[gi][k];
+                    g.E[k] = 1 << g.lev[k];
+                    g.nf[k] = g.E[k] * M + P->r + 1;
+                    g.n[k] = g.nf[k] - 1 - g.slo[k];
+                    g.fn[k] = g.nf[k] - 1 - g.klo[k];
+                    g.tab[k] = P->tab_of[std::make_pair(k, g.lev[k])];
+                } else {
+                    g.lev[k] = 0; g.E[k] = 1; g.nf[k] = 3; g.n[k] = 1; g.fn[k] = 1; g.tab[k] = 0;
+                }
+            }
+            g.ndof = 1;
+            g.fd_n = 1;
+            g.nqp = 1;
+            for (int k = 0; k < d; ++k) { g.ndof *= g.n[k]; g.fd_n *= g.fn[k]; g.nqp *= (long long)Q * g.E[k]; }
+            g.dof_off = P->ndof;
+            g.fd_off = P->nfd;
+            g.qp_off = P->nqp;
+            P->ndof += g.ndof;
+            P->nfd += g.fd_n;
+            P->nqp += g.nqp;
+            if (mp) { g.gf_off = P->ngf; P->ngf += (long long)g.nf[0] * g.nf[1]; }
+            // chunks of the packed vector (component scalars) and of the local layout
+            const int piece = (int)P->grids.size();
+            g.chunk0 = (int)P->chunks.size();
+            for (long long o = 0; o < g.ndof; o += 4096) {
+                Chunk ch{};
+                ch.grid = (int)gi;
+                ch.piece = piece;
+                ch.start = g.dof_off + o;
+                ch.len = (int)std::min<long long>(4096, g.ndof - o);
+                P->chunks.push_back(ch);
+            }
+            g.nchunk = (int)P->chunks.size() - g.chunk0;
+            for (long long o = 0; o < g.fd_n; o += 4096) {
+                Chunk ch{};
+                ch.grid = (int)gi;
+                ch.piece = piece;
+                ch.start = g.fd_off + o;
+                ch.len = (int)std::min<long long>(4096, g.fd_n - o);
+                P->fdchunks.push_back(ch);
+            }
+            P->grids.push_back(g);
+        }
+        cd.ndof = P->ndof - cd.dof_off;
+        cd.nchunk = (int)P->chunks.size() - cd.chunk0;
+        P->comps.push_back(cd);
+    }
+    // Dirichlet sides of the pieces (multi-patch): (direction, end) per patch
+    if (mp) {
+        static const int dir_sides[3][3][2] = {{{1, 0}, {0, 1}, {1, 1}}, {{0, 1}, {1, 1}, {-1, -1}},
+                                               {{0, 0}, {0, 1}, {1, 1}}};
+        for (size_t pi = 0; pi < P->grids.size(); ++pi) {
+            const GridDesc& g = P->grids[pi];
+            for (int k = 0; k < 3; ++k) {
+                const int dk = dir_sides[g.patch][k][0], end = dir_sides[g.patch][k][1];
+                if (dk < 0) continue;
+                SideDesc sd{};
+                sd.piece = (int)pi;
+                sd.k = dk;
+                sd.end = end;
+                sd.goff = P->ngdata;
+                sd.soff = P->nscratch;
+                const int kp = 1 - dk;
+                P->ngdata += 2 + (long long)g.E[kp] * Q;
+                P->nscratch += (long long)g.nf[kp] * (p + 1) + g.nf[kp];
+                P->sides.push_back(sd);
+            }
+            if (g.xcorner) {
+                SideDesc sd{};
+                sd.piece = (int)pi;
+                sd.k = -1;
+                sd.goff = P->ngdata;
+                P->ngdata += 1;
+                P->sides.push_back(sd);
             }
         }
-        int t = w + d - 1 - s;
-        g.coeff = (double)((t % 2) ? -1 : 1) * (double)binom(d - 1, t);
-        g.ndof = 1;
-        g.nqp = 1;
-        for (int k = 0; k < d; ++k) { g.ndof *= g.n[k]; g.nqp *= (long long)Q * g.E[k]; }
-        g.dof_off = P->ndof;
-        g.qp_off = P->nqp;
-        P->ndof += g.ndof;
-        P->nqp += g.nqp;
-        // chunks
-        g.chunk0 = (int)P->chunks.size();
-        for (long long o = 0; o < g.ndof; o += 4096) {
-            Chunk ch{};
-            ch.grid = (int)gi;
-            ch.start = g.dof_off + o;
-            ch.len = (int)std::min<long long>(4096, g.ndof - o);
-            P->chunks.push_back(ch);
-        }
-        g.nchunk = (int)P->chunks.size() - g.chunk0;
-        P->grids.push_back(g);
     }
     make_tiles(P, 110 * 1024, 16384);
     make_fd_items(P, 128);
@@ -477,9 +551,21 @@ static int build(sgiga_plan_s* P) {
         if (!c.patch || make_user_patch(c.patch, d, P->patch) != 0)
             return fail(SGIGA_ERR_ARG, "invalid patch (degree <= 3, <= 12 knots, <= 8 control points per direction, "
                                        "<= 128 in total, nknots = ncp + deg + 1)");
+    } else if (mp) {
+        for (int q = 0; q < 3; ++q) {   // x = s * xi: bilinear unit squares with the origin at the corner
+            static const double sg[3][2] = {{1, 1}, {-1, 1}, {-1, -1}};
+            Patch pt;
+            make_patch(SGIGA_DOMAIN_UNIT, 2, pt);
+            for (int cc = 0; cc < 4; ++cc)
+                for (int k = 0; k < 2; ++k) pt.cp[cc][k] *= sg[q][k];
+            pt.orient = sg[q][0] * sg[q][1] < 0 ? -1 : 1;
+            P->patches.push_back(pt);
+        }
+        P->patch = P->patches[0];
     } else {
         make_patch(c.domain, d, P->patch);
     }
+    if (P->patches.empty()) P->patches.push_back(P->patch);
     std::vector<double> gauss(2 * Q);
     gauss_legendre(Q, gauss.data(), gauss.data() + Q);
     DevPlan& D = P->dp;
@@ -495,11 +581,24 @@ static int build(sgiga_plan_s* P) {
     int rc;
     GridDesc* dg; TileDesc* dt; int* ds; Table1D* dtab; Chunk* dch; Patch* dpatch;
     double *dkn, *dbp, *dgauss;
-    std::vector<Patch> pv(1, P->patch);
+    CompDesc* dcomps; Chunk* dfdch; SideDesc* dsides;
     if ((rc = upload(P, &dtab, P->tabs)) || (rc = upload(P, &dt, P->tiles)) || (rc = upload(P, &ds, P->sched)) ||
-        (rc = upload(P, &dch, P->chunks)) || (rc = upload(P, &dpatch, pv)) || (rc = upload(P, &dkn, P->knots)) ||
-        (rc = upload(P, &dbp, P->bp)) || (rc = upload(P, &dgauss, gauss)))
+        (rc = upload(P, &dch, P->chunks)) || (rc = upload(P, &dpatch, P->patches)) ||
+        (rc = upload(P, &dkn, P->knots)) || (rc = upload(P, &dbp, P->bp)) || (rc = upload(P, &dgauss, gauss)) ||
+        (rc = upload(P, &dcomps, P->comps)) || (rc = upload(P, &dfdch, P->fdchunks)) ||
+        (rc = upload(P, &dsides, P->sides)))
         return rc;
+    D.comps = dcomps; D.ncomps = (int)P->comps.size();
+    D.fdchunks = dfdch; D.nfdchunks = (int)P->fdchunks.size(); D.nfd = P->nfd;
+    D.sides = dsides; D.nsides = (int)P->sides.size();
+    D.multipatch = mp ? 1 : 0;
+    if (mp) {
+        if ((rc = dalloc(P, &D.gfull, P->ngf)) || (rc = dalloc(P, &D.gdata, P->ngdata)) ||
+            (rc = dalloc(P, &D.gscratch, P->nscratch)) || (rc = dalloc(P, &P->d_xb, 2 * P->ngdata)))
+            return rc;
+        CUDA_TRY(cudaMemset(D.gfull, 0, (size_t)P->ngf * 8));
+        CUDA_TRY(cudaMemset(D.gdata, 0, (size_t)P->ngdata * 8));
+    }
     for (int k = 0; k < d; ++k)
         if ((rc = upload(P, &P->d_fd[k], P->fd[k]))) return rc;
     D.tiles = dt; D.sched = ds; D.tabs = dtab; D.chunks = dch; D.patch = dpatch;
@@ -528,18 +627,23 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaMemcpyAsync(hdR.data(), D.dR, hdR.size() * 8, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(hfirst.data(), D.first, hfirst.size() * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    std::map<std::pair<int, int>, int> eig_key;
+    // one eigen table per (level, rational direction or not, first kept
+    // function): klo = 0 keeps the interface end (natural condition there)
+    std::map<std::array<int, 3>, int> eig_key;
+    std::map<std::pair<int, int>, int> eig_of;   // (table, klo) -> eigen table
     std::vector<double> hU, hlam;
     P->eig_of_tab.assign(P->tabs.size(), -1);
-    for (size_t ti = 0; ti < P->tabs.size(); ++ti) {
+    auto eig_for = [&](int ti, int klo) -> int {
+        auto f = eig_of.find(std::make_pair(ti, klo));
+        if (f != eig_of.end()) return f->second;
         const Table1D& t = P->tabs[ti];
-        auto key = std::make_pair(t.level, P->patch.rational[t.dir] ? t.dir : -1);
+        std::array<int, 3> key = {t.level, P->patch.rational[t.dir] ? t.dir : -1, klo};
         auto it = eig_key.find(key);
-        if (it != eig_key.end()) { P->eig_of_tab[ti] = it->second; continue; }
+        if (it != eig_key.end()) { eig_of[std::make_pair(ti, klo)] = it->second; return it->second; }
         std::vector<double> K, Mm;
-        assemble_1d(t.E, Q, p, t.nf, hw.data() + t.off, hR.data() + t.off * (p + 1), hdR.data() + t.off * (p + 1),
-                    hfirst.data() + t.eoff, K, Mm);
-        int n = t.nf - 2;
+        assemble_1d(t.E, Q, p, t.nf, klo, hw.data() + t.off, hR.data() + t.off * (p + 1),
+                    hdR.data() + t.off * (p + 1), hfirst.data() + t.eoff, K, Mm);
+        int n = t.nf - 1 - klo;
         Eig1D e{};
         e.n = n;
         e.uoff = (long long)hU.size();
@@ -547,25 +651,38 @@ static int build(sgiga_plan_s* P) {
         hU.resize(hU.size() + (size_t)n * n);
         hlam.resize(hlam.size() + n);
         if (n > 0 && generalized_eigen(n, p, K.data(), Mm.data(), hU.data() + e.uoff, hlam.data() + e.loff) != 0)
-            return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed (level " + std::to_string(t.level) + ")");
-        eig_key[key] = (int)P->eigs.size();
-        P->eig_of_tab[ti] = (int)P->eigs.size();
+            return -1;
+        const int id = (int)P->eigs.size();
+        eig_key[key] = id;
+        eig_of[std::make_pair(ti, klo)] = id;
         P->eigs.push_back(e);
+        return id;
+    };
+    for (size_t ti = 0; ti < P->tabs.size(); ++ti) {
+        int id = eig_for((int)ti, 1);
+        if (id < 0) return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed (level " +
+                                                   std::to_string(P->tabs[ti].level) + ")");
+        P->eig_of_tab[ti] = id;
     }
     for (auto& g : P->grids)
-        for (int k = 0; k < 3; ++k) g.eig[k] = k < d ? P->eig_of_tab[g.tab[k]] : 0;
-    // reciprocal eigenvalue sums of every packed entry
-    std::vector<double> hdinv((size_t)P->ndof);
+        for (int k = 0; k < 3; ++k) {
+            g.eig[k] = 0;
+            if (k >= d) continue;
+            g.eig[k] = eig_for(g.tab[k], g.klo[k]);
+            if (g.eig[k] < 0) return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed");
+        }
+    // reciprocal eigenvalue sums of every entry of the preconditioner's local layout
+    std::vector<double> hdinv((size_t)P->nfd);
     for (const GridDesc& g : P->grids)
-        for (long long idx = 0; idx < g.ndof; ++idx) {
+        for (long long idx = 0; idx < g.fd_n; ++idx) {
             long long rem = idx;
             double sum = 0.0;
             for (int k = 0; k < d; ++k) {
-                int ik = (int)(rem % g.n[k]);
-                rem /= g.n[k];
-                sum += hlam[P->eigs[P->eig_of_tab[g.tab[k]]].loff + ik];
+                int ik = (int)(rem % g.fn[k]);
+                rem /= g.fn[k];
+                sum += hlam[P->eigs[g.eig[k]].loff + ik];
             }
-            hdinv[g.dof_off + idx] = 1.0 / sum;
+            hdinv[g.fd_off + idx] = 1.0 / sum;
         }
     double* ddinv;
     if ((rc = upload(P, &ddinv, hdinv))) return rc;
@@ -579,6 +696,7 @@ static int build(sgiga_plan_s* P) {
         (rc = upload(P, &dlam, hlam)) || (rc = upload(P, &dg, P->grids)))
         return rc;
     D.eigs = deig; D.U = dU; D.Ut = dUt; D.lam = dlam; D.grids = dg;
+    if (mp) CUDA_TRY(launch_boundary_points(D, P->d_xb, s));
     // geometry coefficients
     CUDA_TRY(launch_geometry(D, s));
     int hflags[4];
@@ -589,15 +707,16 @@ static int build(sgiga_plan_s* P) {
     // operator kernel shared memory
     if ((rc = grant_op_smem(P))) return rc;
     // solver vectors and scalars
-    const size_t nd = (size_t)P->ndof, ng = P->grids.size();
+    const size_t nd = (size_t)P->ndof, ng = P->comps.size(), nt = std::max<size_t>(nd, (size_t)P->nfd);
     if ((rc = dalloc(P, &P->d_b, nd)) || (rc = dalloc(P, &P->d_x, nd)) || (rc = dalloc(P, &P->d_r, nd)) ||
         (rc = dalloc(P, &P->d_z, nd)) || (rc = dalloc(P, &P->d_p, nd)) || (rc = dalloc(P, &P->d_q, nd)) ||
-        (rc = dalloc(P, &P->d_t1, nd)) || (rc = dalloc(P, &P->d_t2, nd)) ||
+        (rc = dalloc(P, &P->d_t1, nt)) || (rc = dalloc(P, &P->d_t2, nt)) ||
+        (mp && (rc = dalloc(P, &P->d_l0, (size_t)P->nfd))) ||
         (rc = dalloc(P, &P->d_partial, P->chunks.size())) || (rc = dalloc(P, &P->d_scal, 8 * ng)) ||
         (rc = dalloc(P, &P->d_active, ng)) || (rc = dalloc(P, &P->d_iters, ng)) || (rc = dalloc(P, &P->d_nactive, 1)))
         return rc;
     std::vector<double> coef(ng);
-    for (size_t i = 0; i < ng; ++i) coef[i] = P->grids[i].coeff;
+    for (size_t i = 0; i < ng; ++i) coef[i] = P->comps[i].coeff;
     if ((rc = upload(P, &P->d_coef, coef))) return rc;
     CUDA_TRY(cudaMemsetAsync(P->d_b, 0, nd * 8, s));
     CUDA_TRY(cudaMemsetAsync(P->d_x, 0, nd * 8, s));
@@ -610,9 +729,10 @@ static int build(sgiga_plan_s* P) {
         const long long ntab = P->tab_entries * (p + 1);
         if ((rc = dalloc(P, &Gf, (size_t)ncomp * P->nqp)) || (rc = dalloc(P, &Rf, ntab)) ||
             (rc = dalloc(P, &dRf, ntab)) || (rc = dalloc(P, &Uf, hU.size())) || (rc = dalloc(P, &Utf, hU.size())) ||
-            (rc = dalloc(P, &dinvf, nd)) || (rc = dalloc(P, &P->f_b, nd)) || (rc = dalloc(P, &P->f_x, nd)) ||
+            (rc = dalloc(P, &dinvf, (size_t)P->nfd)) || (rc = dalloc(P, &P->f_b, nd)) || (rc = dalloc(P, &P->f_x, nd)) ||
             (rc = dalloc(P, &P->f_r, nd)) || (rc = dalloc(P, &P->f_z, nd)) || (rc = dalloc(P, &P->f_p, nd)) ||
-            (rc = dalloc(P, &P->f_q, nd)) || (rc = dalloc(P, &P->f_t1, nd)) || (rc = dalloc(P, &P->f_t2, nd)) ||
+            (rc = dalloc(P, &P->f_q, nd)) || (rc = dalloc(P, &P->f_t1, nt)) || (rc = dalloc(P, &P->f_t2, nt)) ||
+            (mp && (rc = dalloc(P, &P->f_l0, (size_t)P->nfd))) ||
             (rc = dalloc(P, &P->d_active_o, ng)) || (rc = dalloc(P, &P->d_iters_o, ng)) ||
             (rc = dalloc(P, &P->d_scal64o, 8 * ng)))
             return rc;
@@ -621,7 +741,7 @@ static int build(sgiga_plan_s* P) {
         CUDA_TRY(launch_narrow(dRf, D.dR, ntab, s));
         CUDA_TRY(launch_narrow(Uf, D.U, (long long)hU.size(), s));
         CUDA_TRY(launch_narrow(Utf, D.Ut, (long long)hU.size(), s));
-        CUDA_TRY(launch_narrow(dinvf, D.dinv, (long long)nd, s));
+        CUDA_TRY(launch_narrow(dinvf, D.dinv, P->nfd, s));
         D.Gf = Gf; D.Rf = Rf; D.dRf = dRf; D.Uf = Uf; D.Utf = Utf; D.dinvf = dinvf;
     }
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -678,7 +798,10 @@ int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
     if (c.continuity > c.p - 1) return fail(SGIGA_ERR_ARG, "continuity must be <= p-1");
     if (c.min_level < 0) return fail(SGIGA_ERR_ARG, "min_level must be >= 0");
     if (c.w < c.d * c.min_level - c.d + 1) return fail(SGIGA_ERR_ARG, "w too small for min_level");
-    if (c.domain < SGIGA_DOMAIN_UNIT || c.domain > SGIGA_DOMAIN_PATCH) return fail(SGIGA_ERR_ARG, "unknown domain");
+    if (c.domain < SGIGA_DOMAIN_UNIT || c.domain > SGIGA_DOMAIN_LSHAPE) return fail(SGIGA_ERR_ARG, "unknown domain");
+    if (c.domain == SGIGA_DOMAIN_LSHAPE && c.d != 2) return fail(SGIGA_ERR_ARG, "the L-shaped domain is 2D");
+    if (c.domain == SGIGA_DOMAIN_LSHAPE && c.precond == SGIGA_PRECOND_LEARNED)
+        return fail(SGIGA_ERR_ARG, "the learned preconditioner needs a single-patch domain");
     if (c.grading < 0 || c.grading > 2 || (c.grading != 0 && !(c.gamma > 0))) return fail(SGIGA_ERR_ARG, "bad grading");
     if (c.precision != SGIGA_PREC_FP64 && c.precision != SGIGA_PREC_MIXED_FP32)
         return fail(SGIGA_ERR_ARG, "unsupported precision");
@@ -712,28 +835,36 @@ void sgiga_destroy(sgiga_plan_t plan) {
 int sgiga_plan_info(sgiga_plan_t P, sgiga_info* out) {
     if (!P || !out) return fail(SGIGA_ERR_ARG, "null argument");
     out->d = P->d; out->p = P->p; out->continuity = P->r;
-    out->ngrids = (int)P->grids.size();
+    out->ngrids = (int)P->comps.size();
     out->ndof = P->ndof;
     out->nqp = P->nqp;
     out->max_tile_smem = (int)P->smem;
     out->ntiles = (int)P->tiles.size();
     out->diag_metric = P->dp.diag;
+    out->npatches = (int)P->patches.size();
+    out->nbpts = P->ngdata;
     return SGIGA_OK;
 }
 
 int sgiga_grid_info(sgiga_plan_t P, int g, sgiga_grid* out) {
     if (!P || !out) return fail(SGIGA_ERR_ARG, "null argument");
-    if (g < 0 || g >= (int)P->grids.size()) return fail(SGIGA_ERR_ARG, "grid index out of range");
-    const GridDesc& gd = P->grids[g];
+    if (g < 0 || g >= (int)P->comps.size()) return fail(SGIGA_ERR_ARG, "grid index out of range");
+    const CompDesc& cd = P->comps[g];
+    const GridDesc& gd = P->grids[cd.piece0];
     for (int k = 0; k < 3; ++k) {
         out->levels[k] = k < P->d ? gd.lev[k] : 0;
         out->n[k] = k < P->d ? gd.n[k] : 1;
     }
-    out->coeff = (int)gd.coeff;
-    out->ndof = gd.ndof; out->dof_off = gd.dof_off; out->nqp = gd.nqp; out->qp_off = gd.qp_off;
+    out->coeff = (int)cd.coeff;
+    out->ndof = cd.ndof; out->dof_off = cd.dof_off; out->qp_off = gd.qp_off;
+    out->nqp = 0;
+    out->ntiles = 0;
+    for (int q = 0; q < cd.npieces; ++q) {
+        out->nqp += P->grids[cd.piece0 + q].nqp;
+        out->ntiles += P->grids[cd.piece0 + q].ntiles;
+    }
     for (int k = 0; k < 3; ++k) out->tile[k] = k < P->d ? gd.T[k] : 1;
     out->pencil_dir = gd.perm[0];
-    out->ntiles = gd.ntiles;
     return SGIGA_OK;
 }
 
@@ -760,10 +891,24 @@ int sgiga_set_rhs(sgiga_plan_t P, const double* f) {
     return SGIGA_OK;
 }
 
+// Project the boundary data in P->dp.gdata onto every Dirichlet side.
+static int project_boundary(sgiga_plan_s* P) {
+    CUDA_TRY(cudaMemsetAsync(P->dp.gfull, 0, (size_t)P->ngf * 8, P->stream));
+    CUDA_TRY(launch_boundary_project(P->dp, P->stream));
+    P->lifting = true;
+    return SGIGA_OK;
+}
+
 int sgiga_set_rhs_builtin(sgiga_plan_t P, int source) {
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
-    if (source < 0 || source > SGIGA_SRC_ONE) return fail(SGIGA_ERR_ARG, "unknown source");
+    if (source < 0 || source > SGIGA_SRC_HARMONIC_QUADRATIC) return fail(SGIGA_ERR_ARG, "unknown source");
     if ((source == SGIGA_SRC_ANNULUS) && P->d != 2) return fail(SGIGA_ERR_ARG, "source needs d = 2");
+    if (source >= SGIGA_SRC_LSHAPE_CORNER) {   // harmonic u with Dirichlet data g = u
+        if (!P->multipatch) return fail(SGIGA_ERR_ARG, "sources with Dirichlet data need an LSHAPE plan");
+        CUDA_TRY(launch_boundary_builtin(P->dp, source, P->d_xb, P->dp.gdata, P->ngdata, P->stream));
+        int rc = project_boundary(P);
+        if (rc) return rc;
+    }
     CUDA_TRY(launch_rhs_density_builtin(P->dp, source, P->stream));
     int rc = run_rhs_operator(P);
     if (rc) return rc;
@@ -771,9 +916,74 @@ int sgiga_set_rhs_builtin(sgiga_plan_t P, int source) {
     return SGIGA_OK;
 }
 
+int sgiga_boundary_points(sgiga_plan_t P, double* xb) {
+    if (!P || !xb) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!P->multipatch) return fail(SGIGA_ERR_ARG, "plan has no boundary data points (LSHAPE plans only)");
+    const size_t bytes = (size_t)P->ngdata * 2 * 8;
+    CUDA_TRY(cudaMemcpyAsync(xb, P->d_xb, bytes, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_set_dirichlet(sgiga_plan_t P, const double* g) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!P->multipatch) return fail(SGIGA_ERR_ARG, "plan has no Dirichlet data (LSHAPE plans only)");
+    if (!g) {
+        P->lifting = false;
+        CUDA_TRY(cudaMemsetAsync(P->dp.gfull, 0, (size_t)P->ngf * 8, P->stream));
+        return SGIGA_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(P->dp.gdata, g, (size_t)P->ngdata * 8, cudaMemcpyDefault, P->stream));
+    int rc = project_boundary(P);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_eval_grad(sgiga_plan_t P, const double* xi, const int* patch, long long npts, double* ucomp,
+                    double* gcomp) {
+    if (!P || (!xi && npts > 0) || (!ucomp && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->d != 2) return fail(SGIGA_ERR_ARG, "gradient evaluation is 2D only");
+    if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    if (npts == 0) return SGIGA_OK;
+    const size_t ng = P->comps.size();
+    const size_t xb = (size_t)npts * 2 * 8, pb = patch ? (size_t)npts * 4 : 0;
+    const size_t ub = (size_t)npts * ng * 8, gb = gcomp ? 2 * ub : 0;
+    const bool xdev = is_device(xi), pdev = !patch || is_device(patch), udev = is_device(ucomp);
+    const bool gdev = !gcomp || is_device(gcomp);
+    int rc = ensure_stage(P, (xdev ? 0 : xb) + (pdev ? 0 : (pb + 15) / 16 * 16) + (udev ? 0 : ub) + (gdev ? 0 : gb));
+    if (rc) return rc;
+    char* st = (char*)P->stage;
+    const double* xd = xi;
+    const int* pd = patch;
+    if (!xdev) {
+        CUDA_TRY(cudaMemcpyAsync(st, xi, xb, cudaMemcpyHostToDevice, P->stream));
+        xd = (const double*)st;
+        st += xb;
+    }
+    double* ud = udev ? ucomp : (double*)st;
+    if (!udev) st += ub;
+    double* gd = gdev ? gcomp : (double*)st;
+    if (!gdev) st += gb;
+    if (!pdev) {
+        CUDA_TRY(cudaMemcpyAsync(st, patch, pb, cudaMemcpyHostToDevice, P->stream));
+        pd = (const int*)st;
+    }
+    CUDA_TRY(cudaMemsetAsync(P->dp.flags + 1, 0, sizeof(int), P->stream));
+    CUDA_TRY(launch_eval_grad(P->dp, P->d_x, xd, pd, npts, ud, gd, P->lifting ? 1 : 0, P->stream));
+    CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->dp.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    if (!udev) CUDA_TRY(cudaMemcpyAsync(ucomp, ud, ub, cudaMemcpyDeviceToHost, P->stream));
+    if (!gdev) CUDA_TRY(cudaMemcpyAsync(gcomp, gd, gb, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    const int hflag = *P->h_nactive;
+    if (hflag & 2) return fail(SGIGA_ERR_ARG, "patch id out of range");
+    if (hflag) return fail(SGIGA_ERR_ARG, "evaluation point outside [0,1]^d");
+    return SGIGA_OK;
+}
+
 int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
     if (!P || !f) return fail(SGIGA_ERR_ARG, "null argument");
-    if (source < 0 || source > SGIGA_SRC_ONE) return fail(SGIGA_ERR_ARG, "unknown source");
+    if (source < 0 || source > SGIGA_SRC_HARMONIC_QUADRATIC) return fail(SGIGA_ERR_ARG, "unknown source");
     if ((source == SGIGA_SRC_ANNULUS) && P->d != 2) return fail(SGIGA_ERR_ARG, "source needs d = 2");
     double* fd = f;
     const bool dev = is_device(f);
@@ -941,7 +1151,7 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
     if (!(rel_tol > 0) || max_iter < 1) return fail(SGIGA_ERR_ARG, "rel_tol must be > 0 and max_iter >= 1");
     auto t0 = std::chrono::steady_clock::now();
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     P->last_inner_iters = 0;
     if (P->cfg.precision == SGIGA_PREC_FP64) {
         int nact = pcg<double>(P, P->d_b, vecs64(P), rel_tol, max_iter, nullptr, P->d_active, P->d_iters, P->d_scal,
@@ -1026,8 +1236,9 @@ int sgiga_set_solution(sgiga_plan_t P, const double* u) {
 int sgiga_eval(sgiga_plan_t P, const double* xi, long long npts, double* ucomp) {
     if (!P || (!xi && npts > 0) || (!ucomp && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
     if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    if (P->multipatch) return fail(SGIGA_ERR_ARG, "multi-patch plan: evaluate with sgiga_eval_grad (patch ids)");
     if (npts == 0) return SGIGA_OK;
-    const size_t ng = P->grids.size();
+    const size_t ng = P->comps.size();
     const size_t xb = (size_t)npts * P->d * 8, ub = (size_t)npts * ng * 8;
     const bool xdev = is_device(xi), udev = is_device(ucomp);
     size_t need = (xdev ? 0 : xb) + (udev ? 0 : ub);
@@ -1071,7 +1282,7 @@ int sgiga_combine(sgiga_plan_t P, const double* ucomp, long long npts, double* u
     if (!P || (!ucomp && npts > 0) || (!u && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
     if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
     if (npts == 0) return SGIGA_OK;
-    const size_t ng = P->grids.size();
+    const size_t ng = P->comps.size();
     const size_t ub = (size_t)npts * ng * 8, ob = (size_t)npts * 8;
     const bool idev = is_device(ucomp), odev = is_device(u);
     int rc = ensure_stage(P, (idev ? 0 : ub) + (odev ? 0 : ob));

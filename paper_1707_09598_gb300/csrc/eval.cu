@@ -104,7 +104,91 @@ cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts
                            cudaStream_t s) {
     if (npts <= 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_combine<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(P.ngrids, ucomp, npts, coef, u);
+    k_combine<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(P.ncomps, ucomp, npts, coef, u);
+    return cudaGetLastError();
+}
+
+}  // namespace sgiga
+
+namespace sgiga {
+
+// Values and physical gradients of every component at (patch, xi) points, 2D.
+// Block (x: points, y: component). The point's patch selects the component's
+// piece; a coefficient is the packed solution for a kept function, the
+// boundary array (Dirichlet lifting) otherwise.
+//   u = sum_ab R_a(xi_0) R_b(xi_1) c_ab,  grad_xi u = (sum R'_a R_b c, sum R_a R'_b c),
+//   grad_x u = J^{-T} grad_xi u,  R = B / W_k (eq. u-IGA-approx).
+__global__ void k_eval_grad(DevPlan P, const double* __restrict__ coeffs, const double* __restrict__ xi,
+                            const int* __restrict__ patch, long long npts, double* __restrict__ ucomp,
+                            double* __restrict__ gcomp, int lifting) {
+    const int c = blockIdx.y;
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npts) return;
+    const CompDesc& cd = P.comps[c];
+    int pa = patch ? patch[j] : 0;
+    if (pa < 0 || pa >= cd.npieces) {
+        atomicOr(&P.flags[1], 2);
+        pa = 0;
+    }
+    const GridDesc& g = P.grids[cd.piece0 + pa];
+    const int p = P.p;
+    double x[3] = {xi[2 * j], xi[2 * j + 1], 0.0};
+    double N[2][SGIGA_MAXP + 1], dN[2][SGIGA_MAXP + 1];
+    int f0[2];
+    for (int k = 0; k < 2; ++k) {
+        if (!(x[k] >= 0.0 && x[k] <= 1.0)) {
+            atomicOr(&P.flags[1], 1);
+            x[k] = x[k] < 0.0 ? 0.0 : 1.0;
+        }
+        const Table1D& tb = P.tabs[g.tab[k]];
+        const double* kn = P.knots + tb.koff;
+        const int s = find_span(kn, tb.nf, p, x[k]);
+        double B[SGIGA_MAXP + 1], dB[SGIGA_MAXP + 1];
+        basis_funs<SGIGA_MAXP>(kn, s, p, x[k], B, dB);
+        double W, dW;
+        patch_weight_1d(P.patch[g.patch], k, x[k], W, dW);
+        for (int r = 0; r <= p; ++r) {
+            N[k][r] = B[r] / W;
+            dN[k][r] = (dB[r] * W - B[r] * dW) / (W * W);
+        }
+        f0[k] = s - p;
+    }
+    const double* gf = (lifting && g.gf_off >= 0) ? P.gfull + g.gf_off : nullptr;
+    double u = 0.0, u0 = 0.0, u1 = 0.0;
+    for (int b = 0; b <= p; ++b) {
+        const int i1 = f0[1] + b;
+        double v = 0.0, dv = 0.0;
+        for (int a = 0; a <= p; ++a) {
+            const int i0 = f0[0] + a;
+            double cv;
+            if (piece_kept2(g, i0, i1)) cv = coeffs[piece_addr2(P.grids, g, i0, i1)];
+            else cv = gf ? gf[i0 + (long long)i1 * g.nf[0]] : 0.0;
+            v += N[0][a] * cv;
+            dv += dN[0][a] * cv;
+        }
+        u += N[1][b] * v;
+        u0 += N[1][b] * dv;
+        u1 += dN[1][b] * v;
+    }
+    ucomp[(long long)c * npts + j] = u;
+    if (gcomp) {
+        double X[3], J[3][3];
+        patch_eval(P.patch[g.patch], x, X, J);
+        // J^T grad_x = grad_xi
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double gx = (J[1][1] * u0 - J[1][0] * u1) / det;
+        const double gy = (-J[0][1] * u0 + J[0][0] * u1) / det;
+        gcomp[(long long)c * npts + j] = gx;
+        gcomp[((long long)P.ncomps + c) * npts + j] = gy;
+    }
+}
+
+cudaError_t launch_eval_grad(const DevPlan& P, const double* coeffs, const double* xi, const int* patch,
+                             long long npts, double* ucomp, double* gcomp, int lifting, cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((npts + 127) / 128), P.ncomps);
+    SGIGA_COUNT_LAUNCH();
+    k_eval_grad<<<grid, 128, 0, s>>>(P, coeffs, xi, patch, npts, ucomp, gcomp, lifting);
     return cudaGetLastError();
 }
 

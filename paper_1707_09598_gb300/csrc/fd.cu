@@ -70,20 +70,20 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
     __shared__ double sm_raw[64 * 65];
     Real* sm = reinterpret_cast<Real*>(sm_raw);
     const FDItem it = items[blockIdx.x];
-    if (active && !active[it.grid]) return;
     const GridDesc& g = P.grids[it.grid];
+    if (active && !active[g.comp]) return;
     const int d = P.d;
-    const int n = g.n[dir];
+    const int n = g.fn[dir];
     long long B = 1, A = 1;
-    for (int k = 0; k < dir; ++k) B *= g.n[k];
-    for (int k = dir + 1; k < d; ++k) A *= g.n[k];
+    for (int k = 0; k < dir; ++k) B *= g.fn[k];
+    for (int k = dir + 1; k < d; ++k) A *= g.fn[k];
     const long long Ncol = A * B;
     const Eig1D e = P.eigs[g.eig[dir]];
     // Mat[i][j] = U[j][i] (forward) or U[i][j] (backward); MT[j][i] = Mat[i][j]
     const Real* __restrict__ U = FDData<Real>::U(P) + e.uoff;
     const Real* __restrict__ MT = forward ? FDData<Real>::U(P) + e.uoff : FDData<Real>::Ut(P) + e.uoff;
-    const Real* vin = in + g.dof_off;
-    Real* vout = out + g.dof_off;
+    const Real* vin = in + g.fd_off;
+    Real* vout = out + g.fd_off;
     const bool split = it.j0 > 0 || it.j1 < n;
 
     if (it.mode == FD_SMALL) {
@@ -93,7 +93,7 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
         }
         __syncthreads();
         long long lin = it.c0 + threadIdx.x;
-        if (lin >= g.ndof) return;
+        if (lin >= g.fd_n) return;
         long long b = lin % B, r = lin / B;
         int i = (int)(r % n);
         long long a = r / n;
@@ -184,7 +184,7 @@ template cudaError_t launch_fd_pass<double>(const DevPlan&, const FDItem*, int, 
 template cudaError_t launch_fd_pass<float>(const DevPlan&, const FDItem*, int, int, int, const float*, float*,
                                            const int*, cudaStream_t);
 
-// z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every packed entry.
+// z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every entry of the local layout.
 template <typename Real>
 __global__ void k_fd_scale(const Chunk* __restrict__ chunks, DevPlan P, Real* __restrict__ z,
                            const int* __restrict__ active) {
@@ -196,12 +196,75 @@ __global__ void k_fd_scale(const Chunk* __restrict__ chunks, DevPlan P, Real* __
 
 template <typename Real>
 cudaError_t launch_fd_scale(const DevPlan& P, Real* z, const int* active, cudaStream_t s) {
-    if (P.nchunks == 0) return cudaSuccess;
+    if (P.nfdchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_fd_scale<Real><<<P.nchunks, 256, 0, s>>>(P.chunks, P, z, active);
+    k_fd_scale<Real><<<P.nfdchunks, 256, 0, s>>>(P.fdchunks, P, z, active);
     return cudaGetLastError();
 }
 template cudaError_t launch_fd_scale<double>(const DevPlan&, double*, const int*, cudaStream_t);
 template cudaError_t launch_fd_scale<float>(const DevPlan&, float*, const int*, cudaStream_t);
+
+// Multi-patch preconditioner (weighted additive Schwarz over the patches):
+//   z = sum_pieces R_p^T D_p A_p^{-1} D_p R_p r,
+// with A_p the piece's stiffness on its kept functions and natural conditions
+// at patch interfaces, inverted exactly by fast diagonalisation. R_p gathers
+// the piece's kept functions (interface functions appear in both pieces that
+// share them) into the local layout; R_p^T adds them back. D_p = 1 / (number
+// of pieces sharing the function), the Neumann-Neumann weighting: 1/2 on an
+// interface. The excluded (0,0) corner of a piece is a zero entry of its
+// tensor on the way in and dropped on the way out (the principal part of the
+// local inverse stays SPD).
+__device__ __forceinline__ double share_weight(const GridDesc& g, int f0, int f1) {
+    const int m = 1 + (f0 == 0 && g.klo[0] == 0) + (f1 == 0 && g.klo[1] == 0);
+    return m == 1 ? 1.0 : 1.0 / m;
+}
+
+template <typename Real>
+__global__ void k_fd_gather(DevPlan P, const Real* __restrict__ r, Real* __restrict__ loc,
+                            const int* __restrict__ active) {
+    const Chunk c = P.fdchunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    const GridDesc& g = P.grids[c.piece];
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long l = c.start - g.fd_off + i;
+        const int f0 = (int)(l % g.fn[0]) + g.klo[0], f1 = (int)(l / g.fn[0]) + g.klo[1];
+        Real v = Real(0);
+        if (!(g.xcorner && f0 == 0 && f1 == 0)) v = r[piece_addr2(P.grids, g, f0, f1)] * (Real)share_weight(g, f0, f1);
+        loc[c.start + i] = v;
+    }
+}
+
+template <typename Real>
+__global__ void k_fd_scatter(DevPlan P, const Real* __restrict__ loc, Real* __restrict__ z,
+                             const int* __restrict__ active) {
+    const Chunk c = P.fdchunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    const GridDesc& g = P.grids[c.piece];
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long l = c.start - g.fd_off + i;
+        const int f0 = (int)(l % g.fn[0]) + g.klo[0], f1 = (int)(l / g.fn[0]) + g.klo[1];
+        if (g.xcorner && f0 == 0 && f1 == 0) continue;
+        atomicAdd(z + piece_addr2(P.grids, g, f0, f1), loc[c.start + i] * (Real)share_weight(g, f0, f1));
+    }
+}
+
+template <typename Real>
+cudaError_t launch_fd_gather(const DevPlan& P, const Real* r, Real* loc, const int* active, cudaStream_t s) {
+    if (P.nfdchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_fd_gather<Real><<<P.nfdchunks, 256, 0, s>>>(P, r, loc, active);
+    return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_fd_scatter(const DevPlan& P, const Real* loc, Real* z, const int* active, cudaStream_t s) {
+    if (P.nfdchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_fd_scatter<Real><<<P.nfdchunks, 256, 0, s>>>(P, loc, z, active);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fd_gather<double>(const DevPlan&, const double*, double*, const int*, cudaStream_t);
+template cudaError_t launch_fd_gather<float>(const DevPlan&, const float*, float*, const int*, cudaStream_t);
+template cudaError_t launch_fd_scatter<double>(const DevPlan&, const double*, double*, const int*, cudaStream_t);
+template cudaError_t launch_fd_scatter<float>(const DevPlan&, const float*, float*, const int*, cudaStream_t);
 
 }  // namespace sgiga

@@ -92,7 +92,7 @@ __global__ void k_geometry(DevPlan P) {
     long long nq = 1;
     for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
     const int ncomp = d * (d + 1) / 2;
-    const Patch& pt = *P.patch;
+    const Patch& pt = P.patch[g.patch];
     for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
         double xi[3], wq;
@@ -112,7 +112,7 @@ __global__ void k_geometry(DevPlan P) {
             s *= exp(P.famp * f);
         }
         double det = metric(d, J, s, Gp);
-        if (!(det > 0.0)) atomicOr(&P.flags[0], 1);
+        if (!(det * (pt.orient < 0 ? -1.0 : 1.0) > 0.0)) atomicOr(&P.flags[0], 1);
         long long o = t.g_off + idx;
         int c = 0;
         for (int a = 0; a < d; ++a)
@@ -160,7 +160,7 @@ __global__ void k_qp_coords(DevPlan P, double* xq) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
         double xi[3], wq, x[3], J[3][3];
         qp_param(P, g, L, xi, wq);
-        patch_eval(*P.patch, xi, x, J);
+        patch_eval(P.patch[g.patch], xi, x, J);
         long long nat = natural_index(g, d, Q, L);
         for (int k = 0; k < d; ++k) xq[(long long)k * P.nqp + nat] = x[k];
     }
@@ -206,6 +206,9 @@ __device__ double builtin_source(int src, int d, const double* x) {
         if (d == 2) return -lap2;
         return (-lap2 + pi * pi * u2) * sin(pi * x[2]);
     }
+    case SRC_LSHAPE_CORNER:
+    case SRC_HARMONIC_QUADRATIC:   // harmonic: f = 0, the data is on the boundary
+        return 0.0;
     default:
         return 1.0;
     }
@@ -225,7 +228,7 @@ __global__ void k_rhs_density(DevPlan P, int src, const double* __restrict__ fna
         } else {
             double xi[3], wq, x[3], J[3][3];
             qp_param(P, g, L, xi, wq);
-            patch_eval(*P.patch, xi, x, J);
+            patch_eval(P.patch[g.patch], xi, x, J);
             f = builtin_source(src, d, x);
         }
         long long o = t.g_off + idx;
@@ -244,7 +247,7 @@ __global__ void k_source_qp(DevPlan P, int src, double* __restrict__ fout) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
         double xi[3], wq, x[3], J[3][3];
         qp_param(P, g, L, xi, wq);
-        patch_eval(*P.patch, xi, x, J);
+        patch_eval(P.patch[g.patch], xi, x, J);
         fout[natural_index(g, d, Q, L)] = builtin_source(src, d, x);
     }
 }

@@ -6,13 +6,26 @@
 #define SGIGA_MAXP 4
 #define SGIGA_MAXQ (SGIGA_MAXP + 1)
 
-// One component grid. Physical directions are 0..d-1 (direction 0 fastest in
-// every packed or natural array).
+// Built-in sources with Dirichlet data (values of SGIGA_SRC_* in sgiga.h).
+enum { SRC_LSHAPE_CORNER = 5, SRC_HARMONIC_QUADRATIC = 6 };
+
+// One piece of a component grid: the component's tensor-product space on one
+// geometry patch (single-patch domains: the whole component). Physical
+// directions are 0..d-1 (direction 0 fastest in every packed or natural
+// array).
+//
+// Function (f_0, f_1, ..) of the piece (full 1D indices 0..nf-1) is kept (a
+// degree of freedom) if klo[k] <= f_k <= nf[k]-2 in every direction and it is
+// not the excluded (0,0) corner (xcorner). It is stored at
+//   dof_off + sum_k (f_k - slo[k]) * stride_k   (strides from n[]),
+// except where f_k = 0 < slo[k] with alias[k] >= 0: that function is the same
+// global function as (.., 0, ..) of piece alias[k] and is stored there. The
+// high end of every direction is a Dirichlet end.
 struct GridDesc {
     int lev[3];        // i_k
     int E[3];          // elements 2^{i_k}
-    int nf[3];         // B-splines incl. the two Dirichlet ones
-    int n[3];          // interior DoFs nf - 2
+    int nf[3];         // B-splines incl. the end functions
+    int n[3];          // stored DoFs per direction: nf - 1 - slo
     int tab[3];        // 1D table id per direction
     int eig[3];        // 1D eigen table id per direction
     int perm[3];       // logical axis (a = pencil, b, c) -> physical direction
@@ -23,6 +36,34 @@ struct GridDesc {
     long long qp_off, nqp;   // natural qp numbering
     long long tqp_off;       // first qp of this grid in tile-major numbering
     double coeff;
+    int comp;                // component (CG system) of this piece
+    int patch;               // geometry patch
+    int klo[3];              // first kept function: 1 after a Dirichlet end, 0 at a patch interface
+    int slo[3];              // first stored function (klo, or 1 where alias[k] stores f_k = 0)
+    int alias[3];            // piece that stores the f_k = 0 functions, or -1
+    int xcorner;             // the (0,0) function is a Dirichlet function of a neighbouring patch
+    int fn[3];               // kept functions per direction, nf - 1 - klo (preconditioner tensor)
+    long long fd_off, fd_n;  // that tensor in the preconditioner's local layout
+    long long gf_off;        // full boundary-coefficient array [nf_1][nf_0] (multi-patch), else -1
+};
+
+// One component (CG system): its pieces are consecutive, and so are its
+// stored DoFs and its vector chunks.
+struct CompDesc {
+    int piece0, npieces;
+    int chunk0, nchunk;
+    long long dof_off, ndof;
+    double coeff;
+};
+
+// One Dirichlet side of one piece (multi-patch boundary data): direction k
+// fixed at end (0 or 1); the side's parameter runs along direction 1-k (2D).
+// g is given at 2 + E*Q points from goff: the two side ends, then the Gauss
+// points of the side's elements.
+struct SideDesc {
+    int piece, k, end;
+    long long goff;          // into the boundary data array
+    long long soff;          // scratch of the projection: nf*(p+1) + nf doubles
 };
 
 // One tile of elements: the unit of work of the operator kernels.
@@ -47,11 +88,13 @@ struct Eig1D {
     long long loff;     // lambda [n] at loff
 };
 
-// Vector chunk: a contiguous piece of one grid's packed vector.
+// Vector chunk: a contiguous piece of one component's packed vector (or of
+// one piece's preconditioner tensor); grid = the component (scalar slot).
 struct Chunk {
     int grid;
     int len;
     long long start;
+    int piece;
 };
 
 // Work item of the batched mode product of the preconditioner.
@@ -75,4 +118,31 @@ struct Patch {
     double knots[3][12];
     double w[3][8];       // 1D weights per direction (W = prod_k W_k)
     double cp[128][3];    // control points, direction 0 fastest
+    int orient;           // -1: the map reverses orientation (det J < 0 everywhere), else +1 (0 reads as +1)
 };
+
+// Packed address of function (f0, f1) of a 2D piece (see GridDesc); the
+// function must be kept.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline long long piece_addr2(const GridDesc* grids, const GridDesc& g, int f0, int f1) {
+    if (f0 == 0 && g.slo[0] > 0 && g.alias[0] >= 0) {
+        const GridDesc& h = grids[g.alias[0]];
+        return h.dof_off + (0 - h.slo[0]) + (long long)(f1 - h.slo[1]) * h.n[0];
+    }
+    if (f1 == 0 && g.slo[1] > 0 && g.alias[1] >= 0) {
+        const GridDesc& h = grids[g.alias[1]];
+        return h.dof_off + (f0 - h.slo[0]) + (long long)(0 - h.slo[1]) * h.n[0];
+    }
+    return g.dof_off + (f0 - g.slo[0]) + (long long)(f1 - g.slo[1]) * g.n[0];
+}
+
+// Whether function (f0, f1) of a 2D piece is a degree of freedom.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline bool piece_kept2(const GridDesc& g, int f0, int f1) {
+    return f0 >= g.klo[0] && f0 <= g.nf[0] - 2 && f1 >= g.klo[1] && f1 <= g.nf[1] - 2 &&
+           !(g.xcorner && f0 == 0 && f1 == 0);
+}

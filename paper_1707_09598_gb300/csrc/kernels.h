@@ -50,8 +50,27 @@ struct DevPlan {
     double famp;
     size_t smem_op;          // dynamic shared bytes of the operator kernel
     int diag;                // every geometry plane off the diagonal is exactly zero
+    const CompDesc* comps;   // components (CG systems); pieces are grids[]
+    int ncomps;
+    int multipatch;          // pieces alias interface functions (GridDesc)
+    const Chunk* fdchunks;   // chunks of the preconditioner's local layout
+    int nfdchunks;
+    long long nfd;           // entries of that layout (= ndof for single-patch plans)
+    double* gfull;           // boundary-coefficient arrays of the pieces (multi-patch)
+    const SideDesc* sides;   // Dirichlet sides (multi-patch)
+    int nsides;
+    double* gdata;           // boundary data g at the sides' points
+    double* gscratch;        // projection scratch
 };
 
+// boundary.cu (multi-patch Dirichlet data)
+cudaError_t launch_boundary_points(const DevPlan& P, double* xb, cudaStream_t s);
+cudaError_t launch_boundary_builtin(const DevPlan& P, int src, const double* xb, double* gdata, long long n,
+                                    cudaStream_t s);
+cudaError_t launch_boundary_project(const DevPlan& P, cudaStream_t s);
+// eval.cu: values and physical gradients (2D)
+cudaError_t launch_eval_grad(const DevPlan& P, const double* coeffs, const double* xi, const int* patch,
+                             long long npts, double* ucomp, double* gcomp, int lifting, cudaStream_t s);
 // basis.cu
 cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
 // geometry.cu
@@ -74,6 +93,10 @@ cudaError_t set_op3_smem(int p, size_t bytes);
 template <typename Real>
 cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
                            const Real* in, Real* out, const int* active, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_gather(const DevPlan& P, const Real* r, Real* loc, const int* active, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_scatter(const DevPlan& P, const Real* loc, Real* z, const int* active, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_fd_scale(const DevPlan& P, Real* z, const int* active, cudaStream_t s);
 // vec.cu (Real = double or float; scalars and reductions in FP64)

@@ -41,9 +41,19 @@ struct sgiga_plan_s {
     std::vector<int> eig_of_tab;
     std::vector<Eig1D> eigs;
     std::vector<Chunk> chunks;
+    std::vector<CompDesc> comps;         // components (CG systems); grids are their pieces
+    std::vector<Chunk> fdchunks;         // chunks of the preconditioner's local layout
+    std::vector<SideDesc> sides;         // Dirichlet sides (multi-patch)
+    long long nfd = 0, ngf = 0, ngdata = 0, nscratch = 0;
+    bool multipatch = false;
+    bool lifting = false;                // boundary data set: the load vector subtracts K_IB g_B
+    double* d_l0 = nullptr;              // preconditioner local layout (multi-patch)
+    float* f_l0 = nullptr;
     std::vector<FDItem> fd[3];
     std::vector<double> knots, bp;
-    Patch patch;
+    Patch patch;                         // patch 0 (rational directions of the 1D tables)
+    std::vector<Patch> patches;          // every geometry patch
+    double* d_xb = nullptr;              // boundary data points [nbpts][2] (multi-patch)
     long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
     int maxE = 1;
     int fd_ks = 128;            // contraction depth per preconditioner work item
@@ -146,6 +156,9 @@ inline int run_rhs_operator(sgiga_plan_s* P) {
     CUDA_TRY(cudaMemsetAsync(P->d_b, 0, (size_t)P->ndof * 8, P->stream));
     if (P->d == 3) CUDA_TRY(launch_op3(D, nullptr, P->d_b, nullptr, 1, P->stream));
     else CUDA_TRY(launch_op2(D, nullptr, P->d_b, nullptr, 1, P->stream));
+    // nonhomogeneous Dirichlet data: b -= K_IB g_B (mode 2 reads the pieces'
+    // boundary-coefficient arrays)
+    if (P->lifting) CUDA_TRY(launch_op2(D, nullptr, P->d_b, nullptr, 2, P->stream));
     return SGIGA_OK;
 }
 
@@ -187,8 +200,14 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     const int d = P->d;
     const Real* in = r;
     Real* bufs[2] = {t1, t2};
+    Real* loc = nullptr;
     int cur = 0;
-    const size_t bytes = (size_t)P->ndof * sizeof(Real);
+    const size_t bytes = (size_t)P->nfd * sizeof(Real);
+    if (P->multipatch) {   // additive Schwarz: gather each piece's kept functions
+        loc = sizeof(Real) == 8 ? (Real*)P->d_l0 : (Real*)P->f_l0;
+        CUDA_TRY(launch_fd_gather<Real>(D, r, loc, active, s));
+        in = loc;
+    }
     for (int k = 0; k < d; ++k) {
         Real* out = bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
@@ -198,11 +217,15 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     }
     CUDA_TRY(launch_fd_scale<Real>(D, (Real*)in, active, s));
     for (int k = 0; k < d; ++k) {
-        Real* out = (k == d - 1) ? z : bufs[cur];
+        Real* out = (k == d - 1) ? (loc ? loc : z) : bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
         CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
         in = out;
         cur ^= 1;
+    }
+    if (loc) {
+        CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)P->ndof * sizeof(Real), s));
+        CUDA_TRY(launch_fd_scatter<Real>(D, loc, z, active, s));
     }
     return SGIGA_OK;
 }
@@ -240,7 +263,7 @@ template <typename Real>
 inline int pcg_body_a(sgiga_plan_s* P, Vecs<Real> v, double tol, int* active, int* iters, double* scal) {
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     double* bb = scal + 0 * ng;
     double* rz = scal + 1 * ng;
     double* pq = scal + 2 * ng;
@@ -259,7 +282,7 @@ template <typename Real>
 inline int pcg_body_b(sgiga_plan_s* P, Vecs<Real> v, int* active, double* scal, bool flexible) {
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     double* rz = scal + 1 * ng;
     double* beta = scal + 5 * ng;
     double* rznew = scal + 6 * ng;
@@ -343,7 +366,7 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
                int* active, int* iters, double* scal, int* iters_run, PcgHook* hook = nullptr) {
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     double* bb = scal + 0 * ng;
     double* rz = scal + 1 * ng;
     // a learned (nonlinear) preconditioner needs the flexible (Polak-Ribiere) beta
@@ -398,7 +421,7 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
 inline int solve_stats(sgiga_plan_s* P, const double* rr, const double* bb, const int* iters, int nact,
                        sgiga_solve_stats* stats, std::chrono::steady_clock::time_point t0) {
     if (!stats) return SGIGA_OK;
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     cudaStream_t s = P->stream;
     std::vector<double> hrr(ng), hbb(ng);
     std::vector<int> hit(ng);

@@ -1,8 +1,8 @@
-// Batched preconditioned-CG vector kernels: every component grid keeps its own
+// Batched preconditioned-CG vector kernels: every component keeps its own
 // scalars (alpha, beta, residual norms) and convergence flag. Packed vectors
-// are cut into chunks of at most 4096 entries that never straddle two grids;
-// a block reduces its chunk, and a second kernel sums each grid's chunk
-// partials in a fixed order (deterministic dot products). Vectors may be FP64
+// are cut into chunks of at most 4096 entries that never straddle two
+// components; a block reduces its chunk, and a second kernel sums each
+// component's chunk partials in a fixed order (deterministic dot products). Vectors may be FP64
 // or FP32; scalars and reductions are FP64.
 #include "kernels.h"
 
@@ -24,19 +24,19 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-__global__ void k_reduce(const GridDesc* __restrict__ grids, int ngrids, const double* __restrict__ partial,
+__global__ void k_reduce(const CompDesc* __restrict__ comps, int ncomps, const double* __restrict__ partial,
                          double* __restrict__ out) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ngrids) return;
+    if (g >= ncomps) return;
     double s = 0.0;
-    const int c0 = grids[g].chunk0, nc = grids[g].nchunk;
+    const int c0 = comps[g].chunk0, nc = comps[g].nchunk;
     for (int c = 0; c < nc; ++c) s += partial[c0 + c];
     out[g] = s;
 }
 
 static cudaError_t reduce(const DevPlan& P, const double* partial, double* out, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_reduce<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.grids, P.ngrids, partial, out);
+    k_reduce<<<(P.ncomps + 127) / 128, 128, 0, s>>>(P.comps, P.ncomps, partial, out);
     return cudaGetLastError();
 }
 
@@ -183,7 +183,7 @@ __global__ void k_alpha(int ng, const double* __restrict__ rz, const double* __r
 cudaError_t launch_pcg_alpha(const DevPlan& P, const double* rz, const double* pq, double* alpha,
                              const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_alpha<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, rz, pq, alpha, active);
+    k_alpha<<<(P.ncomps + 127) / 128, 128, 0, s>>>(P.ncomps, rz, pq, alpha, active);
     return cudaGetLastError();
 }
 
@@ -202,7 +202,7 @@ __global__ void k_beta(int ng, double* __restrict__ rz, const double* __restrict
 cudaError_t launch_pcg_beta(const DevPlan& P, double* rz, const double* rznew, const double* rzmid, double* beta,
                             cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_beta<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, rz, rznew, rzmid, beta);
+    k_beta<<<(P.ncomps + 127) / 128, 128, 0, s>>>(P.ncomps, rz, rznew, rzmid, beta);
     return cudaGetLastError();
 }
 
@@ -222,7 +222,7 @@ cudaError_t launch_pcg_check(const DevPlan& P, const double* rr, const double* b
     cudaError_t e = cudaMemsetAsync(nactive, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_check<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, rr, bb, tol2, active, iters, nactive);
+    k_check<<<(P.ncomps + 127) / 128, 128, 0, s>>>(P.ncomps, rr, bb, tol2, active, iters, nactive);
     return cudaGetLastError();
 }
 
@@ -238,7 +238,7 @@ __global__ void k_start(int ng, const double* __restrict__ bb, const int* __rest
 cudaError_t launch_pcg_start(const DevPlan& P, const double* bb, const int* outer, int* active, int* iters,
                              cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_start<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P.ngrids, bb, outer, active, iters);
+    k_start<<<(P.ncomps + 127) / 128, 128, 0, s>>>(P.ncomps, bb, outer, active, iters);
     return cudaGetLastError();
 }
 

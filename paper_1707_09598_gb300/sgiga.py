@@ -26,11 +26,12 @@ SGIGA_ERR_NOT_CONVERGED = -4
 SGIGA_ERR_TIMEOUT = -5
 SGIGA_ERR_GEOMETRY = -6
 
-DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1, "patch": 2}
+DOMAIN = {"unit": 0, "square": 0, "cube": 0, "annulus": 1, "patch": 2, "lshape": 3}
 GRADING = {"uniform": 0, "radical": 1, "onesided": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 PRECOND = {"fd": 0, "none": 1, "learned": 2}
-SOURCE = {"sine": 0, "poly": 1, "annulus": 2, "annulus_paper": 3, "one": 4}
+SOURCE = {"sine": 0, "poly": 1, "annulus": 2, "annulus_paper": 3, "one": 4, "lshape_corner": 5,
+          "harmonic_quadratic": 6}
 
 
 class sgiga_patch(ctypes.Structure):
@@ -48,7 +49,8 @@ class sgiga_config(ctypes.Structure):
 class sgiga_info(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("ngrids", ctypes.c_int),
                 ("ndof", ctypes.c_longlong), ("nqp", ctypes.c_longlong), ("max_tile_smem", ctypes.c_int),
-                ("ntiles", ctypes.c_int), ("diag_metric", ctypes.c_int)]
+                ("ntiles", ctypes.c_int), ("diag_metric", ctypes.c_int), ("npatches", ctypes.c_int),
+                ("nbpts", ctypes.c_longlong)]
 
 
 class sgiga_grid(ctypes.Structure):
@@ -107,6 +109,9 @@ _SIGS = {
     "sgiga_get_solution": (_I, [_P, _P]),
     "sgiga_set_solution": (_I, [_P, _P]),
     "sgiga_eval": (_I, [_P, _P, _L, _P]),
+    "sgiga_eval_grad": (_I, [_P, _P, _P, _L, _P, _P]),
+    "sgiga_boundary_points": (_I, [_P, _P]),
+    "sgiga_set_dirichlet": (_I, [_P, _P]),
     "sgiga_combine": (_I, [_P, _P, _L, _P]),
     "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "sgiga_geometry_coeffs": (_I, [_P, _I, _P, _P]),
@@ -299,6 +304,22 @@ def sgiga_set_solution(plan, u):
 def sgiga_eval(plan, xi, npts, u_comp):
     info = sgiga_plan_info(plan)
     _check(_lib.sgiga_eval(plan, _ptr(xi, npts * info.d), int(npts), _ptr(u_comp, npts * info.ngrids)))
+
+
+def sgiga_eval_grad(plan, xi, patch, npts, u_comp, grad_comp=None):
+    """Values [ngrids][npts] and physical gradients [2][ngrids][npts] (2D)."""
+    info = sgiga_plan_info(plan)
+    _check(_lib.sgiga_eval_grad(plan, _ptr(xi, npts * 2), _ptr(patch, npts, dtype=np.int32), int(npts),
+                                _ptr(u_comp, npts * info.ngrids),
+                                _ptr(grad_comp, 2 * npts * info.ngrids) if grad_comp is not None else None))
+
+
+def sgiga_boundary_points(plan, xb):
+    _check(_lib.sgiga_boundary_points(plan, _ptr(xb, 2 * sgiga_plan_info(plan).nbpts)))
+
+
+def sgiga_set_dirichlet(plan, g):
+    _check(_lib.sgiga_set_dirichlet(plan, None if g is None else _ptr(g, sgiga_plan_info(plan).nbpts)))
 
 
 def sgiga_combine(plan, u_comp, npts, u):

@@ -4,10 +4,12 @@ Calls only the oracle (oracle/) and the shared seeded input module. Run from
 the repository root:
 
     python tests/golden/make_golden.py cube_p3_w10
+    python tests/golden/make_golden.py lshape_p2_w11_g2
 
 Output: tests/golden/<name>.txt with, for each parametric evaluation point,
 the combined sparse-grid value sum_i c_i u_i(xi) and the values of a few
-selected components. The components are solved in parallel worker processes
+selected components (L-shape: the combined value and physical gradient at
+points of each patch). The components are solved in parallel worker processes
 (started with "spawn").
 """
 import multiprocessing as mp
@@ -28,6 +30,50 @@ CASES = {
     "annulus_p3_w12": ("annulus", 2, 3, 12, "annulus_sinx", 64, [(12, 1), (6, 6), (1, 12)]),
     "annulus_p4_w12": ("annulus", 2, 4, 12, "annulus_sinx", 64, [(12, 1), (6, 6), (1, 12)]),
 }
+
+
+# L-shape (three glued patches, Dirichlet data r^(2/3) sin(2 theta/3), one-sided
+# grading toward the corner): name -> (p, w, gamma, per-patch lattice k)
+LSHAPE = {
+    "lshape_p2_w11_g1": (2, 11, 1.0, 8),
+    "lshape_p2_w11_g2": (2, 11, 2.0, 8),
+    "lshape_p2_w11_g3": (2, 11, 3.0, 8),
+}
+
+
+def _one_lshape(args):
+    p, i, gamma, patch, pts = args
+    from oracle import multipatch
+    comp = multipatch.LShapeComponent(i, p, kind="onesided", gamma=gamma).assemble(g=multipatch.corner_u)
+    return comp.evaluate(comp.solve(), patch, pts)
+
+
+def main_lshape(name):
+    from oracle import combination
+    from paper_1707_09598_gb300.inputs import eval_points
+    p, w, gamma, k = LSHAPE[name]
+    lat = eval_points(2, k)
+    pts = np.concatenate([lat] * 3)
+    patch = np.repeat(np.arange(3), len(lat))
+    idx = combination.index_set(2, w)
+    t0 = time.time()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(8, os.cpu_count())) as pool:
+        res = pool.map(_one_lshape, [(p, i, gamma, patch, pts) for i, _ in idx], chunksize=1)
+    coeffs = np.array([c for _, c in idx], dtype=np.float64)
+    val = combination.combine(np.stack([r[0] for r in res]), coeffs)
+    gx = combination.combine(np.stack([r[1][:, 0] for r in res]), coeffs)
+    gy = combination.combine(np.stack([r[1][:, 1] for r in res]), coeffs)
+    out = os.path.join(HERE, name + ".txt")
+    with open(out, "w") as fh:
+        fh.write("# oracle values written by tests/golden/make_golden.py %s\n" % name)
+        fh.write("# L-shape, 3 patches, u = r^(2/3) sin(2 theta/3) on the Dirichlet sides, f = 0, p=%d C^%d, "
+                 "w=%d, one-sided grading gamma=%g toward the corner; points eval_points(2, %d) on each patch\n"
+                 % (p, p - 1, w, gamma, k))
+        fh.write("# columns: patch xi_1 xi_2 combined du/dx du/dy\n")
+        for q, x, v, a, b in zip(patch, pts, val, gx, gy):
+            fh.write("%d %.17e %.17e %.17e %.17e %.17e\n" % (q, x[0], x[1], v, a, b))
+    print("wrote %s in %.1f s" % (out, time.time() - t0))
 
 
 def _one(args):
@@ -66,4 +112,7 @@ def main(name):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    if sys.argv[1] in LSHAPE:
+        main_lshape(sys.argv[1])
+    else:
+        main(sys.argv[1])

@@ -1,0 +1,231 @@
+"""L-shaped domain (three glued patches, Dirichlet data, one-sided grading)
+through the C ABI against the oracle (oracle/multipatch.py).
+
+Operator, load vector with boundary lifting and preconditioner are compared
+entry by entry, after mapping the packed layout (sgiga.h, SGIGA_DOMAIN_LSHAPE)
+to the oracle's global numbering. Solutions are compared through evaluation
+(values and gradients), per component and combined. The full-size workload
+(p = 2, w = 11, gamma = 1, 2, 3) is checked against stored oracle values.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import combination, multipatch as mp  # noqa: E402
+from paper_1707_09598_gb300.inputs import random_points, random_vector  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+STORE_LO = ((0, 1), (1, 0), (1, 1))        # first stored function per direction, patches 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_09598_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1707_09598_gb300 import sgiga
+    return sgiga
+
+
+def _plan(sg, w, gamma=2.0, p=2, precision="fp64"):
+    return sg.Plan(2, p, w, domain="lshape", grading="onesided", gamma=gamma, precision=precision)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def _perm(comp, dof_off):
+    """Packed index of every oracle unknown (oracle interior ordering)."""
+    nf0, nf1 = comp.nf
+    pos = -np.ones(comp.nglob, dtype=np.int64)
+    pos[comp.interior] = np.arange(comp.ndof)
+    out = -np.ones(comp.ndof, dtype=np.int64)
+    off = dof_off
+    for q in range(3):
+        s0, s1 = STORE_LO[q]
+        n0 = nf0 - 1 - s0
+        for f1 in range(s1, nf1 - 1):
+            for f0 in range(s0, nf0 - 1):
+                k = pos[comp.ids[q][f0 + nf0 * f1]]
+                assert k >= 0
+                assert out[k] < 0, "stored twice"
+                out[k] = off + (f0 - s0) + (f1 - s1) * n0
+        off += n0 * (nf1 - 1 - s1)
+    assert (out >= 0).all(), "an unknown is not stored"
+    return out
+
+
+def _oracle_comp(g, gamma, p=2, data=mp.corner_u):
+    return mp.LShapeComponent(tuple(g.levels[:2]), p, kind="onesided", gamma=gamma).assemble(g=data)
+
+
+def test_layout_and_counts(sg):
+    with _plan(sg, 5) as P:
+        assert P.info.npatches == 3 and P.info.nbpts > 0
+        idx = combination.index_set(2, 5)
+        assert P.info.ngrids == len(idx)
+        tot = 0
+        for g, (i, c) in zip(P.grids, idx):
+            assert tuple(g.levels[:2]) == i and g.coeff == c
+            comp = _oracle_comp(g, 2.0)
+            assert g.ndof == comp.ndof
+            _perm(comp, g.dof_off)
+            tot += comp.ndof
+        assert P.info.ndof == tot
+
+
+@pytest.mark.parametrize("gamma", [1.0, 3.0])
+def test_operator_matches_glued_stiffness(sg, gamma):
+    with _plan(sg, 6, gamma) as P:
+        n = P.info.ndof
+        x = random_vector(n, seed=71)
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_apply(P.handle, torch.as_tensor(x, device="cuda"), y)
+        y = y.cpu().numpy()
+        for g in P.grids:
+            comp = _oracle_comp(g, gamma)
+            pm = _perm(comp, g.dof_off)
+            assert _rel(y[pm], comp.K @ x[pm]) < 1e-13, g.levels[:2]
+
+
+@pytest.mark.parametrize("source,data", [("lshape_corner", mp.corner_u), ("harmonic_quadratic", mp.harmonic_quadratic)])
+def test_load_vector_with_lifting(sg, source, data):
+    with _plan(sg, 5) as P:
+        sg.sgiga_set_rhs_builtin(P.handle, source)
+        b = np.zeros(P.info.ndof)
+        sg.sgiga_get_rhs(P.handle, b)
+        for g in P.grids:
+            comp = _oracle_comp(g, 2.0, data=data)
+            pm = _perm(comp, g.dof_off)
+            assert _rel(b[pm], comp.b) < 1e-12, g.levels[:2]
+
+
+def test_boundary_points_and_user_data(sg):
+    """sgiga_set_dirichlet with g computed by the caller at sgiga_boundary_points
+    gives the same load vector as the built-in data."""
+    with _plan(sg, 5) as P:
+        xb = np.zeros(2 * P.info.nbpts)
+        sg.sgiga_boundary_points(P.handle, xb)
+        xb = xb.reshape(-1, 2)
+        assert np.all(np.abs(xb) <= 1.0 + 1e-15)
+        assert not np.any((xb[:, 0] > 1e-15) & (xb[:, 1] < -1e-15))   # nothing in the removed quadrant
+        sg.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
+        b0 = np.zeros(P.info.ndof)
+        sg.sgiga_get_rhs(P.handle, b0)
+        sg.sgiga_set_dirichlet(P.handle, np.ascontiguousarray(mp.corner_u(xb)))
+        f = np.zeros(P.info.nqp)
+        sg.sgiga_set_rhs(P.handle, f)
+        b1 = np.zeros(P.info.ndof)
+        sg.sgiga_get_rhs(P.handle, b1)
+        assert _rel(b1, b0) < 1e-14
+
+
+def test_preconditioner_is_weighted_schwarz(sg):
+    with _plan(sg, 5) as P:
+        n = P.info.ndof
+        r = random_vector(n, seed=72)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_precond(P.handle, torch.as_tensor(r, device="cuda"), z)
+        z = z.cpu().numpy()
+        for g in P.grids:
+            comp = _oracle_comp(g, 2.0)
+            pm = _perm(comp, g.dof_off)
+            assert _rel(z[pm], mp.schwarz_apply(comp, r[pm])) < 1e-11, g.levels[:2]
+
+
+def _points(n=40, seed=73):
+    xi = random_points(3 * n, 2, seed=seed)
+    patch = np.repeat(np.arange(3), n).astype(np.int32)
+    return np.ascontiguousarray(xi), patch
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_solve_eval_against_oracle(sg, precision, tol):
+    xi, patch = _points()
+    with _plan(sg, 6, 2.0, precision=precision) as P:
+        sg.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
+        st, _ = sg.sgiga_solve(P.handle, 1e-12, 500)
+        assert st.converged == P.info.ngrids
+        ng, npts = P.info.ngrids, len(xi)
+        uc = np.zeros(ng * npts)
+        gc = np.zeros(2 * ng * npts)
+        sg.sgiga_eval_grad(P.handle, xi, patch, npts, uc, gc)
+        uc, gc = uc.reshape(ng, npts), gc.reshape(2, ng, npts)
+        coef = []
+        ov, og = [], []
+        for k, g in enumerate(P.grids):
+            comp = _oracle_comp(g, 2.0)
+            v, gr = comp.evaluate(comp.solve(), patch, xi)
+            assert _rel(uc[k], v) < tol, g.levels[:2]
+            assert _rel(gc[:, k, :].T, gr) < 10 * tol, g.levels[:2]
+            ov.append(v)
+            og.append(gr)
+            coef.append(g.coeff)
+        u = np.zeros(npts)
+        sg.sgiga_combine(P.handle, uc.reshape(-1), npts, u)
+        assert _rel(u, combination.combine(np.stack(ov), np.array(coef, float))) < tol
+
+
+def test_harmonic_quadratic_is_reproduced(sg):
+    xi, patch = _points(30, 74)
+    with _plan(sg, 7, 3.0) as P:
+        sg.sgiga_set_rhs_builtin(P.handle, "harmonic_quadratic")
+        sg.sgiga_solve(P.handle, 1e-13, 800)
+        ng, npts = P.info.ngrids, len(xi)
+        uc = np.zeros(ng * npts)
+        gc = np.zeros(2 * ng * npts)
+        sg.sgiga_eval_grad(P.handle, xi, patch, npts, uc, gc)
+        u = np.zeros(npts)
+        sg.sgiga_combine(P.handle, uc, npts, u)
+        x = np.concatenate([mp.physical(q, xi[patch == q]) for q in range(3)])
+        assert np.abs(u - mp.harmonic_quadratic(x)).max() < 1e-9
+        gx = np.zeros(npts)
+        sg.sgiga_combine(P.handle, np.ascontiguousarray(gc[:ng * npts]), npts, gx)
+        assert np.abs(gx - (2.0 + x[:, 0] + x[:, 1])).max() < 1e-7
+
+
+def test_errors_are_reported(sg):
+    with _plan(sg, 5) as P:
+        with pytest.raises(sg.SgigaError):
+            sg.sgiga_eval(P.handle, np.zeros(2), 1, np.zeros(P.info.ngrids))
+        bad = np.array([3], dtype=np.int32)
+        with pytest.raises(sg.SgigaError):
+            sg.sgiga_eval_grad(P.handle, np.full(2, 0.5), bad, 1, np.zeros(P.info.ngrids))
+    with pytest.raises(sg.SgigaError):
+        sg.Plan(3, 2, 5, domain="lshape")
+    with sg.Plan(2, 2, 4) as P:
+        with pytest.raises(sg.SgigaError):
+            sg.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
+
+
+@pytest.mark.parametrize("gamma", [1, 2, 3])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
+    path = os.path.join(GOLD, "lshape_p2_w11_g%d.txt" % gamma)
+    data = np.loadtxt(path)
+    patch = np.ascontiguousarray(data[:, 0].astype(np.int32))
+    xi = np.ascontiguousarray(data[:, 1:3])
+    with _plan(sg, 11, float(gamma), precision=precision) as P:
+        sg.sgiga_autotune(P.handle, reps=2)
+        sg.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
+        st, _ = sg.sgiga_solve(P.handle, 1e-12, 3000)
+        assert st.converged == P.info.ngrids
+        ng, npts = P.info.ngrids, len(xi)
+        uc = torch.zeros(ng * npts, dtype=torch.float64, device="cuda")
+        gc = torch.zeros(2 * ng * npts, dtype=torch.float64, device="cuda")
+        sg.sgiga_eval_grad(P.handle, torch.as_tensor(xi, device="cuda"), torch.as_tensor(patch, device="cuda"),
+                           npts, uc, gc)
+        u = torch.zeros(npts, dtype=torch.float64, device="cuda")
+        sg.sgiga_combine(P.handle, uc, npts, u)
+        assert _rel(u.cpu().numpy(), data[:, 3]) < tol
+        for c in range(2):
+            gcomb = torch.zeros(npts, dtype=torch.float64, device="cuda")
+            sg.sgiga_combine(P.handle, gc[c * ng * npts:(c + 1) * ng * npts], npts, gcomb)
+            assert _rel(gcomb.cpu().numpy(), data[:, 4 + c]) < 10 * tol
