@@ -132,6 +132,9 @@ typedef struct {
     int precision;    /* SGIGA_PREC_* */
     int precond;      /* SGIGA_PRECOND_* */
     const sgiga_patch* patch; /* geometry for SGIGA_DOMAIN_PATCH (host), else NULL */
+    int ncomponents;  /* > 0: the plan holds only these components of the index
+                         set (e.g. one, to solve the grids one at a time); 0: all */
+    const int* components; /* [ncomponents][d] levels (host), each in the index set of w */
 } sgiga_config;
 
 typedef struct {
@@ -162,8 +165,12 @@ typedef struct {
     double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
     double seconds;          /* wall time of the call */
     int inner_iterations;    /* MIXED_FP32: inner CG iterations summed over refinement steps */
-    int fallback;            /* LEARNED: 1 if a refinement step without a tenfold residual
-                                reduction switched the rest of the solve to FD */
+    int fallback;            /* MIXED_FP32 bit flags. 1 (LEARNED): a refinement step without a
+                                tenfold residual reduction switched the rest of the solve to FD.
+                                2: refinement stalled (two steps that did not halve some
+                                component's residual: the FP32 operator's error times the
+                                condition number is not small) and FP64 PCG finished the
+                                remaining components from the current residual */
 } sgiga_solve_stats;
 
 /* Build a plan: index set and coefficients (Sec. 3), knot vectors and

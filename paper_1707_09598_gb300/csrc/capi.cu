@@ -406,6 +406,23 @@ static int build(sgiga_plan_s* P) {
         for (int k = 0; k < d; ++k) if (a[k] != b[k]) return a[k] < b[k];
         return false;
     });
+    if (c.ncomponents > 0) {   // keep only the listed components (in index-set order)
+        if (!c.components) return fail(SGIGA_ERR_ARG, "components is NULL");
+        std::vector<std::array<int, 3>> keep;
+        for (int i = 0; i < c.ncomponents; ++i) {
+            std::array<int, 3> lv3 = {0, 0, 0};
+            for (int k = 0; k < d; ++k) lv3[k] = c.components[i * d + k];
+            if (std::find(idx.begin(), idx.end(), lv3) == idx.end())
+                return fail(SGIGA_ERR_ARG, "a listed component is not in the index set of w");
+        }
+        for (auto& iv : idx)
+            for (int i = 0; i < c.ncomponents; ++i) {
+                bool same = true;
+                for (int k = 0; k < d; ++k) same = same && iv[k] == c.components[i * d + k];
+                if (same) { keep.push_back(iv); break; }
+            }
+        idx.swap(keep);
+    }
     if (idx.empty()) return fail(SGIGA_ERR_ARG, "empty index set");
     for (auto& iv : idx)
         for (int k = 0; k < d; ++k) if (iv[k] > 20) return fail(SGIGA_ERR_ARG, "level above 20");
@@ -734,7 +751,7 @@ static int build(sgiga_plan_s* P) {
             (rc = dalloc(P, &P->f_q, nd)) || (rc = dalloc(P, &P->f_t1, nt)) || (rc = dalloc(P, &P->f_t2, nt)) ||
             (mp && (rc = dalloc(P, &P->f_l0, (size_t)P->nfd))) ||
             (rc = dalloc(P, &P->d_active_o, ng)) || (rc = dalloc(P, &P->d_iters_o, ng)) ||
-            (rc = dalloc(P, &P->d_scal64o, 8 * ng)))
+            (rc = dalloc(P, &P->d_scal64o, 8 * ng)) || (rc = dalloc(P, &P->d_d, nd)))
             return rc;
         CUDA_TRY(launch_narrow(Gf, D.G, (long long)ncomp * P->nqp, s));
         CUDA_TRY(launch_narrow(Rf, D.R, ntab, s));
@@ -1172,21 +1189,50 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     CUDA_TRY(launch_pcg_init<double>(D, P->d_b, P->d_x, P->d_r, P->d_partial, bb, s));
     CUDA_TRY(launch_copy<double>(rr, bb, ng, s));
     CUDA_TRY(launch_pcg_start(D, bb, nullptr, P->d_active_o, P->d_iters_o, s));
-    int nact = ng, outer = 0, inner_total = 0;
+    int nact = ng, outer = 0, inner_total = 0, stalls = 0;
+    bool fp64_fallback = false;
     P->learned_off = false;
     double prev_worst = 0.0;
-    std::vector<double> hrr(ng), hbb(ng);
+    std::vector<double> hrr(ng), hbb(ng), prev_rr(ng, 0.0);
+    std::vector<int> hact(ng);
     for (outer = 0; outer <= max_iter; ++outer) {
         // convergence of the FP64 residual (also counts outer steps per grid)
         CUDA_TRY(launch_pcg_check(D, rr, bb, rel_tol * rel_tol, P->d_active_o, P->d_iters_o, P->d_nactive, s));
         CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if (P->cfg.precond == SGIGA_PRECOND_LEARNED) {
-            CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
-        }
+        CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, ng * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(hact.data(), P->d_active_o, ng * 4, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         nact = *P->h_nactive;
         if (nact == 0 || outer == max_iter) break;
+        // A refinement step that does not halve an active component's residual
+        // means the FP32 inner operator is too far from the FP64 one for this
+        // system (its error times the condition number is not small). After two
+        // such steps the remaining components are finished by FP64 PCG on the
+        // current residual: d = K^{-1} r, x += d (the plain method).
+        bool stalled = false;
+        for (int g = 0; g < ng; ++g)
+            if (outer > 0 && hact[g] && hrr[g] > 0.25 * prev_rr[g]) stalled = true;
+        prev_rr = hrr;
+        stalls = stalled ? stalls + 1 : 0;
+        if (stalls >= 2 && P->cfg.precond != SGIGA_PRECOND_LEARNED) {
+            double ratio = 1.0;   // tightest ||b_g|| / ||r_g|| over the active components
+            for (int g = 0; g < ng; ++g)
+                if (hact[g] && hrr[g] > 0) ratio = std::min(ratio, std::sqrt(hbb[g] / hrr[g]));
+            const double tol64 = std::max(0.5 * rel_tol * ratio, 1e-15);
+            Vecs<double> v{P->d_d, P->d_r, P->d_z, P->d_p, P->d_q, P->d_t1, P->d_t2};
+            int it64 = 0;
+            int rc = pcg<double>(P, P->d_r, v, tol64, max_iter * 10, P->d_active_o, P->d_active, P->d_iters,
+                                 P->d_scal, &it64);
+            if (rc < 0) return rc;
+            inner_total += it64;
+            CUDA_TRY(launch_ir_up64(D, P->d_x, P->d_d, P->d_active_o, s));
+            if ((rc = apply_op(P, P->d_x, P->d_q, P->d_active_o))) return rc;
+            CUDA_TRY(launch_ir_residual(D, P->d_b, P->d_q, P->d_r, P->d_active_o, P->d_partial, rr, s));
+            fp64_fallback = true;
+            stalls = 0;
+            continue;
+        }
         if (P->cfg.precond == SGIGA_PRECOND_LEARNED) {
             // fall back to FD for the rest of the solve when a refinement step
             // with the learned preconditioner does not cut the worst residual by 10
@@ -1212,7 +1258,7 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     if (stats) {
         stats->iterations = outer;
         stats->inner_iterations = inner_total;
-        stats->fallback = P->learned_off ? 1 : 0;
+        stats->fallback = (P->learned_off ? 1 : 0) | (fp64_fallback ? 2 : 0);
     }
     P->learned_off = false;
     if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");

@@ -67,6 +67,7 @@ struct sgiga_plan_s {
     int* d_active_o = nullptr;  // outer (refinement) mask
     int* d_iters_o = nullptr;
     double* d_scal64o = nullptr;
+    double* d_d = nullptr;      // FP64 correction of the refinement's FP64 fallback
     float *f_b = nullptr, *f_x = nullptr, *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_q = nullptr;
     float *f_t1 = nullptr, *f_t2 = nullptr;
     double inner_tol = 1e-5;
@@ -94,6 +95,7 @@ struct sgiga_plan_s {
         double tol = -1.0;
         int max_iter = -1;
         const void* rhs = nullptr;
+        const void* xbuf = nullptr;
         const int* outer = nullptr;
         bool flexible = false;
         bool failed = false;
@@ -304,7 +306,7 @@ inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real
                           int max_iter, const int* outer, int* active, int* iters, double* scal, bool flexible) {
     cudaStream_t ls = P->stream ? P->stream : P->own_stream;
     const bool same = L.exec && L.tol == tol && L.max_iter == max_iter && L.rhs == rhs && L.outer == outer &&
-                      L.flexible == flexible;
+                      L.flexible == flexible && L.xbuf == (const void*)v.x;
     if (!same) {
         destroy_loop_graph(L);
         cudaGraph_t g = nullptr;
@@ -347,6 +349,7 @@ inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real
         L.tol = tol;
         L.max_iter = max_iter;
         L.rhs = rhs;
+        L.xbuf = v.x;
         L.outer = outer;
         L.flexible = flexible;
     }

@@ -274,17 +274,24 @@ cudaError_t launch_ir_down(const DevPlan& P, const double* r64, float* r32, cons
     return cudaGetLastError();
 }
 
-// x64 += (double) d32 on active grids
-__global__ void k_ir_up(const Chunk* __restrict__ chunks, double* __restrict__ x64, const float* __restrict__ d32,
+// x64 += d on active grids (d FP32 from the inner solve, or FP64 from the fallback)
+template <typename Real>
+__global__ void k_ir_up(const Chunk* __restrict__ chunks, double* __restrict__ x64, const Real* __restrict__ d,
                         const int* __restrict__ active) {
     const Chunk c = chunks[blockIdx.x];
     if (!active[c.grid]) return;
-    for (int i = threadIdx.x; i < c.len; i += blockDim.x) x64[c.start + i] += (double)d32[c.start + i];
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) x64[c.start + i] += (double)d[c.start + i];
 }
 
 cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_ir_up<<<P.nchunks, 256, 0, s>>>(P.chunks, x64, d32, active);
+    k_ir_up<float><<<P.nchunks, 256, 0, s>>>(P.chunks, x64, d32, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_up64(const DevPlan& P, double* x64, const double* d64, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_ir_up<double><<<P.nchunks, 256, 0, s>>>(P.chunks, x64, d64, active);
     return cudaGetLastError();
 }
 

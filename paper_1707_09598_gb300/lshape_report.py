@@ -106,7 +106,7 @@ def main():
             h1 = float(np.sqrt(np.sum(wt * np.sum(dg * dg, 1))))
             rows.append({"w": w, "ngrids": ng, "ndof": P.info.ndof, "l2": l2, "h1": h1,
                          "solve_ms": e0.elapsed_time(e1), "outer": st.iterations, "inner": st.inner_iterations,
-                         "max_rel_residual": st.max_rel_residual})
+                         "max_rel_residual": st.max_rel_residual, "fp64_fallback": bool(st.fallback & 2)})
             P.close()
         ws = [r["w"] for r in rows]
         out["results"]["gamma=%g" % gamma] = {

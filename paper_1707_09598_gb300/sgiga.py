@@ -43,7 +43,8 @@ class sgiga_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("continuity", ctypes.c_int), ("w", ctypes.c_int),
                 ("min_level", ctypes.c_int), ("domain", ctypes.c_int), ("grading", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
-                ("patch", ctypes.POINTER(sgiga_patch))]
+                ("patch", ctypes.POINTER(sgiga_patch)), ("ncomponents", ctypes.c_int),
+                ("components", ctypes.POINTER(ctypes.c_int))]
 
 
 class sgiga_info(ctypes.Structure):
@@ -172,8 +173,9 @@ def _ptr(buf, n=None, dtype=np.float64):
 # --- entry points (same names as the C ABI) ------------------------------------
 
 def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="uniform", gamma=1.0,
-               precision="fp64", precond="fd", stream=None, patch=None):
-    """patch: (degrees [d], knots [d arrays], control points [n, d]) for domain "patch"."""
+               precision="fp64", precond="fd", stream=None, patch=None, components=None):
+    """patch: (degrees [d], knots [d arrays], control points [n, d]) for domain "patch";
+    components: levels of the components to keep (default: the whole index set)."""
     keep = []
     pp = None
     if patch is not None:
@@ -193,6 +195,11 @@ def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="unif
         pp = ctypes.pointer(ps)
     cfg = sgiga_config(d, p, continuity, w, min_level, DOMAIN[domain], GRADING[grading], float(gamma),
                        PREC[precision], PRECOND[precond], pp)
+    if components is not None:
+        comp = np.ascontiguousarray(np.asarray(components, dtype=np.int32).reshape(-1, d))
+        keep.append(comp)
+        cfg.ncomponents = len(comp)
+        cfg.components = comp.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     h = _P()
     s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.sgiga_plan(ctypes.byref(cfg), s, ctypes.byref(h)))

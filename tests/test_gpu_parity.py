@@ -432,3 +432,26 @@ def test_autotune_keeps_the_operator(sg):
         g = P.grids[0]
         comp = _component(case, g).assemble(f=problems.get("sine3").f)
         assert _rel(u[g.dof_off:g.dof_off + g.ndof], comp.solve()) < 1e-10
+
+
+def test_component_subset_plan(sg):
+    """A plan restricted to one component (the per-grid comparator) solves that
+    component exactly as the batched plan does."""
+    case = ("unit", 3, 3, 2, 7, "uniform", 1.0, 1)
+    with _plan(sg, case) as P:
+        sg.sgiga_set_rhs_builtin(P.handle, "sine")
+        sg.sgiga_solve(P.handle, 1e-12, 50)
+        u = np.zeros(P.info.ndof)
+        sg.sgiga_get_solution(P.handle, u)
+        g = P.grids[3]
+        lv = tuple(g.levels[:3])
+        with sg.Plan(3, 3, 7, components=[lv]) as Q:
+            assert Q.info.ngrids == 1 and Q.info.ndof == g.ndof and Q.grids[0].coeff == g.coeff
+            sg.sgiga_set_solver_options(Q.handle, use_graph=False)
+            sg.sgiga_set_rhs_builtin(Q.handle, "sine")
+            sg.sgiga_solve(Q.handle, 1e-12, 50)
+            v = np.zeros(Q.info.ndof)
+            sg.sgiga_get_solution(Q.handle, v)
+        assert _rel(v, u[g.dof_off:g.dof_off + g.ndof]) < 1e-12
+    with pytest.raises(sg.SgigaError):
+        sg.Plan(3, 3, 7, components=[(7, 7, 7)])
