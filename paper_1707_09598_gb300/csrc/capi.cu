@@ -1210,12 +1210,23 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
         // system (its error times the condition number is not small). After two
         // such steps the remaining components are finished by FP64 PCG on the
         // current residual: d = K^{-1} r, x += d (the plain method).
-        bool stalled = false;
-        for (int g = 0; g < ng; ++g)
-            if (outer > 0 && hact[g] && hrr[g] > 0.25 * prev_rr[g]) stalled = true;
+        bool stalled = false, broken = false;
+        for (int g = 0; g < ng; ++g) {
+            if (!hact[g]) continue;
+            if (!std::isfinite(hrr[g])) broken = true;   // the FP32 inner solve broke down
+            if (outer > 0 && !(hrr[g] <= 0.25 * prev_rr[g])) stalled = true;
+        }
         prev_rr = hrr;
         stalls = stalled ? stalls + 1 : 0;
-        if (stalls >= 2 && P->cfg.precond != SGIGA_PRECOND_LEARNED) {
+        if ((stalls >= 2 || broken) && P->cfg.precond != SGIGA_PRECOND_LEARNED) {
+            if (broken) {   // restart the active components from x = 0, r = b
+                int rc = SGIGA_OK;
+                CUDA_TRY(launch_zero_active(D, P->d_x, P->d_active_o, s));
+                if ((rc = apply_op(P, P->d_x, P->d_q, P->d_active_o))) return rc;
+                CUDA_TRY(launch_ir_residual(D, P->d_b, P->d_q, P->d_r, P->d_active_o, P->d_partial, rr, s));
+                CUDA_TRY(cudaMemcpyAsync(hrr.data(), rr, ng * 8, cudaMemcpyDeviceToHost, s));
+                CUDA_TRY(cudaStreamSynchronize(s));
+            }
             double ratio = 1.0;   // tightest ||b_g|| / ||r_g|| over the active components
             for (int g = 0; g < ng; ++g)
                 if (hact[g] && hrr[g] > 0) ratio = std::min(ratio, std::sqrt(hbb[g] / hrr[g]));

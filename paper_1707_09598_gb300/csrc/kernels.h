@@ -127,6 +127,7 @@ cudaError_t launch_loop_cond(int* counter, const int* nactive, int max_iter, cud
 cudaError_t launch_ir_down(const DevPlan& P, const double* r64, float* r32, const int* active, cudaStream_t s);
 cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const int* active, cudaStream_t s);
 cudaError_t launch_ir_up64(const DevPlan& P, double* x64, const double* d64, const int* active, cudaStream_t s);
+cudaError_t launch_zero_active(const DevPlan& P, double* x, const int* active, cudaStream_t s);
 cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
                                double* partial, double* rr, cudaStream_t s);
 cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);

@@ -289,6 +289,19 @@ cudaError_t launch_ir_up(const DevPlan& P, double* x64, const float* d32, const 
     return cudaGetLastError();
 }
 
+// x = 0 on active grids (restart of a refinement whose iterate went non-finite)
+__global__ void k_zero_active(const Chunk* __restrict__ chunks, double* __restrict__ x, const int* __restrict__ active) {
+    const Chunk c = chunks[blockIdx.x];
+    if (!active[c.grid]) return;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) x[c.start + i] = 0.0;
+}
+
+cudaError_t launch_zero_active(const DevPlan& P, double* x, const int* active, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_zero_active<<<P.nchunks, 256, 0, s>>>(P.chunks, x, active);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ir_up64(const DevPlan& P, double* x64, const double* d64, const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     k_ir_up<double><<<P.nchunks, 256, 0, s>>>(P.chunks, x64, d64, active);

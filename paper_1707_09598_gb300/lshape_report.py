@@ -65,6 +65,8 @@ def main():
     ap.add_argument("--wmax", type=int, default=11)
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--tol-gamma3", type=float, default=1e-9,
+                    help="gamma = 3 at w = 11: the FP64 true residual floors near 3e-10 (cond ~1e12)")
     a = ap.parse_args()
     xi, patch, wt = error_rule()
     x = xi * SIGNS[patch]
@@ -74,7 +76,7 @@ def main():
     patch_d = torch.as_tensor(patch, device="cuda")
     stream = torch.cuda.Stream()
     out = {"workload": "L-shape, 3 glued bilinear patches, u = r^(2/3) sin(2 theta/3) Dirichlet data, f = 0, p = 2 C^1, "
-                       "one-sided grading toward the corner, %s PCG to %g" % (a.precision, a.tol),
+                       "one-sided grading toward the corner, %s PCG to %g (gamma = 3: %g)" % (a.precision, a.tol, a.tol_gamma3),
            "error_rule": "4x4 Gauss points on a uniform 64x64 mesh per patch", "results": {}}
     for gamma in (1.0, 2.0, 3.0):
         rows = []
@@ -83,13 +85,17 @@ def main():
                            stream=stream)
             sgiga.sgiga_autotune(P.handle, reps=2)
             sgiga.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
-            sgiga.sgiga_solve(P.handle, a.tol, 3000)      # warm-up (graph capture)
+            tol = a.tol_gamma3 if gamma == 3.0 else a.tol
+            sgiga.sgiga_solve(P.handle, tol, 3000, check=False)      # warm-up (graph capture)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            st, _ = sgiga.sgiga_solve(P.handle, a.tol, 3000)
+            st, rc = sgiga.sgiga_solve(P.handle, tol, 3000, check=False)
             e1.record(stream)
             torch.cuda.synchronize()
+            print("gamma=%g w=%d rc=%d outer=%d inner=%d fallback=%d maxres=%.2e" %
+                  (gamma, w, rc, st.iterations, st.inner_iterations, st.fallback, st.max_rel_residual),
+                  file=sys.stderr, flush=True)
             ng = P.info.ngrids
             uc = torch.zeros(ng * npts, dtype=torch.float64, device="cuda")
             gc = torch.zeros(2 * ng * npts, dtype=torch.float64, device="cuda")
@@ -104,9 +110,10 @@ def main():
             dg = np.stack([g0.cpu().numpy(), g1.cpu().numpy()], 1) - ge
             l2 = float(np.sqrt(np.sum(wt * du * du)))
             h1 = float(np.sqrt(np.sum(wt * np.sum(dg * dg, 1))))
-            rows.append({"w": w, "ngrids": ng, "ndof": P.info.ndof, "l2": l2, "h1": h1,
+            rows.append({"w": w, "tol": tol, "ngrids": ng, "ndof": P.info.ndof, "l2": l2, "h1": h1,
                          "solve_ms": e0.elapsed_time(e1), "outer": st.iterations, "inner": st.inner_iterations,
-                         "max_rel_residual": st.max_rel_residual, "fp64_fallback": bool(st.fallback & 2)})
+                         "max_rel_residual": st.max_rel_residual, "fp64_fallback": bool(st.fallback & 2),
+                         "rc": rc})
             P.close()
         ws = [r["w"] for r in rows]
         out["results"]["gamma=%g" % gamma] = {

@@ -208,13 +208,17 @@ def test_errors_are_reported(sg):
 @pytest.mark.parametrize("gamma", [1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
-    """gamma = 3 grades the corner elements down to 1e-9 of the patch: the
-    most anisotropic components have cond(K) ~ 1e12 (4e9 after diagonal
-    equilibration), and in FP64 their solutions are defined to ~1e-8 only
-    (the oracle's refined direct solve stalls there). The bound for gamma = 3
-    is 1e-7 on both paths; gamma = 1, 2 keep the FP64 and mixed targets."""
+    """gamma = 3 grades the corner elements down to 1e-9 of the patch. The
+    most anisotropic components then have cond(K) ~ 1e12 (4e9 after diagonal
+    equilibration). In FP64 their true relative residual cannot go below
+    ~3e-10: the oracle's LU with refinement stalls at 2.6e-10, the GPU's FP64
+    residual at 5.5e-10. Two FP64 solutions of these systems agree to ~1.5e-7
+    (this test measured 1.52e-7 with the GPU solve at 1e-12 and at 1e-14).
+    For gamma = 3 the solve target is 1e-9 and the parity bound 5e-7 on both
+    paths; gamma = 1, 2 keep the FP64 and mixed targets."""
+    solve_tol = 1e-12
     if gamma == 3:
-        tol = 1e-7
+        tol, solve_tol = 5e-7, 1e-9
     path = os.path.join(GOLD, "lshape_p2_w11_g%d.txt" % gamma)
     data = np.loadtxt(path)
     patch = np.ascontiguousarray(data[:, 0].astype(np.int32))
@@ -222,7 +226,7 @@ def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
     with _plan(sg, 11, float(gamma), precision=precision) as P:
         sg.sgiga_autotune(P.handle, reps=2)
         sg.sgiga_set_rhs_builtin(P.handle, "lshape_corner")
-        st, _ = sg.sgiga_solve(P.handle, 1e-12, 3000)
+        st, _ = sg.sgiga_solve(P.handle, solve_tol, 3000)
         assert st.converged == P.info.ngrids
         ng, npts = P.info.ngrids, len(xi)
         uc = torch.zeros(ng * npts, dtype=torch.float64, device="cuda")
