@@ -16,7 +16,7 @@
 namespace sgiga {
 
 template <typename Real, int P, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 2)
 k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
     extern __shared__ double sm_raw[];
@@ -56,6 +56,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     };
     const int Ta = T[0], Tb = T[1], La = L[0], Lb = L[1];
     const int QTb = Q * Tb, npen = QTb, LaP = La | 1;
+    const FastDiv dLa(La);
     Real* tb[2];
     Real* tdv[2];
     Real* cur = sm;
@@ -78,7 +79,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     if (MODE != 1) {
         const int nX = La * Lb;
         for (int idx = tid; idx < nX; idx += nth) {
-            int ja = idx % La, jb = idx / La;
+            const int jb = dLa.div(idx), ja = idx - jb * La;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
             Real v = 0.0;
             if (MODE == 2) {   // every function: boundary coefficients (zero on kept functions)
@@ -94,7 +95,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         __syncthreads();
         const int n1 = npen * La;
         for (int idx = tid; idx < n1; idx += nth) {
-            int ja = idx % La, qb = idx / La;
+            const int qb = dLa.div(idx), ja = idx - qb * La;
             int eb = qb / Q;
             const Real* bt = tb[1] + qb * P1;
             const Real* dt = tdv[1] + qb * P1;
@@ -175,7 +176,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     __syncthreads();
     const int nX = La * Lb;
     for (int idx = tid; idx < nX; idx += nth) {
-        int ja = idx % La, jb = idx / La;
+        const int jb = dLa.div(idx), ja = idx - jb * La;
         int fa = E0[0] * M + ja, fb = E0[1] * M + jb;
         if (!kept(fa, fb)) continue;
         int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);

@@ -17,7 +17,7 @@
 namespace sgiga {
 
 template <typename Real, int P, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 2)
 k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
     extern __shared__ double sm_raw[];
@@ -41,6 +41,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     }
     const int Ta = T[0], Tb = T[1], Tc = T[2], La = L[0], Lb = L[1], Lc = L[2];
     const int QTb = Q * Tb, QTc = Q * Tc, npen = QTb * QTc, LaP = La | 1;
+    const FastDiv dLa(La), dLb(Lb), dQTb(QTb);
     Real* tb[3];
     Real* tdv[3];
     Real* cur = sm;
@@ -67,7 +68,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     if (MODE == 0) {
         const int nX = La * Lb * Lc;
         for (int idx = tid; idx < nX; idx += nth) {
-            int ja = idx % La, r = idx / La, jb = r % Lb, jc = r / Lb;
+            const int r = dLa.div(idx), ja = idx - r * La, jc = dLb.div(r), jb = r - jc * Lb;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
             Real v = 0.0;
             if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)
@@ -77,7 +78,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         __syncthreads();
         // stage 1: contract c (DoF -> qp)
         for (int idx = tid; idx < S1n; idx += nth) {
-            int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
+            const int r = dLa.div(idx), ja = idx - r * La, qc = dLb.div(r), jb = r - qc * Lb;
             int ec = qc / Q;
             const Real* bt = tb[2] + qc * P1;
             const Real* dt = tdv[2] + qc * P1;
@@ -96,7 +97,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         // stage 2: contract b
         const int n2 = npen * La;
         for (int idx = tid; idx < n2; idx += nth) {
-            int ja = idx % La, r = idx / La, qb = r % QTb, qc = r / QTb;
+            const int r = dLa.div(idx), ja = idx - r * La, qc = dQTb.div(r), qb = r - qc * QTb;
             int eb = qb / Q;
             const Real* bt = tb[1] + qb * P1;
             const Real* dt = tdv[1] + qb * P1;
@@ -186,7 +187,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     __syncthreads();
     // backward b: S2 -> S1
     for (int idx = tid; idx < S1n; idx += nth) {
-        int ja = idx % La, r = idx / La, jb = r % Lb, qc = r / Lb;
+        const int r = dLa.div(idx), ja = idx - r * La, qc = dLb.div(r), jb = r - qc * Lb;
         int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
         Real rB = 0.0, rD = 0.0;
         for (int eb = lo; eb <= hi; ++eb) {
@@ -211,7 +212,7 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     // backward c and scatter
     const int nX = La * Lb * Lc;
     for (int idx = tid; idx < nX; idx += nth) {
-        int ja = idx % La, r = idx / La, jb = r % Lb, jc = r / Lb;
+        const int r = dLa.div(idx), ja = idx - r * La, jc = dLb.div(r), jb = r - jc * Lb;
         int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
         if (!(fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)) continue;
         int lo = elem_lo(jc, P, M), hi = elem_hi(jc, M, Tc);

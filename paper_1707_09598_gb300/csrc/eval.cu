@@ -86,25 +86,46 @@ cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi
     return cudaGetLastError();
 }
 
+// u[j] = sum_g coef[g] ucomp[g][j] with Neumaier compensation. A block
+// handles 32 points x 8 groups of components: each thread compensates the sum
+// of its group (components k, k+8, ...), then one thread per point combines the
+// 8 (sum, compensation) pairs, again compensated. Coalesced: a warp reads 32
+// consecutive points of one component.
 __global__ void k_combine(int ng, const double* __restrict__ ucomp, long long npts, const double* __restrict__ coef,
                           double* __restrict__ u) {
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= npts) return;
+    __shared__ double ps[8][33], pc[8][33];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const long long j = (long long)blockIdx.x * 32 + lane;
     double sum = 0.0, comp = 0.0;
-    for (int g = 0; g < ng; ++g) {
-        double t = coef[g] * ucomp[(long long)g * npts + j];
-        double v = sum + t;
-        comp += fabs(sum) >= fabs(t) ? (sum - v) + t : (t - v) + sum;
-        sum = v;
+    if (j < npts) {
+        for (int g = grp; g < ng; g += 8) {
+            const double t = coef[g] * ucomp[(long long)g * npts + j];
+            const double v = sum + t;
+            comp += fabs(sum) >= fabs(t) ? (sum - v) + t : (t - v) + sum;
+            sum = v;
+        }
     }
-    u[j] = sum + comp;
+    ps[grp][lane] = sum;
+    pc[grp][lane] = comp;
+    __syncthreads();
+    if (grp == 0 && j < npts) {
+        double s = 0.0, c = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            const double t = ps[k][lane];
+            const double v = s + t;
+            c += fabs(s) >= fabs(t) ? (s - v) + t : (t - v) + s;
+            s = v;
+            c += pc[k][lane];
+        }
+        u[j] = s + c;
+    }
 }
 
 cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts, const double* coef, double* u,
                            cudaStream_t s) {
     if (npts <= 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_combine<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(P.ncomps, ucomp, npts, coef, u);
+    k_combine<<<(unsigned)((npts + 31) / 32), 256, 0, s>>>(P.ncomps, ucomp, npts, coef, u);
     return cudaGetLastError();
 }
 

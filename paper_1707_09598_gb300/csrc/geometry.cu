@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "kernels.h"
+#include "op_common.cuh"
 #include "spline_dev.cuh"
 
 namespace sgiga {
@@ -264,9 +265,38 @@ cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_
     return cudaGetLastError();
 }
 
+// rho = f * mw from a user f in natural order. One block per tile walks the
+// tile's box of quadrature points in natural order (direction 0 fastest), so
+// the reads of f are rows of Q*T_0 contiguous values, and writes rho at the
+// tile-major position, inside the tile's own contiguous range (the L2 merges
+// those writes before they reach DRAM).
+__global__ void k_rhs_density_nat(DevPlan P, const double* __restrict__ fnat) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc& g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    const int B0 = Q * g.T[0], B1 = d > 1 ? Q * g.T[1] : 1, B2 = d > 2 ? Q * g.T[2] : 1;
+    const int pa = g.perm[0], pb = g.perm[1], pc = g.perm[2];
+    const int QTb = Q * g.T[pb];
+    const int npen = d == 3 ? QTb * Q * g.T[pc] : QTb;
+    const long long n0 = (long long)Q * g.E[0], n1 = d > 1 ? (long long)Q * g.E[1] : 1;
+    const long long base = g.qp_off + Q * t.e0[0] + n0 * ((long long)Q * t.e0[1] + n1 * (long long)Q * t.e0[2]);
+    const FastDiv dB0(B0), dB1(B1);
+    const int nq = B0 * B1 * B2;
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        int l[3];
+        const int r = dB0.div(j);
+        l[0] = j - r * B0;
+        l[2] = dB1.div(r);
+        l[1] = r - l[2] * B1;
+        const int idx = l[pa] * npen + l[pb] + (d == 3 ? QTb * l[pc] : 0);
+        const long long o = t.g_off + idx;
+        P.rho[o] = fnat[base + l[0] + n0 * (l[1] + n1 * l[2])] * P.mw[o];
+    }
+}
+
 cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_rhs_density<<<P.ntiles, 256, 0, s>>>(P, 0, f_nat);
+    k_rhs_density_nat<<<P.ntiles, 256, 0, s>>>(P, f_nat);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,23 @@ template <> struct OpData<float> {
     static __device__ __forceinline__ const float* dR(const DevPlan& P) { return P.dRf; }
 };
 
+// Exact n / d for 0 <= n < 2^21 with 1 <= d <= 256, and for 0 <= n < 2^17
+// with 1 <= d <= 4096: a float reciprocal estimate is off by at most one there
+// and one correction step fixes it (checked exhaustively over both ranges). Replaces runtime integer division
+// in the staging loops, where it cost more instructions than the FMAs.
+struct FastDiv {
+    int d;
+    float inv;
+    __device__ explicit FastDiv(int dd) : d(dd), inv(1.0f / (float)dd) {}
+    __device__ __forceinline__ int div(int n) const {
+        int q = __float2int_rz((float)n * inv);
+        const int r = n - q * d;
+        if (r >= d) ++q;
+        else if (r < 0) --q;
+        return q;
+    }
+};
+
 __device__ __forceinline__ int elem_lo(int j, int P, int M) { return j >= P ? (j - P + M - 1) / M : 0; }
 __device__ __forceinline__ int elem_hi(int j, int M, int T) { int e = j / M; return e < T - 1 ? e : T - 1; }
 
