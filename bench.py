@@ -341,8 +341,11 @@ def run_ours(args):
     tuning = {"seconds": tune_s, "best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
                                           "apply_ms": tune.best_ms, "ntiles": tune.ntiles},
               "candidates_ms": [round(tune.ms[i], 4) for i in range(tune.ncand)],
-              "precond_split": {"best_ks": tune.fd_ks[tune.fd_best], "items": tune.fd_nitems,
-                                "candidates_ms": {str(tune.fd_ks[i]): round(tune.fd_ms[i], 4)
+              "precond_split": {"best_ks": tune.fd_ks[tune.fd_best],
+                                "best_layout": "grouped" if tune.fd_grouped[tune.fd_best] else "per piece",
+                                "items": tune.fd_nitems,
+                                "candidates_ms": {("grouped " if tune.fd_grouped[i] else "per piece ") +
+                                                  str(tune.fd_ks[i]): round(tune.fd_ms[i], 4)
                                                   for i in range(tune.fd_ncand)}}}
     ndof, ng = P.info.ndof, P.info.ngrids
     pts_h = eval_points(W["d"], W["lattice"])

@@ -268,13 +268,14 @@ int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
  * (1) Re-plans the tiles of every component under each candidate policy
  * (shared-memory budget per block, cap on quadrature points per tile; the
  * shape within a policy comes from the planner's cost model), times `reps`
- * stiffness applies on the plan's stream for each (CUDA events), and keeps
+ * stiffness applies (FP32 in MIXED_FP32 plans, whose inner solve they
+ * dominate; else FP64) on the plan's stream for each (CUDA events), and keeps
  * the fastest; the geometry planes are recomputed in the chosen tile layout.
  * (2) Re-splits the fast-diagonalisation mode products into work items of
- * each candidate contraction depth (fd_ks: entries of a long 1D contraction
- * per item; shorter items balance the SMs better, longer ones need fewer
- * atomic partial sums), times `reps` preconditioner applications for each and
- * keeps the fastest. Overwrites the plan's work vectors (not its load vector
+ * each candidate layout (per piece, level-grouped) and contraction depth
+ * (fd_ks: entries of a long 1D contraction per item; shorter items balance
+ * the SMs better, longer ones need fewer atomic partial sums), times `reps`
+ * preconditioner applications for each and keeps the fastest. Overwrites the plan's work vectors (not its load vector
  * or solution). out (host, may be NULL) receives the per-candidate mean
  * times. */
 typedef struct {
@@ -286,6 +287,7 @@ typedef struct {
     int fd_ncand, fd_best, fd_nitems;
     int fd_ks[8];     /* contraction depth per preconditioner work item */
     double fd_ms[8];  /* mean time of one preconditioner application */
+    int fd_grouped[8];/* 1: level-grouped layout, 0: per-piece layout */
 } sgiga_tune_result;
 int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
 
@@ -297,12 +299,15 @@ int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
  * inner solve of SGIGA_PREC_MIXED_FP32 (defaults 1e-5, 100). */
 int sgiga_set_solver_options(sgiga_plan_t plan, int use_graph, double inner_tol, int inner_max);
 
-/* Contraction depth of the preconditioner's work items: a 1D contraction
+/* Work layout of the preconditioner's mode products. ks: a 1D contraction
  * longer than ks entries is split into ks-deep items whose partial sums are
- * added atomically (the autotuner picks ks by measurement; default 128).
- * ks must be a multiple of 16 in [16, 4096], else SGIGA_ERR_ARG. The result
+ * added atomically. grouped = 0: items of one component piece each (ROWS /
+ * TILE shapes; the FP64 default); 1: the long directions of all pieces that
+ * share an eigenvector matrix form one GEMM over all their fibres (the FP32
+ * default). The autotuner picks both by measurement; default ks = 32. ks
+ * must be a multiple of 16 in [16, 4096], else SGIGA_ERR_ARG. The result
  * changes only by summation order. */
-int sgiga_set_precond_split(sgiga_plan_t plan, int ks);
+int sgiga_set_precond_split(sgiga_plan_t plan, int ks, int grouped);
 
 /* Packed solution coefficients (device [ndof]). */
 int sgiga_get_solution(sgiga_plan_t plan, double* u);

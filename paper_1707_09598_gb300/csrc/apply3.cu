@@ -80,8 +80,9 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         for (int idx = tid; idx < S1n; idx += nth) {
             const int r = dLa.div(idx), ja = idx - r * La, qc = dLb.div(r), jb = r - qc * Lb;
             int ec = qc / Q;
-            const Real* bt = tb[2] + qc * P1;
-            const Real* dt = tdv[2] + qc * P1;
+            Real bt[P1], dt[P1];
+            load_row<Real, P1>(tb[2] + qc * P1, bt);
+            load_row<Real, P1>(tdv[2] + qc * P1, dt);
             const Real* xp = X + ((ec * M) * Lb + jb) * La + ja;
             Real sB = 0.0, sD = 0.0;
 #pragma unroll
@@ -99,8 +100,9 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         for (int idx = tid; idx < n2; idx += nth) {
             const int r = dLa.div(idx), ja = idx - r * La, qc = dQTb.div(r), qb = r - qc * QTb;
             int eb = qb / Q;
-            const Real* bt = tb[1] + qb * P1;
-            const Real* dt = tdv[1] + qb * P1;
+            Real bt[P1], dt[P1];
+            load_row<Real, P1>(tb[1] + qb * P1, bt);
+            load_row<Real, P1>(tdv[1] + qb * P1, dt);
             const Real* s1b = S1 + (qc * Lb + eb * M) * La + ja;
             const Real* s1d = s1b + S1n;
             Real s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -140,8 +142,9 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int qa = ea * Q + q;
-                const Real* bt = tb[0] + qa * P1;
-                const Real* dt = tdv[0] + qa * P1;
+                Real bt[P1], dt[P1];
+                load_row<Real, P1>(tb[0] + qa * P1, bt);
+                load_row<Real, P1>(tdv[0] + qa * P1, dt);
                 if (MODE == 0) {
                     Real ga = 0.0, gb = 0.0, gc = 0.0;
 #pragma unroll

@@ -248,29 +248,47 @@ static void free_plan(sgiga_plan_s* P) {
 }
 
 // After the geometry planes change: is the metric diagonal everywhere?
-// Preconditioner work items per direction. The shape of each component's
-// mode product picks SMALL / ROWS / TILE; contractions longer than ks are
-// split into ks-deep items whose partial sums add atomically. Items are
-// ordered by estimated FMAs, largest first (greedy longest-processing-time
-// order), so that the short ones fill the tail of the launch.
-static void make_fd_items(sgiga_plan_s* P, int ks) {
+// Preconditioner work items per direction. Short directions (n <= 64): SMALL
+// items of one piece. Longer ones: the pieces whose direction k uses the same
+// eigen table form one segment (a GEMM over all their fibres), cut into 64 x 64
+// output tiles and ks-deep contraction ranges whose partial sums add
+// atomically. Items are ordered by estimated FMAs, largest first (greedy
+// longest-processing-time order), so that the short ones fill the tail.
+static void make_fd_items(sgiga_plan_s* P, int ks, bool grouped) {
     const int d = P->d;
     P->fd_ks = ks;
+    P->fd_grouped = grouped;
+    P->fdsegs.clear();
+    P->fdcb.clear();
+    P->fdcs.clear();
+    P->fdcc.clear();
+    auto lpt = [](std::vector<FDItem>& v, const std::vector<long long>& cost) {
+        std::vector<size_t> ord(v.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+        std::vector<FDItem> sorted(v.size());
+        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = v[ord[i]];
+        v.swap(sorted);
+    };
     for (int k = 0; k < d; ++k) {
         std::vector<FDItem>& v = P->fd[k];
         v.clear();
-        std::vector<long long> cost;
+        for (int t = 0; t < 3; ++t) P->fdl[k][t].clear();
+        std::vector<long long> cost, lcost[3];
+        std::map<int, std::vector<int>> by_eig;
         for (size_t gi = 0; gi < P->grids.size(); ++gi) {
             const GridDesc& g = P->grids[gi];
-            long long n = g.fn[k];
+            const long long n = g.fn[k];
             if (g.fd_n == 0) continue;
-            long long ncol = g.fd_n / n;
+            const long long ncol = g.fd_n / n;
             auto depth = [&](int j0) { return (int)std::min<long long>(n, j0 + ks); };
             if (n <= 64) {
                 for (long long c0 = 0; c0 < g.fd_n; c0 += 256) {
                     v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
                     cost.push_back(std::min<long long>(256, g.fd_n - c0) * n);
                 }
+            } else if (grouped) {
+                by_eig[g.eig[k]].push_back((int)gi);
             } else if (ncol >= 64) {
                 for (long long i0 = 0; i0 < n; i0 += 32)
                     for (long long c0 = 0; c0 < ncol; c0 += 64)
@@ -280,37 +298,97 @@ static void make_fd_items(sgiga_plan_s* P, int ks) {
                                            (depth(j0) - j0));
                         }
             } else {
-                long long ng = (ncol + 7) / 8, per = (ncol + ng - 1) / ng;
+                const long long ngr = (ncol + 7) / 8, per = (ncol + ngr - 1) / ngr;
                 for (long long i0 = 0; i0 < n; i0 += 256)
                     for (long long c0 = 0; c0 < ncol; c0 += per)
                         for (int j0 = 0; j0 < n; j0 += ks) {
-                            int nc = (int)std::min(per, ncol - c0);
+                            const int nc = (int)std::min(per, ncol - c0);
                             v.push_back(FDItem{(int)gi, FD_ROWS, nc, (int)i0, c0, j0, depth(j0)});
                             cost.push_back(std::min<long long>(256, n - i0) * nc * (depth(j0) - j0));
                         }
             }
         }
-        std::vector<size_t> ord(v.size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
-        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-        std::vector<FDItem> sorted(v.size());
-        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = v[ord[i]];
-        v.swap(sorted);
+        for (auto& kv : by_eig) {
+            FDSeg sg{};
+            sg.eig = kv.first;
+            sg.n = P->grids[kv.second[0]].fn[k];
+            sg.unit = k == 0 ? 1 : 0;
+            sg.col0 = (long long)P->fdcb.size();
+            for (int gi : kv.second) {
+                const GridDesc& g = P->grids[gi];
+                long long B = 1;
+                for (int j = 0; j < k; ++j) B *= g.fn[j];
+                const long long n = g.fn[k], ncol = g.fd_n / n;
+                for (long long c = 0; c < ncol; ++c) {
+                    const long long a = c / B, b = c - a * B;
+                    P->fdcb.push_back(g.fd_off + a * n * B + b);
+                    P->fdcs.push_back((int)B);
+                    P->fdcc.push_back(g.comp);
+                }
+            }
+            sg.ncols = (int)((long long)P->fdcb.size() - sg.col0);
+            // output tile class: the fewest padded columns, ties to the wider tile
+            int cls = 2;
+            long long best = -1;
+            for (int t = 2; t >= 0; --t) {
+                const long long tn = 16LL << t, padded = (sg.ncols + tn - 1) / tn * tn;
+                if (best < 0 || padded < best) { best = padded; cls = t; }
+            }
+            sg.tn = 16 << cls;
+            const int tm = 4096 / sg.tn;
+            const int seg = (int)P->fdsegs.size();
+            P->fdsegs.push_back(sg);
+            for (int i0 = 0; i0 < sg.n; i0 += tm)
+                for (int c0 = 0; c0 < sg.ncols; c0 += sg.tn)
+                    for (int j0 = 0; j0 < sg.n; j0 += ks) {
+                        const int j1 = std::min(sg.n, j0 + ks);
+                        P->fdl[k][cls].push_back(FDItem{seg, FD_LEVEL, 0, i0, c0, j0, j1});
+                        lcost[cls].push_back((long long)std::min(tm, sg.n - i0) * std::min(sg.tn, sg.ncols - c0) *
+                                             (j1 - j0));
+                    }
+        }
+        lpt(v, cost);
+        for (int t = 0; t < 3; ++t) lpt(P->fdl[k][t], lcost[t]);
     }
 }
 
-// Re-split the preconditioner work items at depth ks and upload them.
-static int refd(sgiga_plan_s* P, int ks) {
-    CUDA_TRY(cudaStreamSynchronize(P->stream));
-    make_fd_items(P, ks);
-    for (int k = 0; k < P->d; ++k) {
-        auto it = std::find(P->allocs.begin(), P->allocs.end(), (void*)P->d_fd[k]);
+// Upload the preconditioner work lists (host vectors -> plan device arrays).
+static int upload_fd(sgiga_plan_s* P) {
+    auto drop = [&](void* old) {
+        if (!old) return;
+        auto it = std::find(P->allocs.begin(), P->allocs.end(), old);
         if (it != P->allocs.end()) P->allocs.erase(it);
-        cudaFree(P->d_fd[k]);
+        cudaFree(old);
+    };
+    int rc;
+    for (int k = 0; k < P->d; ++k) {
+        drop(P->d_fd[k]);
         P->d_fd[k] = nullptr;
-        int rc = upload(P, &P->d_fd[k], P->fd[k]);
-        if (rc) return rc;
+        if ((rc = upload(P, &P->d_fd[k], P->fd[k]))) return rc;
+        for (int t = 0; t < 3; ++t) {
+            drop(P->d_fdl[k][t]);
+            P->d_fdl[k][t] = nullptr;
+            if ((rc = upload(P, &P->d_fdl[k][t], P->fdl[k][t]))) return rc;
+        }
     }
+    drop(P->d_fdsegs); drop(P->d_fdcb); drop(P->d_fdcs); drop(P->d_fdcc);
+    if ((rc = upload(P, &P->d_fdsegs, P->fdsegs)) || (rc = upload(P, &P->d_fdcb, P->fdcb)) ||
+        (rc = upload(P, &P->d_fdcs, P->fdcs)) || (rc = upload(P, &P->d_fdcc, P->fdcc)))
+        return rc;
+    DevPlan& D = P->dp;
+    D.fdsegs = P->d_fdsegs;
+    D.fdcb = P->d_fdcb;
+    D.fdcs = P->d_fdcs;
+    D.fdcc = P->d_fdcc;
+    return SGIGA_OK;
+}
+
+// Re-split the preconditioner work items (depth ks, layout) and upload them.
+static int refd(sgiga_plan_s* P, int ks, bool grouped) {
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    make_fd_items(P, ks, grouped);
+    int rc = upload_fd(P);
+    if (rc) return rc;
     destroy_loop_graph(P->loop64);   // the captured loops hold the old item arrays
     destroy_loop_graph(P->loop32);
     return SGIGA_OK;
@@ -562,7 +640,6 @@ static int build(sgiga_plan_s* P) {
         }
     }
     make_tiles(P, 110 * 1024, 16384);
-    make_fd_items(P, 128);
     // device data
     if (c.domain == SGIGA_DOMAIN_PATCH) {
         if (!c.patch || make_user_patch(c.patch, d, P->patch) != 0)
@@ -616,8 +693,7 @@ static int build(sgiga_plan_s* P) {
         CUDA_TRY(cudaMemset(D.gfull, 0, (size_t)P->ngf * 8));
         CUDA_TRY(cudaMemset(D.gdata, 0, (size_t)P->ngdata * 8));
     }
-    for (int k = 0; k < d; ++k)
-        if ((rc = upload(P, &P->d_fd[k], P->fd[k]))) return rc;
+
     D.tiles = dt; D.sched = ds; D.tabs = dtab; D.chunks = dch; D.patch = dpatch;
     P->d_tiles = dt;
     P->d_sched = ds;
@@ -688,6 +764,10 @@ static int build(sgiga_plan_s* P) {
             g.eig[k] = eig_for(g.tab[k], g.klo[k]);
             if (g.eig[k] < 0) return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed");
         }
+    // preconditioner work items (grouped by eigen table)
+    // default layout: grouped for FP32 (latency-bound) plans, per piece for FP64
+    make_fd_items(P, 32, c.precision == SGIGA_PREC_MIXED_FP32);
+    if ((rc = upload_fd(P))) return rc;
     // reciprocal eigenvalue sums of every entry of the preconditioner's local layout
     std::vector<double> hdinv((size_t)P->nfd);
     for (const GridDesc& g : P->grids)
@@ -1093,11 +1173,17 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     double best = 1e30;
     int bi = 3;
     int rc = SGIGA_OK;
+    // the operator the plan's CG runs: FP32 in mixed plans (inner solve), else FP64
+    const bool f32 = P->cfg.precision == SGIGA_PREC_MIXED_FP32;
+    if (f32) CUDA_TRY(cudaMemsetAsync(P->f_p, 0, (size_t)P->ndof * 4, s));
+    auto apply_once = [&]() {
+        return f32 ? apply_op(P, P->f_p, P->f_q, nullptr) : apply_op(P, P->d_b, P->d_q, nullptr);
+    };
     for (int i = 0; i < nc && rc == SGIGA_OK; ++i) {
         if ((rc = retile(P, cands[i].budget, cands[i].qpcap))) break;
-        if ((rc = apply_op(P, P->d_b, P->d_q, nullptr))) break;   // warm-up
+        if ((rc = apply_once())) break;   // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_op(P, P->d_b, P->d_q, nullptr);
+        for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_once();
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
         float ms = 0.0f;
@@ -1108,12 +1194,15 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     }
     if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap);
     // preconditioner item depth
-    const int ks_c[] = {16, 32, 64, 128, 256};
-    const int nks = (int)(sizeof(ks_c) / sizeof(ks_c[0]));
+    const int ks_v[] = {16, 32, 64, 128};
+    const int nksv = (int)(sizeof(ks_v) / sizeof(ks_v[0]));
+    const int nks = 2 * nksv;   // per-piece layout, then grouped layout
     double fbest = 1e30;
-    int fbi = 3;
+    int fbi = 1;
     for (int i = 0; i < nks && rc == SGIGA_OK; ++i) {
-        if ((rc = refd(P, ks_c[i]))) break;
+        const int ksi = ks_v[i % nksv];
+        const bool grp = i >= nksv;
+        if ((rc = refd(P, ksi, grp))) break;
         // the precision the plan's CG runs in; plain FD (no learned correction)
         auto fd_once = [&]() {
             if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
@@ -1128,13 +1217,13 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         double per = ms / reps;
-        if (out) { out->fd_ms[i] = per; out->fd_ks[i] = ks_c[i]; }
+        if (out) { out->fd_ms[i] = per; out->fd_ks[i] = ksi; out->fd_grouped[i] = grp ? 1 : 0; }
         if (per < fbest) { fbest = per; fbi = i; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if ((rc = refd(P, ks_c[fbi]))) return rc;
+    if ((rc = refd(P, ks_v[fbi % nksv], fbi >= nksv))) return rc;
     if (out) {
         out->ncand = nc;
         out->best = bi;
@@ -1143,16 +1232,19 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         out->fd_ncand = nks;
         out->fd_best = fbi;
         size_t items = 0;
-        for (int k = 0; k < P->d; ++k) items += P->fd[k].size();
+        for (int k = 0; k < P->d; ++k) {
+            items += P->fd[k].size();
+            for (int t = 0; t < 3; ++t) items += P->fdl[k][t].size();
+        }
         out->fd_nitems = (int)items;
     }
     return SGIGA_OK;
 }
 
-int sgiga_set_precond_split(sgiga_plan_t P, int ks) {
+int sgiga_set_precond_split(sgiga_plan_t P, int ks, int grouped) {
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
     if (ks < 16 || ks > 4096 || ks % 16) return fail(SGIGA_ERR_ARG, "ks must be a multiple of 16 in [16, 4096]");
-    return refd(P, ks);
+    return refd(P, ks, grouped != 0);
 }
 
 int sgiga_set_solver_options(sgiga_plan_t P, int use_graph, double inner_tol, int inner_max) {

@@ -7,19 +7,22 @@
 //
 // One pass applies Mat = U_k^T (forward) or U_k (backward) along direction k of
 // every component: out[a][i][b] = sum_j Mat[i][j] in[a][j][b], a GEMM with
-// M = K = n_k and ncol = ndof / n_k columns. Work items pick one of three
-// shapes so that FP64 work is not wasted on padding:
-//   SMALL (n_k <= 64): one thread per output, Mat staged in shared memory;
-//   ROWS  (long direction, < 64 columns): one lane per row, a group of at most
-//         8 columns in registers; Mat is read through its transpose so that a
-//         warp's loads are coalesced, the input entries are warp broadcasts;
-//   TILE  (otherwise): 32 x 64 output tile, 16-deep K loop through shared
-//         memory, 2 x 4 outputs per thread.
-// Long contractions (n_k > 128) are split into 128-deep ranges of j so that no
-// block carries more than ~10^5 FMAs; such items add their partial sums
-// atomically into an output that was cleared before the pass. The division by
-// the eigenvalue sums is a separate elementwise pass between the forward and
-// the backward passes, with the reciprocals precomputed per DoF.
+// M = K = n_k and ncol = ndof / n_k columns. Two work layouts; the autotuner
+// measures both and keeps the faster for the plan's precision:
+//   per piece: SMALL (n_k <= 64), ROWS (long direction, < 64 columns) and
+//         TILE (otherwise) items of one piece each, shaped so that FP64 work
+//         is not wasted on padding (FP64 is bound by its FMA pipe);
+//   grouped: SMALL items, and for longer directions all pieces whose
+//         direction k uses the same eigenvector matrix form one GEMM over all
+//         their fibres (a "segment"), cut into output tiles of 64x64, 128x32
+//         or 256x16 (by column count) with 4 x 4 outputs per thread. Each
+//         element of U read from memory then serves many pieces' columns,
+//         which is what the latency-bound FP32 instances need.
+// Contractions longer than the autotuned depth are split into items whose
+// partial sums add atomically into an output cleared before the pass.
+// The division by the eigenvalue sums is a separate elementwise pass between
+// the forward and the backward passes, with the reciprocals precomputed per
+// entry.
 #include "kernels.h"
 
 namespace sgiga {
@@ -63,6 +66,10 @@ template <> struct FDData<float> {
     static __device__ __forceinline__ const float* dinv(const DevPlan& P) { return P.dinvf; }
 };
 
+// Per-piece items: SMALL (one output per thread, Mat in shared memory), ROWS
+// (one lane per row, a group of at most 8 columns in registers; Mat read through
+// its transpose so that a warp's loads are coalesced) and TILE (32 x 64 output
+// tile, 16-deep K loop through shared memory, 2 x 4 outputs per thread).
 template <typename Real>
 __global__ void __launch_bounds__(256, 2)
 k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
@@ -171,17 +178,150 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
     }
 }
 
+// Four consecutive values from shared memory (16-byte aligned): one 128-bit
+// load for FP32, two for FP64.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// LEVEL items: Y[i][c] = sum_j MT[j][i] X[j][c] over one TM x TN tile
+// (TM = 4096 / TN); thread (tx, ty) owns rows 4 ty .. 4 ty + 3 and columns
+// 4 tx .. 4 tx + 3. Segments with few columns (the long directions of the most
+// anisotropic components) take tall tiles so that the lanes stay busy. Rows and
+// columns past the segment's end are neither computed nor written: the last
+// row tile of an n = 2^l + p - 2 direction holds only p - 2 rows.
+template <typename Real, int TN>
+__global__ void __launch_bounds__(256)
+k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real* __restrict__ in,
+           Real* __restrict__ out, const int* __restrict__ active) {
+    constexpr int TM = 4096 / TN, NTX = TN / 4;
+    constexpr int LA = 16 * TM / 256, LB = 16 * TN / 256;   // tile loads per thread per K step
+    __shared__ __align__(16) Real As[16][TM + 4];   // MT tile [j][i]
+    __shared__ __align__(16) Real Bs[16][TN + 4];   // X tile  [j][c]
+    const FDItem it = items[blockIdx.x];
+    const FDSeg sg = P.fdsegs[it.grid];
+    const Eig1D e = P.eigs[sg.eig];
+    const Real* __restrict__ MT = forward ? FDData<Real>::U(P) + e.uoff : FDData<Real>::Ut(P) + e.uoff;
+    const int n = sg.n, tid = threadIdx.x;
+    const long long* cb = P.fdcb + sg.col0;
+    const int* cs = P.fdcs + sg.col0;
+    const int* cc = P.fdcc + sg.col0;
+    const int i0 = it.i0;
+    const int c0 = (int)it.c0;
+    const int nrows = min(TM, n - i0), ncols = min(TN, sg.ncols - c0);
+    const bool split = it.j0 > 0 || it.j1 < n;
+    // this thread's loads of the X tile per K step: (kk, column) fixed over the loop
+    int ldk[LB], ldc[LB];
+    const Real* ldp[LB];
+    long long lds[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+        const int l = tid + 256 * u;
+        int kk, col;
+        if (sg.unit) { kk = l & 15; col = l >> 4; }   // stride-1 fibres: runs of 16 along j
+        else { col = l % TN; kk = l / TN; }            // strided fibres: neighbouring columns
+        ldk[u] = kk;
+        ldc[u] = col;
+        const bool ok = col < ncols && (!active || active[cc[c0 + col]]);
+        ldp[u] = ok ? in + cb[c0 + col] : nullptr;
+        lds[u] = ok ? cs[c0 + col] : 0;
+    }
+    const int tx = tid % NTX, ty = tid / NTX;
+    const bool work = 4 * ty < nrows && 4 * tx < ncols;
+    Real acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = Real(0);
+    for (int j0 = it.j0; j0 < it.j1; j0 += 16) {
+        const int kn = min(16, it.j1 - j0);
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            const int l = tid + 256 * u;
+            const int kk = l / TM, ii = l % TM;
+            As[kk][ii] = (ii < nrows && kk < kn) ? MT[(long long)(j0 + kk) * n + i0 + ii] : Real(0);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u)
+            Bs[ldk[u]][ldc[u]] = (ldp[u] && ldk[u] < kn) ? ldp[u][(long long)(j0 + ldk[u]) * lds[u]] : Real(0);
+        __syncthreads();
+        if (work) {
+            if (kn == 16) {
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    Real a[4], b[4];
+                    ld4(&As[kk][4 * ty], a);
+                    ld4(&Bs[kk][4 * tx], b);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+                }
+            } else {
+                for (int kk = 0; kk < kn; ++kk) {
+                    Real a[4], b[4];
+                    ld4(&As[kk][4 * ty], a);
+                    ld4(&Bs[kk][4 * tx], b);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!work) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int col = 4 * tx + c;
+        if (col >= ncols) continue;
+        if (active && !active[cc[c0 + col]]) continue;
+        Real* o = out + cb[c0 + col];
+        const long long st = cs[c0 + col];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = 4 * ty + r;
+            if (i >= nrows) continue;
+            if (split) atomicAdd(o + (long long)(i0 + i) * st, acc[r][c]);
+            else o[(long long)(i0 + i) * st] = acc[r][c];
+        }
+    }
+}
+
 template <typename Real>
-cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
-                           const Real* in, Real* out, const int* active, cudaStream_t s) {
-    if (nitems == 0) return cudaSuccess;
+cudaError_t launch_fd_pass(const DevPlan& P, const FDLists& L, int dir, int forward, const Real* in, Real* out,
+                           const int* active, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (L.nlvl[0] > 0) {
+        SGIGA_COUNT_LAUNCH();
+        k_fd_level<Real, 16><<<L.nlvl[0], 256, 0, s>>>(P, L.lvl[0], forward, in, out, active);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (L.nlvl[1] > 0) {
+        SGIGA_COUNT_LAUNCH();
+        k_fd_level<Real, 32><<<L.nlvl[1], 256, 0, s>>>(P, L.lvl[1], forward, in, out, active);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (L.nlvl[2] > 0) {
+        SGIGA_COUNT_LAUNCH();
+        k_fd_level<Real, 64><<<L.nlvl[2], 256, 0, s>>>(P, L.lvl[2], forward, in, out, active);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (L.nsmall == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_fd_pass<Real><<<nitems, 256, 0, s>>>(P, items, dir, forward, in, out, active);
+    k_fd_pass<Real><<<L.nsmall, 256, 0, s>>>(P, L.small, dir, forward, in, out, active);
     return cudaGetLastError();
 }
-template cudaError_t launch_fd_pass<double>(const DevPlan&, const FDItem*, int, int, int, const double*, double*,
+template cudaError_t launch_fd_pass<double>(const DevPlan&, const FDLists&, int, int, const double*, double*,
                                             const int*, cudaStream_t);
-template cudaError_t launch_fd_pass<float>(const DevPlan&, const FDItem*, int, int, int, const float*, float*,
+template cudaError_t launch_fd_pass<float>(const DevPlan&, const FDLists&, int, int, const float*, float*,
                                            const int*, cudaStream_t);
 
 // z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every entry of the local layout.

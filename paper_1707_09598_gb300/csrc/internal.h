@@ -98,14 +98,32 @@ struct Chunk {
 };
 
 // Work item of the batched mode product of the preconditioner.
-enum { FD_SMALL = 0, FD_ROWS = 1, FD_TILE = 2 };
+//   FD_SMALL: grid = piece, c0 = first output of the piece's tensor (256 per item)
+//   FD_ROWS / FD_TILE: grid = piece, rows from i0, columns from c0 (a*B + b)
+//   FD_LEVEL: grid = level segment (FDSeg), an output tile at rows i0,
+//             columns c0 of the segment, contraction range [j0, j1)
+enum { FD_SMALL = 0, FD_ROWS = 1, FD_TILE = 2, FD_LEVEL = 3 };
 struct FDItem {
     int grid;
-    int mode;           // FD_SMALL / FD_ROWS / FD_TILE
+    int mode;
     int nc;             // FD_ROWS: columns of the group (1..8)
     int i0;             // first row (output index along the direction)
-    long long c0;       // first column (a*B + b); FD_SMALL: first packed output
+    long long c0;       // first column of the segment; FD_SMALL: first packed output
     int j0, j1;         // contraction range [j0, j1) (split K: partial sums are added atomically)
+};
+
+// All long-direction mode products of one pass that share one eigenvector
+// matrix (same direction, level and kind): one GEMM Y = Mat X whose columns
+// are the columns of every such piece. Column c of the segment is the fibre
+// at fdcb[col0 + c] + j * fdcs[col0 + c], j = 0..n-1, of component fdcc[...].
+struct FDSeg {
+    int eig;            // eigen table
+    int n;              // its size
+    int ncols;
+    int unit;           // every column has stride 1 (direction 0)
+    long long col0;     // first column in the column arrays
+    int tn;             // output tile: 4096/tn rows x tn columns (tn = 16, 32 or 64, by column count)
+    int pad;
 };
 
 // Geometry patch: tensor-product NURBS with separable weights.

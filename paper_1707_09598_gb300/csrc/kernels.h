@@ -61,6 +61,10 @@ struct DevPlan {
     int nsides;
     double* gdata;           // boundary data g at the sides' points
     double* gscratch;        // projection scratch
+    const FDSeg* fdsegs;     // preconditioner level segments and their columns
+    const long long* fdcb;
+    const int* fdcs;
+    const int* fdcc;
 };
 
 // boundary.cu (multi-patch Dirichlet data)
@@ -90,9 +94,17 @@ cudaError_t launch_op2_f32(const DevPlan& P, const float* x, float* y, const int
 cudaError_t launch_op3_f32(const DevPlan& P, const float* x, float* y, const int* active, cudaStream_t s);
 cudaError_t set_op3_smem(int p, size_t bytes);
 // fd.cu
+// Work lists of one preconditioner pass: SMALL items, and LEVEL items by
+// output-tile class (16, 32, 64 columns).
+struct FDLists {
+    const FDItem* small;
+    int nsmall;
+    const FDItem* lvl[3];
+    int nlvl[3];
+};
 template <typename Real>
-cudaError_t launch_fd_pass(const DevPlan& P, const FDItem* items, int nitems, int dir, int forward,
-                           const Real* in, Real* out, const int* active, cudaStream_t s);
+cudaError_t launch_fd_pass(const DevPlan& P, const FDLists& L, int dir, int forward, const Real* in, Real* out,
+                           const int* active, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_fd_gather(const DevPlan& P, const Real* r, Real* loc, const int* active, cudaStream_t s);
 template <typename Real>

@@ -43,6 +43,20 @@ struct FastDiv {
     }
 };
 
+// A table row of N values from shared memory into registers: 128-bit loads
+// for FP32 rows of 4 (the rows start at multiples of 4 floats: every table
+// region holds T*Q rows of P+1 = 4 values), scalar loads otherwise.
+template <typename Real, int N>
+__device__ __forceinline__ void load_row(const Real* p, Real (&v)[N]) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) v[t] = p[t];
+}
+template <>
+__device__ __forceinline__ void load_row<float, 4>(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
 __device__ __forceinline__ int elem_lo(int j, int P, int M) { return j >= P ? (j - P + M - 1) / M : 0; }
 __device__ __forceinline__ int elem_hi(int j, int M, int T) { int e = j / M; return e < T - 1 ? e : T - 1; }
 

@@ -49,18 +49,28 @@ struct sgiga_plan_s {
     bool lifting = false;                // boundary data set: the load vector subtracts K_IB g_B
     double* d_l0 = nullptr;              // preconditioner local layout (multi-patch)
     float* f_l0 = nullptr;
-    std::vector<FDItem> fd[3];
+    std::vector<FDItem> fd[3];           // SMALL items per direction
+    std::vector<FDItem> fdl[3][3];       // LEVEL items per direction and tile class (16, 32, 64 columns)
+    std::vector<FDSeg> fdsegs;
+    std::vector<long long> fdcb;
+    std::vector<int> fdcs, fdcc;
     std::vector<double> knots, bp;
     Patch patch;                         // patch 0 (rational directions of the 1D tables)
     std::vector<Patch> patches;          // every geometry patch
     double* d_xb = nullptr;              // boundary data points [nbpts][2] (multi-patch)
     long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
     int maxE = 1;
-    int fd_ks = 128;            // contraction depth per preconditioner work item
+    int fd_ks = 32;             // contraction depth per preconditioner work item
+    bool fd_grouped = false;    // preconditioner layout: level-grouped GEMMs, else per-piece items
     size_t smem = 0;
     std::vector<void*> allocs;
     DevPlan dp;
     FDItem* d_fd[3] = {nullptr, nullptr, nullptr};
+    FDItem* d_fdl[3][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    FDSeg* d_fdsegs = nullptr;
+    long long* d_fdcb = nullptr;
+    int* d_fdcs = nullptr;
+    int* d_fdcc = nullptr;
     double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
     double *d_t1 = nullptr, *d_t2 = nullptr, *d_partial = nullptr, *d_scal = nullptr, *d_coef = nullptr;
     int* d_active = nullptr;
@@ -191,6 +201,17 @@ inline Vecs<float> vecs32(sgiga_plan_s* P) {
     return Vecs<float>{P->f_x, P->f_r, P->f_z, P->f_p, P->f_q, P->f_t1, P->f_t2};
 }
 
+inline FDLists fd_lists(const sgiga_plan_s* P, int k) {
+    FDLists L{};
+    L.small = P->d_fd[k];
+    L.nsmall = (int)P->fd[k].size();
+    for (int t = 0; t < 3; ++t) {
+        L.lvl[t] = P->d_fdl[k][t];
+        L.nlvl[t] = (int)P->fdl[k][t].size();
+    }
+    return L;
+}
+
 template <typename Real>
 inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active, Real* t1, Real* t2) {
     const DevPlan& D = P->dp;
@@ -213,7 +234,7 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     for (int k = 0; k < d; ++k) {
         Real* out = bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
-        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 1, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 1, in, out, active, s));
         in = out;
         cur ^= 1;
     }
@@ -221,7 +242,7 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     for (int k = 0; k < d; ++k) {
         Real* out = (k == d - 1) ? (loc ? loc : z) : bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
-        CUDA_TRY(launch_fd_pass<Real>(D, P->d_fd[k], (int)P->fd[k].size(), k, 0, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 0, in, out, active, s));
         in = out;
         cur ^= 1;
     }

@@ -30,17 +30,27 @@ def main():
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--w", type=int, default=10)
-    ap.add_argument("--domain", default="unit")
+    ap.add_argument("--domain", default="unit", help="unit, annulus or perturbed (cube with a seeded cubic perturbation)")
+    ap.add_argument("--tune", action="store_true", help="run the autotuner first")
     a = ap.parse_args()
     stream = torch.cuda.Stream()
     f32 = a.op.endswith("_f32")
-    P = sgiga.Plan(a.d, a.p, a.w, domain=a.domain, stream=stream, precision="mixed" if f32 else "fp64")
+    kw = {}
+    if a.domain == "perturbed":   # the learned-preconditioner geometry: seeded cubic perturbation, general metric
+        from paper_1707_09598_gb300.inputs import perturbed_cube_patch
+        kn, cp = perturbed_cube_patch(1)
+        kw = dict(domain="patch", patch=([3, 3, 3], kn, cp))
+    else:
+        kw = dict(domain=a.domain)
+    P = sgiga.Plan(a.d, a.p, a.w, stream=stream, precision="mixed" if f32 else "fp64", **kw)
+    if a.tune:
+        sgiga.sgiga_autotune(P.handle, reps=3)
     n = P.info.ndof
     x = torch.as_tensor(random_vector(n, 1), device="cuda")
     if f32:
         x = x.float()
     y = torch.zeros_like(x)
-    src = "sine" if a.domain == "unit" else "annulus_paper"
+    src = {"unit": "sine", "annulus": "annulus_paper"}.get(a.domain, "one")
     sgiga.sgiga_set_rhs_builtin(P.handle, src)
     pts = torch.as_tensor(eval_points(a.d, 16), device="cuda")
     uc = torch.zeros(P.info.ngrids * len(pts), dtype=torch.float64, device="cuda")

@@ -56,6 +56,7 @@ def main():
         P = sgiga.Plan(3, 3, a.w, domain="patch", patch=([3, 3, 3], kn, cp), precision=precision,
                        precond=precond, stream=stream)
         sgiga.sgiga_set_coefficient(P.handle, om, ph, amp)
+        sgiga.sgiga_autotune(P.handle, reps=2)     # tiles and preconditioner layout, measured
         sgiga.sgiga_set_rhs_builtin(P.handle, "one")
         return P, time.perf_counter() - t0
 

@@ -76,7 +76,7 @@ class sgiga_tune_result(ctypes.Structure):
     _fields_ = [("ncand", ctypes.c_int), ("best", ctypes.c_int), ("ntiles", ctypes.c_int), ("best_ms", ctypes.c_double),
                 ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8),
                 ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
-                ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8)]
+                ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8)]
 
 
 class sgiga_solve_stats(ctypes.Structure):
@@ -101,7 +101,7 @@ _SIGS = {
     "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
     "sgiga_apply_f32": (_I, [_P, _P, _P]),
-    "sgiga_set_precond_split": (_I, [_P, _I]),
+    "sgiga_set_precond_split": (_I, [_P, _I, _I]),
     "sgiga_precond_f32": (_I, [_P, _P, _P]),
     "sgiga_precond": (_I, [_P, _P, _P]),
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
@@ -284,8 +284,8 @@ def sgiga_autotune(plan, reps=3):
     return out
 
 
-def sgiga_set_precond_split(plan, ks):
-    _check(_lib.sgiga_set_precond_split(plan, int(ks)))
+def sgiga_set_precond_split(plan, ks, grouped=False):
+    _check(_lib.sgiga_set_precond_split(plan, int(ks), int(bool(grouped))))
 
 
 def sgiga_set_solver_options(plan, use_graph=True, inner_tol=1e-5, inner_max=100):

@@ -127,8 +127,10 @@ def test_boundary_points_and_user_data(sg):
         assert _rel(b1, b0) < 1e-14
 
 
-def test_preconditioner_is_weighted_schwarz(sg):
-    with _plan(sg, 5) as P:
+@pytest.mark.parametrize("grouped", [False, True])
+def test_preconditioner_is_weighted_schwarz(sg, grouped):
+    with _plan(sg, 7) as P:
+        sg.sgiga_set_precond_split(P.handle, 32, grouped)
         n = P.info.ndof
         r = random_vector(n, seed=72)
         z = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -137,7 +139,8 @@ def test_preconditioner_is_weighted_schwarz(sg):
         for g in P.grids:
             comp = _oracle_comp(g, 2.0)
             pm = _perm(comp, g.dof_off)
-            assert _rel(z[pm], mp.schwarz_apply(comp, r[pm])) < 1e-11, g.levels[:2]
+            # graded level-7 directions: the eigenvectors' conditioning limits both FP64 sides to ~1e-11
+            assert _rel(z[pm], mp.schwarz_apply(comp, r[pm])) < 1e-10, g.levels[:2]
 
 
 def _points(n=40, seed=73):

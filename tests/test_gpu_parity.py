@@ -197,13 +197,15 @@ def test_preconditioner(sg, case):
             assert _rel(z[sl], ref) < 1e-11, (g.levels[:d], _rel(z[sl], ref))
 
 
+@pytest.mark.parametrize("grouped", [False, True])
 @pytest.mark.parametrize("ks", [16, 32, 64, 128, 256])
-def test_preconditioner_split_depths(sg, ks):
-    """Long 1D contractions (ROWS and TILE items, split into ks-deep partial
-    sums added atomically) give the oracle's FD result at every depth."""
+def test_preconditioner_split_depths(sg, ks, grouped):
+    """Long 1D contractions (per-piece ROWS and TILE items, or level-grouped
+    GEMM tiles, split into ks-deep partial sums added atomically) give the
+    oracle's FD result at every depth."""
     case = ("unit", 3, 3, 2, 10, "uniform", 1.0, 1)
     with _plan(sg, case) as P:
-        sg.sgiga_set_precond_split(P.handle, ks)
+        sg.sgiga_set_precond_split(P.handle, ks, grouped)
         n = P.info.ndof
         rv = random_vector(n, seed=13)
         z = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -418,7 +420,7 @@ def test_autotune_keeps_the_operator(sg):
         sg.sgiga_precond(P.handle, rv, z0)
         res = sg.sgiga_autotune(P.handle, reps=2)
         assert res.ncand >= 4 and 0 <= res.best < res.ncand and res.best_ms > 0
-        assert res.fd_ncand == 5 and 0 <= res.fd_best < 5 and res.fd_ms[res.fd_best] > 0 and res.fd_nitems > 0
+        assert res.fd_ncand == 8 and 0 <= res.fd_best < 8 and res.fd_ms[res.fd_best] > 0 and res.fd_nitems > 0
         z1 = torch.zeros_like(x)
         sg.sgiga_precond(P.handle, rv, z1)
         assert _rel(z1.cpu().numpy(), z0.cpu().numpy()) < 1e-13
