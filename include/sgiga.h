@@ -165,8 +165,10 @@ typedef struct {
     double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
     double seconds;          /* wall time of the call */
     int inner_iterations;    /* MIXED_FP32: inner CG iterations summed over refinement steps */
-    int fallback;            /* MIXED_FP32 bit flags. 1 (LEARNED): a refinement step without a
-                                tenfold residual reduction switched the rest of the solve to FD.
+    int fallback;            /* MIXED_FP32 bit flags. 1 (LEARNED): the correction was switched
+                                off for the rest of the solve, after a refinement step without a
+                                tenfold residual reduction or an inner solve that had not cut its
+                                residual 100x in 16 iterations (FD continues).
                                 2: refinement stalled (two steps that did not halve some
                                 component's residual: the FP32 operator's error times the
                                 condition number is not small) and FP64 PCG finished the

@@ -1347,9 +1347,40 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
         }
         CUDA_TRY(launch_ir_down(D, P->d_r, P->f_b, P->d_active_o, s));
         int inner = 0;
+        // With the learned correction, the inner flexible CG must cut its
+        // residual 100x within 16 iterations (FD-preconditioned CG does on
+        // these systems); otherwise that inner solve stops there and FD takes
+        // over for the rest of the solve.
+        struct ProgressHook : PcgHook {
+            sgiga_plan_s* P;
+            int ng;
+            int after_iteration(int it) override {
+                if (it + 1 != 16 || P->learned_off) return 0;
+                std::vector<double> rr(ng), bb(ng);
+                std::vector<int> act(ng);
+                cudaStream_t st = P->stream;
+                if (cudaMemcpyAsync(rr.data(), P->d_scal + 3 * ng, ng * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaMemcpyAsync(bb.data(), P->d_scal, ng * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaMemcpyAsync(act.data(), P->d_active, ng * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return fail(SGIGA_ERR_CUDA, "progress check failed");
+                double worst = 0.0;
+                for (int g = 0; g < ng; ++g)
+                    if (act[g] && bb[g] > 0) worst = std::max(worst, std::sqrt(rr[g] / bb[g]));
+                if (worst > 1e-2) {
+                    P->learned_off = true;
+                    return 1;   // stop this inner solve (not an error)
+                }
+                return 0;
+            }
+        } hook;
+        hook.P = P;
+        hook.ng = ng;
+        const bool watch = P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready && !P->learned_off;
         int rc = pcg<float>(P, P->f_b, vecs32(P), P->inner_tol, P->inner_max, P->d_active_o, P->d_active,
-                            P->d_iters, P->d_scal, &inner);
+                            P->d_iters, P->d_scal, &inner, watch ? &hook : nullptr);
         if (rc < 0) return rc;
+        if (watch && P->learned_off) inner = 16;
         inner_total += inner;
         CUDA_TRY(launch_ir_up(D, P->d_x, P->f_x, P->d_active_o, s));
         if ((rc = apply_op(P, P->d_x, P->d_q, P->d_active_o))) return rc;
