@@ -132,12 +132,33 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
 #pragma unroll
         for (int t = 0; t < P1; ++t) a0[t] = a1[t] = a2[t] = 0.0;
         long long gi = td.g_off + pid;
+        // FP32: the metric values of the element's Q quadrature points are
+        // loaded before any is used, so that their loads are in flight together
+        // (the FP32 instance is latency-bound on them; the FP64 one is bound by
+        // its FMA pipe and keeps its registers)
+        constexpr bool PRE = sizeof(Real) == 4 && MODE == 0;
+        constexpr int NGP = DIAG ? 3 : 6;
+        Real gpre[PRE ? Q : 1][PRE ? NGP : 1];
         for (int ea = 0; ea < Ta; ++ea) {
             const int base = ea * M;
             Real i0[P1], i1[P1], i2[P1];
             if (MODE == 0) {
 #pragma unroll
                 for (int t = 0; t < P1; ++t) { i0[t] = c0[base + t]; i1[t] = c1[base + t]; i2[t] = c2[base + t]; }
+            }
+            if constexpr (PRE) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const long long gq = gi + (long long)q * npen;
+                    if (DIAG) {
+                        gpre[q][0] = G[gq];
+                        gpre[q][1] = G[3 * nqp + gq];
+                        gpre[q][2] = G[5 * nqp + gq];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NGP; ++c) gpre[q][c] = G[c * nqp + gq];
+                    }
+                }
             }
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -150,7 +171,19 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
 #pragma unroll
                     for (int t = 0; t < P1; ++t) { ga += dt[t] * i0[t]; gb += bt[t] * i1[t]; gc += bt[t] * i2[t]; }
                     Real va, vb, vc;
-                    if (DIAG) {   // metric with zero off-diagonal entries: only G_aa, G_bb, G_cc
+                    if constexpr (PRE) {
+                        if (DIAG) {
+                            va = gpre[q][0] * ga;
+                            vb = gpre[q][1] * gb;
+                            vc = gpre[q][2] * gc;
+                        } else {
+                            const Real G00 = gpre[q][0], G01 = gpre[q][1], G02 = gpre[q][2];
+                            const Real G11 = gpre[q][3], G12 = gpre[q][4], G22 = gpre[q][NGP - 1];
+                            va = G00 * ga + G01 * gb + G02 * gc;
+                            vb = G01 * ga + G11 * gb + G12 * gc;
+                            vc = G02 * ga + G12 * gb + G22 * gc;
+                        }
+                    } else if (DIAG) {   // metric with zero off-diagonal entries: only G_aa, G_bb, G_cc
                         va = G[gi] * ga;
                         vb = G[3 * nqp + gi] * gb;
                         vc = G[5 * nqp + gi] * gc;
