@@ -333,6 +333,14 @@ int sgiga_eval(sgiga_plan_t plan, const double* xi, long long npts, double* u_co
 int sgiga_eval_grad(sgiga_plan_t plan, const double* xi, const int* patch, long long npts, double* u_comp,
                     double* grad_comp);
 
+/* The geometry map at parametric points (eq. F-B-splines): x = F(xi)
+ * [npts][d] and det J [npts] (signed; NULL to skip), for points xi [npts][d]
+ * of the given patches (patch [npts], NULL: patch 0); host or device buffers.
+ * Serves error integrals on the physical domain (weights times |det J|).
+ * SGIGA_ERR_ARG for a point outside [0,1]^d or a patch id out of range. */
+int sgiga_map_points(sgiga_plan_t plan, const double* xi, const int* patch, long long npts, double* x,
+                     double* detj);
+
 /* u[j] = sum_g c_g u_comp[g][j], FP64 with Neumaier compensation
  * (eq. TD-combi-tec). u_comp [ngrids][npts], u [npts], host or device. */
 int sgiga_combine(sgiga_plan_t plan, const double* u_comp, long long npts, double* u);

@@ -1078,6 +1078,37 @@ int sgiga_eval_grad(sgiga_plan_t P, const double* xi, const int* patch, long lon
     return SGIGA_OK;
 }
 
+int sgiga_map_points(sgiga_plan_t P, const double* xi, const int* patch, long long npts, double* x, double* detj) {
+    if (!P || (npts > 0 && (!xi || !x))) return fail(SGIGA_ERR_ARG, "null argument");
+    if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    if (npts == 0) return SGIGA_OK;
+    const int d = P->d;
+    const size_t xb = (size_t)npts * d * 8, pb = patch ? ((size_t)npts * 4 + 15) / 16 * 16 : 0, db = (size_t)npts * 8;
+    const bool xidev = is_device(xi), pdev = !patch || is_device(patch), xdev = is_device(x);
+    const bool ddev = !detj || is_device(detj);
+    int rc = ensure_stage(P, (xidev ? 0 : xb) + (pdev ? 0 : pb) + (xdev ? 0 : xb) + (ddev ? 0 : db));
+    if (rc) return rc;
+    char* st = (char*)P->stage;
+    cudaStream_t s = P->stream;
+    const double* xid = xi;
+    if (!xidev) { CUDA_TRY(cudaMemcpyAsync(st, xi, xb, cudaMemcpyHostToDevice, s)); xid = (const double*)st; st += xb; }
+    const int* pd = patch;
+    if (!pdev) { CUDA_TRY(cudaMemcpyAsync(st, patch, (size_t)npts * 4, cudaMemcpyHostToDevice, s)); pd = (const int*)st; st += pb; }
+    double* xd = xdev ? x : (double*)st;
+    if (!xdev) st += xb;
+    double* dd = ddev ? detj : (double*)st;
+    CUDA_TRY(cudaMemsetAsync(P->dp.flags + 1, 0, sizeof(int), s));
+    CUDA_TRY(launch_map_points(P->dp, xid, pd, npts, (int)P->patches.size(), xd, dd, s));
+    CUDA_TRY(cudaMemcpyAsync(P->h_nactive, P->dp.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!xdev) CUDA_TRY(cudaMemcpyAsync(x, xd, xb, cudaMemcpyDeviceToHost, s));
+    if (!ddev) CUDA_TRY(cudaMemcpyAsync(detj, dd, db, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int hflag = *P->h_nactive;
+    if (hflag & 2) return fail(SGIGA_ERR_ARG, "patch id out of range");
+    if (hflag) return fail(SGIGA_ERR_ARG, "point outside [0,1]^d");
+    return SGIGA_OK;
+}
+
 int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
     if (!P || !f) return fail(SGIGA_ERR_ARG, "null argument");
     if (source < 0 || source > SGIGA_SRC_HARMONIC_QUADRATIC) return fail(SGIGA_ERR_ARG, "unknown source");

@@ -337,4 +337,45 @@ cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh,
     return cudaGetLastError();
 }
 
+// Physical coordinates and Jacobian determinant of the patch map at
+// parametric points (eq. F-B-splines; NURBS with separable weights).
+// patch_eval called out of line: inlined into this kernel, the build produced
+// NaN maps (the other call sites, checked by the parity tests, are correct
+// inlined); this kernel is off the hot path.
+__device__ __noinline__ void patch_eval_call(const Patch& pt, const double* t, double* X, double (*J)[3]) {
+    patch_eval(pt, t, X, J);
+}
+
+__global__ void k_map_points(DevPlan P, const double* xi, const int* patch, long long npts, int npatch, double* x,
+                             double* detj) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npts) return;
+    const int d = P.d;
+    int q = patch ? patch[j] : 0;
+    if (q < 0 || q >= npatch) { atomicOr(&P.flags[1], 2); q = 0; }
+    double t[3] = {0.0, 0.0, 0.0}, X[3] = {0.0, 0.0, 0.0};
+    double J[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int k = 0; k < d; ++k) {
+        t[k] = xi[j * d + k];
+        if (!(t[k] >= 0.0 && t[k] <= 1.0)) { atomicOr(&P.flags[1], 1); t[k] = t[k] < 0.0 ? 0.0 : 1.0; }
+    }
+    patch_eval_call(P.patch[q], t, X, J);
+    for (int k = 0; k < d; ++k) x[j * d + k] = X[k];
+    if (detj) {
+        double dt;
+        if (d == 2) dt = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        else dt = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                  J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        detj[j] = dt;
+    }
+}
+
+cudaError_t launch_map_points(const DevPlan& P, const double* xi, const int* patch, long long npts, int npatch,
+                              double* x, double* detj, cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_map_points<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(P, xi, patch, npts, npatch, x, detj);
+    return cudaGetLastError();
+}
+
 }  // namespace sgiga

@@ -81,6 +81,8 @@ cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
 cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s);
 cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s);
+cudaError_t launch_map_points(const DevPlan& P, const double* xi, const int* patch, long long npts, int npatch,
+                              double* x, double* detj, cudaStream_t s);
 cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s);
 cudaError_t launch_source_qp(const DevPlan& P, int source, double* fout, cudaStream_t s);
 cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s);

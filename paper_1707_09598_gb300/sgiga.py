@@ -112,6 +112,7 @@ _SIGS = {
     "sgiga_eval": (_I, [_P, _P, _L, _P]),
     "sgiga_eval_grad": (_I, [_P, _P, _P, _L, _P, _P]),
     "sgiga_boundary_points": (_I, [_P, _P]),
+    "sgiga_map_points": (_I, [_P, _P, _P, _L, _P, _P]),
     "sgiga_set_dirichlet": (_I, [_P, _P]),
     "sgiga_combine": (_I, [_P, _P, _L, _P]),
     "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
@@ -319,6 +320,12 @@ def sgiga_eval_grad(plan, xi, patch, npts, u_comp, grad_comp=None):
     _check(_lib.sgiga_eval_grad(plan, _ptr(xi, npts * 2), _ptr(patch, npts, dtype=np.int32), int(npts),
                                 _ptr(u_comp, npts * info.ngrids),
                                 _ptr(grad_comp, 2 * npts * info.ngrids) if grad_comp is not None else None))
+
+
+def sgiga_map_points(plan, xi, patch, npts, x, detj=None):
+    d = sgiga_plan_info(plan).d
+    _check(_lib.sgiga_map_points(plan, _ptr(xi, npts * d), _ptr(patch, npts, dtype=np.int32), int(npts),
+                                 _ptr(x, npts * d), _ptr(detj, npts) if detj is not None else None))
 
 
 def sgiga_boundary_points(plan, xb):

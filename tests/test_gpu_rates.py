@@ -1,0 +1,62 @@
+"""Convergence of the GPU path on the quarter annulus (the paper's Table 2,
+Sec. 4.2): the error integrals agree with the oracle's at small levels, and
+the fitted rates match the printed ones."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import driver  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_09598_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1707_09598_gb300 import rates_report
+    return rates_report
+
+
+@pytest.mark.parametrize("p,r", [(2, 1), (3, 2)])
+def test_errors_match_the_oracle(rr, p, r):
+    stream = torch.cuda.Stream()
+    rows = rr.run_case(p, r, [3, 4], 16, stream)
+    for row in rows:
+        res = driver.solve_components("annulus", 2, p, row["w"], "annulus_paper2", r=r)
+        l2, h1 = driver.errors(res, "annulus_paper2", nel=16)
+        assert abs(row["l2"] - l2) / l2 < 1e-6, (row, l2)
+        assert abs(row["h1"] - h1) / h1 < 1e-6, (row, h1)
+
+
+@pytest.mark.parametrize("rp", sorted([(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)]))
+def test_rates_match_table2(rr, rp):
+    """Fit over w = 3..7. The paper states neither its range of levels nor its
+    error rule; the fitted slopes depend on both by up to ~0.4 (p = 3 C^0 H1:
+    2.8-2.9 here, 3.21 printed). The discrete solutions themselves match the
+    oracle's (test above and the parity tests)."""
+    p, r = rp
+    ws = list(range(3, 8))
+    rows = rr.run_case(p, r, ws, 32, torch.cuda.Stream())
+    h1_ref, l2_ref = rr.TABLE2[(r, p)]
+    assert abs(rr.rate(ws, [x["l2"] for x in rows]) - l2_ref) < 0.4
+    assert abs(rr.rate(ws, [x["h1"] for x in rows]) - h1_ref) < 0.4
+
+
+def test_map_points_against_the_oracle_geometry(rr):
+    from paper_1707_09598_gb300 import sgiga
+    from oracle import geometry
+    from paper_1707_09598_gb300.inputs import random_points
+    xi = np.ascontiguousarray(random_points(50, 2, seed=81))
+    g = geometry.make("annulus", 2)
+    with sgiga.Plan(2, 2, 3, domain="annulus") as P:
+        x = np.zeros(100)
+        det = np.zeros(50)
+        sgiga.sgiga_map_points(P.handle, xi, None, 50, x, det)
+    assert np.abs(x.reshape(-1, 2) - g.map(xi)).max() < 1e-14
+    assert np.abs(det - np.linalg.det(g.jacobian(xi))).max() < 1e-13
