@@ -9,6 +9,8 @@ errors            L2 / H1 errors of the combined solution against the exact
                   u, by Gauss quadrature on a fine parametric mesh mapped by F
 rate              least-squares slope of log2(error) against the level
                   (Sec. 4.2: rates fitted with a polynomial fit)
+functional        l(u) = int g u of the combined solution from the
+                  components' load vectors (no evaluation points)
 """
 import numpy as np
 
@@ -82,3 +84,17 @@ def rate(levels, errs):
     A = np.vstack([np.asarray(levels, dtype=np.float64), np.ones(len(levels))]).T
     slope, _ = np.linalg.lstsq(A, np.log2(np.asarray(errs)), rcond=None)[0]
     return -slope
+
+
+def functional(results, g):
+    """Linear functional l(u) = int_Omega g u dx of the combined solution,
+    without evaluating it anywhere: sum_i c_i l(u_i), with l(u_i) = b_g . u_i,
+    b_g the Galerkin load vector of g in component i's space (the same rule as
+    the right-hand side, Sec. 2.2). Returns (per-component values, combined
+    value with Neumaier compensation, eq. TD-combi-tec)."""
+    vals, coef = [], []
+    for _, c, comp, u in results:
+        vals.append(float(comp.load_vector(g) @ u))
+        coef.append(c)
+    vals = np.array(vals)
+    return vals, float(combination.combine(vals[:, None], np.array(coef, dtype=np.float64))[0])

@@ -188,6 +188,19 @@ class Component:
         self.b = bfull[I] if f is not None else None
         return self
 
+    def load_vector(self, g):
+        """b_i = sum_q w_q |det J_q| g(x_q) R_i(xi_q) over the interior
+        functions: the load vector of g (the assembly's rule), without
+        touching the assembled system."""
+        bfull = np.zeros(self.nfull)
+        for em in self._element_batches(512):
+            val, _, Xi, W, loc = self._element_data(em)
+            nb, nq = W.shape
+            det = np.abs(np.linalg.det(self.geom.jacobian(Xi).reshape(nb, nq, self.d, self.d)))
+            gx = g(self.geom.map(Xi)).reshape(nb, nq)
+            np.add.at(bfull, loc.reshape(-1), np.einsum("eqA,eq->eA", val, W * det * gx).reshape(-1))
+        return bfull[self.interior]
+
     def solve(self, b=None):
         """Sparse direct solve of the Dirichlet-eliminated system (Sec. 4.1)."""
         rhs = self.b if b is None else b
