@@ -188,8 +188,8 @@ void sgiga_destroy(sgiga_plan_t plan);
 int sgiga_plan_info(sgiga_plan_t plan, sgiga_info* out /* host */);
 int sgiga_grid_info(sgiga_plan_t plan, int g, sgiga_grid* out /* host */);
 
-/* Physical coordinates x = F(xi_q) of every quadrature point: xq is a device
- * buffer [d][nqp] (one plane per coordinate, natural qp order). */
+/* Physical coordinates x = F(xi_q) of every quadrature point: xq is a host or
+ * device buffer [d][nqp] (one plane per coordinate, natural qp order). */
 int sgiga_qp_coords(sgiga_plan_t plan, double* xq);
 
 /* Load vector b_i = sum_q w_q |det J_q| f(x_q) R_i(xi_q) (Sec. 2.2, Galerkin
@@ -332,6 +332,17 @@ int sgiga_eval(sgiga_plan_t plan, const double* xi, long long npts, double* u_co
  * SGIGA_ERR_ARG for d = 3 or a patch id out of range. */
 int sgiga_eval_grad(sgiga_plan_t plan, const double* xi, const int* patch, long long npts, double* u_comp,
                     double* grad_comp);
+
+/* Linear functional of the combined solution without evaluation points:
+ * l(u) = sum_g c_g int_Omega q u_g dx = sum_g c_g (b_q . u_g), with b_q the
+ * load vector of q in component g's space (the right-hand side's rule,
+ * Sec. 2.2) and the combination coefficients of eq. TD-combi-tec. q_qp is q at
+ * the quadrature points [nqp] in natural order (as for sgiga_set_rhs), host or
+ * device. comp [ngrids] (host, may be NULL) receives the per-component
+ * values, *combined (host) the Neumaier-compensated sum. Uses the plan's
+ * solution; the load vector is not changed. SGIGA_ERR_ARG on a plan with
+ * Dirichlet data. */
+int sgiga_functional(sgiga_plan_t plan, const double* q_qp, double* comp, double* combined);
 
 /* The geometry map at parametric points (eq. F-B-splines): x = F(xi)
  * [npts][d] and det J [npts] (signed; NULL to skip), for points xi [npts][d]

@@ -967,7 +967,15 @@ int sgiga_grid_info(sgiga_plan_t P, int g, sgiga_grid* out) {
 
 int sgiga_qp_coords(sgiga_plan_t P, double* xq) {
     if (!P || !xq) return fail(SGIGA_ERR_ARG, "null argument");
-    CUDA_TRY(launch_qp_coords(P->dp, xq, P->stream));
+    const size_t bytes = (size_t)P->d * P->nqp * 8;
+    double* out = xq;
+    if (!is_device(xq)) {   // host buffer: through the staging area
+        int rc = ensure_stage(P, bytes);
+        if (rc) return rc;
+        out = (double*)P->stage;
+    }
+    CUDA_TRY(launch_qp_coords(P->dp, out, P->stream));
+    if (out != xq) CUDA_TRY(cudaMemcpyAsync(xq, out, bytes, cudaMemcpyDeviceToHost, P->stream));
     CUDA_TRY(cudaStreamSynchronize(P->stream));
     return SGIGA_OK;
 }
@@ -1078,6 +1086,33 @@ int sgiga_eval_grad(sgiga_plan_t P, const double* xi, const int* patch, long lon
     return SGIGA_OK;
 }
 
+int sgiga_functional(sgiga_plan_t P, const double* q, double* comp, double* combined) {
+    if (!P || !q || !combined) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->lifting) return fail(SGIGA_ERR_ARG, "functional: plans with Dirichlet data are not supported");
+    cudaStream_t s = P->stream;
+    const DevPlan& D = P->dp;
+    const double* qd = q;
+    if (!is_device(q)) {
+        int rc = ensure_stage(P, (size_t)P->nqp * 8);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(P->stage, q, (size_t)P->nqp * 8, cudaMemcpyHostToDevice, s));
+        qd = (const double*)P->stage;
+    }
+    const int ng = (int)P->comps.size();
+    // b_q into a work vector (the density buffer is an intermediate of the load vector only)
+    CUDA_TRY(launch_rhs_density_user(D, qd, s));
+    CUDA_TRY(cudaMemsetAsync(P->d_t1, 0, (size_t)P->ndof * 8, s));
+    if (P->d == 3) CUDA_TRY(launch_op3(D, nullptr, P->d_t1, nullptr, 1, s));
+    else CUDA_TRY(launch_op2(D, nullptr, P->d_t1, nullptr, 1, s));
+    double* vals = P->d_scal + 7 * ng;        // scratch slot of the CG scalars
+    CUDA_TRY(launch_dot<double>(D, P->d_t1, P->d_x, P->d_partial, vals, s));
+    CUDA_TRY(launch_combine(D, vals, 1, P->d_coef, P->d_scal + 6 * ng, s));
+    if (comp) CUDA_TRY(cudaMemcpyAsync(comp, vals, (size_t)ng * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(combined, P->d_scal + 6 * ng, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SGIGA_OK;
+}
+
 int sgiga_map_points(sgiga_plan_t P, const double* xi, const int* patch, long long npts, double* x, double* detj) {
     if (!P || (npts > 0 && (!xi || !x))) return fail(SGIGA_ERR_ARG, "null argument");
     if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
@@ -1163,6 +1198,7 @@ int sgiga_get_rhs(sgiga_plan_t P, double* b) {
 
 int sgiga_apply(sgiga_plan_t P, const double* x, double* y) {
     if (!P || !x || !y) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!is_device(x) || !is_device(y)) return fail(SGIGA_ERR_ARG, "x and y must be device buffers");
     int rc = apply_op(P, x, y, nullptr);
     if (rc) return rc;
     CUDA_TRY(cudaGetLastError());
@@ -1171,6 +1207,7 @@ int sgiga_apply(sgiga_plan_t P, const double* x, double* y) {
 
 int sgiga_apply_f32(sgiga_plan_t P, const float* x, float* y) {
     if (!P || !x || !y) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!is_device(x) || !is_device(y)) return fail(SGIGA_ERR_ARG, "x and y must be device buffers");
     if (P->cfg.precision != SGIGA_PREC_MIXED_FP32) return fail(SGIGA_ERR_ARG, "plan has no FP32 data (precision)");
     int rc = apply_op(P, x, y, nullptr);
     if (rc) return rc;
@@ -1180,11 +1217,13 @@ int sgiga_apply_f32(sgiga_plan_t P, const float* x, float* y) {
 
 int sgiga_precond(sgiga_plan_t P, const double* r, double* z) {
     if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!is_device(r) || !is_device(z)) return fail(SGIGA_ERR_ARG, "r and z must be device buffers");
     return precond_fd<double>(P, r, z, nullptr, P->d_t1, P->d_t2);
 }
 
 int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
     if (!P || !r || !z) return fail(SGIGA_ERR_ARG, "null argument");
+    if (!is_device(r) || !is_device(z)) return fail(SGIGA_ERR_ARG, "r and z must be device buffers");
     if (P->cfg.precision != SGIGA_PREC_MIXED_FP32) return fail(SGIGA_ERR_ARG, "plan has no FP32 data (precision)");
     return precond_fd<float>(P, r, z, nullptr, P->f_t1, P->f_t2);
 }

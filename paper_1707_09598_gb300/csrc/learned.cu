@@ -235,6 +235,7 @@ int sgiga_net_set_params(sgiga_plan_t P, const float* host) {
 
 int sgiga_net_forward(sgiga_plan_t P, const float* in, float* out) {
     if (!P || !P->net || !in || !out) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    if (!is_device(in) || !is_device(out)) return fail(SGIGA_ERR_ARG, "in and out must be device buffers");
     Net* n = P->net;
     CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
     int rc = net_forward(P);
@@ -246,6 +247,7 @@ int sgiga_net_forward(sgiga_plan_t P, const float* in, float* out) {
 
 int sgiga_net_backward(sgiga_plan_t P, const float* in, const float* dy, float* grad_host) {
     if (!P || !P->net || !in || !dy || !grad_host) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    if (!is_device(in) || !is_device(dy)) return fail(SGIGA_ERR_ARG, "in and dy must be device buffers");
     Net* n = P->net;
     CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
     int rc = net_forward(P);

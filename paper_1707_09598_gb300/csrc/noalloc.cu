@@ -103,6 +103,18 @@ extern "C" int sgiga_fd_apply_noalloc(int d, const int* n, const double* const* 
         G.lam[k] = lam[k];
         N *= n[k];
     }
+    // every array is read or written by kernels: host memory would fault the device
+    auto on_device = [](const void* ptr) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    };
+    bool dev_ok = on_device(r) && on_device(z);
+    for (int k = 0; k < d; ++k) dev_ok = dev_ok && on_device(U[k]) && on_device(lam[k]);
+    if (!dev_ok) {
+        set_last_error("sgiga_fd_apply_noalloc: r, z, U[k] and lam[k] must be device buffers");
+        return SGIGA_ERR_ARG;
+    }
     if (N > SGIGA_NOALLOC_MAX_DOFS) {
         set_last_error("sgiga_fd_apply_noalloc: grid has more than SGIGA_NOALLOC_MAX_DOFS (262144) entries");
         return SGIGA_ERR_ARG;

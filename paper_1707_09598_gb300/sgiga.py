@@ -113,6 +113,7 @@ _SIGS = {
     "sgiga_eval_grad": (_I, [_P, _P, _P, _L, _P, _P]),
     "sgiga_boundary_points": (_I, [_P, _P]),
     "sgiga_map_points": (_I, [_P, _P, _P, _L, _P, _P]),
+    "sgiga_functional": (_I, [_P, _P, _P, _P]),
     "sgiga_set_dirichlet": (_I, [_P, _P]),
     "sgiga_combine": (_I, [_P, _P, _L, _P]),
     "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
@@ -320,6 +321,15 @@ def sgiga_eval_grad(plan, xi, patch, npts, u_comp, grad_comp=None):
     _check(_lib.sgiga_eval_grad(plan, _ptr(xi, npts * 2), _ptr(patch, npts, dtype=np.int32), int(npts),
                                 _ptr(u_comp, npts * info.ngrids),
                                 _ptr(grad_comp, 2 * npts * info.ngrids) if grad_comp is not None else None))
+
+
+def sgiga_functional(plan, q_qp):
+    """(per-component values, combined value) of l(u) = sum_g c_g int q u_g."""
+    info = sgiga_plan_info(plan)
+    comp = np.zeros(info.ngrids)
+    out = np.zeros(1)
+    _check(_lib.sgiga_functional(plan, _ptr(q_qp, info.nqp), _ptr(comp), _ptr(out)))
+    return comp, float(out[0])
 
 
 def sgiga_map_points(plan, xi, patch, npts, x, detj=None):

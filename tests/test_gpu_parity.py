@@ -13,7 +13,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import combination, fd, geometry, problems  # noqa: E402
+from oracle import combination, driver, fd, geometry, problems  # noqa: E402
 from oracle.galerkin import Component, Space1D  # noqa: E402
 from paper_1707_09598_gb300.inputs import eval_points, random_points, random_vector  # noqa: E402
 
@@ -457,3 +457,46 @@ def test_component_subset_plan(sg):
         assert _rel(v, u[g.dof_off:g.dof_off + g.ndof]) < 1e-12
     with pytest.raises(sg.SgigaError):
         sg.Plan(3, 3, 7, components=[(7, 7, 7)])
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[5]])
+def test_functional_against_oracle(sg, case):
+    """l(u) = sum_g c_g int q u_g from the load vector of q, without evaluation
+    points, matches the oracle's (per component and combined)."""
+    domain, d, p, r, w, grading, gamma, mn = case
+    prob = {"unit": "sine%d" % d, "annulus": "annulus_sinx"}[domain]
+    if domain == "annulus" and d == 3:
+        pytest.skip("no 3D annulus source")
+    src = {"unit": "sine", "annulus": "annulus"}[domain]
+    with _plan(sg, case) as P:
+        sg.sgiga_set_rhs_builtin(P.handle, src)
+        sg.sgiga_solve(P.handle, 1e-13, 100)
+        xq = torch.zeros(d * P.info.nqp, dtype=torch.float64, device="cuda")   # device buffer
+        sg.sgiga_qp_coords(P.handle, xq)
+        xq = xq.cpu().numpy().reshape(d, -1).T
+        qfun = lambda x: 1.0 + np.cos(2.0 * x[:, 0]) * x[:, 1]
+        vals, comb = sg.sgiga_functional(P.handle, np.ascontiguousarray(qfun(xq)))
+        res = []
+        for g in P.grids:
+            comp = _component(case, g).assemble(f=problems.get(prob).f)
+            res.append((tuple(g.levels[:d]), g.coeff, comp, comp.solve()))
+        ov, oc = driver.functional(res, qfun)
+        assert _rel(vals, ov) < 1e-10
+        assert abs(comb - oc) <= 1e-10 * abs(oc)
+
+
+def test_host_pointers_are_refused_not_dereferenced(sg):
+    """Entry points whose kernels read caller buffers refuse host memory with
+    an error status (the binding accepts numpy arrays; a kernel would fault)."""
+    with _plan(sg, CASES[0]) as P:
+        n = P.info.ndof
+        xh, yh = np.zeros(n), np.zeros(n)
+        for fn in (sg.sgiga_apply, sg.sgiga_precond):
+            with pytest.raises(sg.SgigaError):
+                fn(P.handle, xh, yh)
+        # host buffers are fine where the call stages them
+        xq = np.zeros(2 * P.info.nqp)
+        sg.sgiga_qp_coords(P.handle, xq)
+        xd = torch.zeros(2 * P.info.nqp, dtype=torch.float64, device="cuda")
+        sg.sgiga_qp_coords(P.handle, xd)
+        assert np.abs(xd.cpu().numpy() - xq).max() == 0.0
