@@ -17,6 +17,9 @@ Modules
   fd           fast-diagonalisation preconditioner written from its
                definition (not in the paper; the CUDA preconditioner's
                definition, cross-checked against the direct solve)
+  adaptive     hierarchical surpluses, their profits, the coefficients of an
+               arbitrary index set and the Dantzig (knapsack) choice of it
+               (Sec. 4.2, optimal sets)
   multipatch   the L-shaped domain: three glued bilinear patches, Dirichlet
                lifting by edge L2 projection, L2/H1 errors (not in the
                paper's experiments; its graded-mesh topic, Sec. 4.4)
