@@ -135,6 +135,11 @@ typedef struct {
     int ncomponents;  /* > 0: the plan holds only these components of the index
                          set (e.g. one, to solve the grids one at a time); 0: all */
     const int* components; /* [ncomponents][d] levels (host), each in the index set of w */
+    const double* coefficients; /* with ncomponents > 0: the combination coefficient of each
+                         listed component (host); the components then form an arbitrary
+                         index set (levels >= min_level, w ignored), e.g. one chosen by the
+                         profits of the hierarchical surpluses (Sec. 4.2, the knapsack view
+                         of the sparse-grid set). NULL: coefficients of eq. TD-combi-tec */
 } sgiga_config;
 
 typedef struct {

@@ -484,7 +484,21 @@ static int build(sgiga_plan_s* P) {
         for (int k = 0; k < d; ++k) if (a[k] != b[k]) return a[k] < b[k];
         return false;
     });
-    if (c.ncomponents > 0) {   // keep only the listed components (in index-set order)
+    std::map<std::array<int, 3>, double> given_coef;
+    if (c.ncomponents > 0 && c.coefficients) {   // an arbitrary index set with given coefficients
+        if (!c.components) return fail(SGIGA_ERR_ARG, "components is NULL");
+        idx.clear();
+        for (int i = 0; i < c.ncomponents; ++i) {
+            std::array<int, 3> lv3 = {0, 0, 0};
+            for (int k = 0; k < d; ++k) {
+                lv3[k] = c.components[i * d + k];
+                if (lv3[k] < mn || lv3[k] > 20) return fail(SGIGA_ERR_ARG, "component level outside [min_level, 20]");
+            }
+            if (given_coef.count(lv3)) return fail(SGIGA_ERR_ARG, "a component is listed twice");
+            given_coef[lv3] = c.coefficients[i];
+            idx.push_back(lv3);
+        }
+    } else if (c.ncomponents > 0) {   // keep only the listed components (in index-set order)
         if (!c.components) return fail(SGIGA_ERR_ARG, "components is NULL");
         std::vector<std::array<int, 3>> keep;
         for (int i = 0; i < c.ncomponents; ++i) {
@@ -543,7 +557,7 @@ static int build(sgiga_plan_s* P) {
         int s = 0;
         for (int k = 0; k < d; ++k) s += idx[gi][k];
         const int t = w + d - 1 - s;
-        cd.coeff = (double)((t % 2) ? -1 : 1) * (double)binom(d - 1, t);
+        cd.coeff = given_coef.empty() ? (double)((t % 2) ? -1 : 1) * (double)binom(d - 1, t) : given_coef[idx[gi]];
         for (int q = 0; q < npatch; ++q) {
             GridDesc g{};
             g.comp = (int)gi;

@@ -44,7 +44,7 @@ class sgiga_config(ctypes.Structure):
                 ("min_level", ctypes.c_int), ("domain", ctypes.c_int), ("grading", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
                 ("patch", ctypes.POINTER(sgiga_patch)), ("ncomponents", ctypes.c_int),
-                ("components", ctypes.POINTER(ctypes.c_int))]
+                ("components", ctypes.POINTER(ctypes.c_int)), ("coefficients", ctypes.POINTER(ctypes.c_double))]
 
 
 class sgiga_info(ctypes.Structure):
@@ -175,9 +175,10 @@ def _ptr(buf, n=None, dtype=np.float64):
 # --- entry points (same names as the C ABI) ------------------------------------
 
 def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="uniform", gamma=1.0,
-               precision="fp64", precond="fd", stream=None, patch=None, components=None):
+               precision="fp64", precond="fd", stream=None, patch=None, components=None, coefficients=None):
     """patch: (degrees [d], knots [d arrays], control points [n, d]) for domain "patch";
-    components: levels of the components to keep (default: the whole index set)."""
+    components: levels of the components to keep (default: the whole index set);
+    coefficients: with components, their combination coefficients (an arbitrary index set)."""
     keep = []
     pp = None
     if patch is not None:
@@ -202,6 +203,12 @@ def sgiga_plan(d, p, w, domain="unit", continuity=-1, min_level=1, grading="unif
         keep.append(comp)
         cfg.ncomponents = len(comp)
         cfg.components = comp.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if coefficients is not None:
+            cf = np.ascontiguousarray(np.asarray(coefficients, dtype=np.float64).reshape(-1))
+            if len(cf) != len(comp):
+                raise ValueError("one coefficient per component")
+            keep.append(cf)
+            cfg.coefficients = cf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     h = _P()
     s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.sgiga_plan(ctypes.byref(cfg), s, ctypes.byref(h)))

@@ -60,3 +60,30 @@ def test_map_points_against_the_oracle_geometry(rr):
         sgiga.sgiga_map_points(P.handle, xi, None, 50, x, det)
     assert np.abs(x.reshape(-1, 2) - g.map(xi)).max() < 1e-14
     assert np.abs(det - np.linalg.det(g.jacobian(xi))).max() < 1e-13
+
+
+def test_arbitrary_index_set_plan_matches_the_oracle(rr):
+    """A plan over an arbitrary admissible index set with the coefficients of
+    its surpluses combines like the oracle."""
+    from paper_1707_09598_gb300 import sgiga
+    from oracle import adaptive, geometry, problems
+    from oracle.galerkin import Component
+    from paper_1707_09598_gb300.inputs import random_points
+    I = [(1, 1), (2, 1), (1, 2), (3, 1), (2, 2), (1, 3), (4, 1), (3, 2), (5, 1)]
+    coef = adaptive.coefficients(I)
+    comps = sorted(coef)
+    xi = np.ascontiguousarray(random_points(64, 2, seed=82))
+    with sgiga.Plan(2, 2, 2, domain="annulus", components=comps, coefficients=[coef[c] for c in comps]) as P:
+        assert P.info.ngrids == len(comps)
+        sgiga.sgiga_set_rhs_builtin(P.handle, "annulus_paper")
+        sgiga.sgiga_solve(P.handle, 1e-13, 200)
+        uc = np.zeros(len(comps) * 64)
+        sgiga.sgiga_eval(P.handle, xi, 64, uc)
+        u = np.zeros(64)
+        sgiga.sgiga_combine(P.handle, uc, 64, u)
+    geom = geometry.make("annulus", 2)
+    ref = 0.0
+    for c in comps:
+        comp = Component(geom, c, 2).assemble(f=problems.get("annulus_paper2").f)
+        ref = ref + coef[c] * comp.evaluate(comp.solve(), xi)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-10
