@@ -14,6 +14,7 @@ with the coefficients of its surpluses, is solved, and its L2 error against
 the exact u is compared with the standard set's. Prints one JSON line.
 
   python -m paper_1707_09598_gb300.adaptive_report [--J 8] [--p 2] [--r 1]
+"""
 import argparse
 import itertools
 import json
