@@ -27,7 +27,9 @@
  *   - device pointers unless the parameter says "host or device"; such
  *     pointers are detected with cudaPointerGetAttributes and staged;
  *   - work is ordered on the plan's stream; a call returns once its status is
- *     known (calls that read results back synchronise the stream);
+ *     known (calls that read results back synchronise the stream); a device
+ *     buffer written on another stream must be complete, or that stream
+ *     ordered before the plan's (an event), when the call is made;
  *   - the caller owns every buffer it passes; the plan owns the device memory
  *     it allocates and frees it in sgiga_destroy.
  */
@@ -328,13 +330,14 @@ int sgiga_set_solution(sgiga_plan_t plan, const double* u);
  * point F(xi) in every component because all share the exact geometry. */
 int sgiga_eval(sgiga_plan_t plan, const double* xi, long long npts, double* u_comp);
 
-/* Values and physical gradients of every component (2D plans, any domain;
- * the one evaluation of multi-patch plans). xi [npts][2] parametric points,
- * patch [npts] the patch of each point (NULL: patch 0), u_comp
- * [ngrids][npts], grad_comp [2][ngrids][npts] (x then y derivative; NULL to
+/* Values and physical gradients of every component (2D and 3D plans, any
+ * domain; the one evaluation of multi-patch plans). xi [npts][d] parametric
+ * points, patch [npts] the patch of each point (NULL: patch 0), u_comp
+ * [ngrids][npts], grad_comp [d][ngrids][npts] (x, y [, z] derivative; NULL to
  * skip), all host or device. grad u = J^{-T} grad_xi u with J the patch's
- * Jacobian. Values include the Dirichlet lifting where boundary data is set.
- * SGIGA_ERR_ARG for d = 3 or a patch id out of range. */
+ * Jacobian (eq. F-B-splines). Values include the Dirichlet lifting where
+ * boundary data is set. SGIGA_ERR_ARG for a point outside [0,1]^d or a patch
+ * id out of range. */
 int sgiga_eval_grad(sgiga_plan_t plan, const double* xi, const int* patch, long long npts, double* u_comp,
                     double* grad_comp);
 

@@ -50,6 +50,9 @@ def main():
     a = ap.parse_args()
     src = "annulus_paper" if a.source == "paper" else "one"
     stream = torch.cuda.Stream()
+    # torch's fills and reads of the buffers handed to the plan run on the
+    # plan's stream, in order with its calls
+    torch.cuda.set_stream(stream)
     xi, wt = rates_report.rule(a.nel, a.p + 2)
     npts = len(xi)
     xi_d = torch.as_tensor(xi, device="cuda")

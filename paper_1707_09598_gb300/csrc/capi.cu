@@ -1062,12 +1062,11 @@ int sgiga_set_dirichlet(sgiga_plan_t P, const double* g) {
 int sgiga_eval_grad(sgiga_plan_t P, const double* xi, const int* patch, long long npts, double* ucomp,
                     double* gcomp) {
     if (!P || (!xi && npts > 0) || (!ucomp && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
-    if (P->d != 2) return fail(SGIGA_ERR_ARG, "gradient evaluation is 2D only");
     if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
     if (npts == 0) return SGIGA_OK;
     const size_t ng = P->comps.size();
-    const size_t xb = (size_t)npts * 2 * 8, pb = patch ? (size_t)npts * 4 : 0;
-    const size_t ub = (size_t)npts * ng * 8, gb = gcomp ? 2 * ub : 0;
+    const size_t xb = (size_t)npts * P->d * 8, pb = patch ? (size_t)npts * 4 : 0;
+    const size_t ub = (size_t)npts * ng * 8, gb = gcomp ? (size_t)P->d * ub : 0;
     const bool xdev = is_device(xi), pdev = !patch || is_device(patch), udev = is_device(ucomp);
     const bool gdev = !gcomp || is_device(gcomp);
     int rc = ensure_stage(P, (xdev ? 0 : xb) + (pdev ? 0 : (pb + 15) / 16 * 16) + (udev ? 0 : ub) + (gdev ? 0 : gb));

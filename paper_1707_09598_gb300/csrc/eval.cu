@@ -133,12 +133,15 @@ cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts
 
 namespace sgiga {
 
-// Values and physical gradients of every component at (patch, xi) points, 2D.
+// Values and physical gradients of every component at (patch, xi) points.
 // Block (x: points, y: component). The point's patch selects the component's
 // piece; a coefficient is the packed solution for a kept function, the
-// boundary array (Dirichlet lifting) otherwise.
-//   u = sum_ab R_a(xi_0) R_b(xi_1) c_ab,  grad_xi u = (sum R'_a R_b c, sum R_a R'_b c),
+// boundary array (Dirichlet lifting) otherwise. 3D plans are single-patch:
+// every kept function is interior and there is no lifting.
+//   u = sum_abc R_a(xi_0) R_b(xi_1) R_c(xi_2) c_abc,
+//   d u / d xi_k = the same sum with R' in direction k,
 //   grad_x u = J^{-T} grad_xi u,  R = B / W_k (eq. u-IGA-approx).
+template <int D>
 __global__ void k_eval_grad(DevPlan P, const double* __restrict__ coeffs, const double* __restrict__ xi,
                             const int* __restrict__ patch, long long npts, double* __restrict__ ucomp,
                             double* __restrict__ gcomp, int lifting) {
@@ -153,10 +156,11 @@ __global__ void k_eval_grad(DevPlan P, const double* __restrict__ coeffs, const 
     }
     const GridDesc& g = P.grids[cd.piece0 + pa];
     const int p = P.p;
-    double x[3] = {xi[2 * j], xi[2 * j + 1], 0.0};
-    double N[2][SGIGA_MAXP + 1], dN[2][SGIGA_MAXP + 1];
-    int f0[2];
-    for (int k = 0; k < 2; ++k) {
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < D; ++k) x[k] = xi[D * j + k];
+    double N[D][SGIGA_MAXP + 1], dN[D][SGIGA_MAXP + 1];
+    int f0[D];
+    for (int k = 0; k < D; ++k) {
         if (!(x[k] >= 0.0 && x[k] <= 1.0)) {
             atomicOr(&P.flags[1], 1);
             x[k] = x[k] < 0.0 ? 0.0 : 1.0;
@@ -174,33 +178,74 @@ __global__ void k_eval_grad(DevPlan P, const double* __restrict__ coeffs, const 
         }
         f0[k] = s - p;
     }
-    const double* gf = (lifting && g.gf_off >= 0) ? P.gfull + g.gf_off : nullptr;
-    double u = 0.0, u0 = 0.0, u1 = 0.0;
-    for (int b = 0; b <= p; ++b) {
-        const int i1 = f0[1] + b;
-        double v = 0.0, dv = 0.0;
-        for (int a = 0; a <= p; ++a) {
-            const int i0 = f0[0] + a;
-            double cv;
-            if (piece_kept2(g, i0, i1)) cv = coeffs[piece_addr2(P.grids, g, i0, i1)];
-            else cv = gf ? gf[i0 + (long long)i1 * g.nf[0]] : 0.0;
-            v += N[0][a] * cv;
-            dv += dN[0][a] * cv;
+    double u = 0.0, gxi[3] = {0.0, 0.0, 0.0};
+    if (D == 2) {
+        const double* gf = (lifting && g.gf_off >= 0) ? P.gfull + g.gf_off : nullptr;
+        for (int b = 0; b <= p; ++b) {
+            const int i1 = f0[1] + b;
+            double v = 0.0, dv = 0.0;
+            for (int a = 0; a <= p; ++a) {
+                const int i0 = f0[0] + a;
+                double cv;
+                if (piece_kept2(g, i0, i1)) cv = coeffs[piece_addr2(P.grids, g, i0, i1)];
+                else cv = gf ? gf[i0 + (long long)i1 * g.nf[0]] : 0.0;
+                v += N[0][a] * cv;
+                dv += dN[0][a] * cv;
+            }
+            u += N[1][b] * v;
+            gxi[0] += N[1][b] * dv;
+            gxi[1] += dN[1][b] * v;
         }
-        u += N[1][b] * v;
-        u0 += N[1][b] * dv;
-        u1 += dN[1][b] * v;
+    } else {
+        const long long st1 = g.n[0], st2 = (long long)g.n[0] * g.n[1];
+        const double* cg = coeffs + g.dof_off;
+        for (int cc = 0; cc <= p; ++cc) {
+            const int i2 = f0[D - 1] + cc;
+            if (i2 < 1 || i2 > g.nf[D - 1] - 2) continue;
+            double w = 0.0, w0 = 0.0, w1 = 0.0;
+            for (int b = 0; b <= p; ++b) {
+                const int i1 = f0[1] + b;
+                if (i1 < 1 || i1 > g.nf[1] - 2) continue;
+                double v = 0.0, dv = 0.0;
+                for (int a = 0; a <= p; ++a) {
+                    const int i0 = f0[0] + a;
+                    if (i0 < 1 || i0 > g.nf[0] - 2) continue;
+                    const double cv = cg[(i0 - 1) + (i1 - 1) * st1 + (i2 - 1) * st2];
+                    v += N[0][a] * cv;
+                    dv += dN[0][a] * cv;
+                }
+                w += N[1][b] * v;
+                w0 += N[1][b] * dv;
+                w1 += dN[1][b] * v;
+            }
+            u += N[D - 1][cc] * w;
+            gxi[0] += N[D - 1][cc] * w0;
+            gxi[1] += N[D - 1][cc] * w1;
+            gxi[2] += dN[D - 1][cc] * w;
+        }
     }
     ucomp[(long long)c * npts + j] = u;
     if (gcomp) {
         double X[3], J[3][3];
         patch_eval(P.patch[g.patch], x, X, J);
-        // J^T grad_x = grad_xi
-        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        const double gx = (J[1][1] * u0 - J[1][0] * u1) / det;
-        const double gy = (-J[0][1] * u0 + J[0][0] * u1) / det;
-        gcomp[(long long)c * npts + j] = gx;
-        gcomp[((long long)P.ncomps + c) * npts + j] = gy;
+        // J^T grad_x = grad_xi, J[i][k] = d x_i / d xi_k
+        if (D == 2) {
+            const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            gcomp[(long long)c * npts + j] = (J[1][1] * gxi[0] - J[1][0] * gxi[1]) / det;
+            gcomp[((long long)P.ncomps + c) * npts + j] = (-J[0][1] * gxi[0] + J[0][0] * gxi[1]) / det;
+        } else {
+            // grad_x = adj(J)^T grad_xi / det J, with adj(J)^T = the cofactor matrix of J
+            double C[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) {
+                    const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                    C[r][k] = J[r1][k1] * J[r2][k2] - J[r1][k2] * J[r2][k1];
+                }
+            const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+            for (int r = 0; r < 3; ++r)
+                gcomp[((long long)r * P.ncomps + c) * npts + j] =
+                    (C[r][0] * gxi[0] + C[r][1] * gxi[1] + C[r][2] * gxi[2]) / det;
+        }
     }
 }
 
@@ -209,7 +254,8 @@ cudaError_t launch_eval_grad(const DevPlan& P, const double* coeffs, const doubl
     if (npts <= 0) return cudaSuccess;
     dim3 grid((unsigned)((npts + 127) / 128), P.ncomps);
     SGIGA_COUNT_LAUNCH();
-    k_eval_grad<<<grid, 128, 0, s>>>(P, coeffs, xi, patch, npts, ucomp, gcomp, lifting);
+    if (P.d == 3) k_eval_grad<3><<<grid, 128, 0, s>>>(P, coeffs, xi, patch, npts, ucomp, gcomp, lifting);
+    else k_eval_grad<2><<<grid, 128, 0, s>>>(P, coeffs, xi, patch, npts, ucomp, gcomp, lifting);
     return cudaGetLastError();
 }
 

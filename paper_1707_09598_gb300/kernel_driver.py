@@ -34,6 +34,9 @@ def main():
     ap.add_argument("--tune", action="store_true", help="run the autotuner first")
     a = ap.parse_args()
     stream = torch.cuda.Stream()
+    # torch's fills and reads of the buffers handed to the plan run on the
+    # plan's stream, in order with its calls
+    torch.cuda.set_stream(stream)
     f32 = a.op.endswith("_f32")
     kw = {}
     if a.domain == "perturbed":   # the learned-preconditioner geometry: seeded cubic perturbation, general metric

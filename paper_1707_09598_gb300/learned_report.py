@@ -46,8 +46,11 @@ def main():
     a = ap.parse_args()
     kn, cp = perturbed_cube_patch(1)
     om, ph, amp = lognormal_features(2, nfeat=a.nfeat)
-    pts = torch.as_tensor(eval_points(3, 16), device="cuda")
     stream = torch.cuda.Stream()
+    # torch's fills and reads of the buffers handed to the plan run on the
+    # plan's stream, in order with its calls
+    torch.cuda.set_stream(stream)
+    pts = torch.as_tensor(eval_points(3, 16), device="cuda")
     out = {"workload": "perturbed cube (amp 0.1, seed 1), log-normal a (std 0.5, ell 0.2, %d features, seed 2), "
                        "f = 1, p = 3, w = %d" % (a.nfeat, a.w)}
 

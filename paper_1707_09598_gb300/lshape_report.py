@@ -72,9 +72,12 @@ def main():
     x = xi * SIGNS[patch]
     ue, ge = exact(x)
     npts = len(xi)
+    stream = torch.cuda.Stream()
+    # torch's fills and reads of the buffers handed to the plan run on the
+    # plan's stream, in order with its calls
+    torch.cuda.set_stream(stream)
     xi_d = torch.as_tensor(xi, device="cuda")
     patch_d = torch.as_tensor(patch, device="cuda")
-    stream = torch.cuda.Stream()
     out = {"workload": "L-shape, 3 glued bilinear patches, u = r^(2/3) sin(2 theta/3) Dirichlet data, f = 0, p = 2 C^1, "
                        "one-sided grading toward the corner, %s PCG to %g (gamma = 3: %g)" % (a.precision, a.tol, a.tol_gamma3),
            "error_rule": "4x4 Gauss points on a uniform 64x64 mesh per patch", "results": {}}

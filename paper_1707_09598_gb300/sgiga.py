@@ -323,11 +323,11 @@ def sgiga_eval(plan, xi, npts, u_comp):
 
 
 def sgiga_eval_grad(plan, xi, patch, npts, u_comp, grad_comp=None):
-    """Values [ngrids][npts] and physical gradients [2][ngrids][npts] (2D)."""
+    """Values [ngrids][npts] and physical gradients [d][ngrids][npts]."""
     info = sgiga_plan_info(plan)
-    _check(_lib.sgiga_eval_grad(plan, _ptr(xi, npts * 2), _ptr(patch, npts, dtype=np.int32), int(npts),
+    _check(_lib.sgiga_eval_grad(plan, _ptr(xi, npts * info.d), _ptr(patch, npts, dtype=np.int32), int(npts),
                                 _ptr(u_comp, npts * info.ngrids),
-                                _ptr(grad_comp, 2 * npts * info.ngrids) if grad_comp is not None else None))
+                                _ptr(grad_comp, info.d * npts * info.ngrids) if grad_comp is not None else None))
 
 
 def sgiga_functional(plan, q_qp):
