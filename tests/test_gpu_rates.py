@@ -144,3 +144,65 @@ def test_rates_3d_match_table2(rr, rp):
     h1 = rr.rate(ws, [x["h1"] for x in rows])
     assert abs(l2 - (p + 1)) < 0.25 and abs(h1 - p) < 0.25, (l2, h1)
     assert abs(l2 - l2_ref) < 0.5 and abs(h1 - h1_ref) < 0.5, (l2, h1)
+
+
+def test_errors_against_a_reference_match_the_oracle(rr):
+    """f = 1 on a radical mesh (gamma = 2): the errors of the combined solution
+    against the full tensor solution of level 5, through the C ABI, against
+    the same measurement from the oracle's components (graded rule, weights
+    times |det J|)."""
+    from oracle import geometry, problems
+    from oracle.galerkin import Component
+    stream = torch.cuda.Stream()
+    rows = rr.run_case(2, 1, [3], 8, stream, d=2, source="one", grading="radical", gamma=2.0, ref_level=5)
+    xi, wt = rr.rule(8, 4, 2, "radical", 2.0)
+    geom = geometry.make("annulus", 2)
+    prob = problems.get("one2")
+    J = geom.jacobian(xi)
+    w = wt * np.abs(np.linalg.det(J))
+    JT = np.transpose(J, (0, 2, 1))
+
+    def fields(results):
+        u = sum(c * comp.evaluate(x, xi) for _, c, comp, x in results)
+        g = sum(c * comp.evaluate_grad(x, xi) for _, c, comp, x in results)
+        return u, np.linalg.solve(JT, g[..., None])[..., 0]
+
+    sg = driver.solve_components("annulus", 2, 2, 3, "one2", r=1, kind="radical", gamma=2.0)
+    ref = Component(geom, (5, 5), 2, 1, "radical", 2.0).assemble(f=prob.f)
+    u0, g0 = fields(sg)
+    u1, g1 = fields([((5, 5), 1.0, ref, ref.solve())])
+    l2 = np.sqrt(np.sum(w * (u0 - u1) ** 2))
+    h1 = np.sqrt(np.sum(w * np.sum((g0 - g1) ** 2, 1)))
+    assert abs(rows[0]["l2"] - l2) / l2 < 1e-6, (rows[0], l2)
+    assert abs(rows[0]["h1"] - h1) / h1 < 1e-6, (rows[0], h1)
+    assert rows[0]["reference"]["converged"]
+
+
+@pytest.mark.parametrize("rp", [(2, 1), (3, 2)])
+def test_lowreg_rates_table3(rr, rp):
+    """f = 1 (Table 3, d = 2), w = 3..7 against the full tensor solution of
+    level 9: the rates sit on the theoretical lower bounds (H1: 1, L2: 1.5;
+    Table 3's parentheses) within 0.15, and within 0.35 of the printed SG-IGA
+    rates, which are above the bounds."""
+    p, r = rp
+    ws = list(range(3, 8))
+    rows = rr.run_case(p, r, ws, 32, torch.cuda.Stream(), source="one", ref_level=9)
+    h1_ref, l2_ref = rr.TABLE3_D[2][(r, p)]
+    l2 = rr.rate(ws, [x["l2"] for x in rows])
+    h1 = rr.rate(ws, [x["h1"] for x in rows])
+    assert abs(l2 - 1.5) < 0.15 and abs(h1 - 1.0) < 0.15, (l2, h1)
+    assert abs(l2 - l2_ref) < 0.35 and abs(h1 - h1_ref) < 0.35, (l2, h1)
+
+
+def test_radical_mesh_raises_the_rates(rr):
+    """Sec. 4.4: radical meshes raise the rates of the f = 1 problem. p = 2 C^0,
+    w = 3..7, reference level 9 on the same mesh family: gamma = 2 lifts the
+    H1 rate from the uniform mesh's ~1 to within 0.25 of the optimal p = 2."""
+    ws = list(range(3, 8))
+    out = {}
+    for gamma in (1.0, 2.0):
+        rows = rr.run_case(2, 0, ws, 32, torch.cuda.Stream(), source="one", grading="radical", gamma=gamma,
+                           ref_level=9)
+        out[gamma] = (rr.rate(ws, [x["l2"] for x in rows]), rr.rate(ws, [x["h1"] for x in rows]))
+    assert out[2.0][1] - out[1.0][1] > 0.6 and out[2.0][0] - out[1.0][0] > 0.6, out
+    assert abs(out[2.0][1] - 2.0) < 0.25, out
