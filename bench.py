@@ -37,8 +37,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
 # components solved by the CPU oracle in its bounded sample (assembly + direct solve + evaluation)
 ORACLE_SAMPLE = [(4, 4, 4), (10, 1, 1), (3, 5, 4), (2, 2, 7)]
 # DRAM bytes (read + write) of one launch of the diagonal-metric FP64 apply on
-# this workload, from one ncu capture; see profiles/k_op3_fp64_apply_cube_p3_w10.md
-APPLY_DRAM_BYTES = 555.391488e6 + 9.998592e6
+# this workload at the autotuned tiles (mean of three launches of one ncu
+# capture); see profiles/k_op3_fp64_apply_cube_p3_w10.md
+APPLY_DRAM_BYTES = 555.403520e6 + 4.524971e6
 
 
 def parse():
