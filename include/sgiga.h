@@ -202,7 +202,10 @@ int sgiga_qp_coords(sgiga_plan_t plan, double* xq);
 /* Load vector b_i = sum_q w_q |det J_q| f(x_q) R_i(xi_q) (Sec. 2.2, Galerkin
  * right-hand side) from f at the quadrature points: f_qp is [nqp] in natural
  * order, host or device. With a device buffer the call is stream-ordered and
- * returns without synchronising; a host buffer is copied before it returns. */
+ * returns without synchronising. A host buffer has been read in full when the
+ * call returns: page-locked host memory (cudaHostAlloc, cudaHostRegister) is
+ * read in place by the kernel over the host link, pageable memory through a
+ * staging copy. */
 int sgiga_set_rhs(sgiga_plan_t plan, const double* f_qp);
 
 /* Same, with f from a built-in manufactured solution (SGIGA_SRC_*),

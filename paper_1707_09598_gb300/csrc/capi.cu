@@ -997,16 +997,22 @@ int sgiga_qp_coords(sgiga_plan_t P, double* xq) {
 int sgiga_set_rhs(sgiga_plan_t P, const double* f) {
     if (!P || !f) return fail(SGIGA_ERR_ARG, "null argument");
     const double* fd = f;
-    if (!is_device(f)) {
-        int rc = ensure_stage(P, (size_t)P->nqp * 8);
-        if (rc) return rc;
-        CUDA_TRY(cudaMemcpyAsync(P->stage, f, (size_t)P->nqp * 8, cudaMemcpyHostToDevice, P->stream));
-        fd = (const double*)P->stage;
+    const bool host = !is_device(f);
+    if (host) {
+        // page-locked: the density kernel reads f over the host link, once per
+        // value, in place of a staging copy; pageable: staged
+        fd = (const double*)mapped_host_alias(f);
+        if (!fd) {
+            int rc = ensure_stage(P, (size_t)P->nqp * 8);
+            if (rc) return rc;
+            CUDA_TRY(cudaMemcpyAsync(P->stage, f, (size_t)P->nqp * 8, cudaMemcpyHostToDevice, P->stream));
+            fd = (const double*)P->stage;
+        }
     }
     CUDA_TRY(launch_rhs_density_user(P->dp, fd, P->stream));
     int rc = run_rhs_operator(P);
     if (rc) return rc;
-    if (fd != f) CUDA_TRY(cudaStreamSynchronize(P->stream));   // host buffer may be reused on return
+    if (host) CUDA_TRY(cudaStreamSynchronize(P->stream));   // host buffer may be reused on return
     return SGIGA_OK;
 }
 

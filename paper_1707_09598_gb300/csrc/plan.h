@@ -149,6 +149,18 @@ inline bool is_device(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The address at which the current device reads a page-locked host buffer
+// (cudaHostAlloc, or cudaHostRegister with mapping: the CUDA runtime reports
+// it as devicePointer), or null for any other pointer.
+inline const void* mapped_host_alias(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 inline int ensure_stage(sgiga_plan_s* P, size_t bytes) {
     if (P->stage_bytes >= bytes) return SGIGA_OK;
     if (P->stage) cudaFree(P->stage);

@@ -373,6 +373,28 @@ def test_host_buffers_and_user_rhs(sg):
         assert _rel(b1, b2) < 1e-13
 
 
+def test_pinned_host_rhs_is_read_in_place(sg):
+    """f in page-locked host memory (read by the density kernel over the host
+    link), in pageable host memory (staged) and on the device give the same
+    load vector, bit for bit; the pinned buffer may be reused on return."""
+    case = CASES[3]
+    with _plan(sg, case) as P:
+        fd = torch.zeros(P.info.nqp, dtype=torch.float64, device="cuda")
+        sg.sgiga_source_at_qp(P.handle, "annulus_paper", fd)
+        fd = fd * 1.5 + 0.25
+        fpin = fd.cpu().pin_memory()
+        fpage = fd.cpu().numpy().copy()
+        out = []
+        for f in (fd, fpin, fpage):
+            sg.sgiga_set_rhs(P.handle, f)
+            b = np.zeros(P.info.ndof)
+            sg.sgiga_get_rhs(P.handle, b)
+            out.append(b)
+        fpin.zero_()                      # read in full before the call returned
+        assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+        assert np.abs(out[0]).max() > 0
+
+
 def test_errors_are_reported_not_crashes(sg):
     with pytest.raises(sg.SgigaError):
         sg.sgiga_plan(4, 2, 6)
