@@ -168,3 +168,22 @@ def test_fd_eig_properties():
     np.testing.assert_allclose(U.T @ M @ U, np.eye(len(lam)), atol=1e-10)
     np.testing.assert_allclose(K @ U, M @ U * lam[None, :], atol=1e-8 * lam.max())
     assert np.all(lam > 0)
+
+
+@pytest.mark.parametrize("domain,levels,p", [("annulus", (2, 3, 1), 2), ("unit", (1, 2, 3), 3)])
+def test_parametric_gradient_3d_matches_central_differences(domain, levels, p):
+    """evaluate_grad in 3D (rational directions included) against central
+    differences of evaluate, for random coefficients at interior points."""
+    from oracle import geometry
+    from oracle.galerkin import Component
+    comp = Component(geometry.make(domain, 3), levels, p)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(comp.ndof)
+    pts = rng.uniform(0.05, 0.95, size=(20, 3))
+    g = comp.evaluate_grad(u, pts)
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (comp.evaluate(u, pts + e) - comp.evaluate(u, pts - e)) / (2 * h)
+        assert np.abs(g[:, k] - fd).max() < 1e-6 * max(1.0, np.abs(g[:, k]).max()), k
