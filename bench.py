@@ -171,6 +171,69 @@ class Clocks:
                 "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, ctypes) every `period` seconds in a background thread,
+    between start() and stop(): dense enough for a timed region of tens of
+    milliseconds. Read-only; the device is matched by PCI bus id."""
+
+    # nvmlClocksEventReasons bits (nvml.h)
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, torch, local, period=0.005):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(local)
+        bus = None
+        if all(hasattr(props, k) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id")):
+            bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        if bus is None or self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(local, ctypes.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.period = period
+        self.sm, self.bits, self.stop_flag, self.thread = [], 0, False, None
+
+    def _run(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag:
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0:   # NVML_CLOCK_SM
+                self.sm.append(float(mhz.value))
+            if self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.bits |= rs.value
+            time.sleep(self.period)
+
+    def start(self):
+        import threading
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        self.thread.join(timeout=2)
+        mx = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(mx))
+        if not self.sm:
+            return None
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": float(mx.value),
+                "reasons": sorted(n for b, n in self.BITS.items() if self.bits & b), "samples": len(self.sm),
+                "source": "NVML, %g ms period, timed region only" % (self.period * 1e3)}
+
+
+def clock_sampler(torch, local):
+    """NVML sampler where the driver library loads, else nvidia-smi at 200 ms."""
+    try:
+        return NvmlClocks(torch, local)
+    except Exception:
+        return Clocks(local)
+
+
 def apply_flops(plan):
     """Algorithmic FP64 flops of one operator apply: untiled sum factorisation
     (forward: 2(p+1) + 3(p+1) + 3(p+1) FMA per output of the three stages,
@@ -381,7 +444,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = Clocks(local)
+    clocks = clock_sampler(torch, local)
     clocks.start()
     l0 = sgiga.sgiga_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

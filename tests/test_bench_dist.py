@@ -72,3 +72,52 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch):
     monkeypatch.setattr(bench, "run_oracle_sample", boom)
     args = type("Args", (), {"warmup": 3, "steps": 2, "gpus": 2})()
     assert bench.run_reference(args) == 0
+
+
+def test_clock_sampler_reads_nvml_state_and_falls_back(monkeypatch):
+    """The NVML sampler reports the median SM clock and the union of the
+    throttle reasons seen while it ran (a fake driver library here); without
+    NVML the sampler is the nvidia-smi one."""
+    import ctypes
+    import types
+    import bench
+
+    class FakeLib:
+        def __init__(self):
+            self.clocks = iter([1900, 2070, 2070, 2070, 1950] + [2070] * 1000)
+
+        def nvmlInit_v2(self):
+            return 0
+
+        def nvmlDeviceGetHandleByPciBusId_v2(self, bus, h):
+            return 0
+
+        def nvmlDeviceGetHandleByIndex_v2(self, i, h):
+            return 0
+
+        def nvmlDeviceGetClockInfo(self, h, kind, out):
+            out._obj.value = next(self.clocks)
+            return 0
+
+        def nvmlDeviceGetMaxClockInfo(self, h, kind, out):
+            out._obj.value = 2070
+            return 0
+
+        def nvmlDeviceGetCurrentClocksEventReasons(self, h, out):
+            out._obj.value = 0x1 | 0x4          # idle + sw_power_cap
+            return 0
+
+    fake = FakeLib()
+    monkeypatch.setattr(ctypes, "CDLL", lambda name: fake)
+    props = types.SimpleNamespace(pci_domain_id=0, pci_bus_id=0x1b, pci_device_id=0)
+    torch_stub = types.SimpleNamespace(cuda=types.SimpleNamespace(get_device_properties=lambda i: props))
+    ck = bench.NvmlClocks(torch_stub, 0, period=0.001)
+    ck.start()
+    import time
+    time.sleep(0.05)
+    out = ck.stop()
+    assert out["samples"] >= 5 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["sm_mhz"] == 2070.0
+
+    monkeypatch.setattr(ctypes, "CDLL", lambda name: (_ for _ in ()).throw(OSError("no NVML")))
+    assert isinstance(bench.clock_sampler(torch_stub, 0), bench.Clocks)
