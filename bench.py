@@ -37,8 +37,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
 # components solved by the CPU oracle in its bounded sample (assembly + direct solve + evaluation)
 ORACLE_SAMPLE = [(4, 4, 4), (10, 1, 1), (3, 5, 4), (2, 2, 7)]
 # DRAM bytes (read + write) of one launch of the diagonal-metric FP64 apply on
-# this workload at the autotuned tiles (mean of three launches of one ncu
-# capture); see profiles/k_op3_fp64_apply_cube_p3_w10.md
+# this workload at the autotuned tiles (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of three launches of one ncu capture)
 APPLY_DRAM_BYTES = 555.403520e6 + 4.524971e6
 
 
@@ -53,6 +53,7 @@ def parse():
                          "profilers list the kernels of a device-side graph loop only this way)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision line of the same workload")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-parallel", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -61,29 +62,48 @@ def parse():
 # ----------------------------------------------------------------------------
 
 def oracle_sample_child(nrep):
-    from oracle import geometry, problems
-    from oracle.galerkin import Component
-    from paper_1707_09598_gb300.inputs import eval_points
-    pts = eval_points(3, WORKLOAD["lattice"])
-    prob = problems.get("sine3")
-    geom = geometry.UnitCube(3)
     dofs = 0
     t0 = time.perf_counter()
     for rep in range(nrep):
-        lv = ORACLE_SAMPLE[rep % len(ORACLE_SAMPLE)]
-        comp = Component(geom, lv, 3).assemble(f=prob.f)
-        u = comp.solve()
-        comp.evaluate(u, pts)
-        dofs += comp.ndof
+        dofs += oracle_task(ORACLE_SAMPLE[rep % len(ORACLE_SAMPLE)])
     dt = time.perf_counter() - t0
     print(json.dumps({"dofs": dofs, "seconds": dt, "components": nrep}))
 
 
-def run_oracle_sample(nrep):
+def oracle_task(lv):
+    """One component of the workload through the oracle: assembly, sparse
+    direct solve, evaluation on the lattice. Returns its DoFs."""
+    from oracle import geometry, problems
+    from oracle.galerkin import Component
+    from paper_1707_09598_gb300.inputs import eval_points
+    comp = Component(geometry.UnitCube(3), lv, 3).assemble(f=problems.get("sine3").f)
+    comp.evaluate(comp.solve(), eval_points(3, WORKLOAD["lattice"]))
+    return comp.ndof
+
+
+def oracle_parallel_child(per_core):
+    """The paper's parallelisation of the combination technique on the host:
+    a pool of one-thread workers (spawned) over every core, components in LPT
+    order (largest first), per_core tasks per core drawn from ORACLE_SAMPLE."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    tasks = [ORACLE_SAMPLE[i % len(ORACLE_SAMPLE)] for i in range(per_core * ncores)]
+    tasks.sort(key=lambda lv: -(2 ** sum(lv)))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(ncores) as pool:
+        pool.map(int, range(ncores))                    # workers up before timing
+        t0 = time.perf_counter()
+        dofs = sum(pool.imap_unordered(oracle_task, tasks, chunksize=1))
+        dt = time.perf_counter() - t0
+    print(json.dumps({"dofs": dofs, "seconds": dt, "components": len(tasks), "cores": ncores}))
+
+
+def run_oracle_sample(nrep, parallel=False):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(nrep)],
+    flag = "--oracle-parallel" if parallel else "--oracle-sample"
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), flag, str(nrep)],
                          env=env, capture_output=True, text=True, cwd=ROOT)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
@@ -534,13 +554,18 @@ def run_ours(args):
 
     mixed = None if args.no_mixed else run_mixed(args, sgiga, torch, f_dev, pts, npts, gold, ndof, world)
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0:
         r = run_oracle_sample(len(ORACLE_SAMPLE))
         cpu = {"value": r["dofs"] / r["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
                "sample": "%d components of the workload %s: assembly + sparse direct solve + evaluation "
                          "on 17^3 points, FP64, one BLAS thread, %.1f s" % (len(ORACLE_SAMPLE),
                                                                             ORACLE_SAMPLE, r["seconds"])}
+        rp = run_oracle_sample(2, parallel=True)
+        cpu_par = {"value": rp["dofs"] / rp["seconds"], "unit": "DoF/s", "cores": rp["cores"], "kind": "oracle",
+                   "sample": "%d components (the serial sample's, 2 per core) over a spawned pool of %d "
+                             "one-thread workers in LPT order (the paper's parallelisation), %.1f s"
+                             % (rp["components"], rp["cores"], rp["seconds"])}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -558,6 +583,7 @@ def run_ours(args):
             "roofline": roofline,
             "mixed_fp32_ir": mixed,
             "cpu_baseline": cpu,
+            "cpu_baseline_parallel": cpu_par,
             "e2e": {"value": whole_job_rate(ndof, world, e2e_s), "unit": "DoF/s",
                     "h2d_bytes_per_step": int(P.info.nqp * 8 + npts * W["d"] * 8),
                     "d2h_bytes_per_step": int(npts * 8)},
@@ -575,6 +601,9 @@ def main():
     args = parse()
     if args.oracle_sample:
         oracle_sample_child(args.oracle_sample)
+        return 0
+    if args.oracle_parallel:
+        oracle_parallel_child(args.oracle_parallel)
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -121,3 +121,17 @@ def test_clock_sampler_reads_nvml_state_and_falls_back(monkeypatch):
 
     monkeypatch.setattr(ctypes, "CDLL", lambda name: (_ for _ in ()).throw(OSError("no NVML")))
     assert isinstance(bench.clock_sampler(torch_stub, 0), bench.Clocks)
+
+
+def test_parallel_oracle_baseline_runs_the_sample_on_every_core():
+    """cpu_baseline_parallel: the oracle over a spawned pool of one-thread
+    workers, per_core tasks per core, in LPT order; it reports the cores used
+    and DoFs that match the serial sample's components."""
+    import bench
+    from oracle import geometry
+    from oracle.galerkin import Component
+    r = bench.run_oracle_sample(1, parallel=True)
+    ncores = os.cpu_count() or 1
+    assert r["cores"] == ncores and r["components"] == ncores and r["seconds"] > 0
+    per = [Component(geometry.UnitCube(3), lv, 3).ndof for lv in bench.ORACLE_SAMPLE]
+    assert r["dofs"] == sum(per[i % len(per)] for i in range(ncores))
