@@ -20,6 +20,10 @@ template <typename Real, int P, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 2)
 k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
+    // FP32 stiffness: the b-direction stages run as register-window pencils
+    // (fewer index divisions and shared loads per FMA; FP64 is FMA-bound and
+    // keeps the per-output form)
+    constexpr bool PB = sizeof(Real) == 4 && MODE == 0;
     extern __shared__ double sm_raw[];
     Real* sm = reinterpret_cast<Real*>(sm_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -96,27 +100,70 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         }
         __syncthreads();
         // stage 2: contract b
-        const int n2 = npen * La;
-        for (int idx = tid; idx < n2; idx += nth) {
-            const int r = dLa.div(idx), ja = idx - r * La, qc = dQTb.div(r), qb = r - qc * QTb;
-            int eb = qb / Q;
-            Real bt[P1], dt[P1];
-            load_row<Real, P1>(tb[1] + qb * P1, bt);
-            load_row<Real, P1>(tdv[1] + qb * P1, dt);
-            const Real* s1b = S1 + (qc * Lb + eb * M) * La + ja;
-            const Real* s1d = s1b + S1n;
-            Real s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        if constexpr (PB) {
+            // FP32: one thread per (ja, qc) pencil walks along b with a
+            // register window of the p+1 functions the current element touches
+            // (M new ones loaded per element), writing Q qp per element
+            for (int k = tid; k < La * QTc; k += nth) {
+                const int qc = dLa.div(k), ja = k - qc * La;
+                const Real* s1v = S1 + (long long)qc * Lb * La + ja;
+                const Real* s1d = s1v + S1n;
+                Real wv[P1], wd[P1];
 #pragma unroll
-            for (int t = 0; t < P1; ++t) {
-                Real vb = s1b[t * La], vd = s1d[t * La];
-                s0 += bt[t] * vb;
-                s1 += dt[t] * vb;
-                s2 += bt[t] * vd;
+                for (int t = 0; t < P1; ++t) { wv[t] = s1v[t * La]; wd[t] = s1d[t * La]; }
+                for (int eb = 0; eb < Tb; ++eb) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const int qb = eb * Q + q;
+                        Real bt[P1], dt[P1];
+                        load_row<Real, P1>(tb[1] + qb * P1, bt);
+                        load_row<Real, P1>(tdv[1] + qb * P1, dt);
+                        Real s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+                        for (int t = 0; t < P1; ++t) {
+                            s0 += bt[t] * wv[t];
+                            s1 += dt[t] * wv[t];
+                            s2 += bt[t] * wd[t];
+                        }
+                        const int o = (qb + QTb * qc) * LaP + ja;
+                        S2[o] = s0;
+                        S2[S2n + o] = s1;
+                        S2[2 * S2n + o] = s2;
+                    }
+                    if (eb + 1 < Tb) {
+                        for (int u = 0; u < M; ++u) {
+#pragma unroll
+                            for (int t = 0; t < P; ++t) { wv[t] = wv[t + 1]; wd[t] = wd[t + 1]; }
+                            const int jn = eb * M + P1 + u;   // <= (Tb - 1) * M + P = Lb - 1
+                            wv[P] = s1v[jn * La];
+                            wd[P] = s1d[jn * La];
+                        }
+                    }
+                }
             }
-            int pid = qb + QTb * qc;
-            S2[pid * LaP + ja] = s0;
-            S2[S2n + pid * LaP + ja] = s1;
-            S2[2 * S2n + pid * LaP + ja] = s2;
+        } else {
+            const int n2 = npen * La;
+            for (int idx = tid; idx < n2; idx += nth) {
+                const int r = dLa.div(idx), ja = idx - r * La, qc = dQTb.div(r), qb = r - qc * QTb;
+                int eb = qb / Q;
+                Real bt[P1], dt[P1];
+                load_row<Real, P1>(tb[1] + qb * P1, bt);
+                load_row<Real, P1>(tdv[1] + qb * P1, dt);
+                const Real* s1b = S1 + (qc * Lb + eb * M) * La + ja;
+                const Real* s1d = s1b + S1n;
+                Real s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    #pragma unroll
+                for (int t = 0; t < P1; ++t) {
+                    Real vb = s1b[t * La], vd = s1d[t * La];
+                    s0 += bt[t] * vb;
+                    s1 += dt[t] * vb;
+                    s2 += bt[t] * vd;
+                }
+                int pid = qb + QTb * qc;
+                S2[pid * LaP + ja] = s0;
+                S2[S2n + pid * LaP + ja] = s1;
+                S2[2 * S2n + pid * LaP + ja] = s2;
+            }
         }
         __syncthreads();
     }
@@ -222,27 +269,73 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     }
     __syncthreads();
     // backward b: S2 -> S1
-    for (int idx = tid; idx < S1n; idx += nth) {
-        const int r = dLa.div(idx), ja = idx - r * La, qc = dLb.div(r), jb = r - qc * Lb;
-        int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
-        Real rB = 0.0, rD = 0.0;
-        for (int eb = lo; eb <= hi; ++eb) {
-            const int t = jb - eb * M;
+    if constexpr (PB) {
+        // FP32: one thread per (ja, qc) pencil along b, accumulating the p+1
+        // functions of the current element in registers; the lowest M are
+        // complete after each element and are written out (as the a pencils)
+        for (int k = tid; k < La * QTc; k += nth) {
+            const int qc = dLa.div(k), ja = k - qc * La;
+            Real* o1v = S1 + (long long)qc * Lb * La + ja;
+            Real* o1d = o1v + S1n;
+            Real aB[P1], aD[P1];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int qb = eb * Q + q;
-                const int o = (qb + QTb * qc) * LaP + ja;
-                const Real bv = tb[1][qb * P1 + t];
-                if (MODE == 0) {
-                    rB += bv * S2[o] + tdv[1][qb * P1 + t] * S2[S2n + o];
-                    rD += bv * S2[2 * S2n + o];
-                } else {
-                    rB += bv * S2[o];
+            for (int t = 0; t < P1; ++t) aB[t] = aD[t] = 0.0;
+            for (int eb = 0; eb < Tb; ++eb) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int qb = eb * Q + q;
+                    const int o = (qb + QTb * qc) * LaP + ja;
+                    const Real v0 = S2[o], v1 = S2[S2n + o], v2 = S2[2 * S2n + o];
+                    Real bt[P1], dt[P1];
+                    load_row<Real, P1>(tb[1] + qb * P1, bt);
+                    load_row<Real, P1>(tdv[1] + qb * P1, dt);
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) {
+                        aB[t] += bt[t] * v0 + dt[t] * v1;
+                        aD[t] += bt[t] * v2;
+                    }
+                }
+                const int base = eb * M;
+                for (int u = 0; u < M; ++u) {
+                    o1v[(base + u) * La] = aB[0];
+                    o1d[(base + u) * La] = aD[0];
+#pragma unroll
+                    for (int t = 0; t < P; ++t) { aB[t] = aB[t + 1]; aD[t] = aD[t + 1]; }
+                    aB[P] = aD[P] = 0.0;
                 }
             }
+            const int base = Tb * M;
+            for (int u = 0; u <= P - M; ++u) {
+                o1v[(base + u) * La] = aB[0];
+                o1d[(base + u) * La] = aD[0];
+#pragma unroll
+                for (int t = 0; t < P; ++t) { aB[t] = aB[t + 1]; aD[t] = aD[t + 1]; }
+                aB[P] = aD[P] = 0.0;
+            }
         }
-        S1[idx] = rB;
-        if (MODE == 0) S1[S1n + idx] = rD;
+    } else {
+        for (int idx = tid; idx < S1n; idx += nth) {
+            const int r = dLa.div(idx), ja = idx - r * La, qc = dLb.div(r), jb = r - qc * Lb;
+            int lo = elem_lo(jb, P, M), hi = elem_hi(jb, M, Tb);
+            Real rB = 0.0, rD = 0.0;
+            for (int eb = lo; eb <= hi; ++eb) {
+                const int t = jb - eb * M;
+    #pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int qb = eb * Q + q;
+                    const int o = (qb + QTb * qc) * LaP + ja;
+                    const Real bv = tb[1][qb * P1 + t];
+                    if (MODE == 0) {
+                        rB += bv * S2[o] + tdv[1][qb * P1 + t] * S2[S2n + o];
+                        rD += bv * S2[2 * S2n + o];
+                    } else {
+                        rB += bv * S2[o];
+                    }
+                }
+            }
+            S1[idx] = rB;
+            if (MODE == 0) S1[S1n + idx] = rD;
+        }
     }
     __syncthreads();
     // backward c and scatter
