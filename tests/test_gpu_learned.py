@@ -62,6 +62,38 @@ def test_perturbed_cube_with_coefficient(sg):
             assert _rel(u[sl], comp.solve()) < 1e-9, tuple(g.levels)
 
 
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-12, 1e-9), ("mixed", 1e-10, 1e-7)])
+def test_perturbed_cube_full_size_sampled_components(sg, precision, tol, bound):
+    """The learned-preconditioner workload at its full size (p = 3, w = 12, 199
+    components, 3.03 M DoFs, 128 Fourier features), solved by the plan as the
+    report solves it. Sampled components (the longest in directions 0 and 2 at
+    |i| = 12, and the cube-shaped one) are compared, by their values on the
+    17^3 lattice, with the oracle's assembly and direct solve of the same
+    component."""
+    from paper_1707_09598_gb300.inputs import eval_points
+    kn, cp = perturbed_cube_patch(1)
+    om, ph, amp = lognormal_features(2, nfeat=128)
+    geom = geometry.BSplinePatch([3, 3, 3], kn, cp)
+    a = geometry.lognormal_coefficient(om, ph, amp)
+    pts = eval_points(3, 16)
+    npts = len(pts)
+    sample = [(10, 1, 1), (1, 1, 10), (4, 4, 4)]
+    with sg.Plan(3, 3, 12, domain="patch", patch=([3, 3, 3], kn, cp), precision=precision) as P:
+        assert P.info.ngrids == 199 and P.info.ndof == 3026945
+        sg.sgiga_set_coefficient(P.handle, om, ph, amp)
+        sg.sgiga_set_rhs_builtin(P.handle, "one")
+        st, _ = sg.sgiga_solve(P.handle, tol, 3000)
+        uc = torch.zeros(P.info.ngrids * npts, dtype=torch.float64, device="cuda")
+        sg.sgiga_eval(P.handle, torch.as_tensor(pts, device="cuda"), npts, uc)
+        uc = uc.cpu().numpy().reshape(P.info.ngrids, npts)
+        levels = [tuple(g.levels[:3]) for g in P.grids]
+    prob = problems.get("one3")
+    for lv in sample:
+        comp = Component(geom, lv, 3).assemble(f=prob.f, diffusion=a)
+        ref = comp.evaluate(comp.solve(), pts)
+        assert _rel(uc[levels.index(lv)], ref) < bound, (lv, _rel(uc[levels.index(lv)], ref))
+
+
 def _bf16(x):
     return torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
 
