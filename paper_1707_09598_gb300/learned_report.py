@@ -21,6 +21,7 @@ The mixed plans run each FP32 inner solve to --inner-tol (1e-3, the fastest
 of 1e-2 .. 1e-6 measured on this workload; 3 refinement steps either way).
 
   python -m paper_1707_09598_gb300.learned_report [--w 12] [--pairs 10000] [--epochs 6] [--inner-tol 1e-3]
+      [--inner-tol-sweep 1e-2,3e-3,1e-3,1e-4,1e-5,1e-6]
 """
 import argparse
 import json
@@ -46,6 +47,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--nfeat", type=int, default=128)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner-tol-sweep", default="",
+                    help="comma-separated inner tolerances: also time the mixed FD solve at each (best of 3)")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative tolerance of each FP32 inner solve of the mixed plans (measured best of "
                          "1e-2 .. 1e-6 on this workload; the library default is 1e-5)")
@@ -134,6 +137,18 @@ def main():
     st, rc, ms = timed_solve(P, a.tol, 50)
     out["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
                        "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
+    if a.inner_tol_sweep:
+        sweep = []
+        for t in [float(v) for v in a.inner_tol_sweep.split(",")]:
+            sgiga.sgiga_set_solver_options(P.handle, use_graph=True, inner_tol=t, inner_max=100)
+            timed_solve(P, a.tol, 50)
+            runs = [timed_solve(P, a.tol, 50) for _ in range(3)]
+            st_t, rc_t, _ = runs[-1]
+            sweep.append({"inner_tol": t, "ms": min(r[2] for r in runs), "outer": st_t.iterations,
+                          "inner": st_t.inner_iterations, "rc": rc_t,
+                          "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))})
+        out["mixed_fd_inner_tol_sweep"] = sweep
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=True, inner_tol=a.inner_tol, inner_max=100)
     sgiga.sgiga_net_init(P.handle, 11)
     tr = sgiga.sgiga_train_net(P.handle, target_pairs=a.pairs, max_iter_record=30, epochs=a.epochs, lr=1e-3,
                                seed=100)
