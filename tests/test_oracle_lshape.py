@@ -128,3 +128,49 @@ def test_grading_raises_the_combined_rate():
             H.append(mp.errors(v, g, mp.corner_u, mp.corner_grad, P, xi, w)[1])
         rates[gamma] = rate(ws, H)
     assert rates[3.0] > rates[1.0] + 0.4, rates
+
+
+def _glued(levels, gamma=1.0, p=2):
+    return mp.LShapeComponent(levels, p, kind="onesided", gamma=gamma).assemble()
+
+
+def test_schwarz_preconditioner_is_symmetric():
+    c = _glued((3, 2))
+    rng = np.random.default_rng(21)
+    u, v = rng.standard_normal((2, c.ndof))
+    a, b = u @ mp.schwarz_apply(c, v), v @ mp.schwarz_apply(c, u)
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_schwarz_is_exact_inside_a_patch():
+    """For e on functions of one patch at least p+1 away from its interface
+    sides, K e involves that patch alone and its rows equal the patch's own
+    stiffness, so the weighted Schwarz preconditioner returns e exactly."""
+    p = 2
+    c = _glued((4, 4), p=p)
+    nf0, nf1 = c.nf
+    pos = -np.ones(c.nglob, dtype=np.int64)
+    pos[c.interior] = np.arange(c.ndof)
+    rng = np.random.default_rng(22)
+    for q in range(3):
+        e = np.zeros(c.ndof)
+        a, b = np.meshgrid(np.arange(p + 1, nf0 - 1), np.arange(p + 1, nf1 - 1), indexing="xy")
+        idx = pos[c.ids[q][(a + nf0 * b).reshape(-1)]]
+        assert (idx >= 0).all()
+        e[idx] = rng.standard_normal(len(idx))
+        z = mp.schwarz_apply(c, c.K @ e)
+        assert np.abs(z - e).max() < 1e-10 * np.abs(e).max(), q
+
+
+def test_schwarz_condition_grows_like_inverse_h():
+    """The interface weights 1/2 (Neumann-Neumann) keep cond(M K) growing like
+    h^-1 across levels (about 2x per level); without them it grows like h^-2."""
+    conds = []
+    for lv in (3, 4):
+        c = _glued((lv, lv))
+        K = c.K.toarray()
+        M = np.column_stack([mp.schwarz_apply(c, col) for col in np.eye(c.ndof)])
+        ev = np.linalg.eigvals(M @ K)
+        assert np.abs(ev.imag).max() < 1e-8 * np.abs(ev.real).max() and ev.real.min() > 0
+        conds.append(ev.real.max() / ev.real.min())
+    assert conds[1] / conds[0] < 2.6, conds
