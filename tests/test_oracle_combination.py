@@ -103,3 +103,23 @@ def test_tiny_levels_agree_with_full_tensor_solve():
         gap = np.max(np.abs(uc - uf))
         assert gap <= np.max(np.abs(uc - ex)) + np.max(np.abs(uf - ex))
         assert gap < 0.05
+
+
+def test_compensated_combination_matches_an_exactly_rounded_sum():
+    """combine (Neumaier) against math.fsum, which is correctly rounded, on
+    +-1e16 components that cancel down to O(1) values (the regime of the
+    +- combination sum)."""
+    import math
+    from oracle import combination
+    rng = np.random.default_rng(31)
+    ng, npts = 40, 25
+    big = 1e16 * rng.standard_normal((ng // 2, npts))
+    vals = np.vstack([big, big + rng.standard_normal((ng // 2, npts))])
+    coef = np.concatenate([-np.ones(ng // 2), np.ones(ng // 2)])
+    got = combination.combine(vals, coef)
+    ref = np.array([math.fsum(coef * vals[:, j]) for j in range(npts)])
+    naive = (coef[:, None] * vals).sum(axis=0)
+    # Neumaier: error <= 2 eps |sum| + O(n eps^2) sum |x| (~1e-13 here); the
+    # plain sum is off by O(eps sum |x|), of the order of the result itself
+    assert np.abs(got - ref).max() < 1e-12
+    assert np.abs(naive - ref).max() > 1.0
