@@ -23,8 +23,11 @@ Modules
   multipatch   the L-shaped domain: three glued bilinear patches, Dirichlet
                lifting by edge L2 projection, L2/H1 errors (not in the
                paper's experiments; its graded-mesh topic, Sec. 4.4)
-  net          the learned correction network's forward and backward (not in
+  net          the learned scaling network's forward and backward (not in
                the paper; the CUDA network's definition)
+  learned      features, scaled fast-diagonalisation preconditioner
+               S * FD(S * r), and the training loss with its gradient (not
+               in the paper; the CUDA learned preconditioner's definition)
   problems     manufactured solutions; f = -Laplace(u) derived symbolically
   driver       whole-method runs: solve every component, evaluate, combine
 

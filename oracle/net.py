@@ -1,24 +1,25 @@
-"""Learned correction network of the oracle: plain FP64 forward and backward.
+"""Network of the learned preconditioner scaling: plain FP64 forward and backward.
 
 TEST INFRASTRUCTURE: see the package header. Not in the paper (it is the
-CUDA library's learned correction of its preconditioner); this module is the
-definition its kernels are checked against.
+CUDA library's learned scaling of its preconditioner, see oracle.learned);
+this module is the definition its kernels are checked against.
 
 N(x) on each component's DoF tensor (shape (n_d, .., n_1), direction 1
-fastest in the packed vector), zero padding, channels 2 -> 32 -> 32 -> 1:
+fastest in the packed vector), zero padding, channels 1 -> 32 -> 32 -> 1
+(input: the log of the local effective coefficient; output: log S):
     Z1 = conv(x, W1) + b1,  A1 = relu(Z1)
     Z2 = conv(A1, W2) + b2, A2 = relu(Z2)
     Y  = conv(A2, W3) + b3
 conv(X, W)[co][v] = sum_{ci, t} W[co][ci][t] X[ci][v + offset(t)], offsets in
 {-1, 0, 1}^d with the offset of direction 1 varying fastest over t.
-Parameters are one vector: W1 [32][2][T], b1 [32], W2 [32][32][T], b2 [32],
+Parameters are one vector: W1 [32][1][T], b1 [32], W2 [32][32][T], b2 [32],
 W3 [1][32][T], b3 [1] (T = 3^d).
 """
 import itertools
 
 import numpy as np
 
-CIN = (2, 32, 32)
+CIN = (1, 32, 32)
 COUT = (32, 32, 1)
 
 
@@ -95,7 +96,7 @@ def conv_weight_grad(dY, X, T):
 
 
 def forward(params, x):
-    """x: (2, *shape) for one component; returns Y (shape) and the activations."""
+    """x: (1, *shape) for one component; returns Y (shape) and the activations."""
     d = x.ndim - 1
     (W1, b1), (W2, b2), (W3, b3) = unpack(params, d)
     A1 = np.maximum(conv(x, W1, b1), 0.0)

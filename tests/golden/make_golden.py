@@ -5,6 +5,7 @@ the repository root:
 
     python tests/golden/make_golden.py cube_p3_w10
     python tests/golden/make_golden.py lshape_p2_w11_g2
+    python tests/golden/make_golden.py perturbed_p3_w12
 
 Output: tests/golden/<name>.txt with, for each parametric evaluation point,
 the combined sparse-grid value sum_i c_i u_i(xi) and the values of a few
@@ -76,11 +77,32 @@ def main_lshape(name):
     print("wrote %s in %.1f s" % (out, time.time() - t0))
 
 
+# The learned-preconditioner workload: the unit cube mapped by the seeded cubic
+# B-spline perturbation (amplitude 0.1, seed 1) with the log-normal coefficient
+# a = exp(g) (128 random Fourier features, seed 2), f = 1:
+# name -> (d, p, w, problem, eval lattice k, selected components)
+PERTURBED = {
+    "perturbed_p3_w12": (3, 3, 12, "one3", 16, [(12, 1, 1), (1, 1, 12), (4, 5, 5)]),
+}
+
+
+def _perturbed_geometry():
+    from oracle import geometry
+    from paper_1707_09598_gb300.inputs import lognormal_features, perturbed_cube_patch
+    kn, cp = perturbed_cube_patch(1)
+    om, ph, amp = lognormal_features(2, nfeat=128)
+    return geometry.BSplinePatch([3, 3, 3], kn, cp), geometry.lognormal_coefficient(om, ph, amp)
+
+
 def _one(args):
     domain, d, p, i, problem, pts = args
     from oracle import geometry, problems
     from oracle.galerkin import Component
-    comp = Component(geometry.make(domain, d), i, p).assemble(f=problems.get(problem).f)
+    if domain == "perturbed":
+        geom, a = _perturbed_geometry()
+        comp = Component(geom, i, p).assemble(f=problems.get(problem).f, diffusion=a)
+    else:
+        comp = Component(geometry.make(domain, d), i, p).assemble(f=problems.get(problem).f)
     u = comp.solve()
     return comp.evaluate(u, pts)
 
@@ -88,13 +110,23 @@ def _one(args):
 def main(name):
     from oracle import combination
     from paper_1707_09598_gb300.inputs import eval_points
-    domain, d, p, w, problem, k, sel = CASES[name]
+    if name in PERTURBED:
+        d, p, w, problem, k, sel = PERTURBED[name]
+        domain = "perturbed"
+    else:
+        domain, d, p, w, problem, k, sel = CASES[name]
     pts = eval_points(d, k)
     idx = combination.index_set(d, w)
+    # largest components first (their assembly and LU take longest)
+    order = sorted(range(len(idx)), key=lambda j: -sum(idx[j][0]))
     t0 = time.time()
     ctx = mp.get_context("spawn")
-    with ctx.Pool(min(8, os.cpu_count())) as pool:
-        vals = pool.map(_one, [(domain, d, p, i, problem, pts) for i, _ in idx], chunksize=1)
+    nproc = int(os.environ.get("GOLDEN_PROCS", min(8, os.cpu_count())))
+    with ctx.Pool(nproc) as pool:
+        done = pool.map(_one, [(domain, d, p, idx[j][0], problem, pts) for j in order], chunksize=1)
+    vals = [None] * len(idx)
+    for j, v in zip(order, done):
+        vals[j] = v
     vals = np.stack(vals)
     coeffs = np.array([c for _, c in idx], dtype=np.float64)
     comb = combination.combine(vals, coeffs)
@@ -103,6 +135,9 @@ def main(name):
     out = os.path.join(HERE, name + ".txt")
     with open(out, "w") as fh:
         fh.write("# oracle values written by tests/golden/make_golden.py %s\n" % name)
+        if domain == "perturbed":
+            fh.write("# unit cube mapped by perturbed_cube_patch(1) (cubic, amplitude 0.1), diffusion "
+                     "a = exp(field) of lognormal_features(2, nfeat=128), f = 1\n")
         fh.write("# domain=%s d=%d p=%d C^%d w=%d problem=%s lattice k=%d (eval_points(d, k))\n"
                  % (domain, d, p, p - 1, w, problem, k))
         fh.write("# columns: combined %s\n" % " ".join("u" + "_".join(map(str, s)) for s in sel))

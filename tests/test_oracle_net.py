@@ -33,7 +33,7 @@ def test_conv_matches_scipy_correlate(d, shape):
 def test_backward_matches_finite_differences(d, shape):
     rng = np.random.default_rng(2)
     p = _params(d)
-    x = rng.standard_normal((2,) + tuple(reversed(shape)))
+    x = rng.standard_normal((net.CIN[0],) + tuple(reversed(shape)))
     dy = rng.standard_normal(tuple(reversed(shape)))
     g = net.backward(p, x, dy)
     f = lambda q: float(np.sum(dy * net.forward(q, x)[0]))
