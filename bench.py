@@ -1,15 +1,24 @@
-"""Benchmark of the sparse-grid isogeometric solve on GB300.
+"""Benchmark of the sparse-grid isogeometric solve on GB300: learned/mixed
+against plain per-grid FP64 PCG.
 
-Workload: 3D Poisson on the unit cube, u = sin(pi x) sin(pi y) sin(pi z),
-p = 3 C^2 B-splines, combination level w = 10 (136 component grids with
-10 <= |i| <= 12, 557,030 DoFs in total), batched FP64 matrix-free operator +
-fast-diagonalisation PCG to relative residual 1e-12, then evaluation of every
+Workload (the learned-preconditioner configuration): 3D Poisson
+-div(a grad u) = 1 on the unit cube mapped by a seeded cubic B-spline
+perturbation (amplitude 0.1), log-normal coefficient a (std 0.5, correlation
+length 0.2, 128 random Fourier features), p = 3 C^2 B-splines, combination
+level w = 12 (199 component grids with 12 <= |i| <= 14, 3,026,945 DoFs),
+every component solved to relative residual 1e-8, then evaluation of every
 component on the 17^3 parametric lattice and the +-combination sum.
 
 A step = load vector from f at the quadrature points (resident in HBM) +
-batched solve + evaluation + combination, through the C ABI. `value` is the whole job's DoF/s (sum of
-component DoFs over all ranks / step time); each rank under torchrun solves
-its own replica of the workload (weak scaling).
+batched solve (the faster of the mixed FP32/FP64 solve with fast
+diagonalisation and the same with the learned scaling, chosen at set-up) +
+evaluation + combination, through the C ABI. `value` is the whole job's DoF/s
+(sum of component DoFs over all ranks / step time); each rank under torchrun
+solves its own replica of the workload (weak scaling). The comparators of the
+metric (plain per-grid FP64 PCG, batched FP64 PCG, mixed FD, learned + mixed,
+and the network-free scaling) are timed once each beside it, with their error
+against the oracle's stored combined values; the set-up is broken down by
+phase. The earlier FP64 unit-cube line (w = 10) is kept under "cube_fp64".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -29,17 +38,25 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "sparse-grid IGA solve wall time & DoF/s at 1e-8 L2, learned/mixed vs plain PCG"
-WORKLOAD = dict(d=3, p=3, w=10, domain="unit", source="sine", tol=1e-12, lattice=16)
-WORKLOAD_NAME = ("3D unit-cube Poisson, u=sin(pi x)sin(pi y)sin(pi z), p=3 C^2 B-splines, combination "
-                 "level w=10 (136 grids, 10<=|i|<=12, 557030 DoFs), FP64 matrix-free apply + batched "
-                 "FD-PCG to rel. residual 1e-12, eval+combine on the 17^3 parametric lattice")
-GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
-# components solved by the CPU oracle in its bounded sample (assembly + direct solve + evaluation)
-ORACLE_SAMPLE = [(4, 4, 4), (10, 1, 1), (3, 5, 4), (2, 2, 7)]
-# DRAM bytes (read + write) of one launch of the diagonal-metric FP64 apply on
-# this workload at the autotuned tiles (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of three launches of one ncu capture)
-APPLY_DRAM_BYTES = 555.403520e6 + 4.524971e6
+WORKLOAD = dict(d=3, p=3, w=12, nfeat=128, tol=1e-8, lattice=16, inner_tol=1e-3)
+WORKLOAD_NAME = ("3D Poisson -div(a grad u) = 1 on the unit cube mapped by a seeded cubic B-spline perturbation "
+                 "(amplitude 0.1), log-normal a (std 0.5, correlation length 0.2, 128 Fourier features), p=3 C^2 "
+                 "B-splines, combination level w=12 (199 grids, 12<=|i|<=14, 3026945 DoFs), every component solved "
+                 "to rel. residual 1e-8, eval+combine on the 17^3 parametric lattice")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "perturbed_p3_w12.txt")
+# the earlier FP64 unit-cube line (kept beside the headline)
+CUBE = dict(d=3, p=3, w=10, tol=1e-12, lattice=16)
+CUBE_NAME = ("3D unit-cube Poisson, u=sin(pi x)sin(pi y)sin(pi z), p=3 C^2, w=10 (136 grids, 557030 DoFs), FP64 "
+             "matrix-free apply + batched FD-PCG to rel. residual 1e-12, eval+combine on 17^3")
+CUBE_GOLDEN = os.path.join(ROOT, "tests", "golden", "cube_p3_w10.txt")
+# components of the workload solved by the CPU oracle in its bounded sample
+# (assembly + sparse direct solve + evaluation); |i| = 12, the smallest grids
+ORACLE_SAMPLE = [(10, 1, 1), (4, 4, 4)]
+# the reference arm's one component per step, cycling
+REFERENCE_SAMPLE = [(10, 1, 1), (1, 10, 1), (4, 4, 4), (1, 1, 10)]
+# DRAM bytes (read + write) of one launch of the FP32 apply on this workload
+# at the autotuned tiles, from an ncu capture (None until captured)
+APPLY_F32_DRAM_BYTES = None
 
 
 def parse():
@@ -49,11 +66,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--host-loop", action="store_true",
-                    help="run the CG loop from the host instead of the captured graph (same kernels; "
+                    help="run the CG loops from the host instead of the captured graph (same kernels; "
                          "profilers list the kernels of a device-side graph loop only this way)")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision line of the same workload")
-    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: skip the comparators, the cube line and the CPU baselines")
     ap.add_argument("--oracle-parallel", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-list", default="", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -61,24 +79,28 @@ def parse():
 # CPU oracle sample (runs in a child process with one BLAS thread)
 # ----------------------------------------------------------------------------
 
-def oracle_sample_child(nrep):
-    dofs = 0
-    t0 = time.perf_counter()
-    for rep in range(nrep):
-        dofs += oracle_task(ORACLE_SAMPLE[rep % len(ORACLE_SAMPLE)])
-    dt = time.perf_counter() - t0
-    print(json.dumps({"dofs": dofs, "seconds": dt, "components": nrep}))
-
-
 def oracle_task(lv):
     """One component of the workload through the oracle: assembly, sparse
     direct solve, evaluation on the lattice. Returns its DoFs."""
     from oracle import geometry, problems
     from oracle.galerkin import Component
-    from paper_1707_09598_gb300.inputs import eval_points
-    comp = Component(geometry.UnitCube(3), lv, 3).assemble(f=problems.get("sine3").f)
+    from paper_1707_09598_gb300.inputs import eval_points, lognormal_features, perturbed_cube_patch
+    kn, cp = perturbed_cube_patch(1)
+    om, ph, amp = lognormal_features(2, nfeat=WORKLOAD["nfeat"])
+    geom = geometry.BSplinePatch([3, 3, 3], kn, cp)
+    comp = Component(geom, lv, WORKLOAD["p"]).assemble(f=problems.get("one3").f,
+                                                       diffusion=geometry.lognormal_coefficient(om, ph, amp))
     comp.evaluate(comp.solve(), eval_points(3, WORKLOAD["lattice"]))
     return comp.ndof
+
+
+def oracle_sample_child(comps):
+    dofs = 0
+    t0 = time.perf_counter()
+    for lv in comps:
+        dofs += oracle_task(lv)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"dofs": dofs, "seconds": dt, "components": len(comps)}))
 
 
 def oracle_parallel_child(per_core):
@@ -98,12 +120,18 @@ def oracle_parallel_child(per_core):
     print(json.dumps({"dofs": dofs, "seconds": dt, "components": len(tasks), "cores": ncores}))
 
 
-def run_oracle_sample(nrep, parallel=False):
+def run_oracle_sample(n, parallel=False, comps=None):
+    """Serial: the components `comps` (default ORACLE_SAMPLE) in one child;
+    parallel: n tasks per core over a spawned pool."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    flag = "--oracle-parallel" if parallel else "--oracle-sample"
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), flag, str(nrep)],
+    if parallel:
+        argv = ["--oracle-parallel", str(n)]
+    else:
+        comps = ORACLE_SAMPLE if comps is None else comps
+        argv = ["--oracle-list", ";".join(",".join(map(str, lv)) for lv in comps)]
+    out = subprocess.run([sys.executable, os.path.abspath(__file__)] + argv,
                          env=env, capture_output=True, text=True, cwd=ROOT)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
@@ -313,12 +341,14 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    per_step = 1
+    k = 0
     for _ in range(args.warmup):
-        run_oracle_sample(per_step)
+        run_oracle_sample(0, comps=[REFERENCE_SAMPLE[k % len(REFERENCE_SAMPLE)]])
+        k += 1
     dofs, secs = 0, 0.0
     for _ in range(args.steps):
-        r = run_oracle_sample(per_step)
+        r = run_oracle_sample(0, comps=[REFERENCE_SAMPLE[k % len(REFERENCE_SAMPLE)]])
+        k += 1
         dofs += r["dofs"]
         secs += r["seconds"]
     value = dofs / secs
@@ -330,7 +360,7 @@ def run_reference(args):
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "DoF/s", "cores": 1,
                          "sample": "per step: one component of the workload (cycling %s), assembly + sparse "
                                    "direct solve + evaluation on 17^3 points, FP64, one BLAS thread"
-                                   % ORACLE_SAMPLE},
+                                   % REFERENCE_SAMPLE},
         "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -341,68 +371,211 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------
 
-def run_mixed(args, sgiga, torch, f_dev, pts, npts, gold, ndof, world):
-    """The same workload and tolerance with the FP32 inner solve inside FP64
-    iterative refinement (FP64 residual; FP32 apply and preconditioner)."""
-    W = WORKLOAD
-    stream = torch.cuda.Stream()
-    # torch's fills and reads of the buffers handed to the plan run on the
-    # plan's stream, in order with its calls (the inputs are complete)
-    prev = torch.cuda.current_stream()
-    torch.cuda.synchronize()
-    torch.cuda.set_stream(stream)
-    P = sgiga.Plan(W["d"], W["p"], W["w"], domain=W["domain"], precision="mixed", stream=stream)
-    sgiga.sgiga_autotune(P.handle, reps=3)
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+
+
+class Workload:
+    """Inputs of the perturbed-cube workload shared by every plan of the bench."""
+
+    def __init__(self, sgiga, torch, stream):
+        from paper_1707_09598_gb300.inputs import eval_points, lognormal_features, perturbed_cube_patch
+        self.sg, self.torch, self.stream = sgiga, torch, stream
+        self.kn, self.cp = perturbed_cube_patch(1)
+        self.om, self.ph, self.amp = lognormal_features(2, nfeat=WORKLOAD["nfeat"])
+        self.pts_h = eval_points(3, WORKLOAD["lattice"])
+        self.pts = torch.as_tensor(self.pts_h, device="cuda")
+        self.npts = len(self.pts_h)
+        self.gold = np.loadtxt(GOLDEN)[:, 0]
+
+    def plan(self, precision, precond, components=None, autotune=True):
+        """A plan with the coefficient set and (optionally) autotuned; returns
+        (plan, set-up seconds, phase times)."""
+        sg = self.sg
+        t0 = time.perf_counter()
+        kw = {} if components is None else {"components": components}
+        P = sg.Plan(3, WORKLOAD["p"], WORKLOAD["w"], domain="patch", patch=([3, 3, 3], self.kn, self.cp),
+                    precision=precision, precond=precond, stream=self.stream, **kw)
+        sg.sgiga_set_coefficient(P.handle, self.om, self.ph, self.amp)
+        tune = sg.sgiga_autotune(P.handle, reps=2) if autotune else None
+        return P, time.perf_counter() - t0, sg.sgiga_plan_times(P.handle), tune
+
+    def combined(self, P):
+        torch = self.torch
+        uc = torch.zeros(P.info.ngrids * self.npts, dtype=torch.float64, device="cuda")
+        self.sg.sgiga_eval(P.handle, self.pts, self.npts, uc)
+        u = torch.zeros(self.npts, dtype=torch.float64, device="cuda")
+        self.sg.sgiga_combine(P.handle, uc, self.npts, u)
+        return u.cpu().numpy()
+
+    def timed_solve(self, P, tol, maxit, reps=2):
+        """Best of `reps` solves after one warm-up (CUDA events on the plan's stream)."""
+        sg, torch = self.sg, self.torch
+        sg.sgiga_solve(P.handle, tol, maxit, check=False)
+        best, st = 1e30, None
+        for _ in range(reps):
+            e0, e1 = _events(torch)
+            torch.cuda.synchronize()
+            e0.record(self.stream)
+            st, rc = sg.sgiga_solve(P.handle, tol, maxit, check=False)
+            e1.record(self.stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return st, rc, best
+
+
+def measure_comparators(W, args):
+    """Plain per-grid FP64 PCG, batched FP64 PCG and mixed FD, each timed once
+    (best of 2 after a warm-up) at the workload's tolerance, with the error of
+    its combined values against the oracle. Returns (dict, mixed FD plan)."""
+    sg, torch, tol = W.sg, W.torch, WORKLOAD["tol"]
+    out = {}
+    P, ps, pt, _ = W.plan("fp64", "fd")
     if args.host_loop:
-        sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
+        sg.sgiga_set_solver_options(P.handle, use_graph=False)
+    sg.sgiga_set_rhs_builtin(P.handle, "one")
+    st, rc, ms = W.timed_solve(P, tol, 2000)
+    out["batched_fp64"] = {"ms": ms, "iterations": st.iterations, "rc": rc, "setup_s": ps,
+                           "rel_l2_vs_oracle": _rel(W.combined(P), W.gold)}
+    comps = [tuple(g.levels[:3]) for g in P.grids]
+    coefs = [g.coeff for g in P.grids]
+    P.close()
+    # plain per-grid FP64 PCG: one plan per component, solved one after the other
+    # on the stream with the host loop (no batching, no captured graph)
+    t0 = time.perf_counter()
+    singles = []
+    for cl in comps:
+        Q, _, _, _ = W.plan("fp64", "fd", components=[cl], autotune=False)
+        sg.sgiga_set_rhs_builtin(Q.handle, "one")
+        sg.sgiga_set_solver_options(Q.handle, use_graph=False)
+        singles.append(Q)
+    setup_s = time.perf_counter() - t0
+    for Q in singles[:4]:
+        sg.sgiga_solve(Q.handle, tol, 2000, check=False)
+    e0, e1 = _events(torch)
+    torch.cuda.synchronize()
+    e0.record(W.stream)
+    its = 0
+    for Q in singles:
+        st, _ = sg.sgiga_solve(Q.handle, tol, 2000, check=False)
+        its = max(its, st.iterations)
+    e1.record(W.stream)
+    torch.cuda.synchronize()
+    acc = np.zeros(W.npts)
+    for Q, c in zip(singles, coefs):
+        uq = torch.zeros(W.npts, dtype=torch.float64, device="cuda")
+        sg.sgiga_eval(Q.handle, W.pts, W.npts, uq)
+        acc += c * uq.cpu().numpy()
+        Q.close()
+    out["per_grid_fp64"] = {"ms": e0.elapsed_time(e1), "iterations": its, "plans": len(singles),
+                            "setup_s": setup_s, "rel_l2_vs_oracle": _rel(acc, W.gold)}
+    # mixed: FP32 inner FD-CG in FP64 refinement
+    M, ps, pt, _ = W.plan("mixed", "fd")
+    sg.sgiga_set_solver_options(M.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
+                                inner_max=100)
+    sg.sgiga_set_rhs_builtin(M.handle, "one")
+    st, rc, ms = W.timed_solve(M, tol, 50)
+    out["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc, "setup_s": ps,
+                       "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(M), W.gold)}
+    return out, M
+
+
+def train_learned(W, args):
+    """The learned plan: set-up, the network trained on the plan's own CG
+    pairs, and its solve. Returns (plan, dict, tuning)."""
+    sg = W.sg
+    L, ps, pt, tune = W.plan("mixed", "learned")
+    sg.sgiga_set_solver_options(L.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
+                                inner_max=100)
+    t0 = time.perf_counter()
+    sg.sgiga_net_init(L.handle, 11)
+    tr = sg.sgiga_train_net(L.handle, target_pairs=10000, max_iter_record=30, epochs=12, lr=5e-4, seed=100,
+                            batch=2)
+    train_s = time.perf_counter() - t0
+    sg.sgiga_set_rhs_builtin(L.handle, "one")
+    st, rc, ms = W.timed_solve(L, WORKLOAD["tol"], 50)
+    out = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc, "fallback": st.fallback,
+           "setup_s": ps, "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(L), W.gold),
+           "training": {"seconds": train_s, "pairs": tr.pairs, "samples": tr.samples, "adam_steps": tr.steps,
+                        "loss_first_epoch": tr.loss_first_epoch, "loss_last_epoch": tr.loss_last_epoch}}
+    tuning = {"best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
+                       "apply_f32_ms": tune.best_ms, "ntiles": tune.ntiles},
+              "precond": {"best_ks": tune.fd_ks[tune.fd_best],
+                          "layout": "grouped" if tune.fd_grouped[tune.fd_best] else "per piece"}}
+    return L, out, tuning
+
+
+def network_free_scaling(W, L):
+    """The learned plan with S = c^(-1/2) (no network), then the network's S restored."""
+    sg, torch = W.sg, W.torch
+    params = sg.sgiga_net_get_params(L.handle)
+    phi = torch.zeros(L.info.ndof, dtype=torch.float32, device="cuda")
+    sg.sgiga_net_features(L.handle, phi)
+    sg.sgiga_net_set_scaling(L.handle, torch.exp(-0.5 * phi).contiguous())
+    st, rc, ms = W.timed_solve(L, WORKLOAD["tol"], 50)
+    out = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
+           "rel_l2_vs_oracle": _rel(W.combined(L), W.gold)}
+    sg.sgiga_net_set_params(L.handle, params)
+    return out
+
+
+def cube_line(sgiga, torch, stream, steps):
+    """The FP64 unit-cube workload (w = 10): step = load vector + batched FD-PCG
+    to 1e-12 + eval + combine; its FP64 operator apply against the FP64 rate
+    (cuBLAS DGEMM, measured here)."""
+    from paper_1707_09598_gb300.inputs import eval_points
+    C = CUBE
+    P = sgiga.Plan(C["d"], C["p"], C["w"], domain="unit", stream=stream)
+    sgiga.sgiga_autotune(P.handle, reps=3)
+    pts_h = eval_points(3, C["lattice"])
+    npts = len(pts_h)
+    pts = torch.as_tensor(pts_h, device="cuda")
     uc = torch.zeros(P.info.ngrids * npts, dtype=torch.float64, device="cuda")
     u = torch.zeros(npts, dtype=torch.float64, device="cuda")
-    stats = []
+    f = torch.zeros(P.info.nqp, dtype=torch.float64, device="cuda")
+    sgiga.sgiga_source_at_qp(P.handle, "sine", f)
 
     def step():
-        sgiga.sgiga_set_rhs(P.handle, f_dev)
-        st, _ = sgiga.sgiga_solve(P.handle, W["tol"], 50)
-        stats.append((st.iterations, st.inner_iterations))
+        sgiga.sgiga_set_rhs(P.handle, f)
+        sgiga.sgiga_solve(P.handle, C["tol"], 50)
         sgiga.sgiga_eval(P.handle, pts, npts, uc)
         sgiga.sgiga_combine(P.handle, uc, npts, u)
 
-    for _ in range(args.warmup):
+    for _ in range(3):
         step()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(torch)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
-    uh = u.cpu().numpy()
-    # the FP32 apply alone (HBM-bound: FP32 geometry planes + x and y)
-    x = torch.randn(ndof, dtype=torch.float32, device="cuda")
+    ms = e0.elapsed_time(e1) / steps
+    l2 = _rel(u.cpu().numpy(), np.loadtxt(CUBE_GOLDEN)[:, 0])
+    x = torch.randn(P.info.ndof, dtype=torch.float64, device="cuda")
     y = torch.zeros_like(x)
     for _ in range(3):
-        sgiga.sgiga_apply_f32(P.handle, x, y)
-    reps = 20
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sgiga.sgiga_apply(P.handle, x, y)
+    a0, a1 = _events(torch)
     torch.cuda.synchronize()
     a0.record(stream)
-    for _ in range(reps):
-        sgiga.sgiga_apply_f32(P.handle, x, y)
+    for _ in range(20):
+        sgiga.sgiga_apply(P.handle, x, y)
     a1.record(stream)
     torch.cuda.synchronize()
-    apply_s = a0.elapsed_time(a1) / reps / 1e3
-    nplanes = 3 if P.info.diag_metric else 6
-    g_bytes = nplanes * 4 * P.info.nqp + 2 * 4 * ndof
-    hbm = load_peaks().get("hbm_gbs", 6800.0)
-    out = {"value": whole_job_rate(ndof, world, ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
-           "dtype": "f32 inner solve, f64 residual and combination",
-           "rel_l2_vs_oracle": float(np.linalg.norm(uh - gold) / np.linalg.norm(gold)),
-           "outer_iterations": max(s[0] for s in stats), "inner_iterations": max(s[1] for s in stats),
-           "apply_f32": {"ms": apply_s * 1e3, "algorithmic_bytes": g_bytes, "GBps": g_bytes / apply_s / 1e9,
-                         "frac_of_measured_hbm": g_bytes / apply_s / 1e9 / hbm}}
+    apply_s = a0.elapsed_time(a1) / 20 / 1e3
+    flops = apply_flops(P)
+    peak = fp64_peak_tflops(torch)
+    out = {"workload": CUBE_NAME, "value": P.info.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
+           "dtype": "f64", "rel_l2_vs_oracle": l2, "target": 1e-10,
+           "apply_fp64": {"ms": apply_s * 1e3, "algorithmic_flops": flops, "TFLOPs": flops / apply_s / 1e12,
+                          "fp64_peak_TFLOPs": peak, "frac": flops / apply_s / 1e12 / peak,
+                          "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU"}}
     P.close()
-    torch.cuda.synchronize()
-    torch.cuda.set_stream(prev)
     return out
 
 
@@ -417,46 +590,47 @@ def run_ours(args):
     if not os.path.exists(b.LIB):
         b.build()
     from paper_1707_09598_gb300 import sgiga
-    from paper_1707_09598_gb300.inputs import eval_points
 
-    W = WORKLOAD
     stream = torch.cuda.Stream()
-    # torch's fills and reads of the buffers handed to the plan run on the
-    # plan's stream, in order with its calls
+    # torch's fills and reads of the buffers handed to the plans run on the
+    # plans' stream, in order with their calls
     torch.cuda.set_stream(stream)
-    t0 = time.perf_counter()
-    P = sgiga.Plan(W["d"], W["p"], W["w"], domain=W["domain"], stream=stream)
-    plan_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    tune = sgiga.sgiga_autotune(P.handle, reps=3)
-    tune_s = time.perf_counter() - t0
-    if args.host_loop:
-        sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
-    tuning = {"seconds": tune_s, "best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
-                                          "apply_ms": tune.best_ms, "ntiles": tune.ntiles},
-              "candidates_ms": [round(tune.ms[i], 4) for i in range(tune.ncand)],
-              "precond_split": {"best_ks": tune.fd_ks[tune.fd_best],
-                                "best_layout": "grouped" if tune.fd_grouped[tune.fd_best] else "per piece",
-                                "items": tune.fd_nitems,
-                                "candidates_ms": {("grouped " if tune.fd_grouped[i] else "per piece ") +
-                                                  str(tune.fd_ks[i]): round(tune.fd_ms[i], 4)
-                                                  for i in range(tune.fd_ncand)}}}
-    ndof, ng = P.info.ndof, P.info.ngrids
-    pts_h = eval_points(W["d"], W["lattice"])
-    npts = len(pts_h)
-    pts = torch.as_tensor(pts_h, device="cuda")
+    W = Workload(sgiga, torch, stream)
+    tol = WORKLOAD["tol"]
+    comparison = {}
+    if not args.quick:
+        comparison, M = measure_comparators(W, args)
+    else:
+        M, _, _, _ = W.plan("mixed", "fd")
+        sgiga.sgiga_set_solver_options(M.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
+                                       inner_max=100)
+        sgiga.sgiga_set_rhs_builtin(M.handle, "one")
+        st, rc, ms = W.timed_solve(M, tol, 50)
+        comparison["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc}
+    L, comparison["learned_mixed"], tuning = train_learned(W, args)
+    if not args.quick:
+        comparison["scaled_no_network"] = network_free_scaling(W, L)
+    # the headline path: the faster of mixed FD and learned + mixed, at the tolerance
+    use_learned = (comparison["learned_mixed"]["rc"] == 0 and
+                   comparison["learned_mixed"]["ms"] <= comparison["mixed_fd"]["ms"])
+    P = L if use_learned else M
+    (M if use_learned else L).close()
+    if "per_grid_fp64" in comparison:
+        pg = comparison["per_grid_fp64"]["ms"]
+        for k, v in comparison.items():
+            if k != "per_grid_fp64":
+                v["speedup_vs_per_grid_fp64"] = pg / v["ms"]
+    ndof, ng, nqp, npts = P.info.ndof, P.info.ngrids, P.info.nqp, W.npts
     uc = torch.zeros(ng * npts, dtype=torch.float64, device="cuda")
     u = torch.zeros(npts, dtype=torch.float64, device="cuda")
-    iters = []
-    # the step's input: f at every quadrature point, resident in HBM
-    f_dev = torch.zeros(P.info.nqp, dtype=torch.float64, device="cuda")
-    sgiga.sgiga_source_at_qp(P.handle, W["source"], f_dev)
+    f_dev = torch.ones(nqp, dtype=torch.float64, device="cuda")     # f = 1 at every quadrature point
+    stats = []
 
     def step():
         sgiga.sgiga_set_rhs(P.handle, f_dev)
-        st, _ = sgiga.sgiga_solve(P.handle, W["tol"], 50)
-        iters.append(st.iterations)
-        sgiga.sgiga_eval(P.handle, pts, npts, uc)
+        st, _ = sgiga.sgiga_solve(P.handle, tol, 50)
+        stats.append(st)
+        sgiga.sgiga_eval(P.handle, W.pts, npts, uc)
         sgiga.sgiga_combine(P.handle, uc, npts, u)
 
     for _ in range(args.warmup):
@@ -467,7 +641,7 @@ def run_ours(args):
     clocks = clock_sampler(torch, local)
     clocks.start()
     l0 = sgiga.sgiga_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(torch)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
@@ -480,66 +654,55 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     value = whole_job_rate(ndof, world, ms / 1e3)
-
-    # accuracy of the combined solution against the stored oracle values
-    gold = np.loadtxt(GOLDEN)[:, 0]
-    uh = u.cpu().numpy()
-    l2 = float(np.linalg.norm(uh - gold) / np.linalg.norm(gold))
+    l2 = _rel(u.cpu().numpy(), W.gold)
 
     # per-phase times (one extra step, events between the calls)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record(stream)
     sgiga.sgiga_set_rhs(P.handle, f_dev)
     ev[1].record(stream)
-    sgiga.sgiga_solve(P.handle, W["tol"], 50)
+    sgiga.sgiga_solve(P.handle, tol, 50)
     ev[2].record(stream)
-    sgiga.sgiga_eval(P.handle, pts, npts, uc)
+    sgiga.sgiga_eval(P.handle, W.pts, npts, uc)
     sgiga.sgiga_combine(P.handle, uc, npts, u)
     ev[3].record(stream)
-    sgiga.sgiga_precond(P.handle, f_dev[:ndof].contiguous(), uc[:ndof])
-    ev[4].record(stream)
-    sgiga.sgiga_set_rhs_builtin(P.handle, W["source"])
-    ev[5].record(stream)
     torch.cuda.synchronize()
     phases = {"rhs_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
-              "eval_combine_ms": ev[2].elapsed_time(ev[3]), "one_precond_ms": ev[3].elapsed_time(ev[4]),
-              "rhs_builtin_source_ms (not in the step)": ev[4].elapsed_time(ev[5])}
+              "eval_combine_ms": ev[2].elapsed_time(ev[3])}
 
-    # dominant kernel: the FP64 operator apply, timed alone on the plan's stream
-    x = torch.randn(ndof, dtype=torch.float64, device="cuda")
+    # dominant kernel of the mixed path: the FP32 operator apply, timed alone
+    x = torch.randn(ndof, dtype=torch.float32, device="cuda")
     y = torch.zeros_like(x)
     for _ in range(3):
-        sgiga.sgiga_apply(P.handle, x, y)
+        sgiga.sgiga_apply_f32(P.handle, x, y)
     reps = 20
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0, a1 = _events(torch)
     torch.cuda.synchronize()
     a0.record(stream)
     for _ in range(reps):
-        sgiga.sgiga_apply(P.handle, x, y)
+        sgiga.sgiga_apply_f32(P.handle, x, y)
     a1.record(stream)
     torch.cuda.synchronize()
     apply_s = a0.elapsed_time(a1) / reps / 1e3
-    flops = apply_flops(P)
-    peak64 = fp64_peak_tflops(torch)
-    achieved = flops / apply_s / 1e12
-    g_bytes = (3 if P.info.diag_metric else 6) * 8 * P.info.nqp + 2 * 8 * ndof
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": APPLY_DRAM_BYTES if P.info.diag_metric else None,
-                "kernel": "k_op3<3,0> (FP64 sum-factorised stiffness apply)",
-                "apply_ms": apply_s * 1e3, "algorithmic_flops": flops,
-                "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64 pipe)",
-                "hbm_GBps": g_bytes / apply_s / 1e9,
-                "hbm_frac_of_measured": g_bytes / apply_s / 1e9 / load_peaks().get("hbm_gbs", 6800.0)}
+    nplanes = 3 if P.info.diag_metric else 6
+    g_bytes = nplanes * 4 * nqp + 2 * 4 * ndof
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "hbm", "achieved": g_bytes / apply_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": g_bytes / apply_s / 1e9 / hbm, "traffic": APPLY_F32_DRAM_BYTES,
+                "kernel": "k_op3<float,3,0,false> (FP32 sum-factorised stiffness apply, general metric)",
+                "apply_ms": apply_s * 1e3, "algorithmic_bytes": g_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 
-    # end to end through the C ABI with host buffers (pinned)
-    f_h = f_dev.cpu().pin_memory()
-    pts_pin = torch.as_tensor(pts_h).pin_memory()
+    # end to end through the C ABI with host buffers (pinned): f, points in; u out
+    f_h = torch.ones(nqp, dtype=torch.float64).pin_memory()
+    pts_pin = torch.as_tensor(W.pts_h).pin_memory()
     u_pin = torch.zeros(npts, dtype=torch.float64).pin_memory()
     f_np, pts_np, u_np = f_h.numpy(), pts_pin.numpy(), u_pin.numpy()
 
     def step_e2e():
         sgiga.sgiga_set_rhs(P.handle, f_np)
-        sgiga.sgiga_solve(P.handle, W["tol"], 50)
+        sgiga.sgiga_solve(P.handle, tol, 50)
         sgiga.sgiga_eval(P.handle, pts_np, npts, uc)
         sgiga.sgiga_combine(P.handle, uc, npts, u_np)
 
@@ -550,48 +713,54 @@ def run_ours(args):
         step_e2e()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, "cuda")
-    l2_e2e = float(np.linalg.norm(u_np - gold) / np.linalg.norm(gold))
+    l2_e2e = _rel(u_np, W.gold)
+    setup = {"headline_plan_s": comparison["learned_mixed"]["setup_s"] if use_learned
+             else comparison["mixed_fd"].get("setup_s"),
+             "headline_plan_phases_s": sgiga.sgiga_plan_times(P.handle)}
+    if use_learned:
+        setup["training_s"] = comparison["learned_mixed"]["training"]["seconds"]
+    setup["setup_plus_solve_s"] = (setup["headline_plan_s"] or 0.0) + setup.get("training_s", 0.0) + \
+        phases["solve_ms"] / 1e3
+    P.close()
+    del f_h, pts_pin, u_pin
+    torch.cuda.synchronize()
 
-    mixed = None if args.no_mixed else run_mixed(args, sgiga, torch, f_dev, pts, npts, gold, ndof, world)
-
+    cube = None if args.quick else cube_line(sgiga, torch, stream, 10)
     cpu = cpu_par = None
-    if rank == 0:
-        r = run_oracle_sample(len(ORACLE_SAMPLE))
+    if rank == 0 and not args.quick:
+        r = run_oracle_sample(0)
         cpu = {"value": r["dofs"] / r["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
                "sample": "%d components of the workload %s: assembly + sparse direct solve + evaluation "
-                         "on 17^3 points, FP64, one BLAS thread, %.1f s" % (len(ORACLE_SAMPLE),
-                                                                            ORACLE_SAMPLE, r["seconds"])}
-        rp = run_oracle_sample(2, parallel=True)
+                         "on 17^3 points, FP64, one BLAS thread, %.1f s" % (len(ORACLE_SAMPLE), ORACLE_SAMPLE,
+                                                                            r["seconds"])}
+        rp = run_oracle_sample(1, parallel=True)
         cpu_par = {"value": rp["dofs"] / rp["seconds"], "unit": "DoF/s", "cores": rp["cores"], "kind": "oracle",
-                   "sample": "%d components (the serial sample's, 2 per core) over a spawned pool of %d "
+                   "sample": "%d components (the serial sample's, one per core) over a spawned pool of %d "
                              "one-thread workers in LPT order (the paper's parallelisation), %.1f s"
                              % (rp["components"], rp["cores"], rp["seconds"])}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "ngrids": ng, "ndof": ndof, "nqp": P.info.nqp,
-                       "diag_metric": P.info.diag_metric,
-                       "eval_points": npts, "parallelism": "replica per GPU" if world > 1 else "single GPU",
-                       "l2_policy": "inputs larger than L2 (FP64 geometry planes %.2f GB per apply)"
-                                    % ((3 if P.info.diag_metric else 6) * 8 * P.info.nqp / 1e9),
+            "vs_baseline": None, "dtype": "f32 inner solve, f64 residual/combination", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "ngrids": ng, "ndof": ndof, "nqp": nqp, "eval_points": npts,
+                       "path": "learned + mixed" if use_learned else "mixed FD",
+                       "inner_tol": WORKLOAD["inner_tol"],
+                       "parallelism": "replica per GPU" if world > 1 else "single GPU",
+                       "l2_policy": "inputs larger than L2 (FP32 geometry planes %.2f GB per inner apply)"
+                                    % (nplanes * 4 * nqp / 1e9),
                        "cg_loop": "host loop" if args.host_loop else "captured graph with device-side while"},
-            "accuracy": {"rel_l2_vs_oracle": l2, "rel_l2_vs_oracle_e2e": l2_e2e,
-                         "target": 1e-10, "iterations": max(iters)},
-            "phases_ms": phases, "plan_s": plan_s, "autotune": tuning,
+            "accuracy": {"rel_l2_vs_oracle": l2, "rel_l2_vs_oracle_e2e": l2_e2e, "target": 1e-8,
+                         "outer_iterations": max(s.iterations for s in stats),
+                         "inner_iterations": max(s.inner_iterations for s in stats)},
+            "phases_ms": phases, "setup": setup, "autotune": tuning, "comparison": comparison,
             "roofline": roofline,
-            "mixed_fp32_ir": mixed,
-            "cpu_baseline": cpu,
-            "cpu_baseline_parallel": cpu_par,
+            "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
             "e2e": {"value": whole_job_rate(ndof, world, e2e_s), "unit": "DoF/s",
-                    "h2d_bytes_per_step": int(P.info.nqp * 8 + npts * W["d"] * 8),
-                    "d2h_bytes_per_step": int(npts * 8)},
-            "gpu_launches": int(launches),
-            "clocks": ck,
+                    "h2d_bytes_per_step": int(nqp * 8 + npts * 3 * 8), "d2h_bytes_per_step": int(npts * 8)},
+            "gpu_launches": int(launches), "clocks": ck, "cube_fp64": cube,
         }
         print(json.dumps(line))
-    P.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -599,8 +768,8 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.oracle_sample:
-        oracle_sample_child(args.oracle_sample)
+    if args.oracle_list:
+        oracle_sample_child([tuple(int(v) for v in c.split(",")) for c in args.oracle_list.split(";")])
         return 0
     if args.oracle_parallel:
         oracle_parallel_child(args.oracle_parallel)

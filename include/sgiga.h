@@ -102,9 +102,9 @@ enum { SGIGA_PREC_FP64 = 0, SGIGA_PREC_MIXED_FP32 = 1 };
 
 /* Preconditioner of the batched conjugate-gradient solve. FD: fast
  * diagonalisation with the 1D generalised eigenpairs; NONE: plain CG;
- * LEARNED: FD plus a trained convolutional correction (sgiga_net_*), used by
- * the inner FP32 solve of SGIGA_PREC_MIXED_FP32 as flexible CG (needs that
- * precision; falls back to FD until a network is initialised). */
+ * LEARNED: FD with a trained elementwise scaling S * FD(S * r) (sgiga_net_*),
+ * used by the inner FP32 solve of SGIGA_PREC_MIXED_FP32 as flexible CG (needs
+ * that precision; plain FD until a network is initialised). */
 enum { SGIGA_PRECOND_FD = 0, SGIGA_PRECOND_NONE = 1, SGIGA_PRECOND_LEARNED = 2 };
 
 /* Built-in right-hand sides f = -Laplace(u) for manufactured solutions u:
@@ -172,10 +172,9 @@ typedef struct {
     double max_rel_residual; /* max_g ||b_g - K_g x_g|| / ||b_g|| (recursive residual) */
     double seconds;          /* wall time of the call */
     int inner_iterations;    /* MIXED_FP32: inner CG iterations summed over refinement steps */
-    int fallback;            /* MIXED_FP32 bit flags. 1 (LEARNED): the correction was switched
-                                off for the rest of the solve, after a refinement step without a
-                                tenfold residual reduction or an inner solve that had not cut its
-                                residual 100x in 16 iterations (FD continues).
+    int fallback;            /* MIXED_FP32 bit flags. 1 (LEARNED): the learned scaling was
+                                switched off for the rest of the solve, after a refinement step
+                                without a tenfold residual reduction (FD continues).
                                 2: refinement stalled (two steps that did not halve some
                                 component's residual: the FP32 operator's error times the
                                 condition number is not small) and FP64 PCG finished the
@@ -193,6 +192,25 @@ int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out);
 void sgiga_destroy(sgiga_plan_t plan);
 
 int sgiga_plan_info(sgiga_plan_t plan, sgiga_info* out /* host */);
+
+/* Wall-clock seconds of the plan's set-up phases (host clock; every phase
+ * ends with a stream synchronisation). total = host + basis + eigen + fd +
+ * geometry + vectors, the sgiga_plan call (Sec. 4.1 times set-up, here the
+ * analogue of the paper's mesh set-up and assembly, together with the solve).
+ *   host        index set, coefficients, knots, tiles (host)
+ *   basis       1D B-spline/NURBS tables on the device and their copy back
+ *   eigen       1D generalised eigenproblems on the device (band assembly on
+ *               the host, bisection and inverse iteration on the device)
+ *   fd          preconditioner work items and eigenvalue-sum reciprocals
+ *   geometry    geometry coefficients at every quadrature point
+ *   vectors     solver vectors and FP32 copies
+ * coefficient: the last sgiga_set_coefficient; autotune: the last
+ * sgiga_autotune (0 if not called). */
+typedef struct {
+    double total, host, basis, eigen, fd, geometry, vectors;
+    double coefficient, autotune;
+} sgiga_plan_times_t;
+int sgiga_plan_times(sgiga_plan_t plan, sgiga_plan_times_t* out /* host */);
 int sgiga_grid_info(sgiga_plan_t plan, int g, sgiga_grid* out /* host */);
 
 /* Physical coordinates x = F(xi_q) of every quadrature point: xq is a host or
@@ -383,16 +401,25 @@ int sgiga_geometry_coeffs(sgiga_plan_t plan, int g, double* G, double* mw);
 int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam);
 
 /* ---------------------------------------------------------------------------
- * Learned correction of the preconditioner (not in the paper; its conclusions
- * suggest using a fast approximation as a preconditioner, Sec. 5).
+ * Learned scaling of the preconditioner (not in the paper; its conclusions
+ * name fast solvers used as preconditioners as future work, Sec. 5).
  *
- *   M(r) = z + s_z N([r / s_r, z / s_z]),  z = FD(r),  s_* = RMS of r, z per
- *   component,
- * N: three 3^d convolutions over each component's DoF tensor (zero padding),
- * 2 -> 32 -> 32 -> 1 channels, ReLU after the first two; BF16 weights with an
- * FP32 master copy, FP32 accumulation. Every function below needs a plan built
- * with SGIGA_PREC_MIXED_FP32. A non-finite network output for a component
- * falls back to z = FD(r) for that component.
+ *   M(r) = S * FD(S * r)   (elementwise products, FD = sgiga_precond_f32),
+ *   S = exp(N(phi)),  phi_i = log c_i,
+ *   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
+ * c_i being the local effective coefficient of DoF i: the R_i-weighted mean of
+ * the trace of the Galerkin metric G_q = w_q |det J_q| a(x_q) (J_q^T J_q)^{-1}
+ * relative to the parametric Laplacian (G_q = w_q I), which FD inverts
+ * exactly. N: three 3^d convolutions over each component's DoF tensor (zero
+ * padding), 1 -> 32 -> 32 -> 1 channels, ReLU after the first two; BF16
+ * weights with an FP32 master copy, FP32 accumulation. S depends only on the
+ * operator, so M is a fixed symmetric positive definite operator: the
+ * network runs once per plan (after training, loading or a geometry change),
+ * not once per CG iteration. The inner FP32 solve of SGIGA_PREC_MIXED_FP32
+ * uses M in flexible CG; a component whose network output is not finite
+ * keeps S = 1 there (plain FD), and a refinement step that does not cut the
+ * worst residual tenfold switches back to FD for the rest of the solve. Every
+ * function below needs a single-patch plan built with SGIGA_PREC_MIXED_FP32.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int target_pairs;     /* component-level (residual, error) pairs to record (e.g. 10000) */
@@ -400,34 +427,50 @@ typedef struct {
     int epochs;           /* passes over the recorded samples */
     float lr;             /* Adam learning rate */
     unsigned seed;        /* right-hand sides and sample order */
+    int batch;            /* samples per Adam step (0: 2) */
 } sgiga_train_cfg;
 
 typedef struct {
     int pairs, samples, rhs, steps;
-    double loss_first_epoch, loss_last_epoch;  /* mean relative squared error of N */
+    double loss_first_epoch, loss_last_epoch;  /* mean over samples of the mean over components of
+                                                  ||M(r) - e||^2 / ||e||^2 */
     double seconds;
 } sgiga_train_stats;
 
 /* Allocate the network and initialise it (seeded Kaiming-uniform; the last
- * layer scaled by 0.05 so that the untrained M is close to FD). */
+ * layer scaled by 0.05 so that the untrained S is close to 1, M close to FD). */
 int sgiga_net_init(sgiga_plan_t plan, unsigned seed);
 /* Number of parameters (a negative status if there is no network). Layout of
- * the FP32 vector: W1 [32][2][T], b1 [32], W2 [32][32][T], b2 [32], W3 [1][32][T],
+ * the FP32 vector: W1 [32][1][T], b1 [32], W2 [32][32][T], b2 [32], W3 [1][32][T],
  * b3 [1], T = 3^d taps ordered offset_0 fastest over (-1, 0, 1)^d. */
 int sgiga_net_num_params(sgiga_plan_t plan);
 int sgiga_net_get_params(sgiga_plan_t plan, float* params /* host [nparams] */);
 int sgiga_net_set_params(sgiga_plan_t plan, const float* params /* host [nparams] */);
-/* N(in) with in = device float [2][ndof] (channel planes over the packed
- * vector), out = device float [ndof]. */
+/* N(in) with in = device float [ndof] (one channel over the packed vector),
+ * out = device float [ndof]. */
 int sgiga_net_forward(sgiga_plan_t plan, const float* in, float* out);
 /* Gradient of sum_v dy_v N(in)_v with respect to every parameter (host
- * [nparams]); in, dy device float. */
+ * [nparams]); in, dy device float [ndof]. */
 int sgiga_net_backward(sgiga_plan_t plan, const float* in, const float* dy, float* grad);
+/* The network input phi = log c of the plan's current geometry coefficients
+ * (float [ndof], host or device). */
+int sgiga_net_features(sgiga_plan_t plan, float* phi);
+/* The scaling S the preconditioner uses (float [ndof], host or device). */
+int sgiga_net_scaling(sgiga_plan_t plan, float* S);
+/* Replace S by the caller's positive values (float [ndof], host or device),
+ * bypassing the network until the next sgiga_net_init, _set_params, _load or
+ * sgiga_train_net (e.g. S = c^{-1/2}, a scaling without a network). */
+int sgiga_net_set_scaling(sgiga_plan_t plan, const float* S);
+/* Training loss of one sample at the current S, the mean over components of
+ * ||M(r) - e||^2 / ||e||^2 (*loss, host), and its gradient with respect to
+ * log S (grad, device float [ndof]); r, e device float [ndof]. */
+int sgiga_net_loss_grad(sgiga_plan_t plan, const float* r, const float* e, double* loss, float* grad);
 /* Record (residual, error) pairs from the plan's own FD-preconditioned FP64 CG
- * on seeded random right-hand sides and train N by Adam on them. Overwrites the
- * plan's load vector and solution. */
+ * on seeded random right-hand sides and train N by Adam on the loss above,
+ * back-propagated through S = exp(N(phi)). Overwrites the plan's load vector
+ * and solution. */
 int sgiga_train_net(sgiga_plan_t plan, const sgiga_train_cfg* cfg, sgiga_train_stats* stats /* may be NULL */);
-/* Checkpoint: magic "SGIGANET", version 1, taps, nparams, Adam step, then the
+/* Checkpoint: magic "SGIGANET", version 2, taps, nparams, Adam step, then the
  * FP32 parameters and both Adam moments. */
 int sgiga_net_save(sgiga_plan_t plan, const char* path);
 int sgiga_net_load(sgiga_plan_t plan, const char* path);

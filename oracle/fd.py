@@ -49,3 +49,57 @@ def fd_apply(levels, p, r, rvec, scales=None, kind="uniform", gamma=1.0, geom=No
         ax = d - 1 - k
         T = np.moveaxis(np.tensordot(eig[k][1], T, axes=([1], [ax])), 0, ax)
     return T.reshape(-1)
+
+
+def sturm_eigenvalues(K, M, js, dtype=np.longdouble, bw=None):
+    """Eigenvalues number js (ascending, 0-based) of the symmetric-definite
+    pencil (K, M) by bisection on the inertia of K - s M: by Sylvester's law of
+    inertia the number of eigenvalues below s is the number of negative pivots
+    of its LDL^T factorisation (M positive definite). Written out entry by
+    entry in `dtype` (extended precision by default) for banded K, M of
+    bandwidth bw; it forms neither M^{-1} nor a Cholesky factor of M, so graded
+    meshes (ill-conditioned M) keep their accuracy. Returns float64 values."""
+    K = np.asarray(K, dtype=dtype)
+    M = np.asarray(M, dtype=dtype)
+    n = K.shape[0]
+    if bw is None:
+        bw = max(abs(i - j) for i, j in zip(*np.nonzero(np.asarray(K, dtype=np.float64))))
+
+    eps = np.finfo(dtype).eps
+
+    def count(s):
+        A = K - s * M
+        floor = eps * eps * np.abs(A).max()
+        L = np.zeros((n, n), dtype=dtype)
+        D = np.zeros(n, dtype=dtype)
+        neg = 0
+        for i in range(n):
+            lo = max(0, i - bw)
+            for j in range(lo, i):
+                v = A[i, j] - sum(L[i, k] * D[k] * L[j, k] for k in range(max(lo, j - bw), j))
+                L[i, j] = v / D[j]
+            d = A[i, i] - sum(L[i, k] * L[i, k] * D[k] for k in range(lo, i))
+            if abs(d) < floor:
+                d = -floor
+            D[i] = d
+            neg += d < 0
+        return neg
+
+    # first bound and descent factor are no powers of 2 (a bisection point equal
+    # to some K_ii / M_ii would make a pivot vanish exactly)
+    hi = dtype(2.17) * max(K[i, i] / M[i, i] for i in range(n))
+    while count(hi) < n:
+        hi = hi * 4
+    out = []
+    for j in js:
+        lo, h = dtype(0), hi
+        while h - lo > 4 * eps * h:
+            mid = (lo + h) / 2 if lo > 0 and h < 2 * lo else (np.sqrt(lo * h) if lo > 0 else h / 7)
+            if not (lo < mid < h):
+                break
+            if count(mid) > j:
+                h = mid
+            else:
+                lo = mid
+        out.append(float((lo + h) / 2 if lo > 0 else h / 2))
+    return np.array(out)

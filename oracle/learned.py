@@ -15,9 +15,10 @@ the support of R_i, relative to the parametric Laplacian (G_q = w_q I), the
 operator the fast-diagonalisation preconditioner inverts. The network input
 is log c_i.
 
-Scaled preconditioner. With a positive scaling S (one value per DoF, the
-network's output exponentiated), M(r) = S * FD(S * r), elementwise products:
-symmetric positive definite whenever FD is.
+Scaled preconditioner. With a positive scaling S (one value per DoF, from the
+network's output y as S = exp(4 tanh(y / 4)), a smooth bound |log S| <= 4),
+M(r) = S * FD(S * r), elementwise products: symmetric positive definite
+whenever FD is.
 
 Loss of one (residual, error) pair of one component:
     L = ||M(r) - e||^2 / ||e||^2,
@@ -29,6 +30,11 @@ log S_i (FD symmetric):
 import numpy as np
 
 from . import fd
+
+
+def scaling_from_output(y):
+    """S = exp(4 tanh(y / 4)) of the network output y."""
+    return np.exp(4.0 * np.tanh(np.asarray(y, dtype=np.float64) / 4.0))
 
 
 def features(comp, diffusion=None):

@@ -8,7 +8,7 @@
 //   - the tile decomposition of every component and its launch order (largest
 //     tiles first, the greedy longest-processing-time order of Sec. 4.1);
 //   - device tables (basis, geometry coefficients) through the CUDA kernels;
-//   - the 1D generalised eigenpairs of the preconditioner (host, eig.cpp).
+//   - the 1D generalised eigenpairs of the preconditioner (on the device, eig.cu).
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -23,7 +23,6 @@
 #include "op_common.cuh"
 
 namespace sgiga {
-int generalized_eigen(int n, int bw, const double* K, const double* M, double* U, double* lam);
 }
 
 using namespace sgiga;
@@ -208,25 +207,27 @@ static void choose_tile(int d, int P, int M, const int* E, size_t budget, long l
             }
 }
 
-// 1D interior matrices of a table, from the device-computed tables.
-// 1D stiffness and mass matrices of the functions klo .. nf-2 (klo = 1: both
-// ends Dirichlet; klo = 0: natural condition at the low end).
-static void assemble_1d(int E, int Q, int p, int nf, int klo, const double* w, const double* R, const double* dR,
-                        const int* first, std::vector<double>& K, std::vector<double>& Mm) {
-    int n = nf - 1 - klo;
-    K.assign((size_t)n * n, 0.0);
-    Mm.assign((size_t)n * n, 0.0);
+// 1D interior matrices of a table, from the device-computed tables: the
+// upper bands [n][p+1] (entry (i, t) = matrix(i, i+t)) of the stiffness and
+// mass matrices of the functions klo .. klo+n-1 (klo = 1: both ends
+// Dirichlet; klo = 0: natural condition at the low end), appended to Kb, Mb.
+static void assemble_band(int E, int Q, int p, int n, int klo, const double* w, const double* R, const double* dR,
+                          const int* first, std::vector<double>& Kb, std::vector<double>& Mb) {
+    const size_t b0 = Kb.size();
+    Kb.resize(b0 + (size_t)n * (p + 1), 0.0);
+    Mb.resize(b0 + (size_t)n * (p + 1), 0.0);
     for (int e = 0; e < E; ++e)
         for (int q = 0; q < Q; ++q) {
             long long o = (long long)e * Q + q;
             for (int a = 0; a <= p; ++a) {
                 int i = first[e] + a - klo;
                 if (i < 0 || i >= n) continue;
-                for (int b = 0; b <= p; ++b) {
+                for (int b = a; b <= p; ++b) {
                     int j = first[e] + b - klo;
                     if (j < 0 || j >= n) continue;
-                    K[(size_t)i * n + j] += w[o] * dR[o * (p + 1) + a] * dR[o * (p + 1) + b];
-                    Mm[(size_t)i * n + j] += w[o] * R[o * (p + 1) + a] * R[o * (p + 1) + b];
+                    const size_t at = b0 + (size_t)i * (p + 1) + (j - i);
+                    Kb[at] += w[o] * dR[o * (p + 1) + a] * dR[o * (p + 1) + b];
+                    Mb[at] += w[o] * R[o * (p + 1) + a] * R[o * (p + 1) + b];
                 }
             }
         }
@@ -463,7 +464,12 @@ static void make_tiles(sgiga_plan_s* P, size_t budget, long long qpcap) {
     std::stable_sort(P->sched.begin(), P->sched.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
 }
 
+static double since(std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+}
+
 static int build(sgiga_plan_s* P) {
+    const auto tb0 = std::chrono::steady_clock::now();
     const sgiga_config& c = P->cfg;
     const int d = P->d, p = P->p, M = P->m, Q = P->Q;
     // index set
@@ -654,6 +660,7 @@ static int build(sgiga_plan_s* P) {
         }
     }
     make_tiles(P, 110 * 1024, 16384);
+    P->t_host = since(tb0);
     // device data
     if (c.domain == SGIGA_DOMAIN_PATCH) {
         if (!c.patch || make_user_patch(c.patch, d, P->patch) != 0)
@@ -725,6 +732,7 @@ static int build(sgiga_plan_s* P) {
         (rc = dalloc(P, &D.rho, P->nqp)))
         return rc;
     cudaStream_t s = P->stream;
+    const auto tbasis = std::chrono::steady_clock::now();
     CUDA_TRY(launch_basis_tables(D, P->maxE, s));
     // eigen tables: one per (level, rational direction or not)
     std::vector<double> hw(P->tab_entries), hR(P->tab_entries * (p + 1)), hdR(P->tab_entries * (p + 1));
@@ -734,11 +742,14 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaMemcpyAsync(hdR.data(), D.dR, hdR.size() * 8, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(hfirst.data(), D.first, hfirst.size() * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    P->t_basis = since(tbasis);
     // one eigen table per (level, rational direction or not, first kept
     // function): klo = 0 keeps the interface end (natural condition there)
     std::map<std::array<int, 3>, int> eig_key;
     std::map<std::pair<int, int>, int> eig_of;   // (table, klo) -> eigen table
-    std::vector<double> hU, hlam;
+    std::vector<EigJob> jobs;
+    std::vector<double> hKb, hMb, hlam;
+    long long ulen = 0, llen = 0;
     P->eig_of_tab.assign(P->tabs.size(), -1);
     auto eig_for = [&](int ti, int klo) -> int {
         auto f = eig_of.find(std::make_pair(ti, klo));
@@ -747,37 +758,51 @@ static int build(sgiga_plan_s* P) {
         std::array<int, 3> key = {t.level, P->patch.rational[t.dir] ? t.dir : -1, klo};
         auto it = eig_key.find(key);
         if (it != eig_key.end()) { eig_of[std::make_pair(ti, klo)] = it->second; return it->second; }
-        std::vector<double> K, Mm;
-        assemble_1d(t.E, Q, p, t.nf, klo, hw.data() + t.off, hR.data() + t.off * (p + 1),
-                    hdR.data() + t.off * (p + 1), hfirst.data() + t.eoff, K, Mm);
-        int n = t.nf - 1 - klo;
+        const int n = t.nf - 1 - klo;
         Eig1D e{};
         e.n = n;
-        e.uoff = (long long)hU.size();
-        e.loff = (long long)hlam.size();
-        hU.resize(hU.size() + (size_t)n * n);
-        hlam.resize(hlam.size() + n);
-        if (n > 0 && generalized_eigen(n, p, K.data(), Mm.data(), hU.data() + e.uoff, hlam.data() + e.loff) != 0)
-            return -1;
+        e.uoff = ulen;
+        e.loff = llen;
+        ulen += (long long)n * n;
+        llen += n;
+        if (n > 0) {
+            EigJob J{};
+            J.n = n;
+            J.boff = (long long)hKb.size();
+            J.uoff = e.uoff;
+            J.loff = e.loff;
+            assemble_band(t.E, Q, p, n, klo, hw.data() + t.off, hR.data() + t.off * (p + 1),
+                          hdR.data() + t.off * (p + 1), hfirst.data() + t.eoff, hKb, hMb);
+            jobs.push_back(J);
+        }
         const int id = (int)P->eigs.size();
         eig_key[key] = id;
         eig_of[std::make_pair(ti, klo)] = id;
         P->eigs.push_back(e);
         return id;
     };
-    for (size_t ti = 0; ti < P->tabs.size(); ++ti) {
-        int id = eig_for((int)ti, 1);
-        if (id < 0) return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed (level " +
-                                                   std::to_string(P->tabs[ti].level) + ")");
-        P->eig_of_tab[ti] = id;
-    }
+    for (size_t ti = 0; ti < P->tabs.size(); ++ti) P->eig_of_tab[ti] = eig_for((int)ti, 1);
     for (auto& g : P->grids)
-        for (int k = 0; k < 3; ++k) {
-            g.eig[k] = 0;
-            if (k >= d) continue;
-            g.eig[k] = eig_for(g.tab[k], g.klo[k]);
-            if (g.eig[k] < 0) return fail(SGIGA_ERR_ARG, "1D generalised eigenproblem failed");
-        }
+        for (int k = 0; k < 3; ++k) g.eig[k] = k < d ? eig_for(g.tab[k], g.klo[k]) : 0;
+    P->ulen = ulen;
+    P->llen = llen;
+    // the eigenpairs on the device, FP64 (eig.cu)
+    Eig1D* deig; double *dU, *dUt, *dlam;
+    if ((rc = upload(P, &deig, P->eigs)) || (rc = dalloc(P, &dU, (size_t)ulen)) ||
+        (rc = dalloc(P, &dUt, (size_t)ulen)) || (rc = dalloc(P, &dlam, (size_t)llen)))
+        return rc;
+    {
+        const auto te = std::chrono::steady_clock::now();
+        std::string msg;
+        std::vector<double> jl;
+        if (gpu_generalized_eigen(p, jobs, hKb, hMb, dU, dUt, dlam, jl, s, msg) != 0)
+            return fail(SGIGA_ERR_CUDA, "1D generalised eigenproblems: " + msg);
+        hlam.assign((size_t)llen, 0.0);
+        for (const EigJob& J : jobs)
+            std::copy(jl.begin() + J.t0, jl.begin() + J.t0 + J.n, hlam.begin() + J.loff);
+        P->t_eigen = std::chrono::duration<double>(std::chrono::steady_clock::now() - te).count();
+    }
+    const auto tfd = std::chrono::steady_clock::now();
     // preconditioner work items (grouped by eigen table)
     // default layout: grouped for FP32 (latency-bound) plans, per piece for FP64
     make_fd_items(P, 32, c.precision == SGIGA_PREC_MIXED_FP32);
@@ -798,15 +823,10 @@ static int build(sgiga_plan_s* P) {
     double* ddinv;
     if ((rc = upload(P, &ddinv, hdinv))) return rc;
     D.dinv = ddinv;
-    std::vector<double> hUt(hU.size());
-    for (const Eig1D& e : P->eigs)
-        for (int i = 0; i < e.n; ++i)
-            for (int j = 0; j < e.n; ++j) hUt[e.uoff + (size_t)j * e.n + i] = hU[e.uoff + (size_t)i * e.n + j];
-    Eig1D* deig; double *dU, *dUt, *dlam;
-    if ((rc = upload(P, &deig, P->eigs)) || (rc = upload(P, &dU, hU)) || (rc = upload(P, &dUt, hUt)) ||
-        (rc = upload(P, &dlam, hlam)) || (rc = upload(P, &dg, P->grids)))
-        return rc;
+    if ((rc = upload(P, &dg, P->grids))) return rc;
     D.eigs = deig; D.U = dU; D.Ut = dUt; D.lam = dlam; D.grids = dg;
+    P->t_fd = since(tfd);
+    const auto tgeo = std::chrono::steady_clock::now();
     if (mp) CUDA_TRY(launch_boundary_points(D, P->d_xb, s));
     // geometry coefficients
     CUDA_TRY(launch_geometry(D, s));
@@ -815,6 +835,8 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
     if ((rc = update_diag(P))) return rc;
+    P->t_geometry = since(tgeo);
+    const auto tvec = std::chrono::steady_clock::now();
     // operator kernel shared memory
     if ((rc = grant_op_smem(P))) return rc;
     // solver vectors and scalars
@@ -839,7 +861,7 @@ static int build(sgiga_plan_s* P) {
         float *Gf, *Rf, *dRf, *Uf, *Utf, *dinvf;
         const long long ntab = P->tab_entries * (p + 1);
         if ((rc = dalloc(P, &Gf, (size_t)ncomp * P->nqp)) || (rc = dalloc(P, &Rf, ntab)) ||
-            (rc = dalloc(P, &dRf, ntab)) || (rc = dalloc(P, &Uf, hU.size())) || (rc = dalloc(P, &Utf, hU.size())) ||
+            (rc = dalloc(P, &dRf, ntab)) || (rc = dalloc(P, &Uf, (size_t)ulen)) || (rc = dalloc(P, &Utf, (size_t)ulen)) ||
             (rc = dalloc(P, &dinvf, (size_t)P->nfd)) || (rc = dalloc(P, &P->f_b, nd)) || (rc = dalloc(P, &P->f_x, nd)) ||
             (rc = dalloc(P, &P->f_r, nd)) || (rc = dalloc(P, &P->f_z, nd)) || (rc = dalloc(P, &P->f_p, nd)) ||
             (rc = dalloc(P, &P->f_q, nd)) || (rc = dalloc(P, &P->f_t1, nt)) || (rc = dalloc(P, &P->f_t2, nt)) ||
@@ -850,12 +872,14 @@ static int build(sgiga_plan_s* P) {
         CUDA_TRY(launch_narrow(Gf, D.G, (long long)ncomp * P->nqp, s));
         CUDA_TRY(launch_narrow(Rf, D.R, ntab, s));
         CUDA_TRY(launch_narrow(dRf, D.dR, ntab, s));
-        CUDA_TRY(launch_narrow(Uf, D.U, (long long)hU.size(), s));
-        CUDA_TRY(launch_narrow(Utf, D.Ut, (long long)hU.size(), s));
+        CUDA_TRY(launch_narrow(Uf, D.U, ulen, s));
+        CUDA_TRY(launch_narrow(Utf, D.Ut, ulen, s));
         CUDA_TRY(launch_narrow(dinvf, D.dinv, P->nfd, s));
         D.Gf = Gf; D.Rf = Rf; D.dRf = dRf; D.Uf = Uf; D.Utf = Utf; D.dinvf = dinvf;
     }
     CUDA_TRY(cudaStreamSynchronize(s));
+    P->t_vectors = since(tvec);
+    P->t_total = since(tb0);
     return SGIGA_OK;
 }
 
@@ -887,6 +911,7 @@ static int retile(sgiga_plan_s* P, size_t budget, long long qpcap) {
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(D.Gf, D.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    net_invalidate_features(P);
     return update_diag(P);
 }
 
@@ -1182,6 +1207,7 @@ int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
 
 int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const double* phase, double amp) {
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    const auto t0 = std::chrono::steady_clock::now();
     if (nfeat < 0 || (nfeat > 0 && (!omega || !phase))) return fail(SGIGA_ERR_ARG, "bad coefficient features");
     cudaStream_t s = P->stream;
     const int d = P->d;
@@ -1205,7 +1231,10 @@ int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const 
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    return update_diag(P);
+    net_invalidate_features(P);
+    const int rc = update_diag(P);
+    P->t_coefficient = since(t0);
+    return rc;
 }
 
 int sgiga_get_rhs(sgiga_plan_t P, double* b) {
@@ -1249,6 +1278,7 @@ int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
 
 int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
+    const auto tt0 = std::chrono::steady_clock::now();
     struct Cand { size_t budget; long long qpcap; };
     const Cand cands[] = {{48 * 1024, 4096}, {48 * 1024, 16384}, {110 * 1024, 8192},
                           {110 * 1024, 16384}, {200 * 1024, 16384}, {200 * 1024, 32768}};
@@ -1327,6 +1357,21 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         }
         out->fd_nitems = (int)items;
     }
+    P->t_autotune = since(tt0);
+    return SGIGA_OK;
+}
+
+int sgiga_plan_times(sgiga_plan_t P, sgiga_plan_times_t* out) {
+    if (!P || !out) return fail(SGIGA_ERR_ARG, "null argument");
+    out->total = P->t_total;
+    out->host = P->t_host;
+    out->basis = P->t_basis;
+    out->eigen = P->t_eigen;
+    out->fd = P->t_fd;
+    out->geometry = P->t_geometry;
+    out->vectors = P->t_vectors;
+    out->coefficient = P->t_coefficient;
+    out->autotune = P->t_autotune;
     return SGIGA_OK;
 }
 
@@ -1373,6 +1418,7 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     int nact = ng, outer = 0, inner_total = 0, stalls = 0;
     bool fp64_fallback = false;
     P->learned_off = false;
+    if (int rc0 = learned_prepare(P)) return rc0;
     double prev_worst = 0.0;
     std::vector<double> hrr(ng), hbb(ng), prev_rr(ng, 0.0);
     std::vector<int> hact(ng);
@@ -1427,7 +1473,7 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
         }
         if (P->cfg.precond == SGIGA_PRECOND_LEARNED) {
             // fall back to FD for the rest of the solve when a refinement step
-            // with the learned preconditioner does not cut the worst residual by 10
+            // with the learned scaling does not cut the worst residual by 10
             double worst = 0.0;
             for (int g = 0; g < ng; ++g)
                 if (hbb[g] > 0) worst = std::max(worst, std::sqrt(hrr[g] / hbb[g]));
@@ -1436,40 +1482,9 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
         }
         CUDA_TRY(launch_ir_down(D, P->d_r, P->f_b, P->d_active_o, s));
         int inner = 0;
-        // With the learned correction, the inner flexible CG must cut its
-        // residual 100x within 16 iterations (FD-preconditioned CG does on
-        // these systems); otherwise that inner solve stops there and FD takes
-        // over for the rest of the solve.
-        struct ProgressHook : PcgHook {
-            sgiga_plan_s* P;
-            int ng;
-            int after_iteration(int it) override {
-                if (it + 1 != 16 || P->learned_off) return 0;
-                std::vector<double> rr(ng), bb(ng);
-                std::vector<int> act(ng);
-                cudaStream_t st = P->stream;
-                if (cudaMemcpyAsync(rr.data(), P->d_scal + 3 * ng, ng * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                    cudaMemcpyAsync(bb.data(), P->d_scal, ng * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                    cudaMemcpyAsync(act.data(), P->d_active, ng * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                    cudaStreamSynchronize(st) != cudaSuccess)
-                    return fail(SGIGA_ERR_CUDA, "progress check failed");
-                double worst = 0.0;
-                for (int g = 0; g < ng; ++g)
-                    if (act[g] && bb[g] > 0) worst = std::max(worst, std::sqrt(rr[g] / bb[g]));
-                if (worst > 1e-2) {
-                    P->learned_off = true;
-                    return 1;   // stop this inner solve (not an error)
-                }
-                return 0;
-            }
-        } hook;
-        hook.P = P;
-        hook.ng = ng;
-        const bool watch = P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready && !P->learned_off;
         int rc = pcg<float>(P, P->f_b, vecs32(P), P->inner_tol, P->inner_max, P->d_active_o, P->d_active,
-                            P->d_iters, P->d_scal, &inner, watch ? &hook : nullptr);
+                            P->d_iters, P->d_scal, &inner);
         if (rc < 0) return rc;
-        if (watch && P->learned_off) inner = 16;
         inner_total += inner;
         CUDA_TRY(launch_ir_up(D, P->d_x, P->f_x, P->d_active_o, s));
         if ((rc = apply_op(P, P->d_x, P->d_q, P->d_active_o))) return rc;

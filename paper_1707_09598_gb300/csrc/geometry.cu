@@ -300,6 +300,38 @@ cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaS
     return cudaGetLastError();
 }
 
+// Densities of the learned scaling's features at every quadrature point
+// (tile-major, the layout of rho): mode 0 the trace of G_q (its diagonal
+// planes; the trace does not depend on the tile's axis order), mode 1 d times
+// the parametric Gauss weight w_q. Their load vectors give
+// c_i = sum_q R_i tr(G_q) / (d sum_q R_i w_q).
+__global__ void k_feature_density(DevPlan P, double* __restrict__ out, int mode) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        const long long o = t.g_off + idx;
+        double v;
+        if (mode == 0) {
+            v = d == 3 ? P.G[o] + P.G[3 * P.nqp + o] + P.G[5 * P.nqp + o] : P.G[o] + P.G[2 * P.nqp + o];
+        } else {
+            QpLoc L = tile_qp(g, t, d, Q, idx);
+            double xi[3], wq;
+            qp_param(P, g, L, xi, wq);
+            v = d * wq;
+        }
+        out[o] = v;
+    }
+}
+
+cudaError_t launch_feature_density(const DevPlan& P, double* out, int mode, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_feature_density<<<P.ntiles, 256, 0, s>>>(P, out, mode);
+    return cudaGetLastError();
+}
+
 // Copy one grid's G (physical component order) and mw into natural order.
 __global__ void k_geometry_natural(DevPlan P, int tile0, double* Gnat, double* mwnat) {
     const TileDesc t = P.tiles[tile0 + blockIdx.x];

@@ -88,6 +88,19 @@ struct Eig1D {
     long long loff;     // lambda [n] at loff
 };
 
+// One 1D generalised eigenproblem of the GPU eigensolver (eig.cu): n interior
+// functions; band arrays Kb, Mb [n][p+1] with Kb[i][t] = K(i, i+t) (zero past
+// the end) at boff; outputs at uoff (U and U^T, n x n) and loff (lam, n).
+struct EigJob {
+    int n;
+    long long boff;
+    long long uoff;
+    long long loff;
+    long long t0;          // first global thread of the job (bisection)
+    double hi0;            // first upper bound tried for the eigenvalues: 2.17 max_i K_ii / M_ii
+    double anorm;          // max_i sum_t |K_it| + hi0 |M_it|: the scale of K - s M's entries
+};
+
 // Vector chunk: a contiguous piece of one component's packed vector (or of
 // one piece's preconditioner tensor); grid = the component (scalar slot).
 struct Chunk {

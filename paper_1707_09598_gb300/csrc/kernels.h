@@ -3,6 +3,8 @@
 #include "internal.h"
 
 #include <atomic>
+#include <string>
+#include <vector>
 
 namespace sgiga {
 
@@ -77,6 +79,10 @@ cudaError_t launch_eval_grad(const DevPlan& P, const double* coeffs, const doubl
                              long long npts, double* ucomp, double* gcomp, int lifting, cudaStream_t s);
 // basis.cu
 cudaError_t launch_basis_tables(const DevPlan& P, int maxE, cudaStream_t s);
+// eig.cu: eigenpairs of every job on the device (0, or -1 with msg set)
+int gpu_generalized_eigen(int p, std::vector<EigJob>& jobs, const std::vector<double>& Kb,
+                          const std::vector<double>& Mb, double* dU, double* dUt, double* dlam,
+                          std::vector<double>& hlam, cudaStream_t s, std::string& msg);
 // geometry.cu
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
 cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s);
@@ -86,6 +92,8 @@ cudaError_t launch_map_points(const DevPlan& P, const double* xi, const int* pat
 cudaError_t launch_rhs_density_builtin(const DevPlan& P, int source, cudaStream_t s);
 cudaError_t launch_source_qp(const DevPlan& P, int source, double* fout, cudaStream_t s);
 cudaError_t launch_rhs_density_user(const DevPlan& P, const double* f_nat, cudaStream_t s);
+// learned-scaling features: mode 0 writes tr(G_q), mode 1 d w_q (tile-major)
+cudaError_t launch_feature_density(const DevPlan& P, double* out, int mode, cudaStream_t s);
 cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh, double* Gnat,
                                     double* mwnat, cudaStream_t s);
 // apply2.cu / apply3.cu: mode 0 = stiffness apply y += K x, mode 1 = load vector y += b
@@ -145,23 +153,26 @@ cudaError_t launch_zero_active(const DevPlan& P, double* x, const int* active, c
 cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
                                double* partial, double* rr, cudaStream_t s);
 cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);
-// net.cu (learned correction network)
+// net.cu (learned scaling network) and learned.cu
 cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, const float* bias, const float* X,
                         float* Y, int transpose, int relu, cudaStream_t s);
 cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, const float* dZ, float* dW, float* db,
                          cudaStream_t s);
 cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s);
-cudaError_t launch_scale_grid(const DevPlan& P, float* x, const double* scale, int nch, int invert, cudaStream_t s);
-cudaError_t launch_net_candidate(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
-                                 float* cand, cudaStream_t s);
-cudaError_t launch_net_select(const DevPlan& P, const float* z, const float* cand, const int* ok, const double* rz,
-                              const double* rc, float* out, const int* active, cudaStream_t s);
-cudaError_t launch_loss(const float* y, const float* t, long long n, double* acc, float* dy, cudaStream_t s);
+cudaError_t launch_log_ratio(const double* num, const double* den, float* out, long long n, cudaStream_t s);
+cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s);
+cudaError_t launch_mul_active(const DevPlan& P, const float* S, const float* in, float* out, const int* active,
+                              cudaStream_t s);
+cudaError_t launch_pair_residual(const DevPlan& P, const float* S, const float* z1, const float* e, float* res,
+                                 cudaStream_t s);
+cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res, const double* rr, const double* ee,
+                              float* delta, float* t2, double* lossacc, cudaStream_t s);
+cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delta, const float* z1, const float* r,
+                             const float* z2, float weight, float* dls, cudaStream_t s);
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, const int* wmap, int n, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);
 cudaError_t launch_f2bf(const float* p, const int* wmap, void* wb, int n, cudaStream_t s);
-cudaError_t launch_rms(const DevPlan& P, const double* dots, double* rms, cudaStream_t s);
-cudaError_t launch_target(const DevPlan& P, const float* e, const float* z, const double* sz, float* t, cudaStream_t s);
 cudaError_t launch_pair_store(const DevPlan& P, const double* r, const double* xstar, const double* x, float* rd,
                               float* ed, cudaStream_t s);
 

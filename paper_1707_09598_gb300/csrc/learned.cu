@@ -1,16 +1,26 @@
-// Host side of the learned correction network: parameters, the learned
-// preconditioner used by flexible CG, training-data generation from the
-// solver's own CG iterates, the training loop (the library's forward,
-// backward and Adam kernels), checkpoints, and the C ABI entry points.
+// Host side of the learned scaling of the fast-diagonalisation preconditioner:
+// features, the network's parameters, the scaled preconditioner used by the
+// inner FP32 flexible CG, training-data generation from the solver's own CG
+// iterates, the training loop (the library's forward, backward and Adam
+// kernels), checkpoints, and the C ABI entry points.
+//
+// Preconditioner: M(r) = S * FD(S * r) (elementwise products),
+// S = exp(4 tanh(N(phi) / 4)) (a smooth bound |log S| <= 4),
+// phi_i = log c_i with c_i the local effective coefficient of DoF i,
+//   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
+// the R_i-weighted mean of the trace of the Galerkin metric G_q relative to the
+// parametric Laplacian (G_q = w_q I) that FD inverts exactly. S depends only on
+// the operator, so M is a fixed symmetric positive definite operator: the
+// network runs once per plan (and once per training step), not per iteration.
 //
 // Pairs. For a right-hand side b the FP64 FD-preconditioned CG is run twice:
 // once to convergence for x*, once more recording after every iteration k the
 // residual r_k and the error e_k = x* - x_k of every component. One recorded
 // iteration is one training sample (all components at once).
 //
-// Loss of a sample: sum_v (N_v - t_v)^2 / sum_v t_v^2 with the target
-// t = (e - FD(r)) / s_z, i.e. the part of the error that FD misses, in the
-// network's per-component scale.
+// Loss of a sample: the mean over components of ||M(r) - e||^2 / ||e||^2; its
+// gradient with respect to log S_i is S_i (delta_i FD(S r)_i + r_i FD(S delta)_i)
+// with delta = 2 (M(r) - e) / (||e||^2 ncomp) (FD symmetric).
 #include <cstdio>
 #include <random>
 
@@ -22,28 +32,32 @@ struct Net {
     int T = 0, np = 0, nw = 0;
     long long N = 0;
     long long oW[3], ob[3], obw[3];   // offsets of W_l and b_l in p; of W_l in the BF16 copy
-    int cin[3] = {2, 32, 32}, cout[3] = {32, 32, 1};
+    int cin[3] = {1, 32, 32}, cout[3] = {32, 32, 1};
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     void* wb = nullptr;               // BF16 weights
     int* wmap = nullptr;
     int step = 0;
     float *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *Y = nullptr, *dY = nullptr, *dA1 = nullptr, *dA2 = nullptr;
-    float *zfd = nullptr, *tgt = nullptr;
-    double *sr = nullptr, *sz = nullptr, *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr;
+    float *feat = nullptr;            // phi = log c (the network input)
+    float *S = nullptr;               // scaling of the preconditioner
+    float *tA = nullptr, *z1 = nullptr, *z2 = nullptr, *res = nullptr, *delta = nullptr;
+    double *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr;
     int* ok = nullptr;
+    bool feat_stale = true;           // the geometry planes changed since phi was computed
+    bool s_stale = true;              // S must be recomputed from the network
+    bool s_override = false;          // S was set by the caller (no network evaluation)
     float* data = nullptr;            // training pairs [S][2][N]
     int nsamples = 0, capacity = 0;
     std::vector<void*> allocs;
 };
 
-static int nalloc(sgiga_plan_s* P, Net* n, void** out, size_t bytes) {
+static int nalloc(Net* n, void** out, size_t bytes) {
     cudaError_t e = cudaMalloc(out, std::max<size_t>(bytes, 16));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(SGIGA_ERR_NOMEM, "network buffer allocation failed (" + std::to_string(bytes) + " bytes)");
     }
     n->allocs.push_back(*out);
-    (void)P;
     return SGIGA_OK;
 }
 
@@ -53,6 +67,13 @@ void free_net(sgiga_plan_s* P) {
     delete P->net;
     P->net = nullptr;
     P->net_ready = false;
+}
+
+void net_invalidate_features(sgiga_plan_s* P) {
+    if (P && P->net) {
+        P->net->feat_stale = true;
+        if (!P->net->s_override) P->net->s_stale = true;
+    }
 }
 
 static int net_create(sgiga_plan_s* P) {
@@ -73,18 +94,20 @@ static int net_create(sgiga_plan_s* P) {
     }
     n->np = (int)o;
     n->nw = (int)ow;
-    const size_t N = (size_t)n->N, ng = P->grids.size();
+    const size_t N = (size_t)n->N, ng = P->comps.size();
     int rc;
-    if ((rc = nalloc(P, n, (void**)&n->p, n->np * 4)) || (rc = nalloc(P, n, (void**)&n->g, n->np * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->m, n->np * 4)) || (rc = nalloc(P, n, (void**)&n->v, n->np * 4)) ||
-        (rc = nalloc(P, n, &n->wb, n->nw * 2)) || (rc = nalloc(P, n, (void**)&n->wmap, n->np * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->A0, 2 * N * 4)) || (rc = nalloc(P, n, (void**)&n->A1, 32 * N * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->A2, 32 * N * 4)) || (rc = nalloc(P, n, (void**)&n->Y, N * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->dY, N * 4)) || (rc = nalloc(P, n, (void**)&n->dA1, 32 * N * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->dA2, 32 * N * 4)) || (rc = nalloc(P, n, (void**)&n->zfd, N * 4)) ||
-        (rc = nalloc(P, n, (void**)&n->tgt, N * 4)) || (rc = nalloc(P, n, (void**)&n->sr, ng * 8)) ||
-        (rc = nalloc(P, n, (void**)&n->sz, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots, ng * 8)) || (rc = nalloc(P, n, (void**)&n->dots2, ng * 8)) ||
-        (rc = nalloc(P, n, (void**)&n->lossacc, 16)) || (rc = nalloc(P, n, (void**)&n->ok, ng * 4)))
+    void** bufs1[] = {(void**)&n->A0, (void**)&n->Y, (void**)&n->dY, (void**)&n->feat, (void**)&n->S,
+                      (void**)&n->tA, (void**)&n->z1, (void**)&n->z2, (void**)&n->res, (void**)&n->delta};
+    for (void** b : bufs1)
+        if ((rc = nalloc(n, b, N * 4))) return rc;
+    void** bufs32[] = {(void**)&n->A1, (void**)&n->A2, (void**)&n->dA1, (void**)&n->dA2};
+    for (void** b : bufs32)
+        if ((rc = nalloc(n, b, 32 * N * 4))) return rc;
+    if ((rc = nalloc(n, (void**)&n->p, n->np * 4)) || (rc = nalloc(n, (void**)&n->g, n->np * 4)) ||
+        (rc = nalloc(n, (void**)&n->m, n->np * 4)) || (rc = nalloc(n, (void**)&n->v, n->np * 4)) ||
+        (rc = nalloc(n, &n->wb, n->nw * 2)) || (rc = nalloc(n, (void**)&n->wmap, n->np * 4)) ||
+        (rc = nalloc(n, (void**)&n->dots, ng * 8)) || (rc = nalloc(n, (void**)&n->dots2, ng * 8)) ||
+        (rc = nalloc(n, (void**)&n->lossacc, 16)) || (rc = nalloc(n, (void**)&n->ok, ng * 4)))
         return rc;
     std::vector<int> wmap(n->np, -1);
     for (int l = 0; l < 3; ++l) {
@@ -95,22 +118,63 @@ static int net_create(sgiga_plan_s* P) {
     return SGIGA_OK;
 }
 
+// phi = log c on the device: two load-vector launches (transposed sum
+// factorisation, the load vector's kernel) with the densities tr(G_q) and
+// d w_q, then their log ratio.
+static int net_features(sgiga_plan_s* P) {
+    Net* n = P->net;
+    if (!n->feat_stale) return SGIGA_OK;
+    cudaStream_t s = P->stream;
+    const size_t nd = (size_t)P->ndof;
+    double *rho = nullptr, *num = nullptr, *den = nullptr;
+    if (cudaMalloc(&rho, (size_t)P->nqp * 8) != cudaSuccess || cudaMalloc(&num, nd * 8) != cudaSuccess ||
+        cudaMalloc(&den, nd * 8) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(rho);
+        cudaFree(num);
+        return fail(SGIGA_ERR_NOMEM, "feature buffers");
+    }
+    DevPlan D = P->dp;
+    D.rho = rho;
+    int rc = SGIGA_OK;
+    for (int mode = 0; mode < 2 && rc == SGIGA_OK; ++mode) {
+        double* out = mode == 0 ? num : den;
+        cudaError_t e = launch_feature_density(D, rho, mode, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, nd * 8, s);
+        if (e == cudaSuccess) e = P->d == 3 ? launch_op3(D, nullptr, out, nullptr, 1, s)
+                                            : launch_op2(D, nullptr, out, nullptr, 1, s);
+        if (e != cudaSuccess) rc = fail(SGIGA_ERR_CUDA, std::string("features: ") + cudaGetErrorString(e));
+    }
+    if (rc == SGIGA_OK) {
+        cudaError_t e = launch_log_ratio(num, den, n->feat, P->ndof, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(SGIGA_ERR_CUDA, std::string("features: ") + cudaGetErrorString(e));
+    }
+    cudaFree(rho);
+    cudaFree(num);
+    cudaFree(den);
+    if (rc == SGIGA_OK) n->feat_stale = false;
+    return rc;
+}
+
 static int net_upload(sgiga_plan_s* P, const std::vector<float>& host) {
     Net* n = P->net;
     CUDA_TRY(cudaMemcpy(n->p, host.data(), n->np * 4, cudaMemcpyHostToDevice));
     CUDA_TRY(launch_f2bf(n->p, n->wmap, n->wb, n->np, P->stream));
     CUDA_TRY(cudaStreamSynchronize(P->stream));
+    n->s_stale = true;
+    n->s_override = false;
     return SGIGA_OK;
 }
 
 static const void* wl(const Net* n, int l) { return (const char*)n->wb + n->obw[l] * 2; }
 
-// forward: A0 (2 channels) -> A1 -> A2 -> Y
+// forward: A0 (1 channel) -> A1 -> A2 -> Y
 static int net_forward(sgiga_plan_s* P) {
     Net* n = P->net;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    CUDA_TRY(launch_conv(D, 2, 32, wl(n, 0), n->p + n->ob[0], n->A0, n->A1, 0, 1, s));
+    CUDA_TRY(launch_conv(D, 1, 32, wl(n, 0), n->p + n->ob[0], n->A0, n->A1, 0, 1, s));
     CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), n->p + n->ob[1], n->A1, n->A2, 0, 1, s));
     CUDA_TRY(launch_conv(D, 32, 1, wl(n, 2), n->p + n->ob[2], n->A2, n->Y, 0, 0, s));
     return SGIGA_OK;
@@ -129,41 +193,65 @@ static int net_backward(sgiga_plan_s* P) {
     CUDA_TRY(launch_wgrad(D, 32, 32, n->A1, n->dA2, n->g + n->oW[1], n->g + n->ob[1], s));
     CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), nullptr, n->dA2, n->dA1, 1, 0, s));
     CUDA_TRY(launch_relu_mask(n->dA1, n->A1, 32 * N, s));
-    CUDA_TRY(launch_wgrad(D, 2, 32, n->A0, n->dA1, n->g + n->oW[0], n->g + n->ob[0], s));
+    CUDA_TRY(launch_wgrad(D, 1, 32, n->A0, n->dA1, n->g + n->oW[0], n->g + n->ob[0], s));
     return SGIGA_OK;
 }
 
-// A0 = [r / s_r, z / s_z] with z = FD(r) (into n->zfd), s_* per component
-static int net_inputs(sgiga_plan_s* P, const float* r, const int* active) {
+// S = exp(N(phi)); a component whose network output is not finite keeps S = 1
+// there (plain FD for that component).
+static int net_scaling(sgiga_plan_s* P) {
     Net* n = P->net;
-    const DevPlan& D = P->dp;
-    cudaStream_t s = P->stream;
-    const long long N = n->N;
-    int rc = precond_fd<float>(P, r, n->zfd, active, P->f_t1, P->f_t2);
-    if (rc) return rc;
-    CUDA_TRY(launch_dot<float>(D, r, r, P->d_partial, n->dots, s));
-    CUDA_TRY(launch_rms(D, n->dots, n->sr, s));
-    CUDA_TRY(launch_dot<float>(D, n->zfd, n->zfd, P->d_partial, n->dots, s));
-    CUDA_TRY(launch_rms(D, n->dots, n->sz, s));
-    CUDA_TRY(launch_copy<float>(n->A0, r, N, s));
-    CUDA_TRY(launch_copy<float>(n->A0 + N, n->zfd, N, s));
-    CUDA_TRY(launch_scale_grid(D, n->A0, n->sr, 1, 1, s));
-    CUDA_TRY(launch_scale_grid(D, n->A0 + N, n->sz, 1, 1, s));
+    int rc;
+    if ((rc = net_features(P))) return rc;
+    CUDA_TRY(launch_copy<float>(n->A0, n->feat, n->N, P->stream));
+    if ((rc = net_forward(P))) return rc;
+    CUDA_TRY(launch_exp_scaling(P->dp, n->Y, n->ok, n->S, P->stream));
     return SGIGA_OK;
+}
+
+static int ensure_scaling(sgiga_plan_s* P) {
+    Net* n = P->net;
+    if (!n || n->s_override || !n->s_stale) return SGIGA_OK;
+    int rc = net_scaling(P);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    n->s_stale = false;
+    return SGIGA_OK;
+}
+
+int learned_prepare(sgiga_plan_s* P) {
+    if (P->cfg.precond != SGIGA_PRECOND_LEARNED || !P->net_ready) return SGIGA_OK;
+    return ensure_scaling(P);
 }
 
 int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active) {
     Net* n = P->net;
     if (P->learned_off) return precond_fd<float>(P, r, z, active, P->f_t1, P->f_t2);
-    int rc = net_inputs(P, r, active);
-    if (rc) return rc;
-    if ((rc = net_forward(P))) return rc;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    CUDA_TRY(launch_net_candidate(D, n->zfd, n->Y, n->sz, n->ok, n->tgt, s));
-    CUDA_TRY(launch_dot<float>(D, r, n->zfd, P->d_partial, n->dots, s));
-    CUDA_TRY(launch_dot<float>(D, r, n->tgt, P->d_partial, n->dots2, s));
-    CUDA_TRY(launch_net_select(D, n->zfd, n->tgt, n->ok, n->dots, n->dots2, z, active, s));
+    CUDA_TRY(launch_mul_active(D, n->S, r, n->tA, active, s));
+    int rc = precond_fd<float>(P, n->tA, z, active, P->f_t1, P->f_t2);
+    if (rc) return rc;
+    CUDA_TRY(launch_mul_active(D, n->S, z, z, active, s));
+    return SGIGA_OK;
+}
+
+// Loss of the pair (r, e) at the current S (accumulated into n->lossacc[0]
+// as the mean over components) and its gradient with respect to log S added
+// to dls scaled by `weight`.
+static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, float* dls, float weight) {
+    Net* n = P->net;
+    const DevPlan& D = P->dp;
+    cudaStream_t s = P->stream;
+    int rc;
+    CUDA_TRY(launch_mul_active(D, n->S, r, n->tA, nullptr, s));
+    if ((rc = precond_fd<float>(P, n->tA, n->z1, nullptr, P->f_t1, P->f_t2))) return rc;
+    CUDA_TRY(launch_pair_residual(D, n->S, n->z1, e, n->res, s));          // res = S z1 - e
+    CUDA_TRY(launch_dot<float>(D, n->res, n->res, P->d_partial, n->dots, s));
+    CUDA_TRY(launch_dot<float>(D, e, e, P->d_partial, n->dots2, s));
+    CUDA_TRY(launch_pair_delta(D, n->S, n->res, n->dots, n->dots2, n->delta, n->tA, n->lossacc, s));
+    if ((rc = precond_fd<float>(P, n->tA, n->z2, nullptr, P->f_t1, P->f_t2))) return rc;
+    CUDA_TRY(launch_pair_grad(D, n->S, n->delta, n->z1, r, n->z2, weight, dls, s));
     return SGIGA_OK;
 }
 
@@ -173,7 +261,6 @@ struct RecordHook : PcgHook {
     const double* xstar;
     int limit;
     int after_iteration(int it) override {
-        (void)it;
         Net* n = P->net;
         if (n->nsamples >= n->capacity || it >= limit) return 0;
         float* rd = n->data + (size_t)n->nsamples * 2 * n->N;
@@ -184,6 +271,14 @@ struct RecordHook : PcgHook {
     }
 };
 
+static int needs_net(sgiga_plan_t P) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32)
+        return fail(SGIGA_ERR_ARG, "the network needs a SGIGA_PREC_MIXED_FP32 plan (FP32 preconditioner data)");
+    if (P->multipatch) return fail(SGIGA_ERR_ARG, "the learned preconditioner needs a single-patch domain");
+    return SGIGA_OK;
+}
+
 }  // namespace sgiga
 
 using namespace sgiga;
@@ -191,17 +286,15 @@ using namespace sgiga;
 extern "C" {
 
 int sgiga_net_init(sgiga_plan_t P, unsigned seed) {
-    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
-    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32)
-        return fail(SGIGA_ERR_ARG, "the network needs a SGIGA_PREC_MIXED_FP32 plan (FP32 preconditioner data)");
-    int rc = net_create(P);
+    int rc = needs_net(P);
     if (rc) return rc;
+    if ((rc = net_create(P))) return rc;
     Net* n = P->net;
     std::mt19937_64 rng(seed);
     std::vector<float> h(n->np, 0.0f);
     for (int l = 0; l < 3; ++l) {
         // Kaiming-uniform for ReLU layers; the last layer starts small so that
-        // the untrained correction is close to zero (M close to FD)
+        // the untrained S is close to 1 (M close to FD)
         const double fan = (double)n->cin[l] * n->T;
         const double b = std::sqrt(6.0 / fan) * (l == 2 ? 0.05 : 1.0);
         std::uniform_real_distribution<double> U(-b, b);
@@ -237,7 +330,7 @@ int sgiga_net_forward(sgiga_plan_t P, const float* in, float* out) {
     if (!P || !P->net || !in || !out) return fail(SGIGA_ERR_ARG, "no network or null argument");
     if (!is_device(in) || !is_device(out)) return fail(SGIGA_ERR_ARG, "in and out must be device buffers");
     Net* n = P->net;
-    CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
+    CUDA_TRY(launch_copy<float>(n->A0, in, n->N, P->stream));
     int rc = net_forward(P);
     if (rc) return rc;
     CUDA_TRY(launch_copy<float>(out, n->Y, n->N, P->stream));
@@ -249,33 +342,87 @@ int sgiga_net_backward(sgiga_plan_t P, const float* in, const float* dy, float* 
     if (!P || !P->net || !in || !dy || !grad_host) return fail(SGIGA_ERR_ARG, "no network or null argument");
     if (!is_device(in) || !is_device(dy)) return fail(SGIGA_ERR_ARG, "in and dy must be device buffers");
     Net* n = P->net;
-    CUDA_TRY(launch_copy<float>(n->A0, in, 2 * n->N, P->stream));
+    CUDA_TRY(launch_copy<float>(n->A0, in, n->N, P->stream));
     int rc = net_forward(P);
     if (rc) return rc;
     CUDA_TRY(launch_copy<float>(n->dY, dy, n->N, P->stream));
     if ((rc = net_backward(P))) return rc;
     CUDA_TRY(cudaMemcpyAsync(grad_host, n->g, n->np * 4, cudaMemcpyDeviceToHost, P->stream));
     CUDA_TRY(cudaStreamSynchronize(P->stream));
+    // the activations no longer belong to the features
+    n->s_stale = !n->s_override;
+    return SGIGA_OK;
+}
+
+int sgiga_net_features(sgiga_plan_t P, float* phi) {
+    int rc = needs_net(P);
+    if (rc) return rc;
+    if (!phi) return fail(SGIGA_ERR_ARG, "null argument");
+    if ((rc = net_create(P)) || (rc = net_features(P))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(phi, P->net->feat, (size_t)P->ndof * 4, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_net_scaling(sgiga_plan_t P, float* S) {
+    if (!P || !P->net || !P->net_ready || !S) return fail(SGIGA_ERR_ARG, "no network or null argument");
+    int rc = ensure_scaling(P);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(S, P->net->S, (size_t)P->ndof * 4, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
+int sgiga_net_set_scaling(sgiga_plan_t P, const float* S) {
+    int rc = needs_net(P);
+    if (rc) return rc;
+    if (!S) return fail(SGIGA_ERR_ARG, "null argument");
+    if ((rc = net_create(P))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(P->net->S, S, (size_t)P->ndof * 4, cudaMemcpyDefault, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    P->net->s_override = true;
+    P->net->s_stale = false;
+    P->net_ready = true;
+    return SGIGA_OK;
+}
+
+int sgiga_net_loss_grad(sgiga_plan_t P, const float* r, const float* e, double* loss, float* grad) {
+    if (!P || !P->net || !P->net_ready || !r || !e || !loss || !grad)
+        return fail(SGIGA_ERR_ARG, "no network or null argument");
+    if (!is_device(r) || !is_device(e) || !is_device(grad))
+        return fail(SGIGA_ERR_ARG, "r, e and grad must be device buffers");
+    int rc = ensure_scaling(P);
+    if (rc) return rc;
+    Net* n = P->net;
+    cudaStream_t s = P->stream;
+    CUDA_TRY(cudaMemsetAsync(n->lossacc, 0, 16, s));
+    CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)P->ndof * 4, s));
+    if ((rc = pair_loss_grad(P, r, e, grad, 1.0f))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(loss, n->lossacc, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
     return SGIGA_OK;
 }
 
 int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stats* stats) {
     if (!P || !cfg) return fail(SGIGA_ERR_ARG, "null argument");
-    if (!P->net_ready) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
-    if (cfg->target_pairs < 1 || cfg->epochs < 1 || !(cfg->lr > 0)) return fail(SGIGA_ERR_ARG, "bad training config");
+    if (!P->net_ready || !P->net) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
+    if (cfg->target_pairs < 1 || cfg->epochs < 1 || !(cfg->lr > 0) || cfg->batch < 0)
+        return fail(SGIGA_ERR_ARG, "bad training config");
     auto t0 = std::chrono::steady_clock::now();
     Net* n = P->net;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const int ng = (int)P->grids.size();
+    const int ng = (int)P->comps.size();
     const long long N = n->N;
-    // 1. data: samples of all components, ceil(target_pairs / ngrids) of them
+    int rc;
+    if ((rc = net_features(P))) return rc;
+    // 1. data: samples of all components, ceil(target_pairs / ncomponents) of them
     const int S = (cfg->target_pairs + ng - 1) / ng;
     if (n->capacity < S) {
         if (n->data) { cudaFree(n->data); n->allocs.erase(std::find(n->allocs.begin(), n->allocs.end(), (void*)n->data)); }
         n->data = nullptr;
-        int rc = nalloc(P, n, (void**)&n->data, (size_t)S * 2 * N * 4);
-        if (rc) return rc;
+        n->capacity = 0;
+        if ((rc = nalloc(n, (void**)&n->data, (size_t)S * 2 * N * 4))) return rc;
         n->capacity = S;
     }
     n->nsamples = 0;
@@ -286,7 +433,6 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     std::normal_distribution<double> gauss(0.0, 1.0);
     const int per_rhs = std::max(1, cfg->max_iter_record);
     int nrhs = 0;
-    int rc = SGIGA_OK;
     const int saved_precond = P->cfg.precond;
     P->cfg.precond = SGIGA_PRECOND_FD;    // data come from plain FD-preconditioned CG
     while (n->nsamples < S && nrhs < 10000) {
@@ -314,38 +460,64 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     cudaFree(xstar);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(P->d_b, 0, N * 8, s));   // the load vector was overwritten
-    // 2. training
+    // 2. training: minibatches of `batch` samples, one network evaluation and
+    // one Adam step per minibatch; the learning rate ramps up linearly over the
+    // first 50 steps (Adam's first steps move every weight by about lr in the
+    // same direction); the parameters of the epoch with the lowest mean loss
+    // are kept
+    const int B = cfg->batch > 0 ? cfg->batch : 2;
+    n->s_override = false;
     std::vector<int> order(n->nsamples);
     for (int i = 0; i < n->nsamples; ++i) order[i] = i;
-    double first = 0.0, last = 0.0;
-    double hacc[2];
+    double first = 0.0, last = 0.0, best = 1e300;
+    std::vector<float> best_p(n->np);
+    CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
+    int steps = 0;
     for (int ep = 0; ep < cfg->epochs; ++ep) {
         std::shuffle(order.begin(), order.end(), rng);
-        double sum = 0.0;
-        for (int k = 0; k < n->nsamples; ++k) {
-            const float* r = n->data + (size_t)order[k] * 2 * N;
-            const float* e = r + N;
-            if ((rc = net_inputs(P, r, nullptr))) return rc;
-            CUDA_TRY(launch_target(D, e, n->zfd, n->sz, n->tgt, s));
-            if ((rc = net_forward(P))) return rc;
-            CUDA_TRY(launch_loss(n->Y, n->tgt, N, n->lossacc, n->dY, s));
+        CUDA_TRY(cudaMemsetAsync(n->lossacc, 0, 16, s));
+        for (int k0 = 0; k0 < n->nsamples; k0 += B) {
+            const int nb = std::min(B, n->nsamples - k0);
+            if ((rc = net_scaling(P))) return rc;             // S from the current parameters (A0..A2 kept)
+            CUDA_TRY(cudaMemsetAsync(n->dY, 0, N * 4, s));
+            for (int k = k0; k < k0 + nb; ++k) {
+                const float* r = n->data + (size_t)order[k] * 2 * N;
+                if ((rc = pair_loss_grad(P, r, r + N, n->dY, 1.0f / nb))) return rc;
+            }
+            CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, s));    // d/dlog S -> d/dy
             if ((rc = net_backward(P))) return rc;
             n->step++;
-            CUDA_TRY(launch_adam(n->p, n->g, n->m, n->v, n->wb, n->wmap, n->np, cfg->lr, 0.9f, 0.999f, 1e-8f,
+            steps++;
+            const float lr = cfg->lr * std::min(1.0f, (float)steps / 50.0f);
+            CUDA_TRY(launch_adam(n->p, n->g, n->m, n->v, n->wb, n->wmap, n->np, lr, 0.9f, 0.999f, 1e-8f,
                                  n->step, s));
-            CUDA_TRY(cudaMemcpyAsync(hacc, n->lossacc, 16, cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            sum += hacc[1] > 0 ? hacc[0] / hacc[1] : 0.0;
         }
-        double mean = n->nsamples ? sum / n->nsamples : 0.0;
+        double hacc[2];
+        CUDA_TRY(cudaMemcpyAsync(hacc, n->lossacc, 16, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const double mean = n->nsamples ? hacc[0] / n->nsamples : 0.0;
         if (ep == 0) first = mean;
         last = mean;
+        // the epoch's mean loss belongs to parameters between the epoch's first
+        // and last step; the parameters after the epoch are kept if it is the best
+        if (mean < best) {
+            best = mean;
+            CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
+        }
     }
+    {
+        std::vector<float> keep = best_p;
+        const int st = n->step;
+        if ((rc = net_upload(P, keep))) return rc;
+        n->step = st;
+    }
+    n->s_stale = true;
+    if ((rc = ensure_scaling(P))) return rc;
     if (stats) {
         stats->pairs = n->nsamples * ng;
         stats->samples = n->nsamples;
         stats->rhs = nrhs;
-        stats->steps = cfg->epochs * n->nsamples;
+        stats->steps = steps;
         stats->loss_first_epoch = first;
         stats->loss_last_epoch = last;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -353,7 +525,7 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     return SGIGA_OK;
 }
 
-// Checkpoint: "SGIGANET" | version 1 | taps | nparams | step | p | m | v (float32)
+// Checkpoint: "SGIGANET" | version 2 | taps | nparams | step | p | m | v (float32)
 int sgiga_net_save(sgiga_plan_t P, const char* path) {
     if (!P || !P->net || !path) return fail(SGIGA_ERR_ARG, "no network or null path");
     Net* n = P->net;
@@ -364,7 +536,7 @@ int sgiga_net_save(sgiga_plan_t P, const char* path) {
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(SGIGA_ERR_ARG, std::string("cannot open ") + path);
     const char magic[8] = {'S', 'G', 'I', 'G', 'A', 'N', 'E', 'T'};
-    int hdr[4] = {1, n->T, n->np, n->step};
+    int hdr[4] = {2, n->T, n->np, n->step};
     bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 4, f) == 4 &&
               std::fwrite(p.data(), 4, n->np, f) == (size_t)n->np && std::fwrite(m.data(), 4, n->np, f) == (size_t)n->np &&
               std::fwrite(v.data(), 4, n->np, f) == (size_t)n->np;
@@ -374,11 +546,10 @@ int sgiga_net_save(sgiga_plan_t P, const char* path) {
 }
 
 int sgiga_net_load(sgiga_plan_t P, const char* path) {
-    if (!P || !path) return fail(SGIGA_ERR_ARG, "null argument");
-    if (P->cfg.precision != SGIGA_PREC_MIXED_FP32)
-        return fail(SGIGA_ERR_ARG, "the network needs a SGIGA_PREC_MIXED_FP32 plan");
-    int rc = net_create(P);
+    int rc = needs_net(P);
     if (rc) return rc;
+    if (!path) return fail(SGIGA_ERR_ARG, "null argument");
+    if ((rc = net_create(P))) return rc;
     Net* n = P->net;
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(SGIGA_ERR_ARG, std::string("cannot open ") + path);
@@ -386,7 +557,7 @@ int sgiga_net_load(sgiga_plan_t P, const char* path) {
     int hdr[4];
     std::vector<float> p(n->np), m(n->np), v(n->np);
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "SGIGANET", 8) == 0 &&
-              std::fread(hdr, 4, 4, f) == 4 && hdr[0] == 1 && hdr[1] == n->T && hdr[2] == n->np &&
+              std::fread(hdr, 4, 4, f) == 4 && hdr[0] == 2 && hdr[1] == n->T && hdr[2] == n->np &&
               std::fread(p.data(), 4, n->np, f) == (size_t)n->np && std::fread(m.data(), 4, n->np, f) == (size_t)n->np &&
               std::fread(v.data(), 4, n->np, f) == (size_t)n->np;
     std::fclose(f);

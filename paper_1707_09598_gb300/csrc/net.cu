@@ -1,11 +1,13 @@
-// Learned correction of the fast-diagonalisation preconditioner (not in the
-// paper; its conclusions suggest the combination technique itself as a
-// preconditioner, Sec. 5 — this is a different, data-driven companion):
+// Network of the learned scaling of the fast-diagonalisation preconditioner
+// (not in the paper; its conclusions name fast solvers used as
+// preconditioners as future work, Sec. 5), and the elementwise kernels of the
+// scaled preconditioner and of its training loss:
 //
-//   M(r) = z + s_z N([r / s_r, z / s_z]),  z = FD(r),  s_* = RMS per component,
+//   M(r) = S * FD(S * r),  S = exp(N(phi)),  phi = log of the local effective
+//   coefficient of each DoF,
 //
 // N = three 3x3(x3) convolutions over each component's DoF tensor with zero
-// padding, 2 -> 32 -> 32 -> 1 channels, ReLU after the first two. Weights are
+// padding, 1 -> 32 -> 32 -> 1 channels, ReLU after the first two. Weights are
 // kept as an FP32 master copy (Adam) and a BF16 copy used by every forward and
 // backward kernel; all accumulation is FP32. Activations are channel planes
 // over the packed vector of all components: X[c][v].
@@ -17,7 +19,7 @@
 //   wgrad     dW[co][ci][tap] += sum_v dZ[co][v] X[ci][nb(v,tap)] (tiles of 32
 //             DoFs gathered im2col-style in shared memory, 8x32 thread grid,
 //             partial sums in registers, one atomic add per block and weight)
-//   relu/mask, per-component RMS scaling, loss, Adam.
+//   relu/mask, features, scaling, pair loss and gradient, Adam.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -169,43 +171,15 @@ __global__ void k_relu_mask(float* __restrict__ dA, const float* __restrict__ A,
         if (!(A[i] > 0.0f)) dA[i] = 0.0f;
 }
 
-// x[c][v] *= scale[grid(v)] over every channel c (per-component scaling)
-__global__ void k_scale_grid(DevPlan P, float* __restrict__ x, const double* __restrict__ scale, int nch,
-                             long long N, int invert) {
-    const Chunk c = P.chunks[blockIdx.x];
-    double s = scale[c.grid];
-    float f = (float)(invert ? (s > 0.0 ? 1.0 / s : 0.0) : s);
-    for (int ch = 0; ch < nch; ++ch)
-        for (int i = threadIdx.x; i < c.len; i += blockDim.x) x[(long long)ch * N + c.start + i] *= f;
+// phi = log(num / den) (FP64 ratio, FP32 result)
+__global__ void k_log_ratio(const double* __restrict__ num, const double* __restrict__ den, float* __restrict__ out,
+                            long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) out[i] = (float)log(num[i] / den[i]);
 }
 
-// cand = z + s_z * y (all grids)
-__global__ void k_net_candidate(DevPlan P, const float* __restrict__ z, const float* __restrict__ y,
-                                const double* __restrict__ sz, float* __restrict__ cand) {
-    const Chunk c = P.chunks[blockIdx.x];
-    const float s = (float)sz[c.grid];
-    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
-        long long k = c.start + i;
-        cand[k] = z[k] + s * y[k];
-    }
-}
-
-// out = cand where the component's network output is finite and
-// r.cand >= r.z / 2 (the learned direction keeps the descent property of FD),
-// else z; active grids only
-__global__ void k_net_select(DevPlan P, const float* __restrict__ z, const float* __restrict__ cand,
-                             const int* __restrict__ ok, const double* __restrict__ rz, const double* __restrict__ rc,
-                             float* __restrict__ out, const int* __restrict__ active) {
-    const Chunk c = P.chunks[blockIdx.x];
-    if (active && !active[c.grid]) return;
-    const bool use = ok[c.grid] != 0 && rc[c.grid] >= 0.5 * rz[c.grid];
-    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
-        long long k = c.start + i;
-        out[k] = use ? cand[k] : z[k];
-    }
-}
-
-// per-component: ok[g] = all entries of y finite (partial flags by chunk)
+// per component: ok[g] = all entries of y finite (partial flags by chunk)
 __global__ void k_finite(DevPlan P, const float* __restrict__ y, int* __restrict__ ok) {
     const Chunk c = P.chunks[blockIdx.x];
     bool bad = false;
@@ -213,34 +187,92 @@ __global__ void k_finite(DevPlan P, const float* __restrict__ y, int* __restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAnd(&ok[c.grid], 0);
 }
 
-// loss = sum_v (y - t)^2 / sum_v t^2 (partials: [0] numerator, [1] denominator);
-// dy = 2 (y - t) / sum t^2 is written in a second pass
-__global__ void k_loss_partial(const float* __restrict__ y, const float* __restrict__ t, long long n,
-                               double* __restrict__ acc) {
-    double a = 0.0, b = 0.0;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) {
-        double e = (double)y[i] - (double)t[i];
-        a += e * e;
-        b += (double)t[i] * (double)t[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0], a);
-        atomicAdd(&acc[1], b);
+// log S = L tanh(y / L) with L = SGIGA_LOGS_MAX: a smooth bound on the
+// scaling (S in [e^-L, e^L]) that keeps a training step from driving one
+// component's preconditioner far from FD; the scalings that matter here have
+// |log S| below 2.
+#define SGIGA_LOGS_MAX 4.0f
+
+// S = exp(L tanh(y / L)) where the component's y is finite, else 1 (plain FD there)
+__global__ void k_exp_scaling(DevPlan P, const float* __restrict__ y, const int* __restrict__ ok,
+                              float* __restrict__ S) {
+    const Chunk c = P.chunks[blockIdx.x];
+    const bool use = ok[c.grid] != 0;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long k = c.start + i;
+        S[k] = use ? expf(SGIGA_LOGS_MAX * tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX))) : 1.0f;
     }
 }
 
-__global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict__ t, long long n,
-                            const double* __restrict__ acc, float* __restrict__ dy) {
-    const float f = (float)(2.0 / acc[1]);
+// out = S * in on the active components (out may alias in)
+__global__ void k_mul_active(DevPlan P, const float* __restrict__ S, const float* in, float* out,
+                             const int* __restrict__ active) {
+    const Chunk c = P.chunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long k = c.start + i;
+        out[k] = S[k] * in[k];
+    }
+}
+
+// res = S * z1 - e
+__global__ void k_pair_residual(long long n, const float* __restrict__ S, const float* __restrict__ z1,
+                                const float* __restrict__ e, float* __restrict__ res) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) dy[i] = f * (y[i] - t[i]);
+    for (; i < n; i += stride) res[i] = S[i] * z1[i] - e[i];
+}
+
+// delta = 2 res / (||e_g||^2 ncomp), t2 = S delta (components with e_g = 0: 0)
+__global__ void k_pair_delta(DevPlan P, const float* __restrict__ S, const float* __restrict__ res,
+                             const double* __restrict__ ee, float* __restrict__ delta, float* __restrict__ t2) {
+    const Chunk c = P.chunks[blockIdx.x];
+    const double e2 = ee[c.grid];
+    const float f = e2 > 0.0 ? (float)(2.0 / (e2 * (double)P.ncomps)) : 0.0f;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long k = c.start + i;
+        const float dl = f * res[k];
+        delta[k] = dl;
+        t2[k] = S[k] * dl;
+    }
+}
+
+// acc[0] += mean over components of rr_g / ee_g (one block)
+__global__ void k_pair_loss(int ng, const double* __restrict__ rr, const double* __restrict__ ee,
+                            double* __restrict__ acc) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) v += ee[g] > 0.0 ? rr[g] / ee[g] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        acc[0] += t / (double)ng;
+    }
+}
+
+// dls += weight * S (delta z1 + r z2): the gradient with respect to log S
+__global__ void k_pair_grad(long long n, const float* __restrict__ S, const float* __restrict__ delta,
+                            const float* __restrict__ z1, const float* __restrict__ r, const float* __restrict__ z2,
+                            float weight, float* __restrict__ dls) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dls[i] += weight * S[i] * (delta[i] * z1[i] + r[i] * z2[i]);
+}
+
+// chain rule from d/dlog S to d/dy through log S = L tanh(y / L); no gradient
+// through a component that fell back to S = 1
+__global__ void k_mask_scaled(DevPlan P, float* __restrict__ dy, const int* __restrict__ ok,
+                              const float* __restrict__ y) {
+    const Chunk c = P.chunks[blockIdx.x];
+    const bool use = ok[c.grid] != 0;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const long long k = c.start + i;
+        const float t = tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX));
+        dy[k] = use ? dy[k] * (1.0f - t * t) : 0.0f;
+    }
 }
 
 // Adam update of the FP32 master parameters and their BF16 copy
@@ -287,7 +319,7 @@ cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, cons
         k_conv<CI, CO><<<P.nchunks, 256, sm, s>>>(P, w, bias, X, Y, N, transpose, relu);                 \
         return cudaGetLastError();                                                                         \
     }
-    CONV(2, 32) CONV(32, 32) CONV(32, 1) CONV(1, 32)
+    CONV(32, 32) CONV(32, 1) CONV(1, 32)
 #undef CONV
     return cudaErrorInvalidValue;
 }
@@ -306,7 +338,7 @@ cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, co
         k_wgrad<CI, CO, R><<<blocks, 256, sm, s>>>(P, X, dZ, dW, db, N);                                  \
         return cudaGetLastError();                                                                         \
     }
-    WG(2, 32, 7) WG(32, 32, 108) WG(32, 1, 4)
+    WG(1, 32, 4) WG(32, 32, 108) WG(32, 1, 4)
 #undef WG
     return cudaErrorInvalidValue;
 }
@@ -317,44 +349,62 @@ cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_grid(const DevPlan& P, float* x, const double* scale, int nch, int invert, cudaStream_t s) {
-    if (P.nchunks == 0) return cudaSuccess;
+cudaError_t launch_log_ratio(const double* num, const double* den, float* out, long long n, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_scale_grid<<<P.nchunks, 256, 0, s>>>(P, x, scale, nch, P.ndof, invert);
+    k_log_ratio<<<eblocks(n), 256, 0, s>>>(num, den, out, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_candidate(const DevPlan& P, const float* z, const float* y, const double* sz, int* ok,
-                                 float* cand, cudaStream_t s) {
+cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ok, 0xff, sizeof(int) * P.ngrids, s);   // all ones = finite
+    cudaError_t e = cudaMemsetAsync(ok, 0xff, sizeof(int) * P.ncomps, s);   // all ones = finite
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
     k_finite<<<P.nchunks, 256, 0, s>>>(P, y, ok);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_net_candidate<<<P.nchunks, 256, 0, s>>>(P, z, y, sz, cand);
+    k_exp_scaling<<<P.nchunks, 256, 0, s>>>(P, y, ok, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_select(const DevPlan& P, const float* z, const float* cand, const int* ok, const double* rz,
-                              const double* rc, float* out, const int* active, cudaStream_t s) {
+cudaError_t launch_mul_active(const DevPlan& P, const float* S, const float* in, float* out, const int* active,
+                              cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_net_select<<<P.nchunks, 256, 0, s>>>(P, z, cand, ok, rz, rc, out, active);
+    k_mul_active<<<P.nchunks, 256, 0, s>>>(P, S, in, out, active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const float* y, const float* t, long long n, double* acc, float* dy, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+cudaError_t launch_pair_residual(const DevPlan& P, const float* S, const float* z1, const float* e, float* res,
+                                 cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_pair_residual<<<eblocks(P.ndof), 256, 0, s>>>(P.ndof, S, z1, e, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res, const double* rr, const double* ee,
+                              float* delta, float* t2, double* lossacc, cudaStream_t s) {
+    if (P.nchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_pair_delta<<<P.nchunks, 256, 0, s>>>(P, S, res, ee, delta, t2);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_loss_partial<<<eblocks(n), 256, 0, s>>>(y, t, n, acc);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || !dy) return e;
+    k_pair_loss<<<1, 256, 0, s>>>(P.ncomps, rr, ee, lossacc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delta, const float* z1, const float* r,
+                             const float* z2, float weight, float* dls, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    k_loss_grad<<<eblocks(n), 256, 0, s>>>(y, t, n, acc, dy);
+    k_pair_grad<<<eblocks(P.ndof), 256, 0, s>>>(P.ndof, S, delta, z1, r, z2, weight, dls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s) {
+    if (P.nchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_mask_scaled<<<P.nchunks, 256, 0, s>>>(P, dy, ok, y);
     return cudaGetLastError();
 }
 
@@ -369,39 +419,6 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, 
 cudaError_t launch_f2bf(const float* p, const int* wmap, void* wb, int n, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     k_f2bf<<<(n + 255) / 256, 256, 0, s>>>(p, wmap, (__nv_bfloat16*)wb, n);
-    return cudaGetLastError();
-}
-
-// rms[g] = sqrt(dots[g] / ndof_g)
-__global__ void k_rms(DevPlan P, const double* __restrict__ dots, double* __restrict__ rms) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.ngrids) return;
-    long long n = P.grids[g].ndof;
-    rms[g] = n > 0 ? sqrt(dots[g] / (double)n) : 0.0;
-}
-
-cudaError_t launch_rms(const DevPlan& P, const double* dots, double* rms, cudaStream_t s) {
-    SGIGA_COUNT_LAUNCH();
-    k_rms<<<(P.ngrids + 127) / 128, 128, 0, s>>>(P, dots, rms);
-    return cudaGetLastError();
-}
-
-// training target t = (e - z) / s_z per component
-__global__ void k_target(DevPlan P, const float* __restrict__ e, const float* __restrict__ z,
-                         const double* __restrict__ sz, float* __restrict__ t) {
-    const Chunk c = P.chunks[blockIdx.x];
-    const double s = sz[c.grid];
-    const float f = (float)(s > 0.0 ? 1.0 / s : 0.0);
-    for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
-        long long k = c.start + i;
-        t[k] = (e[k] - z[k]) * f;
-    }
-}
-
-cudaError_t launch_target(const DevPlan& P, const float* e, const float* z, const double* sz, float* t, cudaStream_t s) {
-    if (P.nchunks == 0) return cudaSuccess;
-    SGIGA_COUNT_LAUNCH();
-    k_target<<<P.nchunks, 256, 0, s>>>(P, e, z, sz, t);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,9 @@ struct sgiga_plan_s {
     std::vector<Patch> patches;          // every geometry patch
     double* d_xb = nullptr;              // boundary data points [nbpts][2] (multi-patch)
     long long ndof = 0, nqp = 0, tab_entries = 0, ulen = 0, llen = 0;
+    // set-up phases, seconds (sgiga_plan_times)
+    double t_total = 0, t_host = 0, t_basis = 0, t_eigen = 0, t_fd = 0, t_geometry = 0, t_vectors = 0;
+    double t_coefficient = 0, t_autotune = 0;
     int maxE = 1;
     int fd_ks = 32;             // contraction depth per preconditioner work item
     bool fd_grouped = false;    // preconditioner layout: level-grouped GEMMs, else per-piece items
@@ -108,6 +111,7 @@ struct sgiga_plan_s {
         const void* xbuf = nullptr;
         const int* outer = nullptr;
         bool flexible = false;
+        bool learned = false;         // the body applies the learned preconditioner
         bool failed = false;
         long long body_kernels = 0;   // kernels per iteration of the captured body
     } loop64, loop32;
@@ -269,10 +273,14 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
 // `outer` (all when null), each with its own scalars, until
 // ||r_g|| <= tol ||rhs_g|| or max_iter iterations. Scalars: scal[0..6].
 // Returns the number of grids still active (or a negative status).
-// Learned preconditioner (learned.cu): z = FD(r) + s_z N([r/s_r, FD(r)/s_z]), FP32.
+// Learned preconditioner (learned.cu): z = S * FD(S * r), S = exp(N(phi)), FP32.
 namespace sgiga {
 int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active);
 void free_net(sgiga_plan_s* P);
+// the geometry planes changed: the network's features (and S) are stale
+void net_invalidate_features(sgiga_plan_s* P);
+// before a solve: S up to date (network evaluated once if needed)
+int learned_prepare(sgiga_plan_s* P);
 }
 
 inline int precond_any(sgiga_plan_s* P, const double* r, double* z, const int* active, double* t1, double* t2) {
@@ -338,8 +346,10 @@ template <typename Real>
 inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real> v, const void* rhs, double tol,
                           int max_iter, const int* outer, int* active, int* iters, double* scal, bool flexible) {
     cudaStream_t ls = P->stream ? P->stream : P->own_stream;
+    const bool learned = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready &&
+                         !P->learned_off;
     const bool same = L.exec && L.tol == tol && L.max_iter == max_iter && L.rhs == rhs && L.outer == outer &&
-                      L.flexible == flexible && L.xbuf == (const void*)v.x;
+                      L.flexible == flexible && L.learned == learned && L.xbuf == (const void*)v.x;
     if (!same) {
         destroy_loop_graph(L);
         cudaGraph_t g = nullptr;
@@ -385,6 +395,7 @@ inline int pcg_graph_loop(sgiga_plan_s* P, sgiga_plan_s::LoopGraph& L, Vecs<Real
         L.xbuf = v.x;
         L.outer = outer;
         L.flexible = flexible;
+        L.learned = learned;
     }
     CUDA_TRY(cudaGraphLaunch(L.exec, ls));
     return SGIGA_OK;
@@ -405,8 +416,10 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     const int ng = (int)P->comps.size();
     double* bb = scal + 0 * ng;
     double* rz = scal + 1 * ng;
-    // a learned (nonlinear) preconditioner needs the flexible (Polak-Ribiere) beta
-    const bool flexible = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready;
+    // the learned preconditioner runs in flexible CG (Polak-Ribiere beta), which
+    // also tolerates the rounding of its FP32 scaling
+    const bool flexible = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready &&
+                          !P->learned_off;
     auto init = [&]() -> int {
         CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
         CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
@@ -419,7 +432,7 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     int rc = init();
     if (rc) return rc;
     sgiga_plan_s::LoopGraph& L = sizeof(Real) == 8 ? P->loop64 : P->loop32;
-    if (P->use_graph && !hook && !flexible && !L.failed) {
+    if (P->use_graph && !hook && !L.failed) {
         // whole loop on the device: one graph launch, no host round trip per iteration
         CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
         rc = pcg_graph_loop<Real>(P, L, v, rhs, tol, max_iter, outer, active, iters, scal, flexible);

@@ -10,8 +10,10 @@ one JSON line:
   fp64_fd_per_grid  plain FP64 FD-CG one component grid at a time (a plan
                per grid, stream-ordered host loop, no batching, no graph)
   mixed_fd     FP32 inner FD-CG inside FP64 refinement
-  mixed_learned  FP32 inner flexible CG with M = FD + trained correction
-  (training: target_pairs residual/error pairs from the plan's own CG)
+  mixed_learned  FP32 inner flexible CG with M(r) = S * FD(S * r), S = exp(N(phi))
+               from the trained network (training: target_pairs
+               residual/error pairs from the plan's own CG)
+  mixed_scaled   the same with the network-free scaling S = c^(-1/2)
 
 with wall time (CUDA events on the plan's stream), iterations, and the
 relative L2 of each solution's combined values (17^3 lattice) against the
@@ -44,7 +46,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--w", type=int, default=12)
     ap.add_argument("--pairs", type=int, default=10000)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=2)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--nfeat", type=int, default=128)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-tol-sweep", default="",
@@ -150,8 +154,8 @@ def main():
         out["mixed_fd_inner_tol_sweep"] = sweep
         sgiga.sgiga_set_solver_options(P.handle, use_graph=True, inner_tol=a.inner_tol, inner_max=100)
     sgiga.sgiga_net_init(P.handle, 11)
-    tr = sgiga.sgiga_train_net(P.handle, target_pairs=a.pairs, max_iter_record=30, epochs=a.epochs, lr=1e-3,
-                               seed=100)
+    tr = sgiga.sgiga_train_net(P.handle, target_pairs=a.pairs, max_iter_record=30, epochs=a.epochs, lr=a.lr,
+                               seed=100, batch=a.batch)
     out["training"] = {"pairs": tr.pairs, "samples": tr.samples, "rhs": tr.rhs, "steps": tr.steps,
                        "loss_first_epoch": tr.loss_first_epoch, "loss_last_epoch": tr.loss_last_epoch,
                        "seconds": tr.seconds}
@@ -161,6 +165,14 @@ def main():
     out["mixed_learned"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
                             "fallback": st.fallback,
                             "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
+    phi = torch.zeros(P.info.ndof, dtype=torch.float32, device="cuda")
+    sgiga.sgiga_net_features(P.handle, phi)
+    sgiga.sgiga_net_set_scaling(P.handle, torch.exp(-0.5 * phi).contiguous())
+    timed_solve(P, a.tol, 50)
+    st, rc, ms = timed_solve(P, a.tol, 50)
+    out["mixed_scaled"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc,
+                           "fallback": st.fallback,
+                           "rel_l2_vs_ref": float(np.linalg.norm(combined(P) - ref) / np.linalg.norm(ref))}
     P.close()
     print(json.dumps(out))
 

@@ -63,7 +63,7 @@ class sgiga_grid(ctypes.Structure):
 
 class sgiga_train_cfg(ctypes.Structure):
     _fields_ = [("target_pairs", ctypes.c_int), ("max_iter_record", ctypes.c_int), ("epochs", ctypes.c_int),
-                ("lr", ctypes.c_float), ("seed", ctypes.c_uint)]
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint), ("batch", ctypes.c_int)]
 
 
 class sgiga_train_stats(ctypes.Structure):
@@ -77,6 +77,11 @@ class sgiga_tune_result(ctypes.Structure):
                 ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8),
                 ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
                 ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8)]
+
+
+class sgiga_plan_times_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("total", "host", "basis", "eigen", "fd", "geometry", "vectors",
+                                               "coefficient", "autotune")]
 
 
 class sgiga_solve_stats(ctypes.Structure):
@@ -93,6 +98,7 @@ _SIGS = {
     "sgiga_destroy": (None, [_P]),
     "sgiga_plan_info": (_I, [_P, ctypes.POINTER(sgiga_info)]),
     "sgiga_grid_info": (_I, [_P, _I, ctypes.POINTER(sgiga_grid)]),
+    "sgiga_plan_times": (_I, [_P, ctypes.POINTER(sgiga_plan_times_t)]),
     "sgiga_qp_coords": (_I, [_P, _P]),
     "sgiga_set_rhs": (_I, [_P, _P]),
     "sgiga_set_rhs_builtin": (_I, [_P, _I]),
@@ -126,6 +132,10 @@ _SIGS = {
     "sgiga_net_set_params": (_I, [_P, _P]),
     "sgiga_net_forward": (_I, [_P, _P, _P]),
     "sgiga_net_backward": (_I, [_P, _P, _P, _P]),
+    "sgiga_net_features": (_I, [_P, _P]),
+    "sgiga_net_scaling": (_I, [_P, _P]),
+    "sgiga_net_set_scaling": (_I, [_P, _P]),
+    "sgiga_net_loss_grad": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "sgiga_train_net": (_I, [_P, ctypes.POINTER(sgiga_train_cfg), ctypes.POINTER(sgiga_train_stats)]),
     "sgiga_net_save": (_I, [_P, ctypes.c_char_p]),
     "sgiga_net_load": (_I, [_P, ctypes.c_char_p]),
@@ -158,7 +168,7 @@ def _ptr(buf, n=None, dtype=np.float64):
         return None
     if hasattr(buf, "data_ptr"):          # torch tensor
         import torch
-        want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
         if buf.dtype != want or not buf.is_contiguous():
             raise TypeError("expected a contiguous %s tensor" % want)
         if n is not None and buf.numel() < n:
@@ -441,18 +451,43 @@ def _f32dev(t, n):
 
 def sgiga_net_forward(plan, inp, out):
     n = sgiga_plan_info(plan).ndof
-    _check(_lib.sgiga_net_forward(plan, _f32dev(inp, 2 * n), _f32dev(out, n)))
+    _check(_lib.sgiga_net_forward(plan, _f32dev(inp, n), _f32dev(out, n)))
 
 
 def sgiga_net_backward(plan, inp, dy):
     n = sgiga_plan_info(plan).ndof
     g = np.zeros(sgiga_net_num_params(plan), dtype=np.float32)
-    _check(_lib.sgiga_net_backward(plan, _f32dev(inp, 2 * n), _f32dev(dy, n), g.ctypes.data))
+    _check(_lib.sgiga_net_backward(plan, _f32dev(inp, n), _f32dev(dy, n), g.ctypes.data))
     return g
 
 
-def sgiga_train_net(plan, target_pairs=10000, max_iter_record=30, epochs=10, lr=1e-3, seed=100):
-    cfg = sgiga_train_cfg(int(target_pairs), int(max_iter_record), int(epochs), float(lr), int(seed))
+def sgiga_net_features(plan, out):
+    """phi = log c into a float32 buffer [ndof] (CUDA tensor or numpy array)."""
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_net_features(plan, _ptr(out, n, np.float32)))
+
+
+def sgiga_net_scaling(plan, out):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_net_scaling(plan, _ptr(out, n, np.float32)))
+
+
+def sgiga_net_set_scaling(plan, S):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_net_set_scaling(plan, _ptr(S, n, np.float32)))
+
+
+def sgiga_net_loss_grad(plan, r, e, grad):
+    """(loss, fills grad): the training loss of one sample and its gradient
+    with respect to log S (float32 CUDA tensors [ndof])."""
+    n = sgiga_plan_info(plan).ndof
+    loss = ctypes.c_double()
+    _check(_lib.sgiga_net_loss_grad(plan, _f32dev(r, n), _f32dev(e, n), ctypes.byref(loss), _f32dev(grad, n)))
+    return loss.value
+
+
+def sgiga_train_net(plan, target_pairs=10000, max_iter_record=30, epochs=10, lr=1e-3, seed=100, batch=2):
+    cfg = sgiga_train_cfg(int(target_pairs), int(max_iter_record), int(epochs), float(lr), int(seed), int(batch))
     st = sgiga_train_stats()
     _check(_lib.sgiga_train_net(plan, ctypes.byref(cfg), ctypes.byref(st)))
     return st
@@ -464,6 +499,13 @@ def sgiga_net_save(plan, path):
 
 def sgiga_net_load(plan, path):
     _check(_lib.sgiga_net_load(plan, str(path).encode()))
+
+
+def sgiga_plan_times(plan):
+    """Set-up phase times of the plan (seconds), as a dict."""
+    t = sgiga_plan_times_t()
+    _check(_lib.sgiga_plan_times(plan, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in sgiga_plan_times_t._fields_}
 
 
 def sgiga_launch_count():

@@ -10,6 +10,7 @@ import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -128,10 +129,9 @@ def test_parallel_oracle_baseline_runs_the_sample_on_every_core():
     workers, per_core tasks per core, in LPT order; it reports the cores used
     and DoFs that match the serial sample's components."""
     import bench
-    from oracle import geometry
-    from oracle.galerkin import Component
     r = bench.run_oracle_sample(1, parallel=True)
     ncores = os.cpu_count() or 1
     assert r["cores"] == ncores and r["components"] == ncores and r["seconds"] > 0
-    per = [Component(geometry.UnitCube(3), lv, 3).ndof for lv in bench.ORACLE_SAMPLE]
+    # p = 3 C^2: 2^l + 1 interior functions per direction
+    per = [int(np.prod([2 ** l + 1 for l in lv])) for lv in bench.ORACLE_SAMPLE]
     assert r["dofs"] == sum(per[i % len(per)] for i in range(ncores))

@@ -187,3 +187,22 @@ def test_parametric_gradient_3d_matches_central_differences(domain, levels, p):
         e[k] = h
         fd = (comp.evaluate(u, pts + e) - comp.evaluate(u, pts - e)) / (2 * h)
         assert np.abs(g[:, k] - fd).max() < 1e-6 * max(1.0, np.abs(g[:, k]).max()), k
+
+
+def test_sturm_eigenvalues_closed_form_and_dense_solver():
+    """Bisection on the inertia of K - s M: the linear-element pencil has the
+    closed form lam_k = 6/h^2 (1 - cos(k pi h)) / (2 + cos(k pi h)); on a
+    uniform cubic pencil it agrees with the dense generalised eigensolver."""
+    import scipy.linalg as sla
+    from oracle import fd
+    from oracle.galerkin import stiffness_1d
+    K, M = stiffness_1d(5, 1, 0)
+    h, n = 1.0 / 32, K.shape[0]
+    k = np.arange(1, n + 1)
+    closed = 6 / h ** 2 * (1 - np.cos(k * np.pi * h)) / (2 + np.cos(k * np.pi * h))
+    js = [0, 1, n // 2, n - 1]
+    np.testing.assert_allclose(fd.sturm_eigenvalues(K, M, js), closed[js], rtol=1e-13)
+    K, M = stiffness_1d(4, 3, 2)
+    ref = sla.eigh(K, M, eigvals_only=True)
+    js = [0, 3, 9, K.shape[0] - 1]
+    np.testing.assert_allclose(fd.sturm_eigenvalues(K, M, js), ref[js], rtol=1e-12)

@@ -83,3 +83,11 @@ def test_packed_loss_is_the_mean_over_components():
     L1, g1 = learned.pair_loss_grad((1, 3), 2, 1, S[16:], r[16:], e[16:])
     assert abs(L - 0.5 * (L0 + L1)) < 1e-14 * L
     np.testing.assert_allclose(g, 0.5 * np.concatenate([g0, g1]), rtol=1e-14)
+
+
+def test_scaling_bound():
+    """S = exp(4 tanh(y/4)): exp(y) to first order near 0, monotone, within e^{+-4}."""
+    y = np.linspace(-50, 50, 2001)
+    S = learned.scaling_from_output(y)
+    assert np.all(np.diff(S) > 0) and S.min() >= np.exp(-4.0) and S.max() <= np.exp(4.0)
+    np.testing.assert_allclose(learned.scaling_from_output([1e-3, -2e-3]), np.exp([1e-3, -2e-3]), rtol=1e-9)
