@@ -265,7 +265,7 @@ def test_eigenpairs(sg, case):
                 # graded meshes: M is ill-conditioned and the dense FP64 solver
                 # (Cholesky of M) loses digits; the oracle's extended-precision
                 # bisection on the inertia of K - s M does not
-                js = sorted({0, 4, n // 2, n - 1})
+                js = sorted({j for j in (0, 4, n // 2, n - 1) if j < n})
                 ref = fd.sturm_eigenvalues(K, M, js)
                 np.testing.assert_allclose(lam[js], ref, rtol=1e-10)
 
