@@ -501,7 +501,9 @@ def train_learned(W, args):
     out = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc, "fallback": st.fallback,
            "setup_s": ps, "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(L), W.gold),
            "training": {"seconds": train_s, "pairs": tr.pairs, "samples": tr.samples, "adam_steps": tr.steps,
-                        "loss_first_epoch": tr.loss_first_epoch, "loss_last_epoch": tr.loss_last_epoch}}
+                        "loss_fd": tr.loss_fd, "loss_initial": tr.loss_initial,
+                        "loss_epochs": [tr.loss_epoch[e] for e in range(min(12, 32))],
+                        "best_epoch": tr.best_epoch, "log_s_range": [tr.logs_min, tr.logs_max]}}
     tuning = {"best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
                        "apply_f32_ms": tune.best_ms, "ntiles": tune.ntiles},
               "precond": {"best_ks": tune.fd_ks[tune.fd_best],

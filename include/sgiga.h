@@ -259,6 +259,16 @@ int sgiga_source_at_qp(sgiga_plan_t plan, int source, double* f);
  * a(x_q)); the load vector and the preconditioner are unchanged. */
 int sgiga_set_coefficient(sgiga_plan_t plan, int nfeat, const double* omega, const double* phase, double amp);
 
+/* Diffusion coefficient given at the quadrature points: a_qp [nqp] in natural
+ * qp order (host or device; values of a(F(xi_q)) > 0), or NULL to restore
+ * a = 1. K_ij = sum_q w_q |det J_q| a_q grad R_i^T (J_q^T J_q)^{-1} grad R_j
+ * (Galerkin stiffness of -div(a grad u), Sec. 2.2 with a variable
+ * coefficient); the geometry coefficients are recomputed, the load vector
+ * and the preconditioner are unchanged. sgiga_set_coefficient evaluates its
+ * Fourier features into the same plane. The plan keeps the values (a
+ * re-tiling by sgiga_autotune reuses them). */
+int sgiga_set_coefficient_qp(sgiga_plan_t plan, const double* a_qp);
+
 /* Copy the current packed load vector to b ([ndof], host or device). */
 int sgiga_get_rhs(sgiga_plan_t plan, double* b);
 
@@ -435,6 +445,11 @@ typedef struct {
     double loss_first_epoch, loss_last_epoch;  /* mean over samples of the mean over components of
                                                   ||M(r) - e||^2 / ||e||^2 */
     double seconds;
+    double loss_initial;     /* the same at the initial parameters (before any step) */
+    double loss_fd;          /* the same with S = 1 (plain FD) */
+    double loss_epoch[32];   /* per epoch (the first 32) */
+    double logs_min, logs_max; /* range of log S after training */
+    int best_epoch;          /* epoch whose parameters were kept */
 } sgiga_train_stats;
 
 /* Allocate the network and initialise it (seeded Kaiming-uniform; the last

@@ -243,7 +243,7 @@ static void free_plan(sgiga_plan_s* P) {
     if (P->d_eval_first) cudaFree(P->d_eval_first);
     for (void* a : P->allocs) cudaFree(a);
     if (P->stage) cudaFree(P->stage);
-    if (P->feat) cudaFree(P->feat);
+    if (P->acoef) cudaFree(P->acoef);
     if (P->h_nactive) cudaFreeHost(P->h_nactive);
     delete P;
 }
@@ -1205,34 +1205,76 @@ int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
     return SGIGA_OK;
 }
 
-int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const double* phase, double amp) {
-    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
-    const auto t0 = std::chrono::steady_clock::now();
-    if (nfeat < 0 || (nfeat > 0 && (!omega || !phase))) return fail(SGIGA_ERR_ARG, "bad coefficient features");
+// Recompute the geometry coefficients with the plan's current coefficient plane.
+static int refresh_geometry(sgiga_plan_s* P) {
     cudaStream_t s = P->stream;
-    const int d = P->d;
-    if (P->feat) { cudaFree(P->feat); P->feat = nullptr; }
-    P->dp.feat = nullptr;
-    P->dp.nfeat = 0;
-    if (nfeat > 0) {
-        std::vector<double> f((size_t)nfeat * 4, 0.0);
-        for (int i = 0; i < nfeat; ++i) {
-            for (int k = 0; k < d; ++k) f[(size_t)i * 4 + k] = omega[(size_t)i * d + k];
-            f[(size_t)i * 4 + 3] = phase[i];
-        }
-        cudaError_t e = cudaMalloc(&P->feat, f.size() * 8);
-        if (e != cudaSuccess) { cudaGetLastError(); return fail(SGIGA_ERR_NOMEM, "feature table allocation failed"); }
-        CUDA_TRY(cudaMemcpy(P->feat, f.data(), f.size() * 8, cudaMemcpyHostToDevice));
-        P->dp.feat = P->feat;
-        P->dp.nfeat = nfeat;
-        P->dp.famp = amp;
-    }
     CUDA_TRY(launch_geometry(P->dp, s));
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     net_invalidate_features(P);
-    const int rc = update_diag(P);
+    return update_diag(P);
+}
+
+static int ensure_acoef(sgiga_plan_s* P) {
+    if (P->acoef) return SGIGA_OK;
+    cudaError_t e = cudaMalloc(&P->acoef, (size_t)P->nqp * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        P->acoef = nullptr;
+        return fail(SGIGA_ERR_NOMEM, "coefficient plane allocation failed");
+    }
+    return SGIGA_OK;
+}
+
+int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const double* phase, double amp) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (nfeat < 0 || (nfeat > 0 && (!omega || !phase))) return fail(SGIGA_ERR_ARG, "bad coefficient features");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = P->stream;
+    const int d = P->d;
+    int rc;
+    if (nfeat == 0) {
+        if (P->acoef) { cudaFree(P->acoef); P->acoef = nullptr; }
+        P->dp.acoef = nullptr;
+    } else {
+        std::vector<double> f((size_t)nfeat * 4, 0.0);
+        for (int i = 0; i < nfeat; ++i) {
+            for (int k = 0; k < d; ++k) f[(size_t)i * 4 + k] = omega[(size_t)i * d + k];
+            f[(size_t)i * 4 + 3] = phase[i];
+        }
+        double* feat = nullptr;
+        if (cudaMalloc(&feat, f.size() * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SGIGA_ERR_NOMEM, "feature table allocation failed");
+        }
+        if ((rc = ensure_acoef(P))) { cudaFree(feat); return rc; }
+        cudaError_t e = cudaMemcpy(feat, f.data(), f.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_coef_features(P->dp, feat, nfeat, amp, P->acoef, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(feat);
+        if (e != cudaSuccess) return fail(SGIGA_ERR_CUDA, std::string("coefficient: ") + cudaGetErrorString(e));
+        P->dp.acoef = P->acoef;
+    }
+    rc = refresh_geometry(P);
+    P->t_coefficient = since(t0);
+    return rc;
+}
+
+int sgiga_set_coefficient_qp(sgiga_plan_t P, const double* a_qp) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc;
+    if (!a_qp) {
+        if (P->acoef) { cudaFree(P->acoef); P->acoef = nullptr; }
+        P->dp.acoef = nullptr;
+    } else {
+        if ((rc = ensure_acoef(P))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(P->acoef, a_qp, (size_t)P->nqp * 8, cudaMemcpyDefault, P->stream));
+        CUDA_TRY(cudaStreamSynchronize(P->stream));
+        P->dp.acoef = P->acoef;
+    }
+    rc = refresh_geometry(P);
     P->t_coefficient = since(t0);
     return rc;
 }

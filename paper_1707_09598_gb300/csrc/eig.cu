@@ -9,7 +9,7 @@
 //      of inertia, the number of eigenvalues below s equals the number of
 //      negative pivots of the LDL^T factorisation of K - s M (M positive
 //      definite), computed in one banded sweep;
-//   2. runs of close eigenvalues (relative gap below 1e-6) found on the host;
+//   2. runs of close eigenvalues (relative gap below 1e-3) found on the host;
 //   3. eigenvectors by inverse iteration, one thread per cluster: three
 //      solves (K - s M) y = M v with banded LU and partial pivoting, each
 //      followed by M-orthogonalisation against the cluster's earlier vectors
@@ -318,13 +318,14 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
         msg = "eigenvalue bisection";
         return e;
     }
-    // units: runs of close eigenvalues (relative gap below 1e-6), at most 32
-    // per unit. Maximally smooth splines have pairs of modes localised at the
-    // two ends of the interval whose eigenvalues agree to many digits (on
-    // uniform and symmetric graded meshes); inverse iteration alone would
-    // leave them far from M-orthogonal (error of order eps lam / gap). Longer
-    // runs do not occur in these pencils, and the cap bounds one thread's
-    // Gram-Schmidt work.
+    // units: runs of close eigenvalues (relative gap below 1e-3), at most 32
+    // per unit. Inverse iteration alone leaves two eigenvectors M-orthogonal
+    // only to about eps lam / gap; maximally smooth splines have pairs of modes
+    // localised at the two ends of the interval whose eigenvalues agree to
+    // many digits (uniform and symmetric graded meshes), and the top of the
+    // spectrum is dense on fine levels. The cap bounds one thread's
+    // Gram-Schmidt work; neighbours across a cut keep the eps lam / gap
+    // orthogonality of gaps above 1e-3 lam.
     std::vector<int2> units;
     std::vector<long long> uoff(jobs.size() + 1, 0);
     size_t scratch_doubles = 0;
@@ -340,7 +341,7 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
         uoff[q] = (long long)units.size();
         for (int j = 0; j < J.n;) {
             int j1 = j + 1;
-            while (j1 < J.n && j1 - j < 32 && l[j1] - l[j1 - 1] <= 1e-6 * l[j1]) ++j1;
+            while (j1 < J.n && j1 - j < 32 && l[j1] - l[j1 - 1] <= 1e-3 * l[j1]) ++j1;
             units.push_back(make_int2(j, j1 - j));
             j = j1;
         }

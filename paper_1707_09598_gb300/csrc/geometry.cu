@@ -102,16 +102,7 @@ __global__ void k_geometry(DevPlan P) {
         patch_eval(pt, xi, x, J);
         double Gp[3][3];
         double s = wq;
-        if (P.nfeat > 0) {   // diffusion coefficient a(x) = exp(amp * sum cos(omega . x + phase))
-            double f = 0.0;
-            for (int i = 0; i < P.nfeat; ++i) {
-                const double* ft = P.feat + 4 * i;
-                double arg = ft[3];
-                for (int k = 0; k < d; ++k) arg += ft[k] * x[k];
-                f += cos(arg);
-            }
-            s *= exp(P.famp * f);
-        }
+        if (P.acoef) s *= P.acoef[natural_index(g, d, Q, L)];   // diffusion coefficient a(x_q)
         double det = metric(d, J, s, Gp);
         if (!(det * (pt.orient < 0 ? -1.0 : 1.0) > 0.0)) atomicOr(&P.flags[0], 1);
         long long o = t.g_off + idx;
@@ -142,6 +133,38 @@ cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s) {
     if (blocks > 152 * 16) blocks = 152 * 16;
     SGIGA_COUNT_LAUNCH();
     k_offdiag<<<(unsigned)blocks, 256, 0, s>>>(P.G, P.nqp, P.d, flag);
+    return cudaGetLastError();
+}
+
+// a(x_q) = exp(amp * sum_f cos(omega_f . x_q + phase_f)) at every quadrature
+// point, natural order (random Fourier features of a log-normal field).
+__global__ void k_coef_features(DevPlan P, const double* __restrict__ feat, int nfeat, double amp,
+                                double* __restrict__ a) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        QpLoc L = tile_qp(g, t, d, Q, idx);
+        double xi[3], wq, x[3], J[3][3];
+        qp_param(P, g, L, xi, wq);
+        patch_eval(P.patch[g.patch], xi, x, J);
+        double f = 0.0;
+        for (int i = 0; i < nfeat; ++i) {
+            const double* ft = feat + 4 * i;
+            double arg = ft[3];
+            for (int k = 0; k < d; ++k) arg += ft[k] * x[k];
+            f += cos(arg);
+        }
+        a[natural_index(g, d, Q, L)] = exp(amp * f);
+    }
+}
+
+cudaError_t launch_coef_features(const DevPlan& P, const double* feat, int nfeat, double amp, double* a,
+                                 cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_coef_features<<<P.ntiles, 256, 0, s>>>(P, feat, nfeat, amp, a);
     return cudaGetLastError();
 }
 

@@ -47,9 +47,7 @@ struct DevPlan {
     const double* lam;
     const double* dinv;      // [ndof] 1 / sum_k lambda_{k,i_k} of every packed entry
     int* flags;              // [0] = geometry error, [1] = eval error
-    const double* feat;      // diffusion features [nfeat][4] (omega, phase) or null
-    int nfeat;
-    double famp;
+    const double* acoef;     // diffusion coefficient a(x_q) [nqp], natural order, or null (a = 1)
     size_t smem_op;          // dynamic shared bytes of the operator kernel
     int diag;                // every geometry plane off the diagonal is exactly zero
     const CompDesc* comps;   // components (CG systems); pieces are grids[]
@@ -85,6 +83,8 @@ int gpu_generalized_eigen(int p, std::vector<EigJob>& jobs, const std::vector<do
                           std::vector<double>& hlam, cudaStream_t s, std::string& msg);
 // geometry.cu
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_coef_features(const DevPlan& P, const double* feat, int nfeat, double amp, double* a,
+                                 cudaStream_t s);
 cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s);
 cudaError_t launch_qp_coords(const DevPlan& P, double* xq, cudaStream_t s);
 cudaError_t launch_map_points(const DevPlan& P, const double* xi, const int* patch, long long npts, int npatch,
@@ -159,6 +159,7 @@ cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, cons
 cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, const float* dZ, float* dW, float* db,
                          cudaStream_t s);
 cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s);
+cudaError_t launch_fill(float* x, float v, long long n, cudaStream_t s);
 cudaError_t launch_log_ratio(const double* num, const double* den, float* out, long long n, cudaStream_t s);
 cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s);
 cudaError_t launch_mul_active(const DevPlan& P, const float* S, const float* in, float* out, const int* active,

@@ -255,6 +255,23 @@ static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, float
     return SGIGA_OK;
 }
 
+// Mean loss over the recorded samples at the current S (no update).
+static int dataset_loss(sgiga_plan_s* P, double* out) {
+    Net* n = P->net;
+    cudaStream_t s = P->stream;
+    CUDA_TRY(cudaMemsetAsync(n->lossacc, 0, 16, s));
+    for (int k = 0; k < n->nsamples; ++k) {
+        const float* r = n->data + (size_t)k * 2 * n->N;
+        int rc = pair_loss_grad(P, r, r + n->N, n->dY, 0.0f);
+        if (rc) return rc;
+    }
+    double h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, n->lossacc, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *out = n->nsamples ? h[0] / n->nsamples : 0.0;
+    return SGIGA_OK;
+}
+
 // Records (r_k, x* - x_k) of every CG iterate into the next dataset slot.
 struct RecordHook : PcgHook {
     sgiga_plan_s* P;
@@ -469,7 +486,13 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     n->s_override = false;
     std::vector<int> order(n->nsamples);
     for (int i = 0; i < n->nsamples; ++i) order[i] = i;
-    double first = 0.0, last = 0.0, best = 1e300;
+    double loss_fd = 0.0, loss_init = 0.0;
+    CUDA_TRY(launch_fill(n->S, 1.0f, N, s));                  // S = 1: plain FD
+    if ((rc = dataset_loss(P, &loss_fd))) return rc;
+    if ((rc = net_scaling(P)) || (rc = dataset_loss(P, &loss_init))) return rc;
+    double first = 0.0, last = 0.0, best = loss_init;
+    int best_epoch = -1;
+    std::vector<double> ep_loss;
     std::vector<float> best_p(n->np);
     CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
     int steps = 0;
@@ -498,10 +521,13 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         const double mean = n->nsamples ? hacc[0] / n->nsamples : 0.0;
         if (ep == 0) first = mean;
         last = mean;
+        ep_loss.push_back(mean);
         // the epoch's mean loss belongs to parameters between the epoch's first
-        // and last step; the parameters after the epoch are kept if it is the best
+        // and last step; the parameters after the epoch are kept if it is the
+        // best so far (the initial parameters compete with their own loss)
         if (mean < best) {
             best = mean;
+            best_epoch = ep;
             CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
         }
     }
@@ -521,6 +547,16 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         stats->loss_first_epoch = first;
         stats->loss_last_epoch = last;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->loss_initial = loss_init;
+        stats->loss_fd = loss_fd;
+        for (int e = 0; e < 32; ++e) stats->loss_epoch[e] = e < (int)ep_loss.size() ? ep_loss[e] : 0.0;
+        std::vector<float> hS((size_t)N);
+        CUDA_TRY(cudaMemcpy(hS.data(), n->S, (size_t)N * 4, cudaMemcpyDeviceToHost));
+        double lo = 1e30, hi = -1e30;
+        for (float v : hS) { lo = std::min(lo, (double)std::log(v)); hi = std::max(hi, (double)std::log(v)); }
+        stats->logs_min = lo;
+        stats->logs_max = hi;
+        stats->best_epoch = best_epoch;
     }
     return SGIGA_OK;
 }

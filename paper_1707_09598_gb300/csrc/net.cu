@@ -171,6 +171,12 @@ __global__ void k_relu_mask(float* __restrict__ dA, const float* __restrict__ A,
         if (!(A[i] > 0.0f)) dA[i] = 0.0f;
 }
 
+__global__ void k_fill(float* __restrict__ x, float v, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) x[i] = v;
+}
+
 // phi = log(num / den) (FP64 ratio, FP32 result)
 __global__ void k_log_ratio(const double* __restrict__ num, const double* __restrict__ den, float* __restrict__ out,
                             long long n) {
@@ -346,6 +352,12 @@ cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, co
 cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
     k_relu_mask<<<eblocks(n), 256, 0, s>>>(dA, A, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* x, float v, long long n, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_fill<<<eblocks(n), 256, 0, s>>>(x, v, n);
     return cudaGetLastError();
 }
 

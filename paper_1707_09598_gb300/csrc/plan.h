@@ -90,7 +90,7 @@ struct sgiga_plan_s {
     int* d_nactive = nullptr;
     int* h_nactive = nullptr;   // pinned
     void* stage = nullptr;      // device staging for host pointers
-    double* feat = nullptr;     // coefficient features [nfeat][omega_0..2, phase]
+    double* acoef = nullptr;    // diffusion coefficient a(x_q) [nqp], natural order (null: a = 1)
     sgiga::Net* net = nullptr;  // learned correction network (allocated by sgiga_net_init)
     bool net_ready = false;
     bool learned_off = false;   // set for the rest of a solve after a refinement step without progress

@@ -69,7 +69,9 @@ class sgiga_train_cfg(ctypes.Structure):
 class sgiga_train_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int), ("samples", ctypes.c_int), ("rhs", ctypes.c_int), ("steps", ctypes.c_int),
                 ("loss_first_epoch", ctypes.c_double), ("loss_last_epoch", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("loss_initial", ctypes.c_double), ("loss_fd", ctypes.c_double),
+                ("loss_epoch", ctypes.c_double * 32), ("logs_min", ctypes.c_double), ("logs_max", ctypes.c_double),
+                ("best_epoch", ctypes.c_int)]
 
 
 class sgiga_tune_result(ctypes.Structure):
@@ -104,6 +106,7 @@ _SIGS = {
     "sgiga_set_rhs_builtin": (_I, [_P, _I]),
     "sgiga_get_rhs": (_I, [_P, _P]),
     "sgiga_set_coefficient": (_I, [_P, _I, _P, _P, _D]),
+    "sgiga_set_coefficient_qp": (_I, [_P, _P]),
     "sgiga_source_at_qp": (_I, [_P, _I, _P]),
     "sgiga_apply": (_I, [_P, _P, _P]),
     "sgiga_apply_f32": (_I, [_P, _P, _P]),
@@ -263,6 +266,11 @@ def sgiga_set_coefficient(plan, omega, phase, amp):
     om = np.ascontiguousarray(omega, dtype=np.float64)
     ph = np.ascontiguousarray(phase, dtype=np.float64)
     _check(_lib.sgiga_set_coefficient(plan, len(ph), om.ctypes.data, ph.ctypes.data, float(amp)))
+
+
+def sgiga_set_coefficient_qp(plan, a_qp):
+    """a(x) at every quadrature point ([nqp], natural order; host or device), or None."""
+    _check(_lib.sgiga_set_coefficient_qp(plan, None if a_qp is None else _ptr(a_qp, sgiga_plan_info(plan).nqp)))
 
 
 def sgiga_get_rhs(plan, b):

@@ -63,6 +63,39 @@ def test_perturbed_cube_with_coefficient(sg):
             assert _rel(u[sl], comp.solve()) < 1e-9, tuple(g.levels)
 
 
+def test_coefficient_given_at_quadrature_points(sg):
+    """A coefficient passed as values at the quadrature points (the oracle's
+    a(x) at the plan's own quadrature coordinates) gives the operator of the
+    oracle's assembly with that a, and the same operator as the plan's own
+    Fourier-feature evaluation of it."""
+    P, geom, a = _patch_plan(sg, 5)
+    kn, cp = perturbed_cube_patch(1)
+    with P, sg.Plan(3, 3, 5, domain="patch", patch=([3, 3, 3], kn, cp)) as Q:
+        xq = np.zeros(3 * Q.info.nqp)
+        sg.sgiga_qp_coords(Q.handle, xq)
+        aq = a(xq.reshape(3, -1).T)
+        sg.sgiga_set_coefficient_qp(Q.handle, aq)
+        n = P.info.ndof
+        x = torch.as_tensor(random_vector(n, 52), device="cuda")
+        y1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        y2 = torch.zeros_like(y1)
+        sg.sgiga_apply(P.handle, x, y1)
+        sg.sgiga_apply(Q.handle, x, y2)
+        y1, y2, xh = y1.cpu().numpy(), y2.cpu().numpy(), x.cpu().numpy()
+        assert _rel(y2, y1) < 1e-13
+        for g in Q.grids[:: max(1, len(Q.grids) // 4)]:
+            comp = Component(geom, tuple(g.levels), 3).assemble(diffusion=a)
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            assert _rel(y2[sl], comp.K @ xh[sl]) < 1e-12, tuple(g.levels)
+        sg.sgiga_set_coefficient_qp(Q.handle, None)      # back to a = 1
+        y3 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sg.sgiga_apply(Q.handle, x, y3)
+        g = Q.grids[0]
+        comp = Component(geom, tuple(g.levels), 3).assemble()
+        sl = slice(g.dof_off, g.dof_off + g.ndof)
+        assert _rel(y3.cpu().numpy()[sl], comp.K @ xh[sl]) < 1e-12
+
+
 @pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-12, 1e-10), ("mixed", 1e-9, 1e-8)])
 def test_perturbed_cube_full_size_against_stored_oracle(sg, precision, tol, bound):
     """The learned-preconditioner workload at its full size (p = 3, w = 12, 199
