@@ -482,8 +482,12 @@ int sgiga_net_set_scaling(sgiga_plan_t plan, const float* S);
 int sgiga_net_loss_grad(sgiga_plan_t plan, const float* r, const float* e, double* loss, float* grad);
 /* Record (residual, error) pairs from the plan's own FD-preconditioned FP64 CG
  * on seeded random right-hand sides and train N by Adam on the loss above,
- * back-propagated through S = exp(N(phi)). Overwrites the plan's load vector
- * and solution. */
+ * back-propagated through S = exp(N(phi)). In a recorded sample only the
+ * components whose residual was still above 1e-6 of their right-hand side
+ * count (a converged component's recorded error is rounding noise of two
+ * solves). The parameters of the epoch with the lowest mean loss are kept
+ * (the initial ones if no epoch improves on them). Overwrites the plan's load
+ * vector and solution. */
 int sgiga_train_net(sgiga_plan_t plan, const sgiga_train_cfg* cfg, sgiga_train_stats* stats /* may be NULL */);
 /* Checkpoint: magic "SGIGANET", version 2, taps, nparams, Adam step, then the
  * FP32 parameters and both Adam moments. */

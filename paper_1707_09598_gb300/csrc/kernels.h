@@ -167,7 +167,8 @@ cudaError_t launch_mul_active(const DevPlan& P, const float* S, const float* in,
 cudaError_t launch_pair_residual(const DevPlan& P, const float* S, const float* z1, const float* e, float* res,
                                  cudaStream_t s);
 cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res, const double* rr, const double* ee,
-                              float* delta, float* t2, double* lossacc, cudaStream_t s);
+                              const int* mask, double* cnt, float* delta, float* t2, double* lossacc, cudaStream_t s);
+cudaError_t launch_pair_mask(int ng, const double* rr, const double* bb, double thr2, int* mask, cudaStream_t s);
 cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delta, const float* z1, const float* r,
                              const float* z2, float weight, float* dls, cudaStream_t s);
 cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s);

@@ -18,9 +18,11 @@
 // residual r_k and the error e_k = x* - x_k of every component. One recorded
 // iteration is one training sample (all components at once).
 //
-// Loss of a sample: the mean over components of ||M(r) - e||^2 / ||e||^2; its
+// Loss of a sample: the mean over its counted components (those whose
+// residual was above 1e-6 of their right-hand side when recorded) of
+// ||M(r) - e||^2 / ||e||^2; its
 // gradient with respect to log S_i is S_i (delta_i FD(S r)_i + r_i FD(S delta)_i)
-// with delta = 2 (M(r) - e) / (||e||^2 ncomp) (FD symmetric).
+// with delta = 2 (M(r) - e) / (||e||^2 ncounted) (FD symmetric).
 #include <cstdio>
 #include <random>
 
@@ -41,8 +43,9 @@ struct Net {
     float *feat = nullptr;            // phi = log c (the network input)
     float *S = nullptr;               // scaling of the preconditioner
     float *tA = nullptr, *z1 = nullptr, *z2 = nullptr, *res = nullptr, *delta = nullptr;
-    double *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr;
+    double *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr, *cnt = nullptr;
     int* ok = nullptr;
+    int* masks = nullptr;             // per training sample: [ncomp] components that count
     bool feat_stale = true;           // the geometry planes changed since phi was computed
     bool s_stale = true;              // S must be recomputed from the network
     bool s_override = false;          // S was set by the caller (no network evaluation)
@@ -107,7 +110,8 @@ static int net_create(sgiga_plan_s* P) {
         (rc = nalloc(n, (void**)&n->m, n->np * 4)) || (rc = nalloc(n, (void**)&n->v, n->np * 4)) ||
         (rc = nalloc(n, &n->wb, n->nw * 2)) || (rc = nalloc(n, (void**)&n->wmap, n->np * 4)) ||
         (rc = nalloc(n, (void**)&n->dots, ng * 8)) || (rc = nalloc(n, (void**)&n->dots2, ng * 8)) ||
-        (rc = nalloc(n, (void**)&n->lossacc, 16)) || (rc = nalloc(n, (void**)&n->ok, ng * 4)))
+        (rc = nalloc(n, (void**)&n->lossacc, 16)) || (rc = nalloc(n, (void**)&n->ok, ng * 4)) ||
+        (rc = nalloc(n, (void**)&n->cnt, 8)))
         return rc;
     std::vector<int> wmap(n->np, -1);
     for (int l = 0; l < 3; ++l) {
@@ -237,9 +241,10 @@ int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active
 }
 
 // Loss of the pair (r, e) at the current S (accumulated into n->lossacc[0]
-// as the mean over components) and its gradient with respect to log S added
-// to dls scaled by `weight`.
-static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, float* dls, float weight) {
+// as the mean over the components that count: mask, or all when null) and
+// its gradient with respect to log S added to dls scaled by `weight`.
+static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, const int* mask, float* dls,
+                          float weight) {
     Net* n = P->net;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
@@ -249,7 +254,7 @@ static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, float
     CUDA_TRY(launch_pair_residual(D, n->S, n->z1, e, n->res, s));          // res = S z1 - e
     CUDA_TRY(launch_dot<float>(D, n->res, n->res, P->d_partial, n->dots, s));
     CUDA_TRY(launch_dot<float>(D, e, e, P->d_partial, n->dots2, s));
-    CUDA_TRY(launch_pair_delta(D, n->S, n->res, n->dots, n->dots2, n->delta, n->tA, n->lossacc, s));
+    CUDA_TRY(launch_pair_delta(D, n->S, n->res, n->dots, n->dots2, mask, n->cnt, n->delta, n->tA, n->lossacc, s));
     if ((rc = precond_fd<float>(P, n->tA, n->z2, nullptr, P->f_t1, P->f_t2))) return rc;
     CUDA_TRY(launch_pair_grad(D, n->S, n->delta, n->z1, r, n->z2, weight, dls, s));
     return SGIGA_OK;
@@ -262,7 +267,7 @@ static int dataset_loss(sgiga_plan_s* P, double* out) {
     CUDA_TRY(cudaMemsetAsync(n->lossacc, 0, 16, s));
     for (int k = 0; k < n->nsamples; ++k) {
         const float* r = n->data + (size_t)k * 2 * n->N;
-        int rc = pair_loss_grad(P, r, r + n->N, n->dY, 0.0f);
+        int rc = pair_loss_grad(P, r, r + n->N, n->masks + (size_t)k * P->comps.size(), n->dY, 0.0f);
         if (rc) return rc;
     }
     double h[2];
@@ -282,6 +287,13 @@ struct RecordHook : PcgHook {
         if (n->nsamples >= n->capacity || it >= limit) return 0;
         float* rd = n->data + (size_t)n->nsamples * 2 * n->N;
         cudaError_t e = launch_pair_store(P->dp, P->d_r, xstar, P->d_x, rd, rd + n->N, P->stream);
+        // the components that count: not yet at 1e-6 of their right-hand side
+        // (x* is converged to 1e-10; below 1e-6 the recorded error would carry
+        // x*'s own error, and a converged component's error is rounding noise)
+        const int ng = (int)P->comps.size();
+        if (e == cudaSuccess)
+            e = launch_pair_mask(ng, P->d_scal + 3 * ng, P->d_scal, 1e-12, n->masks + (size_t)n->nsamples * ng,
+                                 P->stream);
         if (e != cudaSuccess) return fail(SGIGA_ERR_CUDA, cudaGetErrorString(e));
         n->nsamples++;
         return 0;
@@ -414,7 +426,7 @@ int sgiga_net_loss_grad(sgiga_plan_t P, const float* r, const float* e, double* 
     cudaStream_t s = P->stream;
     CUDA_TRY(cudaMemsetAsync(n->lossacc, 0, 16, s));
     CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)P->ndof * 4, s));
-    if ((rc = pair_loss_grad(P, r, e, grad, 1.0f))) return rc;
+    if ((rc = pair_loss_grad(P, r, e, nullptr, grad, 1.0f))) return rc;
     CUDA_TRY(cudaMemcpyAsync(loss, n->lossacc, 8, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SGIGA_OK;
@@ -439,7 +451,11 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         if (n->data) { cudaFree(n->data); n->allocs.erase(std::find(n->allocs.begin(), n->allocs.end(), (void*)n->data)); }
         n->data = nullptr;
         n->capacity = 0;
-        if ((rc = nalloc(n, (void**)&n->data, (size_t)S * 2 * N * 4))) return rc;
+        if (n->masks) { cudaFree(n->masks); n->allocs.erase(std::find(n->allocs.begin(), n->allocs.end(), (void*)n->masks)); }
+        n->masks = nullptr;
+        if ((rc = nalloc(n, (void**)&n->data, (size_t)S * 2 * N * 4)) ||
+            (rc = nalloc(n, (void**)&n->masks, (size_t)S * ng * 4)))
+            return rc;
         n->capacity = S;
     }
     n->nsamples = 0;
@@ -505,7 +521,8 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
             CUDA_TRY(cudaMemsetAsync(n->dY, 0, N * 4, s));
             for (int k = k0; k < k0 + nb; ++k) {
                 const float* r = n->data + (size_t)order[k] * 2 * N;
-                if ((rc = pair_loss_grad(P, r, r + N, n->dY, 1.0f / nb))) return rc;
+                if ((rc = pair_loss_grad(P, r, r + N, n->masks + (size_t)order[k] * ng, n->dY, 1.0f / nb)))
+                    return rc;
             }
             CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, s));    // d/dlog S -> d/dy
             if ((rc = net_backward(P))) return rc;

@@ -229,12 +229,32 @@ __global__ void k_pair_residual(long long n, const float* __restrict__ S, const 
     for (; i < n; i += stride) res[i] = S[i] * z1[i] - e[i];
 }
 
-// delta = 2 res / (||e_g||^2 ncomp), t2 = S delta (components with e_g = 0: 0)
+// The components a sample counts: mask[g] != 0 (all when mask is null) and
+// e_g != 0; their number goes to cnt[0] (one block).
+__global__ void k_pair_count(int ng, const int* __restrict__ mask, const double* __restrict__ ee,
+                             double* __restrict__ cnt) {
+    __shared__ int red[32];
+    int v = 0;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) v += ((!mask || mask[g]) && ee[g] > 0.0) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        cnt[0] = (double)t;
+    }
+}
+
+// delta = 2 res / (||e_g||^2 count) on the counted components, 0 elsewhere;
+// t2 = S delta
 __global__ void k_pair_delta(DevPlan P, const float* __restrict__ S, const float* __restrict__ res,
-                             const double* __restrict__ ee, float* __restrict__ delta, float* __restrict__ t2) {
+                             const double* __restrict__ ee, const int* __restrict__ mask,
+                             const double* __restrict__ cnt, float* __restrict__ delta, float* __restrict__ t2) {
     const Chunk c = P.chunks[blockIdx.x];
     const double e2 = ee[c.grid];
-    const float f = e2 > 0.0 ? (float)(2.0 / (e2 * (double)P.ncomps)) : 0.0f;
+    const bool use = (!mask || mask[c.grid]) && e2 > 0.0 && cnt[0] > 0.0;
+    const float f = use ? (float)(2.0 / (e2 * cnt[0])) : 0.0f;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
         const float dl = f * res[k];
@@ -243,20 +263,30 @@ __global__ void k_pair_delta(DevPlan P, const float* __restrict__ S, const float
     }
 }
 
-// acc[0] += mean over components of rr_g / ee_g (one block)
+// acc[0] += mean over the counted components of rr_g / ee_g (one block)
 __global__ void k_pair_loss(int ng, const double* __restrict__ rr, const double* __restrict__ ee,
-                            double* __restrict__ acc) {
+                            const int* __restrict__ mask, const double* __restrict__ cnt, double* __restrict__ acc) {
     __shared__ double red[32];
     double v = 0.0;
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) v += ee[g] > 0.0 ? rr[g] / ee[g] : 0.0;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x)
+        v += ((!mask || mask[g]) && ee[g] > 0.0) ? rr[g] / ee[g] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        acc[0] += t / (double)ng;
+        if (cnt[0] > 0.0) acc[0] += t / cnt[0];
     }
+}
+
+// mask[g] = ||r_g||^2 > thr2 ||b_g||^2: the component had not converged when
+// the pair was recorded (a converged component's error is the noise of two
+// solves, not the error of its residual)
+__global__ void k_pair_mask(int ng, const double* __restrict__ rr, const double* __restrict__ bb, double thr2,
+                            int* __restrict__ mask) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) mask[g] = rr[g] > thr2 * bb[g] ? 1 : 0;
 }
 
 // dls += weight * S (delta z1 + r z2): the gradient with respect to log S
@@ -395,14 +425,23 @@ cudaError_t launch_pair_residual(const DevPlan& P, const float* S, const float* 
 }
 
 cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res, const double* rr, const double* ee,
-                              float* delta, float* t2, double* lossacc, cudaStream_t s) {
+                              const int* mask, double* cnt, float* delta, float* t2, double* lossacc, cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_pair_delta<<<P.nchunks, 256, 0, s>>>(P, S, res, ee, delta, t2);
+    k_pair_count<<<1, 256, 0, s>>>(P.ncomps, mask, ee, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_pair_loss<<<1, 256, 0, s>>>(P.ncomps, rr, ee, lossacc);
+    k_pair_delta<<<P.nchunks, 256, 0, s>>>(P, S, res, ee, mask, cnt, delta, t2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    SGIGA_COUNT_LAUNCH();
+    k_pair_loss<<<1, 256, 0, s>>>(P.ncomps, rr, ee, mask, cnt, lossacc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_mask(int ng, const double* rr, const double* bb, double thr2, int* mask, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_pair_mask<<<(ng + 127) / 128, 128, 0, s>>>(ng, rr, bb, thr2, mask);
     return cudaGetLastError();
 }
 
