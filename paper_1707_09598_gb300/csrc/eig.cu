@@ -9,7 +9,8 @@
 //      of inertia, the number of eigenvalues below s equals the number of
 //      negative pivots of the LDL^T factorisation of K - s M (M positive
 //      definite), computed in one banded sweep;
-//   2. runs of close eigenvalues (relative gap below 1e-3) found on the host;
+//   2. units of close eigenvalues (relative gaps below 1e-6, or below 1e-3
+//      up to 4 members) found on the host;
 //   3. eigenvectors by inverse iteration, one thread per cluster: three
 //      solves (K - s M) y = M v with banded LU and partial pivoting, each
 //      followed by M-orthogonalisation against the cluster's earlier vectors
@@ -318,14 +319,16 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
         msg = "eigenvalue bisection";
         return e;
     }
-    // units: runs of close eigenvalues (relative gap below 1e-3), at most 32
-    // per unit. Inverse iteration alone leaves two eigenvectors M-orthogonal
-    // only to about eps lam / gap; maximally smooth splines have pairs of modes
+    // units of eigenvalues whose vectors are M-orthogonalised against each
+    // other. Inverse iteration alone leaves two eigenvectors M-orthogonal only
+    // to about eps lam / gap. Maximally smooth splines have pairs of modes
     // localised at the two ends of the interval whose eigenvalues agree to
-    // many digits (uniform and symmetric graded meshes), and the top of the
-    // spectrum is dense on fine levels. The cap bounds one thread's
-    // Gram-Schmidt work; neighbours across a cut keep the eps lam / gap
-    // orthogonality of gaps above 1e-3 lam.
+    // many digits (uniform and symmetric graded meshes): neighbours with a
+    // relative gap below 1e-6 always share a unit (up to 32 members). The top
+    // of the spectrum is dense on fine levels: neighbours with a relative gap
+    // below 1e-3 share a unit while it has fewer than 4 members, which keeps
+    // each thread's Gram-Schmidt work small; across a cut the gap is above
+    // 1e-6 lam.
     std::vector<int2> units;
     std::vector<long long> uoff(jobs.size() + 1, 0);
     size_t scratch_doubles = 0;
@@ -341,7 +344,11 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
         uoff[q] = (long long)units.size();
         for (int j = 0; j < J.n;) {
             int j1 = j + 1;
-            while (j1 < J.n && j1 - j < 32 && l[j1] - l[j1 - 1] <= 1e-3 * l[j1]) ++j1;
+            while (j1 < J.n) {
+                const double gap = l[j1] - l[j1 - 1], size = j1 - j;
+                if ((gap <= 1e-6 * l[j1] && size < 32) || (gap <= 1e-3 * l[j1] && size < 4)) ++j1;
+                else break;
+            }
             units.push_back(make_int2(j, j1 - j));
             j = j1;
         }
