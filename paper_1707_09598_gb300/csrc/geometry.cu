@@ -394,13 +394,6 @@ cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh,
 
 // Physical coordinates and Jacobian determinant of the patch map at
 // parametric points (eq. F-B-splines; NURBS with separable weights).
-// patch_eval called out of line: inlined into this kernel, the build produced
-// NaN maps (the other call sites, checked by the parity tests, are correct
-// inlined); this kernel is off the hot path.
-__device__ __noinline__ void patch_eval_call(const Patch& pt, const double* t, double* X, double (*J)[3]) {
-    patch_eval(pt, t, X, J);
-}
-
 __global__ void k_map_points(DevPlan P, const double* xi, const int* patch, long long npts, int npatch, double* x,
                              double* detj) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,7 +407,7 @@ __global__ void k_map_points(DevPlan P, const double* xi, const int* patch, long
         t[k] = xi[j * d + k];
         if (!(t[k] >= 0.0 && t[k] <= 1.0)) { atomicOr(&P.flags[1], 1); t[k] = t[k] < 0.0 ? 0.0 : 1.0; }
     }
-    patch_eval_call(P.patch[q], t, X, J);
+    patch_eval(P.patch[q], t, X, J);
     for (int k = 0; k < d; ++k) x[j * d + k] = X[k];
     if (detj) {
         double dt;

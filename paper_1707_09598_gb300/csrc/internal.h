@@ -110,6 +110,13 @@ struct Chunk {
     int piece;
 };
 
+// A tile of the network's tensor-core convolutions: 64 consecutive voxels
+// (packed DoFs) of one vector chunk, from offset off.
+struct ConvTile {
+    int chunk;
+    int off;
+};
+
 // Work item of the batched mode product of the preconditioner.
 //   FD_SMALL: grid = piece, c0 = first output of the piece's tensor (256 per item)
 //   FD_ROWS / FD_TILE: grid = piece, rows from i0, columns from c0 (a*B + b)

@@ -154,11 +154,20 @@ cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* 
                                double* partial, double* rr, cudaStream_t s);
 cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);
 // net.cu (learned scaling network) and learned.cu
-cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, const float* bias, const float* X,
-                        float* Y, int transpose, int relu, cudaStream_t s);
-cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, const float* dZ, float* dW, float* db,
-                         cudaStream_t s);
-cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s);
+// conv.cu: the network's convolutions (32-channel activations as BF16 rows [N][32])
+cudaError_t launch_conv_in(const DevPlan& P, const void* W, const float* b, const float* x, void* out,
+                           cudaStream_t s);
+cudaError_t launch_conv_out(const DevPlan& P, const void* W, const float* b, const void* A, float* y,
+                            cudaStream_t s);
+cudaError_t launch_convT_out(const DevPlan& P, const void* W, const float* dy, const void* act, void* dA,
+                             cudaStream_t s);
+cudaError_t launch_conv_mid(const DevPlan& P, const ConvTile* tiles, int ntiles, const void* Wt, const float* bias,
+                            const void* X, const void* gate, int relu, void* out, cudaStream_t s);
+cudaError_t launch_wgrad_mid(const DevPlan& P, const ConvTile* tiles, int ntiles, const void* X, const void* dZ,
+                             float* dW, float* db, cudaStream_t s);
+cudaError_t launch_wgrad_in(const DevPlan& P, const float* x, const void* dZ, float* dW, float* db, cudaStream_t s);
+cudaError_t launch_wgrad_out(const DevPlan& P, const float* dy, const void* A, float* dW, float* db, cudaStream_t s);
+cudaError_t launch_arrange_mid(const void* W, int T, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t launch_fill(float* x, float v, long long n, cudaStream_t s);
 cudaError_t launch_log_ratio(const double* num, const double* den, float* out, long long n, cudaStream_t s);
 cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s);

@@ -39,7 +39,11 @@ struct Net {
     void* wb = nullptr;               // BF16 weights
     int* wmap = nullptr;
     int step = 0;
-    float *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *Y = nullptr, *dY = nullptr, *dA1 = nullptr, *dA2 = nullptr;
+    float *A0 = nullptr, *Y = nullptr, *dY = nullptr;
+    void *A1 = nullptr, *A2 = nullptr, *dA1 = nullptr, *dA2 = nullptr;   // BF16 [N][32]
+    void *wf = nullptr, *wbk = nullptr;   // layer 2's BF16 weights arranged for the tensor cores
+    ConvTile* tiles = nullptr;            // 64-voxel tiles of the tensor-core convolutions
+    int ntiles = 0;
     float *feat = nullptr;            // phi = log c (the network input)
     float *S = nullptr;               // scaling of the preconditioner
     float *tA = nullptr, *z1 = nullptr, *z2 = nullptr, *res = nullptr, *delta = nullptr;
@@ -103,9 +107,17 @@ static int net_create(sgiga_plan_s* P) {
                       (void**)&n->tA, (void**)&n->z1, (void**)&n->z2, (void**)&n->res, (void**)&n->delta};
     for (void** b : bufs1)
         if ((rc = nalloc(n, b, N * 4))) return rc;
-    void** bufs32[] = {(void**)&n->A1, (void**)&n->A2, (void**)&n->dA1, (void**)&n->dA2};
+    void** bufs32[] = {&n->A1, &n->A2, &n->dA1, &n->dA2};
     for (void** b : bufs32)
-        if ((rc = nalloc(n, b, 32 * N * 4))) return rc;
+        if ((rc = nalloc(n, b, 32 * N * 2))) return rc;
+    if ((rc = nalloc(n, &n->wf, (size_t)n->T * 32 * 32 * 2)) || (rc = nalloc(n, &n->wbk, (size_t)n->T * 32 * 32 * 2)))
+        return rc;
+    std::vector<ConvTile> tl;
+    for (size_t c = 0; c < P->chunks.size(); ++c)
+        for (int o = 0; o < P->chunks[c].len; o += 64) tl.push_back(ConvTile{(int)c, o});
+    n->ntiles = (int)tl.size();
+    if ((rc = nalloc(n, (void**)&n->tiles, tl.size() * sizeof(ConvTile)))) return rc;
+    CUDA_TRY(cudaMemcpy(n->tiles, tl.data(), tl.size() * sizeof(ConvTile), cudaMemcpyHostToDevice));
     if ((rc = nalloc(n, (void**)&n->p, n->np * 4)) || (rc = nalloc(n, (void**)&n->g, n->np * 4)) ||
         (rc = nalloc(n, (void**)&n->m, n->np * 4)) || (rc = nalloc(n, (void**)&n->v, n->np * 4)) ||
         (rc = nalloc(n, &n->wb, n->nw * 2)) || (rc = nalloc(n, (void**)&n->wmap, n->np * 4)) ||
@@ -161,43 +173,43 @@ static int net_features(sgiga_plan_s* P) {
     return rc;
 }
 
+static const void* wl(const Net* n, int l) { return (const char*)n->wb + n->obw[l] * 2; }
+
 static int net_upload(sgiga_plan_s* P, const std::vector<float>& host) {
     Net* n = P->net;
     CUDA_TRY(cudaMemcpy(n->p, host.data(), n->np * 4, cudaMemcpyHostToDevice));
     CUDA_TRY(launch_f2bf(n->p, n->wmap, n->wb, n->np, P->stream));
+    CUDA_TRY(launch_arrange_mid(wl(n, 1), n->T, n->wf, n->wbk, P->stream));
     CUDA_TRY(cudaStreamSynchronize(P->stream));
     n->s_stale = true;
     n->s_override = false;
     return SGIGA_OK;
 }
 
-static const void* wl(const Net* n, int l) { return (const char*)n->wb + n->obw[l] * 2; }
 
-// forward: A0 (1 channel) -> A1 -> A2 -> Y
+// forward: A0 (1 channel) -> A1 -> A2 (BF16 rows) -> Y
 static int net_forward(sgiga_plan_s* P) {
     Net* n = P->net;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    CUDA_TRY(launch_conv(D, 1, 32, wl(n, 0), n->p + n->ob[0], n->A0, n->A1, 0, 1, s));
-    CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), n->p + n->ob[1], n->A1, n->A2, 0, 1, s));
-    CUDA_TRY(launch_conv(D, 32, 1, wl(n, 2), n->p + n->ob[2], n->A2, n->Y, 0, 0, s));
+    CUDA_TRY(launch_conv_in(D, wl(n, 0), n->p + n->ob[0], n->A0, n->A1, s));
+    CUDA_TRY(launch_conv_mid(D, n->tiles, n->ntiles, n->wf, n->p + n->ob[1], n->A1, nullptr, 1, n->A2, s));
+    CUDA_TRY(launch_conv_out(D, wl(n, 2), n->p + n->ob[2], n->A2, n->Y, s));
     return SGIGA_OK;
 }
 
-// backward from dY: gradients of every parameter into g (cleared first)
+// backward from dY: gradients of every parameter into g (cleared first); the
+// data gradients pass the ReLUs through the forward activations
 static int net_backward(sgiga_plan_s* P) {
     Net* n = P->net;
     const DevPlan& D = P->dp;
     cudaStream_t s = P->stream;
-    const long long N = n->N;
     CUDA_TRY(cudaMemsetAsync(n->g, 0, n->np * 4, s));
-    CUDA_TRY(launch_wgrad(D, 32, 1, n->A2, n->dY, n->g + n->oW[2], n->g + n->ob[2], s));
-    CUDA_TRY(launch_conv(D, 1, 32, wl(n, 2), nullptr, n->dY, n->dA2, 1, 0, s));
-    CUDA_TRY(launch_relu_mask(n->dA2, n->A2, 32 * N, s));
-    CUDA_TRY(launch_wgrad(D, 32, 32, n->A1, n->dA2, n->g + n->oW[1], n->g + n->ob[1], s));
-    CUDA_TRY(launch_conv(D, 32, 32, wl(n, 1), nullptr, n->dA2, n->dA1, 1, 0, s));
-    CUDA_TRY(launch_relu_mask(n->dA1, n->A1, 32 * N, s));
-    CUDA_TRY(launch_wgrad(D, 1, 32, n->A0, n->dA1, n->g + n->oW[0], n->g + n->ob[0], s));
+    CUDA_TRY(launch_wgrad_out(D, n->dY, n->A2, n->g + n->oW[2], n->g + n->ob[2], s));
+    CUDA_TRY(launch_convT_out(D, wl(n, 2), n->dY, n->A2, n->dA2, s));
+    CUDA_TRY(launch_wgrad_mid(D, n->tiles, n->ntiles, n->A1, n->dA2, n->g + n->oW[1], n->g + n->ob[1], s));
+    CUDA_TRY(launch_conv_mid(D, n->tiles, n->ntiles, n->wbk, nullptr, n->dA2, n->A1, 0, n->dA1, s));
+    CUDA_TRY(launch_wgrad_in(D, n->A0, n->dA1, n->g + n->oW[0], n->g + n->ob[0], s));
     return SGIGA_OK;
 }
 
@@ -531,6 +543,7 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
             const float lr = cfg->lr * std::min(1.0f, (float)steps / 50.0f);
             CUDA_TRY(launch_adam(n->p, n->g, n->m, n->v, n->wb, n->wmap, n->np, lr, 0.9f, 0.999f, 1e-8f,
                                  n->step, s));
+            CUDA_TRY(launch_arrange_mid(wl(n, 1), n->T, n->wf, n->wbk, s));
         }
         double hacc[2];
         CUDA_TRY(cudaMemcpyAsync(hacc, n->lossacc, 16, cudaMemcpyDeviceToHost, s));

@@ -7,169 +7,16 @@
 //   coefficient of each DoF,
 //
 // N = three 3x3(x3) convolutions over each component's DoF tensor with zero
-// padding, 1 -> 32 -> 32 -> 1 channels, ReLU after the first two. Weights are
-// kept as an FP32 master copy (Adam) and a BF16 copy used by every forward and
-// backward kernel; all accumulation is FP32. Activations are channel planes
-// over the packed vector of all components: X[c][v].
+// padding, 1 -> 32 -> 32 -> 1 channels, ReLU after the first two (conv.cu).
+// Weights are kept as an FP32 master copy (Adam) and a BF16 copy used by
+// every forward and backward kernel; all accumulation is FP32.
 //
-// Kernels (one thread per DoF for the convolutions, weights staged in shared
-// memory as FP32 [tap][c_in][c_out]):
-//   conv      Y[co][v] = b[co] + sum_{tap,ci} W[co][ci][tap] X[ci][nb(v,tap)]
-//   convT     data gradient: the same with W transposed and taps mirrored
-//   wgrad     dW[co][ci][tap] += sum_v dZ[co][v] X[ci][nb(v,tap)] (tiles of 32
-//             DoFs gathered im2col-style in shared memory, 8x32 thread grid,
-//             partial sums in registers, one atomic add per block and weight)
-//   relu/mask, features, scaling, pair loss and gradient, Adam.
+// Kernels here: features, scaling, pair loss and gradient, Adam.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
 
 namespace sgiga {
-
-// neighbour of packed DoF (grid-local index loc) at tap offset (ox, oy, oz)
-struct NbInfo {
-    int n0, n1, n2;
-    long long off;
-};
-
-__device__ __forceinline__ long long nb_index(const NbInfo& g, int i0, int i1, int i2, int tap, int d) {
-    int o0, o1, o2;
-    if (d == 3) { o0 = tap % 3 - 1; o1 = (tap / 3) % 3 - 1; o2 = tap / 9 - 1; }
-    else { o0 = tap % 3 - 1; o1 = tap / 3 - 1; o2 = 0; }
-    int j0 = i0 + o0, j1 = i1 + o1, j2 = i2 + o2;
-    if (j0 < 0 || j0 >= g.n0 || j1 < 0 || j1 >= g.n1 || j2 < 0 || j2 >= g.n2) return -1;
-    return g.off + j0 + (long long)g.n0 * (j1 + (long long)g.n1 * j2);
-}
-
-// ---------------------------------------------------------------------------
-// convolution (forward, or data gradient with mirrored taps and swapped channels)
-// ---------------------------------------------------------------------------
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256, 2)
-k_conv(DevPlan P, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, const float* __restrict__ X,
-       float* __restrict__ Y, long long N, int transpose, int relu) {
-    extern __shared__ float ws[];   // [taps][CIN][COUT]
-    const int d = P.d, T = d == 3 ? 27 : 9;
-    // stage weights: forward ws[(t*CIN+ci)*COUT+co] = W[co][ci][t];
-    // transposed (layer with cout=CIN, cin=COUT): W[ci'][co'][T-1-t] with ci' = co, co' = ci
-    const int nw = T * CIN * COUT;
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
-        int co = i % COUT, r = i / COUT, ci = r % CIN, t = r / CIN;
-        float v;
-        if (!transpose) v = __bfloat162float(W[((long long)co * CIN + ci) * T + t]);
-        else v = __bfloat162float(W[((long long)ci * COUT + co) * T + (T - 1 - t)]);
-        ws[i] = v;
-    }
-    __syncthreads();
-    const Chunk c = P.chunks[blockIdx.x];
-    const GridDesc& g = P.grids[c.grid];
-    NbInfo nb{g.n[0], d > 1 ? g.n[1] : 1, d > 2 ? g.n[2] : 1, g.dof_off};
-    for (int k = threadIdx.x; k < c.len; k += blockDim.x) {
-        const long long v = c.start + k;
-        long long loc = v - g.dof_off;
-        int i0 = (int)(loc % nb.n0);
-        loc /= nb.n0;
-        int i1 = (int)(loc % nb.n1);
-        int i2 = (int)(loc / nb.n1);
-        float acc[COUT];
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.0f;
-        for (int t = 0; t < T; ++t) {
-            long long u = nb_index(nb, i0, i1, i2, t, d);
-            if (u < 0) continue;
-            const float* wt = ws + t * CIN * COUT;
-#pragma unroll 2
-            for (int ci = 0; ci < CIN; ++ci) {
-                const float x = X[(long long)ci * N + u];
-#pragma unroll
-                for (int co = 0; co < COUT; ++co) acc[co] += wt[ci * COUT + co] * x;
-            }
-        }
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) {
-            float y = acc[co];
-            if (relu) y = y > 0.0f ? y : 0.0f;
-            Y[(long long)co * N + v] = y;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// weight gradient: dW[co][ci][t] += sum_v dZ[co][v] X[ci][nb(v, t)],
-// db[co] += sum_v dZ[co][v]
-// ---------------------------------------------------------------------------
-template <int CIN, int COUT, int RPT>
-__global__ void __launch_bounds__(256, 1)
-k_wgrad(DevPlan P, const float* __restrict__ X, const float* __restrict__ dZ, float* __restrict__ dW,
-        float* __restrict__ db, long long N) {
-    extern __shared__ float sh[];
-    const int d = P.d, T = d == 3 ? 27 : 9;
-    const int ROWS = CIN * T;
-    constexpr int VT = 32;                          // DoFs per tile
-    float* xcol = sh;                               // [VT][ROWS]
-    float* dzt = sh + VT * ROWS;                    // [VT][COUT]
-    const int RG = 256 / COUT;                      // row groups
-    const int col = threadIdx.x % COUT, rg = threadIdx.x / COUT;
-    float acc[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) acc[i] = 0.0f;
-    float bacc = 0.0f;
-    for (int ch = blockIdx.x; ch < P.nchunks; ch += gridDim.x) {
-        const Chunk c = P.chunks[ch];
-        const GridDesc& g = P.grids[c.grid];
-        NbInfo nb{g.n[0], d > 1 ? g.n[1] : 1, d > 2 ? g.n[2] : 1, g.dof_off};
-        for (int t0 = 0; t0 < c.len; t0 += VT) {
-            const int nv = min(VT, c.len - t0);
-            __syncthreads();
-            for (int i = threadIdx.x; i < VT * ROWS; i += blockDim.x) {
-                int vv = i / ROWS, row = i % ROWS;
-                float val = 0.0f;
-                if (vv < nv) {
-                    long long v = c.start + t0 + vv, loc = v - g.dof_off;
-                    int i0 = (int)(loc % nb.n0);
-                    loc /= nb.n0;
-                    int i1 = (int)(loc % nb.n1), i2 = (int)(loc / nb.n1);
-                    int ci = row / T, t = row % T;
-                    long long u = nb_index(nb, i0, i1, i2, t, d);
-                    if (u >= 0) val = X[(long long)ci * N + u];
-                }
-                xcol[i] = val;
-            }
-            for (int i = threadIdx.x; i < VT * COUT; i += blockDim.x) {
-                int vv = i / COUT, co = i % COUT;
-                dzt[i] = vv < nv ? dZ[(long long)co * N + c.start + t0 + vv] : 0.0f;
-            }
-            __syncthreads();
-            for (int vv = 0; vv < nv; ++vv) {
-                const float z = dzt[vv * COUT + col];
-                if (rg == 0) bacc += z;
-                const float* xr = xcol + vv * ROWS;
-#pragma unroll
-                for (int i = 0; i < RPT; ++i) {
-                    int row = rg + i * RG;
-                    if (row < ROWS) acc[i] += xr[row] * z;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-        int row = rg + i * RG;
-        if (row < ROWS) {
-            int ci = row / T, t = row % T;
-            atomicAdd(&dW[((long long)col * CIN + ci) * T + t], acc[i]);
-        }
-    }
-    if (rg == 0) atomicAdd(&db[col], bacc);
-}
-
-// dA *= (A > 0): ReLU backward through the post-activation values
-__global__ void k_relu_mask(float* __restrict__ dA, const float* __restrict__ A, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += stride)
-        if (!(A[i] > 0.0f)) dA[i] = 0.0f;
-}
 
 __global__ void k_fill(float* __restrict__ x, float v, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,50 +186,6 @@ __global__ void k_f2bf(const float* __restrict__ p, const int* __restrict__ wmap
 static unsigned eblocks(long long n) {
     long long b = (n + 255) / 256;
     return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
-}
-
-cudaError_t launch_conv(const DevPlan& P, int cin, int cout, const void* W, const float* bias, const float* X,
-                        float* Y, int transpose, int relu, cudaStream_t s) {
-    const int T = P.d == 3 ? 27 : 9;
-    const long long N = P.ndof;
-    if (P.nchunks == 0) return cudaSuccess;
-    const size_t sm = (size_t)T * cin * cout * sizeof(float);
-    const __nv_bfloat16* w = (const __nv_bfloat16*)W;
-    SGIGA_COUNT_LAUNCH();
-#define CONV(CI, CO)                                                                                       \
-    if (cin == CI && cout == CO) {                                                                         \
-        cudaFuncSetAttribute(k_conv<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);      \
-        k_conv<CI, CO><<<P.nchunks, 256, sm, s>>>(P, w, bias, X, Y, N, transpose, relu);                 \
-        return cudaGetLastError();                                                                         \
-    }
-    CONV(32, 32) CONV(32, 1) CONV(1, 32)
-#undef CONV
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_wgrad(const DevPlan& P, int cin, int cout, const float* X, const float* dZ, float* dW, float* db,
-                         cudaStream_t s) {
-    const int T = P.d == 3 ? 27 : 9;
-    const long long N = P.ndof;
-    if (P.nchunks == 0) return cudaSuccess;
-    const size_t sm = (size_t)32 * (cin * T + cout) * sizeof(float);
-    const int blocks = P.nchunks < 2 * 152 ? P.nchunks : 2 * 152;
-    SGIGA_COUNT_LAUNCH();
-#define WG(CI, CO, R)                                                                                      \
-    if (cin == CI && cout == CO) {                                                                         \
-        cudaFuncSetAttribute(k_wgrad<CI, CO, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);  \
-        k_wgrad<CI, CO, R><<<blocks, 256, sm, s>>>(P, X, dZ, dW, db, N);                                  \
-        return cudaGetLastError();                                                                         \
-    }
-    WG(1, 32, 4) WG(32, 32, 108) WG(32, 1, 4)
-#undef WG
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_relu_mask(float* dA, const float* A, long long n, cudaStream_t s) {
-    SGIGA_COUNT_LAUNCH();
-    k_relu_mask<<<eblocks(n), 256, 0, s>>>(dA, A, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_fill(float* x, float v, long long n, cudaStream_t s) {

@@ -6,7 +6,12 @@ and profiler captures of a single kernel family).
 Ops: apply (stiffness apply), apply_f32 / precond_f32 (the FP32 kernels of
 the mixed-precision plan), precond (fast diagonalisation), rhs (load
 vector), solve (batched PCG), eval (evaluation + combination on the 17^d
-lattice). Prints the mean CUDA-event time per repetition.
+lattice), solve_scaled (the perturbed-cube mixed solve with the scaled
+preconditioner S * FD(S * r), S = c^(-1/2), to 1e-8 with inner solves to
+1e-3: the kernels of the learned + mixed solve without its training).
+--coef sets the log-normal coefficient (128 Fourier features, seed 2);
+--host-loop runs the CG loops from the host (profilers then list every
+kernel). Prints the mean CUDA-event time per repetition.
 """
 import argparse
 import os
@@ -25,7 +30,9 @@ from paper_1707_09598_gb300.inputs import eval_points, random_vector  # noqa: E4
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="apply", choices=["apply", "apply_f32", "precond", "precond_f32", "rhs", "solve",
-                                                      "eval"])
+                                                      "eval", "solve_scaled"])
+    ap.add_argument("--coef", action="store_true")
+    ap.add_argument("--host-loop", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--p", type=int, default=3)
@@ -37,7 +44,7 @@ def main():
     # torch's fills and reads of the buffers handed to the plan run on the
     # plan's stream, in order with its calls
     torch.cuda.set_stream(stream)
-    f32 = a.op.endswith("_f32")
+    f32 = a.op.endswith("_f32") or a.op == "solve_scaled"
     kw = {}
     if a.domain == "perturbed":   # the learned-preconditioner geometry: seeded cubic perturbation, general metric
         from paper_1707_09598_gb300.inputs import perturbed_cube_patch
@@ -45,9 +52,21 @@ def main():
         kw = dict(domain="patch", patch=([3, 3, 3], kn, cp))
     else:
         kw = dict(domain=a.domain)
-    P = sgiga.Plan(a.d, a.p, a.w, stream=stream, precision="mixed" if f32 else "fp64", **kw)
+    P = sgiga.Plan(a.d, a.p, a.w, stream=stream, precision="mixed" if f32 else "fp64",
+                   precond="learned" if a.op == "solve_scaled" else "fd", **kw)
+    if a.coef or a.op == "solve_scaled":
+        from paper_1707_09598_gb300.inputs import lognormal_features
+        om, ph, amp = lognormal_features(2, nfeat=128)
+        sgiga.sgiga_set_coefficient(P.handle, om, ph, amp)
     if a.tune:
         sgiga.sgiga_autotune(P.handle, reps=3)
+    if a.op == "solve_scaled":
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=not a.host_loop, inner_tol=1e-3, inner_max=100)
+        phi = torch.zeros(P.info.ndof, dtype=torch.float32, device="cuda")
+        sgiga.sgiga_net_features(P.handle, phi)
+        sgiga.sgiga_net_set_scaling(P.handle, torch.exp(-0.5 * phi).contiguous())
+    elif a.host_loop:
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
     n = P.info.ndof
     x = torch.as_tensor(random_vector(n, 1), device="cuda")
     if f32:
@@ -72,6 +91,8 @@ def main():
             sgiga.sgiga_set_rhs_builtin(P.handle, src)
         elif a.op == "solve":
             sgiga.sgiga_solve(P.handle, 1e-12, 50)
+        elif a.op == "solve_scaled":
+            sgiga.sgiga_solve(P.handle, 1e-8, 50)
         else:
             sgiga.sgiga_eval(P.handle, pts, len(pts), uc)
             sgiga.sgiga_combine(P.handle, uc, len(pts), u)

@@ -133,15 +133,45 @@ def _bf16(x):
     return torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
 
 
-def test_network_kernels_against_oracle(sg):
-    """Forward and backward of the CUDA network (BF16 weights, FP32 accumulation)
-    against the oracle's FP64 network with the same BF16-rounded weights."""
-    with sg.Plan(3, 2, 4, precision="mixed", precond="learned") as P:
+def _bf16_t(x):
+    return _bf16(np.asarray(x)).reshape(np.shape(x))
+
+
+def _emulated_net(params, x, dy, d):
+    """The network with the kernels' storage precision emulated around the
+    oracle's FP64 convolutions: the 32-channel activations and their data
+    gradients are stored as BF16 (rounded to nearest), everything else FP64."""
+    T = 3 ** d
+    (W1, b1), (W2, b2), (W3, b3) = net.unpack(params, d)
+    A1 = _bf16_t(np.maximum(net.conv(x, W1, b1), 0.0))
+    A2 = _bf16_t(np.maximum(net.conv(A1, W2, b2), 0.0))
+    Y = net.conv(A2, W3, b3)[0]
+    dY = dy[None]
+    gW3 = net.conv_weight_grad(dY, A2, T)
+    gb3 = dY.reshape(1, -1).sum(axis=1)
+    dA2 = _bf16_t(net.conv_input_grad(dY, W3) * (A2 > 0))
+    gW2 = net.conv_weight_grad(dA2, A1, T)
+    gb2 = dA2.reshape(32, -1).sum(axis=1)
+    dA1 = _bf16_t(net.conv_input_grad(dA2, W2) * (A1 > 0))
+    gW1 = net.conv_weight_grad(dA1, x, T)
+    gb1 = dA1.reshape(32, -1).sum(axis=1)
+    return Y, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+
+
+@pytest.mark.parametrize("d,p,w", [(3, 2, 4), (2, 3, 6)])
+def test_network_kernels_against_oracle(sg, d, p, w):
+    """Forward and backward of the CUDA network (BF16 weights and 32-channel
+    activations, FP32 accumulation; the 32 x 32 layer on the tensor cores)
+    against the oracle's FP64 network with the same BF16 weights and the
+    activations rounded to BF16 where the kernels store them. The bounds allow
+    an activation that rounds the other way in one of the two (one BF16 unit,
+    2^-8 relative, in a few entries) and FP32 accumulation order."""
+    with sg.Plan(d, p, w, precision="mixed", precond="learned") as P:
         sg.sgiga_net_init(P.handle, 7)
         params = sg.sgiga_net_get_params(P.handle).astype(np.float64)
         npar = params.size
         # round weights (not biases) as the kernels do
-        T = 27
+        T = 3 ** d
         q, o = params.copy(), 0
         for ci, co in zip(net.CIN, net.COUT):
             q[o:o + co * ci * T] = _bf16(q[o:o + co * ci * T])
@@ -156,16 +186,17 @@ def test_network_kernels_against_oracle(sg):
         grad = sg.sgiga_net_backward(P.handle, torch.as_tensor(inp, device="cuda"),
                                      torch.as_tensor(dy, device="cuda"))
         out = out.cpu().numpy()
-        shapes = [tuple(g.n[:3]) for g in P.grids]
+        shapes = [tuple(g.n[:d]) for g in P.grids]
         xs = net.split_packed(inp.astype(np.float64), shapes)
         dys = net.split_packed(dy.astype(np.float64), shapes)
-        ref = np.concatenate([net.forward(q, x)[0].ravel() for x in xs])
-        assert _rel(out, ref) < 2e-5
-        gref = sum(net.backward(q, x, d_) for x, d_ in zip(xs, dys))
+        res = [_emulated_net(q, x, d_, d) for x, d_ in zip(xs, dys)]
+        ref = np.concatenate([r[0].ravel() for r in res])
+        assert _rel(out, ref) < 2e-4, _rel(out, ref)
+        gref = sum(r[1] for r in res)
         o = 0
         for ci, co in zip(net.CIN, net.COUT):
             for sl in (slice(o, o + co * ci * T), slice(o + co * ci * T, o + co * ci * T + co)):
-                assert _rel(grad[sl], gref[sl]) < 1e-4
+                assert _rel(grad[sl], gref[sl]) < 1e-3, (ci, co, _rel(grad[sl], gref[sl]))
             o += co * ci * T + co
 
 
