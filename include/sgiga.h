@@ -266,7 +266,8 @@ int sgiga_set_coefficient(sgiga_plan_t plan, int nfeat, const double* omega, con
  * coefficient); the geometry coefficients are recomputed, the load vector
  * and the preconditioner are unchanged. sgiga_set_coefficient evaluates its
  * Fourier features into the same plane. The plan keeps the values (a
- * re-tiling by sgiga_autotune reuses them). */
+ * re-tiling by sgiga_autotune reuses them). SGIGA_ERR_ARG if some value is
+ * not positive and finite (the plan then keeps a = 1). */
 int sgiga_set_coefficient_qp(sgiga_plan_t plan, const double* a_qp);
 
 /* Copy the current packed load vector to b ([ndof], host or device). */
@@ -300,7 +301,8 @@ int sgiga_precond_f32(sgiga_plan_t plan, const float* r, float* z);
  * inner FP32 solve to relative residual 1e-5 or 100 iterations; the stopping
  * test uses the true FP64 residual). The solution stays in the plan
  * (sgiga_get_solution). Returns SGIGA_ERR_NOT_CONVERGED if some component did
- * not converge. */
+ * not converge, SGIGA_ERR_ARG (before any iteration) if some component's load
+ * vector holds a NaN or an infinity. */
 int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
                 sgiga_solve_stats* stats /* host, may be NULL */);
 
@@ -498,11 +500,11 @@ int sgiga_net_load(sgiga_plan_t plan, const char* path);
  * Allocation-free preconditioner apply (the paper has no counterpart; this is
  * a service for callers of the library).
  *
- * For callers that cannot call cudaMalloc where they need it: work recorded
- * into a CUDA stream capture (allocating there is not allowed in the default
- * capture mode), real-time loops that must not touch the device allocator
- * after start-up, and processes whose device memory is owned by another
- * allocator. It needs no plan: the caller passes the 1D eigenpairs.
+ * For callers that cannot call cudaMalloc where they need it: real-time loops
+ * that must not touch the device allocator after start-up, processes whose
+ * device memory is owned by another allocator that must account for every
+ * byte, and code running where an allocation is not permitted. It needs no
+ * plan: the caller passes the 1D eigenpairs.
  *
  * Computes, for ONE tensor-product grid with n[0] x .. x n[d-1] entries
  * (direction 0 fastest),
@@ -522,9 +524,11 @@ int sgiga_net_load(sgiga_plan_t plan, const char* path);
  * SGIGA_NOALLOC_MAX_DOFS entries are rejected with SGIGA_ERR_ARG. The call
  * allocates nothing. The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the array, so calls that overlap on
- * the GPU race on it: order them on one stream. Returns SGIGA_OK, SGIGA_ERR_ARG
- * or SGIGA_ERR_CUDA (message in sgiga_last_error()). */
+ * before any stream capture. The looked-up address stays valid while the
+ * device's primary context lives: after a cudaDeviceReset the entry point must
+ * not be called again on that device. All calls share the array, so calls that
+ * overlap on the GPU race on it: order them on one stream. Returns SGIGA_OK,
+ * SGIGA_ERR_ARG or SGIGA_ERR_CUDA (message in sgiga_last_error()). */
 #define SGIGA_NOALLOC_MAX_DOFS 262144
 int sgiga_fd_apply_noalloc(int d, const int* n, const double* const* U, const double* const* lam,
                            const double* r, double* z, void* stream);

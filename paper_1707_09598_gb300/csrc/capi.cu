@@ -833,7 +833,7 @@ static int build(sgiga_plan_s* P) {
     int hflags[4];
     CUDA_TRY(cudaMemcpyAsync(hflags, dflags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (hflags[0]) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
+    if (hflags[0] & 1) return fail(SGIGA_ERR_GEOMETRY, "det J <= 0 at a quadrature point");
     if ((rc = update_diag(P))) return rc;
     P->t_geometry = since(tgeo);
     const auto tvec = std::chrono::steady_clock::now();
@@ -1205,10 +1205,27 @@ int sgiga_source_at_qp(sgiga_plan_t P, int source, double* f) {
     return SGIGA_OK;
 }
 
-// Recompute the geometry coefficients with the plan's current coefficient plane.
+// Recompute the geometry coefficients with the plan's current coefficient
+// plane; SGIGA_ERR_ARG if some a(x_q) is not positive and finite.
 static int refresh_geometry(sgiga_plan_s* P) {
     cudaStream_t s = P->stream;
+    CUDA_TRY(cudaMemsetAsync(P->dp.flags, 0, sizeof(int), s));
     CUDA_TRY(launch_geometry(P->dp, s));
+    int hf = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hf, P->dp.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hf & 2) {   // leave the plan with a = 1 rather than with non-finite coefficients
+        if (P->acoef) { cudaFree(P->acoef); P->acoef = nullptr; }
+        P->dp.acoef = nullptr;
+        CUDA_TRY(launch_geometry(P->dp, s));
+        if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
+            CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        net_invalidate_features(P);
+        update_diag(P);
+        return fail(SGIGA_ERR_ARG, "the diffusion coefficient must be positive and finite at every quadrature "
+                                   "point (the plan keeps a = 1)");
+    }
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(P->dp.Gf, P->dp.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1438,6 +1455,16 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
     auto t0 = std::chrono::steady_clock::now();
     const int ng = (int)P->comps.size();
     P->last_inner_iters = 0;
+    {   // a right-hand side with a NaN or an infinity is an input error, not a divergence
+        CUDA_TRY(launch_dot<double>(P->dp, P->d_b, P->d_b, P->d_partial, P->d_scal, P->stream));
+        std::vector<double> hb(ng);
+        CUDA_TRY(cudaMemcpyAsync(hb.data(), P->d_scal, ng * 8, cudaMemcpyDeviceToHost, P->stream));
+        CUDA_TRY(cudaStreamSynchronize(P->stream));
+        for (int g = 0; g < ng; ++g)
+            if (!std::isfinite(hb[g]))
+                return fail(SGIGA_ERR_ARG, "the load vector of component " + std::to_string(g) +
+                                               " is not finite (a NaN or infinity in f or the boundary data)");
+    }
     if (P->cfg.precision == SGIGA_PREC_FP64) {
         int nact = pcg<double>(P, P->d_b, vecs64(P), rel_tol, max_iter, nullptr, P->d_active, P->d_iters, P->d_scal,
                                nullptr);

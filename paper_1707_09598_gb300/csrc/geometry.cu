@@ -102,7 +102,11 @@ __global__ void k_geometry(DevPlan P) {
         patch_eval(pt, xi, x, J);
         double Gp[3][3];
         double s = wq;
-        if (P.acoef) s *= P.acoef[natural_index(g, d, Q, L)];   // diffusion coefficient a(x_q)
+        if (P.acoef) {                                        // diffusion coefficient a(x_q)
+            const double a = P.acoef[natural_index(g, d, Q, L)];
+            if (!(a > 0.0 && a < INFINITY)) atomicOr(&P.flags[0], 2);
+            s *= a;
+        }
         double det = metric(d, J, s, Gp);
         if (!(det * (pt.orient < 0 ? -1.0 : 1.0) > 0.0)) atomicOr(&P.flags[0], 1);
         long long o = t.g_off + idx;

@@ -1,21 +1,24 @@
 // Allocation-free fast-diagonalisation apply for one tensor-product grid.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// preconditioner: code that records work into a CUDA stream capture (an
-// allocation there is not allowed in the default capture mode and would break
-// the capture), real-time or embedded loops that must not touch the device
-// allocator after start-up, and processes whose device memory is owned by
-// another allocator (for example a framework's caching allocator) that must
-// see every byte. For them this entry point takes everything as caller-owned
-// buffers (the 1D eigenpairs, the input and the output) and keeps its two
-// intermediate tensors in a file-scope device array instead of allocating.
+// preconditioner: real-time or embedded loops that must not touch the device
+// allocator after start-up (an allocation can block or fail at any time),
+// processes whose device memory is owned by another allocator (for example a
+// framework's caching allocator) that must account for every byte, and code
+// running where an allocation is not permitted at all. For them this entry
+// point takes everything as caller-owned buffers (the 1D eigenpairs, the
+// input and the output) and keeps its two intermediate tensors in a
+// file-scope device array instead of allocating.
 //
 // The array is sized for grids of at most SGIGA_NOALLOC_MAX_DOFS entries
 // (two halves of 2 MB, 4 MB in total); every GPU that loads this library holds
 // it until the process exits. Every call shares it, so calls that overlap on
 // the GPU (different streams, or different host threads) race on it; order
 // them. Each pass writes every entry it later reads, so nothing has to be
-// cleared between calls.
+// cleared between calls. The array's device address is looked up once per
+// device ordinal and cached; a cudaDeviceReset (or any other teardown of the
+// device's primary context) invalidates it, so after one the process must not
+// call this entry point again on that device.
 #include <mutex>
 
 #include "../../include/sgiga.h"
@@ -98,6 +101,12 @@ extern "C" int sgiga_fd_apply_noalloc(int d, const int* n, const double* const* 
             set_last_error("sgiga_fd_apply_noalloc: every n[k] must be >= 1 with U[k], lam[k] given");
             return SGIGA_ERR_ARG;
         }
+        // checked after every factor: the product of up to three 31-bit sizes
+        // must neither overflow nor wrap below the limit
+        if (n[k] > SGIGA_NOALLOC_MAX_DOFS || N * n[k] > SGIGA_NOALLOC_MAX_DOFS) {
+            set_last_error("sgiga_fd_apply_noalloc: grid has more than SGIGA_NOALLOC_MAX_DOFS (262144) entries");
+            return SGIGA_ERR_ARG;
+        }
         G.n[k] = n[k];
         G.U[k] = U[k];
         G.lam[k] = lam[k];
@@ -113,10 +122,6 @@ extern "C" int sgiga_fd_apply_noalloc(int d, const int* n, const double* const* 
     for (int k = 0; k < d; ++k) dev_ok = dev_ok && on_device(U[k]) && on_device(lam[k]);
     if (!dev_ok) {
         set_last_error("sgiga_fd_apply_noalloc: r, z, U[k] and lam[k] must be device buffers");
-        return SGIGA_ERR_ARG;
-    }
-    if (N > SGIGA_NOALLOC_MAX_DOFS) {
-        set_last_error("sgiga_fd_apply_noalloc: grid has more than SGIGA_NOALLOC_MAX_DOFS (262144) entries");
         return SGIGA_ERR_ARG;
     }
     int dev = 0;

@@ -1,12 +1,14 @@
 """The allocation-free preconditioner apply against the plan-based one.
 
 sgiga_fd_apply_noalloc serves callers that cannot call cudaMalloc where they
-need the preconditioner (stream capture, allocation-free real-time loops,
-memory owned by another allocator). It keeps its intermediate tensors in a
-library-owned device array. This test checks, through the C ABI, that it gives
-the same result as sgiga_precond on several components, on two calls in a row
-(the array keeps the previous call's contents), and that it rejects grids
-larger than its array. It runs last (file name) and also alone.
+need the preconditioner (allocation-free real-time loops, memory owned by
+another allocator that must account for every byte). It keeps its
+intermediate tensors in a library-owned device array. This test checks,
+through the C ABI, that it gives the same result as sgiga_precond on several
+components, on two calls in a row (the array keeps the previous call's
+contents), that the device's free memory does not change across calls, and
+that it rejects grids larger than its array, also when the product of the
+sizes would overflow. It runs last (file name) and also alone.
 """
 import os
 
@@ -50,11 +52,17 @@ def test_noalloc_matches_plan_preconditioner(sg, d, p, w):
                 lam.append(torch.as_tensor(lk, device="cuda").contiguous())
             sl = slice(g.dof_off, g.dof_off + g.ndof)
             rg = r[sl].contiguous()
+            z = torch.full_like(rg, float("nan"))
+            sg.sgiga_fd_apply_noalloc(n, U, lam, rg, z)     # first call on the device: address look-up
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            alloc0 = torch.cuda.memory_allocated()
             for call in range(2):          # two calls in a row share the scratch array
-                z = torch.full_like(rg, float("nan"))
+                z.fill_(float("nan"))
                 sg.sgiga_fd_apply_noalloc(n, U, lam, rg, z)
                 torch.cuda.synchronize()
                 assert _rel(z, z_ref[sl]) < 1e-12, (gi, call, _rel(z, z_ref[sl]))
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
             # a second input right after: no state leaks from the previous call
             r2 = torch.as_tensor(random_vector(g.ndof, 32 + gi), device="cuda")
             z2 = torch.zeros_like(r2)
@@ -79,3 +87,11 @@ def test_noalloc_rejects_grids_larger_than_its_array(sg):
     assert rc == sg.SGIGA_ERR_ARG
     assert "SGIGA_NOALLOC_MAX_DOFS" in sg.sgiga_last_error()
     assert float(z.abs().max()) == 0.0  # nothing was launched
+    # sizes whose product would overflow: refused before any pointer is used
+    # (through the C ABI directly; the binding would refuse the buffers first)
+    import ctypes
+    na = (ctypes.c_int * 3)(*([2 ** 31 - 1] * 3))
+    ua = (ctypes.c_void_p * 3)(*[u.data_ptr() for u in U])
+    la = (ctypes.c_void_p * 3)(*[l_.data_ptr() for l_ in lam])
+    rc = sg._lib.sgiga_fd_apply_noalloc(3, na, ua, la, r.data_ptr(), z.data_ptr(), None)
+    assert rc == sg.SGIGA_ERR_ARG and "SGIGA_NOALLOC_MAX_DOFS" in sg.sgiga_last_error()
