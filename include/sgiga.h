@@ -311,7 +311,8 @@ int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
  * (shared-memory budget per block, cap on quadrature points per tile; the
  * shape within a policy comes from the planner's cost model), times `reps`
  * stiffness applies (FP32 in MIXED_FP32 plans, whose inner solve they
- * dominate; else FP64) on the plan's stream for each (CUDA events), and keeps
+ * dominate; else FP64) on the plan's stream for each (CUDA events; FP32 3D
+ * plans time each policy with 256 and with 128 threads per block), and keeps
  * the fastest; the geometry planes are recomputed in the chosen tile layout.
  * (2) Re-splits the fast-diagonalisation mode products into work items of
  * each candidate layout (per piece, level-grouped) and contraction depth
@@ -323,9 +324,10 @@ int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
 typedef struct {
     int ncand, best, ntiles;
     double best_ms;
-    double ms[8];
-    int budget[8];    /* bytes of shared memory per block */
-    int qpcap[8];     /* quadrature points per tile at most */
+    double ms[16];
+    int budget[16];   /* bytes of shared memory per block */
+    int qpcap[16];    /* quadrature points per tile at most */
+    int nthreads[16]; /* threads per block of the operator kernel (FP32 3D plans try 256 and 128) */
     int fd_ncand, fd_best, fd_nitems;
     int fd_ks[8];     /* contraction depth per preconditioner work item */
     double fd_ms[8];  /* mean time of one preconditioner application */

@@ -16,8 +16,11 @@
 
 namespace sgiga {
 
-template <typename Real, int P, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 2)
+// NT threads per block: 256 (FP64, and FP32 with large tiles) or 128 (FP32:
+// more, smaller blocks per SM, so that one block's warps waiting at a stage
+// barrier overlap with other blocks' work; chosen by the autotuner).
+template <typename Real, int P, int MODE, bool DIAG, int NT = 256>
+__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (NT == 128 ? 6 : 3) : 2)
 k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
     constexpr int Q = P + 1, P1 = P + 1;
     // FP32 stiffness: the b-direction stages run as register-window pencils
@@ -68,6 +71,19 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
         for (int i = tid; i < cnt; i += nth) { tb[k][i] = OpData<Real>::R(Pl)[base + i]; tdv[k][i] = OpData<Real>::dR(Pl)[base + i]; }
     }
     const long long doff = g.dof_off;
+    if constexpr (sizeof(Real) == 4 && MODE == 0) {
+        // FP32: start moving this tile's metric planes from HBM to L2 now, so
+        // that the pencil stage, which follows the two forward contractions,
+        // reads them from L2 (each plane's tile segment is contiguous, 256-byte
+        // aligned and a multiple of 256 bytes long: 64 quadrature points per
+        // element)
+        if (tid < (DIAG ? 3 : 6)) {
+            const int c = DIAG ? (tid == 0 ? 0 : 2 * tid + 1) : tid;    // diagonal planes 0, 3, 5
+            const float* src = OpData<Real>::G(Pl) + (long long)c * Pl.nqp + td.g_off;
+            const unsigned bytes = (unsigned)((long long)QTb * QTc * Q * Ta * 4);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+        }
+    }
     __syncthreads();   // tables visible to every thread before any stage reads them
     if (MODE == 0) {
         const int nX = La * Lb * Lc;
@@ -388,10 +404,16 @@ cudaError_t launch_op3(const DevPlan& Pl, const double* x, double* y, const int*
 template <int P>
 static cudaError_t launch3f(const DevPlan& Pl, const float* x, float* y, const int* active, cudaStream_t s) {
     SGIGA_COUNT_LAUNCH();
-    if (Pl.diag)
+    if (Pl.op_nth == 128) {
+        if (Pl.diag)
+            k_op3<float, P, 0, true, 128><<<Pl.ntiles, 128, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+        else
+            k_op3<float, P, 0, false, 128><<<Pl.ntiles, 128, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    } else if (Pl.diag) {
         k_op3<float, P, 0, true><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
-    else
+    } else {
         k_op3<float, P, 0, false><<<Pl.ntiles, 256, Pl.smem_op / 2, s>>>(Pl, x, y, active);
+    }
     return cudaGetLastError();
 }
 
@@ -418,6 +440,10 @@ cudaError_t set_op3_smem(int p, size_t bytes) {
             e = cudaFuncSetAttribute(k_op3<float, PP, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(k_op3<float, PP, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<float, PP, 0, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(k_op3<float, PP, 0, true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes / 2)); \
     }
     SET(1) SET(2) SET(3) SET(4)
 #undef SET

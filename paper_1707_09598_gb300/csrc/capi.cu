@@ -1357,19 +1357,29 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     auto apply_once = [&]() {
         return f32 ? apply_op(P, P->f_p, P->f_q, nullptr) : apply_op(P, P->d_b, P->d_q, nullptr);
     };
+    // FP32 3D plans: each tile policy with 256 and with 128 threads per block
+    const int nth_opts = (f32 && P->d == 3) ? 2 : 1;
+    int bnth = 256, ci = 0;
     for (int i = 0; i < nc && rc == SGIGA_OK; ++i) {
         if ((rc = retile(P, cands[i].budget, cands[i].qpcap))) break;
-        if ((rc = apply_once())) break;   // warm-up
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_once();
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        double per = ms / reps;
-        if (out && i < 8) { out->ms[i] = per; out->budget[i] = (int)cands[i].budget; out->qpcap[i] = (int)cands[i].qpcap; }
-        if (per < best) { best = per; bi = i; }
+        for (int o = 0; o < nth_opts && rc == SGIGA_OK; ++o, ++ci) {
+            P->dp.op_nth = o == 0 ? 256 : 128;
+            if ((rc = apply_once())) break;   // warm-up
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_once();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            double per = ms / reps;
+            if (out && ci < 16) {
+                out->ms[ci] = per; out->budget[ci] = (int)cands[i].budget; out->qpcap[ci] = (int)cands[i].qpcap;
+                out->nthreads[ci] = P->dp.op_nth;
+            }
+            if (per < best) { best = per; bi = i; bnth = P->dp.op_nth; }
+        }
     }
+    P->dp.op_nth = bnth;
     if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap);
     // preconditioner item depth
     const int ks_v[] = {16, 32, 64, 128};
@@ -1403,8 +1413,8 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     if (rc) return rc;
     if ((rc = refd(P, ks_v[fbi % nksv], fbi >= nksv))) return rc;
     if (out) {
-        out->ncand = nc;
-        out->best = bi;
+        out->ncand = ci;
+        out->best = bi * nth_opts + (bnth == 128 ? 1 : 0);
         out->best_ms = best;
         out->ntiles = (int)P->tiles.size();
         out->fd_ncand = nks;

@@ -49,6 +49,7 @@ struct DevPlan {
     int* flags;              // [0] = geometry error, [1] = eval error
     const double* acoef;     // diffusion coefficient a(x_q) [nqp], natural order, or null (a = 1)
     size_t smem_op;          // dynamic shared bytes of the operator kernel
+    int op_nth;              // threads per block of the FP32 3D operator kernel (256 or 128)
     int diag;                // every geometry plane off the diagonal is exactly zero
     const CompDesc* comps;   // components (CG systems); pieces are grids[]
     int ncomps;

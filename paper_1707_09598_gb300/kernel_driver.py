@@ -59,7 +59,11 @@ def main():
         om, ph, amp = lognormal_features(2, nfeat=128)
         sgiga.sgiga_set_coefficient(P.handle, om, ph, amp)
     if a.tune:
-        sgiga.sgiga_autotune(P.handle, reps=3)
+        t = sgiga.sgiga_autotune(P.handle, reps=3)
+        print("autotune: best %d/%d/%d threads %.4f ms; fd ks %d %s; candidates %s" % (
+            t.budget[t.best], t.qpcap[t.best], t.nthreads[t.best], t.best_ms, t.fd_ks[t.fd_best],
+            "grouped" if t.fd_grouped[t.fd_best] else "per piece",
+            " ".join("%d/%d/%d:%.4f" % (t.budget[i], t.qpcap[i], t.nthreads[i], t.ms[i]) for i in range(t.ncand))))
     if a.op == "solve_scaled":
         sgiga.sgiga_set_solver_options(P.handle, use_graph=not a.host_loop, inner_tol=1e-3, inner_max=100)
         phi = torch.zeros(P.info.ndof, dtype=torch.float32, device="cuda")

@@ -76,7 +76,8 @@ class sgiga_train_stats(ctypes.Structure):
 
 class sgiga_tune_result(ctypes.Structure):
     _fields_ = [("ncand", ctypes.c_int), ("best", ctypes.c_int), ("ntiles", ctypes.c_int), ("best_ms", ctypes.c_double),
-                ("ms", ctypes.c_double * 8), ("budget", ctypes.c_int * 8), ("qpcap", ctypes.c_int * 8),
+                ("ms", ctypes.c_double * 16), ("budget", ctypes.c_int * 16), ("qpcap", ctypes.c_int * 16),
+                ("nthreads", ctypes.c_int * 16),
                 ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
                 ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8)]
 
