@@ -6,6 +6,7 @@ the repository root:
     python tests/golden/make_golden.py cube_p3_w10
     python tests/golden/make_golden.py lshape_p2_w11_g2
     python tests/golden/make_golden.py perturbed_p3_w12
+    python tests/golden/make_golden.py lshape_sensitivity
 
 Output: tests/golden/<name>.txt with, for each parametric evaluation point,
 the combined sparse-grid value sum_i c_i u_i(xi) and the values of a few
@@ -96,6 +97,55 @@ def _perturbed_geometry():
     return geometry.BSplinePatch([3, 3, 3], kn, cp), geometry.lognormal_coefficient(om, ph, amp)
 
 
+def _one_sensitivity(args):
+    """Values of one L-shape component from its extended-precision solve, and
+    from the same solve after a symmetric entrywise relative perturbation of
+    its FP64 matrix by 4 units in the last place (random signs)."""
+    p, i, gamma, patch, pts, seed = args
+    from oracle import multipatch
+    comp = multipatch.LShapeComponent(i, p, kind="onesided", gamma=gamma).assemble(g=multipatch.corner_u)
+    v0 = comp.evaluate(comp.solve_extended(), patch, pts)[0]
+    K0 = comp.K.tocsr()
+    Kp = K0.copy()
+    rng = np.random.default_rng(seed)
+    Kp.data = Kp.data * (1.0 + 4.0 * 2.0 ** -53 * rng.choice([-1.0, 1.0], size=Kp.data.size))
+    comp.K = ((Kp + Kp.T) * 0.5).tocsc()
+    v1 = comp.evaluate(comp.solve_extended(), patch, pts)[0]
+    return v0, v1
+
+
+def main_lshape_sensitivity():
+    """How far the combined L-shape solution moves when every component's
+    matrix is perturbed entrywise by 4 units in the last place of FP64 (the
+    size of the rounding any FP64 representation of the Galerkin matrix
+    carries): the accuracy to which the discrete solution is defined in FP64,
+    per grading exponent."""
+    from oracle import combination
+    from paper_1707_09598_gb300.inputs import eval_points
+    out = os.path.join(HERE, "lshape_p2_w11_sensitivity.txt")
+    lines = ["# written by tests/golden/make_golden.py lshape_sensitivity (oracle only)\n",
+             "# L-shape p=2 C^1 w=11, one-sided grading; combined values on eval_points(2, 8) of each patch\n",
+             "# columns: gamma  relative L2 change of the combined values under a 4-ulp entrywise perturbation\n"]
+    t0 = time.time()
+    ctx = mp.get_context("spawn")
+    for gamma in (1.0, 2.0, 3.0):
+        p, w, k = 2, 11, 8
+        lat = eval_points(2, k)
+        pts = np.concatenate([lat] * 3)
+        patch = np.repeat(np.arange(3), len(lat))
+        idx = combination.index_set(2, w)
+        with ctx.Pool(min(8, os.cpu_count())) as pool:
+            res = pool.map(_one_sensitivity, [(p, i, gamma, patch, pts, 1000 + n) for n, (i, _) in enumerate(idx)],
+                           chunksize=1)
+        coeffs = np.array([c for _, c in idx], dtype=np.float64)
+        a = combination.combine(np.stack([r[0] for r in res]), coeffs)
+        b = combination.combine(np.stack([r[1] for r in res]), coeffs)
+        lines.append("%g %.6e\n" % (gamma, np.linalg.norm(a - b) / np.linalg.norm(a)))
+    with open(out, "w") as fh:
+        fh.writelines(lines)
+    print("wrote %s in %.1f s" % (out, time.time() - t0))
+
+
 def _one(args):
     domain, d, p, i, problem, pts = args
     from oracle import geometry, problems
@@ -149,7 +199,9 @@ def main(name):
 
 
 if __name__ == "__main__":
-    if sys.argv[1] in LSHAPE:
+    if sys.argv[1] == "lshape_sensitivity":
+        main_lshape_sensitivity()
+    elif sys.argv[1] in LSHAPE:
         main_lshape(sys.argv[1])
     else:
         main(sys.argv[1])

@@ -211,17 +211,23 @@ def test_errors_are_reported(sg):
 @pytest.mark.parametrize("gamma", [1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
-    """gamma = 3 grades the corner elements down to 1e-9 of the patch. The
-    most anisotropic components then have cond(K) ~ 1e12 (4e9 after diagonal
-    equilibration). In FP64 their true relative residual cannot go below
-    ~3e-10: the oracle's LU with refinement stalls at 2.6e-10, the GPU's FP64
-    residual at 5.5e-10. Two FP64 solutions of these systems agree to ~1.5e-7
-    (this test measured 1.52e-7 with the GPU solve at 1e-12 and at 1e-14).
-    For gamma = 3 the solve target is 1e-9 and the parity bound 5e-7 on both
-    paths; gamma = 1, 2 keep the FP64 and mixed targets."""
+    """Combined values and gradients against the oracle's stored values
+    (extended-precision refinement of every component). gamma = 3 grades the
+    corner elements down to 1e-9 of the patch: the most anisotropic
+    components have cond(K) ~ 1e12, and their discrete solution is defined in
+    FP64 only to the accuracy with which an FP64 matrix represents them. The
+    oracle measures that (tests/golden/lshape_p2_w11_sensitivity.txt): a
+    symmetric entrywise perturbation of every component's matrix by 4 units
+    in the last place moves the combined values by 6.1e-7 for gamma = 3
+    (4.9e-12 and 2.9e-10 for gamma = 1, 2). Two FP64 representations of these
+    systems (the GPU's matrix-free operator from FP64 metric planes, the
+    oracle's assembled FP64 matrix) can differ by that much, so for gamma = 3
+    the bound is that sensitivity, and the solve target the FP64 residual
+    floor 1e-9; gamma = 1, 2 keep the FP64 and mixed targets."""
     solve_tol = 1e-12
     if gamma == 3:
-        tol, solve_tol = 5e-7, 1e-9
+        sens = dict(np.loadtxt(os.path.join(GOLD, "lshape_p2_w11_sensitivity.txt")))
+        tol, solve_tol = max(tol, sens[3.0]), 1e-9
     path = os.path.join(GOLD, "lshape_p2_w11_g%d.txt" % gamma)
     data = np.loadtxt(path)
     patch = np.ascontiguousarray(data[:, 0].astype(np.int32))
