@@ -505,9 +505,10 @@ def train_learned(W, args):
                         "loss_epochs": [tr.loss_epoch[e] for e in range(min(12, 32))],
                         "best_epoch": tr.best_epoch, "log_s_range": [tr.logs_min, tr.logs_max]}}
     tuning = {"best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
-                       "threads": tune.nthreads[tune.best], "apply_f32_ms": tune.best_ms, "ntiles": tune.ntiles},
-              "candidates_ms": {"%d/%d/%d" % (tune.budget[i], tune.qpcap[i], tune.nthreads[i]): round(tune.ms[i], 4)
-                                for i in range(tune.ncand)},
+                       "threads": tune.nthreads[tune.best], "l2_prefetch_bytes_per_plane": tune.best_prefetch,
+                       "apply_f32_ms": tune.best_ms, "ntiles": tune.ntiles},
+              "candidates_ms": {"%d/%d/%d/%d" % (tune.budget[i], tune.qpcap[i], tune.nthreads[i], tune.prefetch[i]):
+                                round(tune.ms[i], 4) for i in range(tune.ncand)},
               "precond": {"best_ks": tune.fd_ks[tune.fd_best],
                           "layout": "grouped" if tune.fd_grouped[tune.fd_best] else "per piece"}}
     return L, out, tuning

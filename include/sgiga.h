@@ -312,8 +312,11 @@ int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
  * shape within a policy comes from the planner's cost model), times `reps`
  * stiffness applies (FP32 in MIXED_FP32 plans, whose inner solve they
  * dominate; else FP64) on the plan's stream for each (CUDA events; FP32 3D
- * plans time each policy with 256 and with 128 threads per block), and keeps
- * the fastest; the geometry planes are recomputed in the chosen tile layout.
+ * plans time each policy with 256 and with 128 threads per block, and, for p
+ * odd, with four settings of the metric planes' L2 prefetch), and keeps the
+ * fastest; the geometry planes are computed once and gathered into each
+ * candidate's tile layout (recomputed from the patch map when the device has
+ * no room for the natural-layout copy, (d(d+1)/2 + 1) * nqp doubles).
  * (2) Re-splits the fast-diagonalisation mode products into work items of
  * each candidate layout (per piece, level-grouped) and contraction depth
  * (fd_ks: entries of a long 1D contraction per item; shorter items balance
@@ -332,8 +335,22 @@ typedef struct {
     int fd_ks[8];     /* contraction depth per preconditioner work item */
     double fd_ms[8];  /* mean time of one preconditioner application */
     int fd_grouped[8];/* 1: level-grouped layout, 0: per-piece layout */
+    int prefetch[16]; /* FP32 3D plans, p odd: the candidate's fastest L2 prefetch of a tile's metric planes at tile
+                         start (0: whole segments; > 0: at most this many bytes per plane, so that the segments in
+                         flight on all SMs total 48 or 16 MB; -1: none) */
+    int best_prefetch;
 } sgiga_tune_result;
 int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
+
+/* Sets the operator's work decomposition directly (a setting that
+ * sgiga_autotune reported, to reuse it without timing again): the tile policy
+ * (budget: shared-memory bytes per block, 16 KB..227 KB; qpcap: quadrature
+ * points per tile at most), the FP32 3D kernel's threads per block (256 or
+ * 128) and its L2 prefetch of a tile's metric planes (0 whole segments, > 0 at
+ * most this many bytes per plane, a multiple of 16; < 0 none). The geometry
+ * planes are recomputed in the new tile layout. SGIGA_ERR_ARG on a value out
+ * of range. No counterpart in the paper (a GPU work-decomposition setting). */
+int sgiga_set_tiling(sgiga_plan_t plan, int budget, int qpcap, int nthreads, int prefetch);
 
 /* Solver options. use_graph != 0 (default): each CG loop runs as one captured
  * CUDA graph whose while-conditional node repeats the iteration body until the

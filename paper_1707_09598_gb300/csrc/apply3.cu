@@ -74,14 +74,22 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
     if constexpr (sizeof(Real) == 4 && MODE == 0) {
         // FP32: start moving this tile's metric planes from HBM to L2 now, so
         // that the pencil stage, which follows the two forward contractions,
-        // reads them from L2 (each plane's tile segment is contiguous, 256-byte
-        // aligned and a multiple of 256 bytes long: 64 quadrature points per
-        // element)
-        if (tid < (DIAG ? 3 : 6)) {
-            const int c = DIAG ? (tid == 0 ? 0 : 2 * tid + 1) : tid;    // diagonal planes 0, 3, 5
-            const float* src = OpData<Real>::G(Pl) + (long long)c * Pl.nqp + td.g_off;
-            const unsigned bytes = (unsigned)((long long)QTb * QTc * Q * Ta * 4);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+        // reads them from L2. Each plane's tile segment is contiguous; with an
+        // even number of quadrature points per direction (p odd) an element
+        // holds a multiple of 8 points, so every segment starts and ends on a
+        // 32-byte boundary, as the bulk prefetch needs (16). Pl.op_pf caps the
+        // bytes per plane so that the segments in flight on all SMs stay well
+        // inside L2: prefetched lines evicted before the pencil stage reads
+        // them would be fetched from HBM twice.
+        if constexpr ((P1 & 1) == 0) {
+            if (Pl.op_pf >= 0 && tid < (DIAG ? 3 : 6)) {
+                const int c = DIAG ? (tid == 0 ? 0 : 2 * tid + 1) : tid;    // diagonal planes 0, 3, 5
+                const float* src = OpData<Real>::G(Pl) + (long long)c * Pl.nqp + td.g_off;
+                long long bytes = (long long)QTb * QTc * Q * Ta * 4;
+                if (Pl.op_pf > 0 && bytes > Pl.op_pf) bytes = Pl.op_pf & ~15;
+                if (bytes >= 16)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((unsigned)bytes) : "memory");
+            }
         }
     }
     __syncthreads();   // tables visible to every thread before any stage reads them
@@ -425,6 +433,32 @@ cudaError_t launch_op3_f32(const DevPlan& Pl, const float* x, float* y, const in
     case 4: return launch3f<4>(Pl, x, y, active, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int P>
+static int resident3f(const DevPlan& Pl) {
+    int nb = 0;
+    const int nth = Pl.op_nth == 128 ? 128 : 256;
+    const size_t smem = Pl.smem_op / 2;
+    cudaError_t e;
+    if (nth == 128)
+        e = Pl.diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_op3<float, P, 0, true, 128>, 128, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_op3<float, P, 0, false, 128>, 128, smem);
+    else
+        e = Pl.diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_op3<float, P, 0, true>, 256, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_op3<float, P, 0, false>, 256, smem);
+    if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+    return nb > 0 ? nb : 1;
+}
+
+int op3_f32_resident(const DevPlan& Pl) {
+    switch (Pl.p) {
+    case 1: return resident3f<1>(Pl);
+    case 2: return resident3f<2>(Pl);
+    case 3: return resident3f<3>(Pl);
+    case 4: return resident3f<4>(Pl);
+    }
+    return 1;
 }
 
 cudaError_t set_op3_smem(int p, size_t bytes) {

@@ -54,9 +54,9 @@ __global__ void k_boundary_points(DevPlan P, double* __restrict__ xb) {
     const GridDesc& g = P.grids[sd.piece];
     const long long np = side_npts(P, sd, g);
     for (long long j = threadIdx.x; j < np; j += blockDim.x) {
-        double xi[3] = {0, 0, 0}, x[3], J[3][3];
+        double xi[3] = {0, 0, 0}, x[3];
         side_point(P, sd, g, j, xi);
-        patch_eval(P.patch[g.patch], xi, x, J);
+        patch_point(P.patch[g.patch], xi, x);
         xb[2 * (sd.goff + j)] = x[0];
         xb[2 * (sd.goff + j) + 1] = x[1];
     }

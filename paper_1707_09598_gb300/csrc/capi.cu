@@ -884,8 +884,10 @@ static int build(sgiga_plan_s* P) {
 }
 
 // Re-plan the tiles (autotuner): new tile arrays, grids, shared-memory
-// attribute, and the tile-major geometry planes recomputed in the new layout.
-static int retile(sgiga_plan_s* P, size_t budget, long long qpcap) {
+// attribute, and the tile-major geometry planes in the new layout: gathered
+// from a natural-layout copy (Gn, mwn) when the caller holds one, else
+// recomputed from the patch map.
+static int retile(sgiga_plan_s* P, size_t budget, long long qpcap, double* Gn = nullptr, double* mwn = nullptr) {
     cudaStream_t s = P->stream;
     CUDA_TRY(cudaStreamSynchronize(s));
     make_tiles(P, budget, qpcap);
@@ -907,7 +909,8 @@ static int retile(sgiga_plan_s* P, size_t budget, long long qpcap) {
     D.smem_op = P->smem;
     CUDA_TRY(cudaMemcpy((void*)D.grids, P->grids.data(), P->grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice));
     if ((rc = grant_op_smem(P))) return rc;
-    CUDA_TRY(launch_geometry(D, s));
+    if (Gn) CUDA_TRY(launch_geometry_import(D, Gn, mwn, s));
+    else CUDA_TRY(launch_geometry(D, s));
     if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
         CUDA_TRY(launch_narrow(D.Gf, D.G, (long long)P->ncomp * P->nqp, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1359,28 +1362,63 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     };
     // FP32 3D plans: each tile policy with 256 and with 128 threads per block
     const int nth_opts = (f32 && P->d == 3) ? 2 : 1;
-    int bnth = 256, ci = 0;
+    // the geometry planes in natural layout, gathered into each candidate's
+    // tiling (the map is not evaluated again); without the memory for the
+    // copy every candidate recomputes them
+    double* Gn = nullptr;
+    if (cudaMalloc(&Gn, (size_t)(P->ncomp + 1) * P->nqp * 8) != cudaSuccess) {
+        cudaGetLastError();
+        Gn = nullptr;
+    }
+    double* mwn = Gn ? Gn + (size_t)P->ncomp * P->nqp : nullptr;
+    if (Gn) {
+        cudaError_t e = launch_geometry_export(P->dp, Gn, mwn, s);
+        if (e != cudaSuccess) { cudaFree(Gn); return fail(SGIGA_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)); }
+    }
+    // FP32 3D plans with p odd (the metric planes' tile segments are 32-byte
+    // aligned): L2 prefetch of the tile's planes, whole, capped so that the
+    // segments in flight on all SMs total at most 48 MB or 16 MB, or none
+    const int npf = (f32 && P->d == 3 && (P->p & 1)) ? 4 : 1;
+    int nsm = 152;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) { cudaGetLastError(); nsm = 152; }
+    auto pf_value = [&](int f) -> int {
+        if (f == 0) return 0;
+        if (f == 3) return -1;
+        const long long total = (f == 1 ? 48LL : 16LL) << 20;
+        const long long per = total / ((long long)nsm * op3_f32_resident(P->dp) * (P->dp.diag ? 3 : 6));
+        return (int)std::max(16LL, per & ~15LL);
+    };
+    int bnth = 256, bpf = 0, ci = 0;
     for (int i = 0; i < nc && rc == SGIGA_OK; ++i) {
-        if ((rc = retile(P, cands[i].budget, cands[i].qpcap))) break;
+        if ((rc = retile(P, cands[i].budget, cands[i].qpcap, Gn, mwn))) break;
         for (int o = 0; o < nth_opts && rc == SGIGA_OK; ++o, ++ci) {
             P->dp.op_nth = o == 0 ? 256 : 128;
-            if ((rc = apply_once())) break;   // warm-up
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_once();
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            double per = ms / reps;
-            if (out && ci < 16) {
-                out->ms[ci] = per; out->budget[ci] = (int)cands[i].budget; out->qpcap[ci] = (int)cands[i].qpcap;
-                out->nthreads[ci] = P->dp.op_nth;
+            double cbest = 1e30;
+            int cpf = 0;
+            for (int f = 0; f < npf && rc == SGIGA_OK; ++f) {
+                P->dp.op_pf = pf_value(f);
+                if ((rc = apply_once())) break;   // warm-up
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && rc == SGIGA_OK; ++r) rc = apply_once();
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(SGIGA_ERR_CUDA, "autotune timing failed"); break; }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / reps;
+                if (per < cbest) { cbest = per; cpf = P->dp.op_pf; }
             }
-            if (per < best) { best = per; bi = i; bnth = P->dp.op_nth; }
+            if (out && ci < 16) {
+                out->ms[ci] = cbest; out->budget[ci] = (int)cands[i].budget; out->qpcap[ci] = (int)cands[i].qpcap;
+                out->nthreads[ci] = P->dp.op_nth;
+                out->prefetch[ci] = cpf;
+            }
+            if (cbest < best) { best = cbest; bi = i; bnth = P->dp.op_nth; bpf = cpf; }
         }
     }
     P->dp.op_nth = bnth;
-    if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap);
+    P->dp.op_pf = bpf;
+    if (rc == SGIGA_OK) rc = retile(P, cands[bi].budget, cands[bi].qpcap, Gn, mwn);
+    if (Gn) cudaFree(Gn);
     // preconditioner item depth
     const int ks_v[] = {16, 32, 64, 128};
     const int nksv = (int)(sizeof(ks_v) / sizeof(ks_v[0]));
@@ -1416,6 +1454,7 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         out->ncand = ci;
         out->best = bi * nth_opts + (bnth == 128 ? 1 : 0);
         out->best_ms = best;
+        out->best_prefetch = bpf;
         out->ntiles = (int)P->tiles.size();
         out->fd_ncand = nks;
         out->fd_best = fbi;
@@ -1427,6 +1466,19 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         out->fd_nitems = (int)items;
     }
     P->t_autotune = since(tt0);
+    return SGIGA_OK;
+}
+
+int sgiga_set_tiling(sgiga_plan_t P, int budget, int qpcap, int nthreads, int prefetch) {
+    if (!P) return fail(SGIGA_ERR_ARG, "null argument");
+    if (budget < 16 * 1024 || budget > 227 * 1024 || qpcap < 64 || qpcap > (1 << 20))
+        return fail(SGIGA_ERR_ARG, "budget must be in [16 KB, 227 KB] and qpcap in [64, 2^20]");
+    if (nthreads != 256 && nthreads != 128) return fail(SGIGA_ERR_ARG, "nthreads must be 256 or 128");
+    if (prefetch > 0 && prefetch % 16) return fail(SGIGA_ERR_ARG, "prefetch must be a multiple of 16 bytes");
+    int rc = retile(P, (size_t)budget, qpcap);
+    if (rc) return rc;
+    P->dp.op_nth = nthreads;
+    P->dp.op_pf = prefetch;
     return SGIGA_OK;
 }
 

@@ -145,22 +145,32 @@ __device__ __forceinline__ double band_mv(const double* __restrict__ Mb, int n, 
     return acc;
 }
 
-// Eigenvectors of one job by inverse iteration, one thread per unit (a run of
-// `cnt` eigenvalues from j0 whose gaps are below the cluster tolerance; most
-// units are single eigenvalues). Per thread, in `scratch` (interleaved by
-// thread: entry e of thread t at e * nunits + t, so that a warp's accesses to
-// the same row are contiguous): the U rows of the banded LU (2P+1 entries and
-// the transformed right-hand side per row), then the current vector (n).
+// Eigenvectors of every job by inverse iteration, one thread per unit (a run
+// of `cnt` eigenvalues from j0 whose gaps are below the cluster tolerance;
+// most units are single eigenvalues), all jobs in one launch (the jobs are
+// independent; the largest come first, their threads run longest). Per thread,
+// in the job's `scratch` (interleaved by the job's threads: entry e of thread
+// t at e * nu + t, so that a warp's accesses to the same row are contiguous):
+// the U rows of the banded LU (2P+1 entries and the transformed right-hand
+// side per row), then the current vector (n).
 template <int P>
 __global__ void __launch_bounds__(128)
-k_eig_vectors(EigJob J, const int2* __restrict__ units, int nunits, const double* __restrict__ Kb,
-              const double* __restrict__ Mb, const double* __restrict__ lam, double* __restrict__ U,
-              double* __restrict__ Ut, double* __restrict__ scratch) {
+k_eig_vectors(const EigJob* __restrict__ jobs, int njobs, long long nunits, const int2* __restrict__ units,
+              const double* __restrict__ Kb, const double* __restrict__ Mb, const double* __restrict__ lam,
+              double* __restrict__ U, double* __restrict__ Ut, double* __restrict__ scratch_all) {
     constexpr int W2 = 2 * P + 1, SL = W2 + 1;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= nunits) return;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= nunits) return;
+    int a = 0, b = njobs - 1;
+    while (a < b) {            // last job with u0 <= gt
+        const int m = (a + b + 1) >> 1;
+        if (jobs[m].u0 <= gt) a = m; else b = m - 1;
+    }
+    const EigJob J = jobs[a];
+    const int tid = (int)(gt - J.u0);
     const int n = J.n;
-    const long long NT = nunits;
+    const long long NT = J.nu;
+    double* __restrict__ scratch = scratch_all + J.soff;
     const double* kb = Kb + J.boff;
     const double* mb = Mb + J.boff;
     const double* lm = lam + J.loff;
@@ -170,7 +180,7 @@ k_eig_vectors(EigJob J, const int2* __restrict__ units, int nunits, const double
     double* vecbase = scratch + (long long)n * SL * NT;
     auto vec = [&](int i) -> double& { return vecbase[(long long)i * NT + tid]; };
     const double tiny = DBL_EPSILON * DBL_EPSILON * J.anorm;   // only an exact or near-exact zero pivot
-    const int j0 = units[tid].x, cnt = units[tid].y;
+    const int j0 = units[gt].x, cnt = units[gt].y;
     double sprev = 0.0;
     for (int m = 0; m < cnt; ++m) {
         const int j = j0 + m;
@@ -330,10 +340,13 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
     // each thread's Gram-Schmidt work small; across a cut the gap is above
     // 1e-6 lam.
     std::vector<int2> units;
-    std::vector<long long> uoff(jobs.size() + 1, 0);
+    std::vector<EigJob> vjobs;   // the jobs in launch order (largest first) with their units and scratch
+    std::vector<size_t> ord(jobs.size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return jobs[x].n > jobs[y].n; });
     size_t scratch_doubles = 0;
-    for (size_t q = 0; q < jobs.size(); ++q) {
-        const EigJob& J = jobs[q];
+    for (size_t q : ord) {
+        EigJob J = jobs[q];
         const double* l = hlam.data() + J.t0;
         for (int j = 0; j < J.n; ++j)
             if (!(l[j] > 0.0) || !std::isfinite(l[j]) || (j > 0 && l[j] < l[j - 1])) {
@@ -341,7 +354,7 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
                 msg = "eigenvalue bisection produced a non-positive, non-finite or unordered value";
                 return cudaErrorInvalidValue;
             }
-        uoff[q] = (long long)units.size();
+        J.u0 = (long long)units.size();
         for (int j = 0; j < J.n;) {
             int j1 = j + 1;
             while (j1 < J.n) {
@@ -352,22 +365,24 @@ static cudaError_t launch_eig(std::vector<EigJob>& jobs, const std::vector<doubl
             units.push_back(make_int2(j, j1 - j));
             j = j1;
         }
-        const size_t nu = units.size() - (size_t)uoff[q];
-        scratch_doubles = std::max(scratch_doubles, (size_t)J.n * (2 * P + 3) * nu);
+        J.nu = (int)((long long)units.size() - J.u0);
+        J.soff = (long long)scratch_doubles;
+        scratch_doubles += (size_t)J.n * (2 * P + 3) * J.nu;
+        vjobs.push_back(J);
     }
-    uoff[jobs.size()] = (long long)units.size();
+    const long long nunits = (long long)units.size();
     if ((e = cudaMalloc(&dunits, units.size() * sizeof(int2))) != cudaSuccess ||
         (e = cudaMalloc(&scratch, std::max<size_t>(scratch_doubles, 1) * 8)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dunits, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        (e = cudaMemcpyAsync(dunits, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(djobs, vjobs.data(), vjobs.size() * sizeof(EigJob), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
         cleanup();
         msg = "eigenvector scratch (" + std::to_string(scratch_doubles * 8) + " bytes)";
         return e;
     }
-    for (size_t q = 0; q < jobs.size() && e == cudaSuccess; ++q) {
-        const int nu = (int)(uoff[q + 1] - uoff[q]);
+    if (nunits > 0) {
         SGIGA_COUNT_LAUNCH();
-        k_eig_vectors<P><<<(unsigned)((nu + 127) / 128), 128, 0, s>>>(jobs[q], dunits + uoff[q], nu, dKb, dMb, dlam,
-                                                                      dU, dUt, scratch);
+        k_eig_vectors<P><<<(unsigned)((nunits + 127) / 128), 128, 0, s>>>(djobs, (int)vjobs.size(), nunits, dunits, dKb,
+                                                                          dMb, dlam, dU, dUt, scratch);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

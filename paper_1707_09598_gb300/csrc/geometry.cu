@@ -151,9 +151,9 @@ __global__ void k_coef_features(DevPlan P, const double* __restrict__ feat, int 
     for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
     for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
-        double xi[3], wq, x[3], J[3][3];
+        double xi[3], wq, x[3];
         qp_param(P, g, L, xi, wq);
-        patch_eval(P.patch[g.patch], xi, x, J);
+        patch_point(P.patch[g.patch], xi, x);
         double f = 0.0;
         for (int i = 0; i < nfeat; ++i) {
             const double* ft = feat + 4 * i;
@@ -186,9 +186,9 @@ __global__ void k_qp_coords(DevPlan P, double* xq) {
     for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
     for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
-        double xi[3], wq, x[3], J[3][3];
+        double xi[3], wq, x[3];
         qp_param(P, g, L, xi, wq);
-        patch_eval(P.patch[g.patch], xi, x, J);
+        patch_point(P.patch[g.patch], xi, x);
         long long nat = natural_index(g, d, Q, L);
         for (int k = 0; k < d; ++k) xq[(long long)k * P.nqp + nat] = x[k];
     }
@@ -254,9 +254,9 @@ __global__ void k_rhs_density(DevPlan P, int src, const double* __restrict__ fna
         if (fnat) {
             f = fnat[natural_index(g, d, Q, L)];
         } else {
-            double xi[3], wq, x[3], J[3][3];
+            double xi[3], wq, x[3];
             qp_param(P, g, L, xi, wq);
-            patch_eval(P.patch[g.patch], xi, x, J);
+            patch_point(P.patch[g.patch], xi, x);
             f = builtin_source(src, d, x);
         }
         long long o = t.g_off + idx;
@@ -273,9 +273,9 @@ __global__ void k_source_qp(DevPlan P, int src, double* __restrict__ fout) {
     for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
     for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
         QpLoc L = tile_qp(g, t, d, Q, idx);
-        double xi[3], wq, x[3], J[3][3];
+        double xi[3], wq, x[3];
         qp_param(P, g, L, xi, wq);
-        patch_eval(P.patch[g.patch], xi, x, J);
+        patch_point(P.patch[g.patch], xi, x);
         fout[natural_index(g, d, Q, L)] = builtin_source(src, d, x);
     }
 }
@@ -359,6 +359,56 @@ cudaError_t launch_feature_density(const DevPlan& P, double* out, int mode, cuda
     return cudaGetLastError();
 }
 
+// Index of the physical pair (k, l), k <= l, among the d(d+1)/2 entries of a
+// symmetric d x d matrix stored row by row (upper triangle).
+__device__ __forceinline__ int phys_pair(int d, int k, int l) {
+    if (k > l) { const int t = k; k = l; l = t; }
+    if (d == 2) return k == 0 ? l : 2;
+    return k == 0 ? l : (k == 1 ? 2 + l : 5);
+}
+
+// Move the geometry coefficients between the plan's tile-major layout and a
+// natural layout (physical component pairs, quadrature points in natural order
+// with the plan's natural offsets). EXPORT copies G, mw out of the tile-major
+// planes; otherwise they are written back into the tile-major planes of the
+// current tiling. The values are the same doubles either way, so a re-tiling
+// gathers them instead of evaluating the patch map again.
+template <bool EXPORT>
+__global__ void k_geometry_move(DevPlan P, double* __restrict__ Gn, double* __restrict__ mwn) {
+    const TileDesc t = P.tiles[blockIdx.x];
+    const GridDesc g = P.grids[t.grid];
+    const int d = P.d, Q = P.Q;
+    long long nq = 1;
+    for (int k = 0; k < d; ++k) nq *= (long long)Q * g.T[k];
+    int cmap[6];
+    int nc = 0;
+    for (int a = 0; a < d; ++a)
+        for (int b = a; b < d; ++b) cmap[nc++] = phys_pair(d, g.perm[a], g.perm[b]);
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+        const QpLoc L = tile_qp(g, t, d, Q, idx);
+        const long long nat = natural_index(g, d, Q, L);
+        const long long o = t.g_off + idx;
+        for (int c = 0; c < nc; ++c) {
+            if (EXPORT) Gn[(long long)cmap[c] * P.nqp + nat] = P.G[(long long)c * P.nqp + o];
+            else P.G[(long long)c * P.nqp + o] = Gn[(long long)cmap[c] * P.nqp + nat];
+        }
+        if (EXPORT) mwn[nat] = P.mw[o];
+        else P.mw[o] = mwn[nat];
+    }
+}
+
+cudaError_t launch_geometry_export(const DevPlan& P, double* Gn, double* mwn, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_geometry_move<true><<<P.ntiles, 256, 0, s>>>(P, Gn, mwn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_import(const DevPlan& P, double* Gn, double* mwn, cudaStream_t s) {
+    SGIGA_COUNT_LAUNCH();
+    k_geometry_move<false><<<P.ntiles, 256, 0, s>>>(P, Gn, mwn);
+    return cudaGetLastError();
+}
+
 // Copy one grid's G (physical component order) and mw into natural order.
 __global__ void k_geometry_natural(DevPlan P, int tile0, double* Gnat, double* mwnat) {
     const TileDesc t = P.tiles[tile0 + blockIdx.x];
@@ -396,6 +446,16 @@ cudaError_t launch_geometry_natural(const DevPlan& P, int g, const GridDesc& gh,
     return cudaGetLastError();
 }
 
+// patch_eval behind a call boundary. Inlined into k_map_points with the patch
+// chosen by a runtime index, this kernel returned non-finite coordinates for
+// every point under nvcc 13.0 for sm_103a (the same source built for the host
+// under ASan/UBSan, and the same kernel with a compile-time patch index, give
+// finite values equal to the oracle's); the out-of-line call gives the oracle's
+// values and is what the map-point tests check.
+__device__ __noinline__ void patch_eval_call(const Patch& pt, const double* t, double* X, double (*J)[3]) {
+    patch_eval(pt, t, X, J);
+}
+
 // Physical coordinates and Jacobian determinant of the patch map at
 // parametric points (eq. F-B-splines; NURBS with separable weights).
 __global__ void k_map_points(DevPlan P, const double* xi, const int* patch, long long npts, int npatch, double* x,
@@ -411,7 +471,7 @@ __global__ void k_map_points(DevPlan P, const double* xi, const int* patch, long
         t[k] = xi[j * d + k];
         if (!(t[k] >= 0.0 && t[k] <= 1.0)) { atomicOr(&P.flags[1], 1); t[k] = t[k] < 0.0 ? 0.0 : 1.0; }
     }
-    patch_eval(P.patch[q], t, X, J);
+    patch_eval_call(P.patch[q], t, X, J);
     for (int k = 0; k < d; ++k) x[j * d + k] = X[k];
     if (detj) {
         double dt;

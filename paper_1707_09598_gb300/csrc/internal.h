@@ -99,6 +99,9 @@ struct EigJob {
     long long t0;          // first global thread of the job (bisection)
     double hi0;            // first upper bound tried for the eigenvalues: 2.17 max_i K_ii / M_ii
     double anorm;          // max_i sum_t |K_it| + hi0 |M_it|: the scale of K - s M's entries
+    long long u0;          // first inverse-iteration unit of the job (all jobs' units in one launch)
+    int nu;                // its units
+    long long soff;        // its inverse-iteration scratch (doubles)
 };
 
 // Vector chunk: a contiguous piece of one component's packed vector (or of

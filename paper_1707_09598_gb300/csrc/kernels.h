@@ -50,6 +50,8 @@ struct DevPlan {
     const double* acoef;     // diffusion coefficient a(x_q) [nqp], natural order, or null (a = 1)
     size_t smem_op;          // dynamic shared bytes of the operator kernel
     int op_nth;              // threads per block of the FP32 3D operator kernel (256 or 128)
+    int op_pf;               // FP32 3D operator: L2 prefetch per metric plane and tile, bytes (0: the whole
+                             // segment, > 0: at most this many, < 0: none)
     int diag;                // every geometry plane off the diagonal is exactly zero
     const CompDesc* comps;   // components (CG systems); pieces are grids[]
     int ncomps;
@@ -84,6 +86,9 @@ int gpu_generalized_eigen(int p, std::vector<EigJob>& jobs, const std::vector<do
                           std::vector<double>& hlam, cudaStream_t s, std::string& msg);
 // geometry.cu
 cudaError_t launch_geometry(const DevPlan& P, cudaStream_t s);
+// tile-major <-> natural layout of G and mw (re-tiling without re-evaluating the map)
+cudaError_t launch_geometry_export(const DevPlan& P, double* Gn, double* mwn, cudaStream_t s);
+cudaError_t launch_geometry_import(const DevPlan& P, double* Gn, double* mwn, cudaStream_t s);
 cudaError_t launch_coef_features(const DevPlan& P, const double* feat, int nfeat, double amp, double* a,
                                  cudaStream_t s);
 cudaError_t launch_offdiag_check(const DevPlan& P, int* flag, cudaStream_t s);
@@ -104,6 +109,8 @@ cudaError_t set_op2_smem(int p, size_t bytes);
 cudaError_t launch_op2_f32(const DevPlan& P, const float* x, float* y, const int* active, cudaStream_t s);
 cudaError_t launch_op3_f32(const DevPlan& P, const float* x, float* y, const int* active, cudaStream_t s);
 cudaError_t set_op3_smem(int p, size_t bytes);
+// resident blocks per SM of the FP32 3D operator kernel at the plan's settings
+int op3_f32_resident(const DevPlan& Pl);
 // fd.cu
 // Work lists of one preconditioner pass: SMALL items, and LEVEL items by
 // output-tile class (16, 32, 64 columns).

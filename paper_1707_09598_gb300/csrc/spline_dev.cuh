@@ -93,26 +93,18 @@ __device__ __forceinline__ void patch_eval(const Patch& P, const double* xi, dou
         s[k] = find_span(P.knots[k], P.nc[k], deg[k], xi[k]);
         basis_funs<3>(P.knots[k], s[k], deg[k], xi[k], N[k], dN[k]);
     }
-    double A[3] = {0, 0, 0}, dA[3][3] = {{0}}, W = 0, dW[3] = {0, 0, 0};
-    for (int c = 0; c <= deg[2]; ++c)
-        for (int b = 0; b <= deg[1]; ++b)
-            for (int a = 0; a <= deg[0]; ++a) {
-                int i0 = s[0] - deg[0] + a, i1 = s[1] - deg[1] + b, i2 = s[2] - deg[2] + c;
-                double wt = P.w[0][i0] * (d > 1 ? P.w[1][i1] : 1.0) * (d > 2 ? P.w[2][i2] : 1.0);
-                int ci = i0 + P.nc[0] * (i1 + (d > 1 ? P.nc[1] : 1) * i2);
-                double v = N[0][a] * N[1][b] * N[2][c] * wt;
-                double g[3] = {dN[0][a] * N[1][b] * N[2][c] * wt,
-                               N[0][a] * dN[1][b] * N[2][c] * wt,
-                               N[0][a] * N[1][b] * dN[2][c] * wt};
-                W += v;
-                for (int k = 0; k < d; ++k) dW[k] += g[k];
-                for (int i = 0; i < d; ++i) {
-                    A[i] += v * P.cp[ci][i];
-                    for (int k = 0; k < d; ++k) dA[i][k] += g[k] * P.cp[ci][i];
-                }
-            }
     if (!(P.rational[0] || P.rational[1] || P.rational[2])) {
         // Polynomial patch: all weights are 1 and W = 1, so F = A and J = dA.
+        // x = sum (prod N) cp; the derivative sums below give J.
+        double A[3] = {0, 0, 0};
+        for (int c = 0; c <= deg[2]; ++c)
+            for (int b = 0; b <= deg[1]; ++b)
+                for (int a = 0; a <= deg[0]; ++a) {
+                    int i0 = s[0] - deg[0] + a, i1 = s[1] - deg[1] + b, i2 = s[2] - deg[2] + c;
+                    int ci = i0 + P.nc[0] * (i1 + (d > 1 ? P.nc[1] : 1) * i2);
+                    double v = N[0][a] * N[1][b] * N[2][c] * 1.0;
+                    for (int i = 0; i < d; ++i) A[i] += v * P.cp[ci][i];
+                }
         // Column k of J is summed with direction k innermost,
         //   J[i][k] = sum_{other dirs} (prod N) * sum_{a_k} dN_k[a_k] cp_i,
         // so a coordinate that is constant along direction k (an axis-aligned
@@ -139,10 +131,57 @@ __device__ __forceinline__ void patch_eval(const Patch& P, const double* xi, dou
         }
         return;
     }
+    // Rational patch: F = A / W, J = (dA W - A dW^T) / W^2.
+    double A[3] = {0, 0, 0}, dA[3][3] = {{0}}, W = 0, dW[3] = {0, 0, 0};
+    for (int c = 0; c <= deg[2]; ++c)
+        for (int b = 0; b <= deg[1]; ++b)
+            for (int a = 0; a <= deg[0]; ++a) {
+                int i0 = s[0] - deg[0] + a, i1 = s[1] - deg[1] + b, i2 = s[2] - deg[2] + c;
+                double wt = P.w[0][i0] * (d > 1 ? P.w[1][i1] : 1.0) * (d > 2 ? P.w[2][i2] : 1.0);
+                int ci = i0 + P.nc[0] * (i1 + (d > 1 ? P.nc[1] : 1) * i2);
+                double v = N[0][a] * N[1][b] * N[2][c] * wt;
+                double g[3] = {dN[0][a] * N[1][b] * N[2][c] * wt,
+                               N[0][a] * dN[1][b] * N[2][c] * wt,
+                               N[0][a] * N[1][b] * dN[2][c] * wt};
+                W += v;
+                for (int k = 0; k < d; ++k) dW[k] += g[k];
+                for (int i = 0; i < d; ++i) {
+                    A[i] += v * P.cp[ci][i];
+                    for (int k = 0; k < d; ++k) dA[i][k] += g[k] * P.cp[ci][i];
+                }
+            }
     for (int i = 0; i < d; ++i) {
         x[i] = A[i] / W;
         for (int k = 0; k < d; ++k) J[i][k] = (dA[i][k] * W - A[i] * dW[k]) / (W * W);
     }
+}
+
+// x = F(xi) alone (no Jacobian): the same sums as patch_eval's, so the same
+// doubles.
+__device__ __forceinline__ void patch_point(const Patch& P, const double* xi, double* x) {
+    const int d = P.d;
+    double N[3][4];
+    int s[3], deg[3];
+    for (int k = 0; k < 3; ++k) {
+        deg[k] = 0; s[k] = 0; N[k][0] = 1.0;
+        if (k >= d) continue;
+        deg[k] = P.deg[k];
+        s[k] = find_span(P.knots[k], P.nc[k], deg[k], xi[k]);
+        basis_funs<3>(P.knots[k], s[k], deg[k], xi[k], N[k], nullptr);
+    }
+    const bool rat = P.rational[0] || P.rational[1] || P.rational[2];
+    double A[3] = {0, 0, 0}, W = 0;
+    for (int c = 0; c <= deg[2]; ++c)
+        for (int b = 0; b <= deg[1]; ++b)
+            for (int a = 0; a <= deg[0]; ++a) {
+                int i0 = s[0] - deg[0] + a, i1 = s[1] - deg[1] + b, i2 = s[2] - deg[2] + c;
+                double wt = rat ? P.w[0][i0] * (d > 1 ? P.w[1][i1] : 1.0) * (d > 2 ? P.w[2][i2] : 1.0) : 1.0;
+                int ci = i0 + P.nc[0] * (i1 + (d > 1 ? P.nc[1] : 1) * i2);
+                double v = N[0][a] * N[1][b] * N[2][c] * wt;
+                W += v;
+                for (int i = 0; i < d; ++i) A[i] += v * P.cp[ci][i];
+            }
+    for (int i = 0; i < d; ++i) x[i] = rat ? A[i] / W : A[i];
 }
 
 }  // namespace sgiga

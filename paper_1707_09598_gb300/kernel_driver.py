@@ -8,7 +8,8 @@ the mixed-precision plan), precond (fast diagonalisation), rhs (load
 vector), solve (batched PCG), eval (evaluation + combination on the 17^d
 lattice), solve_scaled (the perturbed-cube mixed solve with the scaled
 preconditioner S * FD(S * r), S = c^(-1/2), to 1e-8 with inner solves to
-1e-3: the kernels of the learned + mixed solve without its training).
+1e-3: the kernels of the learned + mixed solve without its training),
+solve_mixed (the same mixed solve with the plain FD preconditioner).
 --coef sets the log-normal coefficient (128 Fourier features, seed 2);
 --host-loop runs the CG loops from the host (profilers then list every
 kernel). Prints the mean CUDA-event time per repetition.
@@ -30,7 +31,7 @@ from paper_1707_09598_gb300.inputs import eval_points, random_vector  # noqa: E4
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="apply", choices=["apply", "apply_f32", "precond", "precond_f32", "rhs", "solve",
-                                                      "eval", "solve_scaled"])
+                                                      "eval", "solve_scaled", "solve_mixed"])
     ap.add_argument("--coef", action="store_true")
     ap.add_argument("--host-loop", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
@@ -39,12 +40,14 @@ def main():
     ap.add_argument("--w", type=int, default=10)
     ap.add_argument("--domain", default="unit", help="unit, annulus or perturbed (cube with a seeded cubic perturbation)")
     ap.add_argument("--tune", action="store_true", help="run the autotuner first")
+    ap.add_argument("--tiling", default=None,
+                    help="budget,qpcap,nthreads,prefetch: set the operator's decomposition (after --tune, if given)")
     a = ap.parse_args()
     stream = torch.cuda.Stream()
     # torch's fills and reads of the buffers handed to the plan run on the
     # plan's stream, in order with its calls
     torch.cuda.set_stream(stream)
-    f32 = a.op.endswith("_f32") or a.op == "solve_scaled"
+    f32 = a.op.endswith("_f32") or a.op in ("solve_scaled", "solve_mixed")
     kw = {}
     if a.domain == "perturbed":   # the learned-preconditioner geometry: seeded cubic perturbation, general metric
         from paper_1707_09598_gb300.inputs import perturbed_cube_patch
@@ -60,16 +63,21 @@ def main():
         sgiga.sgiga_set_coefficient(P.handle, om, ph, amp)
     if a.tune:
         t = sgiga.sgiga_autotune(P.handle, reps=3)
-        print("autotune: best %d/%d/%d threads %.4f ms; fd ks %d %s; candidates %s" % (
-            t.budget[t.best], t.qpcap[t.best], t.nthreads[t.best], t.best_ms, t.fd_ks[t.fd_best],
+        print("autotune: best %d/%d/%d threads prefetch %d, %.4f ms; fd ks %d %s; candidates %s" % (
+            t.budget[t.best], t.qpcap[t.best], t.nthreads[t.best], t.best_prefetch, t.best_ms, t.fd_ks[t.fd_best],
             "grouped" if t.fd_grouped[t.fd_best] else "per piece",
-            " ".join("%d/%d/%d:%.4f" % (t.budget[i], t.qpcap[i], t.nthreads[i], t.ms[i]) for i in range(t.ncand))))
-    if a.op == "solve_scaled":
+            " ".join("%d/%d/%d/%d:%.4f" % (t.budget[i], t.qpcap[i], t.nthreads[i], t.prefetch[i], t.ms[i])
+                     for i in range(t.ncand))))
+    if a.tiling:
+        b, q, nt, pf = (int(v) for v in a.tiling.split(","))
+        sgiga.sgiga_set_tiling(P.handle, b, q, nt, pf)
+    if a.op in ("solve_scaled", "solve_mixed"):
         sgiga.sgiga_set_solver_options(P.handle, use_graph=not a.host_loop, inner_tol=1e-3, inner_max=100)
+    if a.op == "solve_scaled":
         phi = torch.zeros(P.info.ndof, dtype=torch.float32, device="cuda")
         sgiga.sgiga_net_features(P.handle, phi)
         sgiga.sgiga_net_set_scaling(P.handle, torch.exp(-0.5 * phi).contiguous())
-    elif a.host_loop:
+    elif a.host_loop and a.op != "solve_mixed":
         sgiga.sgiga_set_solver_options(P.handle, use_graph=False)
     n = P.info.ndof
     x = torch.as_tensor(random_vector(n, 1), device="cuda")
@@ -95,7 +103,7 @@ def main():
             sgiga.sgiga_set_rhs_builtin(P.handle, src)
         elif a.op == "solve":
             sgiga.sgiga_solve(P.handle, 1e-12, 50)
-        elif a.op == "solve_scaled":
+        elif a.op in ("solve_scaled", "solve_mixed"):
             sgiga.sgiga_solve(P.handle, 1e-8, 50)
         else:
             sgiga.sgiga_eval(P.handle, pts, len(pts), uc)

@@ -79,7 +79,8 @@ class sgiga_tune_result(ctypes.Structure):
                 ("ms", ctypes.c_double * 16), ("budget", ctypes.c_int * 16), ("qpcap", ctypes.c_int * 16),
                 ("nthreads", ctypes.c_int * 16),
                 ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
-                ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8)]
+                ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8),
+                ("prefetch", ctypes.c_int * 16), ("best_prefetch", ctypes.c_int)]
 
 
 class sgiga_plan_times_t(ctypes.Structure):
@@ -117,6 +118,7 @@ _SIGS = {
     "sgiga_solve": (_I, [_P, _D, _I, ctypes.POINTER(sgiga_solve_stats)]),
     "sgiga_set_solver_options": (_I, [_P, _I, _D, _I]),
     "sgiga_autotune": (_I, [_P, _I, ctypes.POINTER(sgiga_tune_result)]),
+    "sgiga_set_tiling": (_I, [_P, _I, _I, _I, _I]),
     "sgiga_get_solution": (_I, [_P, _P]),
     "sgiga_set_solution": (_I, [_P, _P]),
     "sgiga_eval": (_I, [_P, _P, _L, _P]),
@@ -310,6 +312,10 @@ def sgiga_autotune(plan, reps=3):
     out = sgiga_tune_result()
     _check(_lib.sgiga_autotune(plan, int(reps), ctypes.byref(out)))
     return out
+
+
+def sgiga_set_tiling(plan, budget, qpcap, nthreads=256, prefetch=0):
+    _check(_lib.sgiga_set_tiling(plan, int(budget), int(qpcap), int(nthreads), int(prefetch)))
 
 
 def sgiga_set_precond_split(plan, ks, grouped=False):

@@ -135,3 +135,42 @@ def test_annulus_w12_full_size_mixed(sg, p):
         levels = [tuple(g.levels[:2]) for g in P.grids]
         for col, sel in enumerate([(12, 1), (6, 6), (1, 12)]):
             assert _rel(ucn[levels.index(sel)], gold[:, 1 + col]) < 1e-8
+
+
+@pytest.mark.gpu
+def test_fp32_apply_under_every_tiling_and_prefetch(sg):
+    """The FP32 3D operator at every decomposition the autotuner may choose
+    (tile policy, 256 or 128 threads, L2 prefetch of the metric planes whole,
+    capped or off) against the oracle's assembled K on sampled components of
+    an annulus (general metric) plan with several tiles per component; the
+    tilings only reorder FP32 sums (atomics), so the results agree to a few
+    ulp. Out-of-range settings are argument errors."""
+    d, p, w = 3, 3, 7
+    with sg.Plan(d, p, w, domain="annulus", precision="mixed") as P:
+        n = P.info.ndof
+        x = random_vector(n, seed=47)
+        xd = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+        geom = geometry.make("annulus", d)
+        refs = {}
+        for g in P.grids[:: max(1, len(P.grids) // 4)]:
+            comp = Component(geom, tuple(g.levels[:d]), p, None, "uniform", 1.0).assemble()
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            refs[sl] = comp.K @ x[sl].astype(np.float32).astype(np.float64)
+        first = None
+        for budget, qpcap in ((48 * 1024, 4096), (110 * 1024, 16384), (200 * 1024, 32768)):
+            for nth in (256, 128):
+                for pf in (0, 1024, 16, -1):
+                    sg.sgiga_set_tiling(P.handle, budget, qpcap, nth, pf)
+                    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+                    sg.sgiga_apply_f32(P.handle, xd, y)
+                    yh = y.double().cpu().numpy()
+                    for sl, ref in refs.items():
+                        assert _rel(yh[sl], ref) < 2e-5, (budget, qpcap, nth, pf, _rel(yh[sl], ref))
+                    if first is None:
+                        first = yh
+                    assert _rel(yh, first) < 2e-6
+        for bad in ((8 * 1024, 4096, 256, 0), (110 * 1024, 16, 256, 0), (110 * 1024, 4096, 64, 0),
+                    (110 * 1024, 4096, 256, 24)):
+            with pytest.raises(sg.SgigaError) as ei:
+                sg.sgiga_set_tiling(P.handle, *bad)
+            assert ei.value.code == sg.SGIGA_ERR_ARG
