@@ -392,15 +392,19 @@ class Workload:
         self.npts = len(self.pts_h)
         self.gold = np.loadtxt(GOLDEN)[:, 0]
 
-    def plan(self, precision, precond, components=None, autotune=True):
-        """A plan with the coefficient set and (optionally) autotuned; returns
-        (plan, set-up seconds, phase times)."""
+    def plan(self, precision, precond, components=None, autotune=True, use_graph=True):
+        """A plan with the coefficient set, the solver options of the workload
+        (mixed plans: inner tolerance; set before the autotuner, whose probe
+        solves use them) and (optionally) autotuned; returns (plan, set-up
+        seconds, phase times, tuning)."""
         sg = self.sg
         t0 = time.perf_counter()
         kw = {} if components is None else {"components": components}
         P = sg.Plan(3, WORKLOAD["p"], WORKLOAD["w"], domain="patch", patch=([3, 3, 3], self.kn, self.cp),
                     precision=precision, precond=precond, stream=self.stream, **kw)
         sg.sgiga_set_coefficient(P.handle, self.om, self.ph, self.amp)
+        if precision == "mixed":
+            sg.sgiga_set_solver_options(P.handle, use_graph=use_graph, inner_tol=WORKLOAD["inner_tol"], inner_max=100)
         tune = sg.sgiga_autotune(P.handle, reps=2) if autotune else None
         return P, time.perf_counter() - t0, sg.sgiga_plan_times(P.handle), tune
 
@@ -474,13 +478,13 @@ def measure_comparators(W, args):
     out["per_grid_fp64"] = {"ms": e0.elapsed_time(e1), "iterations": its, "plans": len(singles),
                             "setup_s": setup_s, "rel_l2_vs_oracle": _rel(acc, W.gold)}
     # mixed: FP32 inner FD-CG in FP64 refinement
-    M, ps, pt, _ = W.plan("mixed", "fd")
-    sg.sgiga_set_solver_options(M.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
-                                inner_max=100)
+    M, ps, pt, mt = W.plan("mixed", "fd", use_graph=not args.host_loop)
     sg.sgiga_set_rhs_builtin(M.handle, "one")
     st, rc, ms = W.timed_solve(M, tol, 50)
     out["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc, "setup_s": ps,
-                       "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(M), W.gold)}
+                       "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(M), W.gold),
+                       "solve_precision": "fp64" if mt.solve_precision == 0 else "mixed",
+                       "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "mixed": mt.solve_ms_mixed}}
     return out, M
 
 
@@ -488,9 +492,7 @@ def train_learned(W, args):
     """The learned plan: set-up, the network trained on the plan's own CG
     pairs, and its solve. Returns (plan, dict, tuning)."""
     sg = W.sg
-    L, ps, pt, tune = W.plan("mixed", "learned")
-    sg.sgiga_set_solver_options(L.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
-                                inner_max=100)
+    L, ps, pt, tune = W.plan("mixed", "learned", use_graph=not args.host_loop)
     t0 = time.perf_counter()
     sg.sgiga_net_init(L.handle, 11)
     tr = sg.sgiga_train_net(L.handle, target_pairs=10000, max_iter_record=30, epochs=12, lr=5e-4, seed=100,
@@ -575,11 +577,40 @@ def cube_line(sgiga, torch, stream, steps):
     apply_s = a0.elapsed_time(a1) / 20 / 1e3
     flops = apply_flops(P)
     peak = fp64_peak_tflops(torch)
+    # the same step on a MIXED plan: its autotuner times the mixed solve against
+    # FP64 PCG (FD is exact on the cube) and keeps the faster
+    M = sgiga.Plan(C["d"], C["p"], C["w"], domain="unit", stream=stream, precision="mixed")
+    sgiga.sgiga_set_rhs(M.handle, f)
+    mt = sgiga.sgiga_autotune(M.handle, reps=3)
+    ucm = torch.zeros_like(uc)
+    um = torch.zeros_like(u)
+
+    def step_m():
+        sgiga.sgiga_set_rhs(M.handle, f)
+        sgiga.sgiga_solve(M.handle, C["tol"], 50)
+        sgiga.sgiga_eval(M.handle, pts, npts, ucm)
+        sgiga.sgiga_combine(M.handle, ucm, npts, um)
+
+    for _ in range(3):
+        step_m()
+    m0, m1 = _events(torch)
+    torch.cuda.synchronize()
+    m0.record(stream)
+    for _ in range(steps):
+        step_m()
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mixed_plan = {"solve_precision": "fp64" if mt.solve_precision == 0 else "mixed",
+                  "ms_per_step": m0.elapsed_time(m1) / steps,
+                  "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "mixed": mt.solve_ms_mixed},
+                  "rel_l2_vs_oracle": _rel(um.cpu().numpy(), np.loadtxt(CUBE_GOLDEN)[:, 0])}
+    M.close()
     out = {"workload": CUBE_NAME, "value": P.info.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
            "dtype": "f64", "rel_l2_vs_oracle": l2, "target": 1e-10,
            "apply_fp64": {"ms": apply_s * 1e3, "algorithmic_flops": flops, "TFLOPs": flops / apply_s / 1e12,
                           "fp64_peak_TFLOPs": peak, "frac": flops / apply_s / 1e12 / peak,
-                          "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU"}}
+                          "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU"},
+           "mixed_plan": mixed_plan}
     P.close()
     return out
 
@@ -606,9 +637,7 @@ def run_ours(args):
     if not args.quick:
         comparison, M = measure_comparators(W, args)
     else:
-        M, _, _, _ = W.plan("mixed", "fd")
-        sgiga.sgiga_set_solver_options(M.handle, use_graph=not args.host_loop, inner_tol=WORKLOAD["inner_tol"],
-                                       inner_max=100)
+        M, _, _, _ = W.plan("mixed", "fd", use_graph=not args.host_loop)
         sgiga.sgiga_set_rhs_builtin(M.handle, "one")
         st, rc, ms = W.timed_solve(M, tol, 50)
         comparison["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc}

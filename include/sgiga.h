@@ -97,7 +97,10 @@ enum { SGIGA_GRADING_UNIFORM = 0, SGIGA_GRADING_RADICAL = 1, SGIGA_GRADING_ONESI
  * MIXED_FP32: FP64 iterative refinement (residual r = b - K x with the FP64
  * operator, x += d) around an inner preconditioned-CG solve K d = r in FP32
  * (FP32 operator apply with FP32 geometry planes and tables, FP32
- * preconditioner), per-component scalars and reductions in FP64. */
+ * preconditioner), per-component scalars and reductions in FP64. After
+ * sgiga_autotune a MIXED_FP32 plan with the FD preconditioner may solve as
+ * FP64 (its FP64 data is complete) when that was faster on the probe
+ * (sgiga_tune_result.solve_precision). */
 enum { SGIGA_PREC_FP64 = 0, SGIGA_PREC_MIXED_FP32 = 1 };
 
 /* Preconditioner of the batched conjugate-gradient solve. FD: fast
@@ -323,7 +326,7 @@ int sgiga_solve(sgiga_plan_t plan, double rel_tol, int max_iter,
  * the SMs better, longer ones need fewer atomic partial sums), times `reps`
  * preconditioner applications for each and keeps the fastest. Overwrites the plan's work vectors (not its load vector
  * or solution). out (host, may be NULL) receives the per-candidate mean
- * times. */
+ * times. (3) See solve_precision below. */
 typedef struct {
     int ncand, best, ntiles;
     double best_ms;
@@ -339,6 +342,15 @@ typedef struct {
                          start (0: whole segments; > 0: at most this many bytes per plane, so that the segments in
                          flight on all SMs total 48 or 16 MB; -1: none) */
     int best_prefetch;
+    /* (3) MIXED_FP32 plans with the FD preconditioner: the precision
+     * sgiga_solve uses from now on (SGIGA_PREC_FP64 when plain FP64 PCG solved
+     * a probe load vector to 1e-8 faster than the mixed solve, as where FD is
+     * nearly exact; the decomposition is then tuned again with the FP64
+     * kernels, and the fields above report that tuning), and the two probe
+     * solves' wall times (ms; 0: not run or, for FP64, not converged within
+     * the mixed solve's time). Other plans: their own precision, times 0. */
+    int solve_precision;
+    double solve_ms_fp64, solve_ms_mixed;
 } sgiga_tune_result;
 int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
 

@@ -1338,9 +1338,71 @@ int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
     return precond_fd<float>(P, r, z, nullptr, P->f_t1, P->f_t2);
 }
 
-int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
-    if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
-    const auto tt0 = std::chrono::steady_clock::now();
+// MIXED_FP32 plans with the FD preconditioner: the mixed solve against plain
+// FP64 PCG, both to a relative residual of 1e-8 on a probe load vector (the
+// plan's own if it is set, else that of f = 1), each timed after one run that
+// captures its graphs; sgiga_solve then runs the faster. FP64 PCG gets at most
+// the iterations that fit in the mixed solve's time. The plan's load vector
+// and solution are restored.
+static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx) {
+    *ms64 = *msmx = 0.0;
+    P->solve_fp64 = false;
+    const size_t n = (size_t)P->ndof;
+    cudaStream_t s = P->stream;
+    double* save = nullptr;
+    if (cudaMalloc(&save, 2 * n * 8) != cudaSuccess) { cudaGetLastError(); return SGIGA_OK; }   // keep MIXED
+    int rc = SGIGA_OK;
+    auto body = [&]() -> int {
+        CUDA_TRY(cudaMemcpyAsync(save, P->d_b, n * 8, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(save + n, P->d_x, n * 8, cudaMemcpyDeviceToDevice, s));
+        const int ng = (int)P->comps.size();
+        CUDA_TRY(launch_dot<double>(P->dp, P->d_b, P->d_b, P->d_partial, P->d_scal, s));
+        std::vector<double> hb(ng);
+        CUDA_TRY(cudaMemcpyAsync(hb.data(), P->d_scal, ng * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        bool zero = true;
+        for (double v : hb) zero = zero && v == 0.0;
+        if (zero) {
+            CUDA_TRY(launch_rhs_density_builtin(P->dp, SGIGA_SRC_ONE, s));
+            int r = run_rhs_operator(P);
+            if (r) return r;
+        }
+        auto timed = [&](int maxit, int& code) {
+            const auto t0 = std::chrono::steady_clock::now();
+            code = sgiga_solve(P, 1e-8, maxit, nullptr);
+            return since(t0) * 1e3;
+        };
+        int c = 0;
+        timed(50, c);
+        double tm = timed(50, c);
+        if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) return c;
+        if (c != SGIGA_OK) tm = 1e30;
+        P->solve_fp64 = true;
+        timed(1, c);
+        const double t1 = timed(1, c);
+        if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = false; return c; }
+        const int cap = (int)std::min(1000.0, std::max(1.0, tm / std::max(t1, 1e-3)));
+        const double t64 = timed(cap, c);
+        const bool fp64_ok = c == SGIGA_OK;
+        if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = false; return c; }
+        *msmx = tm;
+        *ms64 = fp64_ok ? t64 : 0.0;
+        P->solve_fp64 = fp64_ok && t64 < tm;
+        g_last_error.clear();
+        return SGIGA_OK;
+    };
+    rc = body();
+    cudaMemcpyAsync(P->d_b, save, n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(P->d_x, save + n, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == SGIGA_OK) rc = fail(SGIGA_ERR_CUDA, "autotune: restore failed");
+    cudaFree(save);
+    return rc;
+}
+
+// Operator tile policy (and, for FP32 3D plans, threads per block and the
+// metric planes' L2 prefetch) and preconditioner layout, each timed with the
+// kernels of precision f32 (FP32: the mixed inner solve's; else FP64).
+static int tune_decomposition(sgiga_plan_s* P, int reps, bool f32, sgiga_tune_result* out) {
     struct Cand { size_t budget; long long qpcap; };
     const Cand cands[] = {{48 * 1024, 4096}, {48 * 1024, 16384}, {110 * 1024, 8192},
                           {110 * 1024, 16384}, {200 * 1024, 16384}, {200 * 1024, 32768}};
@@ -1355,7 +1417,6 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     int bi = 3;
     int rc = SGIGA_OK;
     // the operator the plan's CG runs: FP32 in mixed plans (inner solve), else FP64
-    const bool f32 = P->cfg.precision == SGIGA_PREC_MIXED_FP32;
     if (f32) CUDA_TRY(cudaMemsetAsync(P->f_p, 0, (size_t)P->ndof * 4, s));
     auto apply_once = [&]() {
         return f32 ? apply_op(P, P->f_p, P->f_q, nullptr) : apply_op(P, P->d_b, P->d_q, nullptr);
@@ -1431,7 +1492,7 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
         if ((rc = refd(P, ksi, grp))) break;
         // the precision the plan's CG runs in; plain FD (no learned correction)
         auto fd_once = [&]() {
-            if (P->cfg.precision == SGIGA_PREC_MIXED_FP32)
+            if (f32)
                 return precond_fd<float>(P, P->f_b, P->f_z, nullptr, P->f_t1, P->f_t2);
             return precond_fd<double>(P, P->d_b, P->d_z, nullptr, P->d_t1, P->d_t2);
         };
@@ -1464,6 +1525,26 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
             for (int t = 0; t < 3; ++t) items += P->fdl[k][t].size();
         }
         out->fd_nitems = (int)items;
+    }
+    return SGIGA_OK;
+}
+
+int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
+    if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
+    const auto tt0 = std::chrono::steady_clock::now();
+    // the kernels the plan's CG runs: FP32 in mixed plans (inner solve), else FP64
+    int rc = tune_decomposition(P, reps, P->cfg.precision == SGIGA_PREC_MIXED_FP32, out);
+    if (rc) return rc;
+    double ms64 = 0.0, msmx = 0.0;
+    if (P->cfg.precision == SGIGA_PREC_MIXED_FP32 && P->cfg.precond == SGIGA_PRECOND_FD)
+        if ((rc = choose_precision(P, &ms64, &msmx))) return rc;
+    // a mixed plan that now solves in FP64: its decomposition tuned for the FP64 kernels
+    if (P->solve_fp64 && (rc = tune_decomposition(P, reps, false, out))) return rc;
+    if (out) {
+        out->solve_precision = P->cfg.precision == SGIGA_PREC_MIXED_FP32 && !P->solve_fp64 ? SGIGA_PREC_MIXED_FP32
+                                                                                           : SGIGA_PREC_FP64;
+        out->solve_ms_fp64 = ms64;
+        out->solve_ms_mixed = msmx;
     }
     P->t_autotune = since(tt0);
     return SGIGA_OK;
@@ -1527,7 +1608,7 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
                 return fail(SGIGA_ERR_ARG, "the load vector of component " + std::to_string(g) +
                                                " is not finite (a NaN or infinity in f or the boundary data)");
     }
-    if (P->cfg.precision == SGIGA_PREC_FP64) {
+    if (P->cfg.precision == SGIGA_PREC_FP64 || P->solve_fp64) {
         int nact = pcg<double>(P, P->d_b, vecs64(P), rel_tol, max_iter, nullptr, P->d_active, P->d_iters, P->d_scal,
                                nullptr);
         if (nact < 0) return nact;

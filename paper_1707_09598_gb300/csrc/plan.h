@@ -95,6 +95,7 @@ struct sgiga_plan_s {
     bool net_ready = false;
     bool learned_off = false;   // set for the rest of a solve after a refinement step without progress
     bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
+    bool solve_fp64 = false;    // MIXED_FP32 plan whose solve the autotuner found faster as plain FP64 PCG
     cudaStream_t own_stream = nullptr;   // capture/launch stream when the plan's stream is the legacy one
     int* d_counter = nullptr;            // iteration counter of the captured loop
     double* d_eval_vals = nullptr;       // evaluation: basis values per (table, point)

@@ -80,7 +80,9 @@ class sgiga_tune_result(ctypes.Structure):
                 ("nthreads", ctypes.c_int * 16),
                 ("fd_ncand", ctypes.c_int), ("fd_best", ctypes.c_int), ("fd_nitems", ctypes.c_int),
                 ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8),
-                ("prefetch", ctypes.c_int * 16), ("best_prefetch", ctypes.c_int)]
+                ("prefetch", ctypes.c_int * 16), ("best_prefetch", ctypes.c_int),
+                ("solve_precision", ctypes.c_int), ("solve_ms_fp64", ctypes.c_double),
+                ("solve_ms_mixed", ctypes.c_double)]
 
 
 class sgiga_plan_times_t(ctypes.Structure):

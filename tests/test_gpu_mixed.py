@@ -174,3 +174,32 @@ def test_fp32_apply_under_every_tiling_and_prefetch(sg):
             with pytest.raises(sg.SgigaError) as ei:
                 sg.sgiga_set_tiling(P.handle, *bad)
             assert ei.value.code == sg.SGIGA_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_autotune_chooses_the_solve_precision(sg):
+    """On the unit cube the FD preconditioner is the exact inverse (K is a
+    sum of Kronecker products of the same 1D pencils), so FP64 PCG converges
+    in one or two iterations and beats the mixed solve's refinement steps: the
+    autotuner switches the MIXED plan's solve to FP64, whose result then meets
+    the FP64 bound against the oracle's sparse direct solves."""
+    with sg.Plan(3, 3, 6, domain="unit", precision="mixed") as P:
+        sg.sgiga_set_rhs_builtin(P.handle, "sine")
+        b0 = np.zeros(P.info.ndof)
+        sg.sgiga_get_rhs(P.handle, b0)
+        res = sg.sgiga_autotune(P.handle, reps=2)
+        assert res.solve_precision == sg.PREC["fp64"], (res.solve_ms_fp64, res.solve_ms_mixed)
+        assert 0 < res.solve_ms_fp64 < res.solve_ms_mixed
+        b1 = np.zeros(P.info.ndof)
+        sg.sgiga_get_rhs(P.handle, b1)
+        assert np.array_equal(b0, b1)          # the probe solves leave the load vector
+        st, rc = sg.sgiga_solve(P.handle, 1e-12, 50)
+        assert rc == sg.SGIGA_OK and st.inner_iterations == 0
+        u = np.zeros(P.info.ndof)
+        sg.sgiga_get_solution(P.handle, u)
+        geom = geometry.make("unit", 3)
+        f = problems.get("sine3").f
+        for g in P.grids[:: max(1, len(P.grids) // 4)]:
+            comp = Component(geom, tuple(g.levels[:3]), 3).assemble(f=f)
+            sl = slice(g.dof_off, g.dof_off + g.ndof)
+            assert _rel(u[sl], comp.solve()) < 1e-10
