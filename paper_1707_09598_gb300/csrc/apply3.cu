@@ -19,6 +19,11 @@ namespace sgiga {
 // NT threads per block: 256 (FP64, and FP32 with large tiles) or 128 (FP32:
 // more, smaller blocks per SM, so that one block's warps waiting at a stage
 // barrier overlap with other blocks' work; chosen by the autotuner).
+// A metric value of the FP32 apply: streamed (read once per apply), loaded
+// with the evict-first policy so that it does not push the tile's x and y
+// entries, which neighbouring tiles reuse, out of L2.
+__device__ __forceinline__ float ldg_stream(const float* p) { return __ldcs(p); }
+
 template <typename Real, int P, int MODE, bool DIAG, int NT = 256>
 __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (NT == 128 ? 6 : 3) : 2)
 k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* __restrict__ active) {
@@ -87,8 +92,13 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 const float* src = OpData<Real>::G(Pl) + (long long)c * Pl.nqp + td.g_off;
                 long long bytes = (long long)QTb * QTc * Q * Ta * 4;
                 if (Pl.op_pf > 0 && bytes > Pl.op_pf) bytes = Pl.op_pf & ~15;
-                if (bytes >= 16)
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((unsigned)bytes) : "memory");
+                if (bytes >= 16) {
+                    // evict-first: the planes are read once; x and y stay in L2
+                    unsigned long long pol;
+                    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+                    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;\n" ::"l"(src),
+                                 "r"((unsigned)bytes), "l"(pol) : "memory");
+                }
             }
         }
     }
@@ -222,12 +232,12 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 for (int q = 0; q < Q; ++q) {
                     const long long gq = gi + (long long)q * npen;
                     if (DIAG) {
-                        gpre[q][0] = G[gq];
-                        gpre[q][1] = G[3 * nqp + gq];
-                        gpre[q][2] = G[5 * nqp + gq];
+                        gpre[q][0] = ldg_stream(G + gq);
+                        gpre[q][1] = ldg_stream(G + 3 * nqp + gq);
+                        gpre[q][2] = ldg_stream(G + 5 * nqp + gq);
                     } else {
 #pragma unroll
-                        for (int c = 0; c < NGP; ++c) gpre[q][c] = G[c * nqp + gq];
+                        for (int c = 0; c < NGP; ++c) gpre[q][c] = ldg_stream(G + c * nqp + gq);
                     }
                 }
             }

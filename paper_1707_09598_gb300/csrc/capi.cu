@@ -239,6 +239,13 @@ static void free_plan(sgiga_plan_s* P) {
     destroy_loop_graph(P->loop64);
     destroy_loop_graph(P->loop32);
     if (P->own_stream) cudaStreamDestroy(P->own_stream);
+    if (P->fds_ok) {
+        for (int i = 0; i < 3; ++i) {
+            cudaStreamDestroy(P->fds.aux[i]);
+            cudaEventDestroy(P->fds.join[i]);
+        }
+        cudaEventDestroy(P->fds.fork);
+    }
     if (P->d_eval_vals) cudaFree(P->d_eval_vals);
     if (P->d_eval_first) cudaFree(P->d_eval_first);
     for (void* a : P->allocs) cudaFree(a);
@@ -856,6 +863,27 @@ static int build(sgiga_plan_s* P) {
     CUDA_TRY(cudaMallocHost(&P->h_nactive, 2 * sizeof(int)));
     if ((rc = dalloc(P, &P->d_counter, 1))) return rc;
     if (!P->stream) CUDA_TRY(cudaStreamCreate(&P->own_stream));
+    CUDA_TRY(fd_prepare());
+    {   // branches for the kernels of a preconditioner pass (all or none)
+        FDStreams& f = P->fds;
+        const bool fork_ok = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+        bool ok = fork_ok;
+        int ns = 0, ne = 0;
+        for (int i = 0; ok && i < 3; ++i) {
+            ok = cudaStreamCreateWithFlags(&f.aux[i], cudaStreamNonBlocking) == cudaSuccess;
+            ns += ok;
+            ok = ok && cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming) == cudaSuccess;
+            ne += ok;
+        }
+        if (!ok) {
+            for (int i = 0; i < ns; ++i) cudaStreamDestroy(f.aux[i]);
+            for (int i = 0; i < ne; ++i) cudaEventDestroy(f.join[i]);
+            if (fork_ok) cudaEventDestroy(f.fork);
+            cudaGetLastError();
+            return fail(SGIGA_ERR_CUDA, "preconditioner streams");
+        }
+        P->fds_ok = true;
+    }
     if (c.precision == SGIGA_PREC_MIXED_FP32) {
         // FP32 copies of the operator and preconditioner data, FP32 work vectors
         float *Gf, *Rf, *dRf, *Uf, *Utf, *dinvf;

@@ -190,20 +190,49 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
     v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
+// Asynchronous element copy global -> shared (cp.async, L1-allocating), or
+// zero fill when src is null (src-size 0: nothing is read; the instruction
+// still gets a valid global address, `any`).
+template <typename Real>
+__device__ __forceinline__ void cp_async_elem(Real* dst, const Real* src, const Real* any) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = src ? (int)sizeof(Real) : 0;
+    const Real* g = src ? src : any;
+    if constexpr (sizeof(Real) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Dynamic shared memory of k_fd_level<Real, TN>: two stages of the MT tile
+// [16][TM + 4] and the X tile [16][TN + 4].
+template <typename Real, int TN>
+constexpr size_t fd_level_smem() {
+    return 2 * 16 * ((4096 / TN + 4) + (TN + 4)) * sizeof(Real);
+}
+
 // LEVEL items: Y[i][c] = sum_j MT[j][i] X[j][c] over one TM x TN tile
 // (TM = 4096 / TN); thread (tx, ty) owns rows 4 ty .. 4 ty + 3 and columns
 // 4 tx .. 4 tx + 3. Segments with few columns (the long directions of the most
 // anisotropic components) take tall tiles so that the lanes stay busy. Rows and
 // columns past the segment's end are neither computed nor written: the last
 // row tile of an n = 2^l + p - 2 direction holds only p - 2 rows.
+// The K loop is double-buffered: the copies of the next 16 rows of MT and X
+// (cp.async, zero-filled past the item's range) are in flight while the
+// current 16 are multiplied out of shared memory.
 template <typename Real, int TN>
 __global__ void __launch_bounds__(256)
 k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real* __restrict__ in,
            Real* __restrict__ out, const int* __restrict__ active) {
     constexpr int TM = 4096 / TN, NTX = TN / 4;
-    constexpr int LA = 16 * TM / 256, LB = 16 * TN / 256;   // tile loads per thread per K step
-    __shared__ __align__(16) Real As[16][TM + 4];   // MT tile [j][i]
-    __shared__ __align__(16) Real Bs[16][TN + 4];   // X tile  [j][c]
+    constexpr int LA = 16 * TM / 256, LB = 16 * TN / 256;   // tile copies per thread per K step
+    constexpr int SA = 16 * (TM + 4), SB = 16 * (TN + 4);  // elements per stage
+    extern __shared__ __align__(16) unsigned char fd_smem[];
+    Real* const Abuf = reinterpret_cast<Real*>(fd_smem);   // [2][16][TM + 4]
+    Real* const Bbuf = Abuf + 2 * SA;                       // [2][16][TN + 4]
     const FDItem it = items[blockIdx.x];
     const FDSeg sg = P.fdsegs[it.grid];
     const Eig1D e = P.eigs[sg.eig];
@@ -216,7 +245,7 @@ k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real*
     const int c0 = (int)it.c0;
     const int nrows = min(TM, n - i0), ncols = min(TN, sg.ncols - c0);
     const bool split = it.j0 > 0 || it.j1 < n;
-    // this thread's loads of the X tile per K step: (kk, column) fixed over the loop
+    // this thread's copies of the X tile per K step: (kk, column) fixed over the loop
     int ldk[LB], ldc[LB];
     const Real* ldp[LB];
     long long lds[LB];
@@ -232,6 +261,24 @@ k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real*
         ldp[u] = ok ? in + cb[c0 + col] : nullptr;
         lds[u] = ok ? cs[c0 + col] : 0;
     }
+    // stage `buf` <- rows j0 .. j0 + 15 of MT (this item's rows) and of X
+    auto issue = [&](int buf, int j0) {
+        const int kn = min(16, it.j1 - j0);
+        Real* As = Abuf + buf * SA;
+        Real* Bs = Bbuf + buf * SB;
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            const int l = tid + 256 * u;
+            const int kk = l / TM, ii = l % TM;
+            cp_async_elem(As + kk * (TM + 4) + ii,
+                          (ii < nrows && kk < kn) ? MT + (long long)(j0 + kk) * n + i0 + ii : nullptr, MT);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u)
+            cp_async_elem(Bs + ldk[u] * (TN + 4) + ldc[u],
+                          (ldp[u] && ldk[u] < kn) ? ldp[u] + (long long)(j0 + ldk[u]) * lds[u] : nullptr, MT);
+        cp_async_commit();
+    };
     const int tx = tid % NTX, ty = tid / NTX;
     const bool work = 4 * ty < nrows && 4 * tx < ncols;
     Real acc[4][4];
@@ -239,43 +286,32 @@ k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real*
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = Real(0);
-    for (int j0 = it.j0; j0 < it.j1; j0 += 16) {
-        const int kn = min(16, it.j1 - j0);
-#pragma unroll
-        for (int u = 0; u < LA; ++u) {
-            const int l = tid + 256 * u;
-            const int kk = l / TM, ii = l % TM;
-            As[kk][ii] = (ii < nrows && kk < kn) ? MT[(long long)(j0 + kk) * n + i0 + ii] : Real(0);
+    const int nsteps = (it.j1 - it.j0 + 15) / 16;
+    if (nsteps > 0) issue(0, it.j0);
+    for (int st = 0; st < nsteps; ++st) {
+        const int buf = st & 1;
+        if (st + 1 < nsteps) {
+            issue(buf ^ 1, it.j0 + 16 * (st + 1));
+            cp_async_wait<1>();   // this step's stage has landed (the next may be in flight)
+        } else {
+            cp_async_wait<0>();
         }
-#pragma unroll
-        for (int u = 0; u < LB; ++u)
-            Bs[ldk[u]][ldc[u]] = (ldp[u] && ldk[u] < kn) ? ldp[u][(long long)(j0 + ldk[u]) * lds[u]] : Real(0);
         __syncthreads();
         if (work) {
-            if (kn == 16) {
+            const Real* As = Abuf + buf * SA;
+            const Real* Bs = Bbuf + buf * SB;
 #pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    Real a[4], b[4];
-                    ld4(&As[kk][4 * ty], a);
-                    ld4(&Bs[kk][4 * tx], b);
+            for (int kk = 0; kk < 16; ++kk) {   // rows past the item's range are zero
+                Real a[4], b[4];
+                ld4(As + kk * (TM + 4) + 4 * ty, a);
+                ld4(Bs + kk * (TN + 4) + 4 * tx, b);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
-                }
-            } else {
-                for (int kk = 0; kk < kn; ++kk) {
-                    Real a[4], b[4];
-                    ld4(&As[kk][4 * ty], a);
-                    ld4(&Bs[kk][4 * tx], b);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
-                }
+                    for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
             }
         }
-        __syncthreads();
+        __syncthreads();   // the stage is read before the next issue overwrites it
     }
     if (!work) return;
 #pragma unroll
@@ -295,34 +331,73 @@ k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real*
     }
 }
 
+// The level kernels' dynamic shared memory above the 48 KB default (FP64, TN =
+// 16 needs 70 KB); set once per process and device before the first launch.
+cudaError_t fd_prepare() {
+    cudaError_t e = cudaSuccess;
+#define FDSET(R, TN)                                                                                    \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_fd_level<R, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                 (int)fd_level_smem<R, TN>());
+    FDSET(double, 16) FDSET(double, 32) FDSET(double, 64) FDSET(float, 16) FDSET(float, 32) FDSET(float, 64)
+#undef FDSET
+    return e;
+}
+
 template <typename Real>
 cudaError_t launch_fd_pass(const DevPlan& P, const FDLists& L, int dir, int forward, const Real* in, Real* out,
-                           const int* active, cudaStream_t s) {
+                           const int* active, cudaStream_t s, const FDStreams* fs) {
     cudaError_t e = cudaSuccess;
+    const int nk = (L.nlvl[0] > 0) + (L.nlvl[1] > 0) + (L.nlvl[2] > 0) + (L.nsmall > 0);
+    const bool fork = fs && nk > 1;
+    if (fork && (e = cudaEventRecord(fs->fork, s)) != cudaSuccess) return e;
+    int branch = 0;
+    // the first kernel runs on s, each further one on its own branch
+    auto begin = [&](cudaStream_t& ks) -> cudaError_t {
+        ks = s;
+        if (!fork || branch == 0) return cudaSuccess;
+        ks = fs->aux[branch - 1];
+        return cudaStreamWaitEvent(ks, fs->fork, 0);
+    };
+    auto end = [&](cudaStream_t ks) -> cudaError_t {
+        cudaError_t r = cudaGetLastError();
+        if (r == cudaSuccess && fork && branch > 0) r = cudaEventRecord(fs->join[branch - 1], ks);
+        ++branch;
+        return r;
+    };
+    cudaStream_t ks;
     if (L.nlvl[0] > 0) {
+        if ((e = begin(ks)) != cudaSuccess) return e;
         SGIGA_COUNT_LAUNCH();
-        k_fd_level<Real, 16><<<L.nlvl[0], 256, 0, s>>>(P, L.lvl[0], forward, in, out, active);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_fd_level<Real, 16><<<L.nlvl[0], 256, fd_level_smem<Real, 16>(), ks>>>(P, L.lvl[0], forward, in, out, active);
+        if ((e = end(ks)) != cudaSuccess) return e;
     }
     if (L.nlvl[1] > 0) {
+        if ((e = begin(ks)) != cudaSuccess) return e;
         SGIGA_COUNT_LAUNCH();
-        k_fd_level<Real, 32><<<L.nlvl[1], 256, 0, s>>>(P, L.lvl[1], forward, in, out, active);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_fd_level<Real, 32><<<L.nlvl[1], 256, fd_level_smem<Real, 32>(), ks>>>(P, L.lvl[1], forward, in, out, active);
+        if ((e = end(ks)) != cudaSuccess) return e;
     }
     if (L.nlvl[2] > 0) {
+        if ((e = begin(ks)) != cudaSuccess) return e;
         SGIGA_COUNT_LAUNCH();
-        k_fd_level<Real, 64><<<L.nlvl[2], 256, 0, s>>>(P, L.lvl[2], forward, in, out, active);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_fd_level<Real, 64><<<L.nlvl[2], 256, fd_level_smem<Real, 64>(), ks>>>(P, L.lvl[2], forward, in, out, active);
+        if ((e = end(ks)) != cudaSuccess) return e;
     }
-    if (L.nsmall == 0) return cudaSuccess;
-    SGIGA_COUNT_LAUNCH();
-    k_fd_pass<Real><<<L.nsmall, 256, 0, s>>>(P, L.small, dir, forward, in, out, active);
-    return cudaGetLastError();
+    if (L.nsmall > 0) {
+        if ((e = begin(ks)) != cudaSuccess) return e;
+        SGIGA_COUNT_LAUNCH();
+        k_fd_pass<Real><<<L.nsmall, 256, 0, ks>>>(P, L.small, dir, forward, in, out, active);
+        if ((e = end(ks)) != cudaSuccess) return e;
+    }
+    for (int b = 1; fork && b < branch; ++b)
+        if ((e = cudaStreamWaitEvent(s, fs->join[b - 1], 0)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 template cudaError_t launch_fd_pass<double>(const DevPlan&, const FDLists&, int, int, const double*, double*,
-                                            const int*, cudaStream_t);
+                                            const int*, cudaStream_t, const FDStreams*);
 template cudaError_t launch_fd_pass<float>(const DevPlan&, const FDLists&, int, int, const float*, float*,
-                                           const int*, cudaStream_t);
+                                           const int*, cudaStream_t, const FDStreams*);
 
 // z[i] *= dinv[i] = 1 / sum_k lambda_{k, i_k} over every entry of the local layout.
 template <typename Real>

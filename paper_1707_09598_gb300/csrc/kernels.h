@@ -120,9 +120,20 @@ struct FDLists {
     const FDItem* lvl[3];
     int nlvl[3];
 };
+// Streams and events on which the kernels of one preconditioner pass (level
+// GEMMs of each output-tile width and the small items; they write disjoint
+// outputs) run as parallel branches forked from and joined to the caller's
+// stream (in a captured graph: parallel nodes).
+struct FDStreams {
+    cudaStream_t aux[3];
+    cudaEvent_t fork;
+    cudaEvent_t join[3];
+};
 template <typename Real>
 cudaError_t launch_fd_pass(const DevPlan& P, const FDLists& L, int dir, int forward, const Real* in, Real* out,
-                           const int* active, cudaStream_t s);
+                           const int* active, cudaStream_t s, const FDStreams* fs = nullptr);
+// shared-memory attributes of the preconditioner kernels (before their first launch)
+cudaError_t fd_prepare();
 template <typename Real>
 cudaError_t launch_fd_gather(const DevPlan& P, const Real* r, Real* loc, const int* active, cudaStream_t s);
 template <typename Real>

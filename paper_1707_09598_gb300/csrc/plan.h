@@ -97,6 +97,8 @@ struct sgiga_plan_s {
     bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
     bool solve_fp64 = false;    // MIXED_FP32 plan whose solve the autotuner found faster as plain FP64 PCG
     cudaStream_t own_stream = nullptr;   // capture/launch stream when the plan's stream is the legacy one
+    FDStreams fds{};                     // branches of a preconditioner pass's kernels
+    bool fds_ok = false;
     int* d_counter = nullptr;            // iteration counter of the captured loop
     double* d_eval_vals = nullptr;       // evaluation: basis values per (table, point)
     int* d_eval_first = nullptr;
@@ -251,7 +253,7 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     for (int k = 0; k < d; ++k) {
         Real* out = bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));     // split contractions accumulate
-        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 1, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 1, in, out, active, s, P->fds_ok ? &P->fds : nullptr));
         in = out;
         cur ^= 1;
     }
@@ -259,7 +261,7 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
     for (int k = 0; k < d; ++k) {
         Real* out = (k == d - 1) ? (loc ? loc : z) : bufs[cur];
         CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
-        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 0, in, out, active, s));
+        CUDA_TRY(launch_fd_pass<Real>(D, fd_lists(P, k), k, 0, in, out, active, s, P->fds_ok ? &P->fds : nullptr));
         in = out;
         cur ^= 1;
     }

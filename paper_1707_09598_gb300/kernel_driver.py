@@ -33,6 +33,7 @@ def main():
     ap.add_argument("--op", default="apply", choices=["apply", "apply_f32", "precond", "precond_f32", "rhs", "solve",
                                                       "eval", "solve_scaled", "solve_mixed"])
     ap.add_argument("--coef", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=1e-3, help="inner FP32 tolerance of the mixed solves")
     ap.add_argument("--host-loop", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--d", type=int, default=3)
@@ -40,6 +41,7 @@ def main():
     ap.add_argument("--w", type=int, default=10)
     ap.add_argument("--domain", default="unit", help="unit, annulus or perturbed (cube with a seeded cubic perturbation)")
     ap.add_argument("--tune", action="store_true", help="run the autotuner first")
+    ap.add_argument("--fd-split", default=None, help="ks,grouped: the preconditioner's item depth and layout")
     ap.add_argument("--tiling", default=None,
                     help="budget,qpcap,nthreads,prefetch: set the operator's decomposition (after --tune, if given)")
     a = ap.parse_args()
@@ -71,8 +73,11 @@ def main():
     if a.tiling:
         b, q, nt, pf = (int(v) for v in a.tiling.split(","))
         sgiga.sgiga_set_tiling(P.handle, b, q, nt, pf)
+    if a.fd_split:
+        ks, grp = (int(v) for v in a.fd_split.split(","))
+        sgiga.sgiga_set_precond_split(P.handle, ks, bool(grp))
     if a.op in ("solve_scaled", "solve_mixed"):
-        sgiga.sgiga_set_solver_options(P.handle, use_graph=not a.host_loop, inner_tol=1e-3, inner_max=100)
+        sgiga.sgiga_set_solver_options(P.handle, use_graph=not a.host_loop, inner_tol=a.inner_tol, inner_max=100)
     if a.op == "solve_scaled":
         phi = torch.zeros(P.info.ndof, dtype=torch.float32, device="cuda")
         sgiga.sgiga_net_features(P.handle, phi)
@@ -116,8 +121,12 @@ def main():
         op()
     e1.record(stream)
     torch.cuda.synchronize()
-    print("op=%s reps=%d mean_ms=%.4f ndof=%d nqp=%d ntiles=%d" %
-          (a.op, a.reps, e0.elapsed_time(e1) / a.reps, n, P.info.nqp, P.info.ntiles))
+    extra = ""
+    if a.op in ("solve_scaled", "solve_mixed", "solve"):
+        st, _ = sgiga.sgiga_solve(P.handle, 1e-8 if a.op != "solve" else 1e-12, 50, check=False)
+        extra = " outer=%d inner=%d max_rel_residual=%.3g" % (st.iterations, st.inner_iterations, st.max_rel_residual)
+    print("op=%s reps=%d mean_ms=%.4f ndof=%d nqp=%d ntiles=%d%s" %
+          (a.op, a.reps, e0.elapsed_time(e1) / a.reps, n, P.info.nqp, P.info.ntiles, extra))
     P.close()
 
 
