@@ -291,9 +291,10 @@ static void make_fd_items(sgiga_plan_s* P, int ks, bool grouped) {
             const long long ncol = g.fd_n / n;
             auto depth = [&](int j0) { return (int)std::min<long long>(n, j0 + ks); };
             if (n <= 64) {
-                for (long long c0 = 0; c0 < g.fd_n; c0 += 256) {
+                const int tc = fd_small_cols((int)n);
+                for (long long c0 = 0; c0 < ncol; c0 += tc) {
                     v.push_back(FDItem{(int)gi, FD_SMALL, 0, 0, c0, 0, (int)n});
-                    cost.push_back(std::min<long long>(256, g.fd_n - c0) * n);
+                    cost.push_back(std::min<long long>(tc, ncol - c0) * n * n);
                 }
             } else if (grouped) {
                 by_eig[g.eig[k]].push_back((int)gi);

@@ -74,7 +74,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256, 2)
 k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
           const Real* __restrict__ in, Real* __restrict__ out, const int* __restrict__ active) {
-    __shared__ double sm_raw[64 * 65];
+    __shared__ double sm_raw[6144];
     Real* sm = reinterpret_cast<Real*>(sm_raw);
     const FDItem it = items[blockIdx.x];
     const GridDesc& g = P.grids[it.grid];
@@ -94,20 +94,34 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
     const bool split = it.j0 > 0 || it.j1 < n;
 
     if (it.mode == FD_SMALL) {
+        // a tile of nc fibres: Mat (n x n) and the fibres (n x nc) staged in
+        // shared memory, each read from memory once, then Y = Mat X. With
+        // B = 1 a fibre is contiguous, so threads run along the fibre;
+        // otherwise neighbouring fibres are neighbours in memory, so threads
+        // run across fibres.
+        const long long rest = Ncol - it.c0;
+        const int nc = rest < fd_small_cols(n) ? (int)rest : fd_small_cols(n);
+        const int ms = n + 1, xs = nc + 1;
+        Real* Ms = sm;
+        Real* Xs = sm + n * ms;
         for (int l = threadIdx.x; l < n * n; l += blockDim.x) {
-            int i = l / n, j = l - i * n;
-            sm[i * 65 + j] = forward ? U[(long long)j * n + i] : U[(long long)i * n + j];
+            const int i = l / n, j = l - i * n;
+            Ms[i * ms + j] = forward ? U[(long long)j * n + i] : U[(long long)i * n + j];
+        }
+        const bool unit = B == 1;
+        for (int l = threadIdx.x; l < n * nc; l += blockDim.x) {
+            const int j = unit ? l % n : l / nc, cl = unit ? l / n : l % nc;
+            const long long col = it.c0 + cl, a = col / B, b = col - a * B;
+            Xs[j * xs + cl] = vin[a * n * B + (long long)j * B + b];
         }
         __syncthreads();
-        long long lin = it.c0 + threadIdx.x;
-        if (lin >= g.fd_n) return;
-        long long b = lin % B, r = lin / B;
-        int i = (int)(r % n);
-        long long a = r / n;
-        const Real* vp = vin + a * n * B + b;
-        Real acc = 0;
-        for (int j = 0; j < n; ++j) acc += sm[i * 65 + j] * vp[(long long)j * B];
-        vout[lin] = acc;
+        for (int l = threadIdx.x; l < n * nc; l += blockDim.x) {
+            const int i = unit ? l % n : l / nc, cl = unit ? l / n : l % nc;
+            Real acc = 0;
+            for (int j = 0; j < n; ++j) acc += Ms[i * ms + j] * Xs[j * xs + cl];
+            const long long col = it.c0 + cl, a = col / B, b = col - a * B;
+            vout[a * n * B + (long long)i * B + b] = acc;
+        }
         return;
     }
     if (it.mode == FD_ROWS) {

@@ -121,11 +121,23 @@ struct ConvTile {
 };
 
 // Work item of the batched mode product of the preconditioner.
-//   FD_SMALL: grid = piece, c0 = first output of the piece's tensor (256 per item)
+//   FD_SMALL: grid = piece, c0 = first column (fibre a*B + b) of a tile of
+//             fd_small_cols(n) columns
 //   FD_ROWS / FD_TILE: grid = piece, rows from i0, columns from c0 (a*B + b)
 //   FD_LEVEL: grid = level segment (FDSeg), an output tile at rows i0,
 //             columns c0 of the segment, contraction range [j0, j1)
 enum { FD_SMALL = 0, FD_ROWS = 1, FD_TILE = 2, FD_LEVEL = 3 };
+
+// Columns per FD_SMALL item for a direction of n <= 64 functions: the n x n
+// matrix and an n x cols tile of fibres (rows padded by one) fill at most 48 KB
+// of FP64 shared memory (6144 doubles); at most 256.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int fd_small_cols(int n) {
+    const int c = (6144 - n * (n + 1)) / (n + 1) - 1;
+    return c < 256 ? (c < 1 ? 1 : c) : 256;
+}
 struct FDItem {
     int grid;
     int mode;

@@ -223,8 +223,12 @@ def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
     systems (the GPU's matrix-free operator from FP64 metric planes, the
     oracle's assembled FP64 matrix) can differ by that much, so for gamma = 3
     the bound is that sensitivity, and the solve target the FP64 residual
-    floor 1e-9; gamma = 1, 2 keep the FP64 and mixed targets."""
-    solve_tol = 1e-12
+    floor 1e-9; gamma = 1, 2 keep the FP64 and mixed targets. The FP64 solves
+    of gamma = 1, 2 stop at a relative residual of 1e-13, so that the
+    gradients near the singular corner (ten times the values' bound) measure
+    the discretisation, not where CG stopped (at 1e-12 a change of the
+    preconditioner's summation order moved them by 4e-10)."""
+    solve_tol = 1e-13 if precision == "fp64" else 1e-12
     if gamma == 3:
         sens = dict(np.loadtxt(os.path.join(GOLD, "lshape_p2_w11_sensitivity.txt")))
         tol, solve_tol = max(tol, sens[3.0]), 1e-9
@@ -249,4 +253,6 @@ def test_full_size_against_stored_oracle_values(sg, gamma, precision, tol):
         for c in range(2):
             gcomb = torch.zeros(npts, dtype=torch.float64, device="cuda")
             sg.sgiga_combine(P.handle, gc[c * ng * npts:(c + 1) * ng * npts], npts, gcomb)
+            print("gamma %d %s: combined gradient %d rel. L2 vs oracle %.3e" %
+                  (gamma, precision, c, _rel(gcomb.cpu().numpy(), data[:, 4 + c])))
             assert _rel(gcomb.cpu().numpy(), data[:, 4 + c]) < 10 * tol
