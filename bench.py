@@ -505,7 +505,8 @@ def train_learned(W, args):
            "training": {"seconds": train_s, "pairs": tr.pairs, "samples": tr.samples, "adam_steps": tr.steps,
                         "loss_fd": tr.loss_fd, "loss_initial": tr.loss_initial,
                         "loss_epochs": [tr.loss_epoch[e] for e in range(min(12, 32))],
-                        "best_epoch": tr.best_epoch, "log_s_range": [tr.logs_min, tr.logs_max]}}
+                        "best_epoch": tr.best_epoch, "log_s_range": [tr.logs_min, tr.logs_max],
+                        "validation_inner_iterations": {"initial": tr.val_iters_initial, "kept": tr.val_iters_best}}}
     tuning = {"best": {"smem_budget": tune.budget[tune.best], "qp_cap": tune.qpcap[tune.best],
                        "threads": tune.nthreads[tune.best], "l2_prefetch_bytes_per_plane": tune.best_prefetch,
                        "apply_f32_ms": tune.best_ms, "ntiles": tune.ntiles},

@@ -448,12 +448,15 @@ int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam
  * name fast solvers used as preconditioners as future work, Sec. 5).
  *
  *   M(r) = S * FD(S * r)   (elementwise products, FD = sgiga_precond_f32),
- *   S = exp(N(phi)),  phi_i = log c_i,
+ *   S = exp(4 tanh((N(phi) - phi / 2) / 4)),  phi_i = log c_i,
  *   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
  * c_i being the local effective coefficient of DoF i: the R_i-weighted mean of
  * the trace of the Galerkin metric G_q = w_q |det J_q| a(x_q) (J_q^T J_q)^{-1}
  * relative to the parametric Laplacian (G_q = w_q I), which FD inverts
- * exactly. N: three 3^d convolutions over each component's DoF tensor (zero
+ * exactly. The network corrects the network-free scaling S = c^(-1/2) (the
+ * inverse square root of the local coefficient, exact for a constant
+ * coefficient on an axis-aligned box up to the bound), which its untrained
+ * state (N near 0) reproduces; the tanh bounds |log S| by 4. N: three 3^d convolutions over each component's DoF tensor (zero
  * padding), 1 -> 32 -> 32 -> 1 channels, ReLU after the first two; BF16
  * weights with an FP32 master copy, FP32 accumulation. S depends only on the
  * operator, so M is a fixed symmetric positive definite operator: the
@@ -482,11 +485,15 @@ typedef struct {
     double loss_fd;          /* the same with S = 1 (plain FD) */
     double loss_epoch[32];   /* per epoch (the first 32) */
     double logs_min, logs_max; /* range of log S after training */
-    int best_epoch;          /* epoch whose parameters were kept */
+    int best_epoch;          /* epoch whose parameters were kept (-1: the initial ones) */
+    int val_iters_initial;   /* inner iterations of the validation solve at the initial parameters
+                                (1000 more if it did not converge) */
+    int val_iters_best;      /* the same at the kept parameters */
 } sgiga_train_stats;
 
 /* Allocate the network and initialise it (seeded Kaiming-uniform; the last
- * layer scaled by 0.05 so that the untrained S is close to 1, M close to FD). */
+ * layer scaled by 0.05 so that the untrained N is close to 0 and S close to
+ * c^(-1/2)). */
 int sgiga_net_init(sgiga_plan_t plan, unsigned seed);
 /* Number of parameters (a negative status if there is no network). Layout of
  * the FP32 vector: W1 [32][1][T], b1 [32], W2 [32][32][T], b2 [32], W3 [1][32][T],
@@ -515,12 +522,14 @@ int sgiga_net_set_scaling(sgiga_plan_t plan, const float* S);
 int sgiga_net_loss_grad(sgiga_plan_t plan, const float* r, const float* e, double* loss, float* grad);
 /* Record (residual, error) pairs from the plan's own FD-preconditioned FP64 CG
  * on seeded random right-hand sides and train N by Adam on the loss above,
- * back-propagated through S = exp(N(phi)). In a recorded sample only the
+ * back-propagated through S (above). In a recorded sample only the
  * components whose residual was still above 1e-6 of their right-hand side
  * count (a converged component's recorded error is rounding noise of two
- * solves). The parameters of the epoch with the lowest mean loss are kept
- * (the initial ones if no epoch improves on them). Overwrites the plan's load
- * vector and solution. */
+ * solves). Kept: the parameters after an epoch (or the initial ones) with
+ * which the plan's own solve (sgiga_solve to 1e-8 with the current solver
+ * options) of a validation right-hand side held out of the pairs
+ * (b = K FD(xi), own seed) needs the fewest inner FP32 iterations, the
+ * earliest among equals. Overwrites the plan's load vector and solution. */
 int sgiga_train_net(sgiga_plan_t plan, const sgiga_train_cfg* cfg, sgiga_train_stats* stats /* may be NULL */);
 /* Checkpoint: magic "SGIGANET", version 2, taps, nparams, Adam step, then the
  * FP32 parameters and both Adam moments. */

@@ -16,7 +16,9 @@ operator the fast-diagonalisation preconditioner inverts. The network input
 is log c_i.
 
 Scaled preconditioner. With a positive scaling S (one value per DoF, from the
-network's output y as S = exp(4 tanh(y / 4)), a smooth bound |log S| <= 4),
+network's output y and the feature phi = log c as
+S = exp(4 tanh((y - phi / 2) / 4)): the network corrects the network-free
+scaling c^(-1/2), under a smooth bound |log S| <= 4),
 M(r) = S * FD(S * r), elementwise products: symmetric positive definite
 whenever FD is.
 
@@ -32,9 +34,11 @@ import numpy as np
 from . import fd
 
 
-def scaling_from_output(y):
-    """S = exp(4 tanh(y / 4)) of the network output y."""
-    return np.exp(4.0 * np.tanh(np.asarray(y, dtype=np.float64) / 4.0))
+def scaling_from_output(y, phi=0.0):
+    """S = exp(4 tanh((y - phi / 2) / 4)) of the network output y at the
+    feature phi = log c."""
+    u = np.asarray(y, dtype=np.float64) - 0.5 * np.asarray(phi, dtype=np.float64)
+    return np.exp(4.0 * np.tanh(u / 4.0))
 
 
 def features(comp, diffusion=None):

@@ -189,7 +189,8 @@ cudaError_t launch_wgrad_out(const DevPlan& P, const float* dy, const void* A, f
 cudaError_t launch_arrange_mid(const void* W, int T, void* Wf, void* Wb, cudaStream_t s);
 cudaError_t launch_fill(float* x, float v, long long n, cudaStream_t s);
 cudaError_t launch_log_ratio(const double* num, const double* den, float* out, long long n, cudaStream_t s);
-cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s);
+cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, const float* phi, int* ok, float* S,
+                               cudaStream_t s);
 cudaError_t launch_mul_active(const DevPlan& P, const float* S, const float* in, float* out, const int* active,
                               cudaStream_t s);
 cudaError_t launch_pair_residual(const DevPlan& P, const float* S, const float* z1, const float* e, float* res,
@@ -199,7 +200,8 @@ cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res
 cudaError_t launch_pair_mask(int ng, const double* rr, const double* bb, double thr2, int* mask, cudaStream_t s);
 cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delta, const float* z1, const float* r,
                              const float* z2, float weight, float* dls, cudaStream_t s);
-cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s);
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, const float* phi,
+                               cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, const int* wmap, int n, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);
 cudaError_t launch_f2bf(const float* p, const int* wmap, void* wb, int n, cudaStream_t s);

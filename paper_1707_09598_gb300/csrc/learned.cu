@@ -5,7 +5,8 @@
 // kernels), checkpoints, and the C ABI entry points.
 //
 // Preconditioner: M(r) = S * FD(S * r) (elementwise products),
-// S = exp(4 tanh(N(phi) / 4)) (a smooth bound |log S| <= 4),
+// S = exp(4 tanh((N(phi) - phi / 2) / 4)) (the network corrects the
+// network-free scaling c^(-1/2); a smooth bound |log S| <= 4),
 // phi_i = log c_i with c_i the local effective coefficient of DoF i,
 //   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
 // the R_i-weighted mean of the trace of the Galerkin metric G_q relative to the
@@ -54,6 +55,7 @@ struct Net {
     bool s_stale = true;              // S must be recomputed from the network
     bool s_override = false;          // S was set by the caller (no network evaluation)
     float* data = nullptr;            // training pairs [S][2][N]
+    double* bval = nullptr;           // validation right-hand side
     int nsamples = 0, capacity = 0;
     std::vector<void*> allocs;
 };
@@ -221,7 +223,7 @@ static int net_scaling(sgiga_plan_s* P) {
     if ((rc = net_features(P))) return rc;
     CUDA_TRY(launch_copy<float>(n->A0, n->feat, n->N, P->stream));
     if ((rc = net_forward(P))) return rc;
-    CUDA_TRY(launch_exp_scaling(P->dp, n->Y, n->ok, n->S, P->stream));
+    CUDA_TRY(launch_exp_scaling(P->dp, n->Y, n->feat, n->ok, n->S, P->stream));
     return SGIGA_OK;
 }
 
@@ -444,6 +446,22 @@ int sgiga_net_loss_grad(sgiga_plan_t P, const float* r, const float* e, double* 
     return SGIGA_OK;
 }
 
+// Total inner FP32 flexible-CG iterations of the plan's own solve (FP64
+// refinement to a relative residual of 1e-8, the plan's inner tolerance) with
+// the network's current scaling on the validation right-hand side; 1000 more
+// when it does not converge in 50 refinement steps.
+static int validation_iters(sgiga_plan_s* P, const double* bval, int* iters) {
+    Net* n = P->net;
+    CUDA_TRY(cudaMemcpyAsync(P->d_b, bval, (size_t)n->N * 8, cudaMemcpyDeviceToDevice, P->stream));
+    n->s_stale = true;
+    n->s_override = false;
+    sgiga_solve_stats st{};
+    const int rc = sgiga_solve(P, 1e-8, 50, &st);
+    if (rc != SGIGA_OK && rc != SGIGA_ERR_NOT_CONVERGED) return rc;
+    *iters = st.inner_iterations + (rc == SGIGA_OK ? 0 : 1000);
+    return SGIGA_OK;
+}
+
 int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stats* stats) {
     if (!P || !cfg) return fail(SGIGA_ERR_ARG, "null argument");
     if (!P->net_ready || !P->net) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
@@ -501,6 +519,16 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         if (nact < 0) { rc = nact; break; }
         ++nrhs;
     }
+    // validation right-hand side, held out of the pairs: b = K FD(xi) with its
+    // own seed
+    if (rc == SGIGA_OK && !n->bval) rc = nalloc(n, (void**)&n->bval, (size_t)N * 8);
+    if (rc == SGIGA_OK) {
+        std::mt19937_64 vrng(cfg->seed ^ 0x5DEECE66DULL);
+        for (long long i = 0; i < N; ++i) hb[i] = gauss(vrng);
+        if (cudaMemcpy(P->d_b, hb.data(), N * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = SGIGA_ERR_CUDA;
+        if (rc == SGIGA_OK) rc = precond_fd<double>(P, P->d_b, P->d_z, nullptr, P->d_t1, P->d_t2);
+        if (rc == SGIGA_OK) rc = apply_op(P, P->d_z, n->bval, nullptr);
+    }
     P->cfg.precond = saved_precond;
     cudaFree(xstar);
     if (rc) return rc;
@@ -508,8 +536,10 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     // 2. training: minibatches of `batch` samples, one network evaluation and
     // one Adam step per minibatch; the learning rate ramps up linearly over the
     // first 50 steps (Adam's first steps move every weight by about lr in the
-    // same direction); the parameters of the epoch with the lowest mean loss
-    // are kept
+    // same direction). Kept: the parameters (after an epoch, or the initial
+    // ones) with which the plan's solve of the validation right-hand side
+    // needs the fewest inner iterations, the earliest among equals: a lower
+    // loss on the pairs alone does not mean fewer CG iterations
     const int B = cfg->batch > 0 ? cfg->batch : 2;
     n->s_override = false;
     std::vector<int> order(n->nsamples);
@@ -518,8 +548,10 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     CUDA_TRY(launch_fill(n->S, 1.0f, N, s));                  // S = 1: plain FD
     if ((rc = dataset_loss(P, &loss_fd))) return rc;
     if ((rc = net_scaling(P)) || (rc = dataset_loss(P, &loss_init))) return rc;
+    int val_init = 0;
+    if ((rc = validation_iters(P, n->bval, &val_init))) return rc;
     double first = 0.0, last = 0.0, best = loss_init;
-    int best_epoch = -1;
+    int best_epoch = -1, best_val = val_init;
     std::vector<double> ep_loss;
     std::vector<float> best_p(n->np);
     CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
@@ -536,7 +568,7 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
                 if ((rc = pair_loss_grad(P, r, r + N, n->masks + (size_t)order[k] * ng, n->dY, 1.0f / nb)))
                     return rc;
             }
-            CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, s));    // d/dlog S -> d/dy
+            CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, n->feat, s));    // d/dlog S -> d/dy
             if ((rc = net_backward(P))) return rc;
             n->step++;
             steps++;
@@ -553,10 +585,12 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         last = mean;
         ep_loss.push_back(mean);
         // the epoch's mean loss belongs to parameters between the epoch's first
-        // and last step; the parameters after the epoch are kept if it is the
-        // best so far (the initial parameters compete with their own loss)
-        if (mean < best) {
+        // and last step; the validation solve uses the parameters after it
+        int val = 0;
+        if ((rc = net_scaling(P)) || (rc = validation_iters(P, n->bval, &val))) return rc;
+        if (val < best_val) {
             best = mean;
+            best_val = val;
             best_epoch = ep;
             CUDA_TRY(cudaMemcpy(best_p.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost));
         }
@@ -587,6 +621,8 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
         stats->logs_min = lo;
         stats->logs_max = hi;
         stats->best_epoch = best_epoch;
+        stats->val_iters_initial = val_init;
+        stats->val_iters_best = best_val;
     }
     return SGIGA_OK;
 }

@@ -40,20 +40,25 @@ __global__ void k_finite(DevPlan P, const float* __restrict__ y, int* __restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAnd(&ok[c.grid], 0);
 }
 
-// log S = L tanh(y / L) with L = SGIGA_LOGS_MAX: a smooth bound on the
-// scaling (S in [e^-L, e^L]) that keeps a training step from driving one
-// component's preconditioner far from FD; the scalings that matter here have
-// |log S| below 2.
+// log S = L tanh((y + A phi) / L) with L = SGIGA_LOGS_MAX and A =
+// SGIGA_LOGS_SKIP: the network output y corrects the network-free scaling
+// S = c^(-1/2) (phi = log c), which an untrained network (y near 0) starts
+// from; the tanh is a smooth bound on the scaling (S in [e^-L, e^L]) that
+// keeps a training step from driving one component's preconditioner far from
+// FD; the scalings that matter here have |log S| below 2.
 #define SGIGA_LOGS_MAX 4.0f
+#define SGIGA_LOGS_SKIP (-0.5f)
 
-// S = exp(L tanh(y / L)) where the component's y is finite, else 1 (plain FD there)
-__global__ void k_exp_scaling(DevPlan P, const float* __restrict__ y, const int* __restrict__ ok,
-                              float* __restrict__ S) {
+// S = exp(L tanh((y + A phi) / L)) where the component's y is finite, else 1
+// (plain FD there)
+__global__ void k_exp_scaling(DevPlan P, const float* __restrict__ y, const float* __restrict__ phi,
+                              const int* __restrict__ ok, float* __restrict__ S) {
     const Chunk c = P.chunks[blockIdx.x];
     const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
-        S[k] = use ? expf(SGIGA_LOGS_MAX * tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX))) : 1.0f;
+        S[k] = use ? expf(SGIGA_LOGS_MAX * tanhf((y[k] + SGIGA_LOGS_SKIP * phi[k]) * (1.0f / SGIGA_LOGS_MAX)))
+                   : 1.0f;
     }
 }
 
@@ -148,12 +153,12 @@ __global__ void k_pair_grad(long long n, const float* __restrict__ S, const floa
 // chain rule from d/dlog S to d/dy through log S = L tanh(y / L); no gradient
 // through a component that fell back to S = 1
 __global__ void k_mask_scaled(DevPlan P, float* __restrict__ dy, const int* __restrict__ ok,
-                              const float* __restrict__ y) {
+                              const float* __restrict__ y, const float* __restrict__ phi) {
     const Chunk c = P.chunks[blockIdx.x];
     const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
-        const float t = tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX));
+        const float t = tanhf((y[k] + SGIGA_LOGS_SKIP * phi[k]) * (1.0f / SGIGA_LOGS_MAX));
         dy[k] = use ? dy[k] * (1.0f - t * t) : 0.0f;
     }
 }
@@ -200,7 +205,8 @@ cudaError_t launch_log_ratio(const double* num, const double* den, float* out, l
     return cudaGetLastError();
 }
 
-cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float* S, cudaStream_t s) {
+cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, const float* phi, int* ok, float* S,
+                               cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(ok, 0xff, sizeof(int) * P.ncomps, s);   // all ones = finite
     if (e != cudaSuccess) return e;
@@ -208,7 +214,7 @@ cudaError_t launch_exp_scaling(const DevPlan& P, const float* y, int* ok, float*
     k_finite<<<P.nchunks, 256, 0, s>>>(P, y, ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     SGIGA_COUNT_LAUNCH();
-    k_exp_scaling<<<P.nchunks, 256, 0, s>>>(P, y, ok, S);
+    k_exp_scaling<<<P.nchunks, 256, 0, s>>>(P, y, phi, ok, S);
     return cudaGetLastError();
 }
 
@@ -255,10 +261,11 @@ cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delt
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s) {
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, const float* phi,
+                               cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_mask_scaled<<<P.nchunks, 256, 0, s>>>(P, dy, ok, y);
+    k_mask_scaled<<<P.nchunks, 256, 0, s>>>(P, dy, ok, y, phi);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,7 @@ class sgiga_train_stats(ctypes.Structure):
                 ("loss_first_epoch", ctypes.c_double), ("loss_last_epoch", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("loss_initial", ctypes.c_double), ("loss_fd", ctypes.c_double),
                 ("loss_epoch", ctypes.c_double * 32), ("logs_min", ctypes.c_double), ("logs_max", ctypes.c_double),
-                ("best_epoch", ctypes.c_int)]
+                ("best_epoch", ctypes.c_int), ("val_iters_initial", ctypes.c_int), ("val_iters_best", ctypes.c_int)]
 
 
 class sgiga_tune_result(ctypes.Structure):

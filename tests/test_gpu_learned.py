@@ -214,6 +214,27 @@ def test_features_against_oracle(sg):
             assert np.max(np.abs(got - ref)) < 2e-6, tuple(g.levels)
 
 
+def test_scaling_from_the_network_against_oracle(sg):
+    """S on the device from the network output y = N(phi) and the feature
+    phi: the oracle's S = exp(4 tanh((y - phi / 2) / 4)) of the same y and
+    phi, to FP32 rounding; with the untrained network (last layer scaled by
+    0.05) log S stays near -phi / 2, the network-free scaling."""
+    P, geom, a = _patch_plan(sg, 4, precision="mixed", precond="learned")
+    with P:
+        n = P.info.ndof
+        sg.sgiga_net_init(P.handle, 3)
+        phi = torch.zeros(n, dtype=torch.float32, device="cuda")
+        sg.sgiga_net_features(P.handle, phi)
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        sg.sgiga_net_forward(P.handle, phi, y)
+        S = torch.zeros(n, dtype=torch.float32, device="cuda")
+        sg.sgiga_net_scaling(P.handle, S)
+        ph, yh, Sh = (t.cpu().numpy().astype(np.float64) for t in (phi, y, S))
+    ref = learned.scaling_from_output(yh, ph)
+    assert np.max(np.abs(Sh / ref - 1.0)) < 2e-6
+    assert np.max(np.abs(np.log(Sh) + 0.5 * ph)) < 0.5
+
+
 def test_loss_and_gradient_against_oracle(sg):
     """Training loss of one sample and its gradient with respect to log S (FP32
     preconditioner on the device) against the oracle's FP64 definition, at a
@@ -263,7 +284,10 @@ def test_learned_scaling_gains_over_fd(sg, tmp_path):
         sg.sgiga_net_init(P.handle, 11)
         st = sg.sgiga_train_net(P.handle, target_pairs=3000, max_iter_record=25, epochs=8, lr=1e-3, seed=100,
                                 batch=2)
-        assert st.pairs >= 3000 and st.loss_last_epoch < 0.5 * st.loss_first_epoch
+        # training lowers the loss below that of its starting point (the
+        # network-free scaling, which the untrained network reproduces) and far
+        # below plain FD's
+        assert st.pairs >= 3000 and st.loss_last_epoch < st.loss_initial and st.loss_last_epoch < 0.2 * st.loss_fd
         sg.sgiga_set_rhs_builtin(P.handle, "one")
         s_l, ms_l = _timed_solve(sg, P, 1e-8)
         assert s_l.fallback == 0
@@ -284,9 +308,10 @@ def test_learned_scaling_gains_over_fd(sg, tmp_path):
         s_f, ms_f = _timed_solve(sg, P2, 1e-8)
         u_f = np.zeros(P2.info.ndof)
         sg.sgiga_get_solution(P2.handle, u_f)
-    print("inner iterations / ms: learned %d / %.2f, c^-1/2 scaling %d / %.2f, FD %d / %.2f; loss %.3f -> %.3f"
-          % (s_l.inner_iterations, ms_l, s_h.inner_iterations, ms_h, s_f.inner_iterations, ms_f,
-             st.loss_first_epoch, st.loss_last_epoch))
+    print("inner iterations / ms: learned %d / %.2f, c^-1/2 scaling %d / %.2f, FD %d / %.2f; loss FD %.4f, "
+          "initial %.4f, epochs %.4f -> %.4f" % (s_l.inner_iterations, ms_l, s_h.inner_iterations, ms_h,
+                                                s_f.inner_iterations, ms_f, st.loss_fd, st.loss_initial,
+                                                st.loss_first_epoch, st.loss_last_epoch))
     assert _rel(u_l, u_f) < 1e-7
     assert s_l.inner_iterations < s_f.inner_iterations
     assert ms_l < ms_f

@@ -91,3 +91,17 @@ def test_scaling_bound():
     S = learned.scaling_from_output(y)
     assert np.all(np.diff(S) > 0) and S.min() >= np.exp(-4.0) and S.max() <= np.exp(4.0)
     np.testing.assert_allclose(learned.scaling_from_output([1e-3, -2e-3]), np.exp([1e-3, -2e-3]), rtol=1e-9)
+
+
+def test_untrained_scaling_is_the_inverse_square_root_of_the_coefficient():
+    """With the network output 0, S = exp(4 tanh(-log(c) / 8)): c^(-1/2) up to
+    the bound's cubic term (|u|^3 / 48 in log S for u = log(c) / 2), and
+    exactly 1 at c = 1; on the unit cube with a constant coefficient a (c = a,
+    by the features' pin) M = S FD S = FD / a to that order, the inverse of
+    a K."""
+    c = np.array([0.25, 0.8, 1.0, 1.3, 4.0])
+    S = learned.scaling_from_output(np.zeros_like(c), np.log(c))
+    u = 0.5 * np.log(c)
+    np.testing.assert_allclose(np.log(S), -u, atol=np.abs(u).max() ** 3 / 40)
+    assert S[2] == 1.0
+    assert np.all(np.diff(S) < 0)
