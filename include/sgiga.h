@@ -448,15 +448,15 @@ int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam
  * name fast solvers used as preconditioners as future work, Sec. 5).
  *
  *   M(r) = S * FD(S * r)   (elementwise products, FD = sgiga_precond_f32),
- *   S = exp(4 tanh((N(phi) - phi / 2) / 4)),  phi_i = log c_i,
+ *   S = exp(-phi / 2 + 4 tanh(N(phi) / 4)),  phi_i = log c_i,
  *   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
  * c_i being the local effective coefficient of DoF i: the R_i-weighted mean of
  * the trace of the Galerkin metric G_q = w_q |det J_q| a(x_q) (J_q^T J_q)^{-1}
  * relative to the parametric Laplacian (G_q = w_q I), which FD inverts
  * exactly. The network corrects the network-free scaling S = c^(-1/2) (the
  * inverse square root of the local coefficient, exact for a constant
- * coefficient on an axis-aligned box up to the bound), which its untrained
- * state (N near 0) reproduces; the tanh bounds |log S| by 4. N: three 3^d convolutions over each component's DoF tensor (zero
+ * coefficient on an axis-aligned box), which its untrained state (N = 0)
+ * gives; the tanh bounds the correction by a factor e^(+-4). N: three 3^d convolutions over each component's DoF tensor (zero
  * padding), 1 -> 32 -> 32 -> 1 channels, ReLU after the first two; BF16
  * weights with an FP32 master copy, FP32 accumulation. S depends only on the
  * operator, so M is a fixed symmetric positive definite operator: the
@@ -492,8 +492,7 @@ typedef struct {
 } sgiga_train_stats;
 
 /* Allocate the network and initialise it (seeded Kaiming-uniform; the last
- * layer scaled by 0.05 so that the untrained N is close to 0 and S close to
- * c^(-1/2)). */
+ * layer zero, so that the untrained N is 0 and S = c^(-1/2)). */
 int sgiga_net_init(sgiga_plan_t plan, unsigned seed);
 /* Number of parameters (a negative status if there is no network). Layout of
  * the FP32 vector: W1 [32][1][T], b1 [32], W2 [32][32][T], b2 [32], W3 [1][32][T],

@@ -17,8 +17,8 @@ is log c_i.
 
 Scaled preconditioner. With a positive scaling S (one value per DoF, from the
 network's output y and the feature phi = log c as
-S = exp(4 tanh((y - phi / 2) / 4)): the network corrects the network-free
-scaling c^(-1/2), under a smooth bound |log S| <= 4),
+S = exp(-phi / 2 + 4 tanh(y / 4)): the network corrects the network-free
+scaling c^(-1/2) by a factor within e^(+-4)),
 M(r) = S * FD(S * r), elementwise products: symmetric positive definite
 whenever FD is.
 
@@ -35,10 +35,10 @@ from . import fd
 
 
 def scaling_from_output(y, phi=0.0):
-    """S = exp(4 tanh((y - phi / 2) / 4)) of the network output y at the
+    """S = exp(-phi / 2 + 4 tanh(y / 4)) of the network output y at the
     feature phi = log c."""
-    u = np.asarray(y, dtype=np.float64) - 0.5 * np.asarray(phi, dtype=np.float64)
-    return np.exp(4.0 * np.tanh(u / 4.0))
+    y = np.asarray(y, dtype=np.float64)
+    return np.exp(-0.5 * np.asarray(phi, dtype=np.float64) + 4.0 * np.tanh(y / 4.0))
 
 
 def features(comp, diffusion=None):

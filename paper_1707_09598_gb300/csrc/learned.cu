@@ -5,8 +5,8 @@
 // kernels), checkpoints, and the C ABI entry points.
 //
 // Preconditioner: M(r) = S * FD(S * r) (elementwise products),
-// S = exp(4 tanh((N(phi) - phi / 2) / 4)) (the network corrects the
-// network-free scaling c^(-1/2); a smooth bound |log S| <= 4),
+// S = exp(-phi / 2 + 4 tanh(N(phi) / 4)) (the network corrects the
+// network-free scaling c^(-1/2) by a factor within [e^-4, e^4]),
 // phi_i = log c_i with c_i the local effective coefficient of DoF i,
 //   c_i = sum_q R_i(xi_q) tr(G_q) / (d sum_q R_i(xi_q) w_q),
 // the R_i-weighted mean of the trace of the Galerkin metric G_q relative to the
@@ -336,10 +336,10 @@ int sgiga_net_init(sgiga_plan_t P, unsigned seed) {
     std::mt19937_64 rng(seed);
     std::vector<float> h(n->np, 0.0f);
     for (int l = 0; l < 3; ++l) {
-        // Kaiming-uniform for ReLU layers; the last layer starts small so that
-        // the untrained S is close to 1 (M close to FD)
+        // Kaiming-uniform for ReLU layers; the last layer starts at zero, so
+        // that the untrained N is 0 and S the network-free scaling c^(-1/2)
         const double fan = (double)n->cin[l] * n->T;
-        const double b = std::sqrt(6.0 / fan) * (l == 2 ? 0.05 : 1.0);
+        const double b = std::sqrt(6.0 / fan) * (l == 2 ? 0.0 : 1.0);
         std::uniform_real_distribution<double> U(-b, b);
         long long w = (long long)n->cout[l] * n->cin[l] * n->T;
         for (long long i = 0; i < w; ++i) h[n->oW[l] + i] = (float)U(rng);

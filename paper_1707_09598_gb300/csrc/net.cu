@@ -40,16 +40,16 @@ __global__ void k_finite(DevPlan P, const float* __restrict__ y, int* __restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAnd(&ok[c.grid], 0);
 }
 
-// log S = L tanh((y + A phi) / L) with L = SGIGA_LOGS_MAX and A =
-// SGIGA_LOGS_SKIP: the network output y corrects the network-free scaling
-// S = c^(-1/2) (phi = log c), which an untrained network (y near 0) starts
-// from; the tanh is a smooth bound on the scaling (S in [e^-L, e^L]) that
-// keeps a training step from driving one component's preconditioner far from
-// FD; the scalings that matter here have |log S| below 2.
+// log S = A phi + L tanh(y / L) with A = SGIGA_LOGS_SKIP and L =
+// SGIGA_LOGS_MAX: the network output y corrects the network-free scaling
+// S = c^(-1/2) (phi = log c), which the untrained network (y = 0) gives
+// exactly; the tanh is a smooth bound on the correction (a factor within
+// [e^-L, e^L]) that keeps a training step from driving one component's
+// preconditioner far from it.
 #define SGIGA_LOGS_MAX 4.0f
 #define SGIGA_LOGS_SKIP (-0.5f)
 
-// S = exp(L tanh((y + A phi) / L)) where the component's y is finite, else 1
+// S = exp(A phi + L tanh(y / L)) where the component's y is finite, else 1
 // (plain FD there)
 __global__ void k_exp_scaling(DevPlan P, const float* __restrict__ y, const float* __restrict__ phi,
                               const int* __restrict__ ok, float* __restrict__ S) {
@@ -57,8 +57,7 @@ __global__ void k_exp_scaling(DevPlan P, const float* __restrict__ y, const floa
     const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
-        S[k] = use ? expf(SGIGA_LOGS_MAX * tanhf((y[k] + SGIGA_LOGS_SKIP * phi[k]) * (1.0f / SGIGA_LOGS_MAX)))
-                   : 1.0f;
+        S[k] = use ? expf(SGIGA_LOGS_SKIP * phi[k] + SGIGA_LOGS_MAX * tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX))) : 1.0f;
     }
 }
 
@@ -158,7 +157,8 @@ __global__ void k_mask_scaled(DevPlan P, float* __restrict__ dy, const int* __re
     const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
-        const float t = tanhf((y[k] + SGIGA_LOGS_SKIP * phi[k]) * (1.0f / SGIGA_LOGS_MAX));
+        const float t = tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX));   // dlog S / dy = 1 - t^2
+        (void)phi;
         dy[k] = use ? dy[k] * (1.0f - t * t) : 0.0f;
     }
 }

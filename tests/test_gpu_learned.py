@@ -168,6 +168,13 @@ def test_network_kernels_against_oracle(sg, d, p, w):
     2^-8 relative, in a few entries) and FP32 accumulation order."""
     with sg.Plan(d, p, w, precision="mixed", precond="learned") as P:
         sg.sgiga_net_init(P.handle, 7)
+        # the initial last layer is zero: give it random weights so that every
+        # layer's forward and backward paths are exercised
+        params = sg.sgiga_net_get_params(P.handle)
+        T = 3 ** d
+        nlast = 32 * T + 1
+        params[-nlast:] = np.random.default_rng(8).uniform(-0.1, 0.1, nlast).astype(np.float32)
+        sg.sgiga_net_set_params(P.handle, params)
         params = sg.sgiga_net_get_params(P.handle).astype(np.float64)
         npar = params.size
         # round weights (not biases) as the kernels do
@@ -216,9 +223,10 @@ def test_features_against_oracle(sg):
 
 def test_scaling_from_the_network_against_oracle(sg):
     """S on the device from the network output y = N(phi) and the feature
-    phi: the oracle's S = exp(4 tanh((y - phi / 2) / 4)) of the same y and
-    phi, to FP32 rounding; with the untrained network (last layer scaled by
-    0.05) log S stays near -phi / 2, the network-free scaling."""
+    phi: the oracle's S = exp(-phi / 2 + 4 tanh(y / 4)) of the same y and
+    phi, to FP32 rounding; the untrained network (last layer zero) gives the
+    network-free scaling c^(-1/2); after one set of random parameters the
+    device S still follows the oracle's formula."""
     P, geom, a = _patch_plan(sg, 4, precision="mixed", precond="learned")
     with P:
         n = P.info.ndof
@@ -230,9 +238,17 @@ def test_scaling_from_the_network_against_oracle(sg):
         S = torch.zeros(n, dtype=torch.float32, device="cuda")
         sg.sgiga_net_scaling(P.handle, S)
         ph, yh, Sh = (t.cpu().numpy().astype(np.float64) for t in (phi, y, S))
-    ref = learned.scaling_from_output(yh, ph)
-    assert np.max(np.abs(Sh / ref - 1.0)) < 2e-6
-    assert np.max(np.abs(np.log(Sh) + 0.5 * ph)) < 0.5
+        ref = learned.scaling_from_output(yh, ph)
+        assert np.max(np.abs(Sh / ref - 1.0)) < 2e-6
+        assert np.max(np.abs(yh)) == 0.0 and np.max(np.abs(np.log(Sh) + 0.5 * ph)) < 1e-6
+        params = sg.sgiga_net_get_params(P.handle)
+        rng = np.random.default_rng(4)
+        sg.sgiga_net_set_params(P.handle, (params + 0.05 * rng.standard_normal(params.size)).astype(np.float32))
+        sg.sgiga_net_forward(P.handle, phi, y)
+        sg.sgiga_net_scaling(P.handle, S)
+        yh, Sh = (t.cpu().numpy().astype(np.float64) for t in (y, S))
+    assert np.max(np.abs(yh)) > 1e-3
+    assert np.max(np.abs(Sh / learned.scaling_from_output(yh, ph) - 1.0)) < 2e-6
 
 
 def test_loss_and_gradient_against_oracle(sg):

@@ -94,14 +94,13 @@ def test_scaling_bound():
 
 
 def test_untrained_scaling_is_the_inverse_square_root_of_the_coefficient():
-    """With the network output 0, S = exp(4 tanh(-log(c) / 8)): c^(-1/2) up to
-    the bound's cubic term (|u|^3 / 48 in log S for u = log(c) / 2), and
-    exactly 1 at c = 1; on the unit cube with a constant coefficient a (c = a,
-    by the features' pin) M = S FD S = FD / a to that order, the inverse of
-    a K."""
+    """With the network output 0, S = c^(-1/2); on the unit cube with a
+    constant coefficient a (c = a, by the features' pin) M = S FD S = FD / a,
+    the inverse of a K. The correction factor exp(4 tanh(y / 4)) is exp(y) to
+    first order and within e^(+-4)."""
     c = np.array([0.25, 0.8, 1.0, 1.3, 4.0])
-    S = learned.scaling_from_output(np.zeros_like(c), np.log(c))
-    u = 0.5 * np.log(c)
-    np.testing.assert_allclose(np.log(S), -u, atol=np.abs(u).max() ** 3 / 40)
-    assert S[2] == 1.0
-    assert np.all(np.diff(S) < 0)
+    np.testing.assert_allclose(learned.scaling_from_output(np.zeros_like(c), np.log(c)), c ** -0.5, rtol=1e-15)
+    y = np.array([-50.0, -1e-3, 0.0, 2e-3, 50.0])
+    f = learned.scaling_from_output(y, np.log(c)) * np.sqrt(c)
+    np.testing.assert_allclose(f[1:4], np.exp(y[1:4]), rtol=1e-8)
+    assert np.all(np.abs(np.log(f)) <= 4.0 + 1e-12)
