@@ -486,7 +486,8 @@ def measure_comparators(W, args):
     out["mixed_fd"] = {"ms": ms, "outer": st.iterations, "inner": st.inner_iterations, "rc": rc, "setup_s": ps,
                        "plan_phases_s": pt, "rel_l2_vs_oracle": _rel(W.combined(M), W.gold),
                        "solve_precision": "fp64" if mt.solve_precision == 0 else "mixed",
-                       "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "mixed": mt.solve_ms_mixed}}
+                       "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "fp64_fd32": mt.solve_ms_fp64_fd32,
+                                          "mixed": mt.solve_ms_mixed}}
     return out, M
 
 
@@ -604,8 +605,10 @@ def cube_line(sgiga, torch, stream, steps):
     m1.record(stream)
     torch.cuda.synchronize()
     mixed_plan = {"solve_precision": "fp64" if mt.solve_precision == 0 else "mixed",
+                  "fp32_preconditioner": bool(mt.solve_fp32_precond),
                   "ms_per_step": m0.elapsed_time(m1) / steps,
-                  "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "mixed": mt.solve_ms_mixed},
+                  "probe_solve_ms": {"fp64": mt.solve_ms_fp64, "fp64_fd32": mt.solve_ms_fp64_fd32,
+                                     "mixed": mt.solve_ms_mixed},
                   "rel_l2_vs_oracle": _rel(um.cpu().numpy(), np.loadtxt(CUBE_GOLDEN)[:, 0])}
     M.close()
     out = {"workload": CUBE_NAME, "value": P.info.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,

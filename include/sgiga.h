@@ -99,8 +99,9 @@ enum { SGIGA_GRADING_UNIFORM = 0, SGIGA_GRADING_RADICAL = 1, SGIGA_GRADING_ONESI
  * (FP32 operator apply with FP32 geometry planes and tables, FP32
  * preconditioner), per-component scalars and reductions in FP64. After
  * sgiga_autotune a MIXED_FP32 plan with the FD preconditioner may solve as
- * FP64 (its FP64 data is complete) when that was faster on the probe
- * (sgiga_tune_result.solve_precision). */
+ * FP64 PCG (its FP64 data is complete), preconditioned in FP64 or in FP32,
+ * when that was faster on the probe (sgiga_tune_result.solve_precision,
+ * solve_fp32_precond). */
 enum { SGIGA_PREC_FP64 = 0, SGIGA_PREC_MIXED_FP32 = 1 };
 
 /* Preconditioner of the batched conjugate-gradient solve. FD: fast
@@ -343,14 +344,21 @@ typedef struct {
                          flight on all SMs total 48 or 16 MB; -1: none) */
     int best_prefetch;
     /* (3) MIXED_FP32 plans with the FD preconditioner: the precision
-     * sgiga_solve uses from now on (SGIGA_PREC_FP64 when plain FP64 PCG solved
-     * a probe load vector to 1e-8 faster than the mixed solve, as where FD is
-     * nearly exact; the decomposition is then tuned again with the FP64
-     * kernels, and the fields above report that tuning), and the two probe
-     * solves' wall times (ms; 0: not run or, for FP64, not converged within
-     * the mixed solve's time). Other plans: their own precision, times 0. */
+     * sgiga_solve uses from now on (SGIGA_PREC_FP64 when FP64 PCG, with the
+     * FP64 or the FP32 preconditioner, solved a probe load vector to 1e-8
+     * faster than the mixed solve, as where FD is nearly exact; the
+     * decomposition is then tuned again with that solve's kernels, and the
+     * fields above report that tuning), and the probe solves' wall times (ms;
+     * 0: not run or, for FP64, not converged within the iterations that fit
+     * in twice the fastest time so far, at least 4).
+     * Other plans: their own precision, times 0. */
     int solve_precision;
     double solve_ms_fp64, solve_ms_mixed;
+    /* FP64 PCG preconditioned by the FP32 FD (narrowed residual, widened
+     * output, flexible CG), the third probe: its time (ms; 0 as above), and 1
+     * when it was the fastest and sgiga_solve now runs it. */
+    double solve_ms_fp64_fd32;
+    int solve_fp32_precond;
 } sgiga_tune_result;
 int sgiga_autotune(sgiga_plan_t plan, int reps, sgiga_tune_result* out);
 

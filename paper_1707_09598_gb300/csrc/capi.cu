@@ -1373,9 +1373,10 @@ int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
 // captures its graphs; sgiga_solve then runs the faster. FP64 PCG gets at most
 // the iterations that fit in the mixed solve's time. The plan's load vector
 // and solution are restored.
-static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx) {
-    *ms64 = *msmx = 0.0;
+static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx, double* ms6432) {
+    *ms64 = *msmx = *ms6432 = 0.0;
     P->solve_fp64 = false;
+    P->fp64_fd32 = false;
     const size_t n = (size_t)P->ndof;
     cudaStream_t s = P->stream;
     double* save = nullptr;
@@ -1406,17 +1407,30 @@ static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx) {
         double tm = timed(50, c);
         if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) return c;
         if (c != SGIGA_OK) tm = 1e30;
-        P->solve_fp64 = true;
-        timed(1, c);
-        const double t1 = timed(1, c);
-        if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = false; return c; }
-        const int cap = (int)std::min(1000.0, std::max(1.0, tm / std::max(t1, 1e-3)));
-        const double t64 = timed(cap, c);
-        const bool fp64_ok = c == SGIGA_OK;
-        if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = false; return c; }
+        // FP64 PCG with the FP64, then with the FP32 preconditioner
+        double best = tm, tfp[2] = {0.0, 0.0};
+        int pick = -1;
+        for (int v = 0; v < 2; ++v) {
+            P->solve_fp64 = true;
+            P->fp64_fd32 = v == 1;
+            timed(1, c);
+            const double t1 = timed(1, c);
+            if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = P->fp64_fd32 = false; return c; }
+            // iterations that fit in twice the fastest time so far (one timed
+            // iteration includes the per-solve overhead), at least 4
+            const int cap = (int)std::min(1000.0, std::max(4.0, 2.0 * best / std::max(t1, 1e-3)));
+            const double t64 = timed(cap, c);
+            if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = P->fp64_fd32 = false; return c; }
+            if (c == SGIGA_OK) {
+                tfp[v] = t64;
+                if (t64 < best) { best = t64; pick = v; }
+            }
+        }
         *msmx = tm;
-        *ms64 = fp64_ok ? t64 : 0.0;
-        P->solve_fp64 = fp64_ok && t64 < tm;
+        *ms64 = tfp[0];
+        *ms6432 = tfp[1];
+        P->solve_fp64 = pick >= 0;
+        P->fp64_fd32 = pick == 1;
         g_last_error.clear();
         return SGIGA_OK;
     };
@@ -1429,9 +1443,10 @@ static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx) {
 }
 
 // Operator tile policy (and, for FP32 3D plans, threads per block and the
-// metric planes' L2 prefetch) and preconditioner layout, each timed with the
-// kernels of precision f32 (FP32: the mixed inner solve's; else FP64).
-static int tune_decomposition(sgiga_plan_s* P, int reps, bool f32, sgiga_tune_result* out) {
+// metric planes' L2 prefetch), timed with the FP32 (f32) or FP64 operator, and
+// preconditioner layout, timed with the FP32 (fd32) or FP64 preconditioner:
+// the kernels the plan's CG runs.
+static int tune_decomposition(sgiga_plan_s* P, int reps, bool f32, bool fd32, sgiga_tune_result* out) {
     struct Cand { size_t budget; long long qpcap; };
     const Cand cands[] = {{48 * 1024, 4096}, {48 * 1024, 16384}, {110 * 1024, 8192},
                           {110 * 1024, 16384}, {200 * 1024, 16384}, {200 * 1024, 32768}};
@@ -1521,7 +1536,7 @@ static int tune_decomposition(sgiga_plan_s* P, int reps, bool f32, sgiga_tune_re
         if ((rc = refd(P, ksi, grp))) break;
         // the precision the plan's CG runs in; plain FD (no learned correction)
         auto fd_once = [&]() {
-            if (f32)
+            if (fd32)
                 return precond_fd<float>(P, P->f_b, P->f_z, nullptr, P->f_t1, P->f_t2);
             return precond_fd<double>(P, P->d_b, P->d_z, nullptr, P->d_t1, P->d_t2);
         };
@@ -1562,18 +1577,21 @@ int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
     if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
     const auto tt0 = std::chrono::steady_clock::now();
     // the kernels the plan's CG runs: FP32 in mixed plans (inner solve), else FP64
-    int rc = tune_decomposition(P, reps, P->cfg.precision == SGIGA_PREC_MIXED_FP32, out);
+    const bool mixed = P->cfg.precision == SGIGA_PREC_MIXED_FP32;
+    int rc = tune_decomposition(P, reps, mixed, mixed, out);
     if (rc) return rc;
-    double ms64 = 0.0, msmx = 0.0;
-    if (P->cfg.precision == SGIGA_PREC_MIXED_FP32 && P->cfg.precond == SGIGA_PRECOND_FD)
-        if ((rc = choose_precision(P, &ms64, &msmx))) return rc;
-    // a mixed plan that now solves in FP64: its decomposition tuned for the FP64 kernels
-    if (P->solve_fp64 && (rc = tune_decomposition(P, reps, false, out))) return rc;
+    double ms64 = 0.0, msmx = 0.0, ms6432 = 0.0;
+    if (mixed && P->cfg.precond == SGIGA_PRECOND_FD)
+        if ((rc = choose_precision(P, &ms64, &msmx, &ms6432))) return rc;
+    // a mixed plan that now solves in FP64: its decomposition tuned for the
+    // kernels of that solve (FP64 operator; FP64 or FP32 preconditioner)
+    if (P->solve_fp64 && (rc = tune_decomposition(P, reps, false, P->fp64_fd32, out))) return rc;
     if (out) {
-        out->solve_precision = P->cfg.precision == SGIGA_PREC_MIXED_FP32 && !P->solve_fp64 ? SGIGA_PREC_MIXED_FP32
-                                                                                           : SGIGA_PREC_FP64;
+        out->solve_precision = mixed && !P->solve_fp64 ? SGIGA_PREC_MIXED_FP32 : SGIGA_PREC_FP64;
         out->solve_ms_fp64 = ms64;
         out->solve_ms_mixed = msmx;
+        out->solve_ms_fp64_fd32 = ms6432;
+        out->solve_fp32_precond = P->fp64_fd32 ? 1 : 0;
     }
     P->t_autotune = since(tt0);
     return SGIGA_OK;

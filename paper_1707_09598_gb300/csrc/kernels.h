@@ -172,6 +172,7 @@ cudaError_t launch_zero_active(const DevPlan& P, double* x, const int* active, c
 cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* q, double* r, const int* active,
                                double* partial, double* rr, cudaStream_t s);
 cudaError_t launch_narrow(float* dst, const double* src, long long n, cudaStream_t s);
+cudaError_t launch_widen_active(const DevPlan& P, double* dst, const float* src, const int* active, cudaStream_t s);
 // net.cu (learned scaling network) and learned.cu
 // conv.cu: the network's convolutions (32-channel activations as BF16 rows [N][32])
 cudaError_t launch_conv_in(const DevPlan& P, const void* W, const float* b, const float* x, void* out,

@@ -96,6 +96,7 @@ struct sgiga_plan_s {
     bool learned_off = false;   // set for the rest of a solve after a refinement step without progress
     bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
     bool solve_fp64 = false;    // MIXED_FP32 plan whose solve the autotuner found faster as plain FP64 PCG
+    bool fp64_fd32 = false;     // ... preconditioned by the FP32 FD (flexible CG), also found faster
     cudaStream_t own_stream = nullptr;   // capture/launch stream when the plan's stream is the legacy one
     FDStreams fds{};                     // branches of a preconditioner pass's kernels
     bool fds_ok = false;
@@ -287,6 +288,16 @@ int learned_prepare(sgiga_plan_s* P);
 }
 
 inline int precond_any(sgiga_plan_s* P, const double* r, double* z, const int* active, double* t1, double* t2) {
+    if (P->fp64_fd32) {
+        // FP32 FD as the preconditioner of FP64 CG (a MIXED_FP32 plan solving in
+        // FP64): r narrowed, FD in FP32, z widened; the FP32 work vectors are
+        // free while the solve runs in FP64
+        CUDA_TRY(launch_narrow(P->f_r, r, P->ndof, P->stream));
+        const int rc = precond_fd<float>(P, P->f_r, P->f_z, active, P->f_t1, P->f_t2);
+        if (rc) return rc;
+        CUDA_TRY(launch_widen_active(P->dp, z, P->f_z, active, P->stream));
+        return SGIGA_OK;
+    }
     return precond_fd<double>(P, r, z, active, t1, t2);
 }
 inline int precond_any(sgiga_plan_s* P, const float* r, float* z, const int* active, float* t1, float* t2) {
@@ -419,10 +430,12 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     const int ng = (int)P->comps.size();
     double* bb = scal + 0 * ng;
     double* rz = scal + 1 * ng;
-    // the learned preconditioner runs in flexible CG (Polak-Ribiere beta), which
-    // also tolerates the rounding of its FP32 scaling
-    const bool flexible = sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready &&
-                          !P->learned_off;
+    // the learned preconditioner, and the FP32 FD inside FP64 CG, run in
+    // flexible CG (Polak-Ribiere beta), which tolerates a preconditioner that
+    // FP32 rounding leaves not exactly symmetric
+    const bool flexible = (sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready &&
+                           !P->learned_off) ||
+                          (sizeof(Real) == 8 && P->fp64_fd32);
     auto init = [&]() -> int {
         CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
         CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));

@@ -334,6 +334,22 @@ cudaError_t launch_ir_residual(const DevPlan& P, const double* b, const double* 
     return reduce(P, partial, rr, s);
 }
 
+// z64 = (double) z32 on the active components (the FP32 preconditioner's
+// output handed back to FP64 CG).
+__global__ void k_widen_active(const Chunk* __restrict__ chunks, double* __restrict__ dst,
+                               const float* __restrict__ src, const int* __restrict__ active) {
+    const Chunk c = chunks[blockIdx.x];
+    if (active && !active[c.grid]) return;
+    for (int i = threadIdx.x; i < c.len; i += blockDim.x) dst[c.start + i] = (double)src[c.start + i];
+}
+
+cudaError_t launch_widen_active(const DevPlan& P, double* dst, const float* src, const int* active, cudaStream_t s) {
+    if (P.nchunks == 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_widen_active<<<P.nchunks, 256, 0, s>>>(P.chunks, dst, src, active);
+    return cudaGetLastError();
+}
+
 // Narrow an FP64 array to FP32 (plan set-up of the mixed-precision copies).
 __global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

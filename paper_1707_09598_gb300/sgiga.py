@@ -82,7 +82,8 @@ class sgiga_tune_result(ctypes.Structure):
                 ("fd_ks", ctypes.c_int * 8), ("fd_ms", ctypes.c_double * 8), ("fd_grouped", ctypes.c_int * 8),
                 ("prefetch", ctypes.c_int * 16), ("best_prefetch", ctypes.c_int),
                 ("solve_precision", ctypes.c_int), ("solve_ms_fp64", ctypes.c_double),
-                ("solve_ms_mixed", ctypes.c_double)]
+                ("solve_ms_mixed", ctypes.c_double), ("solve_ms_fp64_fd32", ctypes.c_double),
+                ("solve_fp32_precond", ctypes.c_int)]
 
 
 class sgiga_plan_times_t(ctypes.Structure):

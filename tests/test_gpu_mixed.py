@@ -182,14 +182,18 @@ def test_autotune_chooses_the_solve_precision(sg):
     sum of Kronecker products of the same 1D pencils), so FP64 PCG converges
     in one or two iterations and beats the mixed solve's refinement steps: the
     autotuner switches the MIXED plan's solve to FP64, whose result then meets
-    the FP64 bound against the oracle's sparse direct solves."""
+    the FP64 bound against the oracle's sparse direct solves, with the FP64
+    or the FP32 preconditioner, whichever the probe found faster."""
     with sg.Plan(3, 3, 6, domain="unit", precision="mixed") as P:
         sg.sgiga_set_rhs_builtin(P.handle, "sine")
         b0 = np.zeros(P.info.ndof)
         sg.sgiga_get_rhs(P.handle, b0)
         res = sg.sgiga_autotune(P.handle, reps=2)
-        assert res.solve_precision == sg.PREC["fp64"], (res.solve_ms_fp64, res.solve_ms_mixed)
-        assert 0 < res.solve_ms_fp64 < res.solve_ms_mixed
+        assert res.solve_precision == sg.PREC["fp64"], (res.solve_ms_fp64, res.solve_ms_fp64_fd32, res.solve_ms_mixed)
+        chosen = res.solve_ms_fp64_fd32 if res.solve_fp32_precond else res.solve_ms_fp64
+        assert 0 < chosen < res.solve_ms_mixed
+        print("probe ms: fp64 %.3f, fp64 with fp32 FD %.3f, mixed %.3f; fp32 preconditioner %d"
+              % (res.solve_ms_fp64, res.solve_ms_fp64_fd32, res.solve_ms_mixed, res.solve_fp32_precond))
         b1 = np.zeros(P.info.ndof)
         sg.sgiga_get_rhs(P.handle, b1)
         assert np.array_equal(b0, b1)          # the probe solves leave the load vector
