@@ -452,6 +452,31 @@ int sgiga_geometry_coeffs(sgiga_plan_t plan, int g, double* G, double* mw);
 int sgiga_fd_eigen(sgiga_plan_t plan, int dir, int level, double* U, double* lam);
 
 /* ---------------------------------------------------------------------------
+ * The combination technique as a preconditioner of a full tensor-product
+ * solve (the paper's closing remark, Sec. 5): the full plan (one component of
+ * levels (J, .., J)) is preconditioned by the additive two-level method
+ *
+ *   z = FD(r) + sum_i c_i P_i K_i^{-1} P_i^T r
+ *
+ * over the components i of the combination plan (its index set and
+ * coefficients, eq. TD-combi-tec), P_i the prolongation of component i's
+ * space into the full space by knot insertion, K_i^{-1} the combination
+ * plan's batched PCG to inner_tol (at most inner_max iterations; an inexact
+ * inner solve is allowed: the full plan's CG runs flexible, from the host).
+ * Both plans: FP64, FD preconditioner, single patch, uniform knots, the same
+ * dimension, degree, continuity and domain (patch), the same stream; every
+ * component at most as fine as the full grid; the same diffusion coefficient
+ * is the caller's to set on both. The combination plan must outlive the
+ * attachment; its load vector and solution are overwritten by every full
+ * solve. Q = NULL detaches. SGIGA_ERR_ARG when a condition fails.
+ * sgiga_solve of the full plan then reports the total inner iterations in
+ * sgiga_solve_stats.inner_iterations. */
+int sgiga_ct_attach(sgiga_plan_t full, sgiga_plan_t ct, double inner_tol, int inner_max);
+/* z = sum_i c_i P_i K_i^{-1} P_i^T r alone (no FD), r and z device double
+ * [ndof of the full plan]. SGIGA_ERR_ARG without an attachment. */
+int sgiga_ct_apply(sgiga_plan_t full, const double* r, double* z);
+
+/* ---------------------------------------------------------------------------
  * Learned scaling of the preconditioner (not in the paper; its conclusions
  * name fast solvers used as preconditioners as future work, Sec. 5).
  *

@@ -236,6 +236,7 @@ static void assemble_band(int E, int Q, int p, int n, int klo, const double* w, 
 static void free_plan(sgiga_plan_s* P) {
     if (!P) return;
     free_net(P);
+    free_ct(P);
     destroy_loop_graph(P->loop64);
     destroy_loop_graph(P->loop32);
     if (P->own_stream) cudaStreamDestroy(P->own_stream);
@@ -1656,11 +1657,13 @@ int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats*
                                                " is not finite (a NaN or infinity in f or the boundary data)");
     }
     if (P->cfg.precision == SGIGA_PREC_FP64 || P->solve_fp64) {
+        ct_inner_iterations(P, true);
         int nact = pcg<double>(P, P->d_b, vecs64(P), rel_tol, max_iter, nullptr, P->d_active, P->d_iters, P->d_scal,
                                nullptr);
         if (nact < 0) return nact;
         int rc = solve_stats(P, P->d_scal + 3 * ng, P->d_scal, P->d_iters, nact, stats, t0);
         if (rc) return rc;
+        if (stats && P->ct) stats->inner_iterations = (int)ct_inner_iterations(P, false);
         if (nact > 0) return fail(SGIGA_ERR_NOT_CONVERGED, std::to_string(nact) + " components did not converge");
         return SGIGA_OK;
     }

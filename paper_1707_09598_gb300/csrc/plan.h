@@ -15,6 +15,7 @@
 
 namespace sgiga {
 struct Net;   // learned correction network (learned.cu)
+struct CTPrec;   // combination technique as a preconditioner of a full solve (ct.cu)
 }
 using namespace sgiga;
 
@@ -92,6 +93,7 @@ struct sgiga_plan_s {
     void* stage = nullptr;      // device staging for host pointers
     double* acoef = nullptr;    // diffusion coefficient a(x_q) [nqp], natural order (null: a = 1)
     sgiga::Net* net = nullptr;  // learned correction network (allocated by sgiga_net_init)
+    sgiga::CTPrec* ct = nullptr;  // two-level combination preconditioner (sgiga_ct_attach)
     bool net_ready = false;
     bool learned_off = false;   // set for the rest of a solve after a refinement step without progress
     bool use_graph = true;      // run CG loops as one captured graph with a device-side while node
@@ -281,6 +283,10 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
 namespace sgiga {
 int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active);
 void free_net(sgiga_plan_s* P);
+// FD(r) + sum_i c_i P_i K_i^{-1} P_i^T r (ct.cu)
+int precond_ct(sgiga_plan_s* P, const double* r, double* z, const int* active, double* t1, double* t2);
+void free_ct(sgiga_plan_s* P);
+long long ct_inner_iterations(sgiga_plan_s* P, bool reset);
 // the geometry planes changed: the network's features (and S) are stale
 void net_invalidate_features(sgiga_plan_s* P);
 // before a solve: S up to date (network evaluated once if needed)
@@ -288,6 +294,7 @@ int learned_prepare(sgiga_plan_s* P);
 }
 
 inline int precond_any(sgiga_plan_s* P, const double* r, double* z, const int* active, double* t1, double* t2) {
+    if (P->ct) return precond_ct(P, r, z, active, t1, t2);
     if (P->fp64_fd32) {
         // FP32 FD as the preconditioner of FP64 CG (a MIXED_FP32 plan solving in
         // FP64): r narrowed, FD in FP32, z widened; the FP32 work vectors are
@@ -435,7 +442,7 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     // FP32 rounding leaves not exactly symmetric
     const bool flexible = (sizeof(Real) == 4 && P->cfg.precond == SGIGA_PRECOND_LEARNED && P->net_ready &&
                            !P->learned_off) ||
-                          (sizeof(Real) == 8 && P->fp64_fd32);
+                          (sizeof(Real) == 8 && (P->fp64_fd32 || P->ct));
     auto init = [&]() -> int {
         CUDA_TRY(launch_pcg_init<Real>(D, rhs, v.x, v.r, P->d_partial, bb, s));
         CUDA_TRY(launch_pcg_start(D, bb, outer, active, iters, s));
@@ -448,7 +455,8 @@ inline int pcg(sgiga_plan_s* P, const Real* rhs, Vecs<Real> v, double tol, int m
     int rc = init();
     if (rc) return rc;
     sgiga_plan_s::LoopGraph& L = sizeof(Real) == 8 ? P->loop64 : P->loop32;
-    if (P->use_graph && !hook && !L.failed) {
+    // (the combination preconditioner runs inner solves from the host: host loop)
+    if (P->use_graph && !hook && !L.failed && !(sizeof(Real) == 8 && P->ct)) {
         // whole loop on the device: one graph launch, no host round trip per iteration
         CUDA_TRY(cudaMemsetAsync(P->d_counter, 0, sizeof(int), s));
         rc = pcg_graph_loop<Real>(P, L, v, rhs, tol, max_iter, outer, active, iters, scal, flexible);

@@ -122,6 +122,8 @@ _SIGS = {
     "sgiga_set_solver_options": (_I, [_P, _I, _D, _I]),
     "sgiga_autotune": (_I, [_P, _I, ctypes.POINTER(sgiga_tune_result)]),
     "sgiga_set_tiling": (_I, [_P, _I, _I, _I, _I]),
+    "sgiga_ct_attach": (_I, [_P, _P, ctypes.c_double, _I]),
+    "sgiga_ct_apply": (_I, [_P, _P, _P]),
     "sgiga_get_solution": (_I, [_P, _P]),
     "sgiga_set_solution": (_I, [_P, _P]),
     "sgiga_eval": (_I, [_P, _P, _L, _P]),
@@ -315,6 +317,15 @@ def sgiga_autotune(plan, reps=3):
     out = sgiga_tune_result()
     _check(_lib.sgiga_autotune(plan, int(reps), ctypes.byref(out)))
     return out
+
+
+def sgiga_ct_attach(plan, ct_plan, inner_tol=1e-6, inner_max=200):
+    _check(_lib.sgiga_ct_attach(plan, ct_plan, float(inner_tol), int(inner_max)))
+
+
+def sgiga_ct_apply(plan, r, z):
+    n = sgiga_plan_info(plan).ndof
+    _check(_lib.sgiga_ct_apply(plan, _ptr(r, n), _ptr(z, n)))
 
 
 def sgiga_set_tiling(plan, budget, qpcap, nthreads=256, prefetch=0):

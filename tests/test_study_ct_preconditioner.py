@@ -1,6 +1,7 @@
 """The combination technique as a preconditioner for the full tensor-product
 solve (the paper's closing remark, Sec. 5), studied on the CPU with the
-oracle's matrices. This backs the design decision not to build it on the GPU.
+oracle's matrices (the GPU version is `sgiga_ct_attach`, checked against
+oracle/ct.py in tests/test_gpu_ct.py).
 
 Full system: A u = b on the tensor grid with every level J (2D quarter annulus,
 p = 2, C^1, diffusion coefficient a(x)). Combination operator:
