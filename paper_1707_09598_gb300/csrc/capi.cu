@@ -958,6 +958,7 @@ const char* sgiga_last_error(void) { return g_last_error.c_str(); }
 long long sgiga_launch_count(void) { return g_launches.load(); }
 
 int sgiga_plan(const sgiga_config* cfg, void* stream, sgiga_plan_t* out) {
+    NvtxRange nvtx_("sgiga_plan");
     if (!cfg || !out) return fail(SGIGA_ERR_ARG, "null argument");
     *out = nullptr;
     sgiga_config c = *cfg;
@@ -1278,6 +1279,7 @@ static int ensure_acoef(sgiga_plan_s* P) {
 }
 
 int sgiga_set_coefficient(sgiga_plan_t P, int nfeat, const double* omega, const double* phase, double amp) {
+    NvtxRange nvtx_("sgiga_set_coefficient");
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
     if (nfeat < 0 || (nfeat > 0 && (!omega || !phase))) return fail(SGIGA_ERR_ARG, "bad coefficient features");
     const auto t0 = std::chrono::steady_clock::now();
@@ -1575,6 +1577,7 @@ static int tune_decomposition(sgiga_plan_s* P, int reps, bool f32, bool fd32, sg
 }
 
 int sgiga_autotune(sgiga_plan_t P, int reps, sgiga_tune_result* out) {
+    NvtxRange nvtx_("sgiga_autotune");
     if (!P || reps < 1) return fail(SGIGA_ERR_ARG, "null plan or reps < 1");
     const auto tt0 = std::chrono::steady_clock::now();
     // the kernels the plan's CG runs: FP32 in mixed plans (inner solve), else FP64
@@ -1641,6 +1644,7 @@ int sgiga_set_solver_options(sgiga_plan_t P, int use_graph, double inner_tol, in
 }
 
 int sgiga_solve(sgiga_plan_t P, double rel_tol, int max_iter, sgiga_solve_stats* stats) {
+    NvtxRange nvtx_("sgiga_solve");
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");
     if (!(rel_tol > 0) || max_iter < 1) return fail(SGIGA_ERR_ARG, "rel_tol must be > 0 and max_iter >= 1");
     auto t0 = std::chrono::steady_clock::now();
@@ -1780,6 +1784,7 @@ int sgiga_set_solution(sgiga_plan_t P, const double* u) {
 }
 
 int sgiga_eval(sgiga_plan_t P, const double* xi, long long npts, double* ucomp) {
+    NvtxRange nvtx_("sgiga_eval");
     if (!P || (!xi && npts > 0) || (!ucomp && npts > 0)) return fail(SGIGA_ERR_ARG, "null argument");
     if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
     if (P->multipatch) return fail(SGIGA_ERR_ARG, "multi-patch plan: evaluate with sgiga_eval_grad (patch ids)");

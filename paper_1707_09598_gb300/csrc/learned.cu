@@ -463,6 +463,7 @@ static int validation_iters(sgiga_plan_s* P, const double* bval, int* iters) {
 }
 
 int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stats* stats) {
+    NvtxRange nvtx_("sgiga_train_net");
     if (!P || !cfg) return fail(SGIGA_ERR_ARG, "null argument");
     if (!P->net_ready || !P->net) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
     if (cfg->target_pairs < 1 || cfg->epochs < 1 || !(cfg->lr > 0) || cfg->batch < 0)

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sgiga.h"
 #include "internal.h"
 #include "kernels.h"
@@ -29,6 +31,15 @@ int fail(int code, const std::string& msg);
             return fail(SGIGA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
         }                                                                                \
     } while (0)
+
+// A named range on the profiler's timeline for the life of the object (NVTX;
+// without an attached tool the calls do nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct sgiga_plan_s {
     sgiga_config cfg;
