@@ -611,6 +611,16 @@ const char* sgiga_last_error(void);
  * (a diagnostic count; memsets and copies are not included). */
 long long sgiga_launch_count(void);
 
+/* Checked build (compiled with -DSGIGA_CHECKED, build.build(checked=True)):
+ * the operator kernels' vector gathers, scatters and metric loads and the
+ * preconditioner's outputs check their indices; a failed check skips the
+ * access and records the site (1..7: operator 3D x, y, metric; operator 2D x,
+ * y; preconditioner level GEMM, small items). sgiga_build_checked() is 1 in
+ * that build, else 0; sgiga_check_site stores the first failed site of the
+ * plan (0: none, always 0 in the default build). No counterpart in the paper. */
+int sgiga_build_checked(void);
+int sgiga_check_site(sgiga_plan_t plan, int* site);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,7 +88,7 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 f[ax[1]] = fb;
                 v = (Real)Pl.gfull[g.gf_off + f[0] + (long long)f[1] * g.nf[0]];
             } else if (kept(fa, fb)) {
-                v = x[addr(fa, fb)];
+                if (SGIGA_GUARD(Pl, addr(fa, fb) >= 0 && addr(fa, fb) < Pl.ndof, CHK_OP2_X)) v = x[addr(fa, fb)];
             }
             X[idx] = v;
         }
@@ -191,7 +191,8 @@ k_op2(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 if (MODE != 1) yv += tdv[1][qb * P1 + t] * S1[S1n + o];
             }
         }
-        atomicAdd(&y[addr(fa, fb)], MODE == 2 ? -yv : yv);
+        if (SGIGA_GUARD(Pl, addr(fa, fb) >= 0 && addr(fa, fb) < Pl.ndof, CHK_OP2_Y))
+            atomicAdd(&y[addr(fa, fb)], MODE == 2 ? -yv : yv);
     }
 }
 

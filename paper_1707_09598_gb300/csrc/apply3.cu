@@ -109,8 +109,10 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
             const int r = dLa.div(idx), ja = idx - r * La, jc = dLb.div(r), jb = r - jc * Lb;
             int fa = E0[0] * M + ja, fb = E0[1] * M + jb, fc = E0[2] * M + jc;
             Real v = 0.0;
-            if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2)
-                v = x[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2]];
+            if (fa >= 1 && fa <= NF[0] - 2 && fb >= 1 && fb <= NF[1] - 2 && fc >= 1 && fc <= NF[2] - 2) {
+                const long long xi = doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2];
+                if (SGIGA_GUARD(Pl, xi >= 0 && xi < Pl.ndof, CHK_OP3_X)) v = x[xi];
+            }
             X[idx] = v;
         }
         __syncthreads();
@@ -230,7 +232,8 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
             if constexpr (PRE) {
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const long long gq = gi + (long long)q * npen;
+                    long long gq = gi + (long long)q * npen;
+                    if (!SGIGA_GUARD(Pl, gq >= 0 && gq < nqp, CHK_OP3_G)) gq = 0;
                     if (DIAG) {
                         gpre[q][0] = ldg_stream(G + gq);
                         gpre[q][1] = ldg_stream(G + 3 * nqp + gq);
@@ -390,7 +393,8 @@ k_op3(DevPlan Pl, const Real* __restrict__ x, Real* __restrict__ y, const int* _
                 if (MODE == 0) yv += tdv[2][qc * P1 + t] * S1[S1n + o];
             }
         }
-        atomicAdd(&y[doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2]], yv);
+        const long long yi = doff + (fa - 1) * ST[0] + (fb - 1) * ST[1] + (fc - 1) * ST[2];
+        if (SGIGA_GUARD(Pl, yi >= 0 && yi < Pl.ndof, CHK_OP3_Y)) atomicAdd(&y[yi], yv);
     }
 }
 

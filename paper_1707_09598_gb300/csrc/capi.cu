@@ -953,6 +953,23 @@ static int retile(sgiga_plan_s* P, size_t budget, long long qpcap, double* Gn = 
 // ---------------------------------------------------------------------------
 extern "C" {
 
+int sgiga_build_checked(void) {
+#ifdef SGIGA_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int sgiga_check_site(sgiga_plan_t P, int* site) {
+    if (!P || !site) return fail(SGIGA_ERR_ARG, "null argument");
+    int h[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(h, P->dp.flags + 2, sizeof(h), cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    *site = h[0] ? h[1] : 0;
+    return SGIGA_OK;
+}
+
 const char* sgiga_last_error(void) { return g_last_error.c_str(); }
 
 long long sgiga_launch_count(void) { return g_launches.load(); }

@@ -120,7 +120,8 @@ k_fd_pass(DevPlan P, const FDItem* __restrict__ items, int dir, int forward,
             Real acc = 0;
             for (int j = 0; j < n; ++j) acc += Ms[i * ms + j] * Xs[j * xs + cl];
             const long long col = it.c0 + cl, a = col / B, b = col - a * B;
-            vout[a * n * B + (long long)i * B + b] = acc;
+            const long long oi = a * n * B + (long long)i * B + b;
+            if (SGIGA_GUARD(P, oi >= 0 && oi < g.fd_n, CHK_FD_SMALL)) vout[oi] = acc;
         }
         return;
     }
@@ -339,6 +340,8 @@ k_fd_level(DevPlan P, const FDItem* __restrict__ items, int forward, const Real*
         for (int r = 0; r < 4; ++r) {
             const int i = 4 * ty + r;
             if (i >= nrows) continue;
+            const long long oi = cb[c0 + col] + (long long)(i0 + i) * st;
+            if (!SGIGA_GUARD(P, oi >= 0 && oi < P.nfd, CHK_FD_LEVEL)) continue;
             if (split) atomicAdd(o + (long long)(i0 + i) * st, acc[r][c]);
             else o[(long long)(i0 + i) * st] = acc[r][c];
         }

@@ -70,6 +70,27 @@ struct DevPlan {
     const int* fdcc;
 };
 
+// Bounds checks of the checked build (-DSGIGA_CHECKED): a failed check sets
+// flags[2], records the first failing site in flags[3] and skips the access;
+// the default build compiles them away (SGIGA_GUARD is then `true`).
+#ifdef SGIGA_CHECKED
+#ifdef __CUDACC__
+__device__ __forceinline__ bool sgiga_guard(int* flags, bool ok, int site) {
+    if (!ok) {
+        atomicOr(flags + 2, 1);
+        atomicCAS(flags + 3, 0, site);
+    }
+    return ok;
+}
+#endif
+#define SGIGA_GUARD(P, cond, site) sgiga_guard((P).flags, (cond), (site))
+#else
+#define SGIGA_GUARD(P, cond, site) true
+#endif
+// sites of the checks (flags[3])
+enum { CHK_OP3_X = 1, CHK_OP3_Y = 2, CHK_OP3_G = 3, CHK_OP2_X = 4, CHK_OP2_Y = 5, CHK_FD_LEVEL = 6,
+       CHK_FD_SMALL = 7 };
+
 // boundary.cu (multi-patch Dirichlet data)
 cudaError_t launch_boundary_points(const DevPlan& P, double* xb, cudaStream_t s);
 cudaError_t launch_boundary_builtin(const DevPlan& P, int src, const double* xb, double* gdata, long long n,

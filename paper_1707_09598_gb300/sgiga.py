@@ -11,7 +11,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libsgiga.so")
+# SGIGA_LIB selects another build of the library (the checked build)
+LIB_PATH = os.environ.get("SGIGA_LIB") or os.path.join(_HERE, "_lib", "libsgiga.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libsgiga.so is not built (%s); run paper_1707_09598_gb300.build.build()" % LIB_PATH)
@@ -122,6 +123,8 @@ _SIGS = {
     "sgiga_set_solver_options": (_I, [_P, _I, _D, _I]),
     "sgiga_autotune": (_I, [_P, _I, ctypes.POINTER(sgiga_tune_result)]),
     "sgiga_set_tiling": (_I, [_P, _I, _I, _I, _I]),
+    "sgiga_build_checked": (_I, []),
+    "sgiga_check_site": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "sgiga_ct_attach": (_I, [_P, _P, ctypes.c_double, _I]),
     "sgiga_ct_apply": (_I, [_P, _P, _P]),
     "sgiga_get_solution": (_I, [_P, _P]),
@@ -317,6 +320,16 @@ def sgiga_autotune(plan, reps=3):
     out = sgiga_tune_result()
     _check(_lib.sgiga_autotune(plan, int(reps), ctypes.byref(out)))
     return out
+
+
+def sgiga_build_checked():
+    return int(_lib.sgiga_build_checked())
+
+
+def sgiga_check_site(plan):
+    site = ctypes.c_int(0)
+    _check(_lib.sgiga_check_site(plan, ctypes.byref(site)))
+    return site.value
 
 
 def sgiga_ct_attach(plan, ct_plan, inner_tol=1e-6, inner_max=200):
