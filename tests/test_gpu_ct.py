@@ -21,6 +21,18 @@ def _coef(x):
     return np.exp(np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]))
 
 
+@pytest.fixture
+def stream():
+    """A side stream that is torch's current stream for the test only (the
+    plans run on it, so torch's fills and reads are ordered with their calls)."""
+    s = torch.cuda.Stream()
+    prev = torch.cuda.current_stream()
+    torch.cuda.set_stream(s)
+    yield s
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(prev)
+
+
 @pytest.fixture(scope="module")
 def sg():
     if not torch.cuda.is_available():
@@ -47,9 +59,7 @@ def _plans(sg, d, p, r, J, stream):
 
 
 @pytest.mark.parametrize("d,J", [(2, 5), (3, 3)])
-def test_combination_operator_against_oracle(sg, d, J):
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
+def test_combination_operator_against_oracle(sg, stream, d, J):
     full, comb = _plans(sg, d, 2, 1, J, stream)
     with full, comb:
         sg.sgiga_ct_attach(full.handle, comb.handle, 1e-13, 2000)
@@ -65,13 +75,11 @@ def test_combination_operator_against_oracle(sg, d, J):
     assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 1e-9
 
 
-def test_two_level_solve_against_oracle(sg):
+def test_two_level_solve_against_oracle(sg, stream):
     """FD + B_CT in flexible CG on the GPU: the solution equals the oracle's
     direct solve, and the outer iteration counts with and without B_CT are
     within one of the oracle's standard PCG counts (exact inner solves there)."""
     d, J = 2, 6
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     full, comb = _plans(sg, d, 2, 1, J, stream)
     T = ct.TwoLevel(geometry.make("unit", d), d, 2, 1, J, diffusion=_coef)
     n_fd, _ = T.cg_iterations(T.b_fd)
