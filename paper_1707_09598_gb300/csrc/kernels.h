@@ -222,8 +222,7 @@ cudaError_t launch_pair_delta(const DevPlan& P, const float* S, const float* res
 cudaError_t launch_pair_mask(int ng, const double* rr, const double* bb, double thr2, int* mask, cudaStream_t s);
 cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delta, const float* z1, const float* r,
                              const float* z2, float weight, float* dls, cudaStream_t s);
-cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, const float* phi,
-                               cudaStream_t s);
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, void* wb, const int* wmap, int n, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);
 cudaError_t launch_f2bf(const float* p, const int* wmap, void* wb, int n, cudaStream_t s);

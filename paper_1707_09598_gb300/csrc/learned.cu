@@ -215,8 +215,8 @@ static int net_backward(sgiga_plan_s* P) {
     return SGIGA_OK;
 }
 
-// S = exp(N(phi)); a component whose network output is not finite keeps S = 1
-// there (plain FD for that component).
+// S = exp(-phi / 2 + 4 tanh(N(phi) / 4)); a component whose network output is
+// not finite keeps S = 1 there (plain FD for that component).
 static int net_scaling(sgiga_plan_s* P) {
     Net* n = P->net;
     int rc;
@@ -569,7 +569,7 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
                 if ((rc = pair_loss_grad(P, r, r + N, n->masks + (size_t)order[k] * ng, n->dY, 1.0f / nb)))
                     return rc;
             }
-            CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, n->feat, s));    // d/dlog S -> d/dy
+            CUDA_TRY(launch_mask_scaled(D, n->dY, n->ok, n->Y, s));    // d/dlog S -> d/dy
             if ((rc = net_backward(P))) return rc;
             n->step++;
             steps++;

@@ -3,8 +3,8 @@
 // preconditioners as future work, Sec. 5), and the elementwise kernels of the
 // scaled preconditioner and of its training loss:
 //
-//   M(r) = S * FD(S * r),  S = exp(N(phi)),  phi = log of the local effective
-//   coefficient of each DoF,
+//   M(r) = S * FD(S * r),  S = exp(-phi / 2 + 4 tanh(N(phi) / 4)),  phi = log
+//   of the local effective coefficient of each DoF,
 //
 // N = three 3x3(x3) convolutions over each component's DoF tensor with zero
 // padding, 1 -> 32 -> 32 -> 1 channels, ReLU after the first two (conv.cu).
@@ -152,13 +152,12 @@ __global__ void k_pair_grad(long long n, const float* __restrict__ S, const floa
 // chain rule from d/dlog S to d/dy through log S = L tanh(y / L); no gradient
 // through a component that fell back to S = 1
 __global__ void k_mask_scaled(DevPlan P, float* __restrict__ dy, const int* __restrict__ ok,
-                              const float* __restrict__ y, const float* __restrict__ phi) {
+                              const float* __restrict__ y) {
     const Chunk c = P.chunks[blockIdx.x];
     const bool use = ok[c.grid] != 0;
     for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
         const long long k = c.start + i;
         const float t = tanhf(y[k] * (1.0f / SGIGA_LOGS_MAX));   // dlog S / dy = 1 - t^2
-        (void)phi;
         dy[k] = use ? dy[k] * (1.0f - t * t) : 0.0f;
     }
 }
@@ -261,11 +260,10 @@ cudaError_t launch_pair_grad(const DevPlan& P, const float* S, const float* delt
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, const float* phi,
-                               cudaStream_t s) {
+cudaError_t launch_mask_scaled(const DevPlan& P, float* dy, const int* ok, const float* y, cudaStream_t s) {
     if (P.nchunks == 0) return cudaSuccess;
     SGIGA_COUNT_LAUNCH();
-    k_mask_scaled<<<P.nchunks, 256, 0, s>>>(P, dy, ok, y, phi);
+    k_mask_scaled<<<P.nchunks, 256, 0, s>>>(P, dy, ok, y);
     return cudaGetLastError();
 }
 

@@ -290,7 +290,8 @@ inline int precond_fd(sgiga_plan_s* P, const Real* r, Real* z, const int* active
 // `outer` (all when null), each with its own scalars, until
 // ||r_g|| <= tol ||rhs_g|| or max_iter iterations. Scalars: scal[0..6].
 // Returns the number of grids still active (or a negative status).
-// Learned preconditioner (learned.cu): z = S * FD(S * r), S = exp(N(phi)), FP32.
+// Learned preconditioner (learned.cu): z = S * FD(S * r),
+// S = exp(-phi / 2 + 4 tanh(N(phi) / 4)), FP32.
 namespace sgiga {
 int precond_learned(sgiga_plan_s* P, const float* r, float* z, const int* active);
 void free_net(sgiga_plan_s* P);
