@@ -507,6 +507,8 @@ typedef struct {
     float lr;             /* Adam learning rate */
     unsigned seed;        /* right-hand sides and sample order */
     int batch;            /* samples per Adam step (0: 2) */
+    int loss_norm;        /* 0: Euclidean ||M(r) - e||^2 / ||e||^2; 1: energy norm
+                             (M(r) - e)^T K (M(r) - e) / e^T K e, K the FP32 operator */
 } sgiga_train_cfg;
 
 typedef struct {
@@ -552,6 +554,11 @@ int sgiga_net_set_scaling(sgiga_plan_t plan, const float* S);
  * ||M(r) - e||^2 / ||e||^2 (*loss, host), and its gradient with respect to
  * log S (grad, device float [ndof]); r, e device float [ndof]. */
 int sgiga_net_loss_grad(sgiga_plan_t plan, const float* r, const float* e, double* loss, float* grad);
+/* Norm of that loss for sgiga_net_loss_grad (sgiga_train_net sets it from its
+ * config): 0 Euclidean, 1 the energy norm of the plan's FP32 operator K,
+ * L = (M(r) - e)^T K (M(r) - e) / e^T K e, whose gradient uses
+ * delta = 2 K (M(r) - e) / e^T K e in place of 2 (M(r) - e) / ||e||^2. */
+int sgiga_net_set_loss_norm(sgiga_plan_t plan, int norm);
 /* Record (residual, error) pairs from the plan's own FD-preconditioned FP64 CG
  * on seeded random right-hand sides and train N by Adam on the loss above,
  * back-propagated through S (above). In a recorded sample only the

@@ -24,7 +24,8 @@ whenever FD is.
 
 Loss of one (residual, error) pair of one component:
     L = ||M(r) - e||^2 / ||e||^2,
-and with several components the mean over them. Its gradient with respect to
+or in the component's energy norm (M(r) - e)^T K (M(r) - e) / e^T K e, and
+with several components the mean over them. Its gradient with respect to
 log S_i (FD symmetric):
     dL/dlog S_i = S_i (delta_i FD(S r)_i + r_i FD(S delta)_i),
     delta = 2 (M(r) - e) / ||e||^2.
@@ -67,31 +68,42 @@ def scaled_fd(levels, p, r, S, rvec, geom=None):
     return S * fd.fd_apply(levels, p, r, S * np.asarray(rvec, dtype=np.float64), geom=geom)
 
 
-def pair_loss_grad(levels, p, r, S, rvec, evec, geom=None):
-    """(L, dL/dlog S) of one pair of one component."""
+def pair_loss_grad(levels, p, r, S, rvec, evec, geom=None, K=None):
+    """(L, dL/dlog S) of one pair of one component. With the component's
+    stiffness K the loss is in its energy norm,
+        L = (M(r) - e)^T K (M(r) - e) / e^T K e,
+    and delta = 2 K (M(r) - e) / e^T K e (K symmetric)."""
     S = np.asarray(S, dtype=np.float64)
     rvec = np.asarray(rvec, dtype=np.float64)
     evec = np.asarray(evec, dtype=np.float64)
     z1 = fd.fd_apply(levels, p, r, S * rvec, geom=geom)
     m = S * z1
-    ee = float(evec @ evec)
     res = m - evec
-    L = float(res @ res) / ee
-    delta = 2.0 * res / ee
+    if K is None:
+        ee = float(evec @ evec)
+        L = float(res @ res) / ee
+        delta = 2.0 * res / ee
+    else:
+        ee = float(evec @ (K @ evec))
+        Kres = K @ res
+        L = float(res @ Kres) / ee
+        delta = 2.0 * Kres / ee
     z2 = fd.fd_apply(levels, p, r, S * delta, geom=geom)
     return L, S * (delta * z1 + rvec * z2)
 
 
-def packed_loss_grad(grids, p, r, S, rvec, evec, geom=None):
+def packed_loss_grad(grids, p, r, S, rvec, evec, geom=None, Ks=None):
     """Mean loss over the components of packed vectors, and its gradient.
 
-    grids: per component (levels, dof_off, ndof)."""
+    grids: per component (levels, dof_off, ndof); Ks: per component its
+    stiffness matrix (energy-norm loss), or None (Euclidean)."""
     S = np.asarray(S, dtype=np.float64)
     grad = np.zeros_like(S)
     tot = 0.0
-    for levels, off, n in grids:
+    for gi, (levels, off, n) in enumerate(grids):
         sl = slice(off, off + n)
-        L, g = pair_loss_grad(levels, p, r, S[sl], rvec[sl], evec[sl], geom=geom)
+        L, g = pair_loss_grad(levels, p, r, S[sl], rvec[sl], evec[sl], geom=geom,
+                              K=None if Ks is None else Ks[gi])
         tot += L
         grad[sl] = g
     return tot / len(grids), grad / len(grids)

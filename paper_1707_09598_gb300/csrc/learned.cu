@@ -48,6 +48,8 @@ struct Net {
     float *feat = nullptr;            // phi = log c (the network input)
     float *S = nullptr;               // scaling of the preconditioner
     float *tA = nullptr, *z1 = nullptr, *z2 = nullptr, *res = nullptr, *delta = nullptr;
+    float *kres = nullptr, *ke = nullptr;   // K res, K e (energy-norm loss)
+    int loss_norm = 0;                       // 0: Euclidean, 1: energy (K) norm
     double *dots = nullptr, *dots2 = nullptr, *lossacc = nullptr, *cnt = nullptr;
     int* ok = nullptr;
     int* masks = nullptr;             // per training sample: [ncomp] components that count
@@ -106,7 +108,8 @@ static int net_create(sgiga_plan_s* P) {
     const size_t N = (size_t)n->N, ng = P->comps.size();
     int rc;
     void** bufs1[] = {(void**)&n->A0, (void**)&n->Y, (void**)&n->dY, (void**)&n->feat, (void**)&n->S,
-                      (void**)&n->tA, (void**)&n->z1, (void**)&n->z2, (void**)&n->res, (void**)&n->delta};
+                      (void**)&n->tA, (void**)&n->z1, (void**)&n->z2, (void**)&n->res, (void**)&n->delta,
+                      (void**)&n->kres, (void**)&n->ke};
     for (void** b : bufs1)
         if ((rc = nalloc(n, b, N * 4))) return rc;
     void** bufs32[] = {&n->A1, &n->A2, &n->dA1, &n->dA2};
@@ -266,9 +269,18 @@ static int pair_loss_grad(sgiga_plan_s* P, const float* r, const float* e, const
     CUDA_TRY(launch_mul_active(D, n->S, r, n->tA, nullptr, s));
     if ((rc = precond_fd<float>(P, n->tA, n->z1, nullptr, P->f_t1, P->f_t2))) return rc;
     CUDA_TRY(launch_pair_residual(D, n->S, n->z1, e, n->res, s));          // res = S z1 - e
-    CUDA_TRY(launch_dot<float>(D, n->res, n->res, P->d_partial, n->dots, s));
-    CUDA_TRY(launch_dot<float>(D, e, e, P->d_partial, n->dots2, s));
-    CUDA_TRY(launch_pair_delta(D, n->S, n->res, n->dots, n->dots2, mask, n->cnt, n->delta, n->tA, n->lossacc, s));
+    // the norm of the loss: Euclidean, or the energy norm (K = the plan's FP32
+    // operator): L = res^T K res / e^T K e, delta = 2 K res / (e^T K e ncounted)
+    const float* kr = n->res;
+    const float* kee = e;
+    if (n->loss_norm == 1) {
+        if ((rc = apply_op(P, n->res, n->kres, nullptr)) || (rc = apply_op(P, e, n->ke, nullptr))) return rc;
+        kr = n->kres;
+        kee = n->ke;
+    }
+    CUDA_TRY(launch_dot<float>(D, n->res, kr, P->d_partial, n->dots, s));
+    CUDA_TRY(launch_dot<float>(D, e, kee, P->d_partial, n->dots2, s));
+    CUDA_TRY(launch_pair_delta(D, n->S, kr, n->dots, n->dots2, mask, n->cnt, n->delta, n->tA, n->lossacc, s));
     if ((rc = precond_fd<float>(P, n->tA, n->z2, nullptr, P->f_t1, P->f_t2))) return rc;
     CUDA_TRY(launch_pair_grad(D, n->S, n->delta, n->z1, r, n->z2, weight, dls, s));
     return SGIGA_OK;
@@ -429,6 +441,13 @@ int sgiga_net_set_scaling(sgiga_plan_t P, const float* S) {
     return SGIGA_OK;
 }
 
+int sgiga_net_set_loss_norm(sgiga_plan_t P, int norm) {
+    if (!P || !P->net) return fail(SGIGA_ERR_ARG, "no network (call sgiga_net_init)");
+    if (norm != 0 && norm != 1) return fail(SGIGA_ERR_ARG, "norm must be 0 (Euclidean) or 1 (energy)");
+    P->net->loss_norm = norm;
+    return SGIGA_OK;
+}
+
 int sgiga_net_loss_grad(sgiga_plan_t P, const float* r, const float* e, double* loss, float* grad) {
     if (!P || !P->net || !P->net_ready || !r || !e || !loss || !grad)
         return fail(SGIGA_ERR_ARG, "no network or null argument");
@@ -542,6 +561,7 @@ int sgiga_train_net(sgiga_plan_t P, const sgiga_train_cfg* cfg, sgiga_train_stat
     // needs the fewest inner iterations, the earliest among equals: a lower
     // loss on the pairs alone does not mean fewer CG iterations
     const int B = cfg->batch > 0 ? cfg->batch : 2;
+    n->loss_norm = cfg->loss_norm == 1 ? 1 : 0;
     n->s_override = false;
     std::vector<int> order(n->nsamples);
     for (int i = 0; i < n->nsamples; ++i) order[i] = i;

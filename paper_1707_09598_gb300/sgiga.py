@@ -64,7 +64,7 @@ class sgiga_grid(ctypes.Structure):
 
 class sgiga_train_cfg(ctypes.Structure):
     _fields_ = [("target_pairs", ctypes.c_int), ("max_iter_record", ctypes.c_int), ("epochs", ctypes.c_int),
-                ("lr", ctypes.c_float), ("seed", ctypes.c_uint), ("batch", ctypes.c_int)]
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint), ("batch", ctypes.c_int), ("loss_norm", ctypes.c_int)]
 
 
 class sgiga_train_stats(ctypes.Structure):
@@ -150,6 +150,7 @@ _SIGS = {
     "sgiga_net_scaling": (_I, [_P, _P]),
     "sgiga_net_set_scaling": (_I, [_P, _P]),
     "sgiga_net_loss_grad": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
+    "sgiga_net_set_loss_norm": (_I, [_P, _I]),
     "sgiga_train_net": (_I, [_P, ctypes.POINTER(sgiga_train_cfg), ctypes.POINTER(sgiga_train_stats)]),
     "sgiga_net_save": (_I, [_P, ctypes.c_char_p]),
     "sgiga_net_load": (_I, [_P, ctypes.c_char_p]),
@@ -519,6 +520,10 @@ def sgiga_net_set_scaling(plan, S):
     _check(_lib.sgiga_net_set_scaling(plan, _ptr(S, n, np.float32)))
 
 
+def sgiga_net_set_loss_norm(plan, norm):
+    _check(_lib.sgiga_net_set_loss_norm(plan, {"euclidean": 0, "energy": 1}.get(norm, norm)))
+
+
 def sgiga_net_loss_grad(plan, r, e, grad):
     """(loss, fills grad): the training loss of one sample and its gradient
     with respect to log S (float32 CUDA tensors [ndof])."""
@@ -528,8 +533,10 @@ def sgiga_net_loss_grad(plan, r, e, grad):
     return loss.value
 
 
-def sgiga_train_net(plan, target_pairs=10000, max_iter_record=30, epochs=10, lr=1e-3, seed=100, batch=2):
-    cfg = sgiga_train_cfg(int(target_pairs), int(max_iter_record), int(epochs), float(lr), int(seed), int(batch))
+def sgiga_train_net(plan, target_pairs=10000, max_iter_record=30, epochs=10, lr=1e-3, seed=100, batch=2,
+                    loss="euclidean"):
+    cfg = sgiga_train_cfg(int(target_pairs), int(max_iter_record), int(epochs), float(lr), int(seed), int(batch),
+                          {"euclidean": 0, "energy": 1}[loss])
     st = sgiga_train_stats()
     _check(_lib.sgiga_train_net(plan, ctypes.byref(cfg), ctypes.byref(st)))
     return st

@@ -251,10 +251,11 @@ def test_scaling_from_the_network_against_oracle(sg):
     assert np.max(np.abs(Sh / learned.scaling_from_output(yh, ph) - 1.0)) < 2e-6
 
 
-def test_loss_and_gradient_against_oracle(sg):
+@pytest.mark.parametrize("norm", ["euclidean", "energy"])
+def test_loss_and_gradient_against_oracle(sg, norm):
     """Training loss of one sample and its gradient with respect to log S (FP32
-    preconditioner on the device) against the oracle's FP64 definition, at a
-    random positive scaling."""
+    preconditioner and, for the energy norm, FP32 operator on the device)
+    against the oracle's FP64 definition, at a random positive scaling."""
     P, geom, a = _patch_plan(sg, 4, precision="mixed", precond="learned")
     with P:
         n = P.info.ndof
@@ -262,13 +263,18 @@ def test_loss_and_gradient_against_oracle(sg):
         S = np.exp(0.3 * rng.standard_normal(n)).astype(np.float32)
         r = rng.standard_normal(n).astype(np.float32)
         e = rng.standard_normal(n).astype(np.float32)
+        sg.sgiga_net_init(P.handle, 1)
+        sg.sgiga_net_set_loss_norm(P.handle, norm)
         sg.sgiga_net_set_scaling(P.handle, S)
         grad = torch.zeros(n, dtype=torch.float32, device="cuda")
         loss = sg.sgiga_net_loss_grad(P.handle, torch.as_tensor(r, device="cuda"), torch.as_tensor(e, device="cuda"),
                                       grad)
         grids = [(tuple(g.levels[:3]), g.dof_off, g.ndof) for g in P.grids]
+        Ks = None
+        if norm == "energy":
+            Ks = [Component(geom, lv, 3).assemble(diffusion=a).K for lv, _, _ in grids]
         Lref, gref = learned.packed_loss_grad(grids, 3, 2, S.astype(np.float64), r.astype(np.float64),
-                                              e.astype(np.float64))
+                                              e.astype(np.float64), Ks=Ks)
     assert abs(loss - Lref) < 1e-5 * Lref, (loss, Lref)
     assert _rel(grad.cpu().numpy(), gref) < 1e-4
 

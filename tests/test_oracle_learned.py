@@ -104,3 +104,30 @@ def test_untrained_scaling_is_the_inverse_square_root_of_the_coefficient():
     f = learned.scaling_from_output(y, np.log(c)) * np.sqrt(c)
     np.testing.assert_allclose(f[1:4], np.exp(y[1:4]), rtol=1e-8)
     assert np.all(np.abs(np.log(f)) <= 4.0 + 1e-12)
+
+
+def test_energy_norm_loss_gradient_and_exact_scaling():
+    """Energy-norm loss: its gradient matches central differences, and it
+    vanishes at the exact scaling of a constant coefficient on the unit cube
+    (M = FD / alpha = (alpha K)^{-1})."""
+    from oracle import geometry
+    from oracle.galerkin import Component
+    lv, p = (2, 2, 3), 3
+    K = Component(geometry.make("unit", 3), lv, p, p - 1).assemble().K.toarray()
+    n = K.shape[0]
+    rng = np.random.default_rng(6)
+    r, e = rng.standard_normal(n), rng.standard_normal(n)
+    ls = 0.2 * rng.standard_normal(n)
+    L, g = learned.pair_loss_grad(lv, p, p - 1, np.exp(ls), r, e, K=K)
+    h = 1e-6
+    for i in rng.choice(n, 25, replace=False):
+        dv = np.zeros(n)
+        dv[i] = h
+        fp, _ = learned.pair_loss_grad(lv, p, p - 1, np.exp(ls + dv), r, e, K=K)
+        fm, _ = learned.pair_loss_grad(lv, p, p - 1, np.exp(ls - dv), r, e, K=K)
+        assert abs((fp - fm) / (2 * h) - g[i]) <= 1e-6 * (1.0 + abs(g[i])), i
+    alpha = 2.5
+    e = rng.standard_normal(n)
+    r = alpha * (K @ e)
+    L, g = learned.pair_loss_grad(lv, p, p - 1, np.full(n, alpha ** -0.5), r, e, K=K)
+    assert L < 1e-24 and np.linalg.norm(g) < 1e-10
