@@ -534,7 +534,7 @@ def network_free_scaling(W, L):
     return out
 
 
-def cube_line(sgiga, torch, stream, steps):
+def cube_line(sgiga, torch, stream, steps, peak=None):
     """The FP64 unit-cube workload (w = 10): step = load vector + batched FD-PCG
     to 1e-12 + eval + combine; its FP64 operator apply against the FP64 rate
     (cuBLAS DGEMM, measured here)."""
@@ -580,7 +580,7 @@ def cube_line(sgiga, torch, stream, steps):
     torch.cuda.synchronize()
     apply_s = a0.elapsed_time(a1) / 20 / 1e3
     flops = apply_flops(P)
-    peak = fp64_peak_tflops(torch)
+    peak = peak if peak else fp64_peak_tflops(torch)
     # the same step on a MIXED plan: its autotuner times the mixed solve against
     # FP64 PCG (FD is exact on the cube) and keeps the faster
     M = sgiga.Plan(C["d"], C["p"], C["w"], domain="unit", stream=stream, precision="mixed")
@@ -667,11 +667,15 @@ def run_ours(args):
     stats = []
 
     def step():
+        # an NVTX range per step, so that a profiler's launch list can be
+        # restricted to the steps (ncu --nvtx --nvtx-include bench_step/)
+        torch.cuda.nvtx.range_push("bench_step")
         sgiga.sgiga_set_rhs(P.handle, f_dev)
         st, _ = sgiga.sgiga_solve(P.handle, tol, 50)
         stats.append(st)
         sgiga.sgiga_eval(P.handle, W.pts, npts, uc)
         sgiga.sgiga_combine(P.handle, uc, npts, u)
+        torch.cuda.nvtx.range_pop()
 
     for _ in range(args.warmup):
         step()
@@ -734,6 +738,28 @@ def run_ours(args):
                 "apply_ms": apply_s * 1e3, "algorithmic_bytes": g_bytes,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 
+    # the refinement's FP64 residual apply (the largest time share of the
+    # solve), against the FP64 rate measured here (cuBLAS DGEMM)
+    fp64_peak = fp64_peak_tflops(torch)
+    xd = torch.randn(ndof, dtype=torch.float64, device="cuda")
+    yd = torch.zeros_like(xd)
+    for _ in range(3):
+        sgiga.sgiga_apply(P.handle, xd, yd)
+    d0, d1 = _events(torch)
+    torch.cuda.synchronize()
+    d0.record(stream)
+    for _ in range(10):
+        sgiga.sgiga_apply(P.handle, xd, yd)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    apply64_s = d0.elapsed_time(d1) / 10 / 1e3
+    flops64 = apply_flops(P)
+    roofline_fp64 = {"bound": "alu", "achieved": flops64 / apply64_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": flops64 / apply64_s / 1e12 / fp64_peak, "traffic": None,
+                     "kernel": "k_op3<double,3,0,false> (FP64 residual apply of the refinement, general metric)",
+                     "apply_ms": apply64_s * 1e3, "algorithmic_flops": flops64,
+                     "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU"}
+
     # end to end through the C ABI with host buffers (pinned): f, points in; u out
     f_h = torch.ones(nqp, dtype=torch.float64).pin_memory()
     pts_pin = torch.as_tensor(W.pts_h).pin_memory()
@@ -765,7 +791,7 @@ def run_ours(args):
     del f_h, pts_pin, u_pin
     torch.cuda.synchronize()
 
-    cube = None if args.quick else cube_line(sgiga, torch, stream, 10)
+    cube = None if args.quick else cube_line(sgiga, torch, stream, 10, peak=fp64_peak)
     cpu = cpu_par = None
     if rank == 0 and not args.quick:
         r = run_oracle_sample(0)
@@ -794,7 +820,7 @@ def run_ours(args):
                          "outer_iterations": max(s.iterations for s in stats),
                          "inner_iterations": max(s.inner_iterations for s in stats)},
             "phases_ms": phases, "setup": setup, "autotune": tuning, "comparison": comparison,
-            "roofline": roofline,
+            "roofline": roofline, "roofline_fp64_residual": roofline_fp64,
             "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
             "e2e": {"value": whole_job_rate(ndof, world, e2e_s), "unit": "DoF/s",
                     "h2d_bytes_per_step": int(nqp * 8 + npts * 3 * 8), "d2h_bytes_per_step": int(npts * 8)},
