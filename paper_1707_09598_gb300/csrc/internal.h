@@ -130,20 +130,21 @@ enum { FD_SMALL = 0, FD_ROWS = 1, FD_TILE = 2, FD_LEVEL = 3 };
 
 // Columns per FD_SMALL item for a direction of n <= 64 functions: the n x n
 // matrix and an n x cols tile of fibres (rows padded by one) fill at most 48 KB
-// of FP64 shared memory (6144 doubles); at most 256.
+// of FP64 shared memory (6144 doubles); at most 2048 (for n = 3 a tile of 256
+// fibres gave each block only 3 outputs per thread).
 #ifdef __CUDACC__
 __host__ __device__
 #endif
 inline int fd_small_cols(int n) {
     const int c = (6144 - n * (n + 1)) / (n + 1) - 1;
-    return c < 256 ? (c < 1 ? 1 : c) : 256;
+    return c < 2048 ? (c < 1 ? 1 : c) : 2048;
 }
 struct FDItem {
     int grid;
     int mode;
     int nc;             // FD_ROWS: columns of the group (1..8)
     int i0;             // first row (output index along the direction)
-    long long c0;       // first column of the segment; FD_SMALL: first packed output
+    long long c0;       // first column of the segment (FD_SMALL: of the piece's fibres)
     int j0, j1;         // contraction range [j0, j1) (split K: partial sums are added atomically)
 };
 
