@@ -356,7 +356,11 @@ typedef struct {
     double solve_ms_fp64, solve_ms_mixed;
     /* FP64 PCG preconditioned by the FP32 FD (narrowed residual, widened
      * output, flexible CG), the third probe: its time (ms; 0 as above), and 1
-     * when it was the fastest and sgiga_solve now runs it. */
+     * when it was the fastest and sgiga_solve now runs it. It is run only if
+     * it was the fastest to 1e-8 and is also not slower than FP64 PCG with
+     * the FP64 preconditioner to 1e-12 (a second pair of probe solves, not
+     * reported): the FP32 rounding of the preconditioned residual costs extra
+     * iterations near FP64 tolerances. */
     double solve_ms_fp64_fd32;
     int solve_fp32_precond;
 } sgiga_tune_result;

@@ -1395,8 +1395,12 @@ int sgiga_precond_f32(sgiga_plan_t P, const float* r, float* z) {
 // FP64 PCG, both to a relative residual of 1e-8 on a probe load vector (the
 // plan's own if it is set, else that of f = 1), each timed after one run that
 // captures its graphs; sgiga_solve then runs the faster. FP64 PCG gets at most
-// the iterations that fit in the mixed solve's time. The plan's load vector
-// and solution are restored.
+// the iterations that fit in the mixed solve's time. FP64 PCG with the FP32
+// preconditioner is kept only if it is also not slower than with the FP64 one
+// to 1e-12: the FP32 rounding of z limits how much each flexible-CG step can
+// gain, so a tie at 1e-8 (the unit cube, where FD is exact) turns into extra
+// iterations at FP64 tolerances. The plan's load vector and solution are
+// restored.
 static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx, double* ms6432) {
     *ms64 = *msmx = *ms6432 = 0.0;
     P->solve_fp64 = false;
@@ -1421,9 +1425,10 @@ static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx, double*
             int r = run_rhs_operator(P);
             if (r) return r;
         }
-        auto timed = [&](int maxit, int& code) {
+        sgiga_solve_stats st{};
+        auto timed = [&](int maxit, int& code, double tol = 1e-8) {
             const auto t0 = std::chrono::steady_clock::now();
-            code = sgiga_solve(P, 1e-8, maxit, nullptr);
+            code = sgiga_solve(P, tol, maxit, &st);
             return since(t0) * 1e3;
         };
         int c = 0;
@@ -1433,7 +1438,7 @@ static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx, double*
         if (c != SGIGA_OK) tm = 1e30;
         // FP64 PCG with the FP64, then with the FP32 preconditioner
         double best = tm, tfp[2] = {0.0, 0.0};
-        int pick = -1;
+        int pick = -1, its[2] = {0, 0};
         for (int v = 0; v < 2; ++v) {
             P->solve_fp64 = true;
             P->fp64_fd32 = v == 1;
@@ -1447,8 +1452,24 @@ static int choose_precision(sgiga_plan_s* P, double* ms64, double* msmx, double*
             if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = P->fp64_fd32 = false; return c; }
             if (c == SGIGA_OK) {
                 tfp[v] = t64;
+                its[v] = st.iterations;
                 if (t64 < best) { best = t64; pick = v; }
             }
+        }
+        if (pick == 1 && tfp[0] > 0.0) {
+            // both FP64 variants converged to 1e-8: the FP32 preconditioner
+            // must keep up to 1e-12 as well (each gets three times its 1e-8
+            // iterations, plus four, after one untimed run)
+            double t12[2] = {1e30, 1e30};
+            for (int v = 0; v < 2; ++v) {
+                P->fp64_fd32 = v == 1;
+                const int cap = 3 * its[v] + 4;
+                timed(cap, c, 1e-12);
+                const double t = timed(cap, c, 1e-12);
+                if (c != SGIGA_OK && c != SGIGA_ERR_NOT_CONVERGED) { P->solve_fp64 = P->fp64_fd32 = false; return c; }
+                if (c == SGIGA_OK) t12[v] = t;
+            }
+            if (t12[1] >= t12[0]) pick = 0;
         }
         *msmx = tm;
         *ms64 = tfp[0];
