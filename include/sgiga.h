@@ -440,6 +440,22 @@ int sgiga_map_points(sgiga_plan_t plan, const double* xi, const int* patch, long
  * (eq. TD-combi-tec). u_comp [ngrids][npts], u [npts], host or device. */
 int sgiga_combine(sgiga_plan_t plan, const double* u_comp, long long npts, double* u);
 
+/* The same compensated sum over the components of several plans, each with
+ * its own combination coefficients: u[j] = sum_k sum_g c_{k,g} u_comp_k[g][j].
+ * u_comp holds the plans' sgiga_eval outputs one after the other, in the
+ * order of plans[] ([sum_k ngrids_k][npts]); u [npts]; host or device.
+ * Serves combinations whose components differ in more than their levels, as
+ * the h-p sparse combination does (components of several degrees at one
+ * continuity, one plan per degree, coefficients from the combination of a
+ * downward-closed set of (levels, degree) indices: eq. Delta-combi-tec with
+ * the degree as one more index; the paper names p- and h-p-sparsification as
+ * possible in Sec. 2.2 and as an extension in Sec. 5). The plans must have
+ * the same dimension d and share one stream (SGIGA_ERR_ARG otherwise); that
+ * they discretise the same problem is the caller's responsibility. Runs on
+ * that stream and synchronises it; uses the first plan's staging buffer. */
+int sgiga_combine_plans(int nplans, const sgiga_plan_t* plans /* host [nplans] */, const double* u_comp,
+                        long long npts, double* u);
+
 /* Diagnostics for parity tests (host outputs). The 1D table of direction
  * `dir` (0-based) at level `level`: Gauss points xi [E(p+1)], weights w
  * [E(p+1)] (times h/2), basis values R and derivatives dR [E(p+1)][p+1] of the

@@ -30,6 +30,9 @@ Modules
                in the paper; the CUDA learned preconditioner's definition)
   problems     manufactured solutions; f = -Laplace(u) derived symbolically
   driver       whole-method runs: solve every component, evaluate, combine
+  hp           h-p sparse combination: the degree as one more combination
+               index at one continuity (named as possible in Sec. 2.2 and 5;
+               the reading is stated in the module)
 
 Parity status: every function is pinned by tests under tests/ (closed forms,
 identities of the paper, brute force, convergence rates); none is unpinned.

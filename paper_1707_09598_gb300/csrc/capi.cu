@@ -1894,6 +1894,48 @@ int sgiga_combine(sgiga_plan_t P, const double* ucomp, long long npts, double* u
     return SGIGA_OK;
 }
 
+int sgiga_combine_plans(int nplans, const sgiga_plan_t* plans, const double* ucomp, long long npts, double* u) {
+    NvtxRange nvtx_("sgiga_combine_plans");
+    if (nplans < 1 || !plans) return fail(SGIGA_ERR_ARG, "nplans must be >= 1 with the plans given");
+    if (npts < 0) return fail(SGIGA_ERR_ARG, "npts < 0");
+    size_t ng = 0;
+    for (int k = 0; k < nplans; ++k) {
+        if (!plans[k]) return fail(SGIGA_ERR_ARG, "null plan");
+        if (plans[k]->d != plans[0]->d) return fail(SGIGA_ERR_ARG, "plans differ in dimension");
+        if (plans[k]->stream != plans[0]->stream) return fail(SGIGA_ERR_ARG, "plans must share one stream");
+        ng += plans[k]->comps.size();
+    }
+    if (ng > (size_t)INT32_MAX) return fail(SGIGA_ERR_ARG, "too many components");
+    if (npts == 0) return SGIGA_OK;
+    if (!ucomp || !u) return fail(SGIGA_ERR_ARG, "null argument");
+    sgiga_plan_s* P = plans[0];
+    const size_t cb = (ng * 8 + 15) / 16 * 16, ub = (size_t)npts * ng * 8, ob = (size_t)npts * 8;
+    const bool idev = is_device(ucomp), odev = is_device(u);
+    int rc = ensure_stage(P, cb + (idev ? 0 : ub) + (odev ? 0 : ob));
+    if (rc) return rc;
+    char* st = (char*)P->stage;
+    // every plan's coefficients, in plan order, as one device array
+    double* coef = (double*)st;
+    st += cb;
+    size_t off = 0;
+    for (int k = 0; k < nplans; ++k) {
+        const size_t n = plans[k]->comps.size();
+        if (n) CUDA_TRY(cudaMemcpyAsync(coef + off, plans[k]->d_coef, n * 8, cudaMemcpyDeviceToDevice, P->stream));
+        off += n;
+    }
+    const double* ud = ucomp;
+    if (!idev) {
+        CUDA_TRY(cudaMemcpyAsync(st, ucomp, ub, cudaMemcpyHostToDevice, P->stream));
+        ud = (const double*)st;
+        st += ub;
+    }
+    double* od = odev ? u : (double*)st;
+    CUDA_TRY(launch_combine_n((int)ng, ud, npts, coef, od, P->stream));
+    if (!odev) CUDA_TRY(cudaMemcpyAsync(u, od, ob, cudaMemcpyDeviceToHost, P->stream));
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return SGIGA_OK;
+}
+
 int sgiga_basis_table(sgiga_plan_t P, int dir, int level, double* xi, double* w, double* R, double* dR,
                       int* first) {
     if (!P) return fail(SGIGA_ERR_ARG, "null argument");

@@ -129,6 +129,14 @@ cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts
     return cudaGetLastError();
 }
 
+cudaError_t launch_combine_n(int ng, const double* ucomp, long long npts, const double* coef, double* u,
+                             cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    SGIGA_COUNT_LAUNCH();
+    k_combine<<<(unsigned)((npts + 31) / 32), 256, 0, s>>>(ng, ucomp, npts, coef, u);
+    return cudaGetLastError();
+}
+
 }  // namespace sgiga
 
 namespace sgiga {

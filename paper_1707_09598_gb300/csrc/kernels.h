@@ -234,5 +234,8 @@ cudaError_t launch_eval(const DevPlan& P, const double* coeffs, const double* xi
                         int* first, double* ucomp, cudaStream_t s);
 cudaError_t launch_combine(const DevPlan& P, const double* ucomp, long long npts, const double* coef,
                            double* u, cudaStream_t s);
+// the same sum over ng value rows with caller-given coefficients (several plans)
+cudaError_t launch_combine_n(int ng, const double* ucomp, long long npts, const double* coef, double* u,
+                             cudaStream_t s);
 
 }  // namespace sgiga

@@ -136,6 +136,7 @@ _SIGS = {
     "sgiga_functional": (_I, [_P, _P, _P, _P]),
     "sgiga_set_dirichlet": (_I, [_P, _P]),
     "sgiga_combine": (_I, [_P, _P, _L, _P]),
+    "sgiga_combine_plans": (_I, [_I, ctypes.POINTER(_P), _P, _L, _P]),
     "sgiga_basis_table": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "sgiga_geometry_coeffs": (_I, [_P, _I, _P, _P]),
     "sgiga_fd_eigen": (_I, [_P, _I, _I, _P, _P]),
@@ -409,6 +410,13 @@ def sgiga_set_dirichlet(plan, g):
 def sgiga_combine(plan, u_comp, npts, u):
     info = sgiga_plan_info(plan)
     _check(_lib.sgiga_combine(plan, _ptr(u_comp, npts * info.ngrids), int(npts), _ptr(u, npts)))
+
+
+def sgiga_combine_plans(plans, u_comp, npts, u):
+    """plans: handles; u_comp: their sgiga_eval outputs, concatenated in that order."""
+    ng = sum(sgiga_plan_info(h).ngrids for h in plans)
+    arr = (_P * len(plans))(*plans)
+    _check(_lib.sgiga_combine_plans(len(plans), arr, _ptr(u_comp, npts * ng), int(npts), _ptr(u, npts)))
 
 
 def sgiga_basis_table(plan, dir, level):
