@@ -622,10 +622,9 @@ int sgiga_net_load(sgiga_plan_t plan, const char* path);
  * library, held until the process exits). Grids with more than
  * SGIGA_NOALLOC_MAX_DOFS entries are rejected with SGIGA_ERR_ARG. The call
  * allocates nothing. The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. The looked-up address stays valid while the
- * device's primary context lives: after a cudaDeviceReset the entry point must
- * not be called again on that device. All calls share the array, so calls that
+ * address (cudaGetSymbolAddress) with that device current. The looked-up
+ * address stays valid while the device's primary context lives: after a
+ * cudaDeviceReset the entry point must not be called again on that device. All calls share the array, so calls that
  * overlap on the GPU race on it: order them on one stream. Returns SGIGA_OK,
  * SGIGA_ERR_ARG or SGIGA_ERR_CUDA (message in sgiga_last_error()). */
 #define SGIGA_NOALLOC_MAX_DOFS 262144
